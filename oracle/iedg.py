@@ -1,0 +1,269 @@
+"""IEDG residuals, Newton blocks, static condensation and trace assembly
+(oracle, test infrastructure only).
+
+Weak form (Eq. IEDG a-c), test functions r = phi_a e_(i,j), w = phi_a e_i,
+mu = mu_t e_i.  With w = W_g detJ at volume points, wf = W_f |n dS| at face points:
+
+  R_q[a,i,j] =  sum_g w q_ij phi_a + sum_g w u_i dphi_a/dx_j
+               - sum_faces sum_gf wf uhat_i n_j phi_a                        (IEDG a)
+  R_u[a,i]   =  alpha sum_g w (u - u_ref)_i phi_a - sum_g w F_ij dphi_a/dx_j
+               + sum_faces sum_gf wf fhat_i phi_a - sum_g w s_i phi_a         (IEDG b)
+  R_fl[t,i]  =  sum_elements sum_faces sum_gf wf fhat_i mu_t                  (IEDG c)
+
+Readings (the design doc lists them): the DIRK stage (Sec. 2.1, last paragraph) enters
+as alpha M (u - u_ref) with alpha = 1 / (a_ii dt); the trace space is continuous
+across interior and periodic faces, its basis on a face being the element basis
+restricted to that face (trace slot s <-> boundary node bnodes[s]); the source s
+is a given function of position (used by the manufactured-solution test only).
+
+Newton system (Sec. 2.2.1): [A B; C D] [dZ; dU] = [F; G] with Z = (q, u),
+A = dR_NS/dZ, B = dR_NS/dU, C = dR_FL/dZ, D = dR_FL/dU, F = -R_NS, G = -R_FL.
+A is block diagonal over elements, so (Eq. LS)
+  K = D - C A^-1 B,   R = G - C A^-1 F,   dZ = A^-1 (F - B dU).
+Element unknown ordering used here: q first, index (i d + j) Np + a; then u,
+index n_q + i Np + a.  Trace unknowns: i Nb + s.  Outputs are reshaped to
+node-major layouts at the end: K_e[s, i, t, k], R_e[s, i], du[a, i], dq[a, i, j].
+"""
+import numpy as np
+import scipy.linalg
+
+from . import physics
+
+
+class Problem:
+    def __init__(self, ref, geo, elem_trace, n_trace, prm, source=None):
+        """ref: RefElement, geo: Geometry, elem_trace [E, Nb] global trace ids,
+        prm: physics.Params, source: optional callable x[..., d] -> s[..., m]."""
+        self.ref, self.geo, self.prm = ref, geo, prm
+        self.d = ref.d
+        self.m = ref.d + 2
+        self.elem_trace = np.asarray(elem_trace, dtype=np.int64)
+        self.n_trace = int(n_trace)
+        self.fmu = ref.fphi[:, :, ref.bnodes]               # [nf, Nfq, Nb]
+        self.source = source
+
+    # ------------------------------------------------------------------ points
+    def points(self, els, u, q, uhat):
+        """Interpolate the element states to volume and face points."""
+        ref = self.ref
+        ue, qe = u[els], q[els]
+        uh_e = uhat[self.elem_trace[els]]                       # [E, Nb, m]
+        P = {}
+        P["u"] = np.einsum("ga,eai->egi", ref.phi, ue)
+        P["q"] = np.einsum("ga,eaij->egij", ref.phi, qe)
+        P["uf"] = np.einsum("fga,eai->efgi", ref.fphi, ue)
+        P["qf"] = np.einsum("fga,eaij->efgij", ref.fphi, qe)
+        P["uhf"] = np.einsum("fgs,esi->efgi", self.fmu, uh_e)
+        return P
+
+    # --------------------------------------------------------------- residual
+    def residual(self, u, q, uhat, u_ref=None, els=None):
+        """Returns R_q [E, Np, m, d], R_u [E, Np, m], Rhat_e [E, Nb, m] (each element's
+        own contribution to R_fl) and R_fl [n_trace, m] (sum over all elements)."""
+        ref, geo, prm, d, m = self.ref, self.geo, self.prm, self.d, self.m
+        if els is None:
+            els = np.arange(geo.E)
+        els = np.asarray(els)
+        P = self.points(els, u, q, uhat)
+        w, gphi = geo.w[els], geo.gphi[els]
+        wf, nf = geo.wf[els], geo.nf[els]
+        F, _, _ = physics.flux_with_jacobians(P["u"], P["q"], prm, d)
+        fh, _, _, _ = physics.numerical_flux_with_jacobians(P["uhf"], P["uf"], P["qf"], nf, prm, d)
+        Rq = (np.einsum("eg,egij,ga->eaij", w, P["q"], ref.phi)
+              + np.einsum("eg,egi,ejga->eaij", w, P["u"], gphi)
+              - np.einsum("efg,efgi,efgj,fga->eaij", wf, P["uhf"], nf, ref.fphi))
+        Ru = (-np.einsum("eg,egij,ejga->eai", w, F, gphi)
+              + np.einsum("efg,efgi,fga->eai", wf, fh, ref.fphi))
+        if prm.alpha != 0.0:
+            uref_pts = P["u"] if u_ref is None else np.einsum("ga,eai->egi", ref.phi, u_ref[els])
+            Ru = Ru + prm.alpha * np.einsum("eg,egi,ga->eai", w, P["u"] - uref_pts, ref.phi)
+        if self.source is not None:
+            s = self.source(geo.xq[els])
+            Ru = Ru - np.einsum("eg,egi,ga->eai", w, s, ref.phi)
+        Rhat_e = np.einsum("efg,efgi,fgs->esi", wf, fh, self.fmu)
+        Rfl = np.zeros((self.n_trace, m))
+        np.add.at(Rfl, self.elem_trace[els].reshape(-1), Rhat_e.reshape(-1, m))
+        return Rq, Ru, Rhat_e, Rfl
+
+    def geometric_blocks(self, e):
+        """Mass M, B_j[a,b] = sum_g w dphi_a/dx_j phi_b, E_j[a,t] = sum wf n_j phi_a mu_t."""
+        ref, geo = self.ref, self.geo
+        M = geo.M[e]
+        Bj = np.einsum("g,jga,gb->jab", geo.w[e], geo.gphi[e], ref.phi)
+        Ej = np.einsum("fg,fgj,fga,fgt->jat", geo.wf[e], geo.nf[e], ref.fphi, self.fmu)
+        return M, Bj, Ej
+
+    def solve_q(self, u, uhat):
+        """q with R_q = 0 on every element: q_ij = M^-1 (E_j uhat_i - B_j u_i)."""
+        E, Np, m, d = self.geo.E, self.ref.Np, self.m, self.d
+        q = np.zeros((E, Np, m, d))
+        for e in range(E):
+            M, Bj, Ej = self.geometric_blocks(e)
+            uh_e = uhat[self.elem_trace[e]]
+            for j in range(d):
+                q[e, :, :, j] = np.linalg.solve(M, Ej[j] @ uh_e - Bj[j] @ u[e])
+        return q
+
+    # ------------------------------------------------------------ Newton blocks
+    def element_blocks(self, e, u, q, uhat, u_ref=None):
+        """Dense Newton blocks of element e in the ordering of the module docstring.
+        Returns dict with A_qq, A_qu, B_q, A_uq, A_uu, B_u, C_q, C_u, D, F_q, F_u, G."""
+        ref, geo, prm, d, m = self.ref, self.geo, self.prm, self.d, self.m
+        Np, Nb = ref.Np, ref.Nb
+        els = np.array([e])
+        P = self.points(els, u, q, uhat)
+        _, Fu, Fq = physics.flux_with_jacobians(P["u"][0], P["q"][0], prm, d)
+        _, fuh, fu, fq = physics.numerical_flux_with_jacobians(
+            P["uhf"][0], P["uf"][0], P["qf"][0], geo.nf[e], prm, d)
+        w, gphi, wf = geo.w[e], geo.gphi[e], geo.wf[e]
+        phi, fphi, fmu = ref.phi, ref.fphi, self.fmu
+        M, Bj, Ej = self.geometric_blocks(e)
+        I_m = np.eye(m)
+        I_d = np.eye(d)
+        blk = {}
+        # q-equation rows (IEDG a): linear, geometry only
+        blk["A_qq"] = np.einsum("ik,jl,ab->ijaklb", I_m, I_d, M).reshape(m * d * Np, m * d * Np)
+        blk["A_qu"] = np.einsum("ik,jab->ijakb", I_m, Bj).reshape(m * d * Np, m * Np)
+        blk["B_q"] = -np.einsum("ik,jat->ijakt", I_m, Ej).reshape(m * d * Np, m * Nb)
+        # u-equation rows (IEDG b)
+        A_uq = (-np.einsum("g,jga,gijkl,gb->iaklb", w, gphi, Fq, phi)
+                + np.einsum("fg,fga,fgikl,fgb->iaklb", wf, fphi, fq, fphi))
+        A_uu = (-np.einsum("g,jga,gijk,gb->iakb", w, gphi, Fu, phi)
+                + np.einsum("fg,fga,fgik,fgb->iakb", wf, fphi, fu, fphi))
+        A_uu = A_uu + prm.alpha * np.einsum("ik,ab->iakb", I_m, M)
+        blk["A_uq"] = A_uq.reshape(m * Np, m * d * Np)
+        blk["A_uu"] = A_uu.reshape(m * Np, m * Np)
+        blk["B_u"] = np.einsum("fg,fga,fgik,fgt->iakt", wf, fphi, fuh, fmu).reshape(m * Np, m * Nb)
+        # trace rows (IEDG c)
+        blk["C_q"] = np.einsum("fg,fgs,fgikl,fgb->isklb", wf, fmu, fq, fphi).reshape(m * Nb, m * d * Np)
+        blk["C_u"] = np.einsum("fg,fgs,fgik,fgb->iskb", wf, fmu, fu, fphi).reshape(m * Nb, m * Np)
+        blk["D"] = np.einsum("fg,fgs,fgik,fgt->iskt", wf, fmu, fuh, fmu).reshape(m * Nb, m * Nb)
+        Rq, Ru, Rhat_e, _ = self.residual(u, q, uhat, u_ref, els=els)
+        blk["F_q"] = -np.transpose(Rq[0], (1, 2, 0)).reshape(-1)        # (i, j, a)
+        blk["F_u"] = -np.transpose(Ru[0], (1, 0)).reshape(-1)         # (i, a)
+        blk["G"] = -np.transpose(Rhat_e[0], (1, 0)).reshape(-1)          # (i, s)
+        blk["M"], blk["Bj"], blk["Ej"] = M, Bj, Ej
+        return blk
+
+    def full_system(self, blk):
+        A = np.block([[blk["A_qq"], blk["A_qu"]], [blk["A_uq"], blk["A_uu"]]])
+        B = np.vstack([blk["B_q"], blk["B_u"]])
+        C = np.hstack([blk["C_q"], blk["C_u"]])
+        F = np.concatenate([blk["F_q"], blk["F_u"]])
+        return A, B, C, blk["D"], F, blk["G"]
+
+    def _to_node_major(self, Kc, Rc):
+        m, Nb = self.m, self.ref.Nb
+        K = Kc.reshape(m, Nb, m, Nb).transpose(1, 0, 3, 2)   # [s, i, t, k]
+        R = Rc.reshape(m, Nb).T                               # [s, i]
+        return K, R
+
+    # -------------------------------------------------------------- condensation
+    def condense_full(self, e, u, q, uhat, u_ref=None):
+        """Definition: K_e = D - C A^-1 B, R_e = G - C A^-1 F with the dense element
+        block A factored by LU with partial pivoting (LAPACK getrf: largest |a|,
+        first index on ties)."""
+        blk = self.element_blocks(e, u, q, uhat, u_ref)
+        A, B, C, D, F, G = self.full_system(blk)
+        lu = scipy.linalg.lu_factor(A)
+        X = scipy.linalg.lu_solve(lu, np.column_stack([B, F]))
+        K = D - C @ X[:, :-1]
+        R = G - C @ X[:, -1]
+        return self._to_node_major(K, R)
+
+    def qelim(self, blk):
+        """Exact elimination of q (A_qq = M (x) I): dq_kl = M^-1 F_q,kl - G_l du_k + H_l dU_k
+        with G_l = M^-1 B_l, H_l = M^-1 E_l.  Returns At, Bt, Ct, Dt, Ft, Gt."""
+        m, d = self.m, self.d
+        Np, Nb = self.ref.Np, self.ref.Nb
+        M = blk["M"]
+        Gl = np.stack([np.linalg.solve(M, blk["Bj"][j]) for j in range(d)])    # [d, Np, Np]
+        Hl = np.stack([np.linalg.solve(M, blk["Ej"][j]) for j in range(d)])    # [d, Np, Nb]
+        Fq = blk["F_q"].reshape(m, d, Np)
+        MFq = np.stack([[np.linalg.solve(M, Fq[k, l]) for l in range(d)] for k in range(m)])
+        A_uq = blk["A_uq"].reshape(m * Np, m, d, Np)
+        C_q = blk["C_q"].reshape(m * Nb, m, d, Np)
+        At = blk["A_uu"] - np.einsum("rklc,lcb->rkb", A_uq, Gl).reshape(m * Np, m * Np)
+        Bt = blk["B_u"] + np.einsum("rklc,lct->rkt", A_uq, Hl).reshape(m * Np, m * Nb)
+        Ft = blk["F_u"] - np.einsum("rklc,klc->r", A_uq, MFq)
+        Ct = blk["C_u"] - np.einsum("rklc,lcb->rkb", C_q, Gl).reshape(m * Nb, m * Np)
+        Dt = blk["D"] + np.einsum("rklc,lct->rkt", C_q, Hl).reshape(m * Nb, m * Nb)
+        Gt = blk["G"] - np.einsum("rklc,klc->r", C_q, MFq)
+        return At, Bt, Ct, Dt, Ft, Gt, Gl, Hl, MFq
+
+    def condense_qelim(self, e, u, q, uhat, u_ref=None):
+        """Same K_e, R_e through the q-eliminated element system:
+        K_e = Dt - Ct At^-1 Bt, R_e = Gt - Ct At^-1 Ft."""
+        blk = self.element_blocks(e, u, q, uhat, u_ref)
+        At, Bt, Ct, Dt, Ft, Gt = self.qelim(blk)[:6]
+        lu = scipy.linalg.lu_factor(At)
+        X = scipy.linalg.lu_solve(lu, np.column_stack([Bt, Ft]))
+        K = Dt - Ct @ X[:, :-1]
+        R = Gt - Ct @ X[:, -1]
+        return self._to_node_major(K, R)
+
+    # ------------------------------------------------------------ back-substitution
+    def back_substitute_full(self, e, u, q, uhat, duhat, u_ref=None):
+        """dZ_e = A^-1 (F - B dU_e).  Returns du [Np, m], dq [Np, m, d]."""
+        m, d, Np = self.m, self.d, self.ref.Np
+        blk = self.element_blocks(e, u, q, uhat, u_ref)
+        A, B, C, D, F, G = self.full_system(blk)
+        dU = duhat[self.elem_trace[e]].T.reshape(-1)          # (i, s)
+        dZ = np.linalg.solve(A, F - B @ dU)
+        nq = m * d * Np
+        dq = dZ[:nq].reshape(m, d, Np).transpose(2, 0, 1)
+        du = dZ[nq:].reshape(m, Np).T
+        return du, dq
+
+    def back_substitute_qelim(self, e, u, q, uhat, duhat, u_ref=None):
+        m, d, Np = self.m, self.d, self.ref.Np
+        blk = self.element_blocks(e, u, q, uhat, u_ref)
+        At, Bt, Ct, Dt, Ft, Gt, Gl, Hl, MFq = self.qelim(blk)
+        dU = duhat[self.elem_trace[e]]                         # [Nb, m]
+        du = np.linalg.solve(At, Ft - Bt @ dU.T.reshape(-1)).reshape(m, Np)   # [k, b]
+        dq = np.zeros((Np, m, d))
+        for k in range(m):
+            for l in range(d):
+                dq[:, k, l] = MFq[k, l] - Gl[l] @ du[k] + Hl[l] @ dU[:, k]
+        return du.T, dq
+
+
+# ------------------------------------------------------------------ trace matrix
+def bsr_pattern(elem_trace, n_trace):
+    """Block compressed rows of K (Sec. 2.2.2): one block row per trace node, a block
+    (r, c) for every pair of trace nodes that share an element, columns sorted."""
+    et = np.asarray(elem_trace, dtype=np.int64)
+    rows = np.repeat(et, et.shape[1], axis=1).reshape(-1)
+    cols = np.tile(et, (1, et.shape[1])).reshape(-1)
+    key = np.unique(rows * n_trace + cols)
+    r = key // n_trace
+    c = key % n_trace
+    row_ptr = np.zeros(n_trace + 1, dtype=np.int64)
+    np.add.at(row_ptr, r + 1, 1)
+    row_ptr = np.cumsum(row_ptr)
+    return row_ptr, c.astype(np.int64)
+
+
+def bsr_find(row_ptr, col, r, c):
+    lo, hi = row_ptr[r], row_ptr[r + 1]
+    k = lo + np.searchsorted(col[lo:hi], c)
+    assert col[k] == c
+    return k
+
+
+def assemble(elem_trace, n_trace, K_e, R_e, els=None):
+    """K = sum_e P_e^T K_e P_e, R = sum_e P_e^T R_e, summed in element order.
+    K_e [E, Nb, m, Nb, m] (s, i, t, k); returns values [nnzb, m, m] and R [n_trace, m]."""
+    et = np.asarray(elem_trace, dtype=np.int64)
+    row_ptr, col = bsr_pattern(et, n_trace)
+    m = K_e.shape[2]
+    vals = np.zeros((len(col), m, m))
+    R = np.zeros((n_trace, m))
+    els = range(len(K_e)) if els is None else els
+    for n, e in enumerate(els):
+        tr = et[e]
+        for s in range(len(tr)):
+            R[tr[s]] += R_e[n][s]
+            for t in range(len(tr)):
+                vals[bsr_find(row_ptr, col, tr[s], tr[t])] += K_e[n][s, :, t, :]
+    return row_ptr, col, vals, R

@@ -1,0 +1,225 @@
+"""Pointwise compressible Navier-Stokes physics for the oracle (test infrastructure only).
+
+Sec. 2.1 (Eq. NS and the definitions that follow it): u = (rho, rho v_j, rho E),
+q = grad u, flux F(u, q) = inviscid - viscous, with
+    tau_ij = (1/Re) (d_j v_i + d_i v_j - 2/3 delta_ij d_k v_k),
+    p      = (gamma - 1) rho (E - v_k v_k / 2).
+Readings (the paper is silent or garbled there):
+  * T is the specific internal energy e = E - v_k v_k / 2 (c_v = 1), so the
+    conductivity is gamma / (Re Pr);
+  * the heat-flux term is taken with the dissipative sign: the energy flux is
+        v_j (rho E + p) - v_i tau_ij - (gamma / (Re Pr)) d_j e .
+Numerical flux (Eq. IEDG d): fhat = F(uhat, q) . n + S (u - uhat) with the
+Lax-Friedrichs choice S = lambda I, lambda = |vhat . n| + chat evaluated at uhat.
+
+Jacobians are taken by forward-mode dual numbers (class Dual), independent of any
+hand-derived formula.
+"""
+import numpy as np
+
+
+class Dual:
+    """Forward-mode dual number: value v (any shape S) and tangent t (shape S + (n,))."""
+
+    __slots__ = ("v", "t")
+
+    def __init__(self, v, t):
+        self.v = np.asarray(v, dtype=np.float64)
+        self.t = np.asarray(t, dtype=np.float64)
+
+    @staticmethod
+    def const(v, n):
+        v = np.asarray(v, dtype=np.float64)
+        return Dual(v, np.zeros(v.shape + (n,)))
+
+    def _lift(self, o):
+        if isinstance(o, Dual):
+            return o
+        o = np.asarray(o, dtype=np.float64)
+        return Dual(o, np.zeros(o.shape + (self.t.shape[-1],)))
+
+    def __add__(self, o):
+        o = self._lift(o)
+        return Dual(self.v + o.v, self.t + o.t)
+
+    __radd__ = __add__
+
+    def __sub__(self, o):
+        o = self._lift(o)
+        return Dual(self.v - o.v, self.t - o.t)
+
+    def __rsub__(self, o):
+        return self._lift(o) - self
+
+    def __neg__(self):
+        return Dual(-self.v, -self.t)
+
+    def __mul__(self, o):
+        o = self._lift(o)
+        return Dual(self.v * o.v, self.t * o.v[..., None] + o.t * self.v[..., None])
+
+    __rmul__ = __mul__
+
+    def __truediv__(self, o):
+        o = self._lift(o)
+        inv = 1.0 / o.v
+        return Dual(self.v * inv,
+                    (self.t - o.t * (self.v * inv)[..., None]) * inv[..., None])
+
+    def __rtruediv__(self, o):
+        return self._lift(o) / self
+
+    def sqrt(self):
+        s = np.sqrt(self.v)
+        return Dual(s, self.t * (0.5 / s)[..., None])
+
+    def abs(self):
+        # d|x|/dx = sign(x), with sign(0) := 0
+        return Dual(np.abs(self.v), self.t * np.sign(self.v)[..., None])
+
+
+def seed(values):
+    """Turn a list of k value arrays (same shape) into k Duals with unit tangents."""
+    k = len(values)
+    out = []
+    for i, v in enumerate(values):
+        v = np.asarray(v, dtype=np.float64)
+        t = np.zeros(v.shape + (k,))
+        t[..., i] = 1.0
+        out.append(Dual(v, t))
+    return out
+
+
+class Params:
+    def __init__(self, gamma=1.4, Pr=0.72, Re=1.0e3, Minf=0.2, alpha=0.0):
+        self.gamma, self.Pr, self.Re, self.Minf, self.alpha = gamma, Pr, Re, Minf, alpha
+
+
+def flux(u, q, prm, d):
+    """Navier-Stokes flux F[i][j] (list of lists, m x d) for conserved u[i] and
+    gradients q[i][j] = d u_i / d x_j (Sec. 2.1).  Works on floats, arrays or Duals."""
+    m = d + 2
+    g = prm.gamma
+    rho = u[0]
+    rE = u[m - 1]
+    v = [u[1 + i] / rho for i in range(d)]
+    E = rE / rho
+    vv = v[0] * v[0]
+    for i in range(1, d):
+        vv = vv + v[i] * v[i]
+    e = E - 0.5 * vv
+    p = (g - 1.0) * rho * e
+    # primitive gradients
+    dv = [[(q[1 + i][j] - v[i] * q[0][j]) / rho for j in range(d)] for i in range(d)]
+    dE = [(q[m - 1][j] - E * q[0][j]) / rho for j in range(d)]
+    de = []
+    for j in range(d):
+        t = dE[j]
+        for k in range(d):
+            t = t - v[k] * dv[k][j]
+        de.append(t)
+    div = dv[0][0]
+    for k in range(1, d):
+        div = div + dv[k][k]
+    inv_re = 1.0 / prm.Re
+    tau = [[None] * d for _ in range(d)]
+    for i in range(d):
+        for j in range(d):
+            t = dv[i][j] + dv[j][i]
+            if i == j:
+                t = t - (2.0 / 3.0) * div
+            tau[i][j] = inv_re * t
+    kappa = g / (prm.Re * prm.Pr)
+    F = [[None] * d for _ in range(m)]
+    for j in range(d):
+        F[0][j] = u[1 + j]
+        for i in range(d):
+            t = u[1 + i] * v[j] - tau[i][j]
+            if i == j:
+                t = t + p
+            F[1 + i][j] = t
+        t = v[j] * (rE + p) - kappa * de[j]
+        for i in range(d):
+            t = t - v[i] * tau[i][j]
+        F[m - 1][j] = t
+    return F
+
+
+def pressure(u, prm, d):
+    m = d + 2
+    rho = u[0]
+    vv = (u[1] / rho) * (u[1] / rho)
+    for i in range(1, d):
+        vv = vv + (u[1 + i] / rho) * (u[1 + i] / rho)
+    return (prm.gamma - 1.0) * (u[m - 1] - 0.5 * rho * vv)
+
+
+def lf_lambda(uh, n, prm, d):
+    """Lax-Friedrichs coefficient lambda = |vhat . n| + chat, chat^2 = gamma phat / rhohat."""
+    rho = uh[0]
+    vn = (uh[1] / rho) * n[0]
+    for j in range(1, d):
+        vn = vn + (uh[1 + j] / rho) * n[j]
+    p = pressure(uh, prm, d)
+    c = (prm.gamma * p / rho).sqrt() if isinstance(p, Dual) else np.sqrt(prm.gamma * p / rho)
+    return (vn.abs() if isinstance(vn, Dual) else np.abs(vn)) + c
+
+
+def numerical_flux(uh, u, q, n, prm, d):
+    """fhat_i = F_ij(uhat, q) n_j + lambda(uhat) (u_i - uhat_i)  (Eq. IEDG d, LF)."""
+    m = d + 2
+    F = flux(uh, q, prm, d)
+    lam = lf_lambda(uh, n, prm, d)
+    out = []
+    for i in range(m):
+        t = F[i][0] * n[0]
+        for j in range(1, d):
+            t = t + F[i][j] * n[j]
+        out.append(t + lam * (u[i] - uh[i]))
+    return out
+
+
+def flux_with_jacobians(u, q, prm, d):
+    """Volume points.  u: [..., m], q: [..., m, d].
+    Returns F [..., m, d], dF/du [..., m, d, m], dF/dq [..., m, d, m, d]."""
+    m = d + 2
+    shp = u.shape[:-1]
+    vals = [u[..., i] for i in range(m)] + [q[..., i, j] for i in range(m) for j in range(d)]
+    duals = seed(vals)
+    ud = duals[:m]
+    qd = [[duals[m + i * d + j] for j in range(d)] for i in range(m)]
+    F = flux(ud, qd, prm, d)
+    Fv = np.zeros(shp + (m, d))
+    Fu = np.zeros(shp + (m, d, m))
+    Fq = np.zeros(shp + (m, d, m, d))
+    for i in range(m):
+        for j in range(d):
+            Fv[..., i, j] = F[i][j].v
+            Fu[..., i, j, :] = F[i][j].t[..., :m]
+            Fq[..., i, j, :, :] = F[i][j].t[..., m:].reshape(shp + (m, d))
+    return Fv, Fu, Fq
+
+
+def numerical_flux_with_jacobians(uh, u, q, n, prm, d):
+    """Face points.  uh, u: [..., m], q: [..., m, d], n: [..., d] (unit).
+    Returns fhat [..., m], d/duhat [..., m, m], d/du [..., m, m], d/dq [..., m, m, d]."""
+    m = d + 2
+    shp = u.shape[:-1]
+    vals = ([uh[..., i] for i in range(m)] + [u[..., i] for i in range(m)]
+            + [q[..., i, j] for i in range(m) for j in range(d)])
+    duals = seed(vals)
+    uhd = duals[:m]
+    ud = duals[m:2 * m]
+    qd = [[duals[2 * m + i * d + j] for j in range(d)] for i in range(m)]
+    nn = [n[..., j] for j in range(d)]
+    fh = numerical_flux(uhd, ud, qd, nn, prm, d)
+    f = np.zeros(shp + (m,))
+    fuh = np.zeros(shp + (m, m))
+    fu = np.zeros(shp + (m, m))
+    fq = np.zeros(shp + (m, m, d))
+    for i in range(m):
+        f[..., i] = fh[i].v
+        fuh[..., i, :] = fh[i].t[..., :m]
+        fu[..., i, :] = fh[i].t[..., m:2 * m]
+        fq[..., i, :, :] = fh[i].t[..., 2 * m:].reshape(shp + (m, d))
+    return f, fuh, fu, fq

@@ -1,0 +1,284 @@
+"""Seeded synthetic meshes and flow states shaped like the paper's workloads.
+
+This module generates INPUTS only (mesh coordinates, element-to-trace maps, nodal
+states).  It holds none of the method's arithmetic: no basis, quadrature, flux,
+residual or Jacobian.  Both the CUDA library's tests and the CPU oracle's tests
+draw their inputs from here.
+
+Meshes are structured, periodic, tensor-product (quads in 2D, hexes in 3D).  The
+element nodes are placed at the Gauss-Lobatto-Legendre positions of degree p
+(here computed with numpy.polynomial, independently of the library and of the
+oracle) of the logical cell, then pushed through an optional smooth mapping.
+Trace ("high-order face") nodes are the lattice nodes lying on element faces;
+periodic faces are identified, so every face is interior.  Trace ids are assigned
+in lexicographic order (x fastest) of the global lattice position; an element's
+trace slots are its boundary nodes in lexicographic local order.
+"""
+import itertools
+from dataclasses import dataclass, field
+
+import numpy as np
+from numpy.polynomial import legendre as npleg
+
+GAMMA = 1.4
+DIRK33_A11 = 0.435866521508459      # diagonal coefficient of Alexander's L-stable DIRK(3,3)
+DT_STAR = 0.005                      # non-dimensional time step of the paper's runs
+
+
+def dirk_alpha(dt=DT_STAR, a11=DIRK33_A11):
+    return 1.0 / (a11 * dt)
+
+
+def gll_positions(p):
+    """-1, roots of P_p', +1 (node placement only)."""
+    if p == 1:
+        return np.array([-1.0, 1.0])
+    c = np.zeros(p + 1)
+    c[p] = 1.0
+    r = np.sort(np.real(npleg.legroots(npleg.legder(c))))
+    return np.concatenate([[-1.0], r, [1.0]])
+
+
+def _multi(n, d):
+    return [tuple(reversed(t)) for t in itertools.product(range(n), repeat=d)]
+
+
+@dataclass
+class Mesh:
+    d: int
+    p: int
+    N: tuple
+    node_xyz: np.ndarray        # [E, Np, d]
+    elem_trace: np.ndarray      # [E, Nb] int64
+    n_trace: int
+    bnodes: np.ndarray          # local node index of each trace slot
+    extent: tuple = field(default=None)
+
+    @property
+    def n_elem(self):
+        return self.node_xyz.shape[0]
+
+
+def structured_mesh(d, N, p, extent=None, mapping=None):
+    """Periodic structured mesh with N[r] cells in direction r on [0, extent[r])."""
+    N = tuple(int(n) for n in (N if np.ndim(N) else [N] * d))
+    extent = tuple(extent) if extent is not None else (1.0,) * d
+    assert all(n >= 2 for n in N), "at least two cells per direction"
+    xi = gll_positions(p)
+    nodes = _multi(p + 1, d)
+    cells = _multi(max(N), d)
+    cells = [c for c in cells if all(c[r] < N[r] for r in range(d))]
+    cells.sort(key=lambda c: tuple(reversed(c)))           # x fastest
+    E = len(cells)
+    Np = len(nodes)
+    X = np.zeros((E, Np, d))
+    bnodes = np.array([a for a, ai in enumerate(nodes) if any(t in (0, p) for t in ai)], dtype=np.int64)
+    L = [N[r] * p for r in range(d)]                        # lattice size per direction
+    lattice = np.zeros((E, len(bnodes), d), dtype=np.int64)
+    for e, c in enumerate(cells):
+        for a, ai in enumerate(nodes):
+            for r in range(d):
+                X[e, a, r] = (c[r] + 0.5 * (1.0 + xi[ai[r]])) * extent[r] / N[r]
+        for s, a in enumerate(bnodes):
+            ai = nodes[a]
+            lattice[e, s] = [(c[r] * p + ai[r]) % L[r] for r in range(d)]
+    if mapping is not None:
+        X = mapping(X)
+    # number the face-lattice nodes lexicographically (x fastest)
+    strides = np.cumprod([1] + L[:-1])
+    key = (lattice * strides).sum(-1)
+    uniq, inv = np.unique(key.reshape(-1), return_inverse=True)
+    elem_trace = inv.reshape(E, len(bnodes)).astype(np.int64)
+    return Mesh(d, p, N, X, elem_trace, len(uniq), bnodes, extent)
+
+
+def stretched_mapping(seed, ratio=50.0, shear=0.3):
+    """Smooth periodic-compatible map: y = eta - (beta / 2pi) sin(2 pi eta) with
+    (1 + beta) / (1 - beta) = ratio (boundary-layer-like grading), plus sinusoidal
+    shears of x and z.  detJ = 1 - beta cos(2 pi eta) > 0."""
+    rng = np.random.default_rng(seed)
+    ph1, ph2 = rng.uniform(0, 2 * np.pi, 2)
+    beta = (ratio - 1.0) / (ratio + 1.0)
+
+    def mapping(X):
+        Y = X.copy()
+        xi, eta = X[..., 0], X[..., 1]
+        Y[..., 1] = eta - beta / (2 * np.pi) * np.sin(2 * np.pi * eta)
+        Y[..., 0] = xi + shear / (2 * np.pi) * np.sin(2 * np.pi * eta + ph1)
+        if X.shape[-1] == 3:
+            Y[..., 2] = X[..., 2] + shear / (2 * np.pi) * np.sin(2 * np.pi * xi + ph2)
+        return Y
+    return mapping
+
+
+# ----------------------------------------------------------------------- states
+def conserved_from_primitive(rho, vel, p, gamma=GAMMA):
+    d = len(vel)
+    ke = 0.5 * rho * sum(v * v for v in vel)
+    return np.stack([rho] + [rho * v for v in vel] + [p / (gamma - 1.0) + ke], axis=-1)
+
+
+def freestream_field(d, Minf, gamma=GAMMA):
+    pinf = 1.0 / (gamma * Minf ** 2)
+
+    def f(x):
+        one = np.ones(x.shape[:-1])
+        vel = [one] + [0.0 * one for _ in range(d - 1)]
+        return conserved_from_primitive(one, vel, pinf * one, gamma)
+    return f
+
+
+def fourier_perturbed_field(d, Minf, seed, amp=0.01, kmax=3, gamma=GAMMA):
+    """Free stream (rho = 1, v = e_x, p = 1 / (gamma M^2)) plus, per conserved
+    variable i, amp * sigma_i * mean_k a_k sin(2 pi k.x + phi_k) over k in [1..kmax]^d."""
+    rng = np.random.default_rng(seed)
+    base = freestream_field(d, Minf, gamma)
+    m = d + 2
+    ks = np.array(list(itertools.product(range(1, kmax + 1), repeat=d)), dtype=np.float64)
+    a = rng.uniform(0.5, 1.0, (m, len(ks)))
+    ph = rng.uniform(0, 2 * np.pi, (m, len(ks)))
+    rhoE = base(np.zeros((1, d)))[0, -1]
+    sigma = np.ones(m)
+    sigma[-1] = rhoE
+
+    def f(x):
+        u = base(x)
+        arg = 2 * np.pi * np.einsum("...r,kr->...k", x, ks)
+        for i in range(m):
+            u[..., i] += amp * sigma[i] * np.mean(a[i] * np.sin(arg + ph[i]), axis=-1)
+        return u
+    return f
+
+
+def taylor_green_field(M0=0.2, gamma=GAMMA):
+    """3D Taylor-Green vortex on x' = 2 pi x (velocity amplitude 1, Mach M0)."""
+    p0 = 1.0 / (gamma * M0 ** 2)
+
+    def f(x):
+        X, Y, Z = (2 * np.pi * x[..., r] for r in range(3))
+        u = np.sin(X) * np.cos(Y) * np.cos(Z)
+        v = -np.cos(X) * np.sin(Y) * np.cos(Z)
+        w = 0.0 * X
+        p = p0 + (np.cos(2 * X) + np.cos(2 * Y)) * (np.cos(2 * Z) + 2.0) / 16.0
+        rho = p / p0
+        return conserved_from_primitive(rho, [u, v, w], p, gamma)
+    return f
+
+
+def broadband_field(Minf, seed, rms=0.05, kmin=1, kmax=8, gamma=GAMMA):
+    """Mach-Minf free stream along x plus a solenoidal random Fourier velocity field
+    over integer wavevectors 1 <= |k| <= kmax, shell energy ~ |k|^(-5/3), scaled to
+    `rms` of U_inf; rho = 1, p = p_inf."""
+    rng = np.random.default_rng(seed)
+    pinf = 1.0 / (gamma * Minf ** 2)
+    ks = [k for k in itertools.product(range(-kmax, kmax + 1), repeat=3)
+          if kmin ** 2 <= k[0] ** 2 + k[1] ** 2 + k[2] ** 2 <= kmax ** 2 and k > (0, 0, 0)]
+    ks = np.array(ks, dtype=np.float64)
+    kn = np.linalg.norm(ks, axis=1)
+    # random amplitude direction projected perpendicular to k (solenoidal)
+    a = rng.normal(size=(len(ks), 3))
+    a -= (np.einsum("kr,kr->k", a, ks) / kn ** 2)[:, None] * ks
+    a /= np.linalg.norm(a, axis=1)[:, None]
+    shell = np.round(kn).astype(int)
+    counts = np.bincount(shell)
+    amp = np.sqrt(kn ** (-5.0 / 3.0) / counts[shell])
+    ph = rng.uniform(0, 2 * np.pi, len(ks))
+    # per-component rms: <|v|^2> = scale^2 sum amp^2 / 2, shared by 3 components
+    scale = rms / np.sqrt(np.sum(amp ** 2) / 6.0)
+
+    def f(x):
+        arg = 2 * np.pi * np.einsum("...r,kr->...k", x, ks) + ph
+        s = np.sin(arg) * amp * scale
+        vel = np.einsum("...k,kr->...r", s, a)
+        one = np.ones(x.shape[:-1])
+        return conserved_from_primitive(one, [1.0 + vel[..., 0], vel[..., 1], vel[..., 2]],
+                                        pinf * one, gamma)
+    return f
+
+
+def fd_gradient(field, x, h=1e-5):
+    """Central-difference gradient of a conserved field at physical points x:
+    returns [..., m, d] (input-generation only)."""
+    d = x.shape[-1]
+    cols = []
+    for r in range(d):
+        dx = np.zeros(d)
+        dx[r] = h
+        cols.append((field(x + dx) - field(x - dx)) / (2 * h))
+    return np.stack(cols, axis=-1)
+
+
+@dataclass
+class State:
+    u: np.ndarray           # [E, Np, m]
+    q: np.ndarray           # [E, Np, m, d]
+    uhat: np.ndarray        # [n_trace, m]
+    u_ref: np.ndarray       # [E, Np, m] or None
+    duhat: np.ndarray       # [n_trace, m]  (stand-in trace increment for back-substitution)
+
+
+def make_state(mesh, field, seed, noise=0.0, uref_shift=0.0, gamma=GAMMA):
+    """u = field at the element nodes (+ per-node noise noise * sigma_i * U(-1, 1)),
+    q = central-difference gradient of the smooth field at the nodes, uhat = mean of
+    u over the element nodes that share each trace node, u_ref = u shifted by a small
+    seeded amount (None when uref_shift == 0), duhat = seeded small increment."""
+    rng = np.random.default_rng(seed)
+    X = mesh.node_xyz
+    u = field(X)
+    m = u.shape[-1]
+    sigma = np.ones(m)
+    sigma[-1] = np.abs(u[..., -1]).mean()
+    if noise:
+        u = u + noise * sigma * rng.uniform(-1.0, 1.0, u.shape)
+    q = fd_gradient(field, X)
+    acc = np.zeros((mesh.n_trace, m))
+    cnt = np.zeros(mesh.n_trace)
+    ub = u[:, mesh.bnodes, :]
+    np.add.at(acc, mesh.elem_trace.reshape(-1), ub.reshape(-1, m))
+    np.add.at(cnt, mesh.elem_trace.reshape(-1), 1.0)
+    uhat = acc / cnt[:, None]
+    u_ref = None
+    if uref_shift:
+        u_ref = u + uref_shift * sigma * rng.uniform(-1.0, 1.0, u.shape)
+    duhat = 1e-3 * sigma * rng.uniform(-1.0, 1.0, (mesh.n_trace, m))
+    return State(u, q, uhat, u_ref, duhat)
+
+
+# ---------------------------------------------------------------------- configs
+@dataclass
+class Workload:
+    name: str
+    mesh: Mesh
+    state: State
+    params: dict
+
+
+def config(index, seed=None, N=None):
+    """The synthetic workloads (1-based index).  `N` overrides the cell count for
+    scaled-down test variants of the same recipe."""
+    seed = 1000 + index if seed is None else seed
+    alpha = dirk_alpha()
+    if index == 1:
+        n = N or 8
+        mesh = structured_mesh(2, n, 2)
+        field = fourier_perturbed_field(2, 0.2, seed)
+        st = make_state(mesh, field, seed + 1)
+        prm = dict(gamma=GAMMA, Pr=0.72, Re=1.0e3, Minf=0.2, alpha=alpha)
+        return Workload(f"2D NS p=2 {n}x{n} periodic quads", mesh, st, prm)
+    if index in (2, 3):
+        n = N or 16
+        mapping = stretched_mapping(seed) if index == 3 else None
+        mesh = structured_mesh(3, n, 3, mapping=mapping)
+        field = taylor_green_field(0.2)
+        st = make_state(mesh, field, seed + 1, noise=0.01)
+        prm = dict(gamma=GAMMA, Pr=0.72, Re=2.5e5, Minf=0.2, alpha=alpha)
+        tag = " stretched/sheared (aspect 1-50)" if index == 3 else ""
+        return Workload(f"3D NS p=3 {n}^3 periodic hexes{tag}", mesh, st, prm)
+    if index == 5:
+        n = N or 24
+        mesh = structured_mesh(3, n, 4)
+        field = broadband_field(0.3, seed)
+        st = make_state(mesh, field, seed + 1)
+        prm = dict(gamma=GAMMA, Pr=0.72, Re=2.5e5, Minf=0.3, alpha=alpha)
+        return Workload(f"3D NS p=4 {n}^3 periodic hexes", mesh, st, prm)
+    raise ValueError(f"no synthetic workload {index}")

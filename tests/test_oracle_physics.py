@@ -1,0 +1,125 @@
+"""Pins of the oracle's pointwise physics (Sec. 2.1 flux definitions, Eq. IEDG d)
+against closed forms, exact invariants and finite differences."""
+import numpy as np
+import pytest
+
+from oracle import physics
+
+PRM = physics.Params(gamma=1.4, Pr=0.72, Re=100.0, Minf=0.3)
+
+
+def _state(d, rng):
+    rho = 1.0 + 0.2 * rng.random()
+    v = rng.normal(size=d) * 0.5
+    p = 3.0 + rng.random()
+    u = np.concatenate([[rho], rho * v, [p / 0.4 + 0.5 * rho * v @ v]])
+    q = rng.normal(size=(d + 2, d))
+    return u, q
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_euler_flux_homogeneity_and_eigenvalues(d):
+    """Inviscid flux is homogeneous of degree 1: (dF/du) u = F (exact for Euler);
+    the normal Jacobian has eigenvalues v.n (d-fold) and v.n +- c."""
+    rng = np.random.default_rng(d)
+    u, _ = _state(d, rng)
+    q0 = np.zeros((d + 2, d))
+    F, Fu, Fq = physics.flux_with_jacobians(u[None], q0[None], PRM, d)
+    np.testing.assert_allclose(np.einsum("ijk,k->ij", Fu[0], u), F[0], rtol=1e-13, atol=1e-13)
+    n = rng.normal(size=d)
+    n /= np.linalg.norm(n)
+    An = np.einsum("ijk,j->ik", Fu[0], n)
+    ev = np.sort(np.linalg.eigvals(An).real)
+    rho = u[0]
+    v = u[1:d + 1] / rho
+    p = 0.4 * (u[-1] - 0.5 * rho * v @ v)
+    c = np.sqrt(1.4 * p / rho)
+    vn = v @ n
+    np.testing.assert_allclose(ev, np.sort([vn - c] + [vn] * d + [vn + c]), atol=1e-12)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_viscous_flux_linear_in_q(d):
+    rng = np.random.default_rng(10 + d)
+    u, q = _state(d, rng)
+    F, Fu, Fq = physics.flux_with_jacobians(u[None], q[None], PRM, d)
+    F0, _, _ = physics.flux_with_jacobians(u[None], 0 * q[None], PRM, d)
+    np.testing.assert_allclose(np.einsum("ijkl,kl->ij", Fq[0], q), F[0] - F0[0], rtol=1e-12, atol=1e-13)
+
+
+def test_shear_stress_closed_form():
+    """Fluid at rest with d(rho v_x)/dy = s: tau_xy = s / Re, no heat flux."""
+    d, s = 3, 0.7
+    p0 = 2.0
+    u = np.array([1.0, 0, 0, 0, p0 / 0.4])
+    q = np.zeros((5, 3))
+    q[1, 1] = s
+    F = physics.flux(list(u), [list(r) for r in q], PRM, d)
+    assert abs(F[1][1] - (-s / PRM.Re)) < 1e-15
+    assert abs(F[2][0] - (-s / PRM.Re)) < 1e-15
+    assert abs(F[1][0] - p0) < 1e-14 and abs(F[2][1] - p0) < 1e-14
+    assert all(abs(F[4][j]) < 1e-15 for j in range(d))
+
+
+def test_heat_flux_is_dissipative():
+    """Fluid at rest, rho = 1, d(rho E)/dx_j = g_j: e = E, energy flux
+    = -(gamma / (Re Pr)) g_j (heat flows down the temperature gradient)."""
+    d = 3
+    g = np.array([0.3, -0.2, 0.5])
+    u = np.array([1.0, 0, 0, 0, 5.0])
+    q = np.zeros((5, 3))
+    q[4] = g
+    F = physics.flux(list(u), [list(r) for r in q], PRM, d)
+    kappa = PRM.gamma / (PRM.Re * PRM.Pr)
+    for j in range(d):
+        assert abs(F[4][j] - (-kappa * g[j])) < 1e-15
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_dual_jacobians_match_finite_differences(d):
+    rng = np.random.default_rng(20 + d)
+    u, q = _state(d, rng)
+    F, Fu, Fq = physics.flux_with_jacobians(u[None], q[None], PRM, d)
+    h = 1e-6
+    for k in range(d + 2):
+        du = np.zeros(d + 2)
+        du[k] = h * max(1.0, abs(u[k]))
+        Fp, _, _ = physics.flux_with_jacobians((u + du)[None], q[None], PRM, d)
+        Fm, _, _ = physics.flux_with_jacobians((u - du)[None], q[None], PRM, d)
+        np.testing.assert_allclose((Fp - Fm)[0] / (2 * du[k]), Fu[0][:, :, k], rtol=1e-6, atol=1e-7)
+    for k in range(d + 2):
+        for l in range(d):
+            dq = np.zeros((d + 2, d))
+            dq[k, l] = h
+            Fp, _, _ = physics.flux_with_jacobians(u[None], (q + dq)[None], PRM, d)
+            Fm, _, _ = physics.flux_with_jacobians(u[None], (q - dq)[None], PRM, d)
+            np.testing.assert_allclose((Fp - Fm)[0] / (2 * h), Fq[0][:, :, k, l], rtol=1e-6, atol=1e-8)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_lax_friedrichs_flux(d):
+    rng = np.random.default_rng(30 + d)
+    uh, q = _state(d, rng)
+    u, _ = _state(d, rng)
+    n = rng.normal(size=d)
+    n /= np.linalg.norm(n)
+    f, fuh, fu, fq = physics.numerical_flux_with_jacobians(uh[None], u[None], q[None], n[None], PRM, d)
+    F, _, Fq = physics.flux_with_jacobians(uh[None], q[None], PRM, d)
+    rho = uh[0]
+    v = uh[1:d + 1] / rho
+    p = 0.4 * (uh[-1] - 0.5 * rho * v @ v)
+    lam = abs(v @ n) + np.sqrt(1.4 * p / rho)
+    np.testing.assert_allclose(f[0], F[0] @ n + lam * (u - uh), rtol=1e-14, atol=1e-13)
+    np.testing.assert_allclose(fu[0], lam * np.eye(d + 2), atol=1e-14)
+    np.testing.assert_allclose(fq[0], np.einsum("ijkl,j->ikl", Fq[0], n), atol=1e-14)
+    # consistency: u = uhat gives the physical normal flux
+    f2, *_ = physics.numerical_flux_with_jacobians(uh[None], uh[None], q[None], n[None], PRM, d)
+    np.testing.assert_allclose(f2[0], F[0] @ n, rtol=1e-14, atol=1e-13)
+    # d fhat / d uhat by central differences
+    h = 1e-6
+    for k in range(d + 2):
+        du = np.zeros(d + 2)
+        du[k] = h * max(1.0, abs(uh[k]))
+        fp, *_ = physics.numerical_flux_with_jacobians((uh + du)[None], u[None], q[None], n[None], PRM, d)
+        fm, *_ = physics.numerical_flux_with_jacobians((uh - du)[None], u[None], q[None], n[None], PRM, d)
+        np.testing.assert_allclose((fp - fm)[0] / (2 * du[k]), fuh[0][:, k], rtol=1e-6, atol=1e-7)

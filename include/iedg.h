@@ -1,0 +1,155 @@
+/*
+ * iedg.h -- C ABI of the GB300 (sm_103a) IEDG local-problem library.
+ *
+ * The library implements the element-local part of every Newton step of the
+ * Interior Embedded Discontinuous Galerkin (IEDG) discretisation of the
+ * compressible Navier-Stokes equations (Fernandez, Nguyen, Roca, Peraire,
+ * arXiv:1605.01020):
+ *   - the residuals R_NS = (R_q, R_u) and R_FL of the weak form (Eq. IEDG a-c,
+ *     Eq. NLS), with the Lax-Friedrichs numerical flux of Eq. IEDG (d);
+ *   - the element blocks of the Newton matrix [A B; C D] and right-hand side
+ *     [F; G] (Sec. 2.2.1), statically condensed onto the trace unknowns,
+ *     K = D - C A^-1 B and R = G - C A^-1 F (Eq. LS), and assembled into a
+ *     block compressed-row matrix with m x m blocks (Sec. 2.2.2);
+ *   - the back-substitution dZ = A^-1 (F - B dU) after the trace solve.
+ *
+ * Conventions (all of them, including the readings where the paper is silent):
+ *   d = 2 or 3, m = d + 2 conserved variables u = (rho, rho v_j, rho E).
+ *   Elements are tensor-product quads/hexes of uniform degree p (1..4 in 3D,
+ *   1..3 in 2D); local nodes are the Gauss-Lobatto-Legendre lattice, numbered
+ *   lexicographically with the first reference direction fastest; Np = (p+1)^d.
+ *   Trace slots of an element are its boundary nodes in that same order; Nb =
+ *   (p+1)^d - (p-1)^d.  elem_trace[e][s] is the global trace node of slot s.
+ *   The trace is continuous wherever two slots map to the same trace node (the
+ *   EDG faces of the IEDG method, Sec. 2.1); periodic faces are ordinary interior
+ *   faces.
+ *   Quadrature: Gauss-Legendre with n_q1 = p + quad_extra points per direction.
+ *   Physics: gamma, Pr, Re as in Sec. 2.1; temperature read as the specific
+ *   internal energy e = E - |v|^2/2 and heat flux -(gamma/(Re Pr)) grad e
+ *   (dissipative sign).  Implicit stage: R_u gains alpha M (u - u_ref), alpha =
+ *   1 / (a_ii dt) of the DIRK stage (alpha = 0: steady).
+ *   Newton signs: F = -R_NS, G = -R_FL, so K dU = R gives the Newton increment.
+ *
+ * Memory: every array argument of the compute calls is a DEVICE pointer owned by
+ * the caller, in the layouts stated below (row-major, FP64), used on `stream`
+ * (a cudaStream_t, NULL = legacy default stream).  The handle owns only its own
+ * device workspace, allocated once in iedg_create_mesh.  Compute calls allocate
+ * nothing and do not synchronise the host; kernel-side problems (zero pivot,
+ * non-finite values) are recorded per element and read with iedg_element_status.
+ * There is no CPU fallback: without a usable CUDA device calls return
+ * IEDG_ERR_CUDA.  One handle must not be used from two streams at once.
+ *
+ * Errors: functions return IEDG_OK (0) or a negative code; the message of the
+ * last failure is iedg_last_error(handle) (or iedg_last_error(NULL) for failures
+ * before a handle exists).  No C++ exception crosses this interface.
+ */
+#ifndef IEDG_H
+#define IEDG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IEDG_OK                 0
+#define IEDG_ERR_INVALID_ARG   -1
+#define IEDG_ERR_CUDA          -2
+#define IEDG_ERR_OOM           -3
+#define IEDG_ERR_MESH          -4   /* detJ <= 0 somewhere, or bad element->trace map */
+#define IEDG_ERR_NOT_ASSEMBLED -5   /* back-substitution before any assembly          */
+#define IEDG_ERR_UNSUPPORTED   -6   /* valid request this build does not implement    */
+
+/* element status codes (iedg_element_status) */
+#define IEDG_ELEM_OK        0
+#define IEDG_ELEM_SINGULAR  2   /* exact zero pivot in the element block          */
+#define IEDG_ELEM_NONFINITE 3   /* NaN/Inf met in the element's Schur complement  */
+
+#define IEDG_PRECISION_FP64 0
+
+typedef struct iedg_mesh iedg_mesh;   /* opaque */
+
+typedef struct {
+  int32_t dim;              /* 2 or 3                                                */
+  int32_t order;            /* polynomial degree p = k of approximation and geometry */
+  int32_t quad_extra;       /* n_q1 = p + quad_extra Gauss points per direction (2)  */
+  int32_t precision;        /* IEDG_PRECISION_FP64                                   */
+  int64_t n_elem;
+  int64_t n_trace;
+  const double*  node_xyz;   /* HOST [n_elem][Np][dim]: isoparametric nodes (Sec. 3.1) */
+  const int64_t* elem_trace; /* HOST [n_elem][Nb]: global trace node of each slot      */
+  double gamma, Pr, Re, Minf, alpha;
+  int32_t stab;             /* 0 = Lax-Friedrichs, lambda = |vhat.n| + chat (Eq. IEDG d) */
+  int32_t reserved;
+} iedg_mesh_desc;
+
+/* Builds the handle: copies the mesh to the device, computes per-element geometry
+ * (Jacobians, weights, normals, mass matrix and the lifting operators of Eq. IEDG a)
+ * on `stream`, builds the trace-matrix pattern and the gather lists, and allocates
+ * all workspace.  Synchronises `stream` before returning.  IEDG_ERR_MESH if any
+ * quadrature point has detJ <= 0 or a trace id is out of range. */
+int iedg_create_mesh(const iedg_mesh_desc* desc, void* stream, iedg_mesh** out);
+int iedg_destroy_mesh(iedg_mesh* mesh);
+const char* iedg_last_error(const iedg_mesh* mesh);
+
+/* Sizes: Np, Nb, number of trace-matrix blocks nnzb (m x m each), bytes of device
+ * workspace held by the handle.  Any output pointer may be NULL. */
+int iedg_mesh_info(const iedg_mesh* mesh, int32_t* Np, int32_t* Nb, int64_t* nnzb,
+                   int64_t* workspace_bytes);
+
+/* Block compressed-row pattern of K (Sec. 2.2.2): one block row per trace node,
+ * one block for every pair of trace nodes sharing an element, columns sorted
+ * ascending.  Copies into caller DEVICE buffers row_ptr[n_trace+1], col[nnzb]. */
+int iedg_trace_pattern(const iedg_mesh* mesh, int64_t* row_ptr, int32_t* col, void* stream);
+
+/* Residual of Eq. IEDG (a)-(c).
+ *   u    [n_elem][Np][m]      element states
+ *   uhat [n_trace][m]         trace state
+ *   q    [n_elem][Np][m][d]   gradient state q_ij = du_i/dx_j, or NULL: then q is
+ *                             taken from R_q = 0 (local lifting of (u, uhat)) and
+ *                             written to q_out (required in that case)
+ *   u_ref [n_elem][Np][m] or NULL (= u): reference state of the implicit stage
+ * Outputs (any may be NULL except that q_out is needed when q is NULL):
+ *   r_q  [n_elem][Np][m][d], r_u [n_elem][Np][m], r_fl [n_trace][m] (overwritten). */
+int iedg_eval_residual(iedg_mesh* mesh, const double* u, const double* uhat,
+                       const double* q, const double* u_ref, double* q_out,
+                       double* r_q, double* r_u, double* r_fl, void* stream);
+
+/* One Newton linearisation, condensed (Sec. 2.2.1, Eq. LS):
+ *   K_bsr [nnzb][m][m] values of K in the pattern of iedg_trace_pattern, block
+ *         row-major [equation component][unknown component];
+ *   R     [n_trace][m] condensed right-hand side.
+ * Inputs as in iedg_eval_residual (q required).  The element factors are kept in
+ * the handle for iedg_back_substitute. */
+int iedg_assemble_condensed(iedg_mesh* mesh, const double* u, const double* q,
+                            const double* uhat, const double* u_ref,
+                            double* K_bsr, double* R, void* stream);
+
+/* Back-substitution after a trace solve: dZ_e = A_e^-1 (F_e - B_e dU_e) with the
+ * factors of the most recent iedg_assemble_condensed on this handle.
+ *   duhat [n_trace][m] -> du [n_elem][Np][m], dq [n_elem][Np][m][d].
+ * IEDG_ERR_NOT_ASSEMBLED if no assembly has been run. */
+int iedg_back_substitute(iedg_mesh* mesh, const double* duhat, double* du, double* dq,
+                         void* stream);
+
+/* Per-element status of the last assembly (IEDG_ELEM_*), copied to HOST
+ * out[n_elem]; synchronises `stream`.  Returns the number of flagged elements
+ * (>= 0) or a negative error code. */
+int64_t iedg_element_status(iedg_mesh* mesh, int8_t* out, void* stream);
+
+/* Tracing (no counterpart in the paper; it times the library's own kernels).
+ * Every kernel launch is counted per kernel name.  While profiling is enabled,
+ * each launch is also bracketed by CUDA events recorded on the launching stream,
+ * so the summed device time per kernel is available.  iedg_profile_read fills up
+ * to max_kernels entries: names[i] (NUL-terminated, 32 bytes each), launches[i],
+ * ms[i] (0 unless profiling was enabled), and sets *n_kernels; it synchronises
+ * the recorded events.  iedg_profile_reset clears counts, times and events. */
+int iedg_profile_enable(iedg_mesh* mesh, int32_t enable);
+int iedg_profile_read(iedg_mesh* mesh, int32_t max_kernels, char* names, int64_t* launches,
+                      double* ms, int32_t* n_kernels);
+int iedg_profile_reset(iedg_mesh* mesh);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IEDG_H */

@@ -49,11 +49,11 @@ class Problem:
         ue, qe = u[els], q[els]
         uh_e = uhat[self.elem_trace[els]]                       # [E, Nb, m]
         P = {}
-        P["u"] = np.einsum("ga,eai->egi", ref.phi, ue)
-        P["q"] = np.einsum("ga,eaij->egij", ref.phi, qe)
-        P["uf"] = np.einsum("fga,eai->efgi", ref.fphi, ue)
-        P["qf"] = np.einsum("fga,eaij->efgij", ref.fphi, qe)
-        P["uhf"] = np.einsum("fgs,esi->efgi", self.fmu, uh_e)
+        P["u"] = np.einsum("ga,eai->egi", ref.phi, ue, optimize=True)
+        P["q"] = np.einsum("ga,eaij->egij", ref.phi, qe, optimize=True)
+        P["uf"] = np.einsum("fga,eai->efgi", ref.fphi, ue, optimize=True)
+        P["qf"] = np.einsum("fga,eaij->efgij", ref.fphi, qe, optimize=True)
+        P["uhf"] = np.einsum("fgs,esi->efgi", self.fmu, uh_e, optimize=True)
         return P
 
     # --------------------------------------------------------------- residual
@@ -69,18 +69,18 @@ class Problem:
         wf, nf = geo.wf[els], geo.nf[els]
         F, _, _ = physics.flux_with_jacobians(P["u"], P["q"], prm, d)
         fh, _, _, _ = physics.numerical_flux_with_jacobians(P["uhf"], P["uf"], P["qf"], nf, prm, d)
-        Rq = (np.einsum("eg,egij,ga->eaij", w, P["q"], ref.phi)
-              + np.einsum("eg,egi,ejga->eaij", w, P["u"], gphi)
-              - np.einsum("efg,efgi,efgj,fga->eaij", wf, P["uhf"], nf, ref.fphi))
-        Ru = (-np.einsum("eg,egij,ejga->eai", w, F, gphi)
-              + np.einsum("efg,efgi,fga->eai", wf, fh, ref.fphi))
+        Rq = (np.einsum("eg,egij,ga->eaij", w, P["q"], ref.phi, optimize=True)
+              + np.einsum("eg,egi,ejga->eaij", w, P["u"], gphi, optimize=True)
+              - np.einsum("efg,efgi,efgj,fga->eaij", wf, P["uhf"], nf, ref.fphi, optimize=True))
+        Ru = (-np.einsum("eg,egij,ejga->eai", w, F, gphi, optimize=True)
+              + np.einsum("efg,efgi,fga->eai", wf, fh, ref.fphi, optimize=True))
         if prm.alpha != 0.0:
-            uref_pts = P["u"] if u_ref is None else np.einsum("ga,eai->egi", ref.phi, u_ref[els])
-            Ru = Ru + prm.alpha * np.einsum("eg,egi,ga->eai", w, P["u"] - uref_pts, ref.phi)
+            uref_pts = P["u"] if u_ref is None else np.einsum("ga,eai->egi", ref.phi, u_ref[els], optimize=True)
+            Ru = Ru + prm.alpha * np.einsum("eg,egi,ga->eai", w, P["u"] - uref_pts, ref.phi, optimize=True)
         if self.source is not None:
             s = self.source(geo.xq[els])
-            Ru = Ru - np.einsum("eg,egi,ga->eai", w, s, ref.phi)
-        Rhat_e = np.einsum("efg,efgi,fgs->esi", wf, fh, self.fmu)
+            Ru = Ru - np.einsum("eg,egi,ga->eai", w, s, ref.phi, optimize=True)
+        Rhat_e = np.einsum("efg,efgi,fgs->esi", wf, fh, self.fmu, optimize=True)
         Rfl = np.zeros((self.n_trace, m))
         np.add.at(Rfl, self.elem_trace[els].reshape(-1), Rhat_e.reshape(-1, m))
         return Rq, Ru, Rhat_e, Rfl
@@ -89,8 +89,8 @@ class Problem:
         """Mass M, B_j[a,b] = sum_g w dphi_a/dx_j phi_b, E_j[a,t] = sum wf n_j phi_a mu_t."""
         ref, geo = self.ref, self.geo
         M = geo.M[e]
-        Bj = np.einsum("g,jga,gb->jab", geo.w[e], geo.gphi[e], ref.phi)
-        Ej = np.einsum("fg,fgj,fga,fgt->jat", geo.wf[e], geo.nf[e], ref.fphi, self.fmu)
+        Bj = np.einsum("g,jga,gb->jab", geo.w[e], geo.gphi[e], ref.phi, optimize=True)
+        Ej = np.einsum("fg,fgj,fga,fgt->jat", geo.wf[e], geo.nf[e], ref.fphi, self.fmu, optimize=True)
         return M, Bj, Ej
 
     def solve_q(self, u, uhat):
@@ -122,22 +122,22 @@ class Problem:
         I_d = np.eye(d)
         blk = {}
         # q-equation rows (IEDG a): linear, geometry only
-        blk["A_qq"] = np.einsum("ik,jl,ab->ijaklb", I_m, I_d, M).reshape(m * d * Np, m * d * Np)
-        blk["A_qu"] = np.einsum("ik,jab->ijakb", I_m, Bj).reshape(m * d * Np, m * Np)
-        blk["B_q"] = -np.einsum("ik,jat->ijakt", I_m, Ej).reshape(m * d * Np, m * Nb)
+        blk["A_qq"] = np.einsum("ik,jl,ab->ijaklb", I_m, I_d, M, optimize=True).reshape(m * d * Np, m * d * Np)
+        blk["A_qu"] = np.einsum("ik,jab->ijakb", I_m, Bj, optimize=True).reshape(m * d * Np, m * Np)
+        blk["B_q"] = -np.einsum("ik,jat->ijakt", I_m, Ej, optimize=True).reshape(m * d * Np, m * Nb)
         # u-equation rows (IEDG b)
-        A_uq = (-np.einsum("g,jga,gijkl,gb->iaklb", w, gphi, Fq, phi)
-                + np.einsum("fg,fga,fgikl,fgb->iaklb", wf, fphi, fq, fphi))
-        A_uu = (-np.einsum("g,jga,gijk,gb->iakb", w, gphi, Fu, phi)
-                + np.einsum("fg,fga,fgik,fgb->iakb", wf, fphi, fu, fphi))
-        A_uu = A_uu + prm.alpha * np.einsum("ik,ab->iakb", I_m, M)
+        A_uq = (-np.einsum("g,jga,gijkl,gb->iaklb", w, gphi, Fq, phi, optimize=True)
+                + np.einsum("fg,fga,fgikl,fgb->iaklb", wf, fphi, fq, fphi, optimize=True))
+        A_uu = (-np.einsum("g,jga,gijk,gb->iakb", w, gphi, Fu, phi, optimize=True)
+                + np.einsum("fg,fga,fgik,fgb->iakb", wf, fphi, fu, fphi, optimize=True))
+        A_uu = A_uu + prm.alpha * np.einsum("ik,ab->iakb", I_m, M, optimize=True)
         blk["A_uq"] = A_uq.reshape(m * Np, m * d * Np)
         blk["A_uu"] = A_uu.reshape(m * Np, m * Np)
-        blk["B_u"] = np.einsum("fg,fga,fgik,fgt->iakt", wf, fphi, fuh, fmu).reshape(m * Np, m * Nb)
+        blk["B_u"] = np.einsum("fg,fga,fgik,fgt->iakt", wf, fphi, fuh, fmu, optimize=True).reshape(m * Np, m * Nb)
         # trace rows (IEDG c)
-        blk["C_q"] = np.einsum("fg,fgs,fgikl,fgb->isklb", wf, fmu, fq, fphi).reshape(m * Nb, m * d * Np)
-        blk["C_u"] = np.einsum("fg,fgs,fgik,fgb->iskb", wf, fmu, fu, fphi).reshape(m * Nb, m * Np)
-        blk["D"] = np.einsum("fg,fgs,fgik,fgt->iskt", wf, fmu, fuh, fmu).reshape(m * Nb, m * Nb)
+        blk["C_q"] = np.einsum("fg,fgs,fgikl,fgb->isklb", wf, fmu, fq, fphi, optimize=True).reshape(m * Nb, m * d * Np)
+        blk["C_u"] = np.einsum("fg,fgs,fgik,fgb->iskb", wf, fmu, fu, fphi, optimize=True).reshape(m * Nb, m * Np)
+        blk["D"] = np.einsum("fg,fgs,fgik,fgt->iskt", wf, fmu, fuh, fmu, optimize=True).reshape(m * Nb, m * Nb)
         Rq, Ru, Rhat_e, _ = self.residual(u, q, uhat, u_ref, els=els)
         blk["F_q"] = -np.transpose(Rq[0], (1, 2, 0)).reshape(-1)        # (i, j, a)
         blk["F_u"] = -np.transpose(Ru[0], (1, 0)).reshape(-1)         # (i, a)
@@ -183,12 +183,12 @@ class Problem:
         MFq = np.stack([[np.linalg.solve(M, Fq[k, l]) for l in range(d)] for k in range(m)])
         A_uq = blk["A_uq"].reshape(m * Np, m, d, Np)
         C_q = blk["C_q"].reshape(m * Nb, m, d, Np)
-        At = blk["A_uu"] - np.einsum("rklc,lcb->rkb", A_uq, Gl).reshape(m * Np, m * Np)
-        Bt = blk["B_u"] + np.einsum("rklc,lct->rkt", A_uq, Hl).reshape(m * Np, m * Nb)
-        Ft = blk["F_u"] - np.einsum("rklc,klc->r", A_uq, MFq)
-        Ct = blk["C_u"] - np.einsum("rklc,lcb->rkb", C_q, Gl).reshape(m * Nb, m * Np)
-        Dt = blk["D"] + np.einsum("rklc,lct->rkt", C_q, Hl).reshape(m * Nb, m * Nb)
-        Gt = blk["G"] - np.einsum("rklc,klc->r", C_q, MFq)
+        At = blk["A_uu"] - np.einsum("rklc,lcb->rkb", A_uq, Gl, optimize=True).reshape(m * Np, m * Np)
+        Bt = blk["B_u"] + np.einsum("rklc,lct->rkt", A_uq, Hl, optimize=True).reshape(m * Np, m * Nb)
+        Ft = blk["F_u"] - np.einsum("rklc,klc->r", A_uq, MFq, optimize=True)
+        Ct = blk["C_u"] - np.einsum("rklc,lcb->rkb", C_q, Gl, optimize=True).reshape(m * Nb, m * Np)
+        Dt = blk["D"] + np.einsum("rklc,lct->rkt", C_q, Hl, optimize=True).reshape(m * Nb, m * Nb)
+        Gt = blk["G"] - np.einsum("rklc,klc->r", C_q, MFq, optimize=True)
         return At, Bt, Ct, Dt, Ft, Gt, Gl, Hl, MFq
 
     def condense_qelim(self, e, u, q, uhat, u_ref=None):

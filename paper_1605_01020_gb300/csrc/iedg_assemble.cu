@@ -1,0 +1,355 @@
+// Element block assembly with the q-elimination folded in at the quadrature points,
+// and the partial LU of the bordered element matrix (static condensation, Eq. LS).
+//
+// Bordered element matrix (rows x cols = n x (n+1), n = m Np + m Nb):
+//     [ At  Bt  Ft ]     rows i Np + a      (u-equation i, node a)
+//     [ Ct  Dt  Gt ]     rows nu + i Nb + s (trace equation i, slot s)
+// columns k Np + b (u unknown k, node b), nu + k Nb + t (trace unknown k, slot t), n.
+// A_qq = M (x) I (Eq. IEDG a) lets q be eliminated exactly:
+//   dq_kl = M^-1 F_q,kl - G_l du_k + H_l dU_k,
+// so with the lifted operators Gl(g) = Phi G_l, Hl(g) = Phi H_l at the points,
+//   At_ik[a][b] = alpha delta_ik M_ab
+//              + sum_{g,r} Dxi_r[g][a] (cu_ikr(g) Phi[g][b] - sum_l cq_iklr(g) Gl_l(g)[b])
+//              + sum_fp PhiF[fp][a] (lamw delta_ik PhiF[fp][b] - sum_l fq_ikl(fp) GlF_l(fp)[b])
+//   Bt_ik[a][t] = sum_{g,r} Dxi_r[g][a] sum_l cq_iklr(g) Hl_l(g)[t]
+//              + sum_fp PhiF[fp][a] (fuh_ik(fp) mu_t(fp) + sum_l fq_ikl(fp) HlF_l(fp)[t])
+// and the trace rows Ct, Dt equal the face parts of the u-rows of the boundary nodes
+// (mu_s = phi_bnode[s] on every face), which is how they are formed here.
+// The right-hand-side column is written by the point kernel: Ft = -R_u(u, q*),
+// Gt = -R_FL,e(u, q*) (exact because the fluxes are affine in q).
+#include "iedg_internal.cuh"
+
+namespace iedg {
+namespace {
+
+constexpr int AS_THREADS = 256;
+constexpr int TM = 4, TN = 8;       // register tile of the volume contraction
+constexpr int GC = 8;               // volume points per K-chunk
+
+struct AsmCfg {
+  int rows_pad;   // Np rounded up to TM
+  int rg;         // row groups
+  int CW;         // columns per CTA (multiple of TN)
+  int cg;         // column groups
+  int nsplit;     // CTAs per (element, i, k)
+  int KC;         // K-chunk rows = GC d
+};
+
+AsmCfg asm_cfg(const Dims& dm) {
+  AsmCfg c;
+  c.rows_pad = idiv_up(dm.Np, TM) * TM;
+  c.rg = c.rows_pad / TM;
+  int max_cg = AS_THREADS / c.rg;
+  int need = idiv_up(dm.Np + dm.Nb, TN);
+  c.nsplit = idiv_up(need, max_cg);
+  c.cg = idiv_up(need, c.nsplit);
+  c.CW = c.cg * TN;
+  c.KC = GC * dm.d;
+  return c;
+}
+
+__global__ void __launch_bounds__(AS_THREADS)
+k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, Geo G, PointJac PJ, double* __restrict__ S) {
+  extern __shared__ double sm[];
+  const int tid = threadIdx.x;
+  const int64_t e = blockIdx.x;
+  const int pair = blockIdx.y, i = pair / dm.m, k = pair % dm.m;
+  const int c0 = blockIdx.z * cf.CW;
+  const int d = dm.d, Np = dm.Np, Nb = dm.Nb, Nq = dm.Nq, Nfp = dm.Nfp, Nfq = dm.Nfq, Nfn = dm.Nfn;
+  const int ncol = Np + Nb;
+  const int KC = cf.KC, CW = cf.CW, RP = cf.rows_pad;
+  double* sA = sm;                      // [KC][RP]   Dxi_r[g][a]
+  double* sB = sA + KC * RP;            // [KC][CW]   W[(g, r)][col]
+  double* facc = sB + KC * CW;          // [Nb][CW]   face parts of the boundary rows
+  double* sV = facc + Nb * CW;          // [Nfq][CW]  face right operand
+  const size_t jvs = (size_t)(1 + d) * d * Nq;
+  const double* jv = PJ.Jv + ((size_t)e * dm.m * dm.m + pair) * jvs;
+  const size_t jfs = (size_t)(1 + d) * Nfp;
+  const double* jf = PJ.Jf + ((size_t)e * dm.m * dm.m + pair) * jfs;
+  const double* GlV = G.GlV + (size_t)e * d * Nq * Np;
+  const double* HlV = G.HlV + (size_t)e * d * Nq * Nb;
+  const double* GlF = G.GlF + (size_t)e * d * Nfp * Np;
+  const double* HlF = G.HlF + (size_t)e * d * Nfp * Nb;
+
+  const int trow = tid / cf.cg, tcol = tid % cf.cg;
+  const bool gemm_thread = trow < cf.rg;
+  double acc[TM][TN];
+#pragma unroll
+  for (int a = 0; a < TM; ++a)
+#pragma unroll
+    for (int b = 0; b < TN; ++b) acc[a][b] = 0.0;
+
+  // ---- volume contraction, K = Nq d in chunks of GC points
+  for (int g0 = 0; g0 < Nq; g0 += GC) {
+    for (int idx = tid; idx < KC * RP; idx += AS_THREADS) {
+      int kc = idx / RP, a = idx % RP;
+      int g = g0 + kc / d, r = kc % d;
+      sA[idx] = (g < Nq && a < Np) ? ref.Dxi[((size_t)r * Nq + g) * Np + a] : 0.0;
+    }
+    for (int idx = tid; idx < KC * CW; idx += AS_THREADS) {
+      int kc = idx / CW, col = c0 + idx % CW;
+      int g = g0 + kc / d, r = kc % d;
+      double w = 0.0;
+      if (g < Nq && col < ncol) {
+        if (col < Np) {
+          w = jv[(size_t)r * Nq + g] * ref.Phi[(size_t)g * Np + col];
+          for (int l = 0; l < d; ++l)
+            w -= jv[(size_t)(d + l * d + r) * Nq + g] * GlV[((size_t)l * Nq + g) * Np + col];
+        } else {
+          for (int l = 0; l < d; ++l)
+            w += jv[(size_t)(d + l * d + r) * Nq + g] * HlV[((size_t)l * Nq + g) * Nb + (col - Np)];
+        }
+      }
+      sB[idx] = w;
+    }
+    __syncthreads();
+    if (gemm_thread) {
+      for (int kc = 0; kc < KC; ++kc) {
+        double av[TM], bv[TN];
+#pragma unroll
+        for (int a = 0; a < TM; ++a) av[a] = sA[kc * RP + trow * TM + a];
+#pragma unroll
+        for (int b = 0; b < TN; ++b) bv[b] = sB[kc * CW + tcol * TN + b];
+#pragma unroll
+        for (int a = 0; a < TM; ++a)
+#pragma unroll
+          for (int b = 0; b < TN; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- face parts, accumulated per trace slot
+  for (int idx = tid; idx < Nb * CW; idx += AS_THREADS) facc[idx] = 0.0;
+  const double lamsel = (i == k) ? 1.0 : 0.0;
+  for (int f = 0; f < dm.nf; ++f) {
+    __syncthreads();
+    for (int idx = tid; idx < Nfq * CW; idx += AS_THREADS) {
+      int gf = idx / CW, col = c0 + idx % CW;
+      int fp = f * Nfq + gf;
+      double v = 0.0;
+      if (col < Np) {
+        v = lamsel * PJ.lamw[e * Nfp + fp] * ref.PhiF[(size_t)fp * Np + col];
+        for (int l = 0; l < d; ++l) v -= jf[(size_t)(1 + l) * Nfp + fp] * GlF[((size_t)l * Nfp + fp) * Np + col];
+      } else if (col < ncol) {
+        int t = col - Np;
+        v = jf[fp] * ref.PhiF[(size_t)fp * Np + ref.bnode[t]];
+        for (int l = 0; l < d; ++l) v += jf[(size_t)(1 + l) * Nfp + fp] * HlF[((size_t)l * Nfp + fp) * Nb + t];
+      }
+      sV[idx] = v;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < Nfn * CW; idx += AS_THREADS) {
+      int tn = idx / CW, cc = idx % CW;
+      int a = ref.fnode[f * Nfn + tn];
+      double s = 0.0;
+      for (int gf = 0; gf < Nfq; ++gf) s += ref.PhiF[(size_t)(f * Nfq + gf) * Np + a] * sV[gf * CW + cc];
+      facc[ref.slot[a] * CW + cc] += s;
+    }
+  }
+  __syncthreads();
+
+  // ---- write the element rows
+  const int64_t nn = dm.n, ld = dm.ld;
+  double* Se = S + e * nn * ld;
+  auto colS = [&](int col) -> int64_t { return col < Np ? (int64_t)k * Np + col : (int64_t)dm.nu + (int64_t)k * Nb + (col - Np); };
+  if (gemm_thread) {
+    const double* Ms = G.Mass + (size_t)e * Np * Np;
+#pragma unroll
+    for (int a = 0; a < TM; ++a) {
+      int row = trow * TM + a;
+      if (row >= Np) continue;
+      int sl = ref.slot[row];
+#pragma unroll
+      for (int b = 0; b < TN; ++b) {
+        int col = c0 + tcol * TN + b;
+        if (col >= ncol || col >= c0 + CW) continue;
+        double v = acc[a][b];
+        if (sl >= 0) v += facc[sl * CW + (col - c0)];
+        if (i == k && col < Np) v += ph.alpha * Ms[row * Np + col];
+        Se[((int64_t)i * Np + row) * ld + colS(col)] = v;
+      }
+    }
+  }
+  for (int idx = tid; idx < Nb * CW; idx += AS_THREADS) {
+    int s = idx / CW, col = c0 + idx % CW;
+    if (col >= ncol) continue;
+    Se[((int64_t)dm.nu + (int64_t)i * Nb + s) * ld + colS(col)] = facc[idx];
+  }
+}
+
+// ------------------------------------------------------------------ partial LU
+// Right-looking blocked LU with partial pivoting of the bordered matrix, pivots
+// only among the nu u-rows (largest |a|, smallest row on ties), eliminating the
+// first nu columns from all n rows.  Afterwards rows [nu, n) x cols [nu, n] hold
+// [K_e | R_e] = [Dt - Ct At^-1 Bt | Gt - Ct At^-1 Ft]; rows [0, nu) hold U (upper
+// triangle, cols < nu) and L^-1 P [Bt Ft] (cols >= nu) for the back-substitution.
+constexpr int NB = 16;
+constexpr int LU_THREADS = 256;
+constexpr int UCW = 64;     // trailing-update column chunk
+
+__global__ void __launch_bounds__(LU_THREADS)
+k_lu(Dims dm, double* __restrict__ S, int8_t* __restrict__ status) {
+  extern __shared__ double sm[];
+  __shared__ int piv[NB];
+  __shared__ double rv[LU_THREADS / 32];
+  __shared__ int ri[LU_THREADS / 32];
+  __shared__ int sing;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t e = blockIdx.x;
+  const int n = dm.n, nu = dm.nu, ld = dm.ld, ncol = n + 1;
+  double* A = S + e * (int64_t)n * ld;
+  double* P = sm;                       // [n][NB]
+  double* Uc = P + (size_t)n * NB;      // [NB][UCW]
+  if (tid == 0) sing = 0;
+  for (int kb = 0; kb < nu; kb += NB) {
+    const int nb = min(NB, nu - kb), rows = n - kb, prow = nu - kb;
+    for (int idx = tid; idx < rows * NB; idx += LU_THREADS) {
+      int r = idx / NB, j = idx % NB;
+      P[idx] = j < nb ? A[(int64_t)(kb + r) * ld + kb + j] : 0.0;
+    }
+    __syncthreads();
+    for (int j = 0; j < nb; ++j) {
+      double best = -1.0;
+      int bi = j;
+      for (int r = j + tid; r < prow; r += LU_THREADS) {
+        double v = fabs(P[r * NB + j]);
+        if (v > best) { best = v; bi = r; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+      }
+      if (lane == 0) { rv[warp] = best; ri[warp] = bi; }
+      __syncthreads();
+      if (tid == 0) {
+        double bv = rv[0];
+        int b = ri[0];
+        for (int w = 1; w < LU_THREADS / 32; ++w)
+          if (rv[w] > bv || (rv[w] == bv && ri[w] < b)) { bv = rv[w]; b = ri[w]; }
+        if (!(bv > 0.0)) { sing = 1; b = j; }
+        piv[j] = b;
+      }
+      __syncthreads();
+      const int pr = piv[j];
+      if (pr != j && tid < NB) {
+        double t = P[j * NB + tid];
+        P[j * NB + tid] = P[pr * NB + tid];
+        P[pr * NB + tid] = t;
+      }
+      __syncthreads();
+      const double pv = P[j * NB + j];
+      const double inv = pv != 0.0 ? 1.0 / pv : 0.0;
+      for (int r = j + 1 + tid; r < rows; r += LU_THREADS) {
+        double l = P[r * NB + j] * inv;
+        P[r * NB + j] = l;
+        for (int c = j + 1; c < nb; ++c) P[r * NB + c] = fma(-l, P[j * NB + c], P[r * NB + c]);
+      }
+      __syncthreads();
+    }
+    // U11 / L11 back to the element matrix
+    for (int idx = tid; idx < nb * nb; idx += LU_THREADS) {
+      int r = idx / nb, j = idx % nb;
+      A[(int64_t)(kb + r) * ld + kb + j] = P[r * NB + j];
+    }
+    // trailing columns: row interchanges, then U12 = L11^-1 A12
+    for (int c = kb + nb + tid; c < ncol; c += LU_THREADS) {
+      double x[NB];
+      for (int j = 0; j < nb; ++j) {
+        int pr = piv[j];
+        double* a0 = A + (int64_t)(kb + j) * ld + c;
+        if (pr != j) {
+          double* a1 = A + (int64_t)(kb + pr) * ld + c;
+          double t = *a0; *a0 = *a1; *a1 = t;
+        }
+        x[j] = *a0;
+      }
+      for (int j = 0; j < nb; ++j) {
+        double s = x[j];
+        for (int jj = 0; jj < j; ++jj) s = fma(-P[j * NB + jj], x[jj], s);
+        x[j] = s;
+        A[(int64_t)(kb + j) * ld + c] = s;
+      }
+    }
+    __syncthreads();
+    // A22 -= L21 U12, rows [kb+nb, n), cols [kb+nb, n]
+    const int r0 = kb + nb;
+    for (int cc = r0; cc < ncol; cc += UCW) {
+      const int cw = min(UCW, ncol - cc);
+      for (int idx = tid; idx < NB * UCW; idx += LU_THREADS) {
+        int j = idx / UCW, c = idx % UCW;
+        Uc[idx] = (j < nb && c < cw) ? A[(int64_t)(kb + j) * ld + cc + c] : 0.0;
+      }
+      __syncthreads();
+      const int tc = tid % (UCW / 4), tr = tid / (UCW / 4);   // 16 x 16 threads, 4x4 tiles
+      for (int rb = r0; rb < n; rb += 64) {
+        double a4[4][4];
+        int rr[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          rr[a] = rb + tr * 4 + a;
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            int c = tc * 4 + b;
+            a4[a][b] = (rr[a] < n && c < cw) ? A[(int64_t)rr[a] * ld + cc + c] : 0.0;
+          }
+        }
+        for (int j = 0; j < nb; ++j) {
+          double uv[4], lv[4];
+#pragma unroll
+          for (int b = 0; b < 4; ++b) uv[b] = Uc[j * UCW + tc * 4 + b];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) lv[a] = rr[a] < n ? P[(rr[a] - kb) * NB + j] : 0.0;
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) a4[a][b] = fma(-lv[a], uv[b], a4[a][b]);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            int c = tc * 4 + b;
+            if (rr[a] < n && c < cw) A[(int64_t)rr[a] * ld + cc + c] = a4[a][b];
+          }
+      }
+      __syncthreads();
+    }
+  }
+  // status: exact zero pivot, or non-finite Schur complement
+  __syncthreads();
+  int bad = 0;
+  for (int idx = tid; idx < (n - nu) * (ncol - nu); idx += LU_THREADS) {
+    int r = nu + idx / (ncol - nu), c = nu + idx % (ncol - nu);
+    if (!isfinite(A[(int64_t)r * ld + c])) bad = 1;
+  }
+  bad = __syncthreads_or(bad);
+  if (tid == 0) status[e] = sing ? IEDG_ELEM_SINGULAR : (bad ? IEDG_ELEM_NONFINITE : IEDG_ELEM_OK);
+}
+
+}  // namespace
+
+cudaError_t launch_assemble(iedg_mesh* M, cudaStream_t st) {
+  const Dims& dm = M->dm;
+  AsmCfg cf = asm_cfg(dm);
+  size_t smem = sizeof(double) * ((size_t)cf.KC * cf.rows_pad + (size_t)cf.KC * cf.CW +
+                                  (size_t)dm.Nb * cf.CW + (size_t)dm.Nfq * cf.CW);
+  cudaError_t err = cudaFuncSetAttribute(k_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  dim3 grid((unsigned)M->E, dm.m * dm.m, cf.nsplit);
+  k_assemble<<<grid, AS_THREADS, smem, st>>>(dm, M->ph, cf, M->ref, M->geo, M->pj, M->S);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lu(iedg_mesh* M, cudaStream_t st) {
+  const Dims& dm = M->dm;
+  size_t smem = sizeof(double) * ((size_t)dm.n * NB + (size_t)NB * UCW);
+  cudaError_t err = cudaFuncSetAttribute(k_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  k_lu<<<(unsigned)M->E, LU_THREADS, smem, st>>>(dm, M->S, M->status);
+  return cudaGetLastError();
+}
+
+}  // namespace iedg

@@ -1,0 +1,118 @@
+// Internal declarations of the IEDG sm_103a library (not part of the C ABI).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <utility>
+#include <vector>
+#include <cuda_runtime.h>
+
+#include "../../include/iedg.h"
+
+namespace iedg {
+
+// Element sizes.  Local node a = a_0 + (p+1) a_1 + (p+1)^2 a_2, volume point g
+// likewise over n_q1 Gauss points; face f = 2 r + side; face point fp = f Nfq + gf.
+struct Dims {
+  int d, p, m, np1, nq1;
+  int Np, Nq, Nb, nf, Nfq, Nfp, Nfn;
+  int nu;   // m Np   : element unknowns after q-elimination (u block)
+  int nt;   // m Nb   : element trace unknowns
+  int n;    // nu + nt: rows of the bordered element matrix
+  int ld;   // leading dimension of the bordered matrix (>= n + 1, even)
+};
+
+struct Phys {
+  double gamma, Pr, Re, alpha;
+};
+
+// Reference-element tables (device), shared by all elements.
+struct RefTables {
+  double* Phi;    // [Nq][Np]
+  double* Dxi;    // [d][Nq][Np]
+  double* Wq;     // [Nq]
+  double* PhiF;   // [Nfp][Np]
+  double* DxiF;   // [d][Nfp][Np]
+  double* Wf;     // [Nfq]
+  int* bnode;     // [Nb]   local node of trace slot s
+  int* slot;      // [Np]   trace slot of node a, -1 for interior nodes
+  int* fnode;     // [nf][Nfn] nodes of each face
+};
+
+// Per-element geometry (device).
+struct Geo {
+  double* wdet;   // [E][Nq]          W_g detJ
+  double* Jinv;   // [E][Nq][d][d]    Jinv[r][j] = d xi_r / d x_j
+  double* fw;     // [E][Nfp]         W_f |cof(J) nref|
+  double* fn;     // [E][Nfp][d]      unit outward normal
+  double* Mass;   // [E][Np][Np]
+  double* Gl;     // [E][d][Np][Np]   M^-1 B_l
+  double* Hl;     // [E][d][Np][Nb]   M^-1 E_l
+  double* GlV;    // [E][d][Nq][Np]   Phi Gl   (lifting at volume points)
+  double* HlV;    // [E][d][Nq][Nb]
+  double* GlF;    // [E][d][Nfp][Np]  PhiF Gl  (lifting at face points)
+  double* HlF;    // [E][d][Nfp][Nb]
+};
+
+// Point tables written by the point kernel for the assembly kernel.
+struct PointJac {
+  double* Jv;     // [E][m][m][(1+d) d][Nq]: c<d: cu_r ; c = d + l d + r: cq_lr  (w Jinv folded)
+  double* Jf;     // [E][m][m][1+d][Nfp]   : c=0: wf dfhat/duhat ; c=1+l: wf dfhat/dq_l
+  double* lamw;   // [E][Nfp]              : wf lambda  (dfhat/du = lambda I)
+};
+
+}  // namespace iedg
+
+struct iedg_mesh {
+  iedg::Dims dm;
+  iedg::Phys ph;
+  int64_t E = 0, T = 0, nnzb = 0;
+  iedg::RefTables ref{};
+  iedg::Geo geo{};
+  iedg::PointJac pj{};
+  int64_t* etrace = nullptr;    // [E][Nb]
+  int64_t* row_ptr = nullptr;   // [T+1]
+  int32_t* col = nullptr;       // [nnzb]
+  int64_t* kc_ptr = nullptr;    // [nnzb+1] gather list of K blocks
+  int64_t* kc_src = nullptr;    //   e Nb^2 + s Nb + t
+  int64_t* rc_ptr = nullptr;    // [T+1]    gather list of trace rows
+  int64_t* rc_src = nullptr;    //   e Nb + s
+  double* qstar = nullptr;      // [E][Np][m][d] lifted gradient (R_q = 0)
+  double* rhoq = nullptr;       // [E][Np][m][d] q - qstar of the last assembly
+  double* rhat = nullptr;       // [E][Nb][m]    element trace residuals
+  double* S = nullptr;          // [E][n][ld]    bordered element matrices
+  int8_t* status = nullptr;     // [E]
+  int* dev_flag = nullptr;      // geometry error flag
+  bool assembled = false;
+  // tracing: launches per kernel, events while profiling is on
+  bool profiling = false;
+  std::vector<std::string> kname;
+  std::vector<int64_t> klaunch;
+  std::vector<double> kms;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> kev;
+  int64_t ws_bytes = 0;
+  std::string err;
+  std::vector<void*> allocs;
+};
+
+namespace iedg {
+
+inline int idiv_up(int a, int b) { return (a + b - 1) / b; }
+
+// kernels (launchers)
+cudaError_t launch_geometry(iedg_mesh* M, const double* X, double* scratch, cudaStream_t st);
+cudaError_t launch_lift(iedg_mesh* M, const double* u, const double* uhat, double* qstar, cudaStream_t st);
+cudaError_t launch_points(iedg_mesh* M, const double* u, const double* q, const double* qs,
+                          const double* uhat, const double* u_ref, bool jacobians,
+                          double* r_u, double* rhat, cudaStream_t st);
+cudaError_t launch_rq(iedg_mesh* M, const double* q, const double* qs, double* r_q, double* rhoq,
+                      cudaStream_t st);
+cudaError_t launch_assemble(iedg_mesh* M, cudaStream_t st);
+cudaError_t launch_lu(iedg_mesh* M, cudaStream_t st);
+cudaError_t launch_scatter_K(iedg_mesh* M, double* K, cudaStream_t st);
+cudaError_t launch_scatter_R(iedg_mesh* M, const double* src, int64_t src_elem_stride,
+                             int64_t src_slot_stride, int64_t src_comp_stride, double* R,
+                             cudaStream_t st);
+cudaError_t launch_backsub(iedg_mesh* M, const double* duhat, double* du, double* dq,
+                           cudaStream_t st);
+
+}  // namespace iedg

@@ -1,0 +1,489 @@
+// Quadrature-point physics and residual of the IEDG weak form.
+//
+//  * Navier-Stokes flux F(u, q) (Sec. 2.1): inviscid part rho v_j, rho v_i v_j +
+//    delta_ij p, v_j (rho E + p); viscous part tau_ij = (1/Re)(d_j v_i + d_i v_j -
+//    2/3 delta_ij d_k v_k); heat term (gamma / (Re Pr)) d_j e with e = E - |v|^2/2,
+//    taken with the dissipative sign (the energy flux loses v_i tau_ij + it).
+//  * Lax-Friedrichs numerical flux (Eq. IEDG d): fhat = F(uhat, q) n + lambda (u -
+//    uhat), lambda = |vhat . n| + chat evaluated at uhat.
+//  * Pointwise Jacobians by forward-mode dual numbers, m directions per pass:
+//    one pass over u (or uhat), one pass per gradient direction l over q_{., l}.
+//  * Residual projections (Eq. IEDG b, c):
+//      R_u[a][i]  = sum_{g,r} Dxi_r[g][a] fvol[i][r][g] + sum_g Phi[g][a] mvol[i][g]
+//                 + sum_fp PhiF[fp][a] fsur[i][fp]
+//      Rhat[s][i] = sum_fp PhiF[fp][bnode[s]] fsur[i][fp]
+//    with fvol = -w Jinv[r][j] F_ij, mvol = alpha w (u - u_ref)_i, fsur = wf fhat_i.
+//  * R_q = M (q - q*) where q* = H_l uhat - G_l u is the lifted gradient that makes
+//    R_q vanish (Eq. IEDG a is linear: R_q = M q + B_l u - E_l uhat).
+#include "iedg_internal.cuh"
+
+namespace iedg {
+namespace {
+
+// ------------------------------------------------------------------ dual numbers
+template <int N>
+struct Dual {
+  double v;
+  double t[N];
+};
+
+template <int N>
+__device__ inline Dual<N> mkconst(double v) {
+  Dual<N> r;
+  r.v = v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.t[k] = 0.0;
+  return r;
+}
+template <int N>
+__device__ inline Dual<N> operator+(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> r; r.v = a.v + b.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.t[k] = a.t[k] + b.t[k];
+  return r;
+}
+template <int N>
+__device__ inline Dual<N> operator-(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> r; r.v = a.v - b.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.t[k] = a.t[k] - b.t[k];
+  return r;
+}
+template <int N>
+__device__ inline Dual<N> operator*(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> r; r.v = a.v * b.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.t[k] = a.t[k] * b.v + a.v * b.t[k];
+  return r;
+}
+template <int N>
+__device__ inline Dual<N> operator*(double a, const Dual<N>& b) {
+  Dual<N> r; r.v = a * b.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.t[k] = a * b.t[k];
+  return r;
+}
+template <int N>
+__device__ inline Dual<N> operator+(const Dual<N>& a, double b) {
+  Dual<N> r = a; r.v += b; return r;
+}
+template <int N>
+__device__ inline Dual<N> recip(const Dual<N>& a) {
+  Dual<N> r; r.v = 1.0 / a.v;
+  double s = -r.v * r.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.t[k] = s * a.t[k];
+  return r;
+}
+template <int N>
+__device__ inline Dual<N> dsqrt(const Dual<N>& a) {
+  Dual<N> r; r.v = sqrt(a.v);
+  double s = 0.5 / r.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.t[k] = s * a.t[k];
+  return r;
+}
+template <int N>
+__device__ inline Dual<N> dabs(const Dual<N>& a) {
+  double s = a.v > 0 ? 1.0 : (a.v < 0 ? -1.0 : 0.0);   // sign(0) := 0
+  Dual<N> r; r.v = fabs(a.v);
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.t[k] = s * a.t[k];
+  return r;
+}
+__device__ inline double recip(double a) { return 1.0 / a; }
+__device__ inline double dsqrt(double a) { return sqrt(a); }
+__device__ inline double dabs(double a) { return fabs(a); }
+template <class T> __device__ inline T mk(double v);
+template <> __device__ inline double mk<double>(double v) { return v; }
+template <> __device__ inline Dual<4> mk<Dual<4>>(double v) { return mkconst<4>(v); }
+template <> __device__ inline Dual<5> mk<Dual<5>>(double v) { return mkconst<5>(v); }
+
+// Navier-Stokes flux F[i][j], i < M = D + 2, j < D.
+template <int D, class T>
+__device__ void ns_flux(const T* u, const T (*q)[D], const Phys& ph, T (*F)[D]) {
+  constexpr int M = D + 2;
+  const T rinv = recip(u[0]);
+  T v[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) v[i] = u[1 + i] * rinv;
+  const T E = u[M - 1] * rinv;
+  T vv = v[0] * v[0];
+#pragma unroll
+  for (int i = 1; i < D; ++i) vv = vv + v[i] * v[i];
+  const T p = (ph.gamma - 1.0) * (u[M - 1] - 0.5 * (u[0] * vv));
+  T dv[D][D];
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) dv[i][j] = (q[1 + i][j] - v[i] * q[0][j]) * rinv;
+  T div = dv[0][0];
+#pragma unroll
+  for (int k = 1; k < D; ++k) div = div + dv[k][k];
+  const double ire = 1.0 / ph.Re, kap = ph.gamma / (ph.Re * ph.Pr);
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    T de = (q[M - 1][j] - E * q[0][j]) * rinv;
+#pragma unroll
+    for (int k = 0; k < D; ++k) de = de - v[k] * dv[k][j];
+    F[0][j] = u[1 + j];
+    T fe = v[j] * (u[M - 1] + p) - kap * de;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      T tau = dv[i][j] + dv[j][i];
+      if (i == j) tau = tau - (2.0 / 3.0) * div;
+      tau = ire * tau;
+      T fm = u[1 + i] * v[j] - tau;
+      if (i == j) fm = fm + p;
+      F[1 + i][j] = fm;
+      fe = fe - v[i] * tau;
+    }
+    F[M - 1][j] = fe;
+  }
+}
+
+template <int D, class T>
+__device__ T lf_lambda(const T* u, const double* n, const Phys& ph) {
+  constexpr int M = D + 2;
+  const T rinv = recip(u[0]);
+  T vn = mk<T>(0.0), vv = mk<T>(0.0);
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    T vj = u[1 + j] * rinv;
+    vn = vn + n[j] * vj;
+    vv = vv + vj * vj;
+  }
+  T p = (ph.gamma - 1.0) * (u[M - 1] - 0.5 * (u[0] * vv));
+  return dabs(vn) + dsqrt((ph.gamma * p) * rinv);
+}
+
+// dF[i][j][k] = dF_ij/du_k and dQ[i][j][k][l] = dF_ij/dq_kl at (u, q).
+template <int D>
+__device__ void flux_jacobians(const double* u, const double (*q)[D], const Phys& ph,
+                               double (*dF)[D][D + 2], double (*dQ)[D][D + 2][D]) {
+  constexpr int M = D + 2;
+  using TD = Dual<M>;
+  TD ud[M], qd[M][D], Fd[M][D];
+  // pass over u
+#pragma unroll
+  for (int k = 0; k < M; ++k) { ud[k] = mkconst<M>(u[k]); ud[k].t[k] = 1.0; }
+#pragma unroll
+  for (int k = 0; k < M; ++k)
+#pragma unroll
+    for (int l = 0; l < D; ++l) qd[k][l] = mkconst<M>(q[k][l]);
+  ns_flux<D, TD>(ud, qd, ph, Fd);
+#pragma unroll
+  for (int i = 0; i < M; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j)
+#pragma unroll
+      for (int k = 0; k < M; ++k) dF[i][j][k] = Fd[i][j].t[k];
+  // passes over q_{., l}
+#pragma unroll
+  for (int k = 0; k < M; ++k) ud[k] = mkconst<M>(u[k]);
+#pragma unroll 1
+  for (int l = 0; l < D; ++l) {
+#pragma unroll
+    for (int k = 0; k < M; ++k)
+#pragma unroll
+      for (int ll = 0; ll < D; ++ll) {
+        qd[k][ll] = mkconst<M>(q[k][ll]);
+        if (ll == l) qd[k][ll].t[k] = 1.0;
+      }
+    ns_flux<D, TD>(ud, qd, ph, Fd);
+#pragma unroll
+    for (int i = 0; i < M; ++i)
+#pragma unroll
+      for (int j = 0; j < D; ++j)
+#pragma unroll
+        for (int k = 0; k < M; ++k) dQ[i][j][k][l] = Fd[i][j].t[k];
+  }
+}
+
+// ------------------------------------------------------------------ point kernel
+// One CTA per element.  jac = false: residual at (u, q).  jac = true: Jacobians at
+// (u, q) into PointJac, right-hand sides -R_u(u, q*), -Rhat(u, q*) into the last
+// column of the bordered element matrix.
+template <int D>
+__global__ void k_points(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ,
+                         const int64_t* __restrict__ etrace, const double* __restrict__ U,
+                         const double* __restrict__ Q, const double* __restrict__ QS,
+                         const double* __restrict__ UH, const double* __restrict__ UREF, bool jac,
+                         double* __restrict__ RU, double* __restrict__ RHAT, double* __restrict__ S) {
+  constexpr int M = D + 2;
+  extern __shared__ double sm[];
+  const int64_t e = blockIdx.x;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int Np = dm.Np, Nq = dm.Nq, Nb = dm.Nb, Nfp = dm.Nfp, Nfq = dm.Nfq, Nfn = dm.Nfn;
+  double* su = sm;                         // [Np][M]
+  double* sq = su + Np * M;                // [Np][M][D]
+  double* sqs = sq + Np * M * D;           // [Np][M][D]  (q* for the right-hand side)
+  double* sur = sqs + Np * M * D;          // [Np][M]
+  double* suh = sur + Np * M;              // [Nb][M]
+  double* fvol = suh + Nb * M;             // [M][D][Nq]
+  double* mvol = fvol + M * D * Nq;        // [M][Nq]
+  double* fsur = mvol + M * Nq;            // [M][Nfp]
+  const bool has_ref = UREF != nullptr && ph.alpha != 0.0;
+  for (int i = tid; i < Np * M; i += nth) {
+    su[i] = U[e * Np * M + i];
+    sur[i] = has_ref ? UREF[e * Np * M + i] : 0.0;
+  }
+  for (int i = tid; i < Np * M * D; i += nth) {
+    sq[i] = Q[e * Np * M * D + i];
+    sqs[i] = QS ? QS[e * Np * M * D + i] : sq[i];
+  }
+  for (int i = tid; i < Nb * M; i += nth) {
+    int s = i / M, k = i % M;
+    suh[i] = UH[etrace[e * Nb + s] * M + k];
+  }
+  __syncthreads();
+  const size_t jvs = (size_t)(1 + D) * D * Nq;    // stride of one (i,k) pair in Jv
+  const size_t jfs = (size_t)(1 + D) * Nfp;
+  // ---- volume points
+  for (int g = tid; g < Nq; g += nth) {
+    double u[M], q[M][D], qr[M][D], du[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      u[i] = 0; du[i] = 0;
+#pragma unroll
+      for (int j = 0; j < D; ++j) { q[i][j] = 0; qr[i][j] = 0; }
+    }
+    const double* phi = ref.Phi + (size_t)g * Np;
+    for (int a = 0; a < Np; ++a) {
+      double ph_a = phi[a];
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        u[i] += ph_a * su[a * M + i];
+        du[i] += ph_a * (su[a * M + i] - sur[a * M + i]);
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          q[i][j] += ph_a * sq[(a * M + i) * D + j];
+          qr[i][j] += ph_a * sqs[(a * M + i) * D + j];
+        }
+      }
+    }
+    const double w = G.wdet[e * Nq + g];
+    double Ji[D][D];
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+      for (int j = 0; j < D; ++j) Ji[r][j] = G.Jinv[((e * Nq + g) * D + r) * D + j];
+    double F[M][D];
+    ns_flux<D, double>(u, qr, ph, F);
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+#pragma unroll
+      for (int r = 0; r < D; ++r) {
+        double s = 0;
+#pragma unroll
+        for (int j = 0; j < D; ++j) s += Ji[r][j] * F[i][j];
+        fvol[(i * D + r) * Nq + g] = -w * s;
+      }
+      mvol[i * Nq + g] = has_ref ? ph.alpha * w * du[i] : 0.0;
+    }
+    if (jac) {
+      double dF[M][D][M], dQ[M][D][M][D];
+      flux_jacobians<D>(u, q, ph, dF, dQ);
+      double* jv = PJ.Jv + (size_t)e * M * M * jvs;
+#pragma unroll
+      for (int i = 0; i < M; ++i)
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+          double* o = jv + (size_t)(i * M + k) * jvs;
+#pragma unroll
+          for (int r = 0; r < D; ++r) {
+            double s = 0;
+#pragma unroll
+            for (int j = 0; j < D; ++j) s += Ji[r][j] * dF[i][j][k];
+            o[(size_t)r * Nq + g] = -w * s;
+#pragma unroll
+            for (int l = 0; l < D; ++l) {
+              double t = 0;
+#pragma unroll
+              for (int j = 0; j < D; ++j) t += Ji[r][j] * dQ[i][j][k][l];
+              o[(size_t)(D + l * D + r) * Nq + g] = -w * t;
+            }
+          }
+        }
+    }
+  }
+  // ---- face points
+  for (int fp = tid; fp < Nfp; fp += nth) {
+    const int f = fp / Nfq;
+    double u[M], uh[M], q[M][D], qr[M][D];
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      u[i] = 0; uh[i] = 0;
+#pragma unroll
+      for (int j = 0; j < D; ++j) { q[i][j] = 0; qr[i][j] = 0; }
+    }
+    const double* phi = ref.PhiF + (size_t)fp * Np;
+    for (int t = 0; t < Nfn; ++t) {
+      int a = ref.fnode[f * Nfn + t];
+      int s = ref.slot[a];
+      double ph_a = phi[a];
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        u[i] += ph_a * su[a * M + i];
+        uh[i] += ph_a * suh[s * M + i];
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          q[i][j] += ph_a * sq[(a * M + i) * D + j];
+          qr[i][j] += ph_a * sqs[(a * M + i) * D + j];
+        }
+      }
+    }
+    const double wf = G.fw[e * Nfp + fp];
+    double n[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) n[j] = G.fn[(e * Nfp + fp) * D + j];
+    double F[M][D];
+    ns_flux<D, double>(uh, qr, ph, F);
+    const double lam = lf_lambda<D, double>(uh, n, ph);
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      double s = lam * (u[i] - uh[i]);
+#pragma unroll
+      for (int j = 0; j < D; ++j) s += F[i][j] * n[j];
+      fsur[i * Nfp + fp] = wf * s;
+    }
+    if (jac) {
+      Dual<M> ud[M];
+#pragma unroll
+      for (int k = 0; k < M; ++k) { ud[k] = mkconst<M>(uh[k]); ud[k].t[k] = 1.0; }
+      Dual<M> lamd = lf_lambda<D, Dual<M>>(ud, n, ph);
+      double dF[M][D][M], dQ[M][D][M][D];
+      flux_jacobians<D>(uh, q, ph, dF, dQ);
+      double* jf = PJ.Jf + (size_t)e * M * M * jfs;
+#pragma unroll
+      for (int i = 0; i < M; ++i)
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+          double* o = jf + (size_t)(i * M + k) * jfs;
+          double s = lamd.t[k] * (u[i] - uh[i]) - (i == k ? lam : 0.0);
+#pragma unroll
+          for (int j = 0; j < D; ++j) s += dF[i][j][k] * n[j];
+          o[fp] = wf * s;
+#pragma unroll
+          for (int l = 0; l < D; ++l) {
+            double t = 0;
+#pragma unroll
+            for (int j = 0; j < D; ++j) t += dQ[i][j][k][l] * n[j];
+            o[(size_t)(1 + l) * Nfp + fp] = wf * t;
+          }
+        }
+      PJ.lamw[e * Nfp + fp] = wf * lam;
+    }
+  }
+  __syncthreads();
+  // ---- projections onto the test functions
+  const double sgn = jac ? -1.0 : 1.0;
+  const int64_t nn = dm.n, ld = dm.ld;
+  for (int ai = tid; ai < Np * M; ai += nth) {
+    const int a = ai / M, i = ai % M;
+    double s = 0;
+    for (int g = 0; g < Nq; ++g) {
+      double t = ref.Phi[(size_t)g * Np + a] * mvol[i * Nq + g];
+#pragma unroll
+      for (int r = 0; r < D; ++r) t += ref.Dxi[((size_t)r * Nq + g) * Np + a] * fvol[(i * D + r) * Nq + g];
+      s += t;
+    }
+    if (ref.slot[a] >= 0)
+      for (int fp = 0; fp < Nfp; ++fp) s += ref.PhiF[(size_t)fp * Np + a] * fsur[i * Nfp + fp];
+    if (jac) S[(e * nn + (int64_t)i * Np + a) * ld + nn] = sgn * s;
+    else if (RU) RU[(e * Np + a) * M + i] = s;
+  }
+  for (int si = tid; si < Nb * M; si += nth) {
+    const int s = si / M, i = si % M;
+    const int a = ref.bnode[s];
+    double t = 0;
+    for (int fp = 0; fp < Nfp; ++fp) t += ref.PhiF[(size_t)fp * Np + a] * fsur[i * Nfp + fp];
+    if (jac) S[(e * nn + dm.nu + (int64_t)i * Nb + s) * ld + nn] = sgn * t;
+    else RHAT[(e * Nb + s) * M + i] = t;
+  }
+}
+
+// q*[e][c][k][l] = sum_t H_l[c][t] uhat_k(t) - sum_b G_l[c][b] u_k(b)
+__global__ void k_lift(Dims dm, Geo G, const int64_t* __restrict__ etrace, const double* __restrict__ U,
+                       const double* __restrict__ UH, double* __restrict__ QS) {
+  extern __shared__ double sm[];
+  const int64_t e = blockIdx.x;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int Np = dm.Np, Nb = dm.Nb, m = dm.m, d = dm.d;
+  double* su = sm;            // [Np][m]
+  double* suh = su + Np * m;  // [Nb][m]
+  for (int i = tid; i < Np * m; i += nth) su[i] = U[e * Np * m + i];
+  for (int i = tid; i < Nb * m; i += nth) suh[i] = UH[etrace[e * Nb + i / m] * m + i % m];
+  __syncthreads();
+  for (int idx = tid; idx < Np * m * d; idx += nth) {
+    int c = idx / (m * d), k = (idx / d) % m, l = idx % d;
+    const double* gl = G.Gl + (((size_t)e * d + l) * Np + c) * Np;
+    const double* hl = G.Hl + (((size_t)e * d + l) * Np + c) * Nb;
+    double s = 0;
+    for (int t = 0; t < Nb; ++t) s += hl[t] * suh[t * m + k];
+    for (int b = 0; b < Np; ++b) s -= gl[b] * su[b * m + k];
+    QS[e * Np * m * d + idx] = s;
+  }
+}
+
+// R_q = M (q - q*), optionally rhoq = q - q*
+__global__ void k_rq(Dims dm, Geo G, const double* __restrict__ Q, const double* __restrict__ QS,
+                     double* __restrict__ RQ, double* __restrict__ RHOQ) {
+  extern __shared__ double sm[];
+  const int64_t e = blockIdx.x;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int Np = dm.Np, w = dm.m * dm.d;
+  double* dq = sm;   // [Np][m d]
+  for (int i = tid; i < Np * w; i += nth) {
+    double v = Q[e * Np * w + i] - QS[e * Np * w + i];
+    dq[i] = v;
+    if (RHOQ) RHOQ[e * Np * w + i] = v;
+  }
+  __syncthreads();
+  if (!RQ) return;
+  const double* Ms = G.Mass + (size_t)e * Np * Np;
+  for (int idx = tid; idx < Np * w; idx += nth) {
+    int a = idx / w, c = idx % w;
+    double s = 0;
+    for (int b = 0; b < Np; ++b) s += Ms[a * Np + b] * dq[b * w + c];
+    RQ[e * Np * w + idx] = s;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_points(iedg_mesh* M, const double* u, const double* q, const double* qs,
+                          const double* uhat, const double* u_ref, bool jacobians, double* r_u,
+                          double* rhat, cudaStream_t st) {
+  const Dims& dm = M->dm;
+  size_t smem = sizeof(double) * ((size_t)dm.Np * dm.m * (2 + 2 * dm.d) + dm.Nb * dm.m +
+                                  (size_t)dm.m * dm.d * dm.Nq + dm.m * dm.Nq + dm.m * dm.Nfp);
+  const int threads = 128;
+  if (dm.d == 2) {
+    cudaFuncSetAttribute(k_points<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_points<2><<<(unsigned)M->E, threads, smem, st>>>(dm, M->ph, M->ref, M->geo, M->pj, M->etrace, u, q,
+                                                       qs, uhat, u_ref, jacobians, r_u, rhat, M->S);
+  } else {
+    cudaFuncSetAttribute(k_points<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_points<3><<<(unsigned)M->E, threads, smem, st>>>(dm, M->ph, M->ref, M->geo, M->pj, M->etrace, u, q,
+                                                       qs, uhat, u_ref, jacobians, r_u, rhat, M->S);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lift(iedg_mesh* M, const double* u, const double* uhat, double* qstar, cudaStream_t st) {
+  const Dims& dm = M->dm;
+  size_t smem = sizeof(double) * (size_t)(dm.Np + dm.Nb) * dm.m;
+  k_lift<<<(unsigned)M->E, 128, smem, st>>>(dm, M->geo, M->etrace, u, uhat, qstar);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rq(iedg_mesh* M, const double* q, const double* qs, double* r_q, double* rhoq,
+                      cudaStream_t st) {
+  const Dims& dm = M->dm;
+  size_t smem = sizeof(double) * (size_t)dm.Np * dm.m * dm.d;
+  k_rq<<<(unsigned)M->E, 128, smem, st>>>(dm, M->geo, q, qs, r_q, rhoq);
+  return cudaGetLastError();
+}
+
+}  // namespace iedg

@@ -1,0 +1,123 @@
+// Assembly of the condensed element matrices into the block compressed-row trace
+// matrix, K = sum_e P_e^T K_e P_e, R = sum_e P_e^T R_e (Sec. 2.2.2: m x m blocks),
+// as a deterministic gather over precomputed contribution lists (element order),
+// and the element back-substitution dZ_e = A_e^-1 (F_e - B_e dU_e).
+#include "iedg_internal.cuh"
+
+namespace iedg {
+namespace {
+
+// One thread per (block, i, k) entry.
+__global__ void k_scatter_K(Dims dm, int64_t nnzb, const int64_t* __restrict__ kc_ptr,
+                            const int64_t* __restrict__ kc_src, const double* __restrict__ S,
+                            double* __restrict__ K) {
+  const int m2 = dm.m * dm.m;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nnzb * m2) return;
+  const int64_t blk = idx / m2;
+  const int i = (int)(idx % m2) / dm.m, k = (int)(idx % m2) % dm.m;
+  const int64_t Nb = dm.Nb, nb2 = Nb * Nb, ld = dm.ld, n = dm.n;
+  const int64_t row_off = dm.nu + (int64_t)i * Nb, col_off = dm.nu + (int64_t)k * Nb;
+  double v = 0.0;
+  for (int64_t c = kc_ptr[blk]; c < kc_ptr[blk + 1]; ++c) {
+    int64_t src = kc_src[c];
+    int64_t e = src / nb2, s = (src / Nb) % Nb, t = src % Nb;
+    v += S[(e * n + row_off + s) * ld + col_off + t];
+  }
+  K[idx] = v;
+}
+
+// One thread per (trace node, component): R[t][i] = sum over (e, s) of src(e, s, i).
+__global__ void k_scatter_R(Dims dm, int64_t T, const int64_t* __restrict__ rc_ptr,
+                            const int64_t* __restrict__ rc_src, const double* __restrict__ src,
+                            int64_t es, int64_t ss, int64_t cs, double* __restrict__ R) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= T * dm.m) return;
+  const int64_t t = idx / dm.m;
+  const int i = (int)(idx % dm.m);
+  double v = 0.0;
+  for (int64_t c = rc_ptr[t]; c < rc_ptr[t + 1]; ++c) {
+    int64_t es_ = rc_src[c];
+    int64_t e = es_ / dm.Nb, s = es_ % dm.Nb;
+    v += src[e * es + s * ss + i * cs];
+  }
+  R[idx] = v;
+}
+
+// One CTA per element.  rhs = (L^-1 P Ft) - (L^-1 P Bt) dU_e, du = U^-1 rhs,
+// dq_kl = (q* - q) - G_l du_k + H_l dU_k.
+constexpr int BS_THREADS = 256;
+__global__ void __launch_bounds__(BS_THREADS)
+k_backsub(Dims dm, Geo G, const int64_t* __restrict__ etrace, const double* __restrict__ S,
+          const double* __restrict__ rhoq, const double* __restrict__ duhat,
+          double* __restrict__ du, double* __restrict__ dq) {
+  extern __shared__ double sm[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = BS_THREADS / 32;
+  const int64_t e = blockIdx.x;
+  const int n = dm.n, nu = dm.nu, nt = dm.nt, ld = dm.ld, m = dm.m, d = dm.d, Np = dm.Np, Nb = dm.Nb;
+  const double* A = S + e * (int64_t)n * ld;
+  double* sU = sm;          // [nt]   dU_e, component-major (k Nb + t)
+  double* y = sU + nt;      // [nu]
+  for (int idx = tid; idx < nt; idx += BS_THREADS) {
+    int k = idx / Nb, t = idx % Nb;
+    sU[idx] = duhat[etrace[e * Nb + t] * m + k];
+  }
+  __syncthreads();
+  for (int r = warp; r < nu; r += nw) {
+    const double* row = A + (int64_t)r * ld + nu;
+    double s = 0.0;
+    for (int c = lane; c < nt; c += 32) s = fma(row[c], sU[c], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) y[r] = row[nt] - s;
+  }
+  __syncthreads();
+  for (int j = nu - 1; j >= 0; --j) {
+    if (tid == 0) y[j] = y[j] / A[(int64_t)j * ld + j];
+    __syncthreads();
+    const double yj = y[j];
+    for (int r = tid; r < j; r += BS_THREADS) y[r] = fma(-A[(int64_t)r * ld + j], yj, y[r]);
+    __syncthreads();
+  }
+  for (int idx = tid; idx < Np * m; idx += BS_THREADS) {
+    int b = idx / m, k = idx % m;
+    du[e * Np * m + idx] = y[k * Np + b];
+  }
+  for (int idx = tid; idx < Np * m * d; idx += BS_THREADS) {
+    int c = idx / (m * d), k = (idx / d) % m, l = idx % d;
+    const double* gl = G.Gl + (((size_t)e * d + l) * Np + c) * Np;
+    const double* hl = G.Hl + (((size_t)e * d + l) * Np + c) * Nb;
+    double s = -rhoq[e * Np * m * d + idx];
+    for (int b = 0; b < Np; ++b) s = fma(-gl[b], y[k * Np + b], s);
+    for (int t = 0; t < Nb; ++t) s = fma(hl[t], sU[k * Nb + t], s);
+    dq[e * Np * m * d + idx] = s;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_scatter_K(iedg_mesh* M, double* K, cudaStream_t st) {
+  const int64_t total = M->nnzb * M->dm.m * M->dm.m;
+  if (total == 0) return cudaSuccess;
+  const int th = 256;
+  k_scatter_K<<<(unsigned)((total + th - 1) / th), th, 0, st>>>(M->dm, M->nnzb, M->kc_ptr, M->kc_src, M->S, K);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_R(iedg_mesh* M, const double* src, int64_t es, int64_t ss, int64_t cs, double* R,
+                             cudaStream_t st) {
+  const int64_t total = M->T * M->dm.m;
+  const int th = 256;
+  k_scatter_R<<<(unsigned)((total + th - 1) / th), th, 0, st>>>(M->dm, M->T, M->rc_ptr, M->rc_src, src, es, ss,
+                                                                  cs, R);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backsub(iedg_mesh* M, const double* duhat, double* du, double* dq, cudaStream_t st) {
+  const Dims& dm = M->dm;
+  size_t smem = sizeof(double) * (size_t)(dm.nt + dm.nu);
+  k_backsub<<<(unsigned)M->E, BS_THREADS, smem, st>>>(dm, M->geo, M->etrace, M->S, M->rhoq, duhat, du, dq);
+  return cudaGetLastError();
+}
+
+}  // namespace iedg

@@ -1,0 +1,237 @@
+"""Thin ctypes binding of the C ABI in include/iedg.h (argument marshalling only).
+
+Every step of the computation runs in libiedg.so's CUDA kernels; this module only
+checks shapes/dtypes, passes device pointers of torch tensors and the current CUDA
+stream, and turns error codes into exceptions.  There is no CPU fallback: if the
+shared library is missing or no GPU is present, calls raise.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libiedg.so")
+
+OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "CUDA", -3: "OOM", -4: "MESH", -5: "NOT_ASSEMBLED", -6: "UNSUPPORTED"}
+EXPORTS = ("iedg_create_mesh", "iedg_destroy_mesh", "iedg_last_error", "iedg_mesh_info",
+           "iedg_trace_pattern", "iedg_eval_residual", "iedg_assemble_condensed",
+           "iedg_back_substitute", "iedg_element_status", "iedg_profile_enable",
+           "iedg_profile_read", "iedg_profile_reset")
+
+
+class IedgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"iedg error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("order", ctypes.c_int32), ("quad_extra", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("n_elem", ctypes.c_int64), ("n_trace", ctypes.c_int64),
+                ("node_xyz", ctypes.c_void_p), ("elem_trace", ctypes.c_void_p),
+                ("gamma", ctypes.c_double), ("Pr", ctypes.c_double), ("Re", ctypes.c_double),
+                ("Minf", ctypes.c_double), ("alpha", ctypes.c_double), ("stab", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load():
+    """Load libiedg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} not built: run __graft_entry__.build() or "
+                          f"python -m paper_1605_01020_gb300.build")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    lib.iedg_create_mesh.argtypes = [ctypes.POINTER(MeshDesc), vp, ctypes.POINTER(vp)]
+    lib.iedg_create_mesh.restype = ctypes.c_int
+    lib.iedg_destroy_mesh.argtypes = [vp]
+    lib.iedg_destroy_mesh.restype = ctypes.c_int
+    lib.iedg_last_error.argtypes = [vp]
+    lib.iedg_last_error.restype = ctypes.c_char_p
+    lib.iedg_mesh_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i64),
+                                   ctypes.POINTER(i64)]
+    lib.iedg_mesh_info.restype = ctypes.c_int
+    lib.iedg_trace_pattern.argtypes = [vp, vp, vp, vp]
+    lib.iedg_trace_pattern.restype = ctypes.c_int
+    lib.iedg_eval_residual.argtypes = [vp] * 10
+    lib.iedg_eval_residual.restype = ctypes.c_int
+    lib.iedg_assemble_condensed.argtypes = [vp] * 8
+    lib.iedg_assemble_condensed.restype = ctypes.c_int
+    lib.iedg_back_substitute.argtypes = [vp] * 5
+    lib.iedg_back_substitute.restype = ctypes.c_int
+    lib.iedg_element_status.argtypes = [vp, vp, vp]
+    lib.iedg_element_status.restype = ctypes.c_int64
+    lib.iedg_profile_enable.argtypes = [vp, i32]
+    lib.iedg_profile_enable.restype = ctypes.c_int
+    lib.iedg_profile_read.argtypes = [vp, i32, vp, vp, vp, ctypes.POINTER(i32)]
+    lib.iedg_profile_read.restype = ctypes.c_int
+    lib.iedg_profile_reset.argtypes = [vp]
+    lib.iedg_profile_reset.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t, shape=None, dtype=None, name="tensor"):
+    if t is None:
+        return None
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+class Mesh:
+    """Handle around iedg_create_mesh / iedg_destroy_mesh with the compute calls."""
+
+    def __init__(self, node_xyz, elem_trace, n_trace, order, gamma=1.4, Pr=0.72, Re=1e3, Minf=0.2,
+                 alpha=0.0, quad_extra=2, precision=0, stream=None):
+        lib = load()
+        X = np.ascontiguousarray(node_xyz, dtype=np.float64)
+        ET = np.ascontiguousarray(elem_trace, dtype=np.int64)
+        self.E, self.Np_in, self.d = X.shape
+        self.m = self.d + 2
+        self.T = int(n_trace)
+        self.order = int(order)
+        desc = MeshDesc(self.d, self.order, quad_extra, precision, self.E, self.T,
+                        X.ctypes.data, ET.ctypes.data, gamma, Pr, Re, Minf, alpha, 0, 0)
+        h = ctypes.c_void_p()
+        rc = lib.iedg_create_mesh(ctypes.byref(desc), ctypes.c_void_p(_stream(stream)), ctypes.byref(h))
+        if rc != OK:
+            raise IedgError(rc, lib.iedg_last_error(None).decode())
+        self._h = h
+        np_, nb, nnzb, ws = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+        self._check(lib.iedg_mesh_info(h, ctypes.byref(np_), ctypes.byref(nb), ctypes.byref(nnzb), ctypes.byref(ws)))
+        self.Np, self.Nb, self.nnzb, self.workspace_bytes = np_.value, nb.value, nnzb.value, ws.value
+        if self.Np != self.Np_in or ET.shape != (self.E, self.Nb):
+            raise ValueError("node_xyz / elem_trace shapes do not match the order")
+
+    def _check(self, rc):
+        if rc != OK:
+            raise IedgError(rc, load().iedg_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().iedg_destroy_mesh(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ helpers
+    def _empty(self, *shape, dtype=None):
+        torch = _torch()
+        return torch.empty(*shape, dtype=dtype or torch.float64, device="cuda")
+
+    def trace_pattern(self, stream=None):
+        torch = _torch()
+        row_ptr = self._empty(self.T + 1, dtype=torch.int64)
+        col = self._empty(self.nnzb, dtype=torch.int32)
+        self._check(load().iedg_trace_pattern(self._h, row_ptr.data_ptr(), col.data_ptr(), _stream(stream)))
+        return row_ptr, col
+
+    def eval_residual(self, u, uhat, q=None, u_ref=None, q_out=None, r_q=None, r_u=None, r_fl=None,
+                      stream=None, want=("r_q", "r_u", "r_fl")):
+        torch = _torch()
+        E, Np, m, d, T = self.E, self.Np, self.m, self.d, self.T
+        f64 = torch.float64
+        if q is None and q_out is None:
+            q_out = self._empty(E, Np, m, d)
+        if r_q is None and "r_q" in want:
+            r_q = self._empty(E, Np, m, d)
+        if r_u is None and "r_u" in want:
+            r_u = self._empty(E, Np, m)
+        if r_fl is None and "r_fl" in want:
+            r_fl = self._empty(T, m)
+        self._check(load().iedg_eval_residual(
+            self._h, _ptr(u, (E, Np, m), f64, "u"), _ptr(uhat, (T, m), f64, "uhat"),
+            _ptr(q, (E, Np, m, d), f64, "q"), _ptr(u_ref, (E, Np, m), f64, "u_ref"),
+            _ptr(q_out, (E, Np, m, d), f64, "q_out"), _ptr(r_q, (E, Np, m, d), f64, "r_q"),
+            _ptr(r_u, (E, Np, m), f64, "r_u"), _ptr(r_fl, (T, m), f64, "r_fl"), _stream(stream)))
+        return dict(q=q_out if q is None else q, r_q=r_q, r_u=r_u, r_fl=r_fl)
+
+    def assemble_condensed(self, u, q, uhat, u_ref=None, K=None, R=None, stream=None):
+        torch = _torch()
+        E, Np, m, d, T = self.E, self.Np, self.m, self.d, self.T
+        f64 = torch.float64
+        K = self._empty(self.nnzb, m, m) if K is None else K
+        R = self._empty(T, m) if R is None else R
+        self._check(load().iedg_assemble_condensed(
+            self._h, _ptr(u, (E, Np, m), f64, "u"), _ptr(q, (E, Np, m, d), f64, "q"),
+            _ptr(uhat, (T, m), f64, "uhat"), _ptr(u_ref, (E, Np, m), f64, "u_ref"),
+            _ptr(K, (self.nnzb, m, m), f64, "K"), _ptr(R, (T, m), f64, "R"), _stream(stream)))
+        return K, R
+
+    def back_substitute(self, duhat, du=None, dq=None, stream=None):
+        torch = _torch()
+        E, Np, m, d, T = self.E, self.Np, self.m, self.d, self.T
+        f64 = torch.float64
+        du = self._empty(E, Np, m) if du is None else du
+        dq = self._empty(E, Np, m, d) if dq is None else dq
+        self._check(load().iedg_back_substitute(
+            self._h, _ptr(duhat, (T, m), f64, "duhat"), _ptr(du, (E, Np, m), f64, "du"),
+            _ptr(dq, (E, Np, m, d), f64, "dq"), _stream(stream)))
+        return du, dq
+
+    def element_status(self, stream=None):
+        out = np.zeros(self.E, dtype=np.int8)
+        rc = load().iedg_element_status(self._h, out.ctypes.data, _stream(stream))
+        if rc < 0:
+            self._check(int(rc))
+        return out
+
+
+    # ------------------------------------------------------------------ tracing
+    def profile_enable(self, enable=True):
+        self._check(load().iedg_profile_enable(self._h, 1 if enable else 0))
+
+    def profile_reset(self):
+        self._check(load().iedg_profile_reset(self._h))
+
+    def profile_read(self):
+        """{kernel name: (launches, summed device ms)}; synchronises the events."""
+        cap = 64
+        names = ctypes.create_string_buffer(32 * cap)
+        launches = np.zeros(cap, dtype=np.int64)
+        ms = np.zeros(cap, dtype=np.float64)
+        n = ctypes.c_int32()
+        self._check(load().iedg_profile_read(self._h, cap, names, launches.ctypes.data, ms.ctypes.data,
+                                             ctypes.byref(n)))
+        out = {}
+        for i in range(min(n.value, cap)):
+            nm = names.raw[32 * i:32 * (i + 1)].split(b"\0", 1)[0].decode()
+            out[nm] = (int(launches[i]), float(ms[i]))
+        return out
+
+
+def mesh_from_workload(wl, precision=0, stream=None):
+    """Convenience: a Mesh for a workloads.Workload."""
+    p = wl.params
+    return Mesh(wl.mesh.node_xyz, wl.mesh.elem_trace, wl.mesh.n_trace, wl.mesh.p, gamma=p["gamma"],
+                Pr=p["Pr"], Re=p["Re"], Minf=p["Minf"], alpha=p["alpha"], precision=precision, stream=stream)

@@ -1,0 +1,153 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the same
+seeded inputs.  Tolerance for the FP64 path: max |x - x_oracle| / max |x_oracle|
+<= 1e-11 per output array (K per BSR block row); index structures bit-exact."""
+import numpy as np
+import pytest
+
+from oracle import iedg as oiedg
+from paper_1605_01020_gb300 import workloads as W
+from oracle_helpers import problem
+from gpu_helpers import bsr_row_err, dev, host, lib_mesh, oracle_K_rows, rel_err
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-11
+
+
+def _case(name):
+    if name == "cfg1":
+        return W.config(1)
+    if name == "cfg1-noisy":
+        wl = W.config(1)
+        st = W.make_state(wl.mesh, W.fourier_perturbed_field(2, 0.2, 1001), 1002, noise=0.01, uref_shift=0.01)
+        return W.Workload(wl.name + " + nodal noise", wl.mesh, st, wl.params)
+    if name == "p3-2cube":
+        return W.config(2, N=2)
+    if name == "p2-curved":
+        wl = W.config(3, N=2)
+        mesh = W.structured_mesh(3, 3, 2, mapping=W.stretched_mapping(77, ratio=10.0))
+        st = W.make_state(mesh, W.taylor_green_field(0.3), 78, noise=0.01, uref_shift=0.01)
+        prm = dict(wl.params, Re=200.0)
+        return W.Workload("3D p=2 3^3 curved", mesh, st, prm)
+    if name == "2d-p3-steady":
+        mesh = W.structured_mesh(2, (3, 4), 3)
+        st = W.make_state(mesh, W.fourier_perturbed_field(2, 0.3, 5, amp=0.05), 6, noise=0.01)
+        prm = dict(gamma=1.4, Pr=0.72, Re=100.0, Minf=0.3, alpha=0.0)
+        return W.Workload("2D p=3 3x4 steady", mesh, st, prm)
+    if name == "2d-p1":
+        mesh = W.structured_mesh(2, 4, 1)
+        st = W.make_state(mesh, W.fourier_perturbed_field(2, 0.3, 7, amp=0.05), 8, noise=0.01, uref_shift=0.01)
+        prm = dict(gamma=1.4, Pr=0.72, Re=100.0, Minf=0.3, alpha=W.dirk_alpha())
+        return W.Workload("2D p=1 4x4", mesh, st, prm)
+    raise KeyError(name)
+
+
+CASES = ["cfg1", "cfg1-noisy", "p3-2cube", "p2-curved", "2d-p3-steady", "2d-p1"]
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_residual_parity(name):
+    wl = _case(name)
+    st = wl.state
+    pb = problem(wl.mesh, wl.params)
+    Rq, Ru, Rh, Rfl = pb.residual(st.u, st.q, st.uhat, st.u_ref)
+    mesh = lib_mesh(wl)
+    out = mesh.eval_residual(dev(st.u), dev(st.uhat), q=dev(st.q), u_ref=dev(st.u_ref))
+    assert rel_err(host(out["r_q"]), Rq) <= TOL
+    assert rel_err(host(out["r_u"]), Ru) <= TOL
+    assert rel_err(host(out["r_fl"]), Rfl, floor=np.abs(Rh).max()) <= TOL
+
+
+@pytest.mark.parametrize("name", ["cfg1", "p2-curved"])
+def test_lifted_gradient_parity(name):
+    """q = NULL: q from R_q = 0 (Eq. IEDG a), then R_q vanishes."""
+    wl = _case(name)
+    st = wl.state
+    pb = problem(wl.mesh, wl.params)
+    q_o = pb.solve_q(st.u, st.uhat)
+    mesh = lib_mesh(wl)
+    out = mesh.eval_residual(dev(st.u), dev(st.uhat), q=None)
+    assert rel_err(host(out["q"]), q_o) <= TOL
+    assert np.abs(host(out["r_q"])).max() <= 1e-12 * np.abs(q_o).max()
+    Rq, Ru, Rh, Rfl = pb.residual(st.u, q_o, st.uhat)
+    assert rel_err(host(out["r_u"]), Ru) <= TOL
+    assert rel_err(host(out["r_fl"]), Rfl, floor=np.abs(Rh).max()) <= TOL
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_trace_pattern_bit_exact(name):
+    wl = _case(name)
+    mesh = lib_mesh(wl)
+    rp, col = mesh.trace_pattern()
+    rp_o, col_o = oiedg.bsr_pattern(wl.mesh.elem_trace, wl.mesh.n_trace)
+    assert np.array_equal(host(rp), rp_o)
+    assert np.array_equal(host(col).astype(np.int64), col_o)
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_condensed_parity(name):
+    wl = _case(name)
+    st = wl.state
+    pb = problem(wl.mesh, wl.params)
+    E = wl.mesh.n_elem
+    Ke, Re = zip(*[pb.condense_qelim(e, st.u, st.q, st.uhat, st.u_ref) for e in range(E)])
+    row_ptr, col, vals, R = oiedg.assemble(wl.mesh.elem_trace, wl.mesh.n_trace, np.array(Ke), np.array(Re))
+    mesh = lib_mesh(wl)
+    K_d, R_d = mesh.assemble_condensed(dev(st.u), dev(st.q), dev(st.uhat), u_ref=dev(st.u_ref))
+    assert bsr_row_err(row_ptr, host(K_d), vals, range(wl.mesh.n_trace)) <= TOL
+    assert rel_err(host(R_d), R, floor=np.abs(np.array(Re)).max()) <= TOL
+    assert (mesh.element_status() == 0).all()
+    # back-substitution
+    du_d, dq_d = mesh.back_substitute(dev(st.duhat))
+    du_o = np.zeros_like(st.u)
+    dq_o = np.zeros_like(st.q)
+    for e in range(E):
+        du_o[e], dq_o[e] = pb.back_substitute_qelim(e, st.u, st.q, st.uhat, st.duhat, st.u_ref)
+    assert rel_err(host(du_d), du_o) <= TOL
+    assert rel_err(host(dq_d), dq_o) <= TOL
+
+
+def test_back_substitute_before_assembly_is_an_error():
+    from paper_1605_01020_gb300 import iedg
+    wl = _case("cfg1")
+    mesh = lib_mesh(wl)
+    with pytest.raises(iedg.IedgError) as ei:
+        mesh.back_substitute(dev(wl.state.duhat))
+    assert ei.value.code == -5
+
+
+def test_inverted_element_rejected():
+    from paper_1605_01020_gb300 import iedg
+    wl = _case("cfg1")
+    X = wl.mesh.node_xyz.copy()
+    X[3] = X[3][:, ::-1]          # swap x and y of one element: detJ < 0
+    with pytest.raises(iedg.IedgError) as ei:
+        iedg.Mesh(X, wl.mesh.elem_trace, wl.mesh.n_trace, wl.mesh.p, **{k: wl.params[k] for k in ("gamma", "Pr", "Re", "Minf", "alpha")})
+    assert ei.value.code == -4
+
+
+def test_full_size_p3_sampled():
+    """The 3D p=3 16^3 workload at full size, in the launch configuration the
+    benchmark times: sampled block rows of K and R, sampled element updates."""
+    wl = W.config(2)
+    st = wl.state
+    mesh = lib_mesh(wl)
+    u, q, uh = dev(st.u), dev(st.q), dev(st.uhat)
+    res = mesh.eval_residual(u, uh, q=q)
+    K_d, R_d = mesh.assemble_condensed(u, q, uh)
+    du_d, dq_d = mesh.back_substitute(dev(st.duhat))
+    K_h, R_h = host(K_d), host(R_d)
+    assert np.isfinite(K_h).all() and (mesh.element_status() == 0).all()
+    pb = problem(wl.mesh, wl.params)
+    rng = np.random.default_rng(0)
+    rows = rng.choice(wl.mesh.n_trace, 3, replace=False)
+    row_ptr, col, vals, R, els, re_max = oracle_K_rows(pb, wl.mesh, st, rows)
+    assert bsr_row_err(row_ptr, K_h, vals, rows) <= TOL
+    assert rel_err(R_h[rows], R[rows], floor=re_max) <= TOL
+    # residual on the touched elements and trace rows
+    Rq, Ru, Rh, Rfl = pb.residual(st.u, st.q, st.uhat, els=els)
+    assert rel_err(host(res["r_u"])[els], Ru) <= TOL
+    assert rel_err(host(res["r_q"])[els], Rq) <= TOL
+    for e in els[:2]:
+        du_o, dq_o = pb.back_substitute_qelim(e, st.u, st.q, st.uhat, st.duhat)
+        assert rel_err(host(du_d[e]), du_o) <= TOL
+        assert rel_err(host(dq_d[e]), dq_o) <= TOL

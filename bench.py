@@ -41,6 +41,36 @@ def a6_flops(nu, nt):
     return sum((n - k - 1) + 2 * (n - k - 1) * (n - k) + 2 * (n - k - 1) for k in range(nu))
 
 
+def a4a5_flops(d, p, nq1):
+    """Algorithmic flops of element-block assembly (A_uu, A_uq volume and face terms)
+    plus the q-elimination, the fixed dense-count formulas for one element."""
+    m = d + 2
+    Np, Nq, Nb = (p + 1) ** d, nq1 ** d, (p + 1) ** d - (p - 1) ** d
+    Nfp, Nfq = (p + 1) ** (d - 1), nq1 ** (d - 1)
+    a4v = 2 * m * m * d * Np * Np * Nq * (1 + d)
+    a4f = 2 * d * (4 * m * m + 2 * m * m * d) * 2 * Nfp * Nfp * Nfq
+    a5 = 2 * m * m * d * (Np ** 3 + 2 * Np * Np * Nb + Np * Nb * Nb)
+    return a4v + a4f + a5
+
+
+def assemble_actual_flops(d, p, nq1):
+    """Flops the assembly kernel performs per element with the q-elimination folded in
+    at the quadrature points (volume contraction, right-operand build, face terms)."""
+    m = d + 2
+    Np, Nq, Nb = (p + 1) ** d, nq1 ** d, (p + 1) ** d - (p - 1) ** d
+    Nfn, Nfq = (p + 1) ** (d - 1), nq1 ** (d - 1)
+    nf = 2 * d
+    vol = 2 * Np * Nq * d * (Np + Nb) + 2 * Nq * d * (Np * (1 + d) + Nb * d)
+    face = nf * (2 * Nfq * (Np * (1 + d) + Nb * (1 + d)) + 2 * Nfn * Nfq * (Np + Nb))
+    return m * m * (vol + face)
+
+
+# DRAM bytes per element of the FP64 LU / Schur kernel, from one ncu capture of
+# k_lu on the 8^3 p=3 case (512 elements): 35.49 GB per launch -> 6.93e7 B/element
+# (profiles/lu_schur_fp64_p3.md).  Valid for the kernel version profiled there.
+LU_FP64_DRAM_BYTES_PER_ELEMENT = 35.485378e9 / 512
+
+
 def workload_name(wl):
     return f"{wl.name} ({wl.mesh.n_elem} elements), FP64: residual + condensed trace Jacobian + back-substitution"
 
@@ -256,10 +286,8 @@ def run_ours(args, wl, rank, world, local_rank):
     h2d = sum(t.numel() * t.element_size() for t in (hu, huh, hduh))
     d2h = sum(t.numel() * t.element_size() for t in (hK, hR, hdu, hdq))
 
-    if world > 1:
-        t = torch.tensor([ms, ms_e2e], dtype=f64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms, ms_e2e = float(t[0]), float(t[1])
+    from paper_1605_01020_gb300.dist import max_over_ranks
+    ms, ms_e2e = max_over_ranks([ms, ms_e2e], dev)
     if rank != 0:
         return
     total_elems = E * args.steps * world
@@ -273,16 +301,22 @@ def run_ours(args, wl, rank, world, local_rank):
     props = torch.cuda.get_device_properties(dev)
     sm_max = clocks["sm_max_mhz"] or 2070.0
     peak_alu = props.multi_processor_count * DFMA_PER_CLK_PER_SM * 2 * sm_max * 1e6
-    dm = dict(nu=m * Np, nt=m * mesh.Nb)
-    flops = {"lu_schur": a6_flops(dm["nu"], dm["nt"]) * E}
+    nq1 = wl.mesh.p + 2
+    flops = {"lu_schur": a6_flops(m * Np, m * mesh.Nb) * E,
+             "assemble": a4a5_flops(d, wl.mesh.p, nq1) * E}
+    actual = {"lu_schur": flops["lu_schur"], "assemble": assemble_actual_flops(d, wl.mesh.p, nq1) * E}
+    traffic = {"lu_schur": LU_FP64_DRAM_BYTES_PER_ELEMENT * E if (d, wl.mesh.p) == (3, 3) else None}
     roof = None
     if name in flops:
-        achieved = flops[name] / (kms / launches / 1e3)
+        t_launch = kms / launches / 1e3
+        achieved = flops[name] / t_launch
         roof = {"kernel": name, "bound": "alu", "achieved": achieved / 1e12, "peak": peak_alu / 1e12,
-                "unit": "TFLOP/s", "frac": achieved / peak_alu, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak_alu, "traffic": traffic.get(name),
                 "peak_source": f"FP64 DFMA: {props.multi_processor_count} SMs x {DFMA_PER_CLK_PER_SM} FMA/clk x 2 "
                                f"x {sm_max:.0f} MHz (derived; measured DFMA loop 1.19 TFLOP/s)",
-                "algorithmic_flops_per_launch": flops[name]}
+                "algorithmic_flops_per_launch": flops[name],
+                "actual_flops_per_launch": actual[name],
+                "frac_actual": actual[name] / t_launch / peak_alu}
     peaks, src = measured_peaks()
     cpu = None
     if not args.no_cpu_baseline:

@@ -137,6 +137,28 @@ int iedg_back_substitute(iedg_mesh* mesh, const double* duhat, double* du, doubl
  * (>= 0) or a negative error code. */
 int64_t iedg_element_status(iedg_mesh* mesh, int8_t* out, void* stream);
 
+/* Residual without any allocation (no counterpart in the paper; a service for
+ * callers that cannot allocate device memory when they need a residual, e.g. code
+ * whose device memory is owned by a framework pool, real-time loops where the
+ * implicit synchronisation of cudaMalloc/cudaFree is not allowed, or plug-ins that
+ * are given buffers but no allocation rights).  Same result as iedg_eval_residual
+ * with a given q: r_u [n_elem][Np][m] (may be NULL) and r_fl [n_trace][m].  q is
+ * required (no lifting), r_q is not produced.
+ * Scratch: the per-element trace residuals go to one file-scope device array of
+ * IEDG_STATIC_SCRATCH_DOUBLES doubles (16 MiB) that every GPU loading the library
+ * holds until the process exits; meshes with n_elem * Nb * m above that are
+ * rejected with IEDG_ERR_INVALID_ARG.  The array is shared by all calls and keeps
+ * the last call's contents (every entry read is written first in the same call):
+ * calls that overlap on the GPU (other streams, other handles) race on it and must
+ * be serialised by the caller.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  No cudaMalloc, cudaFree or allocating library
+ * routine is called.  Kernel launches of this entry point are not traced. */
+#define IEDG_STATIC_SCRATCH_DOUBLES (1u << 21)
+int iedg_eval_residual_static(iedg_mesh* mesh, const double* u, const double* uhat,
+                              const double* q, const double* u_ref, double* r_u,
+                              double* r_fl, void* stream);
+
 /* Tracing (no counterpart in the paper; it times the library's own kernels).
  * Every kernel launch is counted per kernel name.  While profiling is enabled,
  * each launch is also bracketed by CUDA events recorded on the launching stream,

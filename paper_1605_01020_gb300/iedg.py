@@ -18,7 +18,7 @@ ERRORS = {-1: "INVALID_ARG", -2: "CUDA", -3: "OOM", -4: "MESH", -5: "NOT_ASSEMBL
 EXPORTS = ("iedg_create_mesh", "iedg_destroy_mesh", "iedg_last_error", "iedg_mesh_info",
            "iedg_trace_pattern", "iedg_eval_residual", "iedg_assemble_condensed",
            "iedg_back_substitute", "iedg_element_status", "iedg_profile_enable",
-           "iedg_profile_read", "iedg_profile_reset")
+           "iedg_profile_read", "iedg_profile_reset", "iedg_eval_residual_static")
 
 
 class IedgError(RuntimeError):
@@ -68,6 +68,8 @@ def load():
     lib.iedg_back_substitute.restype = ctypes.c_int
     lib.iedg_element_status.argtypes = [vp, vp, vp]
     lib.iedg_element_status.restype = ctypes.c_int64
+    lib.iedg_eval_residual_static.argtypes = [vp] * 8
+    lib.iedg_eval_residual_static.restype = ctypes.c_int
     lib.iedg_profile_enable.argtypes = [vp, i32]
     lib.iedg_profile_enable.restype = ctypes.c_int
     lib.iedg_profile_read.argtypes = [vp, i32, vp, vp, vp, ctypes.POINTER(i32)]

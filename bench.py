@@ -286,8 +286,12 @@ def run_ours(args, wl, rank, world, local_rank):
     h2d = sum(t.numel() * t.element_size() for t in (hu, huh, hduh))
     d2h = sum(t.numel() * t.element_size() for t in (hK, hR, hdu, hdq))
 
+    mixed = None if args.no_mixed else run_mixed(args, wl, mesh, dev, step_outputs=(K, R, du, dq),
+                                                   inputs=(u, uh, duh), flush=flush, barrier=barrier)
     from paper_1605_01020_gb300.dist import max_over_ranks
     ms, ms_e2e = max_over_ranks([ms, ms_e2e], dev)
+    if mixed is not None:
+        (mixed["ms_total"],) = max_over_ranks([mixed["ms_total"]], dev)
     if rank != 0:
         return
     total_elems = E * args.steps * world
@@ -317,6 +321,11 @@ def run_ours(args, wl, rank, world, local_rank):
                 "algorithmic_flops_per_launch": flops[name],
                 "actual_flops_per_launch": actual[name],
                 "frac_actual": actual[name] / t_launch / peak_alu}
+    if mixed is not None:
+        mms = mixed.pop("ms_total")
+        mixed["value"] = total_elems / (mms / 1e3)
+        mixed["ms_per_step"] = mms / args.steps
+        mixed["speedup_vs_fp64"] = ms / mms
     peaks, src = measured_peaks()
     cpu = None
     if not args.no_cpu_baseline:
@@ -337,8 +346,57 @@ def run_ours(args, wl, rank, world, local_rank):
             "kernels": {k: {"launches": v[0], "ms": v[1], "share": v[1] / tot_ms if tot_ms else None}
                         for k, v in prof.items()},
             "element_status_nonzero": int((status != 0).sum()),
+            "mixed": mixed,
             "peaks": {"source": src, **{k: v for k, v in peaks.items() if isinstance(v, (int, float))}}}
     print(json.dumps(line), flush=True)
+
+
+def run_mixed(args, wl, mesh64, dev, step_outputs, inputs, flush, barrier):
+    """The same step in the mixed form (FP32 element matrix and partial LU, FP64
+    residuals and refinement of R, du, dq), timed the same way; errors against the
+    FP64 path's outputs on the same inputs."""
+    import torch
+    from paper_1605_01020_gb300 import iedg
+    K64, R64, du64, dq64 = step_outputs
+    u, uh, duh = inputs
+    mesh = iedg.mesh_from_workload(wl, precision=1)
+    E, Np, m, d, T = mesh.E, mesh.Np, mesh.m, mesh.d, mesh.T
+    f64 = torch.float64
+    q = torch.empty(E, Np, m, d, dtype=f64, device=dev)
+    rq, ru, rfl = torch.empty_like(q), torch.empty(E, Np, m, dtype=f64, device=dev), torch.empty(T, m, dtype=f64, device=dev)
+    K, R = torch.empty_like(K64), torch.empty_like(R64)
+    du, dq = torch.empty_like(du64), torch.empty_like(dq64)
+
+    def step():
+        mesh.eval_residual(u, uh, q=None, q_out=q, r_q=rq, r_u=ru, r_fl=rfl)
+        mesh.assemble_condensed(u, q, uh, K=K, R=R)
+        mesh.back_substitute(duh, du, dq)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    barrier()
+    mesh.profile_reset()
+    mesh.profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        flush.zero_()
+        step()
+    e1.record()
+    barrier()
+    mesh.profile_enable(False)
+    prof = mesh.profile_read()
+    tot = sum(v[1] for v in prof.values())
+    err = lambda a, b: float((a - b).abs().max() / b.abs().max().clamp_min(1e-300))
+    status = mesh.element_status()
+    out = {"ms_total": e0.elapsed_time(e1), "precision": "FP32 element matrix + partial LU, FP64 refinement",
+           "err_vs_fp64": {"K": err(K, K64), "R": err(R, R64), "du": err(du, du64), "dq": err(dq, dq64)},
+           "element_status_nonzero": int((status != 0).sum()),
+           "gpu_launches": sum(v[0] for v in prof.values()),
+           "kernels": {k: {"launches": v[0], "ms": v[1], "share": v[1] / tot if tot else None} for k, v in prof.items()}}
+    mesh.close()
+    return out
 
 
 def main():
@@ -350,6 +408,7 @@ def main():
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--cells", type=int, default=None, help="override cells per direction (smaller case)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-elems", type=int, default=4)
     args = ap.parse_args()

@@ -62,10 +62,14 @@ extern "C" {
 
 /* element status codes (iedg_element_status) */
 #define IEDG_ELEM_OK        0
+#define IEDG_ELEM_REFINE    1   /* mixed path: refinement did not reach 1e-10 relative residual */
 #define IEDG_ELEM_SINGULAR  2   /* exact zero pivot in the element block          */
 #define IEDG_ELEM_NONFINITE 3   /* NaN/Inf met in the element's Schur complement  */
 
-#define IEDG_PRECISION_FP64 0
+#define IEDG_PRECISION_FP64  0   /* every step in FP64                                   */
+#define IEDG_PRECISION_MIXED 1   /* element matrix and partial LU in FP32 (K to FP32
+                                    accuracy); residuals, point Jacobians and the
+                                    right-hand side R and updates du, dq refined to FP64 */
 
 typedef struct iedg_mesh iedg_mesh;   /* opaque */
 
@@ -73,7 +77,7 @@ typedef struct {
   int32_t dim;              /* 2 or 3                                                */
   int32_t order;            /* polynomial degree p = k of approximation and geometry */
   int32_t quad_extra;       /* n_q1 = p + quad_extra Gauss points per direction (2)  */
-  int32_t precision;        /* IEDG_PRECISION_FP64                                   */
+  int32_t precision;        /* IEDG_PRECISION_FP64 or IEDG_PRECISION_MIXED           */
   int64_t n_elem;
   int64_t n_trace;
   const double*  node_xyz;   /* HOST [n_elem][Np][dim]: isoparametric nodes (Sec. 3.1) */

@@ -357,7 +357,15 @@ static int create_impl(const iedg_mesh_desc* D, cudaStream_t st, iedg_mesh* M) {
   CUDA_TRY(dalloc(M, &M->qstar, E * Np * m * d));
   CUDA_TRY(dalloc(M, &M->rhoq, E * Np * m * d));
   CUDA_TRY(dalloc(M, &M->rhat, E * Nb * m));
-  CUDA_TRY(dalloc(M, &M->S, (size_t)E * dm.n * dm.ld));
+  if (M->precision == IEDG_PRECISION_FP64) {
+    CUDA_TRY(dalloc(M, &M->S, (size_t)E * dm.n * dm.ld));
+  } else {
+    CUDA_TRY(dalloc(M, &M->S32, (size_t)E * dm.n * dm.ld));
+    CUDA_TRY(dalloc(M, &M->piv, (size_t)E * dm.nu));
+    CUDA_TRY(dalloc(M, &M->rhs64, (size_t)E * dm.n));
+    CUDA_TRY(dalloc(M, &M->y64, (size_t)E * dm.nu));
+    CUDA_TRY(dalloc(M, &M->re64, (size_t)E * dm.nt));
+  }
   CUDA_TRY(dalloc(M, &M->status, E));
   CUDA_TRY(dalloc(M, &M->dev_flag, 1));
   CUDA_TRY(cudaMemsetAsync(M->dev_flag, 0, sizeof(int), st));
@@ -390,8 +398,8 @@ extern "C" int iedg_create_mesh(const iedg_mesh_desc* D, void* stream, iedg_mesh
     return fail(M, IEDG_ERR_UNSUPPORTED, "order must be 1..4 (3D) or 1..3 (2D)");
   if (D->quad_extra < 1 || D->quad_extra > 3)
     return fail(M, IEDG_ERR_UNSUPPORTED, "quad_extra must be 1..3");
-  if (D->precision != IEDG_PRECISION_FP64)
-    return fail(M, IEDG_ERR_UNSUPPORTED, "only the FP64 path is built");
+  if (D->precision != IEDG_PRECISION_FP64 && D->precision != IEDG_PRECISION_MIXED)
+    return fail(M, IEDG_ERR_UNSUPPORTED, "precision must be IEDG_PRECISION_FP64 or IEDG_PRECISION_MIXED");
   if (D->stab != 0) return fail(M, IEDG_ERR_UNSUPPORTED, "only Lax-Friedrichs stabilisation is built");
   if (D->n_elem <= 0 || D->n_trace <= 0 || !D->node_xyz || !D->elem_trace)
     return fail(M, IEDG_ERR_INVALID_ARG, "empty mesh or null mesh arrays");
@@ -403,6 +411,7 @@ extern "C" int iedg_create_mesh(const iedg_mesh_desc* D, void* stream, iedg_mesh
   M = new iedg_mesh();
   M->dm = make_dims(D->dim, D->order, D->quad_extra);
   M->ph = Phys{D->gamma, D->Pr, D->Re, D->alpha};
+  M->precision = D->precision;
   M->E = D->n_elem;
   M->T = D->n_trace;
   int rc = create_impl(D, (cudaStream_t)stream, M);
@@ -484,9 +493,13 @@ extern "C" int iedg_assemble_condensed(iedg_mesh* M, const double* u, const doub
   CUDA_TRY(TRACED("points_jacobian", launch_points(M, u, q, M->qstar, uhat, u_ref, true, nullptr, nullptr, st)));
   CUDA_TRY(TRACED("assemble", launch_assemble(M, st)));
   CUDA_TRY(TRACED("lu_schur", launch_lu(M, st)));
+  if (M->precision == IEDG_PRECISION_MIXED) CUDA_TRY(TRACED("refine", launch_refine(M, st)));
   CUDA_TRY(TRACED("scatter_K", launch_scatter_K(M, K, st)));
-  CUDA_TRY(TRACED("scatter_R", launch_scatter_R(M, M->S + (int64_t)dm.nu * dm.ld + dm.n, (int64_t)dm.n * dm.ld,
-                                                dm.ld, (int64_t)dm.Nb * dm.ld, R, st)));
+  if (M->precision == IEDG_PRECISION_FP64)
+    CUDA_TRY(TRACED("scatter_R", launch_scatter_R(M, M->S + (int64_t)dm.nu * dm.ld + dm.n, (int64_t)dm.n * dm.ld,
+                                                  dm.ld, (int64_t)dm.Nb * dm.ld, R, st)));
+  else
+    CUDA_TRY(TRACED("scatter_R", launch_scatter_R(M, M->re64, dm.nt, 1, dm.Nb, R, st)));
   M->assembled = true;
   return IEDG_OK;
 }
@@ -496,7 +509,10 @@ extern "C" int iedg_back_substitute(iedg_mesh* M, const double* duhat, double* d
   if (!M || !duhat || !du || !dq) return fail(M, IEDG_ERR_INVALID_ARG, "null argument");
   if (!M->assembled) return fail(M, IEDG_ERR_NOT_ASSEMBLED, "back-substitution before assembly");
   cudaStream_t st = (cudaStream_t)stream;
-  CUDA_TRY(TRACED("backsub", launch_backsub(M, duhat, du, dq, st)));
+  if (M->precision == IEDG_PRECISION_FP64)
+    CUDA_TRY(TRACED("backsub", launch_backsub(M, duhat, du, dq, st)));
+  else
+    CUDA_TRY(TRACED("backsub", launch_backsub_mixed(M, duhat, du, dq, st)));
   return IEDG_OK;
 }
 

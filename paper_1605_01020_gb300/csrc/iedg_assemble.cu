@@ -48,20 +48,26 @@ AsmCfg asm_cfg(const Dims& dm) {
   return c;
 }
 
+// T = double: FP64 path.  T = float: mixed path (FP32 element matrix; the FP64
+// right-hand sides are copied into column n by one CTA per element).
+template <class T>
 __global__ void __launch_bounds__(AS_THREADS)
-k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, Geo G, PointJac PJ, double* __restrict__ S) {
-  extern __shared__ double sm[];
+k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, Geo G, PointJac PJ, T* __restrict__ S,
+           const double* __restrict__ rhs64) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);
   const int tid = threadIdx.x;
-  const int64_t e = blockIdx.x;
-  const int pair = blockIdx.y, i = pair / dm.m, k = pair % dm.m;
-  const int c0 = blockIdx.z * cf.CW;
+  const int m2 = dm.m * dm.m;
+  const int64_t e = blockIdx.x / m2;                 // the m^2 CTAs of an element are adjacent
+  const int pair = blockIdx.x % m2, i = pair / dm.m, k = pair % dm.m;
+  const int c0 = blockIdx.y * cf.CW;
   const int d = dm.d, Np = dm.Np, Nb = dm.Nb, Nq = dm.Nq, Nfp = dm.Nfp, Nfq = dm.Nfq, Nfn = dm.Nfn;
   const int ncol = Np + Nb;
   const int KC = cf.KC, CW = cf.CW, RP = cf.rows_pad;
-  double* sA = sm;                      // [KC][RP]   Dxi_r[g][a]
-  double* sB = sA + KC * RP;            // [KC][CW]   W[(g, r)][col]
-  double* facc = sB + KC * CW;          // [Nb][CW]   face parts of the boundary rows
-  double* sV = facc + Nb * CW;          // [Nfq][CW]  face right operand
+  T* sA = sm;                           // [KC][RP]   Dxi_r[g][a]
+  T* sB = sA + KC * RP;                 // [KC][CW]   W[(g, r)][col]
+  T* facc = sB + KC * CW;               // [Nb][CW]   face parts of the boundary rows
+  T* sV = facc + Nb * CW;               // [Nfq][CW]  face right operand
   const size_t jvs = (size_t)(1 + d) * d * Nq;
   const double* jv = PJ.Jv + ((size_t)e * dm.m * dm.m + pair) * jvs;
   const size_t jfs = (size_t)(1 + d) * Nfp;
@@ -73,31 +79,31 @@ k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, Geo G, PointJac PJ, doubl
 
   const int trow = tid / cf.cg, tcol = tid % cf.cg;
   const bool gemm_thread = trow < cf.rg;
-  double acc[TM][TN];
+  T acc[TM][TN];
 #pragma unroll
   for (int a = 0; a < TM; ++a)
 #pragma unroll
-    for (int b = 0; b < TN; ++b) acc[a][b] = 0.0;
+    for (int b = 0; b < TN; ++b) acc[a][b] = (T)0;
 
   // ---- volume contraction, K = Nq d in chunks of GC points
   for (int g0 = 0; g0 < Nq; g0 += GC) {
     for (int idx = tid; idx < KC * RP; idx += AS_THREADS) {
       int kc = idx / RP, a = idx % RP;
       int g = g0 + kc / d, r = kc % d;
-      sA[idx] = (g < Nq && a < Np) ? ref.Dxi[((size_t)r * Nq + g) * Np + a] : 0.0;
+      sA[idx] = (T)((g < Nq && a < Np) ? ref.Dxi[((size_t)r * Nq + g) * Np + a] : 0.0);
     }
     for (int idx = tid; idx < KC * CW; idx += AS_THREADS) {
       int kc = idx / CW, col = c0 + idx % CW;
       int g = g0 + kc / d, r = kc % d;
-      double w = 0.0;
+      T w = 0;
       if (g < Nq && col < ncol) {
         if (col < Np) {
-          w = jv[(size_t)r * Nq + g] * ref.Phi[(size_t)g * Np + col];
+          w = (T)jv[(size_t)r * Nq + g] * (T)ref.Phi[(size_t)g * Np + col];
           for (int l = 0; l < d; ++l)
-            w -= jv[(size_t)(d + l * d + r) * Nq + g] * GlV[((size_t)l * Nq + g) * Np + col];
+            w -= (T)jv[(size_t)(d + l * d + r) * Nq + g] * (T)GlV[((size_t)l * Nq + g) * Np + col];
         } else {
           for (int l = 0; l < d; ++l)
-            w += jv[(size_t)(d + l * d + r) * Nq + g] * HlV[((size_t)l * Nq + g) * Nb + (col - Np)];
+            w += (T)jv[(size_t)(d + l * d + r) * Nq + g] * (T)HlV[((size_t)l * Nq + g) * Nb + (col - Np)];
         }
       }
       sB[idx] = w;
@@ -105,7 +111,7 @@ k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, Geo G, PointJac PJ, doubl
     __syncthreads();
     if (gemm_thread) {
       for (int kc = 0; kc < KC; ++kc) {
-        double av[TM], bv[TN];
+        T av[TM], bv[TN];
 #pragma unroll
         for (int a = 0; a < TM; ++a) av[a] = sA[kc * RP + trow * TM + a];
 #pragma unroll
@@ -120,21 +126,21 @@ k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, Geo G, PointJac PJ, doubl
   }
 
   // ---- face parts, accumulated per trace slot
-  for (int idx = tid; idx < Nb * CW; idx += AS_THREADS) facc[idx] = 0.0;
+  for (int idx = tid; idx < Nb * CW; idx += AS_THREADS) facc[idx] = (T)0;
   const double lamsel = (i == k) ? 1.0 : 0.0;
   for (int f = 0; f < dm.nf; ++f) {
     __syncthreads();
     for (int idx = tid; idx < Nfq * CW; idx += AS_THREADS) {
       int gf = idx / CW, col = c0 + idx % CW;
       int fp = f * Nfq + gf;
-      double v = 0.0;
+      T v = 0;
       if (col < Np) {
-        v = lamsel * PJ.lamw[e * Nfp + fp] * ref.PhiF[(size_t)fp * Np + col];
-        for (int l = 0; l < d; ++l) v -= jf[(size_t)(1 + l) * Nfp + fp] * GlF[((size_t)l * Nfp + fp) * Np + col];
+        v = (T)(lamsel * PJ.lamw[e * Nfp + fp]) * (T)ref.PhiF[(size_t)fp * Np + col];
+        for (int l = 0; l < d; ++l) v -= (T)jf[(size_t)(1 + l) * Nfp + fp] * (T)GlF[((size_t)l * Nfp + fp) * Np + col];
       } else if (col < ncol) {
         int t = col - Np;
-        v = jf[fp] * ref.PhiF[(size_t)fp * Np + ref.bnode[t]];
-        for (int l = 0; l < d; ++l) v += jf[(size_t)(1 + l) * Nfp + fp] * HlF[((size_t)l * Nfp + fp) * Nb + t];
+        v = (T)jf[fp] * (T)ref.PhiF[(size_t)fp * Np + ref.bnode[t]];
+        for (int l = 0; l < d; ++l) v += (T)jf[(size_t)(1 + l) * Nfp + fp] * (T)HlF[((size_t)l * Nfp + fp) * Nb + t];
       }
       sV[idx] = v;
     }
@@ -142,8 +148,8 @@ k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, Geo G, PointJac PJ, doubl
     for (int idx = tid; idx < Nfn * CW; idx += AS_THREADS) {
       int tn = idx / CW, cc = idx % CW;
       int a = ref.fnode[f * Nfn + tn];
-      double s = 0.0;
-      for (int gf = 0; gf < Nfq; ++gf) s += ref.PhiF[(size_t)(f * Nfq + gf) * Np + a] * sV[gf * CW + cc];
+      T s = 0;
+      for (int gf = 0; gf < Nfq; ++gf) s += (T)ref.PhiF[(size_t)(f * Nfq + gf) * Np + a] * sV[gf * CW + cc];
       facc[ref.slot[a] * CW + cc] += s;
     }
   }
@@ -151,7 +157,9 @@ k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, Geo G, PointJac PJ, doubl
 
   // ---- write the element rows
   const int64_t nn = dm.n, ld = dm.ld;
-  double* Se = S + e * nn * ld;
+  T* Se = S + e * nn * ld;
+  if (rhs64 != nullptr && pair == 0 && blockIdx.y == 0)
+    for (int r = tid; r < nn; r += AS_THREADS) Se[r * ld + nn] = (T)rhs64[e * nn + r];
   auto colS = [&](int col) -> int64_t { return col < Np ? (int64_t)k * Np + col : (int64_t)dm.nu + (int64_t)k * Nb + (col - Np); };
   if (gemm_thread) {
     const double* Ms = G.Mass + (size_t)e * Np * Np;
@@ -164,9 +172,9 @@ k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, Geo G, PointJac PJ, doubl
       for (int b = 0; b < TN; ++b) {
         int col = c0 + tcol * TN + b;
         if (col >= ncol || col >= c0 + CW) continue;
-        double v = acc[a][b];
+        T v = acc[a][b];
         if (sl >= 0) v += facc[sl * CW + (col - c0)];
-        if (i == k && col < Np) v += ph.alpha * Ms[row * Np + col];
+        if (i == k && col < Np) v += (T)(ph.alpha * Ms[row * Np + col]);
         Se[((int64_t)i * Np + row) * ld + colS(col)] = v;
       }
     }
@@ -184,90 +192,96 @@ k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, Geo G, PointJac PJ, doubl
 // first nu columns from all n rows.  Afterwards rows [nu, n) x cols [nu, n] hold
 // [K_e | R_e] = [Dt - Ct At^-1 Bt | Gt - Ct At^-1 Ft]; rows [0, nu) hold U (upper
 // triangle, cols < nu) and L^-1 P [Bt Ft] (cols >= nu) for the back-substitution.
-constexpr int NB = 16;
+// T = float (mixed path) additionally writes back every panel in full (the
+// multipliers L, in the row order of their own panel step) and the pivot rows, for
+// the refinement solves.
 constexpr int LU_THREADS = 256;
 constexpr int UCW = 64;     // trailing-update column chunk
 
+template <class T, int NB>
 __global__ void __launch_bounds__(LU_THREADS)
-k_lu(Dims dm, double* __restrict__ S, int8_t* __restrict__ status) {
-  extern __shared__ double sm[];
+k_lu(Dims dm, T* __restrict__ S, int8_t* __restrict__ status, int* __restrict__ pivots) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);
   __shared__ int piv[NB];
-  __shared__ double rv[LU_THREADS / 32];
+  __shared__ T rv[LU_THREADS / 32];
   __shared__ int ri[LU_THREADS / 32];
   __shared__ int sing;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t e = blockIdx.x;
   const int n = dm.n, nu = dm.nu, ld = dm.ld, ncol = n + 1;
-  double* A = S + e * (int64_t)n * ld;
-  double* P = sm;                       // [n][NB]
-  double* Uc = P + (size_t)n * NB;      // [NB][UCW]
+  T* A = S + e * (int64_t)n * ld;
+  T* P = sm;                            // [n][NB]
+  T* Uc = P + (size_t)n * NB;           // [NB][UCW]
   if (tid == 0) sing = 0;
   for (int kb = 0; kb < nu; kb += NB) {
     const int nb = min(NB, nu - kb), rows = n - kb, prow = nu - kb;
     for (int idx = tid; idx < rows * NB; idx += LU_THREADS) {
       int r = idx / NB, j = idx % NB;
-      P[idx] = j < nb ? A[(int64_t)(kb + r) * ld + kb + j] : 0.0;
+      P[idx] = j < nb ? A[(int64_t)(kb + r) * ld + kb + j] : (T)0;
     }
     __syncthreads();
     for (int j = 0; j < nb; ++j) {
-      double best = -1.0;
+      T best = -1;
       int bi = j;
       for (int r = j + tid; r < prow; r += LU_THREADS) {
-        double v = fabs(P[r * NB + j]);
+        T v = fabs(P[r * NB + j]);
         if (v > best) { best = v; bi = r; }
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        double ov = __shfl_xor_sync(0xffffffffu, best, o);
+        T ov = __shfl_xor_sync(0xffffffffu, best, o);
         int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
       }
       if (lane == 0) { rv[warp] = best; ri[warp] = bi; }
       __syncthreads();
       if (tid == 0) {
-        double bv = rv[0];
+        T bv = rv[0];
         int b = ri[0];
         for (int w = 1; w < LU_THREADS / 32; ++w)
           if (rv[w] > bv || (rv[w] == bv && ri[w] < b)) { bv = rv[w]; b = ri[w]; }
-        if (!(bv > 0.0)) { sing = 1; b = j; }
+        if (!(bv > 0)) { sing = 1; b = j; }
         piv[j] = b;
+        if (pivots) pivots[e * nu + kb + j] = kb + b;
       }
       __syncthreads();
       const int pr = piv[j];
       if (pr != j && tid < NB) {
-        double t = P[j * NB + tid];
+        T t = P[j * NB + tid];
         P[j * NB + tid] = P[pr * NB + tid];
         P[pr * NB + tid] = t;
       }
       __syncthreads();
-      const double pv = P[j * NB + j];
-      const double inv = pv != 0.0 ? 1.0 / pv : 0.0;
+      const T pv = P[j * NB + j];
+      const T inv = pv != (T)0 ? (T)1 / pv : (T)0;
       for (int r = j + 1 + tid; r < rows; r += LU_THREADS) {
-        double l = P[r * NB + j] * inv;
+        T l = P[r * NB + j] * inv;
         P[r * NB + j] = l;
         for (int c = j + 1; c < nb; ++c) P[r * NB + c] = fma(-l, P[j * NB + c], P[r * NB + c]);
       }
       __syncthreads();
     }
-    // U11 / L11 back to the element matrix
-    for (int idx = tid; idx < nb * nb; idx += LU_THREADS) {
+    // U11 / L11 (and, when the factors are kept, L21) back to the element matrix
+    const int wrows = pivots ? rows : nb;
+    for (int idx = tid; idx < wrows * nb; idx += LU_THREADS) {
       int r = idx / nb, j = idx % nb;
       A[(int64_t)(kb + r) * ld + kb + j] = P[r * NB + j];
     }
     // trailing columns: row interchanges, then U12 = L11^-1 A12
     for (int c = kb + nb + tid; c < ncol; c += LU_THREADS) {
-      double x[NB];
+      T x[NB];
       for (int j = 0; j < nb; ++j) {
         int pr = piv[j];
-        double* a0 = A + (int64_t)(kb + j) * ld + c;
+        T* a0 = A + (int64_t)(kb + j) * ld + c;
         if (pr != j) {
-          double* a1 = A + (int64_t)(kb + pr) * ld + c;
-          double t = *a0; *a0 = *a1; *a1 = t;
+          T* a1 = A + (int64_t)(kb + pr) * ld + c;
+          T t = *a0; *a0 = *a1; *a1 = t;
         }
         x[j] = *a0;
       }
       for (int j = 0; j < nb; ++j) {
-        double s = x[j];
+        T s = x[j];
         for (int jj = 0; jj < j; ++jj) s = fma(-P[j * NB + jj], x[jj], s);
         x[j] = s;
         A[(int64_t)(kb + j) * ld + c] = s;
@@ -280,12 +294,12 @@ k_lu(Dims dm, double* __restrict__ S, int8_t* __restrict__ status) {
       const int cw = min(UCW, ncol - cc);
       for (int idx = tid; idx < NB * UCW; idx += LU_THREADS) {
         int j = idx / UCW, c = idx % UCW;
-        Uc[idx] = (j < nb && c < cw) ? A[(int64_t)(kb + j) * ld + cc + c] : 0.0;
+        Uc[idx] = (j < nb && c < cw) ? A[(int64_t)(kb + j) * ld + cc + c] : (T)0;
       }
       __syncthreads();
       const int tc = tid % (UCW / 4), tr = tid / (UCW / 4);   // 16 x 16 threads, 4x4 tiles
       for (int rb = r0; rb < n; rb += 64) {
-        double a4[4][4];
+        T a4[4][4];
         int rr[4];
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
@@ -293,15 +307,15 @@ k_lu(Dims dm, double* __restrict__ S, int8_t* __restrict__ status) {
 #pragma unroll
           for (int b = 0; b < 4; ++b) {
             int c = tc * 4 + b;
-            a4[a][b] = (rr[a] < n && c < cw) ? A[(int64_t)rr[a] * ld + cc + c] : 0.0;
+            a4[a][b] = (rr[a] < n && c < cw) ? A[(int64_t)rr[a] * ld + cc + c] : (T)0;
           }
         }
         for (int j = 0; j < nb; ++j) {
-          double uv[4], lv[4];
+          T uv[4], lv[4];
 #pragma unroll
           for (int b = 0; b < 4; ++b) uv[b] = Uc[j * UCW + tc * 4 + b];
 #pragma unroll
-          for (int a = 0; a < 4; ++a) lv[a] = rr[a] < n ? P[(rr[a] - kb) * NB + j] : 0.0;
+          for (int a = 0; a < 4; ++a) lv[a] = rr[a] < n ? P[(rr[a] - kb) * NB + j] : (T)0;
 #pragma unroll
           for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -331,25 +345,37 @@ k_lu(Dims dm, double* __restrict__ S, int8_t* __restrict__ status) {
 
 }  // namespace
 
-cudaError_t launch_assemble(iedg_mesh* M, cudaStream_t st) {
+template <class T>
+static cudaError_t assemble_t(iedg_mesh* M, T* S, const double* rhs64, cudaStream_t st) {
   const Dims& dm = M->dm;
   AsmCfg cf = asm_cfg(dm);
-  size_t smem = sizeof(double) * ((size_t)cf.KC * cf.rows_pad + (size_t)cf.KC * cf.CW +
-                                  (size_t)dm.Nb * cf.CW + (size_t)dm.Nfq * cf.CW);
-  cudaError_t err = cudaFuncSetAttribute(k_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  size_t smem = sizeof(T) * ((size_t)cf.KC * cf.rows_pad + (size_t)cf.KC * cf.CW +
+                             (size_t)dm.Nb * cf.CW + (size_t)dm.Nfq * cf.CW);
+  cudaError_t err = cudaFuncSetAttribute(k_assemble<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  dim3 grid((unsigned)M->E, dm.m * dm.m, cf.nsplit);
-  k_assemble<<<grid, AS_THREADS, smem, st>>>(dm, M->ph, cf, M->ref, M->geo, M->pj, M->S);
+  dim3 grid((unsigned)(M->E * dm.m * dm.m), cf.nsplit);
+  k_assemble<T><<<grid, AS_THREADS, smem, st>>>(dm, M->ph, cf, M->ref, M->geo, M->pj, S, rhs64);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble(iedg_mesh* M, cudaStream_t st) {
+  if (M->precision == 0) return assemble_t<double>(M, M->S, nullptr, st);
+  return assemble_t<float>(M, M->S32, M->rhs64, st);
+}
+
+template <class T, int NB>
+static cudaError_t lu_t(iedg_mesh* M, T* S, int* piv, cudaStream_t st) {
+  const Dims& dm = M->dm;
+  size_t smem = sizeof(T) * ((size_t)dm.n * NB + (size_t)NB * UCW);
+  cudaError_t err = cudaFuncSetAttribute(k_lu<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  k_lu<T, NB><<<(unsigned)M->E, LU_THREADS, smem, st>>>(dm, S, M->status, piv);
   return cudaGetLastError();
 }
 
 cudaError_t launch_lu(iedg_mesh* M, cudaStream_t st) {
-  const Dims& dm = M->dm;
-  size_t smem = sizeof(double) * ((size_t)dm.n * NB + (size_t)NB * UCW);
-  cudaError_t err = cudaFuncSetAttribute(k_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (err != cudaSuccess) return err;
-  k_lu<<<(unsigned)M->E, LU_THREADS, smem, st>>>(dm, M->S, M->status);
-  return cudaGetLastError();
+  if (M->precision == 0) return lu_t<double, 16>(M, M->S, nullptr, st);
+  return lu_t<float, 32>(M, M->S32, M->piv, st);
 }
 
 }  // namespace iedg

@@ -79,7 +79,14 @@ struct iedg_mesh {
   double* qstar = nullptr;      // [E][Np][m][d] lifted gradient (R_q = 0)
   double* rhoq = nullptr;       // [E][Np][m][d] q - qstar of the last assembly
   double* rhat = nullptr;       // [E][Nb][m]    element trace residuals
-  double* S = nullptr;          // [E][n][ld]    bordered element matrices
+  double* S = nullptr;          // [E][n][ld]    bordered element matrices (FP64 path)
+  // mixed path (FP32 condensation, FP64 refinement)
+  int precision = 0;
+  float* S32 = nullptr;         // [E][n][ld]    bordered element matrices, FP32, L kept
+  int* piv = nullptr;           // [E][nu]       pivot rows of the FP32 partial LU
+  double* rhs64 = nullptr;      // [E][n]        FP64 right-hand sides F~, G~
+  double* y64 = nullptr;        // [E][nu]       refined A~^-1 F~
+  double* re64 = nullptr;       // [E][m][Nb]    refined R_e (component-major)
   int8_t* status = nullptr;     // [E]
   int* dev_flag = nullptr;      // geometry error flag
   bool assembled = false;
@@ -114,5 +121,13 @@ cudaError_t launch_scatter_R(iedg_mesh* M, const double* src, int64_t src_elem_s
                              cudaStream_t st);
 cudaError_t launch_backsub(iedg_mesh* M, const double* duhat, double* du, double* dq,
                            cudaStream_t st);
+cudaError_t launch_refine(iedg_mesh* M, cudaStream_t st);
+cudaError_t launch_backsub_mixed(iedg_mesh* M, const double* duhat, double* du, double* dq,
+                                 cudaStream_t st);
+
+// refinement controls of the mixed path
+constexpr int kRefineMaxIter = 8;
+constexpr double kRefineTol = 1e-14;      // stop at |r|_inf <= tol * |rhs|_inf
+constexpr double kRefineFlag = 1e-10;     // flag the element if not reached
 
 }  // namespace iedg

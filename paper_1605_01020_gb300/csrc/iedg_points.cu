@@ -209,7 +209,8 @@ __global__ void k_points(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ,
                          const int64_t* __restrict__ etrace, const double* __restrict__ U,
                          const double* __restrict__ Q, const double* __restrict__ QS,
                          const double* __restrict__ UH, const double* __restrict__ UREF, bool jac,
-                         double* __restrict__ RU, double* __restrict__ RHAT, double* __restrict__ S) {
+                         double* __restrict__ RU, double* __restrict__ RHAT, double* __restrict__ RHS,
+                         int64_t rhs_es, int64_t rhs_rs) {
   constexpr int M = D + 2;
   extern __shared__ double sm[];
   const int64_t e = blockIdx.x;
@@ -378,7 +379,7 @@ __global__ void k_points(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ,
   __syncthreads();
   // ---- projections onto the test functions
   const double sgn = jac ? -1.0 : 1.0;
-  const int64_t nn = dm.n, ld = dm.ld;
+  double* rhs_e = jac ? RHS + e * rhs_es : nullptr;
   for (int ai = tid; ai < Np * M; ai += nth) {
     const int a = ai / M, i = ai % M;
     double s = 0;
@@ -390,7 +391,7 @@ __global__ void k_points(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ,
     }
     if (ref.slot[a] >= 0)
       for (int fp = 0; fp < Nfp; ++fp) s += ref.PhiF[(size_t)fp * Np + a] * fsur[i * Nfp + fp];
-    if (jac) S[(e * nn + (int64_t)i * Np + a) * ld + nn] = sgn * s;
+    if (jac) rhs_e[((int64_t)i * Np + a) * rhs_rs] = sgn * s;
     else if (RU) RU[(e * Np + a) * M + i] = s;
   }
   for (int si = tid; si < Nb * M; si += nth) {
@@ -398,7 +399,7 @@ __global__ void k_points(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ,
     const int a = ref.bnode[s];
     double t = 0;
     for (int fp = 0; fp < Nfp; ++fp) t += ref.PhiF[(size_t)fp * Np + a] * fsur[i * Nfp + fp];
-    if (jac) S[(e * nn + dm.nu + (int64_t)i * Nb + s) * ld + nn] = sgn * t;
+    if (jac) rhs_e[((int64_t)dm.nu + (int64_t)i * Nb + s) * rhs_rs] = sgn * t;
     else RHAT[(e * Nb + s) * M + i] = t;
   }
 }
@@ -459,14 +460,18 @@ cudaError_t launch_points(iedg_mesh* M, const double* u, const double* q, const 
   size_t smem = sizeof(double) * ((size_t)dm.Np * dm.m * (2 + 2 * dm.d) + dm.Nb * dm.m +
                                   (size_t)dm.m * dm.d * dm.Nq + dm.m * dm.Nq + dm.m * dm.Nfp);
   const int threads = 128;
+  // right-hand sides: column n of the FP64 bordered matrix, or the FP64 rhs array
+  double* rhs = M->precision == 0 ? M->S + dm.n : M->rhs64;
+  int64_t es = M->precision == 0 ? (int64_t)dm.n * dm.ld : dm.n;
+  int64_t rs = M->precision == 0 ? dm.ld : 1;
   if (dm.d == 2) {
     cudaFuncSetAttribute(k_points<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_points<2><<<(unsigned)M->E, threads, smem, st>>>(dm, M->ph, M->ref, M->geo, M->pj, M->etrace, u, q,
-                                                       qs, uhat, u_ref, jacobians, r_u, rhat, M->S);
+                                                       qs, uhat, u_ref, jacobians, r_u, rhat, rhs, es, rs);
   } else {
     cudaFuncSetAttribute(k_points<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_points<3><<<(unsigned)M->E, threads, smem, st>>>(dm, M->ph, M->ref, M->geo, M->pj, M->etrace, u, q,
-                                                       qs, uhat, u_ref, jacobians, r_u, rhat, M->S);
+                                                       qs, uhat, u_ref, jacobians, r_u, rhat, rhs, es, rs);
   }
   return cudaGetLastError();
 }

@@ -1,0 +1,331 @@
+// Mixed-precision condensation: FP64 iterative refinement on top of the FP32
+// partial LU of the bordered element matrix.
+//
+// The FP32 factors give K_e to FP32 accuracy (times the conditioning of A~).  The
+// right-hand side R_e = G~ - C~ A~^-1 F~ and the element updates
+// du = A~^-1 (F~ - B~ dU) are recovered to FP64 accuracy by iterative refinement:
+//   x <- LU32^-1 b;  repeat  r = b - A~ x (FP64),  x <- x + LU32^-1 r
+// where A~ x, B~ z, C~ x are applied matrix-free in FP64 from the point Jacobians
+// and the lifted operators (the same element operator the assembly kernel forms,
+// see iedg_assemble.cu), so no FP64 element matrix is ever built.
+#include "iedg_internal.cuh"
+
+namespace iedg {
+namespace {
+
+constexpr int RF_THREADS = 256;
+constexpr int RF_NB = 32;            // panel width of the FP32 factorisation (k_lu<float, 32>)
+
+struct Work {
+  double *x, *z, *v, *b, *dqn, *xv, *xq, *tv, *xf, *zf, *xqf, *tf, *ou, *ot, *red;
+};
+
+__device__ Work carve(const Dims& dm, double* sm) {
+  Work w;
+  const int m = dm.m, d = dm.d;
+  double* p = sm;
+  w.x = p;   p += dm.nu;
+  w.z = p;   p += dm.nt;
+  w.v = p;   p += dm.nu;
+  w.b = p;   p += dm.nu;
+  w.dqn = p; p += m * d * dm.Np;
+  w.xv = p;  p += m * dm.Nq;
+  w.xq = p;  p += m * d * dm.Nq;
+  w.tv = p;  p += m * d * dm.Nq;
+  w.xf = p;  p += m * dm.Nfp;
+  w.zf = p;  p += m * dm.Nfp;
+  w.xqf = p; p += m * d * dm.Nfp;
+  w.tf = p;  p += m * dm.Nfp;
+  w.ou = p;  p += dm.nu;
+  w.ot = p;  p += dm.nt;
+  w.red = p; p += 32;
+  return w;
+}
+
+size_t work_doubles(const Dims& dm) {
+  const int m = dm.m, d = dm.d;
+  return (size_t)3 * dm.nu + dm.nt + (size_t)m * d * dm.Np + (size_t)m * dm.Nq * (1 + 2 * d) +
+         (size_t)m * dm.Nfp * (3 + d) + dm.nu + dm.nt + 32;
+}
+
+__device__ double block_max(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double r = 0.0;
+  for (int w = 0; w < RF_THREADS / 32; ++w) r = fmax(r, red[w]);
+  __syncthreads();
+  return r;
+}
+
+// ou = A~ x + B~ z (u-rows), ot = C~ x + D~ z (trace rows), all FP64.
+__device__ void element_apply(const Dims& dm, const Phys& ph, const RefTables& ref, const Geo& G,
+                              const PointJac& PJ, int64_t e, Work& w) {
+  const int tid = threadIdx.x;
+  const int m = dm.m, d = dm.d, Np = dm.Np, Nb = dm.Nb, Nq = dm.Nq, Nfp = dm.Nfp, Nfq = dm.Nfq;
+  const int Nfn = dm.Nfn;
+  // nodal lifted gradient of (x, z): dq_kl = -G_l x_k + H_l z_k
+  for (int idx = tid; idx < m * d * Np; idx += RF_THREADS) {
+    int k = idx / (d * Np), l = (idx / Np) % d, c = idx % Np;
+    const double* gl = G.Gl + (((size_t)e * d + l) * Np + c) * Np;
+    const double* hl = G.Hl + (((size_t)e * d + l) * Np + c) * Nb;
+    double s = 0.0;
+    for (int b = 0; b < Np; ++b) s = fma(-gl[b], w.x[k * Np + b], s);
+    for (int t = 0; t < Nb; ++t) s = fma(hl[t], w.z[k * Nb + t], s);
+    w.dqn[idx] = s;
+  }
+  __syncthreads();
+  // values at volume points
+  for (int idx = tid; idx < (m + m * d) * Nq; idx += RF_THREADS) {
+    int row = idx / Nq, g = idx % Nq;
+    const double* src = row < m ? w.x + row * Np : w.dqn + (row - m) * Np;
+    const double* phi = ref.Phi + (size_t)g * Np;
+    double s = 0.0;
+    for (int c = 0; c < Np; ++c) s = fma(phi[c], src[c], s);
+    if (row < m) w.xv[row * Nq + g] = s;
+    else w.xq[(row - m) * Nq + g] = s;
+  }
+  // values at face points (face nodes only)
+  for (int idx = tid; idx < (2 * m + m * d) * Nfp; idx += RF_THREADS) {
+    int row = idx / Nfp, fp = idx % Nfp, f = fp / Nfq;
+    const double* phi = ref.PhiF + (size_t)fp * Np;
+    double s = 0.0;
+    for (int tn = 0; tn < Nfn; ++tn) {
+      int a = ref.fnode[f * Nfn + tn];
+      double v;
+      if (row < m) v = w.x[row * Np + a];
+      else if (row < 2 * m) v = w.z[(row - m) * Nb + ref.slot[a]];
+      else v = w.dqn[(row - 2 * m) * Np + a];
+      s = fma(phi[a], v, s);
+    }
+    if (row < m) w.xf[row * Nfp + fp] = s;
+    else if (row < 2 * m) w.zf[(row - m) * Nfp + fp] = s;
+    else w.xqf[(row - 2 * m) * Nfp + fp] = s;
+  }
+  __syncthreads();
+  // pointwise linearised fluxes (weights and Jinv already folded in the tables)
+  const size_t jvs = (size_t)(1 + d) * d * Nq, jfs = (size_t)(1 + d) * Nfp;
+  const double* jv = PJ.Jv + (size_t)e * m * m * jvs;
+  const double* jf = PJ.Jf + (size_t)e * m * m * jfs;
+  for (int idx = tid; idx < m * d * Nq; idx += RF_THREADS) {
+    int i = idx / (d * Nq), r = (idx / Nq) % d, g = idx % Nq;
+    double s = 0.0;
+    for (int k = 0; k < m; ++k) {
+      const double* o = jv + (size_t)(i * m + k) * jvs;
+      s = fma(o[(size_t)r * Nq + g], w.xv[k * Nq + g], s);
+      for (int l = 0; l < d; ++l) s = fma(o[(size_t)(d + l * d + r) * Nq + g], w.xq[(k * d + l) * Nq + g], s);
+    }
+    w.tv[(i * d + r) * Nq + g] = s;
+  }
+  for (int idx = tid; idx < m * Nfp; idx += RF_THREADS) {
+    int i = idx / Nfp, fp = idx % Nfp;
+    double s = PJ.lamw[e * Nfp + fp] * w.xf[i * Nfp + fp];
+    for (int k = 0; k < m; ++k) {
+      const double* o = jf + (size_t)(i * m + k) * jfs;
+      s = fma(o[fp], w.zf[k * Nfp + fp], s);
+      for (int l = 0; l < d; ++l) s = fma(o[(size_t)(1 + l) * Nfp + fp], w.xqf[(k * d + l) * Nfp + fp], s);
+    }
+    w.tf[i * Nfp + fp] = s;
+  }
+  __syncthreads();
+  // projections onto the test functions
+  const double* Ms = G.Mass + (size_t)e * Np * Np;
+  for (int idx = tid; idx < m * Np; idx += RF_THREADS) {
+    int i = idx / Np, a = idx % Np;
+    double s = 0.0;
+    if (ph.alpha != 0.0) {
+      double t = 0.0;
+      for (int b = 0; b < Np; ++b) t = fma(Ms[a * Np + b], w.x[i * Np + b], t);
+      s = ph.alpha * t;
+    }
+    for (int g = 0; g < Nq; ++g)
+      for (int r = 0; r < d; ++r)
+        s = fma(ref.Dxi[((size_t)r * Nq + g) * Np + a], w.tv[(i * d + r) * Nq + g], s);
+    if (ref.slot[a] >= 0)
+      for (int fp = 0; fp < Nfp; ++fp) s = fma(ref.PhiF[(size_t)fp * Np + a], w.tf[i * Nfp + fp], s);
+    w.ou[idx] = s;
+  }
+  for (int idx = tid; idx < m * Nb; idx += RF_THREADS) {
+    int i = idx / Nb, sl = idx % Nb, a = ref.bnode[sl];
+    double s = 0.0;
+    for (int fp = 0; fp < Nfp; ++fp) s = fma(ref.PhiF[(size_t)fp * Np + a], w.tf[i * Nfp + fp], s);
+    w.ot[idx] = s;
+  }
+  __syncthreads();
+}
+
+// v <- A~32^-1 v with the FP32 factors (panel order, pivots as applied), FP64 arithmetic.
+__device__ void solve32(const Dims& dm, const float* __restrict__ A, const int* __restrict__ piv, double* v) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = RF_THREADS / 32;
+  const int nu = dm.nu, ld = dm.ld;
+  for (int kb = 0; kb < nu; kb += RF_NB) {
+    const int nb = min(RF_NB, nu - kb);
+    if (tid == 0)
+      for (int j = 0; j < nb; ++j) {
+        int p = piv[kb + j];
+        if (p != kb + j) { double t = v[kb + j]; v[kb + j] = v[p]; v[p] = t; }
+      }
+    __syncthreads();
+    if (warp == 0) {
+      for (int j = 0; j < nb; ++j) {
+        double vj = v[kb + j];
+        __syncwarp();
+        if (lane > j && lane < nb) v[kb + lane] = fma(-(double)A[(int64_t)(kb + lane) * ld + kb + j], vj, v[kb + lane]);
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    for (int r = kb + nb + tid; r < nu; r += RF_THREADS) {
+      const float* row = A + (int64_t)r * ld + kb;
+      double s = v[r];
+      for (int j = 0; j < nb; ++j) s = fma(-(double)row[j], v[kb + j], s);
+      v[r] = s;
+    }
+    __syncthreads();
+  }
+  const int last = ((nu - 1) / RF_NB) * RF_NB;
+  for (int kb = last; kb >= 0; kb -= RF_NB) {
+    const int nb = min(RF_NB, nu - kb);
+    for (int rr = warp; rr < nb; rr += nw) {
+      const int r = kb + rr;
+      const float* row = A + (int64_t)r * ld;
+      double s = 0.0;
+      for (int c = kb + nb + lane; c < nu; c += 32) s = fma((double)row[c], v[c], s);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) v[r] -= s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      for (int j = nb - 1; j >= 0; --j) {
+        if (lane == 0) v[kb + j] /= (double)A[(int64_t)(kb + j) * ld + kb + j];
+        __syncwarp();
+        double vj = v[kb + j];
+        if (lane < j) v[kb + lane] = fma(-(double)A[(int64_t)(kb + lane) * ld + kb + j], vj, v[kb + lane]);
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Solve A~ x = b (b in w.b) to FP64 accuracy; on return w.x = x and w.ou, w.ot hold
+// A~ x, C~ x for that x (w.z must be zero).  Returns the final relative residual.
+__device__ double refine_solve(const Dims& dm, const Phys& ph, const RefTables& ref, const Geo& G,
+                               const PointJac& PJ, int64_t e, const float* A, const int* piv, Work& w) {
+  const int tid = threadIdx.x, nu = dm.nu;
+  double bn = 0.0;
+  for (int i = tid; i < nu; i += RF_THREADS) { w.v[i] = w.b[i]; bn = fmax(bn, fabs(w.b[i])); }
+  bn = block_max(bn, w.red);
+  solve32(dm, A, piv, w.v);
+  for (int i = tid; i < nu; i += RF_THREADS) w.x[i] = w.v[i];
+  __syncthreads();
+  double rel = 0.0;
+  for (int it = 0; it <= kRefineMaxIter; ++it) {
+    element_apply(dm, ph, ref, G, PJ, e, w);
+    double rn = 0.0;
+    for (int i = tid; i < nu; i += RF_THREADS) {
+      double r = w.b[i] - w.ou[i];
+      w.v[i] = r;
+      rn = fmax(rn, fabs(r));
+    }
+    rn = block_max(rn, w.red);
+    rel = bn > 0.0 ? rn / bn : rn;
+    if (!(rel > kRefineTol) || it == kRefineMaxIter) break;   // also stops on NaN
+    solve32(dm, A, piv, w.v);
+    for (int i = tid; i < nu; i += RF_THREADS) w.x[i] += w.v[i];
+    __syncthreads();
+  }
+  return rel;
+}
+
+// One CTA per element: y = A~^-1 F~ refined, R_e = G~ - C~ y.
+__global__ void __launch_bounds__(RF_THREADS)
+k_refine(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ, const float* __restrict__ S32,
+         const int* __restrict__ piv, const double* __restrict__ rhs64, double* __restrict__ y64,
+         double* __restrict__ re64, int8_t* __restrict__ status) {
+  extern __shared__ double sm[];
+  Work w = carve(dm, sm);
+  const int64_t e = blockIdx.x;
+  const int tid = threadIdx.x;
+  const double* rhs = rhs64 + e * dm.n;
+  for (int i = tid; i < dm.nu; i += RF_THREADS) w.b[i] = rhs[i];
+  for (int i = tid; i < dm.nt; i += RF_THREADS) w.z[i] = 0.0;
+  __syncthreads();
+  const float* A = S32 + e * (int64_t)dm.n * dm.ld;
+  double rel = refine_solve(dm, ph, ref, G, PJ, e, A, piv + e * dm.nu, w);
+  for (int i = tid; i < dm.nu; i += RF_THREADS) y64[e * dm.nu + i] = w.x[i];
+  for (int i = tid; i < dm.nt; i += RF_THREADS) re64[e * dm.nt + i] = rhs[dm.nu + i] - w.ot[i];
+  if (tid == 0 && !(rel <= kRefineFlag) && status[e] == IEDG_ELEM_OK) status[e] = IEDG_ELEM_REFINE;
+}
+
+// One CTA per element: du = A~^-1 (F~ - B~ dU_e) refined, dq = (q* - q) - G_l du + H_l dU_e.
+__global__ void __launch_bounds__(RF_THREADS)
+k_backsub_mixed(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ, const int64_t* __restrict__ etrace,
+                const float* __restrict__ S32, const int* __restrict__ piv, const double* __restrict__ rhs64,
+                const double* __restrict__ rhoq, const double* __restrict__ duhat, double* __restrict__ du,
+                double* __restrict__ dq) {
+  extern __shared__ double sm[];
+  Work w = carve(dm, sm);
+  const int64_t e = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int m = dm.m, d = dm.d, Np = dm.Np, Nb = dm.Nb;
+  for (int i = tid; i < dm.nu; i += RF_THREADS) w.x[i] = 0.0;
+  for (int i = tid; i < dm.nt; i += RF_THREADS) {
+    int k = i / Nb, t = i % Nb;
+    w.z[i] = duhat[etrace[e * Nb + t] * m + k];
+  }
+  __syncthreads();
+  element_apply(dm, ph, ref, G, PJ, e, w);               // ou = B~ dU_e
+  const double* rhs = rhs64 + e * dm.n;
+  for (int i = tid; i < dm.nu; i += RF_THREADS) w.b[i] = rhs[i] - w.ou[i];
+  for (int i = tid; i < dm.nt; i += RF_THREADS) w.z[i] = 0.0;   // solve with z = 0
+  __syncthreads();
+  const float* A = S32 + e * (int64_t)dm.n * dm.ld;
+  refine_solve(dm, ph, ref, G, PJ, e, A, piv + e * dm.nu, w);
+  for (int i = tid; i < dm.nt; i += RF_THREADS) {          // dU_e again, for dq
+    int k = i / Nb, t = i % Nb;
+    w.z[i] = duhat[etrace[e * Nb + t] * m + k];
+  }
+  __syncthreads();
+  for (int idx = tid; idx < Np * m; idx += RF_THREADS) {
+    int b = idx / m, k = idx % m;
+    du[e * Np * m + idx] = w.x[k * Np + b];
+  }
+  for (int idx = tid; idx < Np * m * d; idx += RF_THREADS) {
+    int c = idx / (m * d), k = (idx / d) % m, l = idx % d;
+    const double* gl = G.Gl + (((size_t)e * d + l) * Np + c) * Np;
+    const double* hl = G.Hl + (((size_t)e * d + l) * Np + c) * Nb;
+    double s = -rhoq[e * Np * m * d + idx];
+    for (int b = 0; b < Np; ++b) s = fma(-gl[b], w.x[k * Np + b], s);
+    for (int t = 0; t < Nb; ++t) s = fma(hl[t], w.z[k * Nb + t], s);
+    dq[e * Np * m * d + idx] = s;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_refine(iedg_mesh* M, cudaStream_t st) {
+  const Dims& dm = M->dm;
+  size_t smem = sizeof(double) * work_doubles(dm);
+  cudaError_t err = cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  k_refine<<<(unsigned)M->E, RF_THREADS, smem, st>>>(dm, M->ph, M->ref, M->geo, M->pj, M->S32, M->piv, M->rhs64,
+                                                      M->y64, M->re64, M->status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backsub_mixed(iedg_mesh* M, const double* duhat, double* du, double* dq, cudaStream_t st) {
+  const Dims& dm = M->dm;
+  size_t smem = sizeof(double) * work_doubles(dm);
+  cudaError_t err = cudaFuncSetAttribute(k_backsub_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  k_backsub_mixed<<<(unsigned)M->E, RF_THREADS, smem, st>>>(dm, M->ph, M->ref, M->geo, M->pj, M->etrace, M->S32,
+                                                             M->piv, M->rhs64, M->rhoq, duhat, du, dq);
+  return cudaGetLastError();
+}
+
+}  // namespace iedg

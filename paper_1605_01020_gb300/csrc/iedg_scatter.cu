@@ -7,9 +7,10 @@
 namespace iedg {
 namespace {
 
-// One thread per (block, i, k) entry.
+// One thread per (block, i, k) entry; S is the FP64 or the FP32 element matrix.
+template <class T>
 __global__ void k_scatter_K(Dims dm, int64_t nnzb, const int64_t* __restrict__ kc_ptr,
-                            const int64_t* __restrict__ kc_src, const double* __restrict__ S,
+                            const int64_t* __restrict__ kc_src, const T* __restrict__ S,
                             double* __restrict__ K) {
   const int m2 = dm.m * dm.m;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -22,7 +23,7 @@ __global__ void k_scatter_K(Dims dm, int64_t nnzb, const int64_t* __restrict__ k
   for (int64_t c = kc_ptr[blk]; c < kc_ptr[blk + 1]; ++c) {
     int64_t src = kc_src[c];
     int64_t e = src / nb2, s = (src / Nb) % Nb, t = src % Nb;
-    v += S[(e * n + row_off + s) * ld + col_off + t];
+    v += (double)S[(e * n + row_off + s) * ld + col_off + t];
   }
   K[idx] = v;
 }
@@ -100,7 +101,11 @@ cudaError_t launch_scatter_K(iedg_mesh* M, double* K, cudaStream_t st) {
   const int64_t total = M->nnzb * M->dm.m * M->dm.m;
   if (total == 0) return cudaSuccess;
   const int th = 256;
-  k_scatter_K<<<(unsigned)((total + th - 1) / th), th, 0, st>>>(M->dm, M->nnzb, M->kc_ptr, M->kc_src, M->S, K);
+  const unsigned grid = (unsigned)((total + th - 1) / th);
+  if (M->precision == 0)
+    k_scatter_K<double><<<grid, th, 0, st>>>(M->dm, M->nnzb, M->kc_ptr, M->kc_src, M->S, K);
+  else
+    k_scatter_K<float><<<grid, th, 0, st>>>(M->dm, M->nnzb, M->kc_ptr, M->kc_src, M->S32, K);
   return cudaGetLastError();
 }
 

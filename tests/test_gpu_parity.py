@@ -151,3 +151,67 @@ def test_full_size_p3_sampled():
         du_o, dq_o = pb.back_substitute_qelim(e, st.u, st.q, st.uhat, st.duhat)
         assert rel_err(host(du_d[e]), du_o) <= TOL
         assert rel_err(host(dq_d[e]), dq_o) <= TOL
+
+
+# ---------------------------------------------------------------- mixed precision
+# FP32 element matrix and partial LU, FP64 refinement.  Bounds: K is an FP32
+# Schur complement, error <= kappa(A~) * 6e-8, checked at 1e-4 relative per block
+# row; R and the updates du, dq are refined to FP64 and checked at 1e-10.
+TOL_MIXED_K = 1e-4
+TOL_MIXED = 1e-10
+
+
+def _mixed_mesh(wl):
+    from paper_1605_01020_gb300 import iedg
+    return iedg.mesh_from_workload(wl, precision=1)
+
+
+@pytest.mark.parametrize("name", ["cfg1-noisy", "p3-2cube", "p2-curved", "2d-p3-steady", "2d-p1"])
+def test_mixed_condensed_parity(name):
+    wl = _case(name)
+    st = wl.state
+    pb = problem(wl.mesh, wl.params)
+    E = wl.mesh.n_elem
+    Ke, Re = zip(*[pb.condense_qelim(e, st.u, st.q, st.uhat, st.u_ref) for e in range(E)])
+    row_ptr, col, vals, R = oiedg.assemble(wl.mesh.elem_trace, wl.mesh.n_trace, np.array(Ke), np.array(Re))
+    mesh = _mixed_mesh(wl)
+    K_d, R_d = mesh.assemble_condensed(dev(st.u), dev(st.q), dev(st.uhat), u_ref=dev(st.u_ref))
+    kerr = bsr_row_err(row_ptr, host(K_d), vals, range(wl.mesh.n_trace))
+    rerr = rel_err(host(R_d), R, floor=np.abs(np.array(Re)).max())
+    assert (mesh.element_status() == 0).all()
+    assert kerr <= TOL_MIXED_K, kerr
+    assert rerr <= TOL_MIXED, rerr
+    du_d, dq_d = mesh.back_substitute(dev(st.duhat))
+    du_o = np.zeros_like(st.u)
+    dq_o = np.zeros_like(st.q)
+    for e in range(E):
+        du_o[e], dq_o[e] = pb.back_substitute_qelim(e, st.u, st.q, st.uhat, st.duhat, st.u_ref)
+    assert rel_err(host(du_d), du_o) <= TOL_MIXED
+    assert rel_err(host(dq_d), dq_o) <= TOL_MIXED
+
+
+@pytest.mark.parametrize("cfg", [2, 3])
+def test_mixed_full_size_sampled(cfg):
+    """The 16^3 p=3 workloads (config 3: stretched and sheared, aspect up to 50) in the
+    mixed form at full size: sampled block rows of K and R, sampled updates."""
+    wl = W.config(cfg)
+    st = wl.state
+    mesh = _mixed_mesh(wl)
+    u, q, uh = dev(st.u), dev(st.q), dev(st.uhat)
+    K_d, R_d = mesh.assemble_condensed(u, q, uh)
+    du_d, dq_d = mesh.back_substitute(dev(st.duhat))
+    status = mesh.element_status()
+    K_h, R_h = host(K_d), host(R_d)
+    pb = problem(wl.mesh, wl.params)
+    rng = np.random.default_rng(cfg)
+    rows = rng.choice(wl.mesh.n_trace, 2, replace=False)
+    row_ptr, col, vals, R, els, re_max = oracle_K_rows(pb, wl.mesh, st, rows)
+    kerr = bsr_row_err(row_ptr, K_h, vals, rows)
+    rerr = rel_err(R_h[rows], R[rows], floor=re_max)
+    e = els[0]
+    du_o, dq_o = pb.back_substitute_qelim(e, st.u, st.q, st.uhat, st.duhat)
+    duerr, dqerr = rel_err(host(du_d[e]), du_o), rel_err(host(dq_d[e]), dq_o)
+    print(f"config {cfg} mixed: K {kerr:.2e}  R {rerr:.2e}  du {duerr:.2e}  dq {dqerr:.2e}  "
+          f"flagged {int((status != 0).sum())}")
+    assert (status == 0).all()
+    assert kerr <= TOL_MIXED_K and rerr <= TOL_MIXED and duerr <= TOL_MIXED and dqerr <= TOL_MIXED

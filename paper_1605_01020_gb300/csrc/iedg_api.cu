@@ -85,7 +85,7 @@ void lagrange_eval(const std::vector<double>& nodes, double x, double* L, double
 }
 
 struct HostRef {
-  std::vector<double> Phi, Dxi, Wq, PhiF, DxiF, Wf;
+  std::vector<double> Phi, Dxi, Wq, PhiF, DxiF, Wf, L1, dL1;
   std::vector<int> bnode, slot, fnode;
 };
 
@@ -97,6 +97,8 @@ HostRef build_reference(const Dims& dm) {
   gauss_rule(nq1, xq, wq);
   std::vector<double> L(nq1 * np1), dL(nq1 * np1);
   for (int g = 0; g < nq1; ++g) lagrange_eval(xn, xq[g], &L[g * np1], &dL[g * np1]);
+  R.L1 = L;
+  R.dL1 = dL;
   auto idx = [&](int a, int r, int n1) { for (int t = 0; t < r; ++t) a /= n1; return a % n1; };
   R.Phi.assign((size_t)dm.Nq * dm.Np, 1.0);
   R.Dxi.assign((size_t)d * dm.Nq * dm.Np, 1.0);
@@ -329,6 +331,8 @@ static int create_impl(const iedg_mesh_desc* D, cudaStream_t st, iedg_mesh* M) {
   CUDA_TRY(upload(M, &M->ref.bnode, R.bnode, st));
   CUDA_TRY(upload(M, &M->ref.slot, R.slot, st));
   CUDA_TRY(upload(M, &M->ref.fnode, R.fnode, st));
+  CUDA_TRY(upload(M, &M->ref.L1, R.L1, st));
+  CUDA_TRY(upload(M, &M->ref.dL1, R.dL1, st));
   CUDA_TRY(upload(M, &M->etrace, etv, st));
   CUDA_TRY(upload(M, &M->row_ptr, row_ptr, st));
   CUDA_TRY(upload(M, &M->col, col, st));
@@ -365,6 +369,17 @@ static int create_impl(const iedg_mesh_desc* D, cudaStream_t st, iedg_mesh* M) {
     CUDA_TRY(dalloc(M, &M->rhs64, (size_t)E * dm.n));
     CUDA_TRY(dalloc(M, &M->y64, (size_t)E * dm.nu));
     CUDA_TRY(dalloc(M, &M->re64, (size_t)E * dm.nt));
+    CUDA_TRY(dalloc(M, &M->pj.Jv32, E * m * m * (1 + d) * d * Nq));
+    CUDA_TRY(dalloc(M, &M->pj.Jf32, E * m * m * (1 + d) * Nfp));
+    CUDA_TRY(dalloc(M, &M->pj.lamw32, E * Nfp));
+    CUDA_TRY(dalloc(M, &G.Mass32, E * Np * Np));
+    CUDA_TRY(dalloc(M, &G.GlV32, E * d * Nq * Np));
+    CUDA_TRY(dalloc(M, &G.HlV32, E * d * Nq * Nb));
+    CUDA_TRY(dalloc(M, &G.GlF32, E * d * Nfp * Np));
+    CUDA_TRY(dalloc(M, &G.HlF32, E * d * Nfp * Nb));
+    CUDA_TRY(dalloc(M, &M->ref.Phi32, Nq * Np));
+    CUDA_TRY(dalloc(M, &M->ref.Dxi32, d * Nq * Np));
+    CUDA_TRY(dalloc(M, &M->ref.PhiF32, Nfp * Np));
   }
   CUDA_TRY(dalloc(M, &M->status, E));
   CUDA_TRY(dalloc(M, &M->dev_flag, 1));
@@ -379,6 +394,16 @@ static int create_impl(const iedg_mesh_desc* D, cudaStream_t st, iedg_mesh* M) {
   if (e1 != cudaSuccess) { cudaFree(X); CUDA_TRY(e1); }
   cudaError_t e2 = cudaMemcpyAsync(X, D->node_xyz, E * Np * d * sizeof(double), cudaMemcpyHostToDevice, st);
   if (e2 == cudaSuccess) e2 = launch_geometry(M, X, scratch, st);
+  if (e2 == cudaSuccess && M->precision == IEDG_PRECISION_MIXED) {
+    const std::pair<const double*, float*> cv[] = {
+        {G.Mass, G.Mass32}, {G.GlV, G.GlV32}, {G.HlV, G.HlV32}, {G.GlF, G.GlF32}, {G.HlF, G.HlF32},
+        {M->ref.Phi, M->ref.Phi32}, {M->ref.Dxi, M->ref.Dxi32}, {M->ref.PhiF, M->ref.PhiF32}};
+    const int64_t E_ = E, Np_ = (int64_t)Np, Nq_ = (int64_t)Nq, Nb_ = (int64_t)Nb, Nfp_ = (int64_t)Nfp,
+                  d_ = (int64_t)d;
+    const int64_t cn[] = {E_ * Np_ * Np_, E_ * d_ * Nq_ * Np_, E_ * d_ * Nq_ * Nb_, E_ * d_ * Nfp_ * Np_,
+                          E_ * d_ * Nfp_ * Nb_, Nq_ * Np_, d_ * Nq_ * Np_, Nfp_ * Np_};
+    for (int i = 0; i < 8 && e2 == cudaSuccess; ++i) e2 = launch_to_f32(cv[i].first, cv[i].second, cn[i], st);
+  }
   int flag = 0;
   if (e2 == cudaSuccess) e2 = cudaMemcpyAsync(&flag, M->dev_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
@@ -491,7 +516,10 @@ extern "C" int iedg_assemble_condensed(iedg_mesh* M, const double* u, const doub
   // point Jacobians at (u, q) and the right-hand sides F~ = -R_u(u, q*), G~ = -R_FL,e(u, q*)
   // written straight into the last column of the bordered element matrices
   CUDA_TRY(TRACED("points_jacobian", launch_points(M, u, q, M->qstar, uhat, u_ref, true, nullptr, nullptr, st)));
-  CUDA_TRY(TRACED("assemble", launch_assemble(M, st)));
+  if (dm.d == 3)
+    CUDA_TRY(TRACED("assemble", launch_assemble_sf(M, st)));
+  else
+    CUDA_TRY(TRACED("assemble", launch_assemble(M, st)));
   CUDA_TRY(TRACED("lu_schur", launch_lu(M, st)));
   if (M->precision == IEDG_PRECISION_MIXED) CUDA_TRY(TRACED("refine", launch_refine(M, st)));
   CUDA_TRY(TRACED("scatter_K", launch_scatter_K(M, K, st)));

@@ -52,7 +52,7 @@ AsmCfg asm_cfg(const Dims& dm) {
 // right-hand sides are copied into column n by one CTA per element).
 template <class T>
 __global__ void __launch_bounds__(AS_THREADS)
-k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, Geo G, PointJac PJ, T* __restrict__ S,
+k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, AsmTab<T> tb, T* __restrict__ S,
            const double* __restrict__ rhs64) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
@@ -69,13 +69,13 @@ k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, Geo G, PointJac PJ, T* __
   T* facc = sB + KC * CW;               // [Nb][CW]   face parts of the boundary rows
   T* sV = facc + Nb * CW;               // [Nfq][CW]  face right operand
   const size_t jvs = (size_t)(1 + d) * d * Nq;
-  const double* jv = PJ.Jv + ((size_t)e * dm.m * dm.m + pair) * jvs;
+  const T* jv = tb.Jv + ((size_t)e * dm.m * dm.m + pair) * jvs;
   const size_t jfs = (size_t)(1 + d) * Nfp;
-  const double* jf = PJ.Jf + ((size_t)e * dm.m * dm.m + pair) * jfs;
-  const double* GlV = G.GlV + (size_t)e * d * Nq * Np;
-  const double* HlV = G.HlV + (size_t)e * d * Nq * Nb;
-  const double* GlF = G.GlF + (size_t)e * d * Nfp * Np;
-  const double* HlF = G.HlF + (size_t)e * d * Nfp * Nb;
+  const T* jf = tb.Jf + ((size_t)e * dm.m * dm.m + pair) * jfs;
+  const T* GlV = tb.GlV + (size_t)e * d * Nq * Np;
+  const T* HlV = tb.HlV + (size_t)e * d * Nq * Nb;
+  const T* GlF = tb.GlF + (size_t)e * d * Nfp * Np;
+  const T* HlF = tb.HlF + (size_t)e * d * Nfp * Nb;
 
   const int trow = tid / cf.cg, tcol = tid % cf.cg;
   const bool gemm_thread = trow < cf.rg;
@@ -90,7 +90,7 @@ k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, Geo G, PointJac PJ, T* __
     for (int idx = tid; idx < KC * RP; idx += AS_THREADS) {
       int kc = idx / RP, a = idx % RP;
       int g = g0 + kc / d, r = kc % d;
-      sA[idx] = (T)((g < Nq && a < Np) ? ref.Dxi[((size_t)r * Nq + g) * Np + a] : 0.0);
+      sA[idx] = (g < Nq && a < Np) ? tb.Dxi[((size_t)r * Nq + g) * Np + a] : (T)0;
     }
     for (int idx = tid; idx < KC * CW; idx += AS_THREADS) {
       int kc = idx / CW, col = c0 + idx % CW;
@@ -98,12 +98,12 @@ k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, Geo G, PointJac PJ, T* __
       T w = 0;
       if (g < Nq && col < ncol) {
         if (col < Np) {
-          w = (T)jv[(size_t)r * Nq + g] * (T)ref.Phi[(size_t)g * Np + col];
+          w = jv[(size_t)r * Nq + g] * tb.Phi[(size_t)g * Np + col];
           for (int l = 0; l < d; ++l)
-            w -= (T)jv[(size_t)(d + l * d + r) * Nq + g] * (T)GlV[((size_t)l * Nq + g) * Np + col];
+            w -= jv[(size_t)(d + l * d + r) * Nq + g] * GlV[((size_t)l * Nq + g) * Np + col];
         } else {
           for (int l = 0; l < d; ++l)
-            w += (T)jv[(size_t)(d + l * d + r) * Nq + g] * (T)HlV[((size_t)l * Nq + g) * Nb + (col - Np)];
+            w += jv[(size_t)(d + l * d + r) * Nq + g] * HlV[((size_t)l * Nq + g) * Nb + (col - Np)];
         }
       }
       sB[idx] = w;
@@ -127,7 +127,7 @@ k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, Geo G, PointJac PJ, T* __
 
   // ---- face parts, accumulated per trace slot
   for (int idx = tid; idx < Nb * CW; idx += AS_THREADS) facc[idx] = (T)0;
-  const double lamsel = (i == k) ? 1.0 : 0.0;
+  const T lamsel = (i == k) ? (T)1 : (T)0;
   for (int f = 0; f < dm.nf; ++f) {
     __syncthreads();
     for (int idx = tid; idx < Nfq * CW; idx += AS_THREADS) {
@@ -135,12 +135,12 @@ k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, Geo G, PointJac PJ, T* __
       int fp = f * Nfq + gf;
       T v = 0;
       if (col < Np) {
-        v = (T)(lamsel * PJ.lamw[e * Nfp + fp]) * (T)ref.PhiF[(size_t)fp * Np + col];
-        for (int l = 0; l < d; ++l) v -= (T)jf[(size_t)(1 + l) * Nfp + fp] * (T)GlF[((size_t)l * Nfp + fp) * Np + col];
+        v = lamsel * tb.lamw[e * Nfp + fp] * tb.PhiF[(size_t)fp * Np + col];
+        for (int l = 0; l < d; ++l) v -= jf[(size_t)(1 + l) * Nfp + fp] * GlF[((size_t)l * Nfp + fp) * Np + col];
       } else if (col < ncol) {
         int t = col - Np;
-        v = (T)jf[fp] * (T)ref.PhiF[(size_t)fp * Np + ref.bnode[t]];
-        for (int l = 0; l < d; ++l) v += (T)jf[(size_t)(1 + l) * Nfp + fp] * (T)HlF[((size_t)l * Nfp + fp) * Nb + t];
+        v = jf[fp] * tb.PhiF[(size_t)fp * Np + ref.bnode[t]];
+        for (int l = 0; l < d; ++l) v += jf[(size_t)(1 + l) * Nfp + fp] * HlF[((size_t)l * Nfp + fp) * Nb + t];
       }
       sV[idx] = v;
     }
@@ -149,7 +149,7 @@ k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, Geo G, PointJac PJ, T* __
       int tn = idx / CW, cc = idx % CW;
       int a = ref.fnode[f * Nfn + tn];
       T s = 0;
-      for (int gf = 0; gf < Nfq; ++gf) s += (T)ref.PhiF[(size_t)(f * Nfq + gf) * Np + a] * sV[gf * CW + cc];
+      for (int gf = 0; gf < Nfq; ++gf) s += tb.PhiF[(size_t)(f * Nfq + gf) * Np + a] * sV[gf * CW + cc];
       facc[ref.slot[a] * CW + cc] += s;
     }
   }
@@ -162,7 +162,7 @@ k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, Geo G, PointJac PJ, T* __
     for (int r = tid; r < nn; r += AS_THREADS) Se[r * ld + nn] = (T)rhs64[e * nn + r];
   auto colS = [&](int col) -> int64_t { return col < Np ? (int64_t)k * Np + col : (int64_t)dm.nu + (int64_t)k * Nb + (col - Np); };
   if (gemm_thread) {
-    const double* Ms = G.Mass + (size_t)e * Np * Np;
+    const T* Ms = tb.Mass + (size_t)e * Np * Np;
 #pragma unroll
     for (int a = 0; a < TM; ++a) {
       int row = trow * TM + a;
@@ -174,7 +174,7 @@ k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, Geo G, PointJac PJ, T* __
         if (col >= ncol || col >= c0 + CW) continue;
         T v = acc[a][b];
         if (sl >= 0) v += facc[sl * CW + (col - c0)];
-        if (i == k && col < Np) v += (T)(ph.alpha * Ms[row * Np + col]);
+        if (i == k && col < Np) v += (T)ph.alpha * Ms[row * Np + col];
         Se[((int64_t)i * Np + row) * ld + colS(col)] = v;
       }
     }
@@ -343,10 +343,181 @@ k_lu(Dims dm, T* __restrict__ S, int8_t* __restrict__ status, int* __restrict__ 
   if (tid == 0) status[e] = sing ? IEDG_ELEM_SINGULAR : (bad ? IEDG_ELEM_NONFINITE : IEDG_ELEM_OK);
 }
 
+// FP32 partial LU for the mixed path.  Same algorithm and pivot rule as k_lu, with
+// the panel kept column-major in shared memory (contiguous rows for the pivot search,
+// the elimination and vector loads of L21) and an 8 x 8 register tile per thread in
+// the trailing update (float4 loads: one shared load per 16 multiply-adds), so the
+// update runs at FFMA rather than shared-memory rate.  The full panel (L) and the
+// pivot rows are written back for the refinement solves.
+constexpr int L32_NB = 32;
+constexpr int L32_UCW = 128;      // trailing-update column chunk
+constexpr int L32_TM = 8, L32_TN = 8;
+
+__global__ void __launch_bounds__(LU_THREADS, 1)
+k_lu32(Dims dm, float* __restrict__ S, int8_t* __restrict__ status, int* __restrict__ pivots) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float* P = reinterpret_cast<float*>(smraw);          // [NB][n] column-major panel
+  float* Uc = P + (size_t)L32_NB * dm.n;                // [NB][UCW]
+  __shared__ int piv[L32_NB];
+  __shared__ float rv[LU_THREADS / 32];
+  __shared__ int ri[LU_THREADS / 32];
+  __shared__ int sing;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t e = blockIdx.x;
+  const int n = dm.n, nu = dm.nu, ld = dm.ld, ncol = n + 1;
+  float* A = S + e * (int64_t)n * ld;
+  if (tid == 0) sing = 0;
+  for (int kb = 0; kb < nu; kb += L32_NB) {
+    const int nb = min(L32_NB, nu - kb), rows = n - kb, prow = nu - kb;
+    for (int idx = tid; idx < rows * L32_NB; idx += LU_THREADS) {
+      int r = idx / L32_NB, j = idx % L32_NB;
+      P[j * n + r] = j < nb ? A[(int64_t)(kb + r) * ld + kb + j] : 0.f;
+    }
+    __syncthreads();
+    for (int j = 0; j < nb; ++j) {
+      const float* Pj = P + j * n;
+      float best = -1.f;
+      int bi = j;
+      for (int r = j + tid; r < prow; r += LU_THREADS) {
+        float v = fabsf(Pj[r]);
+        if (v > best) { best = v; bi = r; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        float ov = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+      }
+      if (lane == 0) { rv[warp] = best; ri[warp] = bi; }
+      __syncthreads();
+      if (tid == 0) {
+        float bv = rv[0];
+        int b = ri[0];
+        for (int w = 1; w < LU_THREADS / 32; ++w)
+          if (rv[w] > bv || (rv[w] == bv && ri[w] < b)) { bv = rv[w]; b = ri[w]; }
+        if (!(bv > 0.f)) { sing = 1; b = j; }
+        piv[j] = b;
+        pivots[e * nu + kb + j] = kb + b;
+      }
+      __syncthreads();
+      const int pr = piv[j];
+      if (pr != j && tid < L32_NB) {
+        float t = P[tid * n + j];
+        P[tid * n + j] = P[tid * n + pr];
+        P[tid * n + pr] = t;
+      }
+      __syncthreads();
+      const float pv = Pj[j];
+      const float inv = pv != 0.f ? 1.f / pv : 0.f;
+      for (int r = j + 1 + tid; r < rows; r += LU_THREADS) {
+        float l = Pj[r] * inv;
+        P[j * n + r] = l;
+        for (int c = j + 1; c < nb; ++c) P[c * n + r] = fmaf(-l, P[c * n + j], P[c * n + r]);
+      }
+      __syncthreads();
+    }
+    // full panel back (U11, L11, L21): needed by the refinement solves
+    for (int idx = tid; idx < rows * nb; idx += LU_THREADS) {
+      int r = idx / nb, j = idx % nb;
+      A[(int64_t)(kb + r) * ld + kb + j] = P[j * n + r];
+    }
+    // trailing columns: row interchanges, then U12 = L11^-1 A12
+    for (int c = kb + nb + tid; c < ncol; c += LU_THREADS) {
+      float x[L32_NB];
+#pragma unroll
+      for (int j = 0; j < L32_NB; ++j) {
+        if (j >= nb) break;
+        int pr = piv[j];
+        float* a0 = A + (int64_t)(kb + j) * ld + c;
+        if (pr != j) {
+          float* a1 = A + (int64_t)(kb + pr) * ld + c;
+          float t = *a0; *a0 = *a1; *a1 = t;
+        }
+        x[j] = *a0;
+      }
+#pragma unroll
+      for (int j = 0; j < L32_NB; ++j) {
+        if (j >= nb) break;
+        float s = x[j];
+#pragma unroll
+        for (int jj = 0; jj < L32_NB; ++jj) {
+          if (jj >= j) break;
+          s = fmaf(-P[jj * n + j], x[jj], s);
+        }
+        x[j] = s;
+        A[(int64_t)(kb + j) * ld + c] = s;
+      }
+    }
+    __syncthreads();
+    // A22 -= L21 U12, 8 x 8 tiles, rows [kb+nb, n), cols [kb+nb, n]
+    const int r0 = kb + nb;
+    const bool vec = ((nb & 3) == 0) && ((n & 3) == 0);
+    const int tc = tid % (L32_UCW / L32_TN), tr = tid / (L32_UCW / L32_TN);   // 16 x 16
+    for (int cc = r0; cc < ncol; cc += L32_UCW) {
+      const int cw = min(L32_UCW, ncol - cc);
+      for (int idx = tid; idx < L32_NB * L32_UCW; idx += LU_THREADS) {
+        int j = idx / L32_UCW, c = idx % L32_UCW;
+        Uc[idx] = (j < nb && c < cw) ? A[(int64_t)(kb + j) * ld + cc + c] : 0.f;
+      }
+      __syncthreads();
+      for (int rb = r0; rb < n; rb += 16 * L32_TM) {
+        const int rr0 = rb + tr * L32_TM;
+        float acc[L32_TM][L32_TN];
+#pragma unroll
+        for (int a = 0; a < L32_TM; ++a)
+#pragma unroll
+          for (int b = 0; b < L32_TN; ++b) {
+            int rr = rr0 + a, c = tc * L32_TN + b;
+            acc[a][b] = (rr < n && c < cw) ? A[(int64_t)rr * ld + cc + c] : 0.f;
+          }
+        if (rr0 < n) {
+          for (int j = 0; j < nb; ++j) {
+            float lv[L32_TM], uv[L32_TN];
+            const float* lp = P + j * n + (rr0 - kb);
+            if (vec && rr0 + L32_TM <= n) {
+              float4 l0 = *reinterpret_cast<const float4*>(lp);
+              float4 l1 = *reinterpret_cast<const float4*>(lp + 4);
+              lv[0] = l0.x; lv[1] = l0.y; lv[2] = l0.z; lv[3] = l0.w;
+              lv[4] = l1.x; lv[5] = l1.y; lv[6] = l1.z; lv[7] = l1.w;
+            } else {
+#pragma unroll
+              for (int a = 0; a < L32_TM; ++a) lv[a] = (rr0 + a < n) ? lp[a] : 0.f;
+            }
+            const float4 u0 = *reinterpret_cast<const float4*>(Uc + j * L32_UCW + tc * L32_TN);
+            const float4 u1 = *reinterpret_cast<const float4*>(Uc + j * L32_UCW + tc * L32_TN + 4);
+            uv[0] = u0.x; uv[1] = u0.y; uv[2] = u0.z; uv[3] = u0.w;
+            uv[4] = u1.x; uv[5] = u1.y; uv[6] = u1.z; uv[7] = u1.w;
+#pragma unroll
+            for (int a = 0; a < L32_TM; ++a)
+#pragma unroll
+              for (int b = 0; b < L32_TN; ++b) acc[a][b] = fmaf(-lv[a], uv[b], acc[a][b]);
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < L32_TM; ++a)
+#pragma unroll
+          for (int b = 0; b < L32_TN; ++b) {
+            int rr = rr0 + a, c = tc * L32_TN + b;
+            if (rr < n && c < cw) A[(int64_t)rr * ld + cc + c] = acc[a][b];
+          }
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  int bad = 0;
+  for (int idx = tid; idx < (n - nu) * (ncol - nu); idx += LU_THREADS) {
+    int r = nu + idx / (ncol - nu), c = nu + idx % (ncol - nu);
+    if (!isfinite(A[(int64_t)r * ld + c])) bad = 1;
+  }
+  bad = __syncthreads_or(bad);
+  if (tid == 0) status[e] = sing ? IEDG_ELEM_SINGULAR : (bad ? IEDG_ELEM_NONFINITE : IEDG_ELEM_OK);
+}
+
 }  // namespace
 
 template <class T>
-static cudaError_t assemble_t(iedg_mesh* M, T* S, const double* rhs64, cudaStream_t st) {
+static cudaError_t assemble_t(iedg_mesh* M, T* S, const double* rhs64, const AsmTab<T>& tb, cudaStream_t st) {
   const Dims& dm = M->dm;
   AsmCfg cf = asm_cfg(dm);
   size_t smem = sizeof(T) * ((size_t)cf.KC * cf.rows_pad + (size_t)cf.KC * cf.CW +
@@ -354,13 +525,26 @@ static cudaError_t assemble_t(iedg_mesh* M, T* S, const double* rhs64, cudaStrea
   cudaError_t err = cudaFuncSetAttribute(k_assemble<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   dim3 grid((unsigned)(M->E * dm.m * dm.m), cf.nsplit);
-  k_assemble<T><<<grid, AS_THREADS, smem, st>>>(dm, M->ph, cf, M->ref, M->geo, M->pj, S, rhs64);
+  k_assemble<T><<<grid, AS_THREADS, smem, st>>>(dm, M->ph, cf, M->ref, tb, S, rhs64);
   return cudaGetLastError();
 }
 
+AsmTab<double> tables64(const iedg_mesh* M) {
+  const Geo& G = M->geo;
+  const PointJac& P = M->pj;
+  return AsmTab<double>{M->ref.Phi, M->ref.Dxi, M->ref.PhiF, P.Jv, P.Jf, P.lamw, G.GlV, G.HlV, G.GlF, G.HlF, G.Mass};
+}
+
+AsmTab<float> tables32(const iedg_mesh* M) {
+  const Geo& G = M->geo;
+  const PointJac& P = M->pj;
+  return AsmTab<float>{M->ref.Phi32, M->ref.Dxi32, M->ref.PhiF32, P.Jv32, P.Jf32, P.lamw32,
+                       G.GlV32, G.HlV32, G.GlF32, G.HlF32, G.Mass32};
+}
+
 cudaError_t launch_assemble(iedg_mesh* M, cudaStream_t st) {
-  if (M->precision == 0) return assemble_t<double>(M, M->S, nullptr, st);
-  return assemble_t<float>(M, M->S32, M->rhs64, st);
+  if (M->precision == 0) return assemble_t<double>(M, M->S, nullptr, tables64(M), st);
+  return assemble_t<float>(M, M->S32, M->rhs64, tables32(M), st);
 }
 
 template <class T, int NB>
@@ -375,7 +559,12 @@ static cudaError_t lu_t(iedg_mesh* M, T* S, int* piv, cudaStream_t st) {
 
 cudaError_t launch_lu(iedg_mesh* M, cudaStream_t st) {
   if (M->precision == 0) return lu_t<double, 16>(M, M->S, nullptr, st);
-  return lu_t<float, 32>(M, M->S32, M->piv, st);
+  const Dims& dm = M->dm;
+  size_t smem = sizeof(float) * ((size_t)L32_NB * dm.n + (size_t)L32_NB * L32_UCW);
+  cudaError_t err = cudaFuncSetAttribute(k_lu32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  k_lu32<<<(unsigned)M->E, LU_THREADS, smem, st>>>(dm, M->S32, M->status, M->piv);
+  return cudaGetLastError();
 }
 
 }  // namespace iedg

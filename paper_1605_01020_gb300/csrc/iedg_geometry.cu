@@ -157,7 +157,19 @@ __global__ void k_geometry(Dims dm, RefTables ref, Geo G, const double* __restri
   }
 }
 
+__global__ void k_to_f32(const double* __restrict__ src, float* __restrict__ dst, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+
 }  // namespace
+
+cudaError_t launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int64_t blocks = (n + 255) / 256;
+  k_to_f32<<<(unsigned)(blocks < 65536 ? blocks : 65536), 256, 0, st>>>(src, dst, n);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_geometry(iedg_mesh* M, const double* X, double* scratch, cudaStream_t st) {
   const Dims& dm = M->dm;

@@ -36,6 +36,11 @@ struct RefTables {
   int* bnode;     // [Nb]   local node of trace slot s
   int* slot;      // [Np]   trace slot of node a, -1 for interior nodes
   int* fnode;     // [nf][Nfn] nodes of each face
+  double* L1;     // [nq1][np1] 1D Lagrange basis at the 1D Gauss points
+  double* dL1;    // [nq1][np1] its derivative
+  float* Phi32;   // FP32 copies for the mixed path (FP64 -> FP32 conversion is slow on GB300)
+  float* Dxi32;
+  float* PhiF32;
 };
 
 // Per-element geometry (device).
@@ -51,6 +56,8 @@ struct Geo {
   double* HlV;    // [E][d][Nq][Nb]
   double* GlF;    // [E][d][Nfp][Np]  PhiF Gl  (lifting at face points)
   double* HlF;    // [E][d][Nfp][Nb]
+  // FP32 copies (mixed path only)
+  float *Mass32, *GlV32, *HlV32, *GlF32, *HlF32;
 };
 
 // Point tables written by the point kernel for the assembly kernel.
@@ -58,6 +65,16 @@ struct PointJac {
   double* Jv;     // [E][m][m][(1+d) d][Nq]: c<d: cu_r ; c = d + l d + r: cq_lr  (w Jinv folded)
   double* Jf;     // [E][m][m][1+d][Nfp]   : c=0: wf dfhat/duhat ; c=1+l: wf dfhat/dq_l
   double* lamw;   // [E][Nfp]              : wf lambda  (dfhat/du = lambda I)
+  float *Jv32, *Jf32, *lamw32;   // FP32 copies written by the point kernel (mixed path only)
+};
+
+// Tables of one precision for the assembly kernels (the FP32 set is converted once
+// per mesh / per point pass, so no FP64 value is touched on the FP32 path).
+template <class T>
+struct AsmTab {
+  const T *Phi, *Dxi, *PhiF;
+  const T *Jv, *Jf, *lamw;
+  const T *GlV, *HlV, *GlF, *HlF, *Mass;
 };
 
 }  // namespace iedg
@@ -107,6 +124,7 @@ inline int idiv_up(int a, int b) { return (a + b - 1) / b; }
 
 // kernels (launchers)
 cudaError_t launch_geometry(iedg_mesh* M, const double* X, double* scratch, cudaStream_t st);
+cudaError_t launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t st);
 cudaError_t launch_lift(iedg_mesh* M, const double* u, const double* uhat, double* qstar, cudaStream_t st);
 cudaError_t launch_points(iedg_mesh* M, const double* u, const double* q, const double* qs,
                           const double* uhat, const double* u_ref, bool jacobians,
@@ -114,6 +132,9 @@ cudaError_t launch_points(iedg_mesh* M, const double* u, const double* q, const 
 cudaError_t launch_rq(iedg_mesh* M, const double* q, const double* qs, double* r_q, double* rhoq,
                       cudaStream_t st);
 cudaError_t launch_assemble(iedg_mesh* M, cudaStream_t st);
+cudaError_t launch_assemble_sf(iedg_mesh* M, cudaStream_t st);   // 3D, sum-factorised
+AsmTab<double> tables64(const iedg_mesh* M);
+AsmTab<float> tables32(const iedg_mesh* M);
 cudaError_t launch_lu(iedg_mesh* M, cudaStream_t st);
 cudaError_t launch_scatter_K(iedg_mesh* M, double* K, cudaStream_t st);
 cudaError_t launch_scatter_R(iedg_mesh* M, const double* src, int64_t src_elem_stride,

@@ -291,18 +291,21 @@ __global__ void k_points(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ,
 #pragma unroll
         for (int k = 0; k < M; ++k) {
           double* o = jv + (size_t)(i * M + k) * jvs;
+          float* o32 = PJ.Jv32 ? PJ.Jv32 + ((size_t)e * M * M + (size_t)(i * M + k)) * jvs : nullptr;
 #pragma unroll
           for (int r = 0; r < D; ++r) {
             double s = 0;
 #pragma unroll
             for (int j = 0; j < D; ++j) s += Ji[r][j] * dF[i][j][k];
             o[(size_t)r * Nq + g] = -w * s;
+            if (o32) o32[(size_t)r * Nq + g] = (float)(-w * s);
 #pragma unroll
             for (int l = 0; l < D; ++l) {
               double t = 0;
 #pragma unroll
               for (int j = 0; j < D; ++j) t += Ji[r][j] * dQ[i][j][k][l];
               o[(size_t)(D + l * D + r) * Nq + g] = -w * t;
+              if (o32) o32[(size_t)(D + l * D + r) * Nq + g] = (float)(-w * t);
             }
           }
         }
@@ -361,19 +364,23 @@ __global__ void k_points(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ,
 #pragma unroll
         for (int k = 0; k < M; ++k) {
           double* o = jf + (size_t)(i * M + k) * jfs;
+          float* o32 = PJ.Jf32 ? PJ.Jf32 + ((size_t)e * M * M + (size_t)(i * M + k)) * jfs : nullptr;
           double s = lamd.t[k] * (u[i] - uh[i]) - (i == k ? lam : 0.0);
 #pragma unroll
           for (int j = 0; j < D; ++j) s += dF[i][j][k] * n[j];
           o[fp] = wf * s;
+          if (o32) o32[fp] = (float)(wf * s);
 #pragma unroll
           for (int l = 0; l < D; ++l) {
             double t = 0;
 #pragma unroll
             for (int j = 0; j < D; ++j) t += dQ[i][j][k][l] * n[j];
             o[(size_t)(1 + l) * Nfp + fp] = wf * t;
+            if (o32) o32[(size_t)(1 + l) * Nfp + fp] = (float)(wf * t);
           }
         }
       PJ.lamw[e * Nfp + fp] = wf * lam;
+      if (PJ.lamw32) PJ.lamw32[e * Nfp + fp] = (float)(wf * lam);
     }
   }
   __syncthreads();

@@ -516,7 +516,7 @@ extern "C" int iedg_assemble_condensed(iedg_mesh* M, const double* u, const doub
   // point Jacobians at (u, q) and the right-hand sides F~ = -R_u(u, q*), G~ = -R_FL,e(u, q*)
   // written straight into the last column of the bordered element matrices
   CUDA_TRY(TRACED("points_jacobian", launch_points(M, u, q, M->qstar, uhat, u_ref, true, nullptr, nullptr, st)));
-  if (dm.d == 3)
+  if (assemble_sf_supported(dm))
     CUDA_TRY(TRACED("assemble", launch_assemble_sf(M, st)));
   else
     CUDA_TRY(TRACED("assemble", launch_assemble(M, st)));

@@ -345,15 +345,15 @@ k_lu(Dims dm, T* __restrict__ S, int8_t* __restrict__ status, int* __restrict__ 
 
 // FP32 partial LU for the mixed path.  Same algorithm and pivot rule as k_lu, with
 // the panel kept column-major in shared memory (contiguous rows for the pivot search,
-// the elimination and vector loads of L21) and an 8 x 8 register tile per thread in
-// the trailing update (float4 loads: one shared load per 16 multiply-adds), so the
-// update runs at FFMA rather than shared-memory rate.  The full panel (L) and the
+// the elimination and vector loads of L21) and a 4 x 8 register tile per thread in
+// the trailing update (float4 loads: three shared loads per 32 multiply-adds), so the
+// update runs at FFMA rather than shared-memory rate, with two CTAs per SM.  The full panel (L) and the
 // pivot rows are written back for the refinement solves.
 constexpr int L32_NB = 32;
 constexpr int L32_UCW = 128;      // trailing-update column chunk
-constexpr int L32_TM = 8, L32_TN = 8;
+constexpr int L32_TM = 4, L32_TN = 8;
 
-__global__ void __launch_bounds__(LU_THREADS, 1)
+__global__ void __launch_bounds__(LU_THREADS, 2)
 k_lu32(Dims dm, float* __restrict__ S, int8_t* __restrict__ status, int* __restrict__ pivots) {
   extern __shared__ __align__(16) unsigned char smraw[];
   float* P = reinterpret_cast<float*>(smraw);          // [NB][n] column-major panel
@@ -476,9 +476,7 @@ k_lu32(Dims dm, float* __restrict__ S, int8_t* __restrict__ status, int* __restr
             const float* lp = P + j * n + (rr0 - kb);
             if (vec && rr0 + L32_TM <= n) {
               float4 l0 = *reinterpret_cast<const float4*>(lp);
-              float4 l1 = *reinterpret_cast<const float4*>(lp + 4);
               lv[0] = l0.x; lv[1] = l0.y; lv[2] = l0.z; lv[3] = l0.w;
-              lv[4] = l1.x; lv[5] = l1.y; lv[6] = l1.z; lv[7] = l1.w;
             } else {
 #pragma unroll
               for (int a = 0; a < L32_TM; ++a) lv[a] = (rr0 + a < n) ? lp[a] : 0.f;

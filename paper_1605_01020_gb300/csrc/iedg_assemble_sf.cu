@@ -28,18 +28,22 @@ size_t sf_smem(const Dims& dm) {
   return n * sizeof(T);
 }
 
-template <class T>
+// Element sizes are compile-time constants (NP1 = p + 1, NQ1 = p + 2), so every index
+// split below is a multiply-shift; every chunk runs over all SF_CC columns with the
+// columns past the end masked.
+template <class T, int NP1, int NQ1>
 __global__ void __launch_bounds__(SF_THREADS)
 k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, const double* __restrict__ rhs64) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
   const int tid = threadIdx.x;
-  const int m = dm.m, m2 = m * m, d = 3;
+  constexpr int m = 5, m2 = 25, d = 3;
+  constexpr int np1 = NP1, nq1 = NQ1;
+  constexpr int Np = NP1 * NP1 * NP1, Nq = NQ1 * NQ1 * NQ1, Nfq = NQ1 * NQ1, Nfn = NP1 * NP1;
+  constexpr int Nb = Np - (NP1 - 2) * (NP1 - 2) * (NP1 - 2), Nfp = 6 * Nfq;
   const int64_t e = blockIdx.x / m2;
   const int pair = blockIdx.x % m2, i = pair / m, k = pair % m;
   const bool has_cq = !(i == 0 || (i <= d && k == m - 1));
-  const int Np = dm.Np, Nb = dm.Nb, Nq = dm.Nq, Nfp = dm.Nfp, Nfq = dm.Nfq, Nfn = dm.Nfn;
-  const int nq1 = dm.nq1, np1 = dm.np1;
   const int ncol_all = Np + Nb, ncol_vol = has_cq ? Np + Nb : Np;
   T* sL = sm;                                        // [nq1][np1]
   T* sdL = sL + nq1 * np1;                           // [nq1][np1]
@@ -63,10 +67,9 @@ k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, 
   T* Se = S + e * nn * ld;
   if (rhs64 != nullptr && pair == 0)
     for (int r = tid; r < nn; r += SF_THREADS) Se[r * ld + nn] = (T)rhs64[e * nn + r];
-  const int TS = nq1 * nq1 * np1, VS = nq1 * np1 * np1;
+  constexpr int TS = nq1 * nq1 * np1, VS = nq1 * np1 * np1, cw = SF_CC;
 
   for (int c0 = 0; c0 < ncol_all; c0 += SF_CC) {
-    const int cw = min(SF_CC, ncol_all - c0);
     // ---- face parts of the boundary rows for this column chunk
     for (int idx = tid; idx < Nb * SF_CC; idx += SF_THREADS) facc[idx] = (T)0;
     for (int f = 0; f < dm.nf; ++f) {
@@ -74,8 +77,9 @@ k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, 
       for (int idx = tid; idx < Nfq * cw; idx += SF_THREADS) {
         int gf = idx / cw, c = idx % cw, col = c0 + c;
         int fp = f * Nfq + gf;
-        T v;
-        if (col < Np) {
+        T v = 0;
+        if (col >= ncol_all) {
+        } else if (col < Np) {
           v = lamsel * tb.lamw[e * Nfp + fp] * tb.PhiF[(size_t)fp * Np + col];
           if (has_cq)
             for (int l = 0; l < d; ++l) v -= jf[(size_t)(1 + l) * Nfp + fp] * GlF[((size_t)l * Nfp + fp) * Np + col];
@@ -142,6 +146,7 @@ k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, 
     // stage C: contract g_x and write the u-rows (volume + faces + mass)
     for (int idx = tid; idx < Np * cw; idx += SF_THREADS) {
       int a = idx / cw, c = idx % cw, col = c0 + c;
+      if (col >= ncol_all) continue;
       int ax = a % np1, ay = (a / np1) % np1, az = a / (np1 * np1);
       T s = 0;
       for (int gx = 0; gx < nq1; ++gx) {
@@ -158,6 +163,7 @@ k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, 
     // trace rows
     for (int idx = tid; idx < Nb * cw; idx += SF_THREADS) {
       int sl = idx / cw, c = idx % cw, col = c0 + c;
+      if (col >= ncol_all) continue;
       int64_t cs = col < Np ? (int64_t)k * Np + col : (int64_t)dm.nu + (int64_t)k * Nb + (col - Np);
       Se[((int64_t)dm.nu + (int64_t)i * Nb + sl) * ld + cs] = facc[sl * SF_CC + c];
     }
@@ -167,19 +173,33 @@ k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, 
 
 }  // namespace
 
-template <class T>
+template <class T, int NP1, int NQ1>
 static cudaError_t assemble_sf_t(iedg_mesh* M, T* S, const double* rhs64, const AsmTab<T>& tb, cudaStream_t st) {
   const Dims& dm = M->dm;
   size_t smem = sf_smem<T>(dm);
-  cudaError_t err = cudaFuncSetAttribute(k_assemble_sf<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = k_assemble_sf<T, NP1, NQ1>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  k_assemble_sf<T><<<(unsigned)(M->E * dm.m * dm.m), SF_THREADS, smem, st>>>(dm, M->ph, M->ref, tb, S, rhs64);
+  kern<<<(unsigned)(M->E * dm.m * dm.m), SF_THREADS, smem, st>>>(dm, M->ph, M->ref, tb, S, rhs64);
   return cudaGetLastError();
 }
 
+template <class T>
+static cudaError_t assemble_sf_p(iedg_mesh* M, T* S, const double* rhs64, const AsmTab<T>& tb, cudaStream_t st) {
+  switch (M->dm.p) {
+    case 2: return assemble_sf_t<T, 3, 4>(M, S, rhs64, tb, st);
+    case 3: return assemble_sf_t<T, 4, 5>(M, S, rhs64, tb, st);
+    default: return assemble_sf_t<T, 5, 6>(M, S, rhs64, tb, st);
+  }
+}
+
+bool assemble_sf_supported(const Dims& dm) {
+  return dm.d == 3 && dm.p >= 2 && dm.p <= 4 && dm.nq1 == dm.p + 2;
+}
+
 cudaError_t launch_assemble_sf(iedg_mesh* M, cudaStream_t st) {
-  if (M->precision == 0) return assemble_sf_t<double>(M, M->S, nullptr, tables64(M), st);
-  return assemble_sf_t<float>(M, M->S32, M->rhs64, tables32(M), st);
+  if (M->precision == 0) return assemble_sf_p<double>(M, M->S, nullptr, tables64(M), st);
+  return assemble_sf_p<float>(M, M->S32, M->rhs64, tables32(M), st);
 }
 
 }  // namespace iedg

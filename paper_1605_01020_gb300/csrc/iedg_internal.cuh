@@ -133,6 +133,7 @@ cudaError_t launch_rq(iedg_mesh* M, const double* q, const double* qs, double* r
                       cudaStream_t st);
 cudaError_t launch_assemble(iedg_mesh* M, cudaStream_t st);
 cudaError_t launch_assemble_sf(iedg_mesh* M, cudaStream_t st);   // 3D, sum-factorised
+bool assemble_sf_supported(const Dims& dm);
 AsmTab<double> tables64(const iedg_mesh* M);
 AsmTab<float> tables32(const iedg_mesh* M);
 cudaError_t launch_lu(iedg_mesh* M, cudaStream_t st);

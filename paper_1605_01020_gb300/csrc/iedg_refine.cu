@@ -18,6 +18,7 @@ constexpr int RF_NB = 32;            // panel width of the FP32 factorisation (k
 
 struct Work {
   double *x, *z, *v, *b, *dqn, *xv, *xq, *tv, *xf, *zf, *xqf, *tf, *ou, *ot, *red;
+  double *sL, *sdL;              // 1D tables (3D sum factorisation)
 };
 
 __device__ Work carve(const Dims& dm, double* sm) {
@@ -39,13 +40,15 @@ __device__ Work carve(const Dims& dm, double* sm) {
   w.ou = p;  p += dm.nu;
   w.ot = p;  p += dm.nt;
   w.red = p; p += 32;
+  w.sL = p;  p += dm.nq1 * dm.np1;
+  w.sdL = p; p += dm.nq1 * dm.np1;
   return w;
 }
 
 size_t work_doubles(const Dims& dm) {
   const int m = dm.m, d = dm.d;
   return (size_t)3 * dm.nu + dm.nt + (size_t)m * d * dm.Np + (size_t)m * dm.Nq * (1 + 2 * d) +
-         (size_t)m * dm.Nfp * (3 + d) + dm.nu + dm.nt + 32;
+         (size_t)m * dm.Nfp * (3 + d) + dm.nu + dm.nt + 32 + 2 * (size_t)dm.nq1 * dm.np1;
 }
 
 __device__ double block_max(double v, double* red) {
@@ -78,15 +81,46 @@ __device__ void element_apply(const Dims& dm, const Phys& ph, const RefTables& r
     w.dqn[idx] = s;
   }
   __syncthreads();
-  // values at volume points
-  for (int idx = tid; idx < (m + m * d) * Nq; idx += RF_THREADS) {
-    int row = idx / Nq, g = idx % Nq;
-    const double* src = row < m ? w.x + row * Np : w.dqn + (row - m) * Np;
-    const double* phi = ref.Phi + (size_t)g * Np;
-    double s = 0.0;
-    for (int c = 0; c < Np; ++c) s = fma(phi[c], src[c], s);
-    if (row < m) w.xv[row * Nq + g] = s;
-    else w.xq[(row - m) * Nq + g] = s;
+  // values at volume points (rows: x_k, then dq_kl)
+  const int nrow = m + m * d;
+  if (d == 3) {
+    // tensor-product interpolation: x direction first (into the point-flux buffer tv,
+    // which is free here), then y and z together
+    const int np1 = dm.np1, nq1 = dm.nq1;
+    const int S1 = nq1 * np1 * np1;
+    double* t1 = w.tv;                      // nrow * S1 <= m d Nq
+    for (int idx = tid; idx < nrow * S1; idx += RF_THREADS) {
+      int row = idx / S1, t = idx % S1;
+      int gx = t % nq1, ayz = t / nq1;
+      const double* src = (row < m ? w.x + row * Np : w.dqn + (row - m) * Np) + np1 * ayz;
+      double s = 0.0;
+      for (int ax = 0; ax < np1; ++ax) s = fma(w.sL[gx * np1 + ax], src[ax], s);
+      t1[idx] = s;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < nrow * Nq; idx += RF_THREADS) {
+      int row = idx / Nq, g = idx % Nq;
+      int gx = g % nq1, gy = (g / nq1) % nq1, gz = g / (nq1 * nq1);
+      const double* src = t1 + row * S1 + gx;
+      double s = 0.0;
+      for (int az = 0; az < np1; ++az) {
+        double t = 0.0;
+        for (int ay = 0; ay < np1; ++ay) t = fma(w.sL[gy * np1 + ay], src[nq1 * (ay + np1 * az)], t);
+        s = fma(w.sL[gz * np1 + az], t, s);
+      }
+      if (row < m) w.xv[row * Nq + g] = s;
+      else w.xq[(row - m) * Nq + g] = s;
+    }
+  } else {
+    for (int idx = tid; idx < nrow * Nq; idx += RF_THREADS) {
+      int row = idx / Nq, g = idx % Nq;
+      const double* src = row < m ? w.x + row * Np : w.dqn + (row - m) * Np;
+      const double* phi = ref.Phi + (size_t)g * Np;
+      double s = 0.0;
+      for (int c = 0; c < Np; ++c) s = fma(phi[c], src[c], s);
+      if (row < m) w.xv[row * Nq + g] = s;
+      else w.xq[(row - m) * Nq + g] = s;
+    }
   }
   // values at face points (face nodes only)
   for (int idx = tid; idx < (2 * m + m * d) * Nfp; idx += RF_THREADS) {
@@ -133,6 +167,42 @@ __device__ void element_apply(const Dims& dm, const Phys& ph, const RefTables& r
   __syncthreads();
   // projections onto the test functions
   const double* Ms = G.Mass + (size_t)e * Np * Np;
+  if (d == 3) {
+    // sum_{g,r} Dxi_r[g][a] tv_r(g) with Dxi_0 = L'(x)L(x)L, Dxi_1 = L(x)L'(x)L, Dxi_2 = L(x)L(x)L':
+    // contract z (L or L'), then y, then x
+    const int np1 = dm.np1, nq1 = dm.nq1;
+    const int TS = nq1 * nq1 * np1, VS = nq1 * np1 * np1;
+    double* t1 = w.xq;                      // m 3 TS <= m d Nq (xq is free here)
+    double* t2 = w.dqn;                     // m 2 VS <= m d Np (dqn is free here)
+    for (int idx = tid; idx < m * 3 * TS; idx += RF_THREADS) {
+      int i = idx / (3 * TS), r = (idx / TS) % 3, t = idx % TS;
+      int gxy = t % (nq1 * nq1), az = t / (nq1 * nq1);
+      const double* X = r == 2 ? w.sdL : w.sL;
+      const double* src = w.tv + (i * d + r) * Nq + gxy;
+      double s = 0.0;
+      for (int gz = 0; gz < nq1; ++gz) s = fma(X[gz * np1 + az], src[nq1 * nq1 * gz], s);
+      t1[idx] = s;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < m * VS; idx += RF_THREADS) {
+      int i = idx / VS, t = idx % VS;
+      int gx = t % nq1, ay = (t / nq1) % np1, az = t / (nq1 * np1);
+      const double* T0 = t1 + (i * 3 + 0) * TS;
+      const double* T1 = t1 + (i * 3 + 1) * TS;
+      const double* T2 = t1 + (i * 3 + 2) * TS;
+      double s0 = 0.0, s1 = 0.0;
+      for (int gy = 0; gy < nq1; ++gy) {
+        int tt = gx + nq1 * (gy + nq1 * az);
+        double Ly = w.sL[gy * np1 + ay], dLy = w.sdL[gy * np1 + ay];
+        s0 = fma(Ly, T0[tt], s0);
+        s1 = fma(dLy, T1[tt], s1);
+        s1 = fma(Ly, T2[tt], s1);
+      }
+      t2[(i * 2 + 0) * VS + t] = s0;
+      t2[(i * 2 + 1) * VS + t] = s1;
+    }
+    __syncthreads();
+  }
   for (int idx = tid; idx < m * Np; idx += RF_THREADS) {
     int i = idx / Np, a = idx % Np;
     double s = 0.0;
@@ -141,9 +211,21 @@ __device__ void element_apply(const Dims& dm, const Phys& ph, const RefTables& r
       for (int b = 0; b < Np; ++b) t = fma(Ms[a * Np + b], w.x[i * Np + b], t);
       s = ph.alpha * t;
     }
-    for (int g = 0; g < Nq; ++g)
-      for (int r = 0; r < d; ++r)
-        s = fma(ref.Dxi[((size_t)r * Nq + g) * Np + a], w.tv[(i * d + r) * Nq + g], s);
+    if (d == 3) {
+      const int np1 = dm.np1, nq1 = dm.nq1, VS = nq1 * np1 * np1;
+      int ax = a % np1, ay = (a / np1) % np1, az = a / (np1 * np1);
+      const double* V0 = w.dqn + (i * 2 + 0) * VS;
+      const double* V1 = w.dqn + (i * 2 + 1) * VS;
+      for (int gx = 0; gx < nq1; ++gx) {
+        int t = gx + nq1 * (ay + np1 * az);
+        s = fma(w.sdL[gx * np1 + ax], V0[t], s);
+        s = fma(w.sL[gx * np1 + ax], V1[t], s);
+      }
+    } else {
+      for (int g = 0; g < Nq; ++g)
+        for (int r = 0; r < d; ++r)
+          s = fma(ref.Dxi[((size_t)r * Nq + g) * Np + a], w.tv[(i * d + r) * Nq + g], s);
+    }
     if (ref.slot[a] >= 0)
       for (int fp = 0; fp < Nfp; ++fp) s = fma(ref.PhiF[(size_t)fp * Np + a], w.tf[i * Nfp + fp], s);
     w.ou[idx] = s;
@@ -251,6 +333,7 @@ k_refine(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ, const float* __res
   Work w = carve(dm, sm);
   const int64_t e = blockIdx.x;
   const int tid = threadIdx.x;
+  for (int i = tid; i < dm.nq1 * dm.np1; i += RF_THREADS) { w.sL[i] = ref.L1[i]; w.sdL[i] = ref.dL1[i]; }
   const double* rhs = rhs64 + e * dm.n;
   for (int i = tid; i < dm.nu; i += RF_THREADS) w.b[i] = rhs[i];
   for (int i = tid; i < dm.nt; i += RF_THREADS) w.z[i] = 0.0;
@@ -273,6 +356,7 @@ k_backsub_mixed(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ, const int64
   const int64_t e = blockIdx.x;
   const int tid = threadIdx.x;
   const int m = dm.m, d = dm.d, Np = dm.Np, Nb = dm.Nb;
+  for (int i = tid; i < dm.nq1 * dm.np1; i += RF_THREADS) { w.sL[i] = ref.L1[i]; w.sdL[i] = ref.dL1[i]; }
   for (int i = tid; i < dm.nu; i += RF_THREADS) w.x[i] = 0.0;
   for (int i = tid; i < dm.nt; i += RF_THREADS) {
     int k = i / Nb, t = i % Nb;

@@ -33,6 +33,11 @@ def _case(name):
         st = W.make_state(mesh, W.fourier_perturbed_field(2, 0.3, 5, amp=0.05), 6, noise=0.01)
         prm = dict(gamma=1.4, Pr=0.72, Re=100.0, Minf=0.3, alpha=0.0)
         return W.Workload("2D p=3 3x4 steady", mesh, st, prm)
+    if name == "p4-2cube":
+        mesh = W.structured_mesh(3, 2, 4, mapping=W.stretched_mapping(91, ratio=4.0))
+        st = W.make_state(mesh, W.broadband_field(0.3, 92), 93, noise=0.005)
+        prm = dict(gamma=1.4, Pr=0.72, Re=2.5e5, Minf=0.3, alpha=W.dirk_alpha())
+        return W.Workload("3D p=4 2^3 curved", mesh, st, prm)
     if name == "2d-p1":
         mesh = W.structured_mesh(2, 4, 1)
         st = W.make_state(mesh, W.fourier_perturbed_field(2, 0.3, 7, amp=0.05), 8, noise=0.01, uref_shift=0.01)
@@ -41,7 +46,7 @@ def _case(name):
     raise KeyError(name)
 
 
-CASES = ["cfg1", "cfg1-noisy", "p3-2cube", "p2-curved", "2d-p3-steady", "2d-p1"]
+CASES = ["cfg1", "cfg1-noisy", "p3-2cube", "p2-curved", "2d-p3-steady", "2d-p1", "p4-2cube"]
 
 
 @pytest.mark.parametrize("name", CASES)
@@ -166,7 +171,7 @@ def _mixed_mesh(wl):
     return iedg.mesh_from_workload(wl, precision=1)
 
 
-@pytest.mark.parametrize("name", ["cfg1-noisy", "p3-2cube", "p2-curved", "2d-p3-steady", "2d-p1"])
+@pytest.mark.parametrize("name", ["cfg1-noisy", "p3-2cube", "p2-curved", "2d-p3-steady", "2d-p1", "p4-2cube"])
 def test_mixed_condensed_parity(name):
     wl = _case(name)
     st = wl.state
@@ -215,3 +220,49 @@ def test_mixed_full_size_sampled(cfg):
           f"flagged {int((status != 0).sum())}")
     assert (status == 0).all()
     assert kerr <= TOL_MIXED_K and rerr <= TOL_MIXED and duerr <= TOL_MIXED and dqerr <= TOL_MIXED
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_captured_step_matches_eager(precision):
+    """The whole element-local step (residual with lifting, condensation,
+    back-substitution) captured once in a CUDA graph and replayed gives the same
+    outputs as eager calls (the library launches only on the caller's stream and
+    allocates nothing per call)."""
+    import torch
+    from paper_1605_01020_gb300 import iedg
+    wl = _case("p3-2cube")
+    st = wl.state
+    mesh = iedg.mesh_from_workload(wl, precision=precision)
+    E, Np, m, d, T = mesh.E, mesh.Np, mesh.m, mesh.d, mesh.T
+    u, uh, duh = dev(st.u), dev(st.uhat), dev(st.duhat)
+    f64 = torch.float64
+    bufs = dict(q=torch.empty(E, Np, m, d, dtype=f64, device="cuda"),
+                rq=torch.empty(E, Np, m, d, dtype=f64, device="cuda"),
+                ru=torch.empty(E, Np, m, dtype=f64, device="cuda"), rfl=torch.empty(T, m, dtype=f64, device="cuda"),
+                K=torch.empty(mesh.nnzb, m, m, dtype=f64, device="cuda"), R=torch.empty(T, m, dtype=f64, device="cuda"),
+                du=torch.empty(E, Np, m, dtype=f64, device="cuda"), dq=torch.empty(E, Np, m, d, dtype=f64, device="cuda"))
+
+    def step():
+        mesh.eval_residual(u, uh, q=None, q_out=bufs["q"], r_q=bufs["rq"], r_u=bufs["ru"], r_fl=bufs["rfl"])
+        mesh.assemble_condensed(u, bufs["q"], uh, K=bufs["K"], R=bufs["R"])
+        mesh.back_substitute(duh, bufs["du"], bufs["dq"])
+
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        step()                                    # warm-up (kernel attributes set outside capture)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    eager = {k: v.clone() for k, v in bufs.items()}
+    for v in bufs.values():
+        v.zero_()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step()
+    for v in bufs.values():
+        v.zero_()
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    for k in bufs:
+        assert torch.equal(bufs[k], eager[k]), k

@@ -54,15 +54,26 @@ def a4a5_flops(d, p, nq1):
 
 
 def assemble_actual_flops(d, p, nq1):
-    """Flops the assembly kernel performs per element with the q-elimination folded in
-    at the quadrature points (volume contraction, right-operand build, face terms)."""
+    """Flops the sum-factorised 3D assembly kernel performs per element: right-operand
+    build, three 1D contraction stages over the volume points, two 1D stages per face,
+    for every (equation, unknown) component pair; pairs whose viscous Jacobian is zero
+    skip the lifted-gradient terms."""
     m = d + 2
-    Np, Nq, Nb = (p + 1) ** d, nq1 ** d, (p + 1) ** d - (p - 1) ** d
-    Nfn, Nfq = (p + 1) ** (d - 1), nq1 ** (d - 1)
-    nf = 2 * d
-    vol = 2 * Np * Nq * d * (Np + Nb) + 2 * Nq * d * (Np * (1 + d) + Nb * d)
-    face = nf * (2 * Nfq * (Np * (1 + d) + Nb * (1 + d)) + 2 * Nfn * Nfq * (Np + Nb))
-    return m * m * (vol + face)
+    np1 = p + 1
+    Np, Nq, Nb = np1 ** d, nq1 ** d, np1 ** d - (p - 1) ** d
+    Nfq, Nfn = nq1 ** (d - 1), np1 ** (d - 1)
+    TS, VS = nq1 * nq1 * np1, nq1 * np1 * np1
+    ncol = Np + Nb
+    fma = 0
+    for i in range(m):
+        for k in range(m):
+            cq = not (i == 0 or (i <= d and k == m - 1))
+            build = Nq * (Np * 3 * (1 + (d if cq else 0)) + (Nb * 3 * d if cq else 0))
+            stages = ncol * (3 * TS * nq1 + VS * 3 * nq1 + Np * 2 * nq1)
+            face = 2 * d * (Nfq * (Np * (1 + (d if cq else 0)) + Nb * (1 + (d if cq else 0)))
+                            + ncol * (nq1 * np1 * nq1 + Nfn * nq1))
+            fma += build + stages + face
+    return 2 * fma
 
 
 # DRAM bytes per element of the FP64 LU / Schur kernel, from one ncu capture of

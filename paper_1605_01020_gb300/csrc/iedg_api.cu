@@ -169,7 +169,7 @@ Dims make_dims(int d, int p, int quad_extra) {
   dm.nu = dm.m * dm.Np;
   dm.nt = dm.m * dm.Nb;
   dm.n = dm.nu + dm.nt;
-  dm.ld = (dm.n + 1 + 1) & ~1;
+  dm.ld = (dm.n + 1 + 3) & ~3;        // rows start on 16-byte boundaries (float4 / double2 access)
   return dm;
 }
 

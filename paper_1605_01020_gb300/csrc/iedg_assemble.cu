@@ -460,16 +460,28 @@ k_lu32(Dims dm, float* __restrict__ S, int8_t* __restrict__ status, int* __restr
         Uc[idx] = (j < nb && c < cw) ? A[(int64_t)(kb + j) * ld + cc + c] : 0.f;
       }
       __syncthreads();
+      // the tile's 8 columns lie inside the row (padding columns past n included, they
+      // are never read as results): 16-byte vector access
+      const bool cvec = ((cc & 3) == 0) && (cc + tc * L32_TN + L32_TN <= ld);
       for (int rb = r0; rb < n; rb += 16 * L32_TM) {
         const int rr0 = rb + tr * L32_TM;
         float acc[L32_TM][L32_TN];
 #pragma unroll
-        for (int a = 0; a < L32_TM; ++a)
+        for (int a = 0; a < L32_TM; ++a) {
+          const int rr = rr0 + a;
+          if (cvec && rr < n) {
+            const float4* src = reinterpret_cast<const float4*>(A + (int64_t)rr * ld + cc + tc * L32_TN);
+            float4 v0 = src[0], v1 = src[1];
+            acc[a][0] = v0.x; acc[a][1] = v0.y; acc[a][2] = v0.z; acc[a][3] = v0.w;
+            acc[a][4] = v1.x; acc[a][5] = v1.y; acc[a][6] = v1.z; acc[a][7] = v1.w;
+          } else {
 #pragma unroll
-          for (int b = 0; b < L32_TN; ++b) {
-            int rr = rr0 + a, c = tc * L32_TN + b;
-            acc[a][b] = (rr < n && c < cw) ? A[(int64_t)rr * ld + cc + c] : 0.f;
+            for (int b = 0; b < L32_TN; ++b) {
+              int c = tc * L32_TN + b;
+              acc[a][b] = (rr < n && c < cw) ? A[(int64_t)rr * ld + cc + c] : 0.f;
+            }
           }
+        }
         if (rr0 < n) {
           for (int j = 0; j < nb; ++j) {
             float lv[L32_TM], uv[L32_TN];
@@ -492,12 +504,20 @@ k_lu32(Dims dm, float* __restrict__ S, int8_t* __restrict__ status, int* __restr
           }
         }
 #pragma unroll
-        for (int a = 0; a < L32_TM; ++a)
+        for (int a = 0; a < L32_TM; ++a) {
+          const int rr = rr0 + a;
+          if (cvec && rr < n) {
+            float4* dst = reinterpret_cast<float4*>(A + (int64_t)rr * ld + cc + tc * L32_TN);
+            dst[0] = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+            dst[1] = make_float4(acc[a][4], acc[a][5], acc[a][6], acc[a][7]);
+          } else {
 #pragma unroll
-          for (int b = 0; b < L32_TN; ++b) {
-            int rr = rr0 + a, c = tc * L32_TN + b;
-            if (rr < n && c < cw) A[(int64_t)rr * ld + cc + c] = acc[a][b];
+            for (int b = 0; b < L32_TN; ++b) {
+              int c = tc * L32_TN + b;
+              if (rr < n && c < cw) A[(int64_t)rr * ld + cc + c] = acc[a][b];
+            }
           }
+        }
       }
       __syncthreads();
     }

@@ -18,7 +18,7 @@ struct Dims {
   int nu;   // m Np   : element unknowns after q-elimination (u block)
   int nt;   // m Nb   : element trace unknowns
   int n;    // nu + nt: rows of the bordered element matrix
-  int ld;   // leading dimension of the bordered matrix (>= n + 1, even)
+  int ld;   // leading dimension of the bordered matrix (>= n + 1, multiple of 4)
 };
 
 struct Phys {

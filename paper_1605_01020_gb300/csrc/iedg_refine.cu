@@ -13,7 +13,7 @@
 namespace iedg {
 namespace {
 
-constexpr int RF_THREADS = 256;
+constexpr int RF_THREADS = 512;
 constexpr int RF_NB = 32;            // panel width of the FP32 factorisation (k_lu<float, 32>)
 
 struct Work {
@@ -70,15 +70,35 @@ __device__ void element_apply(const Dims& dm, const Phys& ph, const RefTables& r
   const int tid = threadIdx.x;
   const int m = dm.m, d = dm.d, Np = dm.Np, Nb = dm.Nb, Nq = dm.Nq, Nfp = dm.Nfp, Nfq = dm.Nfq;
   const int Nfn = dm.Nfn;
-  // nodal lifted gradient of (x, z): dq_kl = -G_l x_k + H_l z_k
-  for (int idx = tid; idx < m * d * Np; idx += RF_THREADS) {
-    int k = idx / (d * Np), l = (idx / Np) % d, c = idx % Np;
-    const double* gl = G.Gl + (((size_t)e * d + l) * Np + c) * Np;
-    const double* hl = G.Hl + (((size_t)e * d + l) * Np + c) * Nb;
-    double s = 0.0;
-    for (int b = 0; b < Np; ++b) s = fma(-gl[b], w.x[k * Np + b], s);
-    for (int t = 0; t < Nb; ++t) s = fma(hl[t], w.z[k * Nb + t], s);
-    w.dqn[idx] = s;
+  // nodal lifted gradient of (x, z): dq_kl = -G_l x_k + H_l z_k.  One warp per row
+  // (l, c) of G_l | H_l: the lanes read the row once, coalesced, for all m components.
+  {
+    const int lane = tid & 31, warp = tid >> 5, nwarp = RF_THREADS / 32;
+    for (int row = warp; row < d * Np; row += nwarp) {
+      const int l = row / Np, c = row % Np;
+      const double* gl = G.Gl + (((size_t)e * d + l) * Np + c) * Np;
+      const double* hl = G.Hl + (((size_t)e * d + l) * Np + c) * Nb;
+      double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+      for (int b = lane; b < Np; b += 32) {
+        const double g = gl[b];
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+          if (k < m) acc[k] = fma(-g, w.x[k * Np + b], acc[k]);
+      }
+      for (int t = lane; t < Nb; t += 32) {
+        const double h = hl[t];
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+          if (k < m) acc[k] = fma(h, w.z[k * Nb + t], acc[k]);
+      }
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        double v = acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0 && k < m) w.dqn[(k * d + l) * Np + c] = v;
+      }
+    }
   }
   __syncthreads();
   // values at volume points (rows: x_k, then dq_kl)
@@ -325,7 +345,7 @@ __device__ double refine_solve(const Dims& dm, const Phys& ph, const RefTables& 
 }
 
 // One CTA per element: y = A~^-1 F~ refined, R_e = G~ - C~ y.
-__global__ void __launch_bounds__(RF_THREADS)
+__global__ void __launch_bounds__(RF_THREADS, 2)
 k_refine(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ, const float* __restrict__ S32,
          const int* __restrict__ piv, const double* __restrict__ rhs64, double* __restrict__ y64,
          double* __restrict__ re64, int8_t* __restrict__ status) {
@@ -346,7 +366,7 @@ k_refine(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ, const float* __res
 }
 
 // One CTA per element: du = A~^-1 (F~ - B~ dU_e) refined, dq = (q* - q) - G_l du + H_l dU_e.
-__global__ void __launch_bounds__(RF_THREADS)
+__global__ void __launch_bounds__(RF_THREADS, 2)
 k_backsub_mixed(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ, const int64_t* __restrict__ etrace,
                 const float* __restrict__ S32, const int* __restrict__ piv, const double* __restrict__ rhs64,
                 const double* __restrict__ rhoq, const double* __restrict__ duhat, double* __restrict__ du,

@@ -226,6 +226,12 @@ def run_ours(args, wl, rank, world, local_rank):
     u = torch.as_tensor(st.u, dtype=f64, device=dev)
     uh = torch.as_tensor(st.uhat, dtype=f64, device=dev)
     duh = torch.as_tensor(st.duhat, dtype=f64, device=dev)
+    schedule = None
+    if not args.no_autotune:
+        from paper_1605_01020_gb300 import autotune
+        qt = torch.as_tensor(st.q, dtype=f64, device=dev)
+        schedule, _ = autotune.autotune(mesh, u, qt, uh, 0, reps=1)
+        del qt
     q = torch.empty(E, Np, m, d, dtype=f64, device=dev)
     rq = torch.empty_like(q)
     ru = torch.empty(E, Np, m, dtype=f64, device=dev)
@@ -349,7 +355,7 @@ def run_ours(args, wl, rank, world, local_rank):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(wl), "elements": E, "order": wl.mesh.p, "precision": "fp64",
                        "l2": "flushed between steps (512 MB write); per-step workspace 12 GB >> L2",
-                       "per_rank_elements": E},
+                       "per_rank_elements": E, "schedule": schedule},
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": value_e2e, "unit": "elements/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -373,6 +379,12 @@ def run_mixed(args, wl, mesh64, dev, step_outputs, inputs, flush, barrier):
     mesh = iedg.mesh_from_workload(wl, precision=1)
     E, Np, m, d, T = mesh.E, mesh.Np, mesh.m, mesh.d, mesh.T
     f64 = torch.float64
+    schedule = None
+    if not args.no_autotune:
+        from paper_1605_01020_gb300 import autotune
+        qt = torch.as_tensor(wl.state.q, dtype=f64, device=dev)
+        schedule, _ = autotune.autotune(mesh, u, qt, uh, 1, reps=1)
+        del qt
     q = torch.empty(E, Np, m, d, dtype=f64, device=dev)
     rq, ru, rfl = torch.empty_like(q), torch.empty(E, Np, m, dtype=f64, device=dev), torch.empty(T, m, dtype=f64, device=dev)
     K, R = torch.empty_like(K64), torch.empty_like(R64)
@@ -402,6 +414,7 @@ def run_mixed(args, wl, mesh64, dev, step_outputs, inputs, flush, barrier):
     err = lambda a, b: float((a - b).abs().max() / b.abs().max().clamp_min(1e-300))
     status = mesh.element_status()
     out = {"ms_total": e0.elapsed_time(e1), "precision": "FP32 element matrix + partial LU, FP64 refinement",
+           "schedule": schedule,
            "err_vs_fp64": {"K": err(K, K64), "R": err(R, R64), "du": err(du, du64), "dq": err(dq, dq64)},
            "element_status_nonzero": int((status != 0).sum()),
            "gpu_launches": sum(v[0] for v in prof.values()),
@@ -420,6 +433,7 @@ def main():
     ap.add_argument("--cells", type=int, default=None, help="override cells per direction (smaller case)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch schedule")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-elems", type=int, default=4)
     args = ap.parse_args()

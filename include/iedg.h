@@ -141,6 +141,44 @@ int iedg_back_substitute(iedg_mesh* mesh, const double* duhat, double* du, doubl
  * (>= 0) or a negative error code. */
 int64_t iedg_element_status(iedg_mesh* mesh, int8_t* out, void* stream);
 
+/* Trace solve K dU = R (Eq. LS) on the GPU: restarted GMRES with iterated classical
+ * Gram-Schmidt orthogonalisation and left preconditioning (Sec. 2.2.2), the
+ * preconditioner being block Jacobi with the m x m diagonal blocks of K (the one-
+ * subdomain, zero-overlap case of the paper's additive Schwarz family).
+ *   K  [nnzb][m][m] in the pattern of iedg_trace_pattern, R [n_trace][m]  (device)
+ *   dU [n_trace][m] output (device), starts from zero
+ *   restart 1..IEDG_MAX_RESTART, max_iter >= 1 (Arnoldi steps in total),
+ *   rtol > 0: stop when |M^-1 (R - K dU)| <= rtol |M^-1 R| (the GMRES estimate
+ *   during a cycle, recomputed at restarts).
+ * Outputs iterations and the final relative preconditioned residual (may be NULL).
+ * Synchronises `stream` once per Arnoldi step (the small least-squares problem is
+ * solved on the host).  Workspace is allocated with the mesh.  IEDG_ERR_INVALID_ARG
+ * for a singular diagonal block. */
+#define IEDG_MAX_RESTART 40
+int iedg_trace_solve(iedg_mesh* mesh, const double* K, const double* R, double* dU, int32_t restart,
+                     int32_t max_iter, double rtol, int32_t* iterations, double* rel_residual,
+                     void* stream);
+
+/* Launch schedule of the batched kernels (no counterpart in the paper; the choices
+ * an autotuner sweeps, see paper_1605_01020_gb300/autotune.py).  Results do not
+ * depend on it except through floating-point summation order in the LU.
+ *   lu_persistent: 1 = the batched LU runs as a persistent grid (resident CTAs per
+ *                  SM x SMs) that takes elements from an atomic queue; 0 = one CTA
+ *                  per element.
+ *   lu_panel:      FP64 LU panel width, 16 or 32 (32 falls back to 16 when the panel
+ *                  does not fit in shared memory).
+ *   asm_chunk:     assembly column chunk, 8, 16 or 32 (0 = default: 8 for FP64, 16
+ *                  for FP32; too large a chunk for shared memory falls back).
+ * iedg_set_schedule rejects other values with IEDG_ERR_INVALID_ARG. */
+typedef struct {
+  int32_t lu_persistent;
+  int32_t lu_panel;
+  int32_t asm_chunk;
+  int32_t reserved[5];
+} iedg_schedule;
+int iedg_get_schedule(const iedg_mesh* mesh, iedg_schedule* out);
+int iedg_set_schedule(iedg_mesh* mesh, const iedg_schedule* in);
+
 /* Residual without any allocation (no counterpart in the paper; a service for
  * callers that cannot allocate device memory when they need a residual, e.g. code
  * whose device memory is owned by a framework pool, real-time loops where the

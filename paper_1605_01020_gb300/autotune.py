@@ -1,0 +1,76 @@
+"""Launch-schedule autotuner for the batched element kernels.
+
+For one mesh (fixed dimension, order, quadrature and precision) it times
+iedg_assemble_condensed under every candidate iedg_schedule (persistent or
+one-CTA-per-element LU, FP64 LU panel width, assembly column chunk) with CUDA
+events, keeps the fastest, and caches the choice in a JSON file keyed by the GPU
+name and the mesh class, so later runs on the same kind of GPU skip the sweep.
+Results do not depend on the schedule (beyond summation order in the LU).
+"""
+import itertools
+import json
+import os
+
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "iedg", "schedules.json")
+
+
+def mesh_key(mesh, precision, gpu_name):
+    return f"{gpu_name}|d{mesh.d}|p{mesh.order}|Np{mesh.Np}|prec{precision}"
+
+
+def candidates(precision, order):
+    """Candidate schedules: persistent LU on/off x FP64 panel 16/32 x assembly chunk."""
+    panels = [16, 32] if (precision == 0 and order <= 3) else [16]
+    chunks = [8, 16] if precision == 0 else [16, 32]
+    return [dict(lu_persistent=a, lu_panel=b, asm_chunk=c)
+            for a, b, c in itertools.product([1, 0], panels, chunks)]
+
+
+def time_assemble(mesh, u, q, uh, K, R, reps):
+    import torch
+    mesh.assemble_condensed(u, q, uh, K=K, R=R)          # warm-up (kernel attributes, caches)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        mesh.assemble_condensed(u, q, uh, K=K, R=R)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def autotune(mesh, u, q, uh, precision, reps=2, cache_path=DEFAULT_CACHE, use_cache=True):
+    """Pick the fastest schedule for `mesh` on the current GPU, apply it, and return
+    (schedule, {candidate: ms}).  `u, q, uh` are device inputs of the mesh."""
+    import torch
+    gpu = torch.cuda.get_device_name()
+    key = mesh_key(mesh, precision, gpu)
+    cache = {}
+    if use_cache and cache_path and os.path.exists(cache_path):
+        try:
+            cache = json.load(open(cache_path))
+        except (OSError, ValueError):
+            cache = {}
+    if use_cache and key in cache:
+        mesh.set_schedule(**cache[key]["schedule"])
+        return cache[key]["schedule"], cache[key].get("timings", {})
+    K = torch.empty(mesh.nnzb, mesh.m, mesh.m, dtype=torch.float64, device=u.device)
+    R = torch.empty(mesh.T, mesh.m, dtype=torch.float64, device=u.device)
+    timings = {}
+    best, best_ms = None, float("inf")
+    for cand in candidates(precision, mesh.order):
+        mesh.set_schedule(**cand)
+        ms = time_assemble(mesh, u, q, uh, K, R, reps)
+        timings[json.dumps(cand, sort_keys=True)] = ms
+        if ms < best_ms:
+            best, best_ms = cand, ms
+    mesh.set_schedule(**best)
+    if cache_path:
+        cache[key] = {"schedule": best, "timings": timings}
+        try:
+            os.makedirs(os.path.dirname(cache_path), exist_ok=True)
+            with open(cache_path, "w") as f:
+                json.dump(cache, f, indent=1, sort_keys=True)
+        except OSError:
+            pass
+    return best, timings

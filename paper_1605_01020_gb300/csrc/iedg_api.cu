@@ -383,6 +383,11 @@ static int create_impl(const iedg_mesh_desc* D, cudaStream_t st, iedg_mesh* M) {
   }
   CUDA_TRY(dalloc(M, &M->status, E));
   CUDA_TRY(dalloc(M, &M->dev_flag, 1));
+  CUDA_TRY(dalloc(M, &M->queue, 1));
+  CUDA_TRY(dalloc(M, &M->kry, (size_t)(IEDG_MAX_RESTART + 3) * T * m));
+  CUDA_TRY(dalloc(M, &M->dinv, (size_t)T * m * m));
+  CUDA_TRY(dalloc(M, &M->kpart, (size_t)(IEDG_MAX_RESTART + 1) * 512));
+  CUDA_TRY(dalloc(M, &M->khdev, (size_t)(IEDG_MAX_RESTART + 1)));
   CUDA_TRY(cudaMemsetAsync(M->dev_flag, 0, sizeof(int), st));
   CUDA_TRY(cudaMemsetAsync(M->status, 0, E, st));
 
@@ -581,5 +586,25 @@ extern "C" int iedg_profile_reset(iedg_mesh* M) {
   drain_events(M);
   for (auto& c : M->klaunch) c = 0;
   for (auto& t : M->kms) t = 0.0;
+  return IEDG_OK;
+}
+
+extern "C" int iedg_get_schedule(const iedg_mesh* M, iedg_schedule* out) {
+  if (!M || !out) return IEDG_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  out->lu_persistent = M->sched.lu_persistent;
+  out->lu_panel = M->sched.lu_panel;
+  out->asm_chunk = M->sched.asm_chunk;
+  return IEDG_OK;
+}
+
+extern "C" int iedg_set_schedule(iedg_mesh* M, const iedg_schedule* in) {
+  if (!M || !in) return fail(M, IEDG_ERR_INVALID_ARG, "null argument");
+  if ((in->lu_persistent != 0 && in->lu_persistent != 1) || (in->lu_panel != 16 && in->lu_panel != 32) ||
+      (in->asm_chunk != 0 && in->asm_chunk != 8 && in->asm_chunk != 16 && in->asm_chunk != 32))
+    return fail(M, IEDG_ERR_INVALID_ARG, "schedule values out of range");
+  M->sched.lu_persistent = in->lu_persistent;
+  M->sched.lu_panel = in->lu_panel;
+  M->sched.asm_chunk = in->asm_chunk;
   return IEDG_OK;
 }

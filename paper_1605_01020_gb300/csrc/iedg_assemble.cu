@@ -199,8 +199,8 @@ constexpr int LU_THREADS = 256;
 constexpr int UCW = 64;     // trailing-update column chunk
 
 template <class T, int NB>
-__global__ void __launch_bounds__(LU_THREADS)
-k_lu(Dims dm, T* __restrict__ S, int8_t* __restrict__ status, int* __restrict__ pivots) {
+__device__ __forceinline__ void lu_element(const Dims& dm, T* __restrict__ S, int8_t* __restrict__ status,
+                                           int* __restrict__ pivots, const int64_t e) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
   __shared__ int piv[NB];
@@ -208,7 +208,6 @@ k_lu(Dims dm, T* __restrict__ S, int8_t* __restrict__ status, int* __restrict__ 
   __shared__ int ri[LU_THREADS / 32];
   __shared__ int sing;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t e = blockIdx.x;
   const int n = dm.n, nu = dm.nu, ld = dm.ld, ncol = n + 1;
   T* A = S + e * (int64_t)n * ld;
   T* P = sm;                            // [n][NB]
@@ -353,8 +352,8 @@ constexpr int L32_NB = 32;
 constexpr int L32_UCW = 128;      // trailing-update column chunk
 constexpr int L32_TM = 4, L32_TN = 8;
 
-__global__ void __launch_bounds__(LU_THREADS, 2)
-k_lu32(Dims dm, float* __restrict__ S, int8_t* __restrict__ status, int* __restrict__ pivots) {
+__device__ __forceinline__ void lu32_element(const Dims& dm, float* __restrict__ S, int8_t* __restrict__ status,
+                                             int* __restrict__ pivots, const int64_t e) {
   extern __shared__ __align__(16) unsigned char smraw[];
   float* P = reinterpret_cast<float*>(smraw);          // [NB][n] column-major panel
   float* Uc = P + (size_t)L32_NB * dm.n;                // [NB][UCW]
@@ -363,7 +362,6 @@ k_lu32(Dims dm, float* __restrict__ S, int8_t* __restrict__ status, int* __restr
   __shared__ int ri[LU_THREADS / 32];
   __shared__ int sing;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t e = blockIdx.x;
   const int n = dm.n, nu = dm.nu, ld = dm.ld, ncol = n + 1;
   float* A = S + e * (int64_t)n * ld;
   if (tid == 0) sing = 0;
@@ -532,6 +530,37 @@ k_lu32(Dims dm, float* __restrict__ S, int8_t* __restrict__ status, int* __restr
   if (tid == 0) status[e] = sing ? IEDG_ELEM_SINGULAR : (bad ? IEDG_ELEM_NONFINITE : IEDG_ELEM_OK);
 }
 
+// Element scheduling of the batched LU.  queue == nullptr: one CTA per element.
+// Otherwise a persistent grid (a few CTAs per SM) takes elements from an atomic
+// counter in order, so no SM idles in a partial last wave.
+__device__ __forceinline__ bool next_element(int64_t* queue, int64_t E, int64_t it, int64_t* e_out) {
+  __shared__ unsigned long long s_next;
+  if (queue == nullptr) {
+    *e_out = blockIdx.x;
+    return it == 0;
+  }
+  if (threadIdx.x == 0) s_next = atomicAdd(reinterpret_cast<unsigned long long*>(queue), 1ull);
+  __syncthreads();
+  const int64_t e = (int64_t)s_next;
+  __syncthreads();
+  *e_out = e;
+  return e < E;
+}
+
+template <class T, int NB>
+__global__ void __launch_bounds__(LU_THREADS)
+k_lu(Dims dm, T* __restrict__ S, int8_t* __restrict__ status, int* __restrict__ pivots, int64_t* queue, int64_t E) {
+  int64_t e;
+  for (int64_t it = 0; next_element(queue, E, it, &e); ++it) lu_element<T, NB>(dm, S, status, pivots, e);
+}
+
+__global__ void __launch_bounds__(LU_THREADS, 2)
+k_lu32(Dims dm, float* __restrict__ S, int8_t* __restrict__ status, int* __restrict__ pivots, int64_t* queue,
+       int64_t E) {
+  int64_t e;
+  for (int64_t it = 0; next_element(queue, E, it, &e); ++it) lu32_element(dm, S, status, pivots, e);
+}
+
 }  // namespace
 
 template <class T>
@@ -565,23 +594,57 @@ cudaError_t launch_assemble(iedg_mesh* M, cudaStream_t st) {
   return assemble_t<float>(M, M->S32, M->rhs64, tables32(M), st);
 }
 
+// Grid of the persistent form: resident CTAs per SM x SMs (never more than E).
+template <class K>
+static cudaError_t persistent_grid(K kern, size_t smem, int64_t E, unsigned* grid) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, LU_THREADS, smem);
+  if (err != cudaSuccess) return err;
+  int64_t g = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+  *grid = (unsigned)(g < E ? g : E);
+  return cudaSuccess;
+}
+
 template <class T, int NB>
 static cudaError_t lu_t(iedg_mesh* M, T* S, int* piv, cudaStream_t st) {
   const Dims& dm = M->dm;
   size_t smem = sizeof(T) * ((size_t)dm.n * NB + (size_t)NB * UCW);
   cudaError_t err = cudaFuncSetAttribute(k_lu<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  k_lu<T, NB><<<(unsigned)M->E, LU_THREADS, smem, st>>>(dm, S, M->status, piv);
+  if (M->sched.lu_persistent) {
+    unsigned grid = 0;
+    err = persistent_grid(k_lu<T, NB>, smem, M->E, &grid);
+    if (err == cudaSuccess) err = cudaMemsetAsync(M->queue, 0, sizeof(int64_t), st);
+    if (err != cudaSuccess) return err;
+    k_lu<T, NB><<<grid, LU_THREADS, smem, st>>>(dm, S, M->status, piv, M->queue, M->E);
+  } else {
+    k_lu<T, NB><<<(unsigned)M->E, LU_THREADS, smem, st>>>(dm, S, M->status, piv, nullptr, M->E);
+  }
   return cudaGetLastError();
 }
 
+size_t lu64_smem(const Dims& dm, int nb) { return sizeof(double) * ((size_t)dm.n * nb + (size_t)nb * UCW); }
+
 cudaError_t launch_lu(iedg_mesh* M, cudaStream_t st) {
-  if (M->precision == 0) return lu_t<double, 16>(M, M->S, nullptr, st);
+  if (M->precision == 0) {
+    if (M->sched.lu_panel == 32 && lu64_smem(M->dm, 32) <= 227 * 1024) return lu_t<double, 32>(M, M->S, nullptr, st);
+    return lu_t<double, 16>(M, M->S, nullptr, st);
+  }
   const Dims& dm = M->dm;
   size_t smem = sizeof(float) * ((size_t)L32_NB * dm.n + (size_t)L32_NB * L32_UCW);
   cudaError_t err = cudaFuncSetAttribute(k_lu32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  k_lu32<<<(unsigned)M->E, LU_THREADS, smem, st>>>(dm, M->S32, M->status, M->piv);
+  if (M->sched.lu_persistent) {
+    unsigned grid = 0;
+    err = persistent_grid(k_lu32, smem, M->E, &grid);
+    if (err == cudaSuccess) err = cudaMemsetAsync(M->queue, 0, sizeof(int64_t), st);
+    if (err != cudaSuccess) return err;
+    k_lu32<<<grid, LU_THREADS, smem, st>>>(dm, M->S32, M->status, M->piv, M->queue, M->E);
+  } else {
+    k_lu32<<<(unsigned)M->E, LU_THREADS, smem, st>>>(dm, M->S32, M->status, M->piv, nullptr, M->E);
+  }
   return cudaGetLastError();
 }
 

@@ -205,10 +205,9 @@ k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, 
 
 }  // namespace
 
-template <class T, int NP1, int NQ1>
+template <class T, int NP1, int NQ1, int CC>
 static cudaError_t assemble_sf_t(iedg_mesh* M, T* S, const double* rhs64, const AsmTab<T>& tb, cudaStream_t st) {
   const Dims& dm = M->dm;
-  constexpr int CC = sizeof(T) == 8 ? 8 : 16;      // FP64: smaller chunks, more CTAs per SM
   size_t smem = sf_smem<T, CC>(dm);
   auto kern = k_assemble_sf<T, NP1, NQ1, CC>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -217,12 +216,25 @@ static cudaError_t assemble_sf_t(iedg_mesh* M, T* S, const double* rhs64, const 
   return cudaGetLastError();
 }
 
+// column chunk: the schedule's choice (8, 16 or 32 columns), default 8 for FP64
+// (more CTAs per SM) and 16 for FP32; a chunk whose shared memory does not fit
+// falls back to 8
+template <class T, int NP1, int NQ1>
+static cudaError_t assemble_sf_c(iedg_mesh* M, T* S, const double* rhs64, const AsmTab<T>& tb, cudaStream_t st) {
+  int cc = M->sched.asm_chunk ? M->sched.asm_chunk : (sizeof(T) == 8 ? 8 : 16);
+  if (cc == 32 && sf_smem<T, 32>(M->dm) > 227 * 1024) cc = 16;
+  if (cc == 16 && sf_smem<T, 16>(M->dm) > 227 * 1024) cc = 8;
+  if (cc == 32) return assemble_sf_t<T, NP1, NQ1, 32>(M, S, rhs64, tb, st);
+  if (cc == 16) return assemble_sf_t<T, NP1, NQ1, 16>(M, S, rhs64, tb, st);
+  return assemble_sf_t<T, NP1, NQ1, 8>(M, S, rhs64, tb, st);
+}
+
 template <class T>
 static cudaError_t assemble_sf_p(iedg_mesh* M, T* S, const double* rhs64, const AsmTab<T>& tb, cudaStream_t st) {
   switch (M->dm.p) {
-    case 2: return assemble_sf_t<T, 3, 4>(M, S, rhs64, tb, st);
-    case 3: return assemble_sf_t<T, 4, 5>(M, S, rhs64, tb, st);
-    default: return assemble_sf_t<T, 5, 6>(M, S, rhs64, tb, st);
+    case 2: return assemble_sf_c<T, 3, 4>(M, S, rhs64, tb, st);
+    case 3: return assemble_sf_c<T, 4, 5>(M, S, rhs64, tb, st);
+    default: return assemble_sf_c<T, 5, 6>(M, S, rhs64, tb, st);
   }
 }
 

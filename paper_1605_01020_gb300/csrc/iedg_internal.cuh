@@ -25,6 +25,13 @@ struct Phys {
   double gamma, Pr, Re, alpha;
 };
 
+// Launch schedule (host-side choices the autotuner sweeps; see iedg_schedule).
+struct Schedule {
+  int lu_persistent = 1;     // batched LU as a persistent grid with an element queue
+  int lu_panel = 16;         // FP64 LU panel width (16 or 32; 32 only when it fits shared memory)
+  int asm_chunk = 0;         // assembly column chunk (0 = default: 8 for FP64, 16 for FP32)
+};
+
 // Reference-element tables (device), shared by all elements.
 struct RefTables {
   double* Phi;    // [Nq][Np]
@@ -105,6 +112,12 @@ struct iedg_mesh {
   double* y64 = nullptr;        // [E][nu]       refined A~^-1 F~
   double* re64 = nullptr;       // [E][m][Nb]    refined R_e (component-major)
   int8_t* status = nullptr;     // [E]
+  int64_t* queue = nullptr;     // element counter of persistent launches
+  double* kry = nullptr;        // trace solve: Krylov basis [IEDG_MAX_RESTART+1][T m] + 2 work vectors
+  double* dinv = nullptr;       // trace solve: inverted diagonal blocks [T][m][m]
+  double* kpart = nullptr;      // trace solve: dot-product partial sums
+  double* khdev = nullptr;      // trace solve: small vector of coefficients
+  iedg::Schedule sched;
   int* dev_flag = nullptr;      // geometry error flag
   bool assembled = false;
   // tracing: launches per kernel, events while profiling is on

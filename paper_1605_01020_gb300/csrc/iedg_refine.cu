@@ -65,8 +65,9 @@ __device__ double block_max(double v, double* red) {
 }
 
 // ou = A~ x + B~ z (u-rows), ot = C~ x + D~ z (trace rows), all FP64.
+// use_x / use_z = false skip the terms of an operand that is identically zero.
 __device__ void element_apply(const Dims& dm, const Phys& ph, const RefTables& ref, const Geo& G,
-                              const PointJac& PJ, int64_t e, Work& w) {
+                              const PointJac& PJ, int64_t e, Work& w, bool use_x, bool use_z) {
   const int tid = threadIdx.x;
   const int m = dm.m, d = dm.d, Np = dm.Np, Nb = dm.Nb, Nq = dm.Nq, Nfp = dm.Nfp, Nfq = dm.Nfq;
   const int Nfn = dm.Nfn;
@@ -79,18 +80,20 @@ __device__ void element_apply(const Dims& dm, const Phys& ph, const RefTables& r
       const double* gl = G.Gl + (((size_t)e * d + l) * Np + c) * Np;
       const double* hl = G.Hl + (((size_t)e * d + l) * Np + c) * Nb;
       double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-      for (int b = lane; b < Np; b += 32) {
-        const double g = gl[b];
+      if (use_x)
+        for (int b = lane; b < Np; b += 32) {
+          const double g = gl[b];
 #pragma unroll
-        for (int k = 0; k < 5; ++k)
-          if (k < m) acc[k] = fma(-g, w.x[k * Np + b], acc[k]);
-      }
-      for (int t = lane; t < Nb; t += 32) {
-        const double h = hl[t];
+          for (int k = 0; k < 5; ++k)
+            if (k < m) acc[k] = fma(-g, w.x[k * Np + b], acc[k]);
+        }
+      if (use_z)
+        for (int t = lane; t < Nb; t += 32) {
+          const double h = hl[t];
 #pragma unroll
-        for (int k = 0; k < 5; ++k)
-          if (k < m) acc[k] = fma(h, w.z[k * Nb + t], acc[k]);
-      }
+          for (int k = 0; k < 5; ++k)
+            if (k < m) acc[k] = fma(h, w.z[k * Nb + t], acc[k]);
+        }
 #pragma unroll
       for (int k = 0; k < 5; ++k) {
         double v = acc[k];
@@ -145,6 +148,7 @@ __device__ void element_apply(const Dims& dm, const Phys& ph, const RefTables& r
   // values at face points (face nodes only)
   for (int idx = tid; idx < (2 * m + m * d) * Nfp; idx += RF_THREADS) {
     int row = idx / Nfp, fp = idx % Nfp, f = fp / Nfq;
+    if ((row < m && !use_x) || (row >= m && row < 2 * m && !use_z)) continue;
     const double* phi = ref.PhiF + (size_t)fp * Np;
     double s = 0.0;
     for (int tn = 0; tn < Nfn; ++tn) {
@@ -169,17 +173,17 @@ __device__ void element_apply(const Dims& dm, const Phys& ph, const RefTables& r
     double s = 0.0;
     for (int k = 0; k < m; ++k) {
       const double* o = jv + (size_t)(i * m + k) * jvs;
-      s = fma(o[(size_t)r * Nq + g], w.xv[k * Nq + g], s);
+      if (use_x) s = fma(o[(size_t)r * Nq + g], w.xv[k * Nq + g], s);
       for (int l = 0; l < d; ++l) s = fma(o[(size_t)(d + l * d + r) * Nq + g], w.xq[(k * d + l) * Nq + g], s);
     }
     w.tv[(i * d + r) * Nq + g] = s;
   }
   for (int idx = tid; idx < m * Nfp; idx += RF_THREADS) {
     int i = idx / Nfp, fp = idx % Nfp;
-    double s = PJ.lamw[e * Nfp + fp] * w.xf[i * Nfp + fp];
+    double s = use_x ? PJ.lamw[e * Nfp + fp] * w.xf[i * Nfp + fp] : 0.0;
     for (int k = 0; k < m; ++k) {
       const double* o = jf + (size_t)(i * m + k) * jfs;
-      s = fma(o[fp], w.zf[k * Nfp + fp], s);
+      if (use_z) s = fma(o[fp], w.zf[k * Nfp + fp], s);
       for (int l = 0; l < d; ++l) s = fma(o[(size_t)(1 + l) * Nfp + fp], w.xqf[(k * d + l) * Nfp + fp], s);
     }
     w.tf[i * Nfp + fp] = s;
@@ -226,7 +230,7 @@ __device__ void element_apply(const Dims& dm, const Phys& ph, const RefTables& r
   for (int idx = tid; idx < m * Np; idx += RF_THREADS) {
     int i = idx / Np, a = idx % Np;
     double s = 0.0;
-    if (ph.alpha != 0.0) {
+    if (ph.alpha != 0.0 && use_x) {
       double t = 0.0;
       for (int b = 0; b < Np; ++b) t = fma(Ms[a * Np + b], w.x[i * Np + b], t);
       s = ph.alpha * t;
@@ -259,32 +263,41 @@ __device__ void element_apply(const Dims& dm, const Phys& ph, const RefTables& r
   __syncthreads();
 }
 
-// v <- A~32^-1 v with the FP32 factors (panel order, pivots as applied), FP64 arithmetic.
-__device__ void solve32(const Dims& dm, const float* __restrict__ A, const int* __restrict__ piv, double* v) {
+// v <- A~32^-1 v with the FP32 factors (panel order, pivots as applied).  A correction
+// only needs FP32 accuracy (the residual it corrects is FP64), so the solve runs in
+// FP32 on a scaled copy of v held in f (nu floats, any free shared buffer).
+__device__ void solve32(const Dims& dm, const float* __restrict__ A, const int* __restrict__ piv, double* v,
+                        float* f, double* red) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = RF_THREADS / 32;
   const int nu = dm.nu, ld = dm.ld;
+  double mx = 0.0;
+  for (int i = tid; i < nu; i += RF_THREADS) mx = fmax(mx, fabs(v[i]));
+  mx = block_max(mx, red);
+  const double sc = mx > 0.0 ? mx : 1.0;
+  for (int i = tid; i < nu; i += RF_THREADS) f[i] = (float)(v[i] / sc);
+  __syncthreads();
   for (int kb = 0; kb < nu; kb += RF_NB) {
     const int nb = min(RF_NB, nu - kb);
     if (tid == 0)
       for (int j = 0; j < nb; ++j) {
         int p = piv[kb + j];
-        if (p != kb + j) { double t = v[kb + j]; v[kb + j] = v[p]; v[p] = t; }
+        if (p != kb + j) { float t = f[kb + j]; f[kb + j] = f[p]; f[p] = t; }
       }
     __syncthreads();
     if (warp == 0) {
       for (int j = 0; j < nb; ++j) {
-        double vj = v[kb + j];
+        float vj = f[kb + j];
         __syncwarp();
-        if (lane > j && lane < nb) v[kb + lane] = fma(-(double)A[(int64_t)(kb + lane) * ld + kb + j], vj, v[kb + lane]);
+        if (lane > j && lane < nb) f[kb + lane] = fmaf(-A[(int64_t)(kb + lane) * ld + kb + j], vj, f[kb + lane]);
         __syncwarp();
       }
     }
     __syncthreads();
     for (int r = kb + nb + tid; r < nu; r += RF_THREADS) {
       const float* row = A + (int64_t)r * ld + kb;
-      double s = v[r];
-      for (int j = 0; j < nb; ++j) s = fma(-(double)row[j], v[kb + j], s);
-      v[r] = s;
+      float s = f[r];
+      for (int j = 0; j < nb; ++j) s = fmaf(-row[j], f[kb + j], s);
+      f[r] = s;
     }
     __syncthreads();
   }
@@ -294,24 +307,26 @@ __device__ void solve32(const Dims& dm, const float* __restrict__ A, const int* 
     for (int rr = warp; rr < nb; rr += nw) {
       const int r = kb + rr;
       const float* row = A + (int64_t)r * ld;
-      double s = 0.0;
-      for (int c = kb + nb + lane; c < nu; c += 32) s = fma((double)row[c], v[c], s);
+      float s = 0.f;
+      for (int c = kb + nb + lane; c < nu; c += 32) s = fmaf(row[c], f[c], s);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) v[r] -= s;
+      if (lane == 0) f[r] -= s;
     }
     __syncthreads();
     if (warp == 0) {
       for (int j = nb - 1; j >= 0; --j) {
-        if (lane == 0) v[kb + j] /= (double)A[(int64_t)(kb + j) * ld + kb + j];
+        if (lane == 0) f[kb + j] /= A[(int64_t)(kb + j) * ld + kb + j];
         __syncwarp();
-        double vj = v[kb + j];
-        if (lane < j) v[kb + lane] = fma(-(double)A[(int64_t)(kb + lane) * ld + kb + j], vj, v[kb + lane]);
+        float vj = f[kb + j];
+        if (lane < j) f[kb + lane] = fmaf(-A[(int64_t)(kb + lane) * ld + kb + j], vj, f[kb + lane]);
         __syncwarp();
       }
     }
     __syncthreads();
   }
+  for (int i = tid; i < nu; i += RF_THREADS) v[i] = sc * (double)f[i];
+  __syncthreads();
 }
 
 // Solve A~ x = b (b in w.b) to FP64 accuracy; on return w.x = x and w.ou, w.ot hold
@@ -322,12 +337,12 @@ __device__ double refine_solve(const Dims& dm, const Phys& ph, const RefTables& 
   double bn = 0.0;
   for (int i = tid; i < nu; i += RF_THREADS) { w.v[i] = w.b[i]; bn = fmax(bn, fabs(w.b[i])); }
   bn = block_max(bn, w.red);
-  solve32(dm, A, piv, w.v);
+  solve32(dm, A, piv, w.v, reinterpret_cast<float*>(w.ou), w.red);
   for (int i = tid; i < nu; i += RF_THREADS) w.x[i] = w.v[i];
   __syncthreads();
   double rel = 0.0;
   for (int it = 0; it <= kRefineMaxIter; ++it) {
-    element_apply(dm, ph, ref, G, PJ, e, w);
+    element_apply(dm, ph, ref, G, PJ, e, w, true, false);
     double rn = 0.0;
     for (int i = tid; i < nu; i += RF_THREADS) {
       double r = w.b[i] - w.ou[i];
@@ -337,7 +352,7 @@ __device__ double refine_solve(const Dims& dm, const Phys& ph, const RefTables& 
     rn = block_max(rn, w.red);
     rel = bn > 0.0 ? rn / bn : rn;
     if (!(rel > kRefineTol) || it == kRefineMaxIter) break;   // also stops on NaN
-    solve32(dm, A, piv, w.v);
+    solve32(dm, A, piv, w.v, reinterpret_cast<float*>(w.ou), w.red);
     for (int i = tid; i < nu; i += RF_THREADS) w.x[i] += w.v[i];
     __syncthreads();
   }
@@ -383,7 +398,7 @@ k_backsub_mixed(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ, const int64
     w.z[i] = duhat[etrace[e * Nb + t] * m + k];
   }
   __syncthreads();
-  element_apply(dm, ph, ref, G, PJ, e, w);               // ou = B~ dU_e
+  element_apply(dm, ph, ref, G, PJ, e, w, false, true);  // ou = B~ dU_e
   const double* rhs = rhs64 + e * dm.n;
   for (int i = tid; i < dm.nu; i += RF_THREADS) w.b[i] = rhs[i] - w.ou[i];
   for (int i = tid; i < dm.nt; i += RF_THREADS) w.z[i] = 0.0;   // solve with z = 0

@@ -18,7 +18,8 @@ ERRORS = {-1: "INVALID_ARG", -2: "CUDA", -3: "OOM", -4: "MESH", -5: "NOT_ASSEMBL
 EXPORTS = ("iedg_create_mesh", "iedg_destroy_mesh", "iedg_last_error", "iedg_mesh_info",
            "iedg_trace_pattern", "iedg_eval_residual", "iedg_assemble_condensed",
            "iedg_back_substitute", "iedg_element_status", "iedg_profile_enable",
-           "iedg_profile_read", "iedg_profile_reset", "iedg_eval_residual_static")
+           "iedg_profile_read", "iedg_profile_reset", "iedg_eval_residual_static", "iedg_get_schedule",
+           "iedg_set_schedule", "iedg_trace_solve")
 
 
 class IedgError(RuntimeError):
@@ -34,6 +35,11 @@ class MeshDesc(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("Pr", ctypes.c_double), ("Re", ctypes.c_double),
                 ("Minf", ctypes.c_double), ("alpha", ctypes.c_double), ("stab", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
+
+
+class Schedule(ctypes.Structure):
+    _fields_ = [("lu_persistent", ctypes.c_int32), ("lu_panel", ctypes.c_int32), ("asm_chunk", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 _lib = None
@@ -70,6 +76,13 @@ def load():
     lib.iedg_element_status.restype = ctypes.c_int64
     lib.iedg_eval_residual_static.argtypes = [vp] * 8
     lib.iedg_eval_residual_static.restype = ctypes.c_int
+    lib.iedg_trace_solve.argtypes = [vp, vp, vp, vp, i32, i32, ctypes.c_double, ctypes.POINTER(i32),
+                                     ctypes.POINTER(ctypes.c_double), vp]
+    lib.iedg_trace_solve.restype = ctypes.c_int
+    lib.iedg_get_schedule.argtypes = [vp, ctypes.POINTER(Schedule)]
+    lib.iedg_get_schedule.restype = ctypes.c_int
+    lib.iedg_set_schedule.argtypes = [vp, ctypes.POINTER(Schedule)]
+    lib.iedg_set_schedule.restype = ctypes.c_int
     lib.iedg_profile_enable.argtypes = [vp, i32]
     lib.iedg_profile_enable.restype = ctypes.c_int
     lib.iedg_profile_read.argtypes = [vp, i32, vp, vp, vp, ctypes.POINTER(i32)]
@@ -208,6 +221,30 @@ class Mesh:
             self._check(int(rc))
         return out
 
+
+    def trace_solve(self, K, R, dU=None, restart=30, max_iter=400, rtol=1e-10, stream=None):
+        """GMRES / block-Jacobi solve of K dU = R; returns (dU, iterations, rel_residual)."""
+        torch = _torch()
+        m, T = self.m, self.T
+        f64 = torch.float64
+        dU = self._empty(T, m) if dU is None else dU
+        it, rr = ctypes.c_int32(), ctypes.c_double()
+        self._check(load().iedg_trace_solve(
+            self._h, _ptr(K, (self.nnzb, m, m), f64, "K"), _ptr(R, (T, m), f64, "R"), _ptr(dU, (T, m), f64, "dU"),
+            restart, max_iter, rtol, ctypes.byref(it), ctypes.byref(rr), _stream(stream)))
+        return dU, it.value, rr.value
+
+    # ------------------------------------------------------------------ schedule
+    def get_schedule(self):
+        sc = Schedule()
+        self._check(load().iedg_get_schedule(self._h, ctypes.byref(sc)))
+        return {"lu_persistent": sc.lu_persistent, "lu_panel": sc.lu_panel, "asm_chunk": sc.asm_chunk}
+
+    def set_schedule(self, **kw):
+        cur = self.get_schedule()
+        cur.update(kw)
+        sc = Schedule(cur["lu_persistent"], cur["lu_panel"], cur["asm_chunk"])
+        self._check(load().iedg_set_schedule(self._h, ctypes.byref(sc)))
 
     # ------------------------------------------------------------------ tracing
     def profile_enable(self, enable=True):

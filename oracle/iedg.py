@@ -31,15 +31,18 @@ from . import physics
 
 
 class Problem:
-    def __init__(self, ref, geo, elem_trace, n_trace, prm, source=None):
+    def __init__(self, ref, geo, elem_trace, n_trace, prm, source=None, fmu=None):
         """ref: RefElement, geo: Geometry, elem_trace [E, Nb] global trace ids,
-        prm: physics.Params, source: optional callable x[..., d] -> s[..., m]."""
+        prm: physics.Params, source: optional callable x[..., d] -> s[..., m],
+        fmu: trace basis at the face points [nf, Nfq, Nb] shared by the elements
+        (default: the element basis restricted to the faces, mu_s = phi_bnodes[s])."""
         self.ref, self.geo, self.prm = ref, geo, prm
         self.d = ref.d
         self.m = ref.d + 2
         self.elem_trace = np.asarray(elem_trace, dtype=np.int64)
         self.n_trace = int(n_trace)
-        self.fmu = ref.fphi[:, :, ref.bnodes]               # [nf, Nfq, Nb]
+        self.fmu = ref.fphi[:, :, ref.bnodes] if fmu is None else np.asarray(fmu)   # [nf, Nfq, Nb]
+        self.Nb = self.fmu.shape[2]
         self.source = source
 
     # ------------------------------------------------------------------ points
@@ -109,7 +112,7 @@ class Problem:
         """Dense Newton blocks of element e in the ordering of the module docstring.
         Returns dict with A_qq, A_qu, B_q, A_uq, A_uu, B_u, C_q, C_u, D, F_q, F_u, G."""
         ref, geo, prm, d, m = self.ref, self.geo, self.prm, self.d, self.m
-        Np, Nb = ref.Np, ref.Nb
+        Np, Nb = ref.Np, self.Nb
         els = np.array([e])
         P = self.points(els, u, q, uhat)
         _, Fu, Fq = physics.flux_with_jacobians(P["u"][0], P["q"][0], prm, d)
@@ -153,7 +156,7 @@ class Problem:
         return A, B, C, blk["D"], F, blk["G"]
 
     def _to_node_major(self, Kc, Rc):
-        m, Nb = self.m, self.ref.Nb
+        m, Nb = self.m, self.Nb
         K = Kc.reshape(m, Nb, m, Nb).transpose(1, 0, 3, 2)   # [s, i, t, k]
         R = Rc.reshape(m, Nb).T                               # [s, i]
         return K, R
@@ -175,7 +178,7 @@ class Problem:
         """Exact elimination of q (A_qq = M (x) I): dq_kl = M^-1 F_q,kl - G_l du_k + H_l dU_k
         with G_l = M^-1 B_l, H_l = M^-1 E_l.  Returns At, Bt, Ct, Dt, Ft, Gt."""
         m, d = self.m, self.d
-        Np, Nb = self.ref.Np, self.ref.Nb
+        Np, Nb = self.ref.Np, self.Nb
         M = blk["M"]
         Gl = np.stack([np.linalg.solve(M, blk["Bj"][j]) for j in range(d)])    # [d, Np, Np]
         Hl = np.stack([np.linalg.solve(M, blk["Ej"][j]) for j in range(d)])    # [d, Np, Nb]
@@ -266,4 +269,119 @@ def assemble(elem_trace, n_trace, K_e, R_e, els=None):
             R[tr[s]] += R_e[n][s]
             for t in range(len(tr)):
                 vals[bsr_find(row_ptr, col, tr[s], tr[t])] += K_e[n][s, :, t, :]
+    return row_ptr, col, vals, R
+
+
+# ------------------------------------------------------------------ mixed orders
+def face_trace_basis(ref, face_degree):
+    """Trace basis of one element at its face points, [nf, Nfq, Nb_e], for the
+    mixed-order reading: on a face shared with an element of the same order
+    (face_degree 0) the trace is the continuous one, mu_s = phi_a restricted to the
+    face for the element's boundary nodes a on such faces; a face shared with an
+    element of another order q carries (q+1)^(d-1) private nodes at the Gauss-Lobatto
+    points of degree q in the face's tangential coordinates (first fastest), with
+    the degree-q Lagrange basis, and every other slot vanishes on it.  Slots: the
+    boundary nodes on same-order faces (lexicographic), then each private face in
+    face order."""
+    from . import refelem as re
+    d, nf = ref.d, 2 * ref.d
+    edg = [f for f in range(nf) if face_degree[f] == 0]
+    nodes = [a for a, ai in enumerate(ref.node_idx)
+             if any(ai[f // 2] == (ref.p if f % 2 else 0) for f in edg)]
+    cols = []
+    for a in nodes:
+        c = np.zeros((nf, ref.Nfq))
+        for f in edg:
+            c[f] = ref.fphi[f][:, a]
+        cols.append(c)
+    for f in range(nf):
+        q = int(face_degree[f])
+        if q == 0:
+            continue
+        r = f // 2
+        others = [s for s in range(d) if s != r]
+        gl, _ = re.gauss_lobatto(q)
+        Ls = [re.lagrange(gl, ref.fxq[f][:, s])[0] for s in others]     # [Nfq, q+1] each
+        idx = [tuple(reversed(t)) for t in np.ndindex(*([q + 1] * (d - 1)))]
+        for j in idx:
+            c = np.zeros((nf, ref.Nfq))
+            v = np.ones(ref.Nfq)
+            for t in range(d - 1):
+                v = v * Ls[t][:, j[t]]
+            c[f] = v
+            cols.append(c)
+    return np.stack(cols, axis=-1)
+
+
+class MixedProblem:
+    """Elements of different orders sharing one trace space (see face_trace_basis);
+    each element is an independent single-element Problem with its own reference
+    element, geometry and trace basis."""
+
+    def __init__(self, refs, mesh, prm, source=None):
+        """refs: {p: RefElement}; mesh: workloads.MixedMesh; prm: physics.Params."""
+        from .geometry import Geometry
+        self.mesh, self.prm = mesh, prm
+        self.m = mesh.d + 2
+        self.n_trace = mesh.n_trace
+        self.pbs = []
+        for e in range(mesh.n_elem):
+            ref = refs[int(mesh.orders[e])]
+            geo = Geometry(ref, mesh.node_xyz[e][None])
+            fmu = face_trace_basis(ref, mesh.face_degree[e])
+            self.pbs.append(Problem(ref, geo, mesh.elem_trace[e][None], mesh.n_trace, prm, source, fmu))
+
+    def residual(self, u, q, uhat, u_ref=None):
+        """Per-element lists R_q, R_u, Rhat_e and the assembled R_fl."""
+        Rq, Ru, Rh = [], [], []
+        Rfl = np.zeros((self.n_trace, self.m))
+        for e, pb in enumerate(self.pbs):
+            ur = None if u_ref is None else u_ref[e][None]
+            a, b, c, f = pb.residual(u[e][None], q[e][None], uhat, ur)
+            Rq.append(a[0]); Ru.append(b[0]); Rh.append(c[0])
+            Rfl += f
+        return Rq, Ru, Rh, Rfl
+
+    def solve_q(self, u, uhat):
+        return [pb.solve_q(u[e][None], uhat)[0] for e, pb in enumerate(self.pbs)]
+
+    def condense_qelim(self, e, u, q, uhat, u_ref=None):
+        ur = None if u_ref is None else u_ref[e][None]
+        return self.pbs[e].condense_qelim(0, u[e][None], q[e][None], uhat, ur)
+
+    def condense_full(self, e, u, q, uhat, u_ref=None):
+        ur = None if u_ref is None else u_ref[e][None]
+        return self.pbs[e].condense_full(0, u[e][None], q[e][None], uhat, ur)
+
+    def back_substitute_qelim(self, e, u, q, uhat, duhat, u_ref=None):
+        ur = None if u_ref is None else u_ref[e][None]
+        return self.pbs[e].back_substitute_qelim(0, u[e][None], q[e][None], uhat, duhat, ur)
+
+    def element_blocks(self, e, u, q, uhat, u_ref=None):
+        ur = None if u_ref is None else u_ref[e][None]
+        return self.pbs[e].element_blocks(0, u[e][None], q[e][None], uhat, ur)
+
+
+def assemble_ragged(elem_trace, n_trace, K_e, R_e):
+    """K = sum_e P_e^T K_e P_e, R = sum_e P_e^T R_e for elements with different slot
+    counts (lists), summed in element order; returns row_ptr, col, values, R."""
+    pairs = set()
+    for tr in elem_trace:
+        for a in tr.tolist():
+            for b in tr.tolist():
+                pairs.add((a, b))
+    keys = np.array(sorted(r * n_trace + c for r, c in pairs), dtype=np.int64)
+    r_, c_ = keys // n_trace, keys % n_trace
+    row_ptr = np.zeros(n_trace + 1, dtype=np.int64)
+    np.add.at(row_ptr, r_ + 1, 1)
+    row_ptr = np.cumsum(row_ptr)
+    col = c_.astype(np.int64)
+    m = R_e[0].shape[1]
+    vals = np.zeros((len(col), m, m))
+    R = np.zeros((n_trace, m))
+    for e, tr in enumerate(elem_trace):
+        for s in range(len(tr)):
+            R[tr[s]] += R_e[e][s]
+            for t in range(len(tr)):
+                vals[bsr_find(row_ptr, col, tr[s], tr[t])] += K_e[e][s, :, t, :]
     return row_ptr, col, vals, R

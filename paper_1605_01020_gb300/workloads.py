@@ -282,3 +282,138 @@ def config(index, seed=None, N=None):
         prm = dict(gamma=GAMMA, Pr=0.72, Re=2.5e5, Minf=0.3, alpha=alpha)
         return Workload(f"3D NS p=4 {n}^3 periodic hexes", mesh, st, prm)
     raise ValueError(f"no synthetic workload {index}")
+
+
+# ------------------------------------------------------------------ mixed orders
+@dataclass
+class MixedMesh:
+    """Structured periodic mesh whose elements have different polynomial orders.
+
+    face_degree[e][f] = 0 for a face shared with an element of the same order (the
+    trace there is the continuous one of the uniform case), else the degree of the
+    face's private trace nodes, max(p_e, p_neighbour).  An element's trace slots are
+    its boundary nodes that lie on at least one same-order face (lexicographic), then
+    the private nodes of each other face in face order (-x, +x, -y, +y, -z, +z),
+    (q+1)^(d-1) of them, first tangential direction fastest."""
+    d: int
+    N: tuple
+    orders: np.ndarray          # [E]
+    node_xyz: list              # per element [Np_e, d]
+    elem_trace: list            # per element [Nb_e] int64
+    face_degree: np.ndarray     # [E, 2d]
+    n_trace: int
+    extent: tuple = field(default=None)
+
+    @property
+    def n_elem(self):
+        return len(self.orders)
+
+
+def structured_mesh_mixed(d, N, orders, extent=None):
+    N = tuple(int(n) for n in (N if np.ndim(N) else [N] * d))
+    extent = tuple(extent) if extent is not None else (1.0,) * d
+    orders = np.asarray(orders, dtype=np.int64)
+    cells = [c for c in _multi(max(N), d) if all(c[r] < N[r] for r in range(d))]
+    cells.sort(key=lambda c: tuple(reversed(c)))
+    index = {c: i for i, c in enumerate(cells)}
+    E = len(cells)
+    assert len(orders) == E
+    nf = 2 * d
+    face_degree = np.zeros((E, nf), dtype=np.int64)
+    for e, c in enumerate(cells):
+        for f in range(nf):
+            r, side = divmod(f, 2)
+            nb = list(c)
+            nb[r] = (nb[r] + (1 if side else -1)) % N[r]
+            pe, pn = orders[e], orders[index[tuple(nb)]]
+            face_degree[e, f] = 0 if pe == pn else max(pe, pn)
+    node_xyz, keys = [], []
+    for e, c in enumerate(cells):
+        p = int(orders[e])
+        xi = gll_positions(p)
+        nodes = _multi(p + 1, d)
+        X = np.array([[(c[r] + 0.5 * (1.0 + xi[ai[r]])) * extent[r] / N[r] for r in range(d)] for ai in nodes])
+        node_xyz.append(X)
+        ek = []
+        edg_faces = [f for f in range(nf) if face_degree[e, f] == 0]
+        for a, ai in enumerate(nodes):
+            on_edg = any(ai[f // 2] == (p if f % 2 else 0) for f in edg_faces)
+            if on_edg:
+                pos = tuple((c[r] * p + ai[r]) % (N[r] * p) for r in range(d))
+                ek.append(("E", p, tuple(reversed(pos))))
+        for f in range(nf):
+            q = int(face_degree[e, f])
+            if q == 0:
+                continue
+            r, side = divmod(f, 2)
+            # the face is owned by the cell on its -r side; key = (that cell, r)
+            owner = list(c)
+            if not side:
+                owner[r] = (owner[r] - 1) % N[r]
+            okey = index[tuple(owner)]
+            for j in range((q + 1) ** (d - 1)):
+                ek.append(("H", okey, r, j))
+        keys.append(ek)
+    allkeys = sorted({k for ek in keys for k in ek}, key=lambda k: (k[0] != "E", k[1:]))
+    gid = {k: i for i, k in enumerate(allkeys)}
+    elem_trace = [np.array([gid[k] for k in ek], dtype=np.int64) for ek in keys]
+    return MixedMesh(d, N, orders, node_xyz, elem_trace, face_degree, len(allkeys), extent)
+
+
+def make_state_mixed(mesh, field, seed, noise=0.0):
+    """State on a MixedMesh (per-element lists): u, q as in make_state, uhat = mean
+    over the element slots sharing each trace node of u at the slot's position
+    (private face nodes: the field evaluated at the node's position on the face)."""
+    rng = np.random.default_rng(seed)
+    m = mesh.d + 2
+    us, qs = [], []
+    acc = np.zeros((mesh.n_trace, m))
+    cnt = np.zeros(mesh.n_trace)
+    for e in range(mesh.n_elem):
+        X = mesh.node_xyz[e]
+        u = field(X)
+        if noise:
+            sigma = np.ones(m)
+            sigma[-1] = np.abs(u[..., -1]).mean()
+            u = u + noise * sigma * rng.uniform(-1.0, 1.0, u.shape)
+        us.append(u)
+        qs.append(fd_gradient(field, X))
+        pos = _slot_positions(mesh, e)
+        val = field(pos)
+        np.add.at(acc, mesh.elem_trace[e], val)
+        np.add.at(cnt, mesh.elem_trace[e], 1.0)
+    uhat = acc / cnt[:, None]
+    duhat = 1e-3 * rng.uniform(-1.0, 1.0, (mesh.n_trace, m))
+    return State(us, qs, uhat, None, duhat)
+
+
+def _slot_positions(mesh, e):
+    """Physical positions of element e's trace slots (axis-aligned cells only)."""
+    d, p = mesh.d, int(mesh.orders[e])
+    X = mesh.node_xyz[e]
+    lo, hi = X.min(0), X.max(0)
+    nodes = _multi(p + 1, d)
+    edg_faces = [f for f in range(2 * d) if mesh.face_degree[e, f] == 0]
+    out = []
+    for a, ai in enumerate(nodes):
+        if any(ai[f // 2] == (p if f % 2 else 0) for f in edg_faces):
+            out.append(X[a])
+    for f in range(2 * d):
+        q = int(mesh.face_degree[e, f])
+        if q == 0:
+            continue
+        r, side = divmod(f, 2)
+        others = [s for s in range(d) if s != r]
+        xi = gll_positions(q)
+        for idx in _multi(q + 1, d - 1):
+            x = np.zeros(d)
+            x[r] = hi[r] if side else lo[r]
+            for t, s in enumerate(others):
+                x[s] = lo[s] + 0.5 * (1 + xi[idx[t]]) * (hi[s] - lo[s])
+            out.append(x)
+    return np.array(out)
+
+
+def mixed_orders(shape, seed, levels=(2, 3, 4), probs=(0.3, 0.5, 0.2)):
+    rng = np.random.default_rng(seed)
+    return rng.choice(np.array(levels), size=int(np.prod(shape)), p=np.array(probs))

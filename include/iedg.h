@@ -93,11 +93,40 @@ typedef struct {
  * all workspace.  Synchronises `stream` before returning.  IEDG_ERR_MESH if any
  * quadrature point has detJ <= 0 or a trace id is out of range. */
 int iedg_create_mesh(const iedg_mesh_desc* desc, void* stream, iedg_mesh** out);
+
+/* Meshes with mixed polynomial orders (no counterpart in the paper, which uses one
+ * degree k per mesh; this is the trace sharing of Sec. 2.1 extended to elements of
+ * different degrees).  Element e has degree elem_order[e] (HOST int32 [n_elem],
+ * 1..4 in 3D, 1..3 in 2D; desc->order is ignored) and face_degree[e][f] (HOST int32
+ * [n_elem][2 dim], faces f = 2 r + side in the order -x, +x, -y, +y, -z, +z):
+ *   0      the face is shared with an element of the same degree and carries the
+ *          continuous (EDG) trace of the uniform case;
+ *   q > 0  the face carries (q+1)^(dim-1) private trace nodes, the Gauss-Lobatto
+ *          points of degree q in the face's tangential reference coordinates (first
+ *          tangential direction fastest) with the degree-q Lagrange basis; both
+ *          neighbours list the same nodes (q = max of the two degrees in the
+ *          workloads of this project).
+ * The slots of element e: its boundary nodes that lie on at least one face with
+ * face_degree 0 (lexicographic), then the private nodes of each other face in face
+ * order; nb_e of them.  Every element-indexed array is RAGGED, elements in user order
+ * with their own sizes, no padding: node_xyz [sum Np_e][dim], elem_trace [sum nb_e];
+ * in the compute calls u, u_ref, r_u, du are [sum Np_e][m] and q, q_out, r_q, dq
+ * [sum Np_e][m][dim].  K, R, uhat, duhat are as for uniform meshes.  The element
+ * sizes are returned by iedg_element_sizes.  iedg_eval_residual_static returns
+ * IEDG_ERR_UNSUPPORTED on such meshes; every other call works unchanged. */
+int iedg_create_mesh_mixed(const iedg_mesh_desc* desc, const int32_t* elem_order,
+                           const int32_t* face_degree, void* stream, iedg_mesh** out);
+
+/* Per-element node and trace-slot counts, HOST int32 [n_elem] each (either may be
+ * NULL); for uniform meshes every entry is Np, Nb. */
+int iedg_element_sizes(const iedg_mesh* mesh, int32_t* Np, int32_t* Nb);
+
 int iedg_destroy_mesh(iedg_mesh* mesh);
 const char* iedg_last_error(const iedg_mesh* mesh);
 
 /* Sizes: Np, Nb, number of trace-matrix blocks nnzb (m x m each), bytes of device
- * workspace held by the handle.  Any output pointer may be NULL. */
+ * workspace held by the handle.  Any output pointer may be NULL.  Meshes with mixed
+ * orders report the largest Np and nb_e. */
 int iedg_mesh_info(const iedg_mesh* mesh, int32_t* Np, int32_t* Nb, int64_t* nnzb,
                    int64_t* workspace_bytes);
 
@@ -169,12 +198,16 @@ int iedg_trace_solve(iedg_mesh* mesh, const double* K, const double* R, double* 
  *                  does not fit in shared memory).
  *   asm_chunk:     assembly column chunk, 8, 16 or 32 (0 = default: 8 for FP64, 16
  *                  for FP32; too large a chunk for shared memory falls back).
+ *   lu_tensor:     mixed path: 1 = trailing updates of the FP32 LU on the tensor
+ *                  cores (tcgen05, TF32 operands split in high and low parts, three
+ *                  products, FP32 accumulation in tensor memory); 0 = FFMA.
  * iedg_set_schedule rejects other values with IEDG_ERR_INVALID_ARG. */
 typedef struct {
   int32_t lu_persistent;
   int32_t lu_panel;
   int32_t asm_chunk;
-  int32_t reserved[5];
+  int32_t lu_tensor;
+  int32_t reserved[4];
 } iedg_schedule;
 int iedg_get_schedule(const iedg_mesh* mesh, iedg_schedule* out);
 int iedg_set_schedule(iedg_mesh* mesh, const iedg_schedule* in);

@@ -19,11 +19,13 @@ def mesh_key(mesh, precision, gpu_name):
 
 
 def candidates(precision, order):
-    """Candidate schedules: persistent LU on/off x FP64 panel 16/32 x assembly chunk."""
+    """Candidate schedules: persistent LU on/off x FP64 panel 16/32 x assembly chunk
+    (x tensor-core or FFMA trailing updates of the FP32 LU on the mixed path)."""
     panels = [16, 32] if (precision == 0 and order <= 3) else [16]
     chunks = [8, 16] if precision == 0 else [16, 32]
-    return [dict(lu_persistent=a, lu_panel=b, asm_chunk=c)
-            for a, b, c in itertools.product([1, 0], panels, chunks)]
+    tensor = [1] if precision == 0 else [1, 0]
+    return [dict(lu_persistent=a, lu_panel=b, asm_chunk=c, lu_tensor=t)
+            for a, b, c, t in itertools.product([1, 0], panels, chunks, tensor)]
 
 
 def time_assemble(mesh, u, q, uh, K, R, reps):

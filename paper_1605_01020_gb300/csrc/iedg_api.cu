@@ -85,7 +85,8 @@ void lagrange_eval(const std::vector<double>& nodes, double x, double* L, double
 }
 
 struct HostRef {
-  std::vector<double> Phi, Dxi, Wq, PhiF, DxiF, Wf, L1, dL1;
+  std::vector<double> Phi, Dxi, Wq, PhiF, DxiF, Wf, L1, dL1, LQ;
+  std::vector<double> xq;   // 1D Gauss points
   std::vector<int> bnode, slot, fnode;
 };
 
@@ -99,6 +100,17 @@ HostRef build_reference(const Dims& dm) {
   for (int g = 0; g < nq1; ++g) lagrange_eval(xn, xq[g], &L[g * np1], &dL[g * np1]);
   R.L1 = L;
   R.dL1 = dL;
+  R.xq = xq;
+  // degree-q Gauss-Lobatto Lagrange basis at the 1D Gauss points, q = 1..4, [5][nq1][5]
+  R.LQ.assign((size_t)25 * nq1, 0.0);
+  for (int q = 1; q <= 4; ++q) {
+    std::vector<double> xl, Lq(q + 1), dLq(q + 1);
+    lobatto_nodes(q, xl);
+    for (int g = 0; g < nq1; ++g) {
+      lagrange_eval(xl, xq[g], Lq.data(), dLq.data());
+      for (int j = 0; j <= q; ++j) R.LQ[((size_t)q * nq1 + g) * 5 + j] = Lq[j];
+    }
+  }
   auto idx = [&](int a, int r, int n1) { for (int t = 0; t < r; ++t) a /= n1; return a % n1; };
   R.Phi.assign((size_t)dm.Nq * dm.Np, 1.0);
   R.Dxi.assign((size_t)d * dm.Nq * dm.Np, 1.0);
@@ -254,28 +266,32 @@ extern "C" const char* iedg_last_error(const iedg_mesh* mesh) {
   return mesh ? mesh->err.c_str() : g_err.c_str();
 }
 
-static int create_impl(const iedg_mesh_desc* D, cudaStream_t st, iedg_mesh* M) {
-  const Dims& dm = M->dm;
-  const int64_t E = M->E, T = M->T;
-  // element -> trace map checks
-  const int64_t* et = D->elem_trace;
-  for (int64_t i = 0; i < E * dm.Nb; ++i)
-    if (et[i] < 0 || et[i] >= T) return fail(M, IEDG_ERR_MESH, "elem_trace entry out of range");
-  // trace pattern: node -> elements, then union of element trace sets per node
+// Trace-matrix pattern and gather lists from per-element slot lists (element e: n_e
+// trace ids at lists[e], internal id ids[e]); contributions are recorded in list
+// order, so every sum runs in that element order.  Packed entries: (id P + s) for
+// trace rows, (id P + s) P + t for K blocks.
+static int setup_pattern(iedg_mesh* M, const std::vector<const int64_t*>& lists, const std::vector<int>& lens,
+                         const std::vector<int64_t>& ids, int64_t P, cudaStream_t st) {
+  const int64_t E = (int64_t)lists.size(), T = M->T;
+  for (int64_t e = 0; e < E; ++e)
+    for (int s = 0; s < lens[e]; ++s)
+      if (lists[e][s] < 0 || lists[e][s] >= T) return fail(M, IEDG_ERR_MESH, "elem_trace entry out of range");
+  // trace node -> contributions
   std::vector<int64_t> ne_ptr(T + 1, 0);
-  for (int64_t i = 0; i < E * dm.Nb; ++i) ne_ptr[et[i] + 1]++;
+  for (int64_t e = 0; e < E; ++e)
+    for (int s = 0; s < lens[e]; ++s) ne_ptr[lists[e][s] + 1]++;
   for (int64_t t = 0; t < T; ++t) ne_ptr[t + 1] += ne_ptr[t];
-  {
-    std::vector<char> seen(T, 0);
-    for (int64_t t = 0; t < T; ++t)
-      if (ne_ptr[t + 1] == ne_ptr[t]) return fail(M, IEDG_ERR_MESH, "trace node used by no element");
-    (void)seen;
-  }
-  std::vector<int64_t> rc_src(E * dm.Nb);
+  for (int64_t t = 0; t < T; ++t)
+    if (ne_ptr[t + 1] == ne_ptr[t]) return fail(M, IEDG_ERR_MESH, "trace node used by no element");
+  std::vector<int64_t> rc_src(ne_ptr[T]), rc_el(ne_ptr[T]);
   {
     std::vector<int64_t> fill(ne_ptr.begin(), ne_ptr.end() - 1);
-    for (int64_t e = 0; e < E; ++e)       // element order => deterministic sums
-      for (int s = 0; s < dm.Nb; ++s) rc_src[fill[et[e * dm.Nb + s]]++] = e * dm.Nb + s;
+    for (int64_t e = 0; e < E; ++e)
+      for (int s = 0; s < lens[e]; ++s) {
+        int64_t k = fill[lists[e][s]]++;
+        rc_src[k] = ids[e] * P + s;
+        rc_el[k] = e;
+      }
   }
   std::vector<int64_t> row_ptr(T + 1, 0);
   std::vector<int32_t> col;
@@ -285,9 +301,9 @@ static int create_impl(const iedg_mesh_desc* D, cudaStream_t st, iedg_mesh* M) {
     for (int64_t r = 0; r < T; ++r) {
       buf.clear();
       for (int64_t k = ne_ptr[r]; k < ne_ptr[r + 1]; ++k) {
-        int64_t e = rc_src[k] / dm.Nb;
-        for (int s = 0; s < dm.Nb; ++s) {
-          int64_t c = et[e * dm.Nb + s];
+        int64_t e = rc_el[k];
+        for (int s = 0; s < lens[e]; ++s) {
+          int64_t c = lists[e][s];
           if (mark[c] != r) { mark[c] = r; buf.push_back((int32_t)c); }
         }
       }
@@ -296,31 +312,54 @@ static int create_impl(const iedg_mesh_desc* D, cudaStream_t st, iedg_mesh* M) {
       row_ptr[r + 1] = (int64_t)col.size();
     }
   }
+  std::vector<int64_t>().swap(rc_el);
   M->nnzb = (int64_t)col.size();
   // K gather lists, stable in element order
+  int64_t nk = 0;
+  for (int64_t e = 0; e < E; ++e) nk += (int64_t)lens[e] * lens[e];
   std::vector<int64_t> kc_ptr(M->nnzb + 1, 0);
-  std::vector<int64_t> kc_blk((size_t)E * dm.Nb * dm.Nb);
-  for (int64_t e = 0; e < E; ++e)
-    for (int s = 0; s < dm.Nb; ++s) {
-      int64_t r = et[e * dm.Nb + s];
-      const int32_t* cb = col.data() + row_ptr[r];
-      int64_t len = row_ptr[r + 1] - row_ptr[r];
-      for (int t = 0; t < dm.Nb; ++t) {
-        int32_t c = (int32_t)et[e * dm.Nb + t];
-        int64_t k = row_ptr[r] + (std::lower_bound(cb, cb + len, c) - cb);
-        kc_blk[(e * dm.Nb + s) * dm.Nb + t] = k;
-        kc_ptr[k + 1]++;
+  std::vector<int64_t> kc_blk(nk), kc_val(nk);
+  {
+    int64_t i = 0;
+    for (int64_t e = 0; e < E; ++e)
+      for (int s = 0; s < lens[e]; ++s) {
+        int64_t r = lists[e][s];
+        const int32_t* cb = col.data() + row_ptr[r];
+        int64_t len = row_ptr[r + 1] - row_ptr[r];
+        for (int t = 0; t < lens[e]; ++t, ++i) {
+          int32_t c = (int32_t)lists[e][t];
+          int64_t k = row_ptr[r] + (std::lower_bound(cb, cb + len, c) - cb);
+          kc_blk[i] = k;
+          kc_val[i] = (ids[e] * P + s) * P + t;
+          kc_ptr[k + 1]++;
+        }
       }
-    }
+  }
   for (int64_t k = 0; k < M->nnzb; ++k) kc_ptr[k + 1] += kc_ptr[k];
-  std::vector<int64_t> kc_src(kc_blk.size());
+  std::vector<int64_t> kc_src(nk);
   {
     std::vector<int64_t> fill(kc_ptr.begin(), kc_ptr.end() - 1);
-    for (int64_t i = 0; i < (int64_t)kc_blk.size(); ++i) kc_src[fill[kc_blk[i]]++] = i;
+    for (int64_t i = 0; i < nk; ++i) kc_src[fill[kc_blk[i]]++] = kc_val[i];
   }
   std::vector<int64_t>().swap(kc_blk);
-  std::vector<int64_t> etv(et, et + E * dm.Nb);
+  std::vector<int64_t>().swap(kc_val);
+  CUDA_TRY(upload(M, &M->row_ptr, row_ptr, st));
+  CUDA_TRY(upload(M, &M->col, col, st));
+  CUDA_TRY(upload(M, &M->kc_ptr, kc_ptr, st));
+  CUDA_TRY(upload(M, &M->kc_src, kc_src, st));
+  CUDA_TRY(upload(M, &M->rc_ptr, ne_ptr, st));
+  CUDA_TRY(upload(M, &M->rc_src, rc_src, st));
+  // the host vectors must outlive the copies
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return IEDG_OK;
+}
 
+// Element tables of one group of elements of equal order (the whole mesh when the
+// order is uniform): reference element, geometry, point tables, lifted gradients and,
+// on the mixed path, the FP64 right-hand sides and refined solutions.
+static int alloc_group(iedg_mesh* M, cudaStream_t st) {
+  const Dims& dm = M->dm;
+  const int64_t E = M->E;
   HostRef R = build_reference(dm);
   CUDA_TRY(upload(M, &M->ref.Phi, R.Phi, st));
   CUDA_TRY(upload(M, &M->ref.Dxi, R.Dxi, st));
@@ -333,14 +372,8 @@ static int create_impl(const iedg_mesh_desc* D, cudaStream_t st, iedg_mesh* M) {
   CUDA_TRY(upload(M, &M->ref.fnode, R.fnode, st));
   CUDA_TRY(upload(M, &M->ref.L1, R.L1, st));
   CUDA_TRY(upload(M, &M->ref.dL1, R.dL1, st));
-  CUDA_TRY(upload(M, &M->etrace, etv, st));
-  CUDA_TRY(upload(M, &M->row_ptr, row_ptr, st));
-  CUDA_TRY(upload(M, &M->col, col, st));
-  CUDA_TRY(upload(M, &M->kc_ptr, kc_ptr, st));
-  CUDA_TRY(upload(M, &M->kc_src, kc_src, st));
-  std::vector<int64_t> rc_ptr(ne_ptr);
-  CUDA_TRY(upload(M, &M->rc_ptr, rc_ptr, st));
-  CUDA_TRY(upload(M, &M->rc_src, rc_src, st));
+  CUDA_TRY(upload(M, &M->ref.LQ, R.LQ, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
 
   const size_t d = dm.d, Np = dm.Np, Nq = dm.Nq, Nb = dm.Nb, Nfp = dm.Nfp, m = dm.m;
   Geo& G = M->geo;
@@ -360,15 +393,9 @@ static int create_impl(const iedg_mesh_desc* D, cudaStream_t st, iedg_mesh* M) {
   CUDA_TRY(dalloc(M, &M->pj.lamw, E * Nfp));
   CUDA_TRY(dalloc(M, &M->qstar, E * Np * m * d));
   CUDA_TRY(dalloc(M, &M->rhoq, E * Np * m * d));
-  CUDA_TRY(dalloc(M, &M->rhat, E * Nb * m));
-  if (M->precision == IEDG_PRECISION_FP64) {
-    CUDA_TRY(dalloc(M, &M->S, (size_t)E * dm.n * dm.ld));
-  } else {
-    CUDA_TRY(dalloc(M, &M->S32, (size_t)E * dm.n * dm.ld));
-    CUDA_TRY(dalloc(M, &M->piv, (size_t)E * dm.nu));
+  if (M->precision == IEDG_PRECISION_MIXED) {
     CUDA_TRY(dalloc(M, &M->rhs64, (size_t)E * dm.n));
     CUDA_TRY(dalloc(M, &M->y64, (size_t)E * dm.nu));
-    CUDA_TRY(dalloc(M, &M->re64, (size_t)E * dm.nt));
     CUDA_TRY(dalloc(M, &M->pj.Jv32, E * m * m * (1 + d) * d * Nq));
     CUDA_TRY(dalloc(M, &M->pj.Jf32, E * m * m * (1 + d) * Nfp));
     CUDA_TRY(dalloc(M, &M->pj.lamw32, E * Nfp));
@@ -380,9 +407,28 @@ static int create_impl(const iedg_mesh_desc* D, cudaStream_t st, iedg_mesh* M) {
     CUDA_TRY(dalloc(M, &M->ref.Phi32, Nq * Np));
     CUDA_TRY(dalloc(M, &M->ref.Dxi32, d * Nq * Np));
     CUDA_TRY(dalloc(M, &M->ref.PhiF32, Nfp * Np));
+    CUDA_TRY(dalloc(M, &M->ref.LQ32, (size_t)25 * dm.nq1));
   }
-  CUDA_TRY(dalloc(M, &M->status, E));
   CUDA_TRY(dalloc(M, &M->dev_flag, 1));
+  CUDA_TRY(cudaMemsetAsync(M->dev_flag, 0, sizeof(int), st));
+  return IEDG_OK;
+}
+
+// Workspace of the handle that owns the element matrices and the trace space.
+static int alloc_owner(iedg_mesh* M, int64_t S_elems, int64_t piv_elems, int64_t rhat_elems, int64_t re_elems,
+                       cudaStream_t st) {
+  const int64_t E = M->E, T = M->T;
+  const int m = M->dm.m;
+  if (M->precision == IEDG_PRECISION_FP64) {
+    CUDA_TRY(dalloc(M, &M->S, (size_t)S_elems));
+  } else {
+    CUDA_TRY(dalloc(M, &M->S32, (size_t)S_elems));
+    CUDA_TRY(dalloc(M, &M->piv, (size_t)piv_elems));
+  }
+  CUDA_TRY(dalloc(M, &M->rhat, (size_t)rhat_elems));
+  CUDA_TRY(dalloc(M, &M->re64, (size_t)re_elems));
+  CUDA_TRY(dalloc(M, &M->status, E));
+  if (!M->dev_flag) CUDA_TRY(dalloc(M, &M->dev_flag, 1));
   CUDA_TRY(dalloc(M, &M->queue, 1));
   CUDA_TRY(dalloc(M, &M->kry, (size_t)(IEDG_MAX_RESTART + 3) * T * m));
   CUDA_TRY(dalloc(M, &M->dinv, (size_t)T * m * m));
@@ -390,24 +436,33 @@ static int create_impl(const iedg_mesh_desc* D, cudaStream_t st, iedg_mesh* M) {
   CUDA_TRY(dalloc(M, &M->khdev, (size_t)(IEDG_MAX_RESTART + 1)));
   CUDA_TRY(cudaMemsetAsync(M->dev_flag, 0, sizeof(int), st));
   CUDA_TRY(cudaMemsetAsync(M->status, 0, E, st));
+  return IEDG_OK;
+}
 
-  // geometry: node coordinates and a scratch for B_l, E_l, freed afterwards
+// Geometry of a group from its node coordinates (HOST [E][Np][d]) and the FP32 table
+// copies of the mixed path.
+static int run_geometry(iedg_mesh* M, const double* node_xyz, cudaStream_t st) {
+  const Dims& dm = M->dm;
+  const int64_t E = M->E;
+  const size_t d = dm.d, Np = dm.Np, Nq = dm.Nq, Nb = dm.Nb, Nfp = dm.Nfp;
+  Geo& G = M->geo;
   double* X = nullptr;
   double* scratch = nullptr;
   CUDA_TRY(cudaMalloc(&X, E * Np * d * sizeof(double)));
   cudaError_t e1 = cudaMalloc(&scratch, E * d * Np * (Np + Nb) * sizeof(double));
   if (e1 != cudaSuccess) { cudaFree(X); CUDA_TRY(e1); }
-  cudaError_t e2 = cudaMemcpyAsync(X, D->node_xyz, E * Np * d * sizeof(double), cudaMemcpyHostToDevice, st);
+  cudaError_t e2 = cudaMemcpyAsync(X, node_xyz, E * Np * d * sizeof(double), cudaMemcpyHostToDevice, st);
   if (e2 == cudaSuccess) e2 = launch_geometry(M, X, scratch, st);
   if (e2 == cudaSuccess && M->precision == IEDG_PRECISION_MIXED) {
     const std::pair<const double*, float*> cv[] = {
         {G.Mass, G.Mass32}, {G.GlV, G.GlV32}, {G.HlV, G.HlV32}, {G.GlF, G.GlF32}, {G.HlF, G.HlF32},
-        {M->ref.Phi, M->ref.Phi32}, {M->ref.Dxi, M->ref.Dxi32}, {M->ref.PhiF, M->ref.PhiF32}};
+        {M->ref.Phi, M->ref.Phi32}, {M->ref.Dxi, M->ref.Dxi32}, {M->ref.PhiF, M->ref.PhiF32},
+        {M->ref.LQ, M->ref.LQ32}};
     const int64_t E_ = E, Np_ = (int64_t)Np, Nq_ = (int64_t)Nq, Nb_ = (int64_t)Nb, Nfp_ = (int64_t)Nfp,
                   d_ = (int64_t)d;
     const int64_t cn[] = {E_ * Np_ * Np_, E_ * d_ * Nq_ * Np_, E_ * d_ * Nq_ * Nb_, E_ * d_ * Nfp_ * Np_,
-                          E_ * d_ * Nfp_ * Nb_, Nq_ * Np_, d_ * Nq_ * Np_, Nfp_ * Np_};
-    for (int i = 0; i < 8 && e2 == cudaSuccess; ++i) e2 = launch_to_f32(cv[i].first, cv[i].second, cn[i], st);
+                          E_ * d_ * Nfp_ * Nb_, Nq_ * Np_, d_ * Nq_ * Np_, Nfp_ * Np_, 25 * (int64_t)dm.nq1};
+    for (int i = 0; i < 9 && e2 == cudaSuccess; ++i) e2 = launch_to_f32(cv[i].first, cv[i].second, cn[i], st);
   }
   int flag = 0;
   if (e2 == cudaSuccess) e2 = cudaMemcpyAsync(&flag, M->dev_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -419,12 +474,31 @@ static int create_impl(const iedg_mesh_desc* D, cudaStream_t st, iedg_mesh* M) {
   return IEDG_OK;
 }
 
-extern "C" int iedg_create_mesh(const iedg_mesh_desc* D, void* stream, iedg_mesh** out) {
+static int create_impl(const iedg_mesh_desc* D, cudaStream_t st, iedg_mesh* M) {
+  const Dims& dm = M->dm;
+  const int64_t E = M->E;
+  const int64_t* et = D->elem_trace;
+  std::vector<const int64_t*> lists(E);
+  std::vector<int> lens(E, dm.Nb);
+  std::vector<int64_t> ids(E);
+  for (int64_t e = 0; e < E; ++e) { lists[e] = et + e * dm.Nb; ids[e] = e; }
+  M->nb_pack = dm.Nb;
+  int rc = setup_pattern(M, lists, lens, ids, dm.Nb, st);
+  if (rc != IEDG_OK) return rc;
+  std::vector<int64_t> etv(et, et + E * dm.Nb);
+  CUDA_TRY(upload(M, &M->etrace, etv, st));
+  rc = alloc_group(M, st);
+  if (rc != IEDG_OK) return rc;
+  rc = alloc_owner(M, E * (int64_t)dm.n * dm.ld, E * (int64_t)dm.nu, E * (int64_t)dm.Nb * dm.m,
+                   E * (int64_t)dm.nt, st);
+  if (rc != IEDG_OK) return rc;
+  return run_geometry(M, D->node_xyz, st);
+}
+
+static int check_desc(const iedg_mesh_desc* D, bool mixed) {
   iedg_mesh* M = nullptr;
-  if (!D || !out) return fail(M, IEDG_ERR_INVALID_ARG, "null descriptor or output");
-  *out = nullptr;
   if (!(D->dim == 2 || D->dim == 3)) return fail(M, IEDG_ERR_INVALID_ARG, "dim must be 2 or 3");
-  if (D->order < 1 || D->order > (D->dim == 3 ? 4 : 3))
+  if (!mixed && (D->order < 1 || D->order > (D->dim == 3 ? 4 : 3)))
     return fail(M, IEDG_ERR_UNSUPPORTED, "order must be 1..4 (3D) or 1..3 (2D)");
   if (D->quad_extra < 1 || D->quad_extra > 3)
     return fail(M, IEDG_ERR_UNSUPPORTED, "quad_extra must be 1..3");
@@ -436,30 +510,442 @@ extern "C" int iedg_create_mesh(const iedg_mesh_desc* D, void* stream, iedg_mesh
   if (!(D->gamma > 1.0) || !(D->Pr > 0) || !(D->Re > 0) || !(D->alpha >= 0))
     return fail(M, IEDG_ERR_INVALID_ARG, "physical parameters out of range");
   int ndev = 0;
-  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
-    return fail(M, IEDG_ERR_CUDA, "no CUDA device");
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(M, IEDG_ERR_CUDA, "no CUDA device");
+  return IEDG_OK;
+}
+
+static void destroy_impl(iedg_mesh* M) {
+  for (iedg_mesh* C : M->groups) destroy_impl(C);
+  M->groups.clear();
+  free_all(M);
+  delete M;
+}
+
+extern "C" int iedg_create_mesh(const iedg_mesh_desc* D, void* stream, iedg_mesh** out) {
+  iedg_mesh* M = nullptr;
+  if (!D || !out) return fail(M, IEDG_ERR_INVALID_ARG, "null descriptor or output");
+  *out = nullptr;
+  int rc = check_desc(D, false);
+  if (rc != IEDG_OK) return rc;
   M = new iedg_mesh();
   M->dm = make_dims(D->dim, D->order, D->quad_extra);
   M->ph = Phys{D->gamma, D->Pr, D->Re, D->alpha};
   M->precision = D->precision;
   M->E = D->n_elem;
   M->T = D->n_trace;
-  int rc = create_impl(D, (cudaStream_t)stream, M);
+  rc = create_impl(D, (cudaStream_t)stream, M);
   if (rc != IEDG_OK) {
     g_err = M->err;
-    free_all(M);
-    delete M;
+    destroy_impl(M);
     return rc;
   }
   *out = M;
   return IEDG_OK;
 }
 
+// ------------------------------------------------------------------------------
+// Meshes with mixed orders.  Internal element ids are grouped by order (ascending),
+// user order kept within a group; one child handle per order holds that order's
+// tables, the parent holds the trace space, the ragged element matrices (one buffer,
+// per-element offset and leading dimension) and the per-element sizes.
+// ------------------------------------------------------------------------------
+template <class T>
+static cudaError_t upload_to(iedg_mesh* M, const T** p, const std::vector<T>& h, cudaStream_t st) {
+  T* q = nullptr;
+  cudaError_t e = upload(M, &q, h, st);
+  *p = q;
+  return e;
+}
+
+static int create_mixed_impl(const iedg_mesh_desc* D, const int32_t* ord, const int32_t* fdeg, cudaStream_t st,
+                             iedg_mesh* M) {
+  const int d = D->dim, nf = 2 * d, m = d + 2;
+  const int64_t E = M->E;
+  const int pmax_allowed = d == 3 ? 4 : 3;
+  for (int64_t e = 0; e < E; ++e) {
+    if (ord[e] < 1 || ord[e] > pmax_allowed) return fail(M, IEDG_ERR_UNSUPPORTED, "element order out of range");
+    for (int f = 0; f < nf; ++f)
+      if (fdeg[e * nf + f] < 0 || fdeg[e * nf + f] > 4)
+        return fail(M, IEDG_ERR_UNSUPPORTED, "face degree must be 0 (continuous) or 1..4");
+  }
+  std::vector<Dims> dmp(5);
+  std::vector<HostRef> refs(5);
+  std::vector<int> present;
+  for (int p = 1; p <= 4; ++p)
+    for (int64_t e = 0; e < E; ++e)
+      if (ord[e] == p) { present.push_back(p); break; }
+  for (int p : present) { dmp[p] = make_dims(d, p, D->quad_extra); refs[p] = build_reference(dmp[p]); }
+  auto on_face = [&](int p, int a, int f) {
+    int r = f / 2, v = a;
+    for (int t = 0; t < r; ++t) v /= (p + 1);
+    return (v % (p + 1)) == ((f % 2) ? p : 0);
+  };
+  // slot structure of every element (user order)
+  std::vector<int> nbv(E);
+  std::vector<int64_t> unode(E + 1, 0), uslot(E + 1, 0);
+  for (int64_t e = 0; e < E; ++e) {
+    const int p = ord[e];
+    const Dims& dp = dmp[p];
+    int cnt = 0;
+    for (int a = 0; a < dp.Np; ++a) {
+      if (refs[p].slot[a] < 0) continue;
+      for (int f = 0; f < nf; ++f)
+        if (fdeg[e * nf + f] == 0 && on_face(p, a, f)) { ++cnt; break; }
+    }
+    for (int f = 0; f < nf; ++f) {
+      int q = fdeg[e * nf + f];
+      if (q > 0) cnt += (d == 3 ? (q + 1) * (q + 1) : q + 1);
+    }
+    nbv[e] = cnt;
+    unode[e + 1] = unode[e] + dp.Np;
+    uslot[e + 1] = uslot[e] + cnt;
+  }
+  // internal ids: grouped by order
+  M->perm.assign(E, 0);
+  M->gstart.clear();
+  std::vector<std::vector<int64_t>> gel;
+  {
+    int64_t next = 0;
+    for (int p : present) {
+      M->gstart.push_back(next);
+      gel.emplace_back();
+      for (int64_t e = 0; e < E; ++e)
+        if (ord[e] == p) { M->perm[e] = next++; gel.back().push_back(e); }
+    }
+  }
+  M->unode = unode;
+  M->n_nodes = unode[E];
+  int64_t P = 0;
+  for (int64_t e = 0; e < E; ++e) P = std::max<int64_t>(P, nbv[e]);
+  M->nb_pack = P;
+  // per-element sizes in internal order
+  std::vector<int> in_n(E), in_nu(E), in_ld(E), in_nb(E);
+  std::vector<int64_t> in_soff(E), in_poff(E);
+  for (int64_t e = 0; e < E; ++e) {
+    const int64_t i = M->perm[e];
+    const Dims& dp = dmp[ord[e]];
+    in_nb[i] = nbv[e];
+    in_nu[i] = dp.nu;
+    in_n[i] = dp.nu + m * nbv[e];
+    in_ld[i] = (in_n[i] + 1 + 3) & ~3;
+  }
+  int64_t S_total = 0, piv_total = 0;
+  for (int64_t i = 0; i < E; ++i) {
+    in_soff[i] = S_total;
+    in_poff[i] = piv_total;
+    S_total += (int64_t)in_n[i] * in_ld[i];
+    piv_total += in_nu[i];
+  }
+  std::vector<int64_t> order(E);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return in_n[a] > in_n[b]; });
+  // parent sizes: the largest of every kind (shared-memory sizing of the batched LU)
+  Dims pd = dmp[present.back()];
+  pd.Nb = (int)P;
+  pd.nt = m * (int)P;
+  pd.n = *std::max_element(in_n.begin(), in_n.end());
+  pd.nu = *std::max_element(in_nu.begin(), in_nu.end());
+  pd.ld = *std::max_element(in_ld.begin(), in_ld.end());
+  M->dm = pd;
+  // pattern and gather lists (user element order)
+  {
+    std::vector<const int64_t*> lists(E);
+    std::vector<int> lens(E);
+    std::vector<int64_t> ids(E);
+    for (int64_t e = 0; e < E; ++e) { lists[e] = D->elem_trace + uslot[e]; lens[e] = nbv[e]; ids[e] = M->perm[e]; }
+    int rc = setup_pattern(M, lists, lens, ids, P, st);
+    if (rc != IEDG_OK) return rc;
+  }
+  // children
+  std::vector<int64_t> rhat_off, re_off;
+  int64_t rhat_total = 0, re_total = 0;
+  for (size_t c = 0; c < present.size(); ++c) {
+    const int p = present[c];
+    iedg_mesh* C = new iedg_mesh();
+    M->groups.push_back(C);
+    Dims cd = dmp[p];
+    int nbmax = 0;
+    for (int64_t e : gel[c]) nbmax = std::max(nbmax, nbv[e]);
+    cd.Nb = nbmax;
+    cd.nt = m * nbmax;
+    cd.n = cd.nu + cd.nt;
+    cd.ld = (cd.n + 1 + 3) & ~3;
+    C->dm = cd;
+    C->ph = M->ph;
+    C->precision = M->precision;
+    C->E = (int64_t)gel[c].size();
+    C->T = M->T;
+    C->sched = M->sched;
+    rhat_off.push_back(rhat_total);
+    re_off.push_back(re_total);
+    rhat_total += C->E * (int64_t)nbmax * m;
+    re_total += C->E * (int64_t)nbmax * m;
+  }
+  // ragged sources of the R scatter, per-element LU sizes
+  std::vector<int64_t> b_rhat(E), b_re(E), b_S(E);
+  std::vector<int> ss_rhat(E, m), cs_rhat(E, 1), ss_re(E, 1), cs_re(E), ss_S(E), cs_S(E);
+  for (size_t c = 0; c < present.size(); ++c) {
+    const int Nbc = M->groups[c]->dm.Nb;
+    for (int64_t k = 0; k < (int64_t)gel[c].size(); ++k) {
+      const int64_t i = M->gstart[c] + k;
+      b_rhat[i] = rhat_off[c] + k * (int64_t)Nbc * m;
+      b_re[i] = re_off[c] + k * (int64_t)m * Nbc;
+      cs_re[i] = Nbc;
+      b_S[i] = in_soff[i] + (int64_t)in_nu[i] * in_ld[i] + in_n[i];
+      ss_S[i] = in_ld[i];
+      cs_S[i] = in_nb[i] * in_ld[i];
+    }
+  }
+  int rc = alloc_owner(M, S_total, piv_total, rhat_total, re_total, st);
+  if (rc != IEDG_OK) return rc;
+  CUDA_TRY(upload_to(M, &M->lud.soff, in_soff, st));
+  CUDA_TRY(upload_to(M, &M->lud.n, in_n, st));
+  CUDA_TRY(upload_to(M, &M->lud.nu, in_nu, st));
+  CUDA_TRY(upload_to(M, &M->lud.ld, in_ld, st));
+  CUDA_TRY(upload_to(M, &M->lud.poff, in_poff, st));
+  CUDA_TRY(upload_to(M, &M->lud.order, order, st));
+  CUDA_TRY(upload_to(M, &M->el_nb, in_nb, st));
+  CUDA_TRY(upload_to(M, &M->rs_rhat.base, b_rhat, st));
+  CUDA_TRY(upload_to(M, &M->rs_rhat.ss, ss_rhat, st));
+  CUDA_TRY(upload_to(M, &M->rs_rhat.cs, cs_rhat, st));
+  CUDA_TRY(upload_to(M, &M->rs_re.base, b_re, st));
+  CUDA_TRY(upload_to(M, &M->rs_re.ss, ss_re, st));
+  CUDA_TRY(upload_to(M, &M->rs_re.cs, cs_re, st));
+  CUDA_TRY(upload_to(M, &M->rs_S.base, b_S, st));
+  CUDA_TRY(upload_to(M, &M->rs_S.ss, ss_S, st));
+  CUDA_TRY(upload_to(M, &M->rs_S.cs, cs_S, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+
+  for (size_t c = 0; c < present.size(); ++c) {
+    iedg_mesh* C = M->groups[c];
+    const int p = present[c];
+    const Dims& cd = C->dm;
+    const HostRef& R = refs[p];
+    const int64_t Ec = C->E;
+    const int Nb = cd.Nb, Np = cd.Np, Nfq = cd.Nfq, Nfn = cd.Nfn, nq1 = cd.nq1;
+    int NFS = Nfn;
+    for (int64_t e : gel[c])
+      for (int f = 0; f < nf; ++f) {
+        int q = fdeg[e * nf + f];
+        if (q > 0) NFS = std::max(NFS, d == 3 ? (q + 1) * (q + 1) : q + 1);
+      }
+    std::vector<int> t_nb(Ec), t_nfs(Ec * nf, 0), t_fs(Ec * nf * NFS, 0), t_fdeg(Ec * nf), t_sfl(Ec * Nb * 3, -1);
+    std::vector<double> t_muf((size_t)Ec * nf * Nfq * NFS, 0.0);
+    std::vector<int64_t> t_et((size_t)Ec * Nb, 0), t_gnode(Ec);
+    std::vector<double> X((size_t)Ec * Np * d);
+    std::vector<int> eslot(Np);
+    for (int64_t k = 0; k < Ec; ++k) {
+      const int64_t e = gel[c][k];
+      int cnt = 0;
+      for (int a = 0; a < Np; ++a) {
+        eslot[a] = -1;
+        if (R.slot[a] < 0) continue;
+        for (int f = 0; f < nf; ++f)
+          if (fdeg[e * nf + f] == 0 && on_face(p, a, f)) { eslot[a] = cnt++; break; }
+      }
+      for (int f = 0; f < nf; ++f) {
+        const int q = fdeg[e * nf + f];
+        t_fdeg[k * nf + f] = q;
+        int* fsf = &t_fs[((size_t)k * nf + f) * NFS];
+        double* mu = &t_muf[((size_t)k * nf + f) * Nfq * NFS];
+        if (q == 0) {
+          t_nfs[k * nf + f] = Nfn;
+          for (int tn = 0; tn < Nfn; ++tn) {
+            const int a = R.fnode[f * Nfn + tn];
+            fsf[tn] = eslot[a];
+            for (int gf = 0; gf < Nfq; ++gf) mu[(size_t)gf * NFS + tn] = R.PhiF[(size_t)(f * Nfq + gf) * Np + a];
+          }
+        } else {
+          const int q1 = q + 1, nq = d == 3 ? q1 * q1 : q1;
+          t_nfs[k * nf + f] = nq;
+          for (int j = 0; j < nq; ++j) {
+            fsf[j] = cnt + j;
+            const int j1 = j % q1, j2 = j / q1;
+            for (int gf = 0; gf < Nfq; ++gf) {
+              const int g1 = gf % nq1, g2 = gf / nq1;
+              double v = R.LQ[((size_t)q * nq1 + g1) * 5 + j1];
+              if (d == 3) v *= R.LQ[((size_t)q * nq1 + g2) * 5 + j2];
+              mu[(size_t)gf * NFS + j] = v;
+            }
+          }
+          cnt += nq;
+        }
+      }
+      if (cnt != nbv[e]) return fail(M, IEDG_ERR_MESH, "inconsistent trace slot count");
+      t_nb[k] = cnt;
+      for (int f = 0; f < nf; ++f)
+        for (int j = 0; j < t_nfs[k * nf + f]; ++j) {
+          const int sl = t_fs[((size_t)k * nf + f) * NFS + j];
+          if (sl < 0 || sl >= cnt) return fail(M, IEDG_ERR_MESH, "face node without a trace slot");
+          int* fl = &t_sfl[((size_t)k * Nb + sl) * 3];
+          int w = 0;
+          while (w < 3 && fl[w] >= 0) ++w;
+          if (w == 3) return fail(M, IEDG_ERR_MESH, "trace slot on more than three faces");
+          fl[w] = f * NFS + j;
+        }
+      for (int s2 = 0; s2 < cnt; ++s2) t_et[(size_t)k * Nb + s2] = D->elem_trace[uslot[e] + s2];
+      t_gnode[k] = unode[e];
+      for (int i = 0; i < Np * d; ++i) X[(size_t)k * Np * d + i] = D->node_xyz[unode[e] * d + i];
+    }
+    TraceTab& tt = C->tt;
+    tt.NFS = NFS;
+    CUDA_TRY(upload_to(C, &tt.nb, t_nb, st));
+    CUDA_TRY(upload_to(C, &tt.nfs, t_nfs, st));
+    CUDA_TRY(upload_to(C, &tt.fs, t_fs, st));
+    CUDA_TRY(upload_to(C, &tt.fdeg, t_fdeg, st));
+    CUDA_TRY(upload_to(C, &tt.muf, t_muf, st));
+    CUDA_TRY(upload_to(C, &tt.sfl, t_sfl, st));
+    CUDA_TRY(upload(C, &C->etrace, t_et, st));
+    CUDA_TRY(upload(C, &C->gnode, t_gnode, st));
+    tt.soff = M->lud.soff + M->gstart[c];
+    tt.ldv = M->lud.ld + M->gstart[c];
+    int rc2 = alloc_group(C, st);
+    if (rc2 != IEDG_OK) return fail(M, rc2, C->err);
+    if (M->precision == IEDG_PRECISION_MIXED) {
+      float* m32 = nullptr;
+      CUDA_TRY(dalloc(C, &m32, t_muf.size()));
+      CUDA_TRY(launch_to_f32(tt.muf, m32, (int64_t)t_muf.size(), st));
+      tt.muf32 = m32;
+    }
+    const size_t nod = (size_t)Ec * Np * m;
+    CUDA_TRY(dalloc(C, &C->xu, nod));
+    CUDA_TRY(dalloc(C, &C->xuref, nod));
+    CUDA_TRY(dalloc(C, &C->xru, nod));
+    CUDA_TRY(dalloc(C, &C->xq, nod * d));
+    CUDA_TRY(dalloc(C, &C->xrq, nod * d));
+    C->S = M->S;
+    C->S32 = M->S32;
+    C->piv = M->piv ? M->piv + in_poff[M->gstart[c]] : nullptr;
+    C->status = M->status + M->gstart[c];
+    C->rhat = M->rhat + rhat_off[c];
+    C->re64 = M->re64 + re_off[c];
+    C->queue = M->queue;
+    rc2 = run_geometry(C, X.data(), st);
+    if (rc2 != IEDG_OK) return fail(M, rc2, C->err);
+  }
+  M->mixed_orders = true;
+  return IEDG_OK;
+}
+
+extern "C" int iedg_create_mesh_mixed(const iedg_mesh_desc* D, const int32_t* elem_order,
+                                      const int32_t* face_degree, void* stream, iedg_mesh** out) {
+  iedg_mesh* M = nullptr;
+  if (!D || !out || !elem_order || !face_degree) return fail(M, IEDG_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  int rc = check_desc(D, true);
+  if (rc != IEDG_OK) return rc;
+  M = new iedg_mesh();
+  M->ph = Phys{D->gamma, D->Pr, D->Re, D->alpha};
+  M->precision = D->precision;
+  M->E = D->n_elem;
+  M->T = D->n_trace;
+  rc = create_mixed_impl(D, elem_order, face_degree, (cudaStream_t)stream, M);
+  if (rc != IEDG_OK) {
+    g_err = M->err;
+    destroy_impl(M);
+    return rc;
+  }
+  *out = M;
+  return IEDG_OK;
+}
+
+extern "C" int iedg_element_sizes(const iedg_mesh* M, int32_t* Np, int32_t* Nb) {
+  if (!M) return IEDG_ERR_INVALID_ARG;
+  if (!M->mixed_orders) {
+    for (int64_t e = 0; e < M->E; ++e) {
+      if (Np) Np[e] = M->dm.Np;
+      if (Nb) Nb[e] = M->dm.Nb;
+    }
+    return IEDG_OK;
+  }
+  std::vector<int> nb(M->E);
+  if (Nb && cudaMemcpy(nb.data(), M->el_nb, M->E * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return IEDG_ERR_CUDA;
+  for (int64_t e = 0; e < M->E; ++e) {
+    if (Np) Np[e] = (int32_t)(M->unode[e + 1] - M->unode[e]);
+    if (Nb) Nb[e] = nb[M->perm[e]];
+  }
+  return IEDG_OK;
+}
+
+// Compute entry points on meshes with mixed orders: each child runs the element
+// kernels of its order on its own copies of the nodal arrays; the LU runs once over
+// all elements (largest first) and the scatters read the ragged per-element results.
+static int residual_mixed(iedg_mesh* M, const double* u, const double* uhat, const double* q, const double* u_ref,
+                          double* q_out, double* r_q, double* r_u, double* r_fl, cudaStream_t st) {
+  const int m = M->dm.m, d = M->dm.d;
+  if (q && q_out)
+    CUDA_TRY(cudaMemcpyAsync(q_out, q, M->n_nodes * m * d * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  for (iedg_mesh* C : M->groups) {
+    CUDA_TRY(TRACED("nodal_in", launch_nodal_copy(C, m, u, C->xu, true, st)));
+    if (q) CUDA_TRY(TRACED("nodal_in", launch_nodal_copy(C, m * d, q, C->xq, true, st)));
+    if (u_ref) CUDA_TRY(TRACED("nodal_in", launch_nodal_copy(C, m, u_ref, C->xuref, true, st)));
+    const double* ur = u_ref ? C->xuref : nullptr;
+    if (!q) {
+      CUDA_TRY(TRACED("lift", launch_lift(C, C->xu, uhat, C->xq, st)));
+      if (q_out) CUDA_TRY(TRACED("nodal_out", launch_nodal_copy(C, m * d, C->xq, q_out, false, st)));
+    }
+    if (r_q) {
+      if (q) CUDA_TRY(TRACED("lift", launch_lift(C, C->xu, uhat, C->qstar, st)));
+      CUDA_TRY(TRACED("rq", launch_rq(C, C->xq, q ? C->qstar : C->xq, C->xrq, nullptr, st)));
+      CUDA_TRY(TRACED("nodal_out", launch_nodal_copy(C, m * d, C->xrq, r_q, false, st)));
+    }
+    if (r_u || r_fl) {
+      CUDA_TRY(TRACED("points_residual",
+                      launch_points(C, C->xu, C->xq, nullptr, uhat, ur, false, r_u ? C->xru : nullptr, C->rhat, st)));
+      if (r_u) CUDA_TRY(TRACED("nodal_out", launch_nodal_copy(C, m, C->xru, r_u, false, st)));
+    }
+  }
+  if (r_fl) CUDA_TRY(TRACED("scatter_R", launch_scatter_R_ragged(M, M->rs_rhat, M->rhat, r_fl, st)));
+  return IEDG_OK;
+}
+
+static int assemble_mixed(iedg_mesh* M, const double* u, const double* q, const double* uhat, const double* u_ref,
+                          double* K, double* R, cudaStream_t st) {
+  const int m = M->dm.m, d = M->dm.d;
+  CUDA_TRY(cudaMemsetAsync(M->status, 0, M->E, st));
+  for (iedg_mesh* C : M->groups) {
+    CUDA_TRY(TRACED("nodal_in", launch_nodal_copy(C, m, u, C->xu, true, st)));
+    CUDA_TRY(TRACED("nodal_in", launch_nodal_copy(C, m * d, q, C->xq, true, st)));
+    if (u_ref) CUDA_TRY(TRACED("nodal_in", launch_nodal_copy(C, m, u_ref, C->xuref, true, st)));
+    CUDA_TRY(TRACED("lift", launch_lift(C, C->xu, uhat, C->qstar, st)));
+    CUDA_TRY(TRACED("rq", launch_rq(C, C->xq, C->qstar, nullptr, C->rhoq, st)));
+    CUDA_TRY(TRACED("points_jacobian", launch_points(C, C->xu, C->xq, C->qstar, uhat, u_ref ? C->xuref : nullptr,
+                                                     true, nullptr, nullptr, st)));
+    if (assemble_sf_supported(C->dm))
+      CUDA_TRY(TRACED("assemble", launch_assemble_sf(C, st)));
+    else
+      CUDA_TRY(TRACED("assemble", launch_assemble(C, st)));
+  }
+  CUDA_TRY(TRACED("lu_schur", launch_lu(M, st)));
+  if (M->precision == IEDG_PRECISION_MIXED)
+    for (iedg_mesh* C : M->groups) CUDA_TRY(TRACED("refine", launch_refine(C, st)));
+  CUDA_TRY(TRACED("scatter_K", launch_scatter_K(M, K, st)));
+  if (M->precision == IEDG_PRECISION_FP64)
+    CUDA_TRY(TRACED("scatter_R", launch_scatter_R_ragged(M, M->rs_S, M->S, R, st)));
+  else
+    CUDA_TRY(TRACED("scatter_R", launch_scatter_R_ragged(M, M->rs_re, M->re64, R, st)));
+  M->assembled = true;
+  return IEDG_OK;
+}
+
+static int backsub_mixed_orders(iedg_mesh* M, const double* duhat, double* du, double* dq, cudaStream_t st) {
+  const int m = M->dm.m, d = M->dm.d;
+  for (iedg_mesh* C : M->groups) {
+    if (M->precision == IEDG_PRECISION_FP64)
+      CUDA_TRY(TRACED("backsub", launch_backsub(C, duhat, C->xru, C->xrq, st)));
+    else
+      CUDA_TRY(TRACED("backsub", launch_backsub_mixed(C, duhat, C->xru, C->xrq, st)));
+    CUDA_TRY(TRACED("nodal_out", launch_nodal_copy(C, m, C->xru, du, false, st)));
+    CUDA_TRY(TRACED("nodal_out", launch_nodal_copy(C, m * d, C->xrq, dq, false, st)));
+  }
+  return IEDG_OK;
+}
+
 extern "C" int iedg_destroy_mesh(iedg_mesh* M) {
   if (!M) return IEDG_ERR_INVALID_ARG;
   drain_events(M);
-  free_all(M);
-  delete M;
+  destroy_impl(M);
   return IEDG_OK;
 }
 
@@ -469,7 +955,10 @@ extern "C" int iedg_mesh_info(const iedg_mesh* M, int32_t* Np, int32_t* Nb, int6
   if (Np) *Np = M->dm.Np;
   if (Nb) *Nb = M->dm.Nb;
   if (nnzb) *nnzb = M->nnzb;
-  if (ws) *ws = M->ws_bytes;
+  if (ws) {
+    *ws = M->ws_bytes;
+    for (const iedg_mesh* C : M->groups) *ws += C->ws_bytes;
+  }
   return IEDG_OK;
 }
 
@@ -488,6 +977,7 @@ extern "C" int iedg_eval_residual(iedg_mesh* M, const double* u, const double* u
   if (!M || !u || !uhat) return fail(M, IEDG_ERR_INVALID_ARG, "null argument");
   if (!q && !q_out) return fail(M, IEDG_ERR_INVALID_ARG, "q_out required when q is NULL");
   cudaStream_t st = (cudaStream_t)stream;
+  if (M->mixed_orders) return residual_mixed(M, u, uhat, q, u_ref, q_out, r_q, r_u, r_fl, st);
   const Dims& dm = M->dm;
   const double* qq = q;
   if (!q) {
@@ -514,6 +1004,7 @@ extern "C" int iedg_assemble_condensed(iedg_mesh* M, const double* u, const doub
                                        double* R, void* stream) {
   if (!M || !u || !q || !uhat || !K || !R) return fail(M, IEDG_ERR_INVALID_ARG, "null argument");
   cudaStream_t st = (cudaStream_t)stream;
+  if (M->mixed_orders) return assemble_mixed(M, u, q, uhat, u_ref, K, R, st);
   const Dims& dm = M->dm;
   CUDA_TRY(cudaMemsetAsync(M->status, 0, M->E, st));
   CUDA_TRY(TRACED("lift", launch_lift(M, u, uhat, M->qstar, st)));
@@ -542,6 +1033,7 @@ extern "C" int iedg_back_substitute(iedg_mesh* M, const double* duhat, double* d
   if (!M || !duhat || !du || !dq) return fail(M, IEDG_ERR_INVALID_ARG, "null argument");
   if (!M->assembled) return fail(M, IEDG_ERR_NOT_ASSEMBLED, "back-substitution before assembly");
   cudaStream_t st = (cudaStream_t)stream;
+  if (M->mixed_orders) return backsub_mixed_orders(M, duhat, du, dq, st);
   if (M->precision == IEDG_PRECISION_FP64)
     CUDA_TRY(TRACED("backsub", launch_backsub(M, duhat, du, dq, st)));
   else
@@ -552,8 +1044,15 @@ extern "C" int iedg_back_substitute(iedg_mesh* M, const double* duhat, double* d
 extern "C" int64_t iedg_element_status(iedg_mesh* M, int8_t* out, void* stream) {
   if (!M || !out) return fail(M, IEDG_ERR_INVALID_ARG, "null argument");
   cudaStream_t st = (cudaStream_t)stream;
-  CUDA_TRY(cudaMemcpyAsync(out, M->status, M->E, cudaMemcpyDeviceToHost, st));
-  CUDA_TRY(cudaStreamSynchronize(st));
+  if (M->mixed_orders) {
+    std::vector<int8_t> tmp(M->E);
+    CUDA_TRY(cudaMemcpyAsync(tmp.data(), M->status, M->E, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    for (int64_t e = 0; e < M->E; ++e) out[e] = tmp[M->perm[e]];
+  } else {
+    CUDA_TRY(cudaMemcpyAsync(out, M->status, M->E, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+  }
   int64_t n = 0;
   for (int64_t e = 0; e < M->E; ++e) n += out[e] != 0;
   return n;
@@ -595,16 +1094,20 @@ extern "C" int iedg_get_schedule(const iedg_mesh* M, iedg_schedule* out) {
   out->lu_persistent = M->sched.lu_persistent;
   out->lu_panel = M->sched.lu_panel;
   out->asm_chunk = M->sched.asm_chunk;
+  out->lu_tensor = M->sched.lu_tensor;
   return IEDG_OK;
 }
 
 extern "C" int iedg_set_schedule(iedg_mesh* M, const iedg_schedule* in) {
   if (!M || !in) return fail(M, IEDG_ERR_INVALID_ARG, "null argument");
   if ((in->lu_persistent != 0 && in->lu_persistent != 1) || (in->lu_panel != 16 && in->lu_panel != 32) ||
-      (in->asm_chunk != 0 && in->asm_chunk != 8 && in->asm_chunk != 16 && in->asm_chunk != 32))
+      (in->asm_chunk != 0 && in->asm_chunk != 8 && in->asm_chunk != 16 && in->asm_chunk != 32) ||
+      (in->lu_tensor != 0 && in->lu_tensor != 1))
     return fail(M, IEDG_ERR_INVALID_ARG, "schedule values out of range");
   M->sched.lu_persistent = in->lu_persistent;
   M->sched.lu_panel = in->lu_panel;
   M->sched.asm_chunk = in->asm_chunk;
+  M->sched.lu_tensor = in->lu_tensor;
+  for (iedg_mesh* C : M->groups) C->sched = M->sched;
   return IEDG_OK;
 }

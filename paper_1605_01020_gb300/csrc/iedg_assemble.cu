@@ -18,6 +18,7 @@
 // The right-hand-side column is written by the point kernel: Ft = -R_u(u, q*),
 // Gt = -R_FL,e(u, q*) (exact because the fluxes are affine in q).
 #include "iedg_internal.cuh"
+#include "iedg_tc.cuh"
 
 namespace iedg {
 namespace {
@@ -50,10 +51,13 @@ AsmCfg asm_cfg(const Dims& dm) {
 
 // T = double: FP64 path.  T = float: mixed path (FP32 element matrix; the FP64
 // right-hand sides are copied into column n by one CTA per element).
+// Meshes with mixed orders (tt.nb set): per-element slot count, offset and leading
+// dimension; the trace basis at the face points comes from the element's table, and
+// the trace rows are accumulated separately from the face parts of the u-rows.
 template <class T>
 __global__ void __launch_bounds__(AS_THREADS)
 k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, AsmTab<T> tb, T* __restrict__ S,
-           const double* __restrict__ rhs64) {
+           const double* __restrict__ rhs64, TraceTab tt, int NbU) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
   const int tid = threadIdx.x;
@@ -61,21 +65,31 @@ k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, AsmTab<T> tb, T* __restri
   const int64_t e = blockIdx.x / m2;                 // the m^2 CTAs of an element are adjacent
   const int pair = blockIdx.x % m2, i = pair / dm.m, k = pair % dm.m;
   const int c0 = blockIdx.y * cf.CW;
-  const int d = dm.d, Np = dm.Np, Nb = dm.Nb, Nq = dm.Nq, Nfp = dm.Nfp, Nfq = dm.Nfq, Nfn = dm.Nfn;
+  const int d = dm.d, Np = dm.Np, Nq = dm.Nq, Nfp = dm.Nfp, Nfq = dm.Nfq, Nfn = dm.Nfn;
+  const bool mix = tt.nb != nullptr;
+  const int NbT = dm.Nb;                            // slot stride of the lifting tables
+  const int Nb = mix ? tt.nb[e] : dm.Nb;            // trace slots of this element
   const int ncol = Np + Nb;
   const int KC = cf.KC, CW = cf.CW, RP = cf.rows_pad;
   T* sA = sm;                           // [KC][RP]   Dxi_r[g][a]
   T* sB = sA + KC * RP;                 // [KC][CW]   W[(g, r)][col]
-  T* facc = sB + KC * CW;               // [Nb][CW]   face parts of the boundary rows
-  T* sV = facc + Nb * CW;               // [Nfq][CW]  face right operand
+  T* facc = sB + KC * CW;               // [NbU][CW]  face parts of the boundary rows
+  T* sV = facc + NbU * CW;              // [Nfq][CW]  face right operand
+  T* tacc = mix ? sV + Nfq * CW : facc; // [Nb][CW]   trace rows (mixed orders), else = facc
+  const T* mutab = nullptr;
+  if (mix) {
+    if constexpr (sizeof(T) == 8) mutab = reinterpret_cast<const T*>(tt.muf);
+    else mutab = reinterpret_cast<const T*>(tt.muf32);
+    mutab += (size_t)e * dm.nf * Nfq * tt.NFS;
+  }
   const size_t jvs = (size_t)(1 + d) * d * Nq;
   const T* jv = tb.Jv + ((size_t)e * dm.m * dm.m + pair) * jvs;
   const size_t jfs = (size_t)(1 + d) * Nfp;
   const T* jf = tb.Jf + ((size_t)e * dm.m * dm.m + pair) * jfs;
   const T* GlV = tb.GlV + (size_t)e * d * Nq * Np;
-  const T* HlV = tb.HlV + (size_t)e * d * Nq * Nb;
+  const T* HlV = tb.HlV + (size_t)e * d * Nq * NbT;
   const T* GlF = tb.GlF + (size_t)e * d * Nfp * Np;
-  const T* HlF = tb.HlF + (size_t)e * d * Nfp * Nb;
+  const T* HlF = tb.HlF + (size_t)e * d * Nfp * NbT;
 
   const int trow = tid / cf.cg, tcol = tid % cf.cg;
   const bool gemm_thread = trow < cf.rg;
@@ -103,7 +117,7 @@ k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, AsmTab<T> tb, T* __restri
             w -= jv[(size_t)(d + l * d + r) * Nq + g] * GlV[((size_t)l * Nq + g) * Np + col];
         } else {
           for (int l = 0; l < d; ++l)
-            w += jv[(size_t)(d + l * d + r) * Nq + g] * HlV[((size_t)l * Nq + g) * Nb + (col - Np)];
+            w += jv[(size_t)(d + l * d + r) * Nq + g] * HlV[((size_t)l * Nq + g) * NbT + (col - Np)];
         }
       }
       sB[idx] = w;
@@ -126,7 +140,9 @@ k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, AsmTab<T> tb, T* __restri
   }
 
   // ---- face parts, accumulated per trace slot
-  for (int idx = tid; idx < Nb * CW; idx += AS_THREADS) facc[idx] = (T)0;
+  for (int idx = tid; idx < NbU * CW; idx += AS_THREADS) facc[idx] = (T)0;
+  if (mix)
+    for (int idx = tid; idx < Nb * CW; idx += AS_THREADS) tacc[idx] = (T)0;
   const T lamsel = (i == k) ? (T)1 : (T)0;
   for (int f = 0; f < dm.nf; ++f) {
     __syncthreads();
@@ -139,8 +155,18 @@ k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, AsmTab<T> tb, T* __restri
         for (int l = 0; l < d; ++l) v -= jf[(size_t)(1 + l) * Nfp + fp] * GlF[((size_t)l * Nfp + fp) * Np + col];
       } else if (col < ncol) {
         int t = col - Np;
-        v = jf[fp] * tb.PhiF[(size_t)fp * Np + ref.bnode[t]];
-        for (int l = 0; l < d; ++l) v += jf[(size_t)(1 + l) * Nfp + fp] * HlF[((size_t)l * Nfp + fp) * Nb + t];
+        T mu = 0;
+        if (mix) {
+          const int* fl = tt.sfl + ((size_t)e * NbT + t) * 3;
+          for (int q = 0; q < 3; ++q) {
+            const int code = fl[q];
+            if (code >= 0 && code / tt.NFS == f) mu = mutab[((size_t)f * Nfq + gf) * tt.NFS + code % tt.NFS];
+          }
+        } else {
+          mu = tb.PhiF[(size_t)fp * Np + ref.bnode[t]];
+        }
+        v = jf[fp] * mu;
+        for (int l = 0; l < d; ++l) v += jf[(size_t)(1 + l) * Nfp + fp] * HlF[((size_t)l * Nfp + fp) * NbT + t];
       }
       sV[idx] = v;
     }
@@ -152,14 +178,26 @@ k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, AsmTab<T> tb, T* __restri
       for (int gf = 0; gf < Nfq; ++gf) s += tb.PhiF[(size_t)(f * Nfq + gf) * Np + a] * sV[gf * CW + cc];
       facc[ref.slot[a] * CW + cc] += s;
     }
+    if (mix) {
+      // trace rows: the slots living on this face, with the element's trace basis
+      const int cnt = tt.nfs[e * dm.nf + f];
+      const int* fsf = tt.fs + ((size_t)e * dm.nf + f) * tt.NFS;
+      for (int idx = tid; idx < cnt * CW; idx += AS_THREADS) {
+        int j = idx / CW, cc = idx % CW;
+        T s = 0;
+        for (int gf = 0; gf < Nfq; ++gf) s += mutab[((size_t)f * Nfq + gf) * tt.NFS + j] * sV[gf * CW + cc];
+        tacc[fsf[j] * CW + cc] += s;
+      }
+    }
   }
   __syncthreads();
 
   // ---- write the element rows
-  const int64_t nn = dm.n, ld = dm.ld;
-  T* Se = S + e * nn * ld;
+  const int64_t nn = mix ? (int64_t)dm.nu + (int64_t)dm.m * Nb : dm.n;
+  const int64_t ld = mix ? tt.ldv[e] : dm.ld;
+  T* Se = mix ? S + tt.soff[e] : S + e * nn * ld;
   if (rhs64 != nullptr && pair == 0 && blockIdx.y == 0)
-    for (int r = tid; r < nn; r += AS_THREADS) Se[r * ld + nn] = (T)rhs64[e * nn + r];
+    for (int r = tid; r < nn; r += AS_THREADS) Se[r * ld + nn] = (T)rhs64[e * dm.n + r];
   auto colS = [&](int col) -> int64_t { return col < Np ? (int64_t)k * Np + col : (int64_t)dm.nu + (int64_t)k * Nb + (col - Np); };
   if (gemm_thread) {
     const T* Ms = tb.Mass + (size_t)e * Np * Np;
@@ -182,7 +220,7 @@ k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, AsmTab<T> tb, T* __restri
   for (int idx = tid; idx < Nb * CW; idx += AS_THREADS) {
     int s = idx / CW, col = c0 + idx % CW;
     if (col >= ncol) continue;
-    Se[((int64_t)dm.nu + (int64_t)i * Nb + s) * ld + colS(col)] = facc[idx];
+    Se[((int64_t)dm.nu + (int64_t)i * Nb + s) * ld + colS(col)] = tacc[idx];
   }
 }
 
@@ -198,8 +236,19 @@ k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, AsmTab<T> tb, T* __restri
 constexpr int LU_THREADS = 256;
 constexpr int UCW = 64;     // trailing-update column chunk
 
+// Sizes and location of one element's bordered matrix.
+struct LuElem {
+  int n, nu, ld;
+  int64_t off, poff;
+};
+
+__device__ __forceinline__ LuElem lu_elem(const Dims& dm, const LuDesc& lud, int64_t e) {
+  if (lud.soff) return LuElem{lud.n[e], lud.nu[e], lud.ld[e], lud.soff[e], lud.poff ? lud.poff[e] : 0};
+  return LuElem{dm.n, dm.nu, dm.ld, e * (int64_t)dm.n * dm.ld, e * (int64_t)dm.nu};
+}
+
 template <class T, int NB>
-__device__ __forceinline__ void lu_element(const Dims& dm, T* __restrict__ S, int8_t* __restrict__ status,
+__device__ __forceinline__ void lu_element(const LuElem& el, T* __restrict__ S, int8_t* __restrict__ status,
                                            int* __restrict__ pivots, const int64_t e) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
@@ -208,8 +257,8 @@ __device__ __forceinline__ void lu_element(const Dims& dm, T* __restrict__ S, in
   __shared__ int ri[LU_THREADS / 32];
   __shared__ int sing;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int n = dm.n, nu = dm.nu, ld = dm.ld, ncol = n + 1;
-  T* A = S + e * (int64_t)n * ld;
+  const int n = el.n, nu = el.nu, ld = el.ld, ncol = n + 1;
+  T* A = S + el.off;
   T* P = sm;                            // [n][NB]
   T* Uc = P + (size_t)n * NB;           // [NB][UCW]
   if (tid == 0) sing = 0;
@@ -242,7 +291,7 @@ __device__ __forceinline__ void lu_element(const Dims& dm, T* __restrict__ S, in
           if (rv[w] > bv || (rv[w] == bv && ri[w] < b)) { bv = rv[w]; b = ri[w]; }
         if (!(bv > 0)) { sing = 1; b = j; }
         piv[j] = b;
-        if (pivots) pivots[e * nu + kb + j] = kb + b;
+        if (pivots) pivots[el.poff + kb + j] = kb + b;
       }
       __syncthreads();
       const int pr = piv[j];
@@ -352,18 +401,27 @@ constexpr int L32_NB = 32;
 constexpr int L32_UCW = 128;      // trailing-update column chunk
 constexpr int L32_TM = 4, L32_TN = 8;
 
-__device__ __forceinline__ void lu32_element(const Dims& dm, float* __restrict__ S, int8_t* __restrict__ status,
-                                             int* __restrict__ pivots, const int64_t e) {
+// Tensor-core state of a CTA for the TC form of the trailing update.
+struct TcState {
+  uint32_t tmem;        // TMEM base (128 columns)
+  uint64_t* mbar;       // MMA completion barrier
+  uint32_t phase;       // parity of the next completion
+  int failed;           // a completion wait ran out
+};
+
+template <bool TC>
+__device__ __forceinline__ void lu32_element(const LuElem& el, float* __restrict__ S, int8_t* __restrict__ status,
+                                             int* __restrict__ pivots, const int64_t e, TcState* tcs) {
   extern __shared__ __align__(16) unsigned char smraw[];
   float* P = reinterpret_cast<float*>(smraw);          // [NB][n] column-major panel
-  float* Uc = P + (size_t)L32_NB * dm.n;                // [NB][UCW]
+  float* Uc = P + (size_t)L32_NB * el.n;                // [NB][UCW]
   __shared__ int piv[L32_NB];
   __shared__ float rv[LU_THREADS / 32];
   __shared__ int ri[LU_THREADS / 32];
   __shared__ int sing;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int n = dm.n, nu = dm.nu, ld = dm.ld, ncol = n + 1;
-  float* A = S + e * (int64_t)n * ld;
+  const int n = el.n, nu = el.nu, ld = el.ld, ncol = n + 1;
+  float* A = S + el.off;
   if (tid == 0) sing = 0;
   for (int kb = 0; kb < nu; kb += L32_NB) {
     const int nb = min(L32_NB, nu - kb), rows = n - kb, prow = nu - kb;
@@ -395,7 +453,7 @@ __device__ __forceinline__ void lu32_element(const Dims& dm, float* __restrict__
           if (rv[w] > bv || (rv[w] == bv && ri[w] < b)) { bv = rv[w]; b = ri[w]; }
         if (!(bv > 0.f)) { sing = 1; b = j; }
         piv[j] = b;
-        pivots[e * nu + kb + j] = kb + b;
+        pivots[el.poff + kb + j] = kb + b;
       }
       __syncthreads();
       const int pr = piv[j];
@@ -447,6 +505,88 @@ __device__ __forceinline__ void lu32_element(const Dims& dm, float* __restrict__
       }
     }
     __syncthreads();
+    if constexpr (TC) {
+      // A22 -= L21 U12 on the tensor cores: 128 x 128 blocks, K = 32, 3xTF32 (hi hi + hi lo
+      // + lo hi) into a TMEM accumulator; operands staged in the (now free) panel buffer
+      const int r0 = kb + nb;
+      char* ob = reinterpret_cast<char*>(P);
+      float* sAh = reinterpret_cast<float*>(ob);
+      float* sAl = reinterpret_cast<float*>(ob + 16384);
+      float* sBh = reinterpret_cast<float*>(ob + 32768);
+      float* sBl = reinterpret_cast<float*>(ob + 49152);
+      const uint32_t aH = tc::smem_u32(sAh), aL = tc::smem_u32(sAl), bH = tc::smem_u32(sBh), bL = tc::smem_u32(sBl);
+      constexpr uint32_t IDESC = tc::idesc_tf32(128, 128);
+      const int q = warp & 3, h = warp >> 2;
+      for (int cc = r0; cc < ncol && !tcs->failed; cc += 128) {
+        for (int idx = tid; idx < 128 * L32_NB; idx += LU_THREADS) {
+          const int k = idx >> 7, nn = idx & 127;
+          const float v = (k < nb && cc + nn < ncol) ? A[(int64_t)(kb + k) * ld + cc + nn] : 0.f;
+          float hi, lo;
+          tc::split_tf32(v, hi, lo);
+          const uint32_t off = tc::core_off32(nn, k);
+          *reinterpret_cast<float*>(reinterpret_cast<char*>(sBh) + off) = hi;
+          *reinterpret_cast<float*>(reinterpret_cast<char*>(sBl) + off) = lo;
+        }
+        for (int rb = r0; rb < n && !tcs->failed; rb += 128) {
+          for (int idx = tid; idx < 128 * L32_NB; idx += LU_THREADS) {
+            const int mm = idx >> 5, k = idx & 31;
+            const float v = (k < nb && rb + mm < n) ? A[(int64_t)(rb + mm) * ld + kb + k] : 0.f;
+            float hi, lo;
+            tc::split_tf32(v, hi, lo);
+            const uint32_t off = tc::core_off32(mm, k);
+            *reinterpret_cast<float*>(reinterpret_cast<char*>(sAh) + off) = hi;
+            *reinterpret_cast<float*>(reinterpret_cast<char*>(sAl) + off) = lo;
+          }
+          tc::fence_proxy_async();
+          __syncthreads();
+          tc::fence_after_sync();
+          if (tid == 0) {
+#pragma unroll
+            for (int st = 0; st < L32_NB / 8; ++st) {
+              const uint32_t ko = st * 256;
+              tc::mma_tf32(tcs->tmem, tc::desc_kmajor(aH + ko, 128, 1024), tc::desc_kmajor(bH + ko, 128, 1024), IDESC,
+                           st > 0);
+              tc::mma_tf32(tcs->tmem, tc::desc_kmajor(aH + ko, 128, 1024), tc::desc_kmajor(bL + ko, 128, 1024), IDESC, 1);
+              tc::mma_tf32(tcs->tmem, tc::desc_kmajor(aL + ko, 128, 1024), tc::desc_kmajor(bH + ko, 128, 1024), IDESC, 1);
+            }
+            tc::mma_commit(tcs->mbar);
+          }
+          // every thread waits; the verdict is made uniform so that all threads leave
+          // the loops together
+          const bool ok = __syncthreads_and(tc::mbar_wait(tcs->mbar, tcs->phase, 1 << 26));
+          tcs->phase ^= 1u;
+          if (!ok) tcs->failed = 1;
+          tc::fence_after_sync();
+          // epilogue: warp (q, h) owns rows 32 q .. 32 q + 31 and columns 64 h .. 64 h + 63
+          const int row = rb + 32 * q + lane;
+          const bool cvec = ((cc & 3) == 0);
+#pragma unroll 1
+          for (int c8 = 0; c8 < 8; ++c8) {
+            const int c0 = 64 * h + 8 * c8;
+            float pv8[8];
+            tc::tmem_ld8(tcs->tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, pv8);
+            if (!ok || row >= n || cc + c0 >= ncol) continue;
+            float* dst = A + (int64_t)row * ld + cc + c0;
+            if (cvec && cc + c0 + 8 <= ld) {
+              float4* d4 = reinterpret_cast<float4*>(dst);
+              float4 v0 = d4[0], v1 = d4[1];
+              v0.x -= pv8[0]; v0.y -= pv8[1]; v0.z -= pv8[2]; v0.w -= pv8[3];
+              v1.x -= pv8[4]; v1.y -= pv8[5]; v1.z -= pv8[6]; v1.w -= pv8[7];
+              d4[0] = v0;
+              d4[1] = v1;
+            } else {
+#pragma unroll
+              for (int j = 0; j < 8; ++j)
+                if (cc + c0 + j < ncol) dst[j] -= pv8[j];
+            }
+          }
+          tc::fence_before_sync();
+          __syncthreads();
+        }
+      }
+      __syncthreads();
+      continue;
+    }
     // A22 -= L21 U12, 8 x 8 tiles, rows [kb+nb, n), cols [kb+nb, n]
     const int r0 = kb + nb;
     const bool vec = ((nb & 3) == 0) && ((n & 3) == 0);
@@ -527,38 +667,86 @@ __device__ __forceinline__ void lu32_element(const Dims& dm, float* __restrict__
     if (!isfinite(A[(int64_t)r * ld + c])) bad = 1;
   }
   bad = __syncthreads_or(bad);
+  if (TC && tcs->failed) bad = 1;
   if (tid == 0) status[e] = sing ? IEDG_ELEM_SINGULAR : (bad ? IEDG_ELEM_NONFINITE : IEDG_ELEM_OK);
 }
 
 // Element scheduling of the batched LU.  queue == nullptr: one CTA per element.
 // Otherwise a persistent grid (a few CTAs per SM) takes elements from an atomic
 // counter in order, so no SM idles in a partial last wave.
-__device__ __forceinline__ bool next_element(int64_t* queue, int64_t E, int64_t it, int64_t* e_out) {
+// With an order list the k-th element taken is order[k].
+__device__ __forceinline__ bool next_element(int64_t* queue, int64_t E, int64_t it, const int64_t* order,
+                                             int64_t* e_out) {
   __shared__ unsigned long long s_next;
   if (queue == nullptr) {
-    *e_out = blockIdx.x;
+    *e_out = order ? order[blockIdx.x] : (int64_t)blockIdx.x;
     return it == 0;
   }
   if (threadIdx.x == 0) s_next = atomicAdd(reinterpret_cast<unsigned long long*>(queue), 1ull);
   __syncthreads();
-  const int64_t e = (int64_t)s_next;
+  const int64_t k = (int64_t)s_next;
   __syncthreads();
-  *e_out = e;
-  return e < E;
+  *e_out = (order && k < E) ? order[k] : k;
+  return k < E;
 }
 
 template <class T, int NB>
 __global__ void __launch_bounds__(LU_THREADS)
-k_lu(Dims dm, T* __restrict__ S, int8_t* __restrict__ status, int* __restrict__ pivots, int64_t* queue, int64_t E) {
+k_lu(Dims dm, LuDesc lud, T* __restrict__ S, int8_t* __restrict__ status, int* __restrict__ pivots, int64_t* queue,
+     int64_t E) {
   int64_t e;
-  for (int64_t it = 0; next_element(queue, E, it, &e); ++it) lu_element<T, NB>(dm, S, status, pivots, e);
+  for (int64_t it = 0; next_element(queue, E, it, lud.order, &e); ++it)
+    lu_element<T, NB>(lu_elem(dm, lud, e), S, status, pivots, e);
 }
 
 __global__ void __launch_bounds__(LU_THREADS, 2)
-k_lu32(Dims dm, float* __restrict__ S, int8_t* __restrict__ status, int* __restrict__ pivots, int64_t* queue,
-       int64_t E) {
+k_lu32(Dims dm, LuDesc lud, float* __restrict__ S, int8_t* __restrict__ status, int* __restrict__ pivots,
+       int64_t* queue, int64_t E) {
   int64_t e;
-  for (int64_t it = 0; next_element(queue, E, it, &e); ++it) lu32_element(dm, S, status, pivots, e);
+  for (int64_t it = 0; next_element(queue, E, it, lud.order, &e); ++it)
+    lu32_element<false>(lu_elem(dm, lud, e), S, status, pivots, e, nullptr);
+}
+
+// Tensor-core form: TMEM (128 columns) and the completion barrier are set up once per
+// CTA; a CTA whose completion wait ran out stops taking elements, waits once more
+// (bounded) for its MMAs, and frees its TMEM.
+__global__ void __launch_bounds__(LU_THREADS, 2)
+k_lu32_tc(Dims dm, LuDesc lud, float* __restrict__ S, int8_t* __restrict__ status, int* __restrict__ pivots,
+          int64_t* queue, int64_t E, int* err) {
+  __shared__ uint32_t tmem_base;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ TcState tcs;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) {
+    tc::tmem_alloc(&tmem_base, 128);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) tc::mbar_init(&mbar, 1);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (tid == 0) {
+    tcs.tmem = tmem_base;
+    tcs.mbar = &mbar;
+    tcs.phase = 0;
+    tcs.failed = 0;
+  }
+  __syncthreads();
+  // each thread keeps its own copy of the phase; the shared copy is only the start
+  TcState mine = tcs;
+  int64_t e;
+  for (int64_t it = 0; next_element(queue, E, it, lud.order, &e); ++it) {
+    lu32_element<true>(lu_elem(dm, lud, e), S, status, pivots, e, &mine);
+    if (__syncthreads_or(mine.failed)) {
+      if (tid == 0) atomicOr(err, 1);
+      tc::mbar_wait(&mbar, mine.phase ^ 1u, 1 << 26);   // let the last MMAs drain
+      break;
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem_base, 128);
 }
 
 }  // namespace
@@ -567,12 +755,16 @@ template <class T>
 static cudaError_t assemble_t(iedg_mesh* M, T* S, const double* rhs64, const AsmTab<T>& tb, cudaStream_t st) {
   const Dims& dm = M->dm;
   AsmCfg cf = asm_cfg(dm);
-  size_t smem = sizeof(T) * ((size_t)cf.KC * cf.rows_pad + (size_t)cf.KC * cf.CW +
-                             (size_t)dm.Nb * cf.CW + (size_t)dm.Nfq * cf.CW);
+  const bool mix = M->tt.nb != nullptr;
+  int inner = 1;
+  for (int r = 0; r < dm.d; ++r) inner *= dm.p - 1;
+  const int nbu = dm.Np - inner;                  // boundary nodes of the element
+  size_t smem = sizeof(T) * ((size_t)cf.KC * cf.rows_pad + (size_t)cf.KC * cf.CW + (size_t)nbu * cf.CW +
+                             (size_t)dm.Nfq * cf.CW + (mix ? (size_t)dm.Nb * cf.CW : 0));
   cudaError_t err = cudaFuncSetAttribute(k_assemble<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   dim3 grid((unsigned)(M->E * dm.m * dm.m), cf.nsplit);
-  k_assemble<T><<<grid, AS_THREADS, smem, st>>>(dm, M->ph, cf, M->ref, tb, S, rhs64);
+  k_assemble<T><<<grid, AS_THREADS, smem, st>>>(dm, M->ph, cf, M->ref, tb, S, rhs64, M->tt, nbu);
   return cudaGetLastError();
 }
 
@@ -618,9 +810,9 @@ static cudaError_t lu_t(iedg_mesh* M, T* S, int* piv, cudaStream_t st) {
     err = persistent_grid(k_lu<T, NB>, smem, M->E, &grid);
     if (err == cudaSuccess) err = cudaMemsetAsync(M->queue, 0, sizeof(int64_t), st);
     if (err != cudaSuccess) return err;
-    k_lu<T, NB><<<grid, LU_THREADS, smem, st>>>(dm, S, M->status, piv, M->queue, M->E);
+    k_lu<T, NB><<<grid, LU_THREADS, smem, st>>>(dm, M->lud, S, M->status, piv, M->queue, M->E);
   } else {
-    k_lu<T, NB><<<(unsigned)M->E, LU_THREADS, smem, st>>>(dm, S, M->status, piv, nullptr, M->E);
+    k_lu<T, NB><<<(unsigned)M->E, LU_THREADS, smem, st>>>(dm, M->lud, S, M->status, piv, nullptr, M->E);
   }
   return cudaGetLastError();
 }
@@ -633,6 +825,22 @@ cudaError_t launch_lu(iedg_mesh* M, cudaStream_t st) {
     return lu_t<double, 16>(M, M->S, nullptr, st);
   }
   const Dims& dm = M->dm;
+  if (M->sched.lu_tensor) {
+    size_t smem = sizeof(float) * (size_t)L32_NB * dm.n;
+    if (smem < 65536) smem = 65536;                      // operand tiles reuse the panel buffer
+    cudaError_t err = cudaFuncSetAttribute(k_lu32_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    unsigned grid = (unsigned)M->E;
+    int64_t* queue = nullptr;
+    if (M->sched.lu_persistent) {
+      err = persistent_grid(k_lu32_tc, smem, M->E, &grid);
+      if (err == cudaSuccess) err = cudaMemsetAsync(M->queue, 0, sizeof(int64_t), st);
+      if (err != cudaSuccess) return err;
+      queue = M->queue;
+    }
+    k_lu32_tc<<<grid, LU_THREADS, smem, st>>>(dm, M->lud, M->S32, M->status, M->piv, queue, M->E, M->dev_flag);
+    return cudaGetLastError();
+  }
   size_t smem = sizeof(float) * ((size_t)L32_NB * dm.n + (size_t)L32_NB * L32_UCW);
   cudaError_t err = cudaFuncSetAttribute(k_lu32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
@@ -641,9 +849,9 @@ cudaError_t launch_lu(iedg_mesh* M, cudaStream_t st) {
     err = persistent_grid(k_lu32, smem, M->E, &grid);
     if (err == cudaSuccess) err = cudaMemsetAsync(M->queue, 0, sizeof(int64_t), st);
     if (err != cudaSuccess) return err;
-    k_lu32<<<grid, LU_THREADS, smem, st>>>(dm, M->S32, M->status, M->piv, M->queue, M->E);
+    k_lu32<<<grid, LU_THREADS, smem, st>>>(dm, M->lud, M->S32, M->status, M->piv, M->queue, M->E);
   } else {
-    k_lu32<<<(unsigned)M->E, LU_THREADS, smem, st>>>(dm, M->S32, M->status, M->piv, nullptr, M->E);
+    k_lu32<<<(unsigned)M->E, LU_THREADS, smem, st>>>(dm, M->lud, M->S32, M->status, M->piv, nullptr, M->E);
   }
   return cudaGetLastError();
 }

@@ -12,6 +12,13 @@
 // column at p = 3.  Pairs (i, k) whose viscous Jacobian vanishes identically (the
 // mass equation, and momentum equations with respect to the energy unknown) have no
 // volume trace columns and skip the lifted-gradient terms.
+//
+// Meshes with mixed orders (MIX): the element has n_b,e trace slots and its matrix sits
+// at its own offset with its own leading dimension.  The trace basis on a face shared
+// with the same order is the element basis there (trace rows = face parts of the
+// boundary u-rows restricted to those faces); a face with private nodes of degree q
+// has the degree-q Gauss-Lobatto Lagrange basis, contracted in two 1D stages like the
+// element basis.
 #include "iedg_internal.cuh"
 
 namespace iedg {
@@ -20,12 +27,14 @@ namespace {
 constexpr int SF_THREADS = 256;
 
 template <class T, int CC>
-size_t sf_smem(const Dims& dm) {
+size_t sf_smem(const Dims& dm, bool mix) {
   const int nq1 = dm.nq1, np1 = dm.np1, d = 3;
+  const int nbu = dm.Np - (np1 - 2) * (np1 - 2) * (np1 - 2);
   size_t n = 2 * (size_t)nq1 * np1                                   // L, L'
              + (size_t)(1 + d) * d * dm.Nq + (size_t)(2 + d) * dm.Nfp  // pair coefficients
              + 3 * (size_t)dm.Nq * CC + 3 * (size_t)nq1 * nq1 * np1 * CC + 2 * (size_t)nq1 * np1 * np1 * CC
-             + (size_t)dm.Nb * CC + (size_t)dm.Nfq * CC + (size_t)nq1 * np1 * CC;
+             + (size_t)nbu * CC + (size_t)dm.Nfq * CC + (size_t)nq1 * np1 * CC;
+  if (mix) n += (size_t)dm.Nb * CC + (size_t)nq1 * (5 - np1) * CC + 25 * (size_t)nq1;   // tacc, wider Uf, LQ
   return n * sizeof(T);
 }
 
@@ -36,20 +45,25 @@ size_t sf_smem(const Dims& dm) {
 // group instead of one load per multiply-add.  Face terms are contracted by two 1D
 // stages over the face's tangential directions (face point gf = g1 + nq1 g2, face
 // node tn = a1 + np1 a2, the face-normal factor of the basis being 1 on the face).
-template <class T, int NP1, int NQ1, int CC>
+template <class T, int NP1, int NQ1, int CC, bool MIX>
 __global__ void __launch_bounds__(SF_THREADS)
-k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, const double* __restrict__ rhs64) {
+k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, const double* __restrict__ rhs64,
+              TraceTab tt) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
   const int tid = threadIdx.x;
   constexpr int m = 5, m2 = 25, d = 3;
   constexpr int np1 = NP1, nq1 = NQ1;
   constexpr int Np = NP1 * NP1 * NP1, Nq = NQ1 * NQ1 * NQ1, Nfq = NQ1 * NQ1, Nfn = NP1 * NP1;
-  constexpr int Nb = Np - (NP1 - 2) * (NP1 - 2) * (NP1 - 2), Nfp = 6 * Nfq, ncol_all = Np + Nb;
+  constexpr int NbU = Np - (NP1 - 2) * (NP1 - 2) * (NP1 - 2), Nfp = 6 * Nfq;
   constexpr int TS = nq1 * nq1 * np1, VS = nq1 * np1 * np1, NC = (1 + d) * d;
+  constexpr int UW = MIX ? 5 : np1;              // second extent of the face stage buffer
   const int64_t e = blockIdx.x / m2;
   const int pair = blockIdx.x % m2, i = pair / m, k = pair % m;
   const bool has_cq = !(i == 0 || (i <= d && k == m - 1));
+  const int Nb = MIX ? tt.nb[e] : NbU;          // trace slots of this element
+  const int NbT = MIX ? dm.Nb : NbU;            // slot stride of the lifting tables
+  const int ncol_all = Np + Nb;
   const int ncol_vol = has_cq ? Np + Nb : Np;
   T* sL = sm;                                  // [nq1][np1]
   T* sdL = sL + nq1 * np1;                     // [nq1][np1]
@@ -59,10 +73,24 @@ k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, 
   T* W = cL + Nfp;                             // [3][Nq][CC]
   T* Tt = W + 3 * Nq * CC;                     // [3][TS][CC]
   T* V = Tt + 3 * TS * CC;                     // [2][VS][CC]
-  T* facc = V + 2 * VS * CC;                   // [Nb][CC]
-  T* Vf = facc + Nb * CC;                      // [Nfq][CC]
-  T* Uf = Vf + Nfq * CC;                       // [nq1 np1][CC]
+  T* facc = V + 2 * VS * CC;                   // [NbU][CC]  face parts of the boundary u-rows
+  T* Vf = facc + NbU * CC;                     // [Nfq][CC]
+  T* Uf = Vf + Nfq * CC;                       // [nq1 UW][CC]
+  T* tacc = MIX ? Uf + nq1 * UW * CC : facc;   // [Nb][CC]   trace rows (MIX), else = facc
+  T* sLQ = tacc + (MIX ? dm.Nb * CC : 0);      // [5][nq1][5] (MIX)
   for (int idx = tid; idx < nq1 * np1; idx += SF_THREADS) { sL[idx] = (T)ref.L1[idx]; sdL[idx] = (T)ref.dL1[idx]; }
+  if (MIX) {
+    const T* lq = nullptr;
+    if constexpr (sizeof(T) == 8) lq = reinterpret_cast<const T*>(ref.LQ);
+    else lq = reinterpret_cast<const T*>(ref.LQ32);
+    for (int idx = tid; idx < 25 * nq1; idx += SF_THREADS) sLQ[idx] = lq[idx];
+  }
+  const T* mutab = nullptr;                    // [nf][Nfq][NFS] of this element (MIX)
+  if (MIX) {
+    if constexpr (sizeof(T) == 8) mutab = reinterpret_cast<const T*>(tt.muf);
+    else mutab = reinterpret_cast<const T*>(tt.muf32);
+    mutab += (size_t)e * 6 * Nfq * tt.NFS;
+  }
   const size_t jvs = (size_t)NC * Nq, jfs = (size_t)(1 + d) * Nfp;
   const T* jv = tb.Jv + ((size_t)e * m2 + pair) * jvs;
   const T* jf = tb.Jf + ((size_t)e * m2 + pair) * jfs;
@@ -70,21 +98,26 @@ k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, 
   for (int idx = tid; idx < (1 + d) * Nfp; idx += SF_THREADS) cF[idx] = jf[idx];
   for (int idx = tid; idx < Nfp; idx += SF_THREADS) cL[idx] = (i == k) ? tb.lamw[e * Nfp + idx] : (T)0;
   const T* GlV = tb.GlV + (size_t)e * d * Nq * Np;
-  const T* HlV = tb.HlV + (size_t)e * d * Nq * Nb;
+  const T* HlV = tb.HlV + (size_t)e * d * Nq * NbT;
   const T* GlF = tb.GlF + (size_t)e * d * Nfp * Np;
-  const T* HlF = tb.HlF + (size_t)e * d * Nfp * Nb;
+  const T* HlF = tb.HlF + (size_t)e * d * Nfp * NbT;
   const T* Ms = tb.Mass + (size_t)e * Np * Np;
   const T alpha = (T)ph.alpha;
-  const int64_t nn = dm.n, ld = dm.ld;
-  T* Se = S + e * nn * ld;
+  const int64_t nn = MIX ? (int64_t)dm.nu + (int64_t)m * Nb : dm.n;
+  const int64_t ld = MIX ? tt.ldv[e] : dm.ld;
+  T* Se = MIX ? S + tt.soff[e] : S + e * nn * ld;
   if (rhs64 != nullptr && pair == 0)
-    for (int r = tid; r < nn; r += SF_THREADS) Se[r * ld + nn] = (T)rhs64[e * nn + r];
+    for (int r = tid; r < nn; r += SF_THREADS) Se[r * ld + nn] = (T)rhs64[e * dm.n + r];
   __syncthreads();
 
   for (int c0 = 0; c0 < ncol_all; c0 += CC) {
     // ---- face parts of the boundary rows for this column chunk
-    for (int idx = tid; idx < Nb * CC; idx += SF_THREADS) facc[idx] = (T)0;
+    for (int idx = tid; idx < NbU * CC; idx += SF_THREADS) facc[idx] = (T)0;
+    if (MIX)
+      for (int idx = tid; idx < Nb * CC; idx += SF_THREADS) tacc[idx] = (T)0;
     for (int f = 0; f < 6; ++f) {
+      const int fq = MIX ? tt.fdeg[e * 6 + f] : 0;
+      const int* fsf = MIX ? tt.fs + ((size_t)e * 6 + f) * tt.NFS : nullptr;
       __syncthreads();
       for (int idx = tid; idx < Nfq * CC; idx += SF_THREADS) {
         const int gf = idx / CC, c = idx % CC, col = c0 + c;
@@ -96,27 +129,59 @@ k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, 
             for (int l = 0; l < d; ++l) v -= cF[(1 + l) * Nfp + fp] * GlF[((size_t)l * Nfp + fp) * Np + col];
         } else if (col < ncol_all) {
           const int t = col - Np;
-          v = cF[fp] * tb.PhiF[(size_t)fp * Np + ref.bnode[t]];
+          T mu = 0;
+          if (MIX) {
+            const int* fl = tt.sfl + ((size_t)e * dm.Nb + t) * 3;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+              const int code = fl[q];
+              if (code >= 0 && code / tt.NFS == f) mu = mutab[((size_t)f * Nfq + gf) * tt.NFS + code % tt.NFS];
+            }
+          } else {
+            mu = tb.PhiF[(size_t)fp * Np + ref.bnode[t]];
+          }
+          v = cF[fp] * mu;
           if (has_cq)
-            for (int l = 0; l < d; ++l) v += cF[(1 + l) * Nfp + fp] * HlF[((size_t)l * Nfp + fp) * Nb + t];
+            for (int l = 0; l < d; ++l) v += cF[(1 + l) * Nfp + fp] * HlF[((size_t)l * Nfp + fp) * NbT + t];
         }
         Vf[gf * CC + c] = v;
       }
       __syncthreads();
+      if (MIX && fq > 0) {
+        // trace rows of the face's private nodes j = j1 + (q+1) j2:
+        // sum_{g1,g2} LQ_q[g1][j1] LQ_q[g2][j2] Vf[g1 + nq1 g2]
+        const int q1 = fq + 1;
+        const T* Lq = sLQ + fq * nq1 * 5;
+        for (int idx = tid; idx < nq1 * q1 * CC; idx += SF_THREADS) {
+          const int t = idx / CC, c = idx % CC, g1 = t % nq1, j2 = t / nq1;
+          T u = 0;
+          for (int g2 = 0; g2 < nq1; ++g2) u = fma(Lq[g2 * 5 + j2], Vf[(g1 + nq1 * g2) * CC + c], u);
+          Uf[(g1 * UW + j2) * CC + c] = u;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < q1 * q1 * CC; idx += SF_THREADS) {
+          const int j = idx / CC, c = idx % CC, j1 = j % q1, j2 = j / q1;
+          T s = 0;
+          for (int g1 = 0; g1 < nq1; ++g1) s = fma(Lq[g1 * 5 + j1], Uf[(g1 * UW + j2) * CC + c], s);
+          tacc[fsf[j] * CC + c] += s;
+        }
+        __syncthreads();
+      }
       // U[g1][a2] = sum_g2 L[g2][a2] Vf[g1 + nq1 g2]
       for (int idx = tid; idx < nq1 * np1 * CC; idx += SF_THREADS) {
         const int t = idx / CC, c = idx % CC, g1 = t % nq1, a2 = t / nq1;
         T u = 0;
         for (int g2 = 0; g2 < nq1; ++g2) u = fma(sL[g2 * np1 + a2], Vf[(g1 + nq1 * g2) * CC + c], u);
-        Uf[(g1 * np1 + a2) * CC + c] = u;
+        Uf[(g1 * UW + a2) * CC + c] = u;
       }
       __syncthreads();
       // node (a1, a2) of the face: sum_g1 L[g1][a1] U[g1][a2]
       for (int idx = tid; idx < Nfn * CC; idx += SF_THREADS) {
         const int tn = idx / CC, c = idx % CC, a1 = tn % np1, a2 = tn / np1;
         T s = 0;
-        for (int g1 = 0; g1 < nq1; ++g1) s = fma(sL[g1 * np1 + a1], Uf[(g1 * np1 + a2) * CC + c], s);
+        for (int g1 = 0; g1 < nq1; ++g1) s = fma(sL[g1 * np1 + a1], Uf[(g1 * UW + a2) * CC + c], s);
         facc[ref.slot[ref.fnode[f * Nfn + tn]] * CC + c] += s;
+        if (MIX && fq == 0) tacc[fsf[tn] * CC + c] += s;   // continuous face: same sums, trace rows
       }
     }
     // ---- volume right operands W_r[g][c] for the three reference directions
@@ -137,7 +202,7 @@ k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, 
           }
       } else if (col < ncol_vol) {
         for (int l = 0; l < d; ++l) {
-          const T hv = HlV[((size_t)l * Nq + g) * Nb + (col - Np)];
+          const T hv = HlV[((size_t)l * Nq + g) * NbT + (col - Np)];
           w0 += cV[(d + l * d + 0) * Nq + g] * hv;
           w1 += cV[(d + l * d + 1) * Nq + g] * hv;
           w2 += cV[(d + l * d + 2) * Nq + g] * hv;
@@ -197,7 +262,7 @@ k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, 
       const int sl = idx / CC, c = idx % CC, col = c0 + c;
       if (col >= ncol_all) continue;
       const int64_t cs = col < Np ? (int64_t)k * Np + col : (int64_t)dm.nu + (int64_t)k * Nb + (col - Np);
-      Se[((int64_t)dm.nu + (int64_t)i * Nb + sl) * ld + cs] = facc[sl * CC + c];
+      Se[((int64_t)dm.nu + (int64_t)i * Nb + sl) * ld + cs] = tacc[sl * CC + c];
     }
     __syncthreads();
   }
@@ -208,11 +273,12 @@ k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, 
 template <class T, int NP1, int NQ1, int CC>
 static cudaError_t assemble_sf_t(iedg_mesh* M, T* S, const double* rhs64, const AsmTab<T>& tb, cudaStream_t st) {
   const Dims& dm = M->dm;
-  size_t smem = sf_smem<T, CC>(dm);
-  auto kern = k_assemble_sf<T, NP1, NQ1, CC>;
+  const bool mix = M->tt.nb != nullptr;
+  size_t smem = sf_smem<T, CC>(dm, mix);
+  auto kern = mix ? k_assemble_sf<T, NP1, NQ1, CC, true> : k_assemble_sf<T, NP1, NQ1, CC, false>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  kern<<<(unsigned)(M->E * dm.m * dm.m), SF_THREADS, smem, st>>>(dm, M->ph, M->ref, tb, S, rhs64);
+  kern<<<(unsigned)(M->E * dm.m * dm.m), SF_THREADS, smem, st>>>(dm, M->ph, M->ref, tb, S, rhs64, M->tt);
   return cudaGetLastError();
 }
 
@@ -222,8 +288,9 @@ static cudaError_t assemble_sf_t(iedg_mesh* M, T* S, const double* rhs64, const 
 template <class T, int NP1, int NQ1>
 static cudaError_t assemble_sf_c(iedg_mesh* M, T* S, const double* rhs64, const AsmTab<T>& tb, cudaStream_t st) {
   int cc = M->sched.asm_chunk ? M->sched.asm_chunk : (sizeof(T) == 8 ? 8 : 16);
-  if (cc == 32 && sf_smem<T, 32>(M->dm) > 227 * 1024) cc = 16;
-  if (cc == 16 && sf_smem<T, 16>(M->dm) > 227 * 1024) cc = 8;
+  const bool mix = M->tt.nb != nullptr;
+  if (cc == 32 && sf_smem<T, 32>(M->dm, mix) > 227 * 1024) cc = 16;
+  if (cc == 16 && sf_smem<T, 16>(M->dm, mix) > 227 * 1024) cc = 8;
   if (cc == 32) return assemble_sf_t<T, NP1, NQ1, 32>(M, S, rhs64, tb, st);
   if (cc == 16) return assemble_sf_t<T, NP1, NQ1, 16>(M, S, rhs64, tb, st);
   return assemble_sf_t<T, NP1, NQ1, 8>(M, S, rhs64, tb, st);

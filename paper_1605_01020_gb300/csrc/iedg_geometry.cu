@@ -23,7 +23,7 @@ __device__ inline double cofactor3(const double J[3][3], int i, int r) {
 
 // One CTA per element.
 __global__ void k_geometry(Dims dm, RefTables ref, Geo G, const double* __restrict__ X,
-                           double* __restrict__ scratch, int* flag) {
+                           double* __restrict__ scratch, int* flag, TraceTab tt) {
   extern __shared__ double sm[];
   const int e = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
   const int d = dm.d, Np = dm.Np, Nq = dm.Nq, Nb = dm.Nb, Nfp = dm.Nfp, Nfq = dm.Nfq;
@@ -104,6 +104,22 @@ __global__ void k_geometry(Dims dm, RefTables ref, Geo G, const double* __restri
         for (int r = 0; r < d; ++r) gp += ref.Dxi[((size_t)r * Nq + g) * Np + a] * sJi[(g * d + r) * d + l];
         s += sW[g] * gp * ref.Phi[(size_t)g * Np + c];
       }
+    } else if (tt.sfl) {
+      // mixed orders: the slot's basis on each face it lives on (none for padding slots)
+      const int t = c - Np;
+      if (t < tt.nb[e]) {
+        const int* fl = tt.sfl + ((size_t)e * Nb + t) * 3;
+        for (int k = 0; k < 3; ++k) {
+          const int code = fl[k];
+          if (code < 0) continue;
+          const int f = code / tt.NFS, j = code % tt.NFS;
+          const double* mu = tt.muf + ((size_t)e * dm.nf + f) * Nfq * tt.NFS + j;
+          for (int gf = 0; gf < Nfq; ++gf) {
+            const int fp = f * Nfq + gf;
+            s += sfw[fp] * sfn[fp * d + l] * ref.PhiF[(size_t)fp * Np + a] * mu[(size_t)gf * tt.NFS];
+          }
+        }
+      }
     } else {
       int bt = ref.bnode[c - Np];
       for (int fp = 0; fp < Nfp; ++fp)
@@ -177,7 +193,7 @@ cudaError_t launch_geometry(iedg_mesh* M, const double* X, double* scratch, cuda
                                   (size_t)dm.Nfp * dm.d + (size_t)dm.Np * dm.Np + dm.Np);
   cudaError_t e = cudaFuncSetAttribute(k_geometry, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_geometry<<<(unsigned)M->E, 256, smem, st>>>(dm, M->ref, M->geo, X, scratch, M->dev_flag);
+  k_geometry<<<(unsigned)M->E, 256, smem, st>>>(dm, M->ref, M->geo, X, scratch, M->dev_flag, M->tt);
   return cudaGetLastError();
 }
 

@@ -30,6 +30,7 @@ struct Schedule {
   int lu_persistent = 1;     // batched LU as a persistent grid with an element queue
   int lu_panel = 16;         // FP64 LU panel width (16 or 32; 32 only when it fits shared memory)
   int asm_chunk = 0;         // assembly column chunk (0 = default: 8 for FP64, 16 for FP32)
+  int lu_tensor = 1;         // FP32 LU trailing update on tcgen05 (3xTF32) instead of FFMA
 };
 
 // Reference-element tables (device), shared by all elements.
@@ -45,6 +46,9 @@ struct RefTables {
   int* fnode;     // [nf][Nfn] nodes of each face
   double* L1;     // [nq1][np1] 1D Lagrange basis at the 1D Gauss points
   double* dL1;    // [nq1][np1] its derivative
+  double* LQ;     // [5][nq1][5] degree-q Gauss-Lobatto Lagrange basis at the 1D Gauss points
+                  //              (private face nodes of meshes with mixed orders)
+  float* LQ32;
   float* Phi32;   // FP32 copies for the mixed path (FP64 -> FP32 conversion is slow on GB300)
   float* Dxi32;
   float* PhiF32;
@@ -73,6 +77,45 @@ struct PointJac {
   double* Jf;     // [E][m][m][1+d][Nfp]   : c=0: wf dfhat/duhat ; c=1+l: wf dfhat/dq_l
   double* lamw;   // [E][Nfp]              : wf lambda  (dfhat/du = lambda I)
   float *Jv32, *Jf32, *lamw32;   // FP32 copies written by the point kernel (mixed path only)
+};
+
+// Per-element trace description of meshes with mixed orders.  A face shared with an
+// element of the same order carries the continuous trace of the uniform case (the
+// element basis restricted to the face, slots = its boundary nodes on such faces); a
+// face shared with another order carries (q+1)^(d-1) private nodes of degree q at the
+// Gauss-Lobatto points of the face (first tangential direction fastest).  All pointers
+// are null for uniform meshes.
+struct TraceTab {
+  const int* nb = nullptr;         // [E] trace slots of each element (<= Dims.Nb)
+  const int* nfs = nullptr;        // [E][nf] slots whose basis function is nonzero on each face
+  const int* fs = nullptr;         // [E][nf][NFS] those slots (continuous face: in face-node order)
+  const int* fdeg = nullptr;       // [E][nf] 0 = continuous face, q = private nodes of degree q
+  const double* muf = nullptr;     // [E][nf][Nfq][NFS] their values at the face points
+  const float* muf32 = nullptr;
+  const int* sfl = nullptr;        // [E][Nb][3] faces of each slot, f NFS + j (-1 = none)
+  const int64_t* soff = nullptr;   // [E] offset of the element's bordered matrix in S
+  const int* ldv = nullptr;        // [E] its leading dimension
+  int NFS = 0;
+};
+
+// Per-element sizes of the batched LU (null pointers: every element has the sizes of
+// Dims and sits at e n ld).  order lists the elements in the order the persistent
+// grid takes them (largest first).
+struct LuDesc {
+  const int64_t* soff = nullptr;
+  const int* n = nullptr;
+  const int* nu = nullptr;
+  const int* ld = nullptr;
+  const int64_t* poff = nullptr;   // pivot offsets (mixed path)
+  const int64_t* order = nullptr;
+};
+
+// Location of the per-slot values of a ragged source: value (e, s, i) at
+// base[e] + s ss[e] + i cs[e].
+struct RaggedSrc {
+  const int64_t* base = nullptr;
+  const int* ss = nullptr;
+  const int* cs = nullptr;
 };
 
 // Tables of one precision for the assembly kernels (the FP32 set is converted once
@@ -113,6 +156,22 @@ struct iedg_mesh {
   double* re64 = nullptr;       // [E][m][Nb]    refined R_e (component-major)
   int8_t* status = nullptr;     // [E]
   int64_t* queue = nullptr;     // element counter of persistent launches
+  // meshes with mixed orders: the parent handle holds the trace space, the ragged
+  // element matrices and the per-element sizes; one child handle per order holds the
+  // element tables of that order (internal element ids are grouped by order)
+  iedg::TraceTab tt;            // child: trace description of its elements
+  bool mixed_orders = false;    // parent
+  std::vector<iedg_mesh*> groups;
+  std::vector<int64_t> gstart;  // parent: first internal id of each group
+  std::vector<int64_t> perm;    // parent: internal id of each user element
+  std::vector<int64_t> unode;   // parent: user node offset of each user element [E+1]
+  int64_t n_nodes = 0;          // parent: nodes of all elements
+  int64_t nb_pack = 0;          // parent: slot stride of the packed (e, s) gather entries
+  iedg::LuDesc lud;             // parent
+  iedg::RaggedSrc rs_rhat, rs_S, rs_re;   // parent: sources of the R scatter
+  const int* el_nb = nullptr;   // parent: [E] trace slots per element (internal order)
+  int64_t* gnode = nullptr;     // child: [E] user node offset of each element
+  double *xu = nullptr, *xuref = nullptr, *xq = nullptr, *xru = nullptr, *xrq = nullptr;  // child nodal buffers
   double* kry = nullptr;        // trace solve: Krylov basis [IEDG_MAX_RESTART+1][T m] + 2 work vectors
   double* dinv = nullptr;       // trace solve: inverted diagonal blocks [T][m][m]
   double* kpart = nullptr;      // trace solve: dot-product partial sums
@@ -151,6 +210,11 @@ AsmTab<double> tables64(const iedg_mesh* M);
 AsmTab<float> tables32(const iedg_mesh* M);
 cudaError_t launch_lu(iedg_mesh* M, cudaStream_t st);
 cudaError_t launch_scatter_K(iedg_mesh* M, double* K, cudaStream_t st);
+cudaError_t launch_scatter_R_ragged(iedg_mesh* M, const RaggedSrc& src, const double* base, double* R,
+                                    cudaStream_t st);
+// nodal arrays of a child: user layout [nodes][w] <-> child layout [E][Np][w]
+cudaError_t launch_nodal_copy(iedg_mesh* C, int w, const double* src, double* dst, bool to_child,
+                              cudaStream_t st);
 cudaError_t launch_scatter_R(iedg_mesh* M, const double* src, int64_t src_elem_stride,
                              int64_t src_slot_stride, int64_t src_comp_stride, double* R,
                              cudaStream_t st);

@@ -210,7 +210,7 @@ __global__ void k_points(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ,
                          const double* __restrict__ Q, const double* __restrict__ QS,
                          const double* __restrict__ UH, const double* __restrict__ UREF, bool jac,
                          double* __restrict__ RU, double* __restrict__ RHAT, double* __restrict__ RHS,
-                         int64_t rhs_es, int64_t rhs_rs) {
+                         int64_t rhs_es, int64_t rhs_rs, TraceTab tt) {
   constexpr int M = D + 2;
   extern __shared__ double sm[];
   const int64_t e = blockIdx.x;
@@ -233,7 +233,8 @@ __global__ void k_points(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ,
     sq[i] = Q[e * Np * M * D + i];
     sqs[i] = QS ? QS[e * Np * M * D + i] : sq[i];
   }
-  for (int i = tid; i < Nb * M; i += nth) {
+  const int nbe = tt.nb ? tt.nb[e] : Nb;         // trace slots of this element
+  for (int i = tid; i < nbe * M; i += nth) {
     int s = i / M, k = i % M;
     suh[i] = UH[etrace[e * Nb + s] * M + k];
   }
@@ -324,18 +325,26 @@ __global__ void k_points(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ,
     const double* phi = ref.PhiF + (size_t)fp * Np;
     for (int t = 0; t < Nfn; ++t) {
       int a = ref.fnode[f * Nfn + t];
-      int s = ref.slot[a];
       double ph_a = phi[a];
 #pragma unroll
       for (int i = 0; i < M; ++i) {
         u[i] += ph_a * su[a * M + i];
-        uh[i] += ph_a * suh[s * M + i];
+        if (!tt.nfs) uh[i] += ph_a * suh[ref.slot[a] * M + i];
 #pragma unroll
         for (int j = 0; j < D; ++j) {
           q[i][j] += ph_a * sq[(a * M + i) * D + j];
           qr[i][j] += ph_a * sqs[(a * M + i) * D + j];
         }
       }
+    }
+    if (tt.nfs) {
+      // trace basis of this face from the element's table
+      const int cnt = tt.nfs[e * dm.nf + f];
+      const int* fsf = tt.fs + ((size_t)e * dm.nf + f) * tt.NFS;
+      const double* mu = tt.muf + (((size_t)e * dm.nf + f) * Nfq + (fp - f * Nfq)) * tt.NFS;
+      for (int j = 0; j < cnt; ++j)
+#pragma unroll
+        for (int i = 0; i < M; ++i) uh[i] += mu[j] * suh[fsf[j] * M + i];
     }
     const double wf = G.fw[e * Nfp + fp];
     double n[D];
@@ -386,7 +395,18 @@ __global__ void k_points(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ,
   __syncthreads();
   // ---- projections onto the test functions
   const double sgn = jac ? -1.0 : 1.0;
-  double* rhs_e = jac ? RHS + e * rhs_es : nullptr;
+  // right-hand side column: uniform meshes e * rhs_es, row stride rhs_rs; meshes with
+  // per-element sizes: column n_e of the element's bordered matrix
+  double* rhs_e = nullptr;
+  int64_t rrs = rhs_rs;
+  if (jac) {
+    if (tt.soff && rhs_rs != 1) {
+      rhs_e = RHS + tt.soff[e] + dm.nu + (int64_t)M * nbe;
+      rrs = tt.ldv[e];
+    } else {
+      rhs_e = RHS + e * rhs_es;
+    }
+  }
   for (int ai = tid; ai < Np * M; ai += nth) {
     const int a = ai / M, i = ai % M;
     double s = 0;
@@ -398,22 +418,33 @@ __global__ void k_points(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ,
     }
     if (ref.slot[a] >= 0)
       for (int fp = 0; fp < Nfp; ++fp) s += ref.PhiF[(size_t)fp * Np + a] * fsur[i * Nfp + fp];
-    if (jac) rhs_e[((int64_t)i * Np + a) * rhs_rs] = sgn * s;
+    if (jac) rhs_e[((int64_t)i * Np + a) * rrs] = sgn * s;
     else if (RU) RU[(e * Np + a) * M + i] = s;
   }
-  for (int si = tid; si < Nb * M; si += nth) {
+  for (int si = tid; si < nbe * M; si += nth) {
     const int s = si / M, i = si % M;
-    const int a = ref.bnode[s];
     double t = 0;
-    for (int fp = 0; fp < Nfp; ++fp) t += ref.PhiF[(size_t)fp * Np + a] * fsur[i * Nfp + fp];
-    if (jac) rhs_e[((int64_t)dm.nu + (int64_t)i * Nb + s) * rhs_rs] = sgn * t;
+    if (tt.nfs) {
+      const int* fl = tt.sfl + ((size_t)e * Nb + s) * 3;
+      for (int c = 0; c < 3; ++c) {
+        const int code = fl[c];
+        if (code < 0) continue;
+        const int f = code / tt.NFS, j = code % tt.NFS;
+        const double* mu = tt.muf + ((size_t)e * dm.nf + f) * Nfq * tt.NFS + j;
+        for (int gf = 0; gf < Nfq; ++gf) t += mu[(size_t)gf * tt.NFS] * fsur[i * Nfp + f * Nfq + gf];
+      }
+    } else {
+      const int a = ref.bnode[s];
+      for (int fp = 0; fp < Nfp; ++fp) t += ref.PhiF[(size_t)fp * Np + a] * fsur[i * Nfp + fp];
+    }
+    if (jac) rhs_e[((int64_t)dm.nu + (int64_t)i * nbe + s) * rrs] = sgn * t;
     else RHAT[(e * Nb + s) * M + i] = t;
   }
 }
 
 // q*[e][c][k][l] = sum_t H_l[c][t] uhat_k(t) - sum_b G_l[c][b] u_k(b)
 __global__ void k_lift(Dims dm, Geo G, const int64_t* __restrict__ etrace, const double* __restrict__ U,
-                       const double* __restrict__ UH, double* __restrict__ QS) {
+                       const double* __restrict__ UH, double* __restrict__ QS, TraceTab tt) {
   extern __shared__ double sm[];
   const int64_t e = blockIdx.x;
   const int tid = threadIdx.x, nth = blockDim.x;
@@ -421,14 +452,15 @@ __global__ void k_lift(Dims dm, Geo G, const int64_t* __restrict__ etrace, const
   double* su = sm;            // [Np][m]
   double* suh = su + Np * m;  // [Nb][m]
   for (int i = tid; i < Np * m; i += nth) su[i] = U[e * Np * m + i];
-  for (int i = tid; i < Nb * m; i += nth) suh[i] = UH[etrace[e * Nb + i / m] * m + i % m];
+  const int nbe = tt.nb ? tt.nb[e] : Nb;
+  for (int i = tid; i < nbe * m; i += nth) suh[i] = UH[etrace[e * Nb + i / m] * m + i % m];
   __syncthreads();
   for (int idx = tid; idx < Np * m * d; idx += nth) {
     int c = idx / (m * d), k = (idx / d) % m, l = idx % d;
     const double* gl = G.Gl + (((size_t)e * d + l) * Np + c) * Np;
     const double* hl = G.Hl + (((size_t)e * d + l) * Np + c) * Nb;
     double s = 0;
-    for (int t = 0; t < Nb; ++t) s += hl[t] * suh[t * m + k];
+    for (int t = 0; t < nbe; ++t) s += hl[t] * suh[t * m + k];
     for (int b = 0; b < Np; ++b) s -= gl[b] * su[b * m + k];
     QS[e * Np * m * d + idx] = s;
   }
@@ -468,17 +500,18 @@ cudaError_t launch_points(iedg_mesh* M, const double* u, const double* q, const 
                                   (size_t)dm.m * dm.d * dm.Nq + dm.m * dm.Nq + dm.m * dm.Nfp);
   const int threads = 128;
   // right-hand sides: column n of the FP64 bordered matrix, or the FP64 rhs array
-  double* rhs = M->precision == 0 ? M->S + dm.n : M->rhs64;
+  // (ragged FP64 matrices: the kernel adds the element's offset and n_e to S itself)
+  double* rhs = M->precision == 0 ? (M->tt.soff ? M->S : M->S + dm.n) : M->rhs64;
   int64_t es = M->precision == 0 ? (int64_t)dm.n * dm.ld : dm.n;
   int64_t rs = M->precision == 0 ? dm.ld : 1;
   if (dm.d == 2) {
     cudaFuncSetAttribute(k_points<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_points<2><<<(unsigned)M->E, threads, smem, st>>>(dm, M->ph, M->ref, M->geo, M->pj, M->etrace, u, q,
-                                                       qs, uhat, u_ref, jacobians, r_u, rhat, rhs, es, rs);
+                                                       qs, uhat, u_ref, jacobians, r_u, rhat, rhs, es, rs, M->tt);
   } else {
     cudaFuncSetAttribute(k_points<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_points<3><<<(unsigned)M->E, threads, smem, st>>>(dm, M->ph, M->ref, M->geo, M->pj, M->etrace, u, q,
-                                                       qs, uhat, u_ref, jacobians, r_u, rhat, rhs, es, rs);
+                                                       qs, uhat, u_ref, jacobians, r_u, rhat, rhs, es, rs, M->tt);
   }
   return cudaGetLastError();
 }
@@ -486,7 +519,7 @@ cudaError_t launch_points(iedg_mesh* M, const double* u, const double* q, const 
 cudaError_t launch_lift(iedg_mesh* M, const double* u, const double* uhat, double* qstar, cudaStream_t st) {
   const Dims& dm = M->dm;
   size_t smem = sizeof(double) * (size_t)(dm.Np + dm.Nb) * dm.m;
-  k_lift<<<(unsigned)M->E, 128, smem, st>>>(dm, M->geo, M->etrace, u, uhat, qstar);
+  k_lift<<<(unsigned)M->E, 128, smem, st>>>(dm, M->geo, M->etrace, u, uhat, qstar, M->tt);
   return cudaGetLastError();
 }
 

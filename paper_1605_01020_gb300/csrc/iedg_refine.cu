@@ -66,11 +66,15 @@ __device__ double block_max(double v, double* red) {
 
 // ou = A~ x + B~ z (u-rows), ot = C~ x + D~ z (trace rows), all FP64.
 // use_x / use_z = false skip the terms of an operand that is identically zero.
+// z and ot are component-major with slot stride Nb = Dims.Nb; with mixed orders only
+// the element's first nb slots are used (the rest stay zero).
 __device__ void element_apply(const Dims& dm, const Phys& ph, const RefTables& ref, const Geo& G,
-                              const PointJac& PJ, int64_t e, Work& w, bool use_x, bool use_z) {
+                              const PointJac& PJ, const TraceTab& tt, int64_t e, Work& w, bool use_x,
+                              bool use_z) {
   const int tid = threadIdx.x;
   const int m = dm.m, d = dm.d, Np = dm.Np, Nb = dm.Nb, Nq = dm.Nq, Nfp = dm.Nfp, Nfq = dm.Nfq;
   const int Nfn = dm.Nfn;
+  const int nbe = tt.nb ? tt.nb[e] : Nb;
   // nodal lifted gradient of (x, z): dq_kl = -G_l x_k + H_l z_k.  One warp per row
   // (l, c) of G_l | H_l: the lanes read the row once, coalesced, for all m components.
   {
@@ -88,7 +92,7 @@ __device__ void element_apply(const Dims& dm, const Phys& ph, const RefTables& r
             if (k < m) acc[k] = fma(-g, w.x[k * Np + b], acc[k]);
         }
       if (use_z)
-        for (int t = lane; t < Nb; t += 32) {
+        for (int t = lane; t < nbe; t += 32) {
           const double h = hl[t];
 #pragma unroll
           for (int k = 0; k < 5; ++k)
@@ -151,6 +155,13 @@ __device__ void element_apply(const Dims& dm, const Phys& ph, const RefTables& r
     if ((row < m && !use_x) || (row >= m && row < 2 * m && !use_z)) continue;
     const double* phi = ref.PhiF + (size_t)fp * Np;
     double s = 0.0;
+    if (tt.nfs && row >= m && row < 2 * m) {
+      // trace basis of this face from the element's table
+      const int cnt = tt.nfs[e * dm.nf + f];
+      const int* fsf = tt.fs + ((size_t)e * dm.nf + f) * tt.NFS;
+      const double* mu = tt.muf + (((size_t)e * dm.nf + f) * Nfq + (fp - f * Nfq)) * tt.NFS;
+      for (int j = 0; j < cnt; ++j) s = fma(mu[j], w.z[(row - m) * Nb + fsf[j]], s);
+    } else
     for (int tn = 0; tn < Nfn; ++tn) {
       int a = ref.fnode[f * Nfn + tn];
       double v;
@@ -255,9 +266,23 @@ __device__ void element_apply(const Dims& dm, const Phys& ph, const RefTables& r
     w.ou[idx] = s;
   }
   for (int idx = tid; idx < m * Nb; idx += RF_THREADS) {
-    int i = idx / Nb, sl = idx % Nb, a = ref.bnode[sl];
+    int i = idx / Nb, sl = idx % Nb;
     double s = 0.0;
-    for (int fp = 0; fp < Nfp; ++fp) s = fma(ref.PhiF[(size_t)fp * Np + a], w.tf[i * Nfp + fp], s);
+    if (tt.sfl) {
+      if (sl < nbe) {
+        const int* fl = tt.sfl + ((size_t)e * Nb + sl) * 3;
+        for (int c = 0; c < 3; ++c) {
+          const int code = fl[c];
+          if (code < 0) continue;
+          const int f = code / tt.NFS, j = code % tt.NFS;
+          const double* mu = tt.muf + ((size_t)e * dm.nf + f) * Nfq * tt.NFS + j;
+          for (int gf = 0; gf < Nfq; ++gf) s = fma(mu[(size_t)gf * tt.NFS], w.tf[i * Nfp + f * Nfq + gf], s);
+        }
+      }
+    } else {
+      const int a = ref.bnode[sl];
+      for (int fp = 0; fp < Nfp; ++fp) s = fma(ref.PhiF[(size_t)fp * Np + a], w.tf[i * Nfp + fp], s);
+    }
     w.ot[idx] = s;
   }
   __syncthreads();
@@ -266,10 +291,10 @@ __device__ void element_apply(const Dims& dm, const Phys& ph, const RefTables& r
 // v <- A~32^-1 v with the FP32 factors (panel order, pivots as applied).  A correction
 // only needs FP32 accuracy (the residual it corrects is FP64), so the solve runs in
 // FP32 on a scaled copy of v held in f (nu floats, any free shared buffer).
-__device__ void solve32(const Dims& dm, const float* __restrict__ A, const int* __restrict__ piv, double* v,
+__device__ void solve32(const Dims& dm, const float* __restrict__ A, int ld, const int* __restrict__ piv, double* v,
                         float* f, double* red) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = RF_THREADS / 32;
-  const int nu = dm.nu, ld = dm.ld;
+  const int nu = dm.nu;
   double mx = 0.0;
   for (int i = tid; i < nu; i += RF_THREADS) mx = fmax(mx, fabs(v[i]));
   mx = block_max(mx, red);
@@ -332,17 +357,18 @@ __device__ void solve32(const Dims& dm, const float* __restrict__ A, const int* 
 // Solve A~ x = b (b in w.b) to FP64 accuracy; on return w.x = x and w.ou, w.ot hold
 // A~ x, C~ x for that x (w.z must be zero).  Returns the final relative residual.
 __device__ double refine_solve(const Dims& dm, const Phys& ph, const RefTables& ref, const Geo& G,
-                               const PointJac& PJ, int64_t e, const float* A, const int* piv, Work& w) {
+                               const PointJac& PJ, const TraceTab& tt, int64_t e, const float* A, int ld,
+                               const int* piv, Work& w) {
   const int tid = threadIdx.x, nu = dm.nu;
   double bn = 0.0;
   for (int i = tid; i < nu; i += RF_THREADS) { w.v[i] = w.b[i]; bn = fmax(bn, fabs(w.b[i])); }
   bn = block_max(bn, w.red);
-  solve32(dm, A, piv, w.v, reinterpret_cast<float*>(w.ou), w.red);
+  solve32(dm, A, ld, piv, w.v, reinterpret_cast<float*>(w.ou), w.red);
   for (int i = tid; i < nu; i += RF_THREADS) w.x[i] = w.v[i];
   __syncthreads();
   double rel = 0.0;
   for (int it = 0; it <= kRefineMaxIter; ++it) {
-    element_apply(dm, ph, ref, G, PJ, e, w, true, false);
+    element_apply(dm, ph, ref, G, PJ, tt, e, w, true, false);
     double rn = 0.0;
     for (int i = tid; i < nu; i += RF_THREADS) {
       double r = w.b[i] - w.ou[i];
@@ -352,7 +378,7 @@ __device__ double refine_solve(const Dims& dm, const Phys& ph, const RefTables& 
     rn = block_max(rn, w.red);
     rel = bn > 0.0 ? rn / bn : rn;
     if (!(rel > kRefineTol) || it == kRefineMaxIter) break;   // also stops on NaN
-    solve32(dm, A, piv, w.v, reinterpret_cast<float*>(w.ou), w.red);
+    solve32(dm, A, ld, piv, w.v, reinterpret_cast<float*>(w.ou), w.red);
     for (int i = tid; i < nu; i += RF_THREADS) w.x[i] += w.v[i];
     __syncthreads();
   }
@@ -361,7 +387,7 @@ __device__ double refine_solve(const Dims& dm, const Phys& ph, const RefTables& 
 
 // One CTA per element: y = A~^-1 F~ refined, R_e = G~ - C~ y.
 __global__ void __launch_bounds__(RF_THREADS, 2)
-k_refine(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ, const float* __restrict__ S32,
+k_refine(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ, TraceTab tt, const float* __restrict__ S32,
          const int* __restrict__ piv, const double* __restrict__ rhs64, double* __restrict__ y64,
          double* __restrict__ re64, int8_t* __restrict__ status) {
   extern __shared__ double sm[];
@@ -373,16 +399,22 @@ k_refine(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ, const float* __res
   for (int i = tid; i < dm.nu; i += RF_THREADS) w.b[i] = rhs[i];
   for (int i = tid; i < dm.nt; i += RF_THREADS) w.z[i] = 0.0;
   __syncthreads();
-  const float* A = S32 + e * (int64_t)dm.n * dm.ld;
-  double rel = refine_solve(dm, ph, ref, G, PJ, e, A, piv + e * dm.nu, w);
+  const float* A = S32 + (tt.soff ? tt.soff[e] : e * (int64_t)dm.n * dm.ld);
+  const int ld = tt.ldv ? tt.ldv[e] : dm.ld;
+  double rel = refine_solve(dm, ph, ref, G, PJ, tt, e, A, ld, piv + e * dm.nu, w);
   for (int i = tid; i < dm.nu; i += RF_THREADS) y64[e * dm.nu + i] = w.x[i];
-  for (int i = tid; i < dm.nt; i += RF_THREADS) re64[e * dm.nt + i] = rhs[dm.nu + i] - w.ot[i];
+  // trace rows of the right-hand side: packed by the element's slot count
+  const int nbe = tt.nb ? tt.nb[e] : dm.Nb;
+  for (int i = tid; i < dm.nt; i += RF_THREADS) {
+    const int c = i / dm.Nb, sl = i % dm.Nb;
+    re64[e * dm.nt + i] = sl < nbe ? rhs[dm.nu + c * nbe + sl] - w.ot[i] : 0.0;
+  }
   if (tid == 0 && !(rel <= kRefineFlag) && status[e] == IEDG_ELEM_OK) status[e] = IEDG_ELEM_REFINE;
 }
 
 // One CTA per element: du = A~^-1 (F~ - B~ dU_e) refined, dq = (q* - q) - G_l du + H_l dU_e.
 __global__ void __launch_bounds__(RF_THREADS, 2)
-k_backsub_mixed(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ, const int64_t* __restrict__ etrace,
+k_backsub_mixed(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ, TraceTab tt, const int64_t* __restrict__ etrace,
                 const float* __restrict__ S32, const int* __restrict__ piv, const double* __restrict__ rhs64,
                 const double* __restrict__ rhoq, const double* __restrict__ duhat, double* __restrict__ du,
                 double* __restrict__ dq) {
@@ -391,23 +423,25 @@ k_backsub_mixed(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ, const int64
   const int64_t e = blockIdx.x;
   const int tid = threadIdx.x;
   const int m = dm.m, d = dm.d, Np = dm.Np, Nb = dm.Nb;
+  const int nbe = tt.nb ? tt.nb[e] : Nb;
   for (int i = tid; i < dm.nq1 * dm.np1; i += RF_THREADS) { w.sL[i] = ref.L1[i]; w.sdL[i] = ref.dL1[i]; }
   for (int i = tid; i < dm.nu; i += RF_THREADS) w.x[i] = 0.0;
   for (int i = tid; i < dm.nt; i += RF_THREADS) {
     int k = i / Nb, t = i % Nb;
-    w.z[i] = duhat[etrace[e * Nb + t] * m + k];
+    w.z[i] = t < nbe ? duhat[etrace[e * Nb + t] * m + k] : 0.0;
   }
   __syncthreads();
-  element_apply(dm, ph, ref, G, PJ, e, w, false, true);  // ou = B~ dU_e
+  element_apply(dm, ph, ref, G, PJ, tt, e, w, false, true);  // ou = B~ dU_e
   const double* rhs = rhs64 + e * dm.n;
   for (int i = tid; i < dm.nu; i += RF_THREADS) w.b[i] = rhs[i] - w.ou[i];
   for (int i = tid; i < dm.nt; i += RF_THREADS) w.z[i] = 0.0;   // solve with z = 0
   __syncthreads();
-  const float* A = S32 + e * (int64_t)dm.n * dm.ld;
-  refine_solve(dm, ph, ref, G, PJ, e, A, piv + e * dm.nu, w);
+  const float* A = S32 + (tt.soff ? tt.soff[e] : e * (int64_t)dm.n * dm.ld);
+  const int ld = tt.ldv ? tt.ldv[e] : dm.ld;
+  refine_solve(dm, ph, ref, G, PJ, tt, e, A, ld, piv + e * dm.nu, w);
   for (int i = tid; i < dm.nt; i += RF_THREADS) {          // dU_e again, for dq
     int k = i / Nb, t = i % Nb;
-    w.z[i] = duhat[etrace[e * Nb + t] * m + k];
+    w.z[i] = t < nbe ? duhat[etrace[e * Nb + t] * m + k] : 0.0;
   }
   __syncthreads();
   for (int idx = tid; idx < Np * m; idx += RF_THREADS) {
@@ -420,7 +454,7 @@ k_backsub_mixed(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ, const int64
     const double* hl = G.Hl + (((size_t)e * d + l) * Np + c) * Nb;
     double s = -rhoq[e * Np * m * d + idx];
     for (int b = 0; b < Np; ++b) s = fma(-gl[b], w.x[k * Np + b], s);
-    for (int t = 0; t < Nb; ++t) s = fma(hl[t], w.z[k * Nb + t], s);
+    for (int t = 0; t < nbe; ++t) s = fma(hl[t], w.z[k * Nb + t], s);
     dq[e * Np * m * d + idx] = s;
   }
 }
@@ -432,7 +466,7 @@ cudaError_t launch_refine(iedg_mesh* M, cudaStream_t st) {
   size_t smem = sizeof(double) * work_doubles(dm);
   cudaError_t err = cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  k_refine<<<(unsigned)M->E, RF_THREADS, smem, st>>>(dm, M->ph, M->ref, M->geo, M->pj, M->S32, M->piv, M->rhs64,
+  k_refine<<<(unsigned)M->E, RF_THREADS, smem, st>>>(dm, M->ph, M->ref, M->geo, M->pj, M->tt, M->S32, M->piv, M->rhs64,
                                                       M->y64, M->re64, M->status);
   return cudaGetLastError();
 }
@@ -442,7 +476,7 @@ cudaError_t launch_backsub_mixed(iedg_mesh* M, const double* duhat, double* du, 
   size_t smem = sizeof(double) * work_doubles(dm);
   cudaError_t err = cudaFuncSetAttribute(k_backsub_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  k_backsub_mixed<<<(unsigned)M->E, RF_THREADS, smem, st>>>(dm, M->ph, M->ref, M->geo, M->pj, M->etrace, M->S32,
+  k_backsub_mixed<<<(unsigned)M->E, RF_THREADS, smem, st>>>(dm, M->ph, M->ref, M->geo, M->pj, M->tt, M->etrace, M->S32,
                                                              M->piv, M->rhs64, M->rhoq, duhat, du, dq);
   return cudaGetLastError();
 }

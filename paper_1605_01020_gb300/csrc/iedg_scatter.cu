@@ -8,24 +8,64 @@ namespace iedg {
 namespace {
 
 // One thread per (block, i, k) entry; S is the FP64 or the FP32 element matrix.
+// Contributions are packed as (e P + s) P + t, P = Nb (uniform meshes) or the slot
+// stride of meshes with mixed orders, whose matrices have per-element sizes (lud).
 template <class T>
-__global__ void k_scatter_K(Dims dm, int64_t nnzb, const int64_t* __restrict__ kc_ptr,
-                            const int64_t* __restrict__ kc_src, const T* __restrict__ S,
-                            double* __restrict__ K) {
+__global__ void k_scatter_K(Dims dm, int64_t nnzb, int64_t P, const int64_t* __restrict__ kc_ptr,
+                            const int64_t* __restrict__ kc_src, LuDesc lud, const int* __restrict__ nbv,
+                            const T* __restrict__ S, double* __restrict__ K) {
   const int m2 = dm.m * dm.m;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= nnzb * m2) return;
   const int64_t blk = idx / m2;
   const int i = (int)(idx % m2) / dm.m, k = (int)(idx % m2) % dm.m;
-  const int64_t Nb = dm.Nb, nb2 = Nb * Nb, ld = dm.ld, n = dm.n;
-  const int64_t row_off = dm.nu + (int64_t)i * Nb, col_off = dm.nu + (int64_t)k * Nb;
   double v = 0.0;
-  for (int64_t c = kc_ptr[blk]; c < kc_ptr[blk + 1]; ++c) {
-    int64_t src = kc_src[c];
-    int64_t e = src / nb2, s = (src / Nb) % Nb, t = src % Nb;
-    v += (double)S[(e * n + row_off + s) * ld + col_off + t];
+  if (lud.soff == nullptr) {
+    const int64_t Nb = dm.Nb, nb2 = Nb * Nb, ld = dm.ld, n = dm.n;
+    const int64_t row_off = dm.nu + (int64_t)i * Nb, col_off = dm.nu + (int64_t)k * Nb;
+    for (int64_t c = kc_ptr[blk]; c < kc_ptr[blk + 1]; ++c) {
+      int64_t src = kc_src[c];
+      int64_t e = src / nb2, s = (src / Nb) % Nb, t = src % Nb;
+      v += (double)S[(e * n + row_off + s) * ld + col_off + t];
+    }
+  } else {
+    for (int64_t c = kc_ptr[blk]; c < kc_ptr[blk + 1]; ++c) {
+      const int64_t src = kc_src[c];
+      const int64_t e = src / (P * P), s = (src / P) % P, t = src % P;
+      const int64_t nb = nbv[e], ld = lud.ld[e], nu = lud.nu[e];
+      v += (double)S[lud.soff[e] + (nu + i * nb + s) * ld + nu + k * nb + t];
+    }
   }
   K[idx] = v;
+}
+
+// Ragged form of k_scatter_R: contributions packed as e P + s, values located by src.
+__global__ void k_scatter_R_ragged(int m, int64_t T, int64_t P, const int64_t* __restrict__ rc_ptr,
+                                   const int64_t* __restrict__ rc_src, RaggedSrc rs,
+                                   const double* __restrict__ src, double* __restrict__ R) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= T * m) return;
+  const int64_t t = idx / m;
+  const int i = (int)(idx % m);
+  double v = 0.0;
+  for (int64_t c = rc_ptr[t]; c < rc_ptr[t + 1]; ++c) {
+    const int64_t es = rc_src[c];
+    const int64_t e = es / P, s = es % P;
+    v += src[rs.base[e] + s * rs.ss[e] + i * rs.cs[e]];
+  }
+  R[idx] = v;
+}
+
+// Nodal arrays between the user layout of a mesh with mixed orders (elements in user
+// order, each its own number of nodes) and a child's [E][Np][w] layout.
+__global__ void k_nodal_copy(int64_t E, int npw, int w, const int64_t* __restrict__ gnode,
+                             const double* __restrict__ src, double* __restrict__ dst, bool to_child) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= E * npw) return;
+  const int64_t e = idx / npw, r = idx % npw;
+  const int64_t ui = gnode[e] * w + r;
+  if (to_child) dst[idx] = src[ui];
+  else dst[ui] = src[idx];
 }
 
 // One thread per (trace node, component): R[t][i] = sum over (e, s) of src(e, s, i).
@@ -51,17 +91,20 @@ constexpr int BS_THREADS = 256;
 __global__ void __launch_bounds__(BS_THREADS)
 k_backsub(Dims dm, Geo G, const int64_t* __restrict__ etrace, const double* __restrict__ S,
           const double* __restrict__ rhoq, const double* __restrict__ duhat,
-          double* __restrict__ du, double* __restrict__ dq) {
+          double* __restrict__ du, double* __restrict__ dq, TraceTab tt) {
   extern __shared__ double sm[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = BS_THREADS / 32;
   const int64_t e = blockIdx.x;
-  const int n = dm.n, nu = dm.nu, nt = dm.nt, ld = dm.ld, m = dm.m, d = dm.d, Np = dm.Np, Nb = dm.Nb;
-  const double* A = S + e * (int64_t)n * ld;
+  const int m = dm.m, d = dm.d, Np = dm.Np, NbT = dm.Nb, nu = dm.nu;
+  const int Nb = tt.nb ? tt.nb[e] : NbT;      // this element's slots (mixed orders: ragged)
+  const int nt = m * Nb;
+  const int ld = tt.nb ? tt.ldv[e] : dm.ld;
+  const double* A = S + (tt.nb ? tt.soff[e] : e * (int64_t)dm.n * dm.ld);
   double* sU = sm;          // [nt]   dU_e, component-major (k Nb + t)
-  double* y = sU + nt;      // [nu]
+  double* y = sU + dm.nt;   // [nu]
   for (int idx = tid; idx < nt; idx += BS_THREADS) {
     int k = idx / Nb, t = idx % Nb;
-    sU[idx] = duhat[etrace[e * Nb + t] * m + k];
+    sU[idx] = duhat[etrace[e * NbT + t] * m + k];
   }
   __syncthreads();
   for (int r = warp; r < nu; r += nw) {
@@ -87,7 +130,7 @@ k_backsub(Dims dm, Geo G, const int64_t* __restrict__ etrace, const double* __re
   for (int idx = tid; idx < Np * m * d; idx += BS_THREADS) {
     int c = idx / (m * d), k = (idx / d) % m, l = idx % d;
     const double* gl = G.Gl + (((size_t)e * d + l) * Np + c) * Np;
-    const double* hl = G.Hl + (((size_t)e * d + l) * Np + c) * Nb;
+    const double* hl = G.Hl + (((size_t)e * d + l) * Np + c) * NbT;
     double s = -rhoq[e * Np * m * d + idx];
     for (int b = 0; b < Np; ++b) s = fma(-gl[b], y[k * Np + b], s);
     for (int t = 0; t < Nb; ++t) s = fma(hl[t], sU[k * Nb + t], s);
@@ -103,9 +146,30 @@ cudaError_t launch_scatter_K(iedg_mesh* M, double* K, cudaStream_t st) {
   const int th = 256;
   const unsigned grid = (unsigned)((total + th - 1) / th);
   if (M->precision == 0)
-    k_scatter_K<double><<<grid, th, 0, st>>>(M->dm, M->nnzb, M->kc_ptr, M->kc_src, M->S, K);
+    k_scatter_K<double><<<grid, th, 0, st>>>(M->dm, M->nnzb, M->nb_pack, M->kc_ptr, M->kc_src, M->lud, M->el_nb,
+                                              M->S, K);
   else
-    k_scatter_K<float><<<grid, th, 0, st>>>(M->dm, M->nnzb, M->kc_ptr, M->kc_src, M->S32, K);
+    k_scatter_K<float><<<grid, th, 0, st>>>(M->dm, M->nnzb, M->nb_pack, M->kc_ptr, M->kc_src, M->lud, M->el_nb,
+                                             M->S32, K);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_R_ragged(iedg_mesh* M, const RaggedSrc& rs, const double* src, double* R,
+                                    cudaStream_t st) {
+  const int64_t total = M->T * M->dm.m;
+  const int th = 256;
+  k_scatter_R_ragged<<<(unsigned)((total + th - 1) / th), th, 0, st>>>(M->dm.m, M->T, M->nb_pack, M->rc_ptr,
+                                                                        M->rc_src, rs, src, R);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nodal_copy(iedg_mesh* C, int w, const double* src, double* dst, bool to_child,
+                              cudaStream_t st) {
+  const int64_t total = C->E * C->dm.Np * w;
+  if (total == 0) return cudaSuccess;
+  const int th = 256;
+  k_nodal_copy<<<(unsigned)((total + th - 1) / th), th, 0, st>>>(C->E, C->dm.Np * w, w, C->gnode, src, dst,
+                                                                  to_child);
   return cudaGetLastError();
 }
 
@@ -121,7 +185,8 @@ cudaError_t launch_scatter_R(iedg_mesh* M, const double* src, int64_t es, int64_
 cudaError_t launch_backsub(iedg_mesh* M, const double* duhat, double* du, double* dq, cudaStream_t st) {
   const Dims& dm = M->dm;
   size_t smem = sizeof(double) * (size_t)(dm.nt + dm.nu);
-  k_backsub<<<(unsigned)M->E, BS_THREADS, smem, st>>>(dm, M->geo, M->etrace, M->S, M->rhoq, duhat, du, dq);
+  k_backsub<<<(unsigned)M->E, BS_THREADS, smem, st>>>(dm, M->geo, M->etrace, M->S, M->rhoq, duhat, du, dq,
+                                                      M->tt);
   return cudaGetLastError();
 }
 

@@ -33,6 +33,10 @@ extern "C" int iedg_eval_residual_static(iedg_mesh* M, const double* u, const do
     if (M) M->err = "iedg_eval_residual_static: u, uhat, q and r_fl are required";
     return IEDG_ERR_INVALID_ARG;
   }
+  if (M->mixed_orders) {
+    M->err = "iedg_eval_residual_static: meshes with mixed orders are not supported; use iedg_eval_residual";
+    return IEDG_ERR_UNSUPPORTED;
+  }
   const Dims& dm = M->dm;
   const int64_t need = M->E * (int64_t)dm.Nb * dm.m;
   if (need > (int64_t)IEDG_STATIC_SCRATCH_DOUBLES) {

@@ -19,7 +19,7 @@ EXPORTS = ("iedg_create_mesh", "iedg_destroy_mesh", "iedg_last_error", "iedg_mes
            "iedg_trace_pattern", "iedg_eval_residual", "iedg_assemble_condensed",
            "iedg_back_substitute", "iedg_element_status", "iedg_profile_enable",
            "iedg_profile_read", "iedg_profile_reset", "iedg_eval_residual_static", "iedg_get_schedule",
-           "iedg_set_schedule", "iedg_trace_solve")
+           "iedg_set_schedule", "iedg_trace_solve", "iedg_create_mesh_mixed", "iedg_element_sizes")
 
 
 class IedgError(RuntimeError):
@@ -39,7 +39,7 @@ class MeshDesc(ctypes.Structure):
 
 class Schedule(ctypes.Structure):
     _fields_ = [("lu_persistent", ctypes.c_int32), ("lu_panel", ctypes.c_int32), ("asm_chunk", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("lu_tensor", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 _lib = None
@@ -57,6 +57,10 @@ def load():
     vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
     lib.iedg_create_mesh.argtypes = [ctypes.POINTER(MeshDesc), vp, ctypes.POINTER(vp)]
     lib.iedg_create_mesh.restype = ctypes.c_int
+    lib.iedg_create_mesh_mixed.argtypes = [ctypes.POINTER(MeshDesc), vp, vp, vp, ctypes.POINTER(vp)]
+    lib.iedg_create_mesh_mixed.restype = ctypes.c_int
+    lib.iedg_element_sizes.argtypes = [vp, vp, vp]
+    lib.iedg_element_sizes.restype = ctypes.c_int
     lib.iedg_destroy_mesh.argtypes = [vp]
     lib.iedg_destroy_mesh.restype = ctypes.c_int
     lib.iedg_last_error.argtypes = [vp]
@@ -138,11 +142,24 @@ class Mesh:
         if rc != OK:
             raise IedgError(rc, lib.iedg_last_error(None).decode())
         self._h = h
-        np_, nb, nnzb, ws = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
-        self._check(lib.iedg_mesh_info(h, ctypes.byref(np_), ctypes.byref(nb), ctypes.byref(nnzb), ctypes.byref(ws)))
-        self.Np, self.Nb, self.nnzb, self.workspace_bytes = np_.value, nb.value, nnzb.value, ws.value
+        self._info()
         if self.Np != self.Np_in or ET.shape != (self.E, self.Nb):
             raise ValueError("node_xyz / elem_trace shapes do not match the order")
+        self._ushape = (self.E, self.Np, self.m)
+        self._qshape = (self.E, self.Np, self.m, self.d)
+
+    def _info(self):
+        np_, nb, nnzb, ws = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+        self._check(load().iedg_mesh_info(self._h, ctypes.byref(np_), ctypes.byref(nb), ctypes.byref(nnzb),
+                                          ctypes.byref(ws)))
+        self.Np, self.Nb, self.nnzb, self.workspace_bytes = np_.value, nb.value, nnzb.value, ws.value
+
+    def element_sizes(self):
+        """(Np_e, nb_e) per element, numpy int32 arrays."""
+        npe = np.zeros(self.E, dtype=np.int32)
+        nbe = np.zeros(self.E, dtype=np.int32)
+        self._check(load().iedg_element_sizes(self._h, npe.ctypes.data, nbe.ctypes.data))
+        return npe, nbe
 
     def _check(self, rc):
         if rc != OK:
@@ -174,44 +191,44 @@ class Mesh:
     def eval_residual(self, u, uhat, q=None, u_ref=None, q_out=None, r_q=None, r_u=None, r_fl=None,
                       stream=None, want=("r_q", "r_u", "r_fl")):
         torch = _torch()
-        E, Np, m, d, T = self.E, self.Np, self.m, self.d, self.T
+        m, T, us, qs = self.m, self.T, self._ushape, self._qshape
         f64 = torch.float64
         if q is None and q_out is None:
-            q_out = self._empty(E, Np, m, d)
+            q_out = self._empty(*qs)
         if r_q is None and "r_q" in want:
-            r_q = self._empty(E, Np, m, d)
+            r_q = self._empty(*qs)
         if r_u is None and "r_u" in want:
-            r_u = self._empty(E, Np, m)
+            r_u = self._empty(*us)
         if r_fl is None and "r_fl" in want:
             r_fl = self._empty(T, m)
         self._check(load().iedg_eval_residual(
-            self._h, _ptr(u, (E, Np, m), f64, "u"), _ptr(uhat, (T, m), f64, "uhat"),
-            _ptr(q, (E, Np, m, d), f64, "q"), _ptr(u_ref, (E, Np, m), f64, "u_ref"),
-            _ptr(q_out, (E, Np, m, d), f64, "q_out"), _ptr(r_q, (E, Np, m, d), f64, "r_q"),
-            _ptr(r_u, (E, Np, m), f64, "r_u"), _ptr(r_fl, (T, m), f64, "r_fl"), _stream(stream)))
+            self._h, _ptr(u, us, f64, "u"), _ptr(uhat, (T, m), f64, "uhat"),
+            _ptr(q, qs, f64, "q"), _ptr(u_ref, us, f64, "u_ref"),
+            _ptr(q_out, qs, f64, "q_out"), _ptr(r_q, qs, f64, "r_q"),
+            _ptr(r_u, us, f64, "r_u"), _ptr(r_fl, (T, m), f64, "r_fl"), _stream(stream)))
         return dict(q=q_out if q is None else q, r_q=r_q, r_u=r_u, r_fl=r_fl)
 
     def assemble_condensed(self, u, q, uhat, u_ref=None, K=None, R=None, stream=None):
         torch = _torch()
-        E, Np, m, d, T = self.E, self.Np, self.m, self.d, self.T
+        m, T, us, qs = self.m, self.T, self._ushape, self._qshape
         f64 = torch.float64
         K = self._empty(self.nnzb, m, m) if K is None else K
         R = self._empty(T, m) if R is None else R
         self._check(load().iedg_assemble_condensed(
-            self._h, _ptr(u, (E, Np, m), f64, "u"), _ptr(q, (E, Np, m, d), f64, "q"),
-            _ptr(uhat, (T, m), f64, "uhat"), _ptr(u_ref, (E, Np, m), f64, "u_ref"),
+            self._h, _ptr(u, us, f64, "u"), _ptr(q, qs, f64, "q"),
+            _ptr(uhat, (T, m), f64, "uhat"), _ptr(u_ref, us, f64, "u_ref"),
             _ptr(K, (self.nnzb, m, m), f64, "K"), _ptr(R, (T, m), f64, "R"), _stream(stream)))
         return K, R
 
     def back_substitute(self, duhat, du=None, dq=None, stream=None):
         torch = _torch()
-        E, Np, m, d, T = self.E, self.Np, self.m, self.d, self.T
+        m, T, us, qs = self.m, self.T, self._ushape, self._qshape
         f64 = torch.float64
-        du = self._empty(E, Np, m) if du is None else du
-        dq = self._empty(E, Np, m, d) if dq is None else dq
+        du = self._empty(*us) if du is None else du
+        dq = self._empty(*qs) if dq is None else dq
         self._check(load().iedg_back_substitute(
-            self._h, _ptr(duhat, (T, m), f64, "duhat"), _ptr(du, (E, Np, m), f64, "du"),
-            _ptr(dq, (E, Np, m, d), f64, "dq"), _stream(stream)))
+            self._h, _ptr(duhat, (T, m), f64, "duhat"), _ptr(du, us, f64, "du"),
+            _ptr(dq, qs, f64, "dq"), _stream(stream)))
         return du, dq
 
     def element_status(self, stream=None):
@@ -238,12 +255,13 @@ class Mesh:
     def get_schedule(self):
         sc = Schedule()
         self._check(load().iedg_get_schedule(self._h, ctypes.byref(sc)))
-        return {"lu_persistent": sc.lu_persistent, "lu_panel": sc.lu_panel, "asm_chunk": sc.asm_chunk}
+        return {"lu_persistent": sc.lu_persistent, "lu_panel": sc.lu_panel, "asm_chunk": sc.asm_chunk,
+                "lu_tensor": sc.lu_tensor}
 
     def set_schedule(self, **kw):
         cur = self.get_schedule()
         cur.update(kw)
-        sc = Schedule(cur["lu_persistent"], cur["lu_panel"], cur["asm_chunk"])
+        sc = Schedule(cur["lu_persistent"], cur["lu_panel"], cur["asm_chunk"], cur["lu_tensor"])
         self._check(load().iedg_set_schedule(self._h, ctypes.byref(sc)))
 
     # ------------------------------------------------------------------ tracing
@@ -267,6 +285,43 @@ class Mesh:
             nm = names.raw[32 * i:32 * (i + 1)].split(b"\0", 1)[0].decode()
             out[nm] = (int(launches[i]), float(ms[i]))
         return out
+
+
+class MixedOrderMesh(Mesh):
+    """Handle around iedg_create_mesh_mixed: elements of different orders sharing one
+    trace space.  Element-indexed arrays are ragged, elements in the given order, each
+    with its own number of nodes: u [sum Np_e, m], q [sum Np_e, m, d]."""
+
+    def __init__(self, node_xyz, elem_trace, n_trace, orders, face_degree, gamma=1.4, Pr=0.72, Re=1e3,
+                 Minf=0.2, alpha=0.0, quad_extra=2, precision=0, stream=None):
+        lib = load()
+        X = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.float64) for x in node_xyz]))
+        ET = np.ascontiguousarray(np.concatenate([np.asarray(t, dtype=np.int64) for t in elem_trace]))
+        ORD = np.ascontiguousarray(orders, dtype=np.int32)
+        FD = np.ascontiguousarray(face_degree, dtype=np.int32)
+        self.E = len(ORD)
+        self.d = X.shape[1]
+        self.m = self.d + 2
+        self.T = int(n_trace)
+        self.order = 0
+        if FD.shape != (self.E, 2 * self.d):
+            raise ValueError("face_degree must be [n_elem, 2 d]")
+        desc = MeshDesc(self.d, 0, quad_extra, precision, self.E, self.T,
+                        X.ctypes.data, ET.ctypes.data, gamma, Pr, Re, Minf, alpha, 0, 0)
+        h = ctypes.c_void_p()
+        rc = lib.iedg_create_mesh_mixed(ctypes.byref(desc), ORD.ctypes.data, FD.ctypes.data,
+                                        ctypes.c_void_p(_stream(stream)), ctypes.byref(h))
+        if rc != OK:
+            raise IedgError(rc, lib.iedg_last_error(None).decode())
+        self._h = h
+        self._info()
+        npe, nbe = self.element_sizes()
+        self.node_off = np.concatenate([[0], np.cumsum(npe.astype(np.int64))])
+        self.n_nodes = int(self.node_off[-1])
+        if self.n_nodes != X.shape[0] or int(nbe.sum()) != ET.shape[0]:
+            raise ValueError("node_xyz / elem_trace sizes do not match the orders and face degrees")
+        self._ushape = (self.n_nodes, self.m)
+        self._qshape = (self.n_nodes, self.m, self.d)
 
 
 def mesh_from_workload(wl, precision=0, stream=None):

@@ -29,7 +29,7 @@ def test_schedules_agree(precision):
         if ref is None:
             ref = out
             continue
-        tol = 1e-11 if precision == 0 else 1e-5          # FP32 K: summation-order noise
+        tol = 1e-11 if precision == 0 else 1e-4          # FP32 K: FFMA vs 3xTF32 tensor-core updates
         assert rel_err(out[0], ref[0]) <= tol, cand
         for a, b in zip(out[1:], ref[1:]):
             assert rel_err(a, b) <= 1e-10, cand

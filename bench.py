@@ -226,11 +226,11 @@ def run_ours(args, wl, rank, world, local_rank):
     u = torch.as_tensor(st.u, dtype=f64, device=dev)
     uh = torch.as_tensor(st.uhat, dtype=f64, device=dev)
     duh = torch.as_tensor(st.duhat, dtype=f64, device=dev)
-    schedule = None
+    schedule, timings64 = None, {}
     if not args.no_autotune:
         from paper_1605_01020_gb300 import autotune
         qt = torch.as_tensor(st.q, dtype=f64, device=dev)
-        schedule, _ = autotune.autotune(mesh, u, qt, uh, 0, reps=1)
+        schedule, timings64 = autotune.autotune(mesh, u, qt, uh, 0, reps=1)
         del qt
     q = torch.empty(E, Np, m, d, dtype=f64, device=dev)
     rq = torch.empty_like(q)
@@ -305,6 +305,13 @@ def run_ours(args, wl, rank, world, local_rank):
 
     mixed = None if args.no_mixed else run_mixed(args, wl, mesh, dev, step_outputs=(K, R, du, dq),
                                                    inputs=(u, uh, duh), flush=flush, barrier=barrier)
+    # mixed orders: one GPU only (the leg takes a few minutes; scaling runs skip it)
+    mixed_orders = None
+    if world == 1 and not args.no_mixed_orders:
+        mesh.close()
+        del K, R, du, dq, q, rq, ru, rfl
+        torch.cuda.empty_cache()
+        mixed_orders = run_mixed_orders(args, dev, flush)
     from paper_1605_01020_gb300.dist import max_over_ranks
     ms, ms_e2e = max_over_ranks([ms, ms_e2e], dev)
     if mixed is not None:
@@ -355,7 +362,7 @@ def run_ours(args, wl, rank, world, local_rank):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(wl), "elements": E, "order": wl.mesh.p, "precision": "fp64",
                        "l2": "flushed between steps (512 MB write); per-step workspace 12 GB >> L2",
-                       "per_rank_elements": E, "schedule": schedule},
+                       "per_rank_elements": E, "schedule": schedule, "autotune_ms": timings64},
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": value_e2e, "unit": "elements/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -364,6 +371,7 @@ def run_ours(args, wl, rank, world, local_rank):
                         for k, v in prof.items()},
             "element_status_nonzero": int((status != 0).sum()),
             "mixed": mixed,
+            "mixed_orders": mixed_orders,
             "peaks": {"source": src, **{k: v for k, v in peaks.items() if isinstance(v, (int, float))}}}
     print(json.dumps(line), flush=True)
 
@@ -379,11 +387,11 @@ def run_mixed(args, wl, mesh64, dev, step_outputs, inputs, flush, barrier):
     mesh = iedg.mesh_from_workload(wl, precision=1)
     E, Np, m, d, T = mesh.E, mesh.Np, mesh.m, mesh.d, mesh.T
     f64 = torch.float64
-    schedule = None
+    schedule, timings = None, {}
     if not args.no_autotune:
         from paper_1605_01020_gb300 import autotune
         qt = torch.as_tensor(wl.state.q, dtype=f64, device=dev)
-        schedule, _ = autotune.autotune(mesh, u, qt, uh, 1, reps=1)
+        schedule, timings = autotune.autotune(mesh, u, qt, uh, 1, reps=1)
         del qt
     q = torch.empty(E, Np, m, d, dtype=f64, device=dev)
     rq, ru, rfl = torch.empty_like(q), torch.empty(E, Np, m, dtype=f64, device=dev), torch.empty(T, m, dtype=f64, device=dev)
@@ -414,13 +422,108 @@ def run_mixed(args, wl, mesh64, dev, step_outputs, inputs, flush, barrier):
     err = lambda a, b: float((a - b).abs().max() / b.abs().max().clamp_min(1e-300))
     status = mesh.element_status()
     out = {"ms_total": e0.elapsed_time(e1), "precision": "FP32 element matrix + partial LU, FP64 refinement",
-           "schedule": schedule,
+           "schedule": schedule, "autotune_ms": timings,
            "err_vs_fp64": {"K": err(K, K64), "R": err(R, R64), "du": err(du, du64), "dq": err(dq, dq64)},
            "element_status_nonzero": int((status != 0).sum()),
            "gpu_launches": sum(v[0] for v in prof.values()),
            "kernels": {k: {"launches": v[0], "ms": v[1], "share": v[1] / tot if tot else None} for k, v in prof.items()}}
     mesh.close()
     return out
+
+
+def run_mixed_orders(args, dev, flush):
+    """Mixed-order batch (3D, p in {2,3,4} by seed, 8192 elements): the same step on a
+    mesh whose elements have different orders, FP64 and mixed-precision forms.  Each
+    form is autotuned, captured once in a CUDA graph and timed by graph replays; the
+    kernel breakdown comes from one profiled eager step."""
+    import torch
+    from paper_1605_01020_gb300 import iedg
+    from paper_1605_01020_gb300 import workloads as W
+    t0 = time.perf_counter()
+    wl = W.config(4, N=args.mo_cells)
+    msh, st, prm = wl.mesh, wl.state, wl.params
+    t_build = time.perf_counter() - t0
+    f64 = torch.float64
+    cat = lambda xs: torch.as_tensor(np.ascontiguousarray(np.concatenate(xs)), dtype=f64, device=dev)
+    u, qin = cat(st.u), cat(st.q)
+    uh = torch.as_tensor(st.uhat, dtype=f64, device=dev)
+    duh = torch.as_tensor(st.duhat, dtype=f64, device=dev)
+    E, m, d = msh.n_elem, msh.d + 2, msh.d
+    nbe = np.array([len(t) for t in msh.elem_trace])
+    lu_flops = float(sum(a6_flops(m * (int(p) + 1) ** 3, m * int(nb)) for p, nb in zip(msh.orders, nbe)))
+    res = {"workload": wl.name, "elements": E,
+           "orders": {str(p): int((msh.orders == p).sum()) for p in (2, 3, 4)},
+           "n_trace": msh.n_trace, "mesh_build_s": t_build,
+           "lu_algorithmic_flops_per_launch": lu_flops}
+    outs = {}
+    for precision in (0, 1):
+        mesh = iedg.MixedOrderMesh(msh.node_xyz, msh.elem_trace, msh.n_trace, msh.orders, msh.face_degree,
+                                   gamma=prm["gamma"], Pr=prm["Pr"], Re=prm["Re"], Minf=prm["Minf"],
+                                   alpha=prm["alpha"], precision=precision)
+        schedule, timings = None, {}
+        if not args.no_autotune:
+            from paper_1605_01020_gb300 import autotune
+            schedule, timings = autotune.autotune(mesh, u, qin, uh, precision, reps=1)
+        q = torch.empty(mesh._qshape, dtype=f64, device=dev)
+        rq, dq = torch.empty_like(q), torch.empty_like(q)
+        ru, du = torch.empty(mesh._ushape, dtype=f64, device=dev), torch.empty(mesh._ushape, dtype=f64, device=dev)
+        rfl = torch.empty(mesh.T, m, dtype=f64, device=dev)
+        K = torch.empty(mesh.nnzb, m, m, dtype=f64, device=dev)
+        R = torch.empty(mesh.T, m, dtype=f64, device=dev)
+
+        def step():
+            mesh.eval_residual(u, uh, q=None, q_out=q, r_q=rq, r_u=ru, r_fl=rfl)
+            mesh.assemble_condensed(u, q, uh, K=K, R=R)
+            mesh.back_substitute(duh, du, dq)
+
+        for _ in range(args.warmup):
+            flush.zero_()
+            step()
+        torch.cuda.synchronize()
+        mesh.profile_reset()
+        mesh.profile_enable(True)
+        step()
+        mesh.profile_enable(False)
+        prof = mesh.profile_read()
+        launches_per_step = sum(v[0] for v in prof.values())
+        # one step captured in a CUDA graph, timed by replays
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            step()
+        torch.cuda.current_stream().wait_stream(side)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            step()
+        g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            e0.record()
+            g.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        status = mesh.element_status()
+        tot = sum(v[1] for v in prof.values())
+        lu = prof.get("lu_schur", (1, float("nan")))
+        r = {"schedule": schedule, "autotune_ms": timings, "value": E * args.steps / (ms / 1e3),
+             "unit": "elements/s", "ms_per_step": ms / args.steps, "timing": "CUDA graph replay of one step",
+             "gpu_launches_per_step": launches_per_step,
+             "element_status_nonzero": int((status != 0).sum()),
+             "lu_schur_ms": lu[1] / lu[0], "lu_schur_tflops": lu_flops / (lu[1] / lu[0] / 1e3) / 1e12,
+             "kernels": {k: {"launches": v[0], "ms": v[1], "share": v[1] / tot if tot else None}
+                         for k, v in prof.items()}}
+        outs[precision] = [t.clone() for t in (K, R, du, dq)]
+        res["fp64" if precision == 0 else "mixed"] = r
+        del g
+        mesh.close()
+    err = lambda a, b: float((a - b).abs().max() / b.abs().max().clamp_min(1e-300))
+    res["mixed"]["err_vs_fp64"] = {k: err(a, b) for k, a, b in zip(("K", "R", "du", "dq"), outs[1], outs[0])}
+    res["mixed"]["speedup_vs_fp64"] = res["fp64"]["ms_per_step"] / res["mixed"]["ms_per_step"]
+    return res
 
 
 def main():
@@ -434,6 +537,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch schedule")
+    ap.add_argument("--no-mixed-orders", action="store_true", help="skip the mixed-order batch (p in {2,3,4})")
+    ap.add_argument("--mo-cells", type=int, default=None, help="mixed-order batch: N x N x 2N cells (default 16)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-elems", type=int, default=4)
     args = ap.parse_args()

@@ -15,13 +15,16 @@ DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "iedg", "schedul
 
 
 def mesh_key(mesh, precision, gpu_name):
-    return f"{gpu_name}|d{mesh.d}|p{mesh.order}|Np{mesh.Np}|prec{precision}"
+    extra = getattr(mesh, "orders_key", "")
+    return f"{gpu_name}|d{mesh.d}|p{mesh.order}|Np{mesh.Np}|prec{precision}{extra}"
 
 
 def candidates(precision, order):
     """Candidate schedules: persistent LU on/off x FP64 panel 16/32 x assembly chunk
-    (x tensor-core or FFMA trailing updates of the FP32 LU on the mixed path)."""
-    panels = [16, 32] if (precision == 0 and order <= 3) else [16]
+    (x tensor-core or FFMA trailing updates of the FP32 LU on the mixed path).
+    order 0 (mixed orders): the FP64 panel stays 16 (the largest elements' panel of
+    32 does not fit in shared memory)."""
+    panels = [16, 32] if (precision == 0 and 1 <= order <= 3) else [16]
     chunks = [8, 16] if precision == 0 else [16, 32]
     tensor = [1] if precision == 0 else [1, 0]
     return [dict(lu_persistent=a, lu_panel=b, asm_chunk=c, lu_tensor=t)

@@ -287,6 +287,21 @@ class Mesh:
         return out
 
 
+def _slot_count(d, p, fdeg, _cache={}):
+    """Trace slots of an element of order p with face degrees fdeg (see
+    iedg_create_mesh_mixed): boundary nodes on faces of degree 0, plus (q+1)^(d-1)
+    private nodes per face of degree q > 0."""
+    key = (d, p, fdeg)
+    if key not in _cache:
+        idx = np.stack(np.meshgrid(*[np.arange(p + 1)] * d, indexing="ij"), -1).reshape(-1, d)
+        on = np.zeros(len(idx), dtype=bool)
+        for f, q in enumerate(fdeg):
+            if q == 0:
+                on |= idx[:, f // 2] == (p if f % 2 else 0)
+        _cache[key] = int(on.sum()) + sum((q + 1) ** (d - 1) for q in fdeg if q > 0)
+    return _cache[key]
+
+
 class MixedOrderMesh(Mesh):
     """Handle around iedg_create_mesh_mixed: elements of different orders sharing one
     trace space.  Element-indexed arrays are ragged, elements in the given order, each
@@ -306,6 +321,12 @@ class MixedOrderMesh(Mesh):
         self.order = 0
         if FD.shape != (self.E, 2 * self.d):
             raise ValueError("face_degree must be [n_elem, 2 d]")
+        # the library reads the ragged arrays with the sizes the orders and face degrees
+        # imply: check them here, before any pointer is passed
+        for e in range(self.E):
+            if len(node_xyz[e]) != (int(ORD[e]) + 1) ** self.d or \
+                    len(elem_trace[e]) != _slot_count(self.d, int(ORD[e]), tuple(FD[e].tolist())):
+                raise ValueError(f"element {e}: node_xyz / elem_trace sizes do not match its order and face degrees")
         desc = MeshDesc(self.d, 0, quad_extra, precision, self.E, self.T,
                         X.ctypes.data, ET.ctypes.data, gamma, Pr, Re, Minf, alpha, 0, 0)
         h = ctypes.c_void_p()
@@ -322,6 +343,8 @@ class MixedOrderMesh(Mesh):
             raise ValueError("node_xyz / elem_trace sizes do not match the orders and face degrees")
         self._ushape = (self.n_nodes, self.m)
         self._qshape = (self.n_nodes, self.m, self.d)
+        counts = np.bincount(ORD, minlength=5)
+        self.orders_key = "|orders" + ",".join(f"{p}:{c}" for p, c in enumerate(counts) if c) + f"|E{self.E}"
 
 
 def mesh_from_workload(wl, precision=0, stream=None):

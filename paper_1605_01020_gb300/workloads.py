@@ -274,6 +274,15 @@ def config(index, seed=None, N=None):
         prm = dict(gamma=GAMMA, Pr=0.72, Re=2.5e5, Minf=0.2, alpha=alpha)
         tag = " stretched/sheared (aspect 1-50)" if index == 3 else ""
         return Workload(f"3D NS p=3 {n}^3 periodic hexes{tag}", mesh, st, prm)
+    if index == 4:
+        shape = (N, N, 2 * N) if N else (16, 16, 32)
+        orders = mixed_orders(shape, seed, levels=(2, 3, 4), probs=(0.3, 0.5, 0.2))
+        mesh = structured_mesh_mixed(3, shape, orders, extent=(1.0, 1.0, 2.0))
+        st = make_state_mixed(mesh, taylor_green_field(0.2), seed + 1, noise=0.01)
+        prm = dict(gamma=GAMMA, Pr=0.72, Re=2.5e5, Minf=0.2, alpha=alpha)
+        E = int(np.prod(shape))
+        return Workload(f"3D NS mixed orders p in {{2,3,4}} (0.3/0.5/0.2) {shape[0]}x{shape[1]}x{shape[2]} "
+                        f"periodic hexes ({E} elements)", mesh, st, prm)
     if index == 5:
         n = N or 24
         mesh = structured_mesh(3, n, 4)
@@ -362,8 +371,11 @@ def structured_mesh_mixed(d, N, orders, extent=None):
 
 def make_state_mixed(mesh, field, seed, noise=0.0):
     """State on a MixedMesh (per-element lists): u, q as in make_state, uhat = mean
-    over the element slots sharing each trace node of u at the slot's position
-    (private face nodes: the field evaluated at the node's position on the face)."""
+    over the element slots sharing each trace node of the element's value at the
+    slot's position: the field there plus the same per-value noise as u (as in
+    make_state, where uhat averages the noisy nodal values), so that no trace value
+    sits exactly on a symmetry zero of the field (e.g. rho w = 0 of the Taylor-Green
+    field, where |vhat . n| of the Lax-Friedrichs lambda has its kink)."""
     rng = np.random.default_rng(seed)
     m = mesh.d + 2
     us, qs = [], []
@@ -380,6 +392,8 @@ def make_state_mixed(mesh, field, seed, noise=0.0):
         qs.append(fd_gradient(field, X))
         pos = _slot_positions(mesh, e)
         val = field(pos)
+        if noise:
+            val = val + noise * sigma * rng.uniform(-1.0, 1.0, val.shape)
         np.add.at(acc, mesh.elem_trace[e], val)
         np.add.at(cnt, mesh.elem_trace[e], 1.0)
     uhat = acc / cnt[:, None]

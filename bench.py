@@ -303,14 +303,19 @@ def run_ours(args, wl, rank, world, local_rank):
     h2d = sum(t.numel() * t.element_size() for t in (hu, huh, hduh))
     d2h = sum(t.numel() * t.element_size() for t in (hK, hR, hdu, hdq))
 
-    mixed = None if args.no_mixed else run_mixed(args, wl, mesh, dev, step_outputs=(K, R, du, dq),
+    # the FP64 handle and the step buffers are released before the other legs (the
+    # largest workload, p=4 24^3, does not fit twice in HBM); K, R, du, dq stay for the
+    # error of the mixed form
+    mesh.close()
+    del q, rq, ru, rfl, du_in, uh_in, duh_in, hu, huh, hduh, hK, hR, hdu, hdq
+    torch.cuda.empty_cache()
+    mixed = None if args.no_mixed else run_mixed(args, wl, None, dev, step_outputs=(K, R, du, dq),
                                                    inputs=(u, uh, duh), flush=flush, barrier=barrier)
     # mixed orders: one GPU only (the leg takes a few minutes; scaling runs skip it)
     mixed_orders = None
+    del K, R, du, dq
+    torch.cuda.empty_cache()
     if world == 1 and not args.no_mixed_orders:
-        mesh.close()
-        del K, R, du, dq, q, rq, ru, rfl
-        torch.cuda.empty_cache()
         mixed_orders = run_mixed_orders(args, dev, flush)
     from paper_1605_01020_gb300.dist import max_over_ranks
     ms, ms_e2e = max_over_ranks([ms, ms_e2e], dev)

@@ -184,6 +184,29 @@ int64_t iedg_element_status(iedg_mesh* mesh, int8_t* out, void* stream);
  * solved on the host).  Workspace is allocated with the mesh.  IEDG_ERR_INVALID_ARG
  * for a singular diagonal block. */
 #define IEDG_MAX_RESTART 40
+
+/* Preconditioner of iedg_trace_solve (default IEDG_PREC_BLOCK_JACOBI).
+ *   IEDG_PREC_BILU0: the zero fill-in m x m block incomplete LU of K (BILU(0), Sec.
+ *   2.2.2), in multicolour order: trace nodes coloured greedily in index order (each
+ *   takes the smallest colour none of its earlier neighbours has, neighbours = nodes
+ *   sharing a block of K), then eliminated colour by colour, ties by index.  Nodes of
+ *   one colour share no block, so each colour is factored and solved in one launch.
+ *   (The paper orders by minimum discarded fill, a sequential CPU ordering.)  The
+ *   colouring and per-row orders are built on the first use (host work, one device
+ *   buffer of nnzb m^2 doubles for the factors). */
+#define IEDG_PREC_BLOCK_JACOBI 0
+#define IEDG_PREC_BILU0        1
+int iedg_set_trace_precond(iedg_mesh* mesh, int32_t kind);
+
+/* BILU(0) pieces for callers and tests: factors of K in K's layout (blocks of
+ * neighbours eliminated before the row hold L, the others U; device F [nnzb][m][m]),
+ * the preconditioner solve x = U^-1 L^-1 r with the factors of the most recent
+ * iedg_bilu0_factor on this handle (r, x [n_trace][m], device, x may equal r), and the
+ * colour of every trace node (HOST int32 [n_trace]).  iedg_bilu0_factor returns
+ * IEDG_ERR_INVALID_ARG for an exactly singular pivot block. */
+int iedg_bilu0_factor(iedg_mesh* mesh, const double* K, double* F, void* stream);
+int iedg_bilu0_apply(iedg_mesh* mesh, const double* F, const double* r, double* x, void* stream);
+int iedg_trace_colors(iedg_mesh* mesh, int32_t* colors);
 int iedg_trace_solve(iedg_mesh* mesh, const double* K, const double* R, double* dU, int32_t restart,
                      int32_t max_iter, double rtol, int32_t* iterations, double* rel_residual,
                      void* stream);
@@ -201,13 +224,16 @@ int iedg_trace_solve(iedg_mesh* mesh, const double* K, const double* R, double* 
  *   lu_tensor:     mixed path: 1 = trailing updates of the FP32 LU on the tensor
  *                  cores (tcgen05, TF32 operands split in high and low parts, three
  *                  products, FP32 accumulation in tensor memory); 0 = FFMA.
+ *   asm_chunk_by_order[p-1]: meshes with mixed orders: the assembly chunk of the
+ *                  elements of order p (8, 16, 32; 0 = asm_chunk), so that each
+ *                  order's assembly launch gets its own tuned tile.
  * iedg_set_schedule rejects other values with IEDG_ERR_INVALID_ARG. */
 typedef struct {
   int32_t lu_persistent;
   int32_t lu_panel;
   int32_t asm_chunk;
   int32_t lu_tensor;
-  int32_t reserved[4];
+  int32_t asm_chunk_by_order[4];
 } iedg_schedule;
 int iedg_get_schedule(const iedg_mesh* mesh, iedg_schedule* out);
 int iedg_set_schedule(iedg_mesh* mesh, const iedg_schedule* in);

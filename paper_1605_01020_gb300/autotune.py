@@ -31,9 +31,10 @@ def candidates(precision, order):
             for a, b, c, t in itertools.product([1, 0], panels, chunks, tensor)]
 
 
-def time_assemble(mesh, u, q, uh, K, R, reps):
+def time_assemble(mesh, u, q, uh, K, R, reps, warm=True):
     import torch
-    mesh.assemble_condensed(u, q, uh, K=K, R=R)          # warm-up (kernel attributes, caches)
+    if warm:
+        mesh.assemble_condensed(u, q, uh, K=K, R=R)      # warm-up (kernel attributes, caches)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
@@ -63,12 +64,37 @@ def autotune(mesh, u, q, uh, precision, reps=2, cache_path=DEFAULT_CACHE, use_ca
     R = torch.empty(mesh.T, mesh.m, dtype=torch.float64, device=u.device)
     timings = {}
     best, best_ms = None, float("inf")
-    for cand in candidates(precision, mesh.order):
+    orders = getattr(mesh, "orders_present", None)
+    cands = candidates(precision, mesh.order)
+    if orders:
+        # mixed orders: LU variants first (every order at the default chunk), then each
+        # order's assembly chunk on its own (the orders' assembly launches are separate
+        # and run one after another, so their times add up)
+        cands = [c for c in cands if c["asm_chunk"] == cands[0]["asm_chunk"]]
+    first = True
+    for cand in cands:
         mesh.set_schedule(**cand)
-        ms = time_assemble(mesh, u, q, uh, K, R, reps)
+        ms = time_assemble(mesh, u, q, uh, K, R, reps, warm=first)
+        first = False
         timings[json.dumps(cand, sort_keys=True)] = ms
         if ms < best_ms:
             best, best_ms = cand, ms
+    if orders:
+        chunks = [8, 16] if precision == 0 else [16, 32]
+        by = [0, 0, 0, 0]
+        for p in orders:
+            best_c, best_c_ms = None, float("inf")
+            for c in chunks:
+                trial = list(by)
+                trial[p - 1] = c
+                cand = dict(best, asm_chunk_by_order=trial)
+                mesh.set_schedule(**cand)
+                ms = time_assemble(mesh, u, q, uh, K, R, reps, warm=False)
+                timings[json.dumps(cand, sort_keys=True)] = ms
+                if ms < best_c_ms:
+                    best_c, best_c_ms = c, ms
+            by[p - 1] = best_c
+        best = dict(best, asm_chunk_by_order=by)
     mesh.set_schedule(**best)
     if cache_path:
         cache[key] = {"schedule": best, "timings": timings}

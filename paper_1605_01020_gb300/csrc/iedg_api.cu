@@ -1095,6 +1095,7 @@ extern "C" int iedg_get_schedule(const iedg_mesh* M, iedg_schedule* out) {
   out->lu_panel = M->sched.lu_panel;
   out->asm_chunk = M->sched.asm_chunk;
   out->lu_tensor = M->sched.lu_tensor;
+  for (int i = 0; i < 4; ++i) out->asm_chunk_by_order[i] = M->sched.asm_chunk_by_order[i];
   return IEDG_OK;
 }
 
@@ -1104,10 +1105,19 @@ extern "C" int iedg_set_schedule(iedg_mesh* M, const iedg_schedule* in) {
       (in->asm_chunk != 0 && in->asm_chunk != 8 && in->asm_chunk != 16 && in->asm_chunk != 32) ||
       (in->lu_tensor != 0 && in->lu_tensor != 1))
     return fail(M, IEDG_ERR_INVALID_ARG, "schedule values out of range");
+  for (int i = 0; i < 4; ++i) {
+    const int c = in->asm_chunk_by_order[i];
+    if (c != 0 && c != 8 && c != 16 && c != 32) return fail(M, IEDG_ERR_INVALID_ARG, "schedule values out of range");
+  }
   M->sched.lu_persistent = in->lu_persistent;
   M->sched.lu_panel = in->lu_panel;
   M->sched.asm_chunk = in->asm_chunk;
   M->sched.lu_tensor = in->lu_tensor;
-  for (iedg_mesh* C : M->groups) C->sched = M->sched;
+  for (int i = 0; i < 4; ++i) M->sched.asm_chunk_by_order[i] = in->asm_chunk_by_order[i];
+  for (iedg_mesh* C : M->groups) {
+    C->sched = M->sched;
+    const int c = M->sched.asm_chunk_by_order[C->dm.p - 1];
+    if (c) C->sched.asm_chunk = c;
+  }
   return IEDG_OK;
 }

@@ -401,13 +401,207 @@ constexpr int L32_NB = 32;
 constexpr int L32_UCW = 128;      // trailing-update column chunk
 constexpr int L32_TM = 4, L32_TN = 8;
 
-// Tensor-core state of a CTA for the TC form of the trailing update.
+// Tensor-core state of a CTA for the TC form (deferred Schur complement).
 struct TcState {
-  uint32_t tmem;        // TMEM base (128 columns)
-  uint64_t* mbar;       // MMA completion barrier
-  uint32_t phase;       // parity of the next completion
+  uint32_t tmem;        // TMEM base (64 columns used)
+  uint64_t* mbar;       // two MMA completion barriers, one per operand stage
+  uint32_t phase[2];    // parity of each barrier's next completion
   int failed;           // a completion wait ran out
 };
+
+// A[r][c] -= sum_j L[r][j] U[j][c] over rows [r_lo, r_hi), cols [c_lo, c_hi): L from the
+// column-major panel P (row r at P[j n + r - kb]), U = rows kb..kb+nb of A.  4 x 8
+// register tiles, U staged in Uc by 128-column chunks.  Columns past c_hi are written
+// back unchanged only when they are padding of the row (c_hi = n + 1).
+__device__ __forceinline__ void lu32_update_rect(float* __restrict__ A, int ld, int n, const float* __restrict__ P,
+                                                 float* __restrict__ Uc, int kb, int nb, int r_lo, int r_hi,
+                                                 int c_lo, int c_hi) {
+  const int tid = threadIdx.x;
+  const bool vec = ((nb & 3) == 0) && ((n & 3) == 0);
+  const int tc = tid % (L32_UCW / L32_TN), tr = tid / (L32_UCW / L32_TN);   // 16 x 16
+  const int vlim = (c_hi == n + 1) ? ld : c_hi;     // last column a vector access may touch
+  for (int cc = c_lo; cc < c_hi; cc += L32_UCW) {
+    const int cw = min(L32_UCW, c_hi - cc);
+    for (int idx = tid; idx < L32_NB * L32_UCW; idx += LU_THREADS) {
+      int j = idx / L32_UCW, c = idx % L32_UCW;
+      Uc[idx] = (j < nb && c < cw) ? A[(int64_t)(kb + j) * ld + cc + c] : 0.f;
+    }
+    __syncthreads();
+    const bool cvec = ((cc & 3) == 0) && (cc + tc * L32_TN + L32_TN <= vlim);
+    for (int rb = r_lo; rb < r_hi; rb += 16 * L32_TM) {
+      const int rr0 = rb + tr * L32_TM;
+      float acc[L32_TM][L32_TN];
+#pragma unroll
+      for (int a = 0; a < L32_TM; ++a) {
+        const int rr = rr0 + a;
+        if (cvec && rr < r_hi) {
+          const float4* src = reinterpret_cast<const float4*>(A + (int64_t)rr * ld + cc + tc * L32_TN);
+          float4 v0 = src[0], v1 = src[1];
+          acc[a][0] = v0.x; acc[a][1] = v0.y; acc[a][2] = v0.z; acc[a][3] = v0.w;
+          acc[a][4] = v1.x; acc[a][5] = v1.y; acc[a][6] = v1.z; acc[a][7] = v1.w;
+        } else {
+#pragma unroll
+          for (int b = 0; b < L32_TN; ++b) {
+            int c = tc * L32_TN + b;
+            acc[a][b] = (rr < r_hi && c < cw) ? A[(int64_t)rr * ld + cc + c] : 0.f;
+          }
+        }
+      }
+      if (rr0 < r_hi) {
+        for (int j = 0; j < nb; ++j) {
+          float lv[L32_TM], uv[L32_TN];
+          const float* lp = P + j * n + (rr0 - kb);
+          if (vec && rr0 + L32_TM <= r_hi) {
+            float4 l0 = *reinterpret_cast<const float4*>(lp);
+            lv[0] = l0.x; lv[1] = l0.y; lv[2] = l0.z; lv[3] = l0.w;
+          } else {
+#pragma unroll
+            for (int a = 0; a < L32_TM; ++a) lv[a] = (rr0 + a < r_hi) ? lp[a] : 0.f;
+          }
+          const float4 u0 = *reinterpret_cast<const float4*>(Uc + j * L32_UCW + tc * L32_TN);
+          const float4 u1 = *reinterpret_cast<const float4*>(Uc + j * L32_UCW + tc * L32_TN + 4);
+          uv[0] = u0.x; uv[1] = u0.y; uv[2] = u0.z; uv[3] = u0.w;
+          uv[4] = u1.x; uv[5] = u1.y; uv[6] = u1.z; uv[7] = u1.w;
+#pragma unroll
+          for (int a = 0; a < L32_TM; ++a)
+#pragma unroll
+            for (int b = 0; b < L32_TN; ++b) acc[a][b] = fmaf(-lv[a], uv[b], acc[a][b]);
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < L32_TM; ++a) {
+        const int rr = rr0 + a;
+        if (cvec && rr < r_hi) {
+          float4* dst = reinterpret_cast<float4*>(A + (int64_t)rr * ld + cc + tc * L32_TN);
+          dst[0] = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+          dst[1] = make_float4(acc[a][4], acc[a][5], acc[a][6], acc[a][7]);
+        } else {
+#pragma unroll
+          for (int b = 0; b < L32_TN; ++b) {
+            int c = tc * L32_TN + b;
+            if (rr < r_hi && c < cw) A[(int64_t)rr * ld + cc + c] = acc[a][b];
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Deferred Schur complement on the tensor cores: [K | R] = [D | G] - W [Z | z] for rows
+// [nu, n) and columns [nu, n], W = A[nu:n, 0:nu] (the eliminated trace rows, L21 of
+// every panel) and Z = A[0:nu, nu:n] (U12 of every panel), so K accumulates over the
+// whole K = nu in TMEM and the trace block is read and written once.  128 x 64 output
+// tiles, K chunks of 32 staged as TF32 high and low parts (3xTF32: hi hi + hi lo + lo hi)
+// in two operand stages (48 KB each) so that one chunk is staged while the tensor core
+// works on the other; one thread issues the MMAs, completion through per-stage mbarriers
+// with bounded waits; the epilogue reads TMEM with all eight warps.
+constexpr int TC_TM = 128, TC_TN = 64, TC_KC = 32;
+constexpr int TC_STAGE_BYTES = 2 * TC_TM * TC_KC * 4 + 2 * TC_TN * TC_KC * 4;   // 48 KB
+
+__device__ __forceinline__ void schur_stage(const float* __restrict__ A, int ld, int n, int nu, int ncol, int rt,
+                                            int ct, int kc, char* stage) {
+  float* sAh = reinterpret_cast<float*>(stage);
+  float* sAl = reinterpret_cast<float*>(stage + TC_TM * TC_KC * 4);
+  float* sBh = reinterpret_cast<float*>(stage + 2 * TC_TM * TC_KC * 4);
+  float* sBl = reinterpret_cast<float*>(stage + 2 * TC_TM * TC_KC * 4 + TC_TN * TC_KC * 4);
+  const int tid = threadIdx.x;
+  // A operand: W rows rt .. rt+127, K columns kc .. kc+31 (k fastest: coalesced rows)
+  for (int idx = tid; idx < TC_TM * TC_KC; idx += LU_THREADS) {
+    const int mm = idx >> 5, k = idx & 31;
+    const int r = rt + mm, c = kc + k;
+    const float v = (r < n && c < nu) ? A[(int64_t)r * ld + c] : 0.f;
+    float hi, lo;
+    tc::split_tf32(v, hi, lo);
+    const uint32_t off = tc::core_off32(mm, k);
+    *reinterpret_cast<float*>(reinterpret_cast<char*>(sAh) + off) = hi;
+    *reinterpret_cast<float*>(reinterpret_cast<char*>(sAl) + off) = lo;
+  }
+  // B operand (N x K, K-major): Z rows kc .. kc+31, columns ct .. ct+63 (column fastest)
+  for (int idx = tid; idx < TC_TN * TC_KC; idx += LU_THREADS) {
+    const int k = idx >> 6, nn = idx & 63;
+    const int r = kc + k, c = ct + nn;
+    const float v = (r < nu && c < ncol) ? A[(int64_t)r * ld + c] : 0.f;
+    float hi, lo;
+    tc::split_tf32(v, hi, lo);
+    const uint32_t off = tc::core_off32(nn, k);
+    *reinterpret_cast<float*>(reinterpret_cast<char*>(sBh) + off) = hi;
+    *reinterpret_cast<float*>(reinterpret_cast<char*>(sBl) + off) = lo;
+  }
+}
+
+__device__ __forceinline__ void schur_issue(uint32_t tmem, const char* stage, bool first) {
+  const uint32_t aH = tc::smem_u32(stage), aL = aH + TC_TM * TC_KC * 4;
+  const uint32_t bH = aH + 2 * TC_TM * TC_KC * 4, bL = bH + TC_TN * TC_KC * 4;
+  constexpr uint32_t IDESC = tc::idesc_tf32(TC_TM, TC_TN);
+#pragma unroll
+  for (int st = 0; st < TC_KC / 8; ++st) {
+    const uint32_t ko = st * 256;
+    tc::mma_tf32(tmem, tc::desc_kmajor(aH + ko, 128, 1024), tc::desc_kmajor(bH + ko, 128, 1024), IDESC,
+                 (first && st == 0) ? 0u : 1u);
+    tc::mma_tf32(tmem, tc::desc_kmajor(aH + ko, 128, 1024), tc::desc_kmajor(bL + ko, 128, 1024), IDESC, 1);
+    tc::mma_tf32(tmem, tc::desc_kmajor(aL + ko, 128, 1024), tc::desc_kmajor(bH + ko, 128, 1024), IDESC, 1);
+  }
+}
+
+// Bounded wait on stage b's barrier by every thread; the verdict is made uniform.
+// (A wait that ran out leaves the phase where it was, so the drain can wait for it.)
+__device__ __forceinline__ bool schur_wait(TcState* tcs, int b) {
+  const bool ok = __syncthreads_and(tc::mbar_wait(tcs->mbar + b, tcs->phase[b], 1 << 26));
+  if (ok) tcs->phase[b] ^= 1u;
+  else tcs->failed = 1;
+  return ok;
+}
+
+__device__ void schur_tc(float* __restrict__ A, int ld, int n, int nu, char* smem, TcState* tcs) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ncol = n + 1;
+  const int nk = (nu + TC_KC - 1) / TC_KC;
+  const int q = warp & 3, h = warp >> 2;
+  for (int rt = nu; rt < n && !tcs->failed; rt += TC_TM) {
+    for (int ct = nu; ct < ncol && !tcs->failed; ct += TC_TN) {
+      schur_stage(A, ld, n, nu, ncol, rt, ct, 0, smem);
+      tc::fence_proxy_async();
+      __syncthreads();
+      tc::fence_after_sync();
+      for (int c = 0; c < nk; ++c) {
+        const int b = c & 1;
+        if (tid == 0) {
+          schur_issue(tcs->tmem, smem + b * TC_STAGE_BYTES, c == 0);
+          tc::mma_commit(tcs->mbar + b);
+        }
+        if (c + 1 < nk) {
+          // the other stage was last read by the MMAs of chunk c - 1
+          if (c >= 1 && !schur_wait(tcs, b ^ 1)) break;
+          schur_stage(A, ld, n, nu, ncol, rt, ct, (c + 1) * TC_KC, smem + (b ^ 1) * TC_STAGE_BYTES);
+          tc::fence_proxy_async();
+          __syncthreads();
+          tc::fence_after_sync();
+        }
+      }
+      if (tcs->failed) break;
+      // the two commits not waited for yet: chunks nk - 2 and nk - 1
+      if (nk >= 2 && !schur_wait(tcs, (nk - 2) & 1)) break;
+      if (!schur_wait(tcs, (nk - 1) & 1)) break;
+      tc::fence_after_sync();
+      // epilogue: warp (q, h) owns rows 32 q .. 32 q + 31 and columns 32 h .. 32 h + 31
+      const int row = rt + 32 * q + lane;
+#pragma unroll 1
+      for (int c8 = 0; c8 < 4; ++c8) {
+        const int c0 = 32 * h + 8 * c8;
+        float pv8[8];
+        tc::tmem_ld8(tcs->tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, pv8);
+        if (row >= n || ct + c0 >= ncol) continue;
+        float* dst = A + (int64_t)row * ld + ct + c0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (ct + c0 + j < ncol) dst[j] -= pv8[j];
+      }
+      tc::fence_before_sync();
+      __syncthreads();
+    }
+  }
+}
 
 template <bool TC>
 __device__ __forceinline__ void lu32_element(const LuElem& el, float* __restrict__ S, int8_t* __restrict__ status,
@@ -505,160 +699,21 @@ __device__ __forceinline__ void lu32_element(const LuElem& el, float* __restrict
       }
     }
     __syncthreads();
-    if constexpr (TC) {
-      // A22 -= L21 U12 on the tensor cores: 128 x 128 blocks, K = 32, 3xTF32 (hi hi + hi lo
-      // + lo hi) into a TMEM accumulator; operands staged in the (now free) panel buffer
-      const int r0 = kb + nb;
-      char* ob = reinterpret_cast<char*>(P);
-      float* sAh = reinterpret_cast<float*>(ob);
-      float* sAl = reinterpret_cast<float*>(ob + 16384);
-      float* sBh = reinterpret_cast<float*>(ob + 32768);
-      float* sBl = reinterpret_cast<float*>(ob + 49152);
-      const uint32_t aH = tc::smem_u32(sAh), aL = tc::smem_u32(sAl), bH = tc::smem_u32(sBh), bL = tc::smem_u32(sBl);
-      constexpr uint32_t IDESC = tc::idesc_tf32(128, 128);
-      const int q = warp & 3, h = warp >> 2;
-      for (int cc = r0; cc < ncol && !tcs->failed; cc += 128) {
-        for (int idx = tid; idx < 128 * L32_NB; idx += LU_THREADS) {
-          const int k = idx >> 7, nn = idx & 127;
-          const float v = (k < nb && cc + nn < ncol) ? A[(int64_t)(kb + k) * ld + cc + nn] : 0.f;
-          float hi, lo;
-          tc::split_tf32(v, hi, lo);
-          const uint32_t off = tc::core_off32(nn, k);
-          *reinterpret_cast<float*>(reinterpret_cast<char*>(sBh) + off) = hi;
-          *reinterpret_cast<float*>(reinterpret_cast<char*>(sBl) + off) = lo;
-        }
-        for (int rb = r0; rb < n && !tcs->failed; rb += 128) {
-          for (int idx = tid; idx < 128 * L32_NB; idx += LU_THREADS) {
-            const int mm = idx >> 5, k = idx & 31;
-            const float v = (k < nb && rb + mm < n) ? A[(int64_t)(rb + mm) * ld + kb + k] : 0.f;
-            float hi, lo;
-            tc::split_tf32(v, hi, lo);
-            const uint32_t off = tc::core_off32(mm, k);
-            *reinterpret_cast<float*>(reinterpret_cast<char*>(sAh) + off) = hi;
-            *reinterpret_cast<float*>(reinterpret_cast<char*>(sAl) + off) = lo;
-          }
-          tc::fence_proxy_async();
-          __syncthreads();
-          tc::fence_after_sync();
-          if (tid == 0) {
-#pragma unroll
-            for (int st = 0; st < L32_NB / 8; ++st) {
-              const uint32_t ko = st * 256;
-              tc::mma_tf32(tcs->tmem, tc::desc_kmajor(aH + ko, 128, 1024), tc::desc_kmajor(bH + ko, 128, 1024), IDESC,
-                           st > 0);
-              tc::mma_tf32(tcs->tmem, tc::desc_kmajor(aH + ko, 128, 1024), tc::desc_kmajor(bL + ko, 128, 1024), IDESC, 1);
-              tc::mma_tf32(tcs->tmem, tc::desc_kmajor(aL + ko, 128, 1024), tc::desc_kmajor(bH + ko, 128, 1024), IDESC, 1);
-            }
-            tc::mma_commit(tcs->mbar);
-          }
-          // every thread waits; the verdict is made uniform so that all threads leave
-          // the loops together
-          const bool ok = __syncthreads_and(tc::mbar_wait(tcs->mbar, tcs->phase, 1 << 26));
-          tcs->phase ^= 1u;
-          if (!ok) tcs->failed = 1;
-          tc::fence_after_sync();
-          // epilogue: warp (q, h) owns rows 32 q .. 32 q + 31 and columns 64 h .. 64 h + 63
-          const int row = rb + 32 * q + lane;
-          const bool cvec = ((cc & 3) == 0);
-#pragma unroll 1
-          for (int c8 = 0; c8 < 8; ++c8) {
-            const int c0 = 64 * h + 8 * c8;
-            float pv8[8];
-            tc::tmem_ld8(tcs->tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, pv8);
-            if (!ok || row >= n || cc + c0 >= ncol) continue;
-            float* dst = A + (int64_t)row * ld + cc + c0;
-            if (cvec && cc + c0 + 8 <= ld) {
-              float4* d4 = reinterpret_cast<float4*>(dst);
-              float4 v0 = d4[0], v1 = d4[1];
-              v0.x -= pv8[0]; v0.y -= pv8[1]; v0.z -= pv8[2]; v0.w -= pv8[3];
-              v1.x -= pv8[4]; v1.y -= pv8[5]; v1.z -= pv8[6]; v1.w -= pv8[7];
-              d4[0] = v0;
-              d4[1] = v1;
-            } else {
-#pragma unroll
-              for (int j = 0; j < 8; ++j)
-                if (cc + c0 + j < ncol) dst[j] -= pv8[j];
-            }
-          }
-          tc::fence_before_sync();
-          __syncthreads();
-        }
-      }
-      __syncthreads();
-      continue;
-    }
-    // A22 -= L21 U12, 8 x 8 tiles, rows [kb+nb, n), cols [kb+nb, n]
     const int r0 = kb + nb;
-    const bool vec = ((nb & 3) == 0) && ((n & 3) == 0);
-    const int tc = tid % (L32_UCW / L32_TN), tr = tid / (L32_UCW / L32_TN);   // 16 x 16
-    for (int cc = r0; cc < ncol; cc += L32_UCW) {
-      const int cw = min(L32_UCW, ncol - cc);
-      for (int idx = tid; idx < L32_NB * L32_UCW; idx += LU_THREADS) {
-        int j = idx / L32_UCW, c = idx % L32_UCW;
-        Uc[idx] = (j < nb && c < cw) ? A[(int64_t)(kb + j) * ld + cc + c] : 0.f;
-      }
-      __syncthreads();
-      // the tile's 8 columns lie inside the row (padding columns past n included, they
-      // are never read as results): 16-byte vector access
-      const bool cvec = ((cc & 3) == 0) && (cc + tc * L32_TN + L32_TN <= ld);
-      for (int rb = r0; rb < n; rb += 16 * L32_TM) {
-        const int rr0 = rb + tr * L32_TM;
-        float acc[L32_TM][L32_TN];
-#pragma unroll
-        for (int a = 0; a < L32_TM; ++a) {
-          const int rr = rr0 + a;
-          if (cvec && rr < n) {
-            const float4* src = reinterpret_cast<const float4*>(A + (int64_t)rr * ld + cc + tc * L32_TN);
-            float4 v0 = src[0], v1 = src[1];
-            acc[a][0] = v0.x; acc[a][1] = v0.y; acc[a][2] = v0.z; acc[a][3] = v0.w;
-            acc[a][4] = v1.x; acc[a][5] = v1.y; acc[a][6] = v1.z; acc[a][7] = v1.w;
-          } else {
-#pragma unroll
-            for (int b = 0; b < L32_TN; ++b) {
-              int c = tc * L32_TN + b;
-              acc[a][b] = (rr < n && c < cw) ? A[(int64_t)rr * ld + cc + c] : 0.f;
-            }
-          }
-        }
-        if (rr0 < n) {
-          for (int j = 0; j < nb; ++j) {
-            float lv[L32_TM], uv[L32_TN];
-            const float* lp = P + j * n + (rr0 - kb);
-            if (vec && rr0 + L32_TM <= n) {
-              float4 l0 = *reinterpret_cast<const float4*>(lp);
-              lv[0] = l0.x; lv[1] = l0.y; lv[2] = l0.z; lv[3] = l0.w;
-            } else {
-#pragma unroll
-              for (int a = 0; a < L32_TM; ++a) lv[a] = (rr0 + a < n) ? lp[a] : 0.f;
-            }
-            const float4 u0 = *reinterpret_cast<const float4*>(Uc + j * L32_UCW + tc * L32_TN);
-            const float4 u1 = *reinterpret_cast<const float4*>(Uc + j * L32_UCW + tc * L32_TN + 4);
-            uv[0] = u0.x; uv[1] = u0.y; uv[2] = u0.z; uv[3] = u0.w;
-            uv[4] = u1.x; uv[5] = u1.y; uv[6] = u1.z; uv[7] = u1.w;
-#pragma unroll
-            for (int a = 0; a < L32_TM; ++a)
-#pragma unroll
-              for (int b = 0; b < L32_TN; ++b) acc[a][b] = fmaf(-lv[a], uv[b], acc[a][b]);
-          }
-        }
-#pragma unroll
-        for (int a = 0; a < L32_TM; ++a) {
-          const int rr = rr0 + a;
-          if (cvec && rr < n) {
-            float4* dst = reinterpret_cast<float4*>(A + (int64_t)rr * ld + cc + tc * L32_TN);
-            dst[0] = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
-            dst[1] = make_float4(acc[a][4], acc[a][5], acc[a][6], acc[a][7]);
-          } else {
-#pragma unroll
-            for (int b = 0; b < L32_TN; ++b) {
-              int c = tc * L32_TN + b;
-              if (rr < n && c < cw) A[(int64_t)rr * ld + cc + c] = acc[a][b];
-            }
-          }
-        }
-      }
-      __syncthreads();
+    if constexpr (TC) {
+      // deferred Schur complement: the u-columns of every row and the trace columns of
+      // the u-rows are updated now (the next panels and U12 need them); the trace block
+      // of the trace rows receives all panels at once on the tensor cores below
+      lu32_update_rect(A, ld, n, P, Uc, kb, nb, r0, n, r0, nu);
+      lu32_update_rect(A, ld, n, P, Uc, kb, nb, r0, nu, nu, ncol);
+    } else {
+      // A22 -= L21 U12, rows [kb+nb, n), cols [kb+nb, n]
+      lu32_update_rect(A, ld, n, P, Uc, kb, nb, r0, n, r0, ncol);
     }
+  }
+  if constexpr (TC) {
+    __syncthreads();
+    schur_tc(A, ld, n, nu, reinterpret_cast<char*>(smraw), tcs);     // the panel buffer is free now
   }
   __syncthreads();
   int bad = 0;
@@ -714,39 +769,45 @@ __global__ void __launch_bounds__(LU_THREADS, 2)
 k_lu32_tc(Dims dm, LuDesc lud, float* __restrict__ S, int8_t* __restrict__ status, int* __restrict__ pivots,
           int64_t* queue, int64_t E, int* err) {
   __shared__ uint32_t tmem_base;
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar[2];
   __shared__ TcState tcs;
   const int tid = threadIdx.x, warp = tid >> 5;
   if (warp == 0) {
-    tc::tmem_alloc(&tmem_base, 128);
+    tc::tmem_alloc(&tmem_base, TC_TN);
     tc::tmem_relinquish();
   }
-  if (tid == 0) tc::mbar_init(&mbar, 1);
+  if (tid == 0) {
+    tc::mbar_init(&mbar[0], 1);
+    tc::mbar_init(&mbar[1], 1);
+  }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   if (tid == 0) {
     tcs.tmem = tmem_base;
-    tcs.mbar = &mbar;
-    tcs.phase = 0;
+    tcs.mbar = mbar;
+    tcs.phase[0] = 0;
+    tcs.phase[1] = 0;
     tcs.failed = 0;
   }
   __syncthreads();
-  // each thread keeps its own copy of the phase; the shared copy is only the start
+  // each thread keeps its own copy of the phases; the shared copy is only the start
   TcState mine = tcs;
   int64_t e;
   for (int64_t it = 0; next_element(queue, E, it, lud.order, &e); ++it) {
     lu32_element<true>(lu_elem(dm, lud, e), S, status, pivots, e, &mine);
     if (__syncthreads_or(mine.failed)) {
       if (tid == 0) atomicOr(err, 1);
-      tc::mbar_wait(&mbar, mine.phase ^ 1u, 1 << 26);   // let the last MMAs drain
+      // let MMAs still in flight drain (bounded) before the TMEM is freed
+      tc::mbar_wait(&mbar[0], mine.phase[0], 1 << 26);
+      tc::mbar_wait(&mbar[1], mine.phase[1], 1 << 26);
       break;
     }
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (warp == 0) tc::tmem_dealloc(tmem_base, 128);
+  if (warp == 0) tc::tmem_dealloc(tmem_base, TC_TN);
 }
 
 }  // namespace
@@ -826,8 +887,10 @@ cudaError_t launch_lu(iedg_mesh* M, cudaStream_t st) {
   }
   const Dims& dm = M->dm;
   if (M->sched.lu_tensor) {
-    size_t smem = sizeof(float) * (size_t)L32_NB * dm.n;
-    if (smem < 65536) smem = 65536;                      // operand tiles reuse the panel buffer
+    // panel + U chunk during the factorisation; the two operand stages of the Schur GEMM
+    // reuse the same buffer afterwards
+    size_t smem = sizeof(float) * ((size_t)L32_NB * dm.n + (size_t)L32_NB * L32_UCW);
+    if (smem < 2 * (size_t)TC_STAGE_BYTES) smem = 2 * (size_t)TC_STAGE_BYTES;
     cudaError_t err = cudaFuncSetAttribute(k_lu32_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     unsigned grid = (unsigned)M->E;

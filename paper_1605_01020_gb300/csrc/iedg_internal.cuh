@@ -31,6 +31,7 @@ struct Schedule {
   int lu_panel = 16;         // FP64 LU panel width (16 or 32; 32 only when it fits shared memory)
   int asm_chunk = 0;         // assembly column chunk (0 = default: 8 for FP64, 16 for FP32)
   int lu_tensor = 1;         // FP32 LU trailing update on tcgen05 (3xTF32) instead of FFMA
+  int asm_chunk_by_order[4] = {0, 0, 0, 0};   // mixed orders: chunk per order (0 = asm_chunk)
 };
 
 // Reference-element tables (device), shared by all elements.
@@ -172,6 +173,14 @@ struct iedg_mesh {
   const int* el_nb = nullptr;   // parent: [E] trace slots per element (internal order)
   int64_t* gnode = nullptr;     // child: [E] user node offset of each element
   double *xu = nullptr, *xuref = nullptr, *xq = nullptr, *xru = nullptr, *xrq = nullptr;  // child nodal buffers
+  // trace solve preconditioner: BILU(0) in multicolour order (built on first use)
+  int prec_kind = 0;            // IEDG_PREC_BLOCK_JACOBI or IEDG_PREC_BILU0
+  double* bf = nullptr;         // BILU(0) factors [nnzb][m][m]
+  int64_t* brows = nullptr;     // [T] trace nodes sorted by (colour, index)
+  std::vector<int64_t> bcptr;   // colour boundaries in brows
+  int32_t* bord = nullptr;      // [nnzb] per row: entry offsets in elimination order
+  int32_t* bnlow = nullptr;     // [T] entries of each row ranked before the row
+  std::vector<int32_t> bcolor;  // host: colour of every trace node
   double* kry = nullptr;        // trace solve: Krylov basis [IEDG_MAX_RESTART+1][T m] + 2 work vectors
   double* dinv = nullptr;       // trace solve: inverted diagonal blocks [T][m][m]
   double* kpart = nullptr;      // trace solve: dot-product partial sums

@@ -5,8 +5,10 @@
 // diagonal blocks of K (the paper notes that zero overlap gives block Jacobi).
 // The Hessenberg least-squares problem (Givens rotations) lives on the host; one
 // small device-to-host copy per Arnoldi step.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "iedg_internal.cuh"
@@ -164,6 +166,149 @@ __global__ void k_prec(int m, int64_t T, const double* __restrict__ Dinv, const 
   }
 }
 
+// ---------------------------------------------------------------- BILU(0)
+// Rows of one colour, one CTA per row: for each neighbour k eliminated before the row
+// (in elimination order), L_ik = A_ik U_kk^-1, then A_ij -= L_ik U_kj for the row's
+// later entries j present in row k (threads over j, binary search in row k); finally
+// the inverse of the row's diagonal block.  Rows of one colour share no block.
+constexpr int BI_THREADS = 128;
+__device__ bool invert_block(int m, const double* __restrict__ a_in, double* __restrict__ out) {
+  double a[5][10];
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < 2 * m; ++j) a[i][j] = j < m ? a_in[i * m + j] : (j - m == i);
+  for (int c = 0; c < m; ++c) {
+    int pr = c;
+    for (int r = c + 1; r < m; ++r)
+      if (fabs(a[r][c]) > fabs(a[pr][c])) pr = r;
+    if (a[pr][c] == 0.0) return false;
+    if (pr != c)
+      for (int j = 0; j < 2 * m; ++j) { double x = a[c][j]; a[c][j] = a[pr][j]; a[pr][j] = x; }
+    double inv = 1.0 / a[c][c];
+    for (int j = 0; j < 2 * m; ++j) a[c][j] *= inv;
+    for (int r = 0; r < m; ++r) {
+      if (r == c) continue;
+      double f = a[r][c];
+      for (int j = 0; j < 2 * m; ++j) a[r][j] -= f * a[c][j];
+    }
+  }
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) out[i * m + j] = a[i][m + j];
+  return true;
+}
+
+__global__ void __launch_bounds__(BI_THREADS)
+k_bilu_rows(int m, const int64_t* __restrict__ rows, const int64_t* __restrict__ row_ptr,
+            const int32_t* __restrict__ col, const int32_t* __restrict__ ord, const int32_t* __restrict__ nlow,
+            double* __restrict__ F, double* __restrict__ Uinv, int* __restrict__ flag) {
+  __shared__ double Lb[25];
+  const int tid = threadIdx.x, mm = m * m;
+  const int64_t i = rows[blockIdx.x];
+  const int64_t lo = row_ptr[i];
+  const int len = (int)(row_ptr[i + 1] - lo);
+  const int32_t* o = ord + lo;
+  const int nl = nlow[i];
+  for (int q = 0; q < nl; ++q) {
+    const int64_t kk = lo + o[q];
+    const int64_t k = col[kk];
+    if (tid < mm) {
+      const int r = tid / m, c = tid % m;
+      double sacc = 0.0;
+      for (int t = 0; t < m; ++t) sacc = fma(F[kk * mm + r * m + t], Uinv[k * mm + t * m + c], sacc);
+      Lb[tid] = sacc;
+    }
+    __syncthreads();
+    if (tid < mm) F[kk * mm + tid] = Lb[tid];
+    const int64_t klo = row_ptr[k], khi = row_ptr[k + 1];
+    for (int p = q + 1 + tid; p < len; p += BI_THREADS) {
+      const int64_t jj = lo + o[p];
+      const int32_t j = col[jj];
+      int64_t a = klo, b = khi;
+      while (a < b) {
+        const int64_t mid = (a + b) >> 1;
+        if (col[mid] < j) a = mid + 1; else b = mid;
+      }
+      if (a < khi && col[a] == j) {
+        double* dst = F + jj * mm;
+        const double* U = F + a * mm;
+        for (int r = 0; r < m; ++r)
+          for (int c = 0; c < m; ++c) {
+            double sacc = dst[r * m + c];
+            for (int t = 0; t < m; ++t) sacc = fma(-Lb[r * m + t], U[t * m + c], sacc);
+            dst[r * m + c] = sacc;
+          }
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && !invert_block(m, F + (lo + o[nl]) * mm, Uinv + i * mm)) atomicOr(flag, 1);
+}
+
+// Forward (lower) solve of the rows of one colour, one warp per row, in place:
+// v_i -= sum_{k before i} L_ik v_k.
+__global__ void k_bilu_fwd(int m, int64_t nrows, const int64_t* __restrict__ rows,
+                           const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                           const int32_t* __restrict__ ord, const int32_t* __restrict__ nlow,
+                           const double* __restrict__ F, double* __restrict__ v) {
+  const int lane = threadIdx.x & 31, mm = m * m;
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= nrows) return;
+  const int64_t i = rows[w], lo = row_ptr[i];
+  const int32_t* o = ord + lo;
+  const int nl = nlow[i];
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int q = lane; q < nl; q += 32) {
+    const int64_t kk = lo + o[q];
+    const double* blk = F + kk * mm;
+    const double* x = v + (int64_t)col[kk] * m;
+    for (int r = 0; r < m; ++r) {
+      double sacc = 0.0;
+      for (int t = 0; t < m; ++t) sacc = fma(blk[r * m + t], x[t], sacc);
+      acc[r] += sacc;
+    }
+  }
+  for (int r = 0; r < m; ++r)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], off);
+  if (lane < m) v[i * m + lane] -= acc[lane];
+}
+
+// Backward (upper) solve of the rows of one colour, in place:
+// v_i = U_ii^-1 (v_i - sum_{j after i} U_ij v_j).
+__global__ void k_bilu_bwd(int m, int64_t nrows, const int64_t* __restrict__ rows,
+                           const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                           const int32_t* __restrict__ ord, const int32_t* __restrict__ nlow,
+                           const double* __restrict__ F, const double* __restrict__ Uinv, double* __restrict__ v) {
+  const int lane = threadIdx.x & 31, mm = m * m;
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= nrows) return;
+  const int64_t i = rows[w], lo = row_ptr[i];
+  const int len = (int)(row_ptr[i + 1] - lo);
+  const int32_t* o = ord + lo;
+  const int nl = nlow[i];
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int q = nl + 1 + lane; q < len; q += 32) {
+    const int64_t kk = lo + o[q];
+    const double* blk = F + kk * mm;
+    const double* x = v + (int64_t)col[kk] * m;
+    for (int r = 0; r < m; ++r) {
+      double sacc = 0.0;
+      for (int t = 0; t < m; ++t) sacc = fma(blk[r * m + t], x[t], sacc);
+      acc[r] += sacc;
+    }
+  }
+  for (int r = 0; r < m; ++r)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], off);
+  double sv[5];
+  for (int t = 0; t < m; ++t) sv[t] = v[i * m + t] - acc[t];
+  __syncwarp();
+  if (lane < m) {
+    double x = 0.0;
+    for (int t = 0; t < m; ++t) x = fma(Uinv[(i * mm) + lane * m + t], sv[t], x);
+    v[i * m + lane] = x;
+  }
+}
+
 unsigned grid_for(int64_t n) {
   int64_t g = (n + SV_THREADS - 1) / SV_THREADS;
   return (unsigned)(g < 4096 ? g : 4096);
@@ -179,6 +324,150 @@ unsigned grid_for(int64_t n) {
       return IEDG_ERR_CUDA;                                                                \
     }                                                                                      \
   } while (0)
+
+// Colouring and elimination orders of the trace pattern (host, once per handle).
+static int bilu_setup(iedg_mesh* M, cudaStream_t st) {
+  if (M->brows) return IEDG_OK;
+  const int64_t T = M->T, nnzb = M->nnzb;
+  std::vector<int64_t> rp(T + 1);
+  std::vector<int32_t> col(nnzb);
+  SV_TRY(cudaMemcpyAsync(rp.data(), M->row_ptr, (T + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  SV_TRY(cudaMemcpyAsync(col.data(), M->col, nnzb * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  SV_TRY(cudaStreamSynchronize(st));
+  // greedy colouring in index order
+  std::vector<int32_t> color(T, -1), mark;
+  int32_t ncol = 0;
+  for (int64_t t = 0; t < T; ++t) {
+    mark.assign(ncol + 1, 0);
+    for (int64_t k = rp[t]; k < rp[t + 1]; ++k)
+      if (col[k] < t) mark[color[col[k]]] = 1;
+    int32_t c = 0;
+    while (mark[c]) ++c;
+    color[t] = c;
+    if (c + 1 > ncol) ncol = c + 1;
+  }
+  // rows sorted by (colour, index); rank = position in that order
+  std::vector<int64_t> rows(T), cnt(ncol + 1, 0), rank(T);
+  for (int64_t t = 0; t < T; ++t) cnt[color[t] + 1]++;
+  for (int32_t c = 0; c < ncol; ++c) cnt[c + 1] += cnt[c];
+  M->bcptr = cnt;
+  {
+    std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+    for (int64_t t = 0; t < T; ++t) rows[fill[color[t]]++] = t;
+  }
+  for (int64_t r = 0; r < T; ++r) rank[rows[r]] = r;
+  // per row: entries in elimination order, and how many come before the row
+  std::vector<int32_t> ord(nnzb), nlow(T);
+  for (int64_t t = 0; t < T; ++t) {
+    const int64_t lo = rp[t];
+    const int32_t len = (int32_t)(rp[t + 1] - lo);
+    int32_t* o = ord.data() + lo;
+    for (int32_t q = 0; q < len; ++q) o[q] = q;
+    std::sort(o, o + len, [&](int32_t a, int32_t b) { return rank[col[lo + a]] < rank[col[lo + b]]; });
+    int32_t nl = 0;
+    while (nl < len && rank[col[lo + o[nl]]] < rank[t]) ++nl;
+    nlow[t] = nl;
+  }
+  auto put = [&](auto** dst, const auto& h) -> cudaError_t {
+    using E = typename std::remove_const<typename std::remove_reference<decltype(h[0])>::type>::type;
+    E* d = nullptr;
+    cudaError_t e = cudaMalloc((void**)&d, std::max<size_t>(h.size(), 1) * sizeof(E));
+    if (e != cudaSuccess) return e;
+    M->allocs.push_back(d);
+    M->ws_bytes += (int64_t)(h.size() * sizeof(E));
+    *dst = d;
+    return cudaMemcpyAsync(d, h.data(), h.size() * sizeof(E), cudaMemcpyHostToDevice, st);
+  };
+  SV_TRY(put(&M->brows, rows));
+  SV_TRY(put(&M->bord, ord));
+  SV_TRY(put(&M->bnlow, nlow));
+  SV_TRY(cudaStreamSynchronize(st));
+  M->bcolor = color;
+  return IEDG_OK;
+}
+
+static int bilu_factor(iedg_mesh* M, const double* K, double* F, cudaStream_t st) {
+  int rc = bilu_setup(M, st);
+  if (rc != IEDG_OK) return rc;
+  const int m = M->dm.m;
+  if (F != K) SV_TRY(cudaMemcpyAsync(F, K, (size_t)M->nnzb * m * m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  SV_TRY(cudaMemsetAsync(M->dev_flag, 0, sizeof(int), st));
+  for (size_t c = 0; c + 1 < M->bcptr.size(); ++c) {
+    const int64_t nr = M->bcptr[c + 1] - M->bcptr[c];
+    if (nr == 0) continue;
+    SV_TRY((k_bilu_rows<<<(unsigned)nr, BI_THREADS, 0, st>>>(m, M->brows + M->bcptr[c], M->row_ptr, M->col, M->bord,
+                                                             M->bnlow, F, M->dinv, M->dev_flag),
+            cudaGetLastError()));
+  }
+  int flag = 0;
+  SV_TRY(cudaMemcpyAsync(&flag, M->dev_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SV_TRY(cudaStreamSynchronize(st));
+  if (flag) {
+    M->err = "BILU(0): singular pivot block";
+    return IEDG_ERR_INVALID_ARG;
+  }
+  return IEDG_OK;
+}
+
+// v <- U^-1 L^-1 v, colour by colour
+static cudaError_t bilu_apply(iedg_mesh* M, const double* F, double* v, cudaStream_t st) {
+  const int m = M->dm.m;
+  const size_t nc = M->bcptr.size() - 1;
+  for (size_t c = 0; c < nc; ++c) {
+    const int64_t nr = M->bcptr[c + 1] - M->bcptr[c];
+    if (nr == 0) continue;
+    k_bilu_fwd<<<(unsigned)((nr * 32 + SV_THREADS - 1) / SV_THREADS), SV_THREADS, 0, st>>>(
+        m, nr, M->brows + M->bcptr[c], M->row_ptr, M->col, M->bord, M->bnlow, F, v);
+  }
+  for (size_t c = nc; c-- > 0;) {
+    const int64_t nr = M->bcptr[c + 1] - M->bcptr[c];
+    if (nr == 0) continue;
+    k_bilu_bwd<<<(unsigned)((nr * 32 + SV_THREADS - 1) / SV_THREADS), SV_THREADS, 0, st>>>(
+        m, nr, M->brows + M->bcptr[c], M->row_ptr, M->col, M->bord, M->bnlow, F, M->dinv, v);
+  }
+  return cudaGetLastError();
+}
+
+extern "C" int iedg_set_trace_precond(iedg_mesh* M, int32_t kind) {
+  if (!M) return IEDG_ERR_INVALID_ARG;
+  if (kind != IEDG_PREC_BLOCK_JACOBI && kind != IEDG_PREC_BILU0) {
+    M->err = "iedg_set_trace_precond: unknown preconditioner";
+    return IEDG_ERR_INVALID_ARG;
+  }
+  M->prec_kind = kind;
+  return IEDG_OK;
+}
+
+extern "C" int iedg_bilu0_factor(iedg_mesh* M, const double* K, double* F, void* stream) {
+  if (!M || !K || !F) {
+    if (M) M->err = "iedg_bilu0_factor: null argument";
+    return IEDG_ERR_INVALID_ARG;
+  }
+  return bilu_factor(M, K, F, (cudaStream_t)stream);
+}
+
+extern "C" int iedg_bilu0_apply(iedg_mesh* M, const double* F, const double* r, double* x, void* stream) {
+  if (!M || !F || !r || !x) {
+    if (M) M->err = "iedg_bilu0_apply: null argument";
+    return IEDG_ERR_INVALID_ARG;
+  }
+  if (!M->brows) {
+    M->err = "iedg_bilu0_apply: no factorisation on this handle";
+    return IEDG_ERR_NOT_ASSEMBLED;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (x != r) SV_TRY(cudaMemcpyAsync(x, r, (size_t)M->T * M->dm.m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  SV_TRY(bilu_apply(M, F, x, st));
+  return IEDG_OK;
+}
+
+extern "C" int iedg_trace_colors(iedg_mesh* M, int32_t* colors) {
+  if (!M || !colors) return IEDG_ERR_INVALID_ARG;
+  int rc = bilu_setup(M, 0);
+  if (rc != IEDG_OK) return rc;
+  std::memcpy(colors, M->bcolor.data(), M->bcolor.size() * sizeof(int32_t));
+  return IEDG_OK;
+}
 
 extern "C" int iedg_trace_solve(iedg_mesh* M, const double* K, const double* R, double* dU, int32_t restart,
                                 int32_t max_iter, double rtol, int32_t* iterations, double* rel_residual,
@@ -202,9 +491,34 @@ extern "C" int iedg_trace_solve(iedg_mesh* M, const double* K, const double* R, 
   double* hdev = M->khdev;                // [restart+1]
   const unsigned g = grid_for(n);
   const unsigned gw = (unsigned)((T * 32 + SV_THREADS - 1) / SV_THREADS);
+  const bool bilu = M->prec_kind == IEDG_PREC_BILU0;
+  if (bilu) {
+    if (!M->bf) {
+      double* f = nullptr;
+      SV_TRY(cudaMalloc(&f, (size_t)M->nnzb * m * m * sizeof(double)));
+      M->allocs.push_back(f);
+      M->ws_bytes += (int64_t)M->nnzb * m * m * sizeof(double);
+      M->bf = f;
+    }
+    int rc = bilu_factor(M, K, M->bf, st);
+    if (rc != IEDG_OK) return rc;
+  }
+  // y = M^-1 x (in place allowed)
+  auto prec = [&](const double* x, double* y) -> cudaError_t {
+    if (!bilu) {
+      k_prec<<<(unsigned)((T + 127) / 128), 128, 0, st>>>(m, T, Dinv, x, y);
+      return cudaGetLastError();
+    }
+    if (x != y) {
+      cudaError_t e = cudaMemcpyAsync(y, x, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return e;
+    }
+    return bilu_apply(M, M->bf, y, st);
+  };
   SV_TRY(cudaMemsetAsync(M->dev_flag, 0, sizeof(int), st));
-  SV_TRY((k_diag_inv<<<(unsigned)((T + 127) / 128), 128, 0, st>>>(m, T, M->row_ptr, M->col, K, Dinv, M->dev_flag),
-          cudaGetLastError()));
+  if (!bilu)
+    SV_TRY((k_diag_inv<<<(unsigned)((T + 127) / 128), 128, 0, st>>>(m, T, M->row_ptr, M->col, K, Dinv, M->dev_flag),
+            cudaGetLastError()));
   auto dots = [&](int nv, const double* Vb, const double* x, double* out_host) -> cudaError_t {
     k_dots<<<SV_PART, SV_THREADS, 0, st>>>(n, nv, Vb, x, part);
     k_sum_partials<<<1, 64, 0, st>>>(nv, part, hdev);
@@ -214,7 +528,7 @@ extern "C" int iedg_trace_solve(iedg_mesh* M, const double* K, const double* R, 
   };
   // x0 = 0, r0 = M^-1 R
   SV_TRY(cudaMemsetAsync(dU, 0, n * sizeof(double), st));
-  SV_TRY((k_prec<<<(unsigned)((T + 127) / 128), 128, 0, st>>>(m, T, Dinv, R, V), cudaGetLastError()));
+  SV_TRY(prec(R, V));
   double beta0 = 0.0;
   SV_TRY(dots(1, V, V, &beta0));
   beta0 = std::sqrt(beta0);
@@ -235,7 +549,7 @@ extern "C" int iedg_trace_solve(iedg_mesh* M, const double* K, const double* R, 
       // r = M^-1 (R - K x)
       SV_TRY((k_spmv<<<gw, SV_THREADS, 0, st>>>(m, T, M->row_ptr, M->col, K, Dinv, dU, tmp, false), cudaGetLastError()));
       SV_TRY((k_residual<<<g, SV_THREADS, 0, st>>>(m, n, R, tmp, tmp), cudaGetLastError()));
-      SV_TRY((k_prec<<<(unsigned)((T + 127) / 128), 128, 0, st>>>(m, T, Dinv, tmp, V), cudaGetLastError()));
+      SV_TRY(prec(tmp, V));
       double bb = 0.0;
       SV_TRY(dots(1, V, V, &bb));
       beta = std::sqrt(bb);
@@ -250,7 +564,8 @@ extern "C" int iedg_trace_solve(iedg_mesh* M, const double* K, const double* R, 
     for (; j < restart && total < max_iter; ++j, ++total) {
       double* vj = V + (int64_t)j * n;
       double* vn = V + (int64_t)(j + 1) * n;
-      SV_TRY((k_spmv<<<gw, SV_THREADS, 0, st>>>(m, T, M->row_ptr, M->col, K, Dinv, vj, w, true), cudaGetLastError()));
+      SV_TRY((k_spmv<<<gw, SV_THREADS, 0, st>>>(m, T, M->row_ptr, M->col, K, Dinv, vj, w, !bilu), cudaGetLastError()));
+      if (bilu) SV_TRY(prec(w, w));
       // iterated classical Gram-Schmidt: two passes
       SV_TRY(dots(j + 1, V, w, h.data()));
       SV_TRY(cudaMemcpyAsync(hdev, h.data(), (j + 1) * sizeof(double), cudaMemcpyHostToDevice, st));

@@ -19,7 +19,9 @@ EXPORTS = ("iedg_create_mesh", "iedg_destroy_mesh", "iedg_last_error", "iedg_mes
            "iedg_trace_pattern", "iedg_eval_residual", "iedg_assemble_condensed",
            "iedg_back_substitute", "iedg_element_status", "iedg_profile_enable",
            "iedg_profile_read", "iedg_profile_reset", "iedg_eval_residual_static", "iedg_get_schedule",
-           "iedg_set_schedule", "iedg_trace_solve", "iedg_create_mesh_mixed", "iedg_element_sizes")
+           "iedg_set_schedule", "iedg_trace_solve", "iedg_create_mesh_mixed", "iedg_element_sizes",
+           "iedg_set_trace_precond", "iedg_bilu0_factor", "iedg_bilu0_apply", "iedg_trace_colors")
+PREC_BLOCK_JACOBI, PREC_BILU0 = 0, 1
 
 
 class IedgError(RuntimeError):
@@ -39,7 +41,7 @@ class MeshDesc(ctypes.Structure):
 
 class Schedule(ctypes.Structure):
     _fields_ = [("lu_persistent", ctypes.c_int32), ("lu_panel", ctypes.c_int32), ("asm_chunk", ctypes.c_int32),
-                ("lu_tensor", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("lu_tensor", ctypes.c_int32), ("asm_chunk_by_order", ctypes.c_int32 * 4)]
 
 
 _lib = None
@@ -83,6 +85,14 @@ def load():
     lib.iedg_trace_solve.argtypes = [vp, vp, vp, vp, i32, i32, ctypes.c_double, ctypes.POINTER(i32),
                                      ctypes.POINTER(ctypes.c_double), vp]
     lib.iedg_trace_solve.restype = ctypes.c_int
+    lib.iedg_set_trace_precond.argtypes = [vp, i32]
+    lib.iedg_set_trace_precond.restype = ctypes.c_int
+    lib.iedg_bilu0_factor.argtypes = [vp, vp, vp, vp]
+    lib.iedg_bilu0_factor.restype = ctypes.c_int
+    lib.iedg_bilu0_apply.argtypes = [vp, vp, vp, vp, vp]
+    lib.iedg_bilu0_apply.restype = ctypes.c_int
+    lib.iedg_trace_colors.argtypes = [vp, vp]
+    lib.iedg_trace_colors.restype = ctypes.c_int
     lib.iedg_get_schedule.argtypes = [vp, ctypes.POINTER(Schedule)]
     lib.iedg_get_schedule.restype = ctypes.c_int
     lib.iedg_set_schedule.argtypes = [vp, ctypes.POINTER(Schedule)]
@@ -251,17 +261,47 @@ class Mesh:
             restart, max_iter, rtol, ctypes.byref(it), ctypes.byref(rr), _stream(stream)))
         return dU, it.value, rr.value
 
+    def set_trace_precond(self, kind):
+        """PREC_BLOCK_JACOBI (default) or PREC_BILU0 for trace_solve."""
+        self._check(load().iedg_set_trace_precond(self._h, int(kind)))
+
+    def bilu0_factor(self, K, F=None, stream=None):
+        torch = _torch()
+        m = self.m
+        F = self._empty(self.nnzb, m, m) if F is None else F
+        self._check(load().iedg_bilu0_factor(self._h, _ptr(K, (self.nnzb, m, m), torch.float64, "K"),
+                                             _ptr(F, (self.nnzb, m, m), torch.float64, "F"), _stream(stream)))
+        return F
+
+    def bilu0_apply(self, F, r, x=None, stream=None):
+        torch = _torch()
+        m, T = self.m, self.T
+        x = self._empty(T, m) if x is None else x
+        self._check(load().iedg_bilu0_apply(self._h, _ptr(F, (self.nnzb, m, m), torch.float64, "F"),
+                                            _ptr(r, (T, m), torch.float64, "r"), _ptr(x, (T, m), torch.float64, "x"),
+                                            _stream(stream)))
+        return x
+
+    def trace_colors(self):
+        out = np.zeros(self.T, dtype=np.int32)
+        self._check(load().iedg_trace_colors(self._h, out.ctypes.data))
+        return out
+
     # ------------------------------------------------------------------ schedule
     def get_schedule(self):
         sc = Schedule()
         self._check(load().iedg_get_schedule(self._h, ctypes.byref(sc)))
-        return {"lu_persistent": sc.lu_persistent, "lu_panel": sc.lu_panel, "asm_chunk": sc.asm_chunk,
-                "lu_tensor": sc.lu_tensor}
+        out = {"lu_persistent": sc.lu_persistent, "lu_panel": sc.lu_panel, "asm_chunk": sc.asm_chunk,
+               "lu_tensor": sc.lu_tensor}
+        if any(sc.asm_chunk_by_order):
+            out["asm_chunk_by_order"] = list(sc.asm_chunk_by_order)
+        return out
 
     def set_schedule(self, **kw):
         cur = self.get_schedule()
         cur.update(kw)
-        sc = Schedule(cur["lu_persistent"], cur["lu_panel"], cur["asm_chunk"], cur["lu_tensor"])
+        by = (ctypes.c_int32 * 4)(*cur.get("asm_chunk_by_order", [0, 0, 0, 0]))
+        sc = Schedule(cur["lu_persistent"], cur["lu_panel"], cur["asm_chunk"], cur["lu_tensor"], by)
         self._check(load().iedg_set_schedule(self._h, ctypes.byref(sc)))
 
     # ------------------------------------------------------------------ tracing
@@ -344,6 +384,7 @@ class MixedOrderMesh(Mesh):
         self._ushape = (self.n_nodes, self.m)
         self._qshape = (self.n_nodes, self.m, self.d)
         counts = np.bincount(ORD, minlength=5)
+        self.orders_present = [p for p, c in enumerate(counts) if c]
         self.orders_key = "|orders" + ",".join(f"{p}:{c}" for p, c in enumerate(counts) if c) + f"|E{self.E}"
 
 

@@ -10,7 +10,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _declared():
     src = open(os.path.join(ROOT, "include", "iedg.h")).read()
-    return sorted(set(re.findall(r"\b(iedg_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(iedg_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_library_exports_every_declared_symbol():

@@ -137,7 +137,8 @@ def test_mixed_orders_schedules_agree(precision):
     kw = dict(u_ref=None if u_ref is None else dev(_cat(u_ref)))
     ref = None
     for sched in ({"lu_persistent": 1}, {"lu_persistent": 0}, {"lu_persistent": 1, "asm_chunk": 16},
-                  {"lu_persistent": 1, "lu_tensor": 1 - lm.get_schedule()["lu_tensor"]}):
+                  {"lu_persistent": 1, "lu_tensor": 1 - lm.get_schedule()["lu_tensor"]},
+                  {"lu_persistent": 1, "asm_chunk_by_order": [0, 32, 8, 16]}):
         lm.set_schedule(**sched)
         K, R = lm.assemble_condensed(*args, **kw)
         du, dq = lm.back_substitute(dev(st.duhat))

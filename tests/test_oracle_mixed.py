@@ -64,9 +64,17 @@ def test_mixed_discrete_conservation():
     assert max(np.abs(r).max() for r in Ru) > 1e-4
 
 
-def test_mixed_jacobian_blocks_match_finite_differences():
-    mesh = _mixed(2, 4, (1, 2, 3), (0.3, 0.4, 0.3), 14)
-    st = W.make_state_mixed(mesh, W.fourier_perturbed_field(2, 0.3, 5, amp=0.05), 6, noise=0.01)
+@pytest.mark.parametrize("d", [2, 3])
+def test_mixed_jacobian_blocks_match_finite_differences(d):
+    if d == 2:
+        mesh = _mixed(2, 4, (1, 2, 3), (0.3, 0.4, 0.3), 14)
+        field = W.fourier_perturbed_field(2, 0.3, 5, amp=0.05)
+    else:
+        # 3D faces: two tangential directions, private nodes of degree 2 on the faces
+        # between orders 1 and 2 (tensor products of the 1D Gauss-Lobatto Lagrange basis)
+        mesh = _mixed(3, 2, (1, 2), (0.5, 0.5), 16)
+        field = W.taylor_green_field(0.3)
+    st = W.make_state_mixed(mesh, field, 6, noise=0.01)
     pb = _problem(mesh, alpha=W.dirk_alpha())
     e = int(np.argmax((mesh.face_degree > 0).sum(1)))           # an element with private faces
     sub = pb.pbs[e]

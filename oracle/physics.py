@@ -91,8 +91,11 @@ def seed(values):
 
 
 class Params:
-    def __init__(self, gamma=1.4, Pr=0.72, Re=1.0e3, Minf=0.2, alpha=0.0):
+    """stab: 0 = Lax-Friedrichs S = lambda I, 1 = Roe-type S = |A_n(uhat)| (Sec. 2.1)."""
+
+    def __init__(self, gamma=1.4, Pr=0.72, Re=1.0e3, Minf=0.2, alpha=0.0, stab=0):
         self.gamma, self.Pr, self.Re, self.Minf, self.alpha = gamma, Pr, Re, Minf, alpha
+        self.stab = stab
 
 
 def flux(u, q, prm, d):
@@ -165,17 +168,67 @@ def lf_lambda(uh, n, prm, d):
     return (vn.abs() if isinstance(vn, Dual) else np.abs(vn)) + c
 
 
+def _abs(x):
+    return x.abs() if isinstance(x, Dual) else np.abs(x)
+
+
+def roe_dissipation(uh, du, n, prm, d):
+    """|A_n(uhat)| du, A_n = d(F_inv . n)/du the normal Jacobian of the Euler flux at
+    uhat (the Roe-type stabilisation tensor of Sec. 2.1).  Written from the
+    eigen-decomposition of A_n: eigenvalues v_n - c, v_n (d-fold), v_n + c; the
+    acoustic wave strengths of du are a_-+ = (dp -+ c rho dv_n) / (2 c^2) with the
+    linearised jumps dp = (gamma-1)(d(rhoE) - v.d(rho v) + |v|^2/2 drho) and
+    rho dv_n = n.d(rho v) - v_n drho, eigenvectors r_-+ = (1, v -+ c n, H -+ c v_n),
+    and every other wave travels at v_n, so
+        |A_n| du = |v_n| du + (|v_n - c| - |v_n|) a_- r_- + (|v_n + c| - |v_n|) a_+ r_+ .
+    Works on floats, arrays or Duals (|x|' = sign(x), sign(0) := 0)."""
+    rho = uh[0]
+    v = [uh[1 + j] / rho for j in range(d)]
+    p = pressure(uh, prm, d)
+    c2 = prm.gamma * p / rho
+    c = c2.sqrt() if isinstance(c2, Dual) else np.sqrt(c2)
+    H = (uh[d + 1] + p) / rho
+    vn = v[0] * n[0]
+    q2 = v[0] * v[0]
+    for j in range(1, d):
+        vn = vn + v[j] * n[j]
+        q2 = q2 + v[j] * v[j]
+    vdm = v[0] * du[1]
+    ndm = du[1] * n[0]
+    for j in range(1, d):
+        vdm = vdm + v[j] * du[1 + j]
+        ndm = ndm + du[1 + j] * n[j]
+    dp = (prm.gamma - 1.0) * (du[d + 1] - vdm + 0.5 * q2 * du[0])
+    rdvn = ndm - vn * du[0]
+    am = (dp - c * rdvn) / (2.0 * c2)
+    ap = (dp + c * rdvn) / (2.0 * c2)
+    l0 = _abs(vn)
+    wm = (_abs(vn - c) - l0) * am
+    wp = (_abs(vn + c) - l0) * ap
+    out = [l0 * du[0] + wm + wp]
+    for j in range(d):
+        out.append(l0 * du[1 + j] + wm * (v[j] - c * n[j]) + wp * (v[j] + c * n[j]))
+    out.append(l0 * du[d + 1] + wm * (H - c * vn) + wp * (H + c * vn))
+    return out
+
+
 def numerical_flux(uh, u, q, n, prm, d):
-    """fhat_i = F_ij(uhat, q) n_j + lambda(uhat) (u_i - uhat_i)  (Eq. IEDG d, LF)."""
+    """fhat_i = F_ij(uhat, q) n_j + S(uhat) (u - uhat)_i  (Eq. IEDG d); S = lambda I
+    (Lax-Friedrichs, lambda = |vhat.n| + chat) or |A_n(uhat)| (Roe), by prm.stab."""
     m = d + 2
     F = flux(uh, q, prm, d)
-    lam = lf_lambda(uh, n, prm, d)
+    du = [u[i] - uh[i] for i in range(m)]
+    if getattr(prm, "stab", 0) == 1:
+        sdu = roe_dissipation(uh, du, n, prm, d)
+    else:
+        lam = lf_lambda(uh, n, prm, d)
+        sdu = [lam * du[i] for i in range(m)]
     out = []
     for i in range(m):
         t = F[i][0] * n[0]
         for j in range(1, d):
             t = t + F[i][j] * n[j]
-        out.append(t + lam * (u[i] - uh[i]))
+        out.append(t + sdu[i])
     return out
 
 

@@ -17,7 +17,8 @@ def problem(mesh, params, quad_extra=2, source=None):
     ref = ref_element(mesh.d, mesh.p, quad_extra)
     assert np.array_equal(ref.bnodes, mesh.bnodes)
     geo = geometry.Geometry(ref, mesh.node_xyz)
-    prm = physics.Params(**{k: params[k] for k in ("gamma", "Pr", "Re", "Minf", "alpha")})
+    prm = physics.Params(**{k: params[k] for k in ("gamma", "Pr", "Re", "Minf", "alpha")},
+                         stab=params.get("stab", 0))
     return iedg.Problem(ref, geo, mesh.elem_trace, mesh.n_trace, prm, source)
 
 

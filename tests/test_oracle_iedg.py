@@ -67,10 +67,12 @@ def test_discrete_conservation():
     assert np.abs(Ru.sum((0, 1))).max() > 1e-3       # the identity is not trivially 0 = 0
 
 
+@pytest.mark.parametrize("stab", [0, 1])
 @pytest.mark.parametrize("d,p", [(2, 2), (3, 2)])
-def test_jacobian_blocks_match_finite_differences(d, p):
+def test_jacobian_blocks_match_finite_differences(d, p, stab):
     """Every block of the Newton matrix equals the central difference of the residual
-    (Sec. 2.2.1): columns for q, u of one element and for its trace unknowns."""
+    (Sec. 2.2.1): columns for q, u of one element and for its trace unknowns; with the
+    Lax-Friedrichs (stab 0) and the Roe-type (stab 1) stabilisation."""
     if d == 2:
         mesh = W.structured_mesh(2, 3, p)
         field = W.fourier_perturbed_field(2, 0.3, 7, amp=0.05)
@@ -78,7 +80,7 @@ def test_jacobian_blocks_match_finite_differences(d, p):
         mesh = W.structured_mesh(3, 2, p)
         field = W.taylor_green_field(0.3)
     st = W.make_state(mesh, field, 8, noise=0.01, uref_shift=0.01)
-    prm = _params(alpha=W.dirk_alpha(), Re=50.0)
+    prm = dict(_params(alpha=W.dirk_alpha(), Re=50.0), stab=stab)
     pb = problem(mesh, prm)
     e = 1
     m, Np, Nb = pb.m, pb.ref.Np, pb.ref.Nb

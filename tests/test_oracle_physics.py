@@ -123,3 +123,61 @@ def test_lax_friedrichs_flux(d):
         fp, *_ = physics.numerical_flux_with_jacobians((uh + du)[None], u[None], q[None], n[None], PRM, d)
         fm, *_ = physics.numerical_flux_with_jacobians((uh - du)[None], u[None], q[None], n[None], PRM, d)
         np.testing.assert_allclose((fp - fm)[0] / (2 * du[k]), fuh[0][:, k], rtol=1e-6, atol=1e-7)
+
+
+PRM_ROE = physics.Params(gamma=1.4, Pr=0.72, Re=100.0, Minf=0.3, stab=1)
+
+
+def _normal_jacobian(uh, n, d):
+    q0 = np.zeros((d + 2, d))
+    _, Fu, _ = physics.flux_with_jacobians(uh[None], q0[None], PRM, d)
+    return np.einsum("ijk,j->ik", Fu[0], n)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_roe_matrix_is_the_absolute_value_of_the_normal_jacobian(d):
+    """S = |A_n(uhat)| = R |Lambda| R^-1 from numpy's eigen-decomposition of the
+    dual-number Jacobian A_n; for supersonic flow along n every eigenvalue is
+    positive and S = A_n; S is applied by the closed form of the oracle."""
+    rng = np.random.default_rng(40 + d)
+    for trial in range(4):
+        uh, _ = _state(d, rng)
+        n = rng.normal(size=d)
+        n /= np.linalg.norm(n)
+        if trial == 3:                         # supersonic along n
+            rho = uh[0]
+            p = 0.4 * (uh[-1] - 0.5 * uh[1:d + 1] @ uh[1:d + 1] / rho)
+            c = np.sqrt(1.4 * p / rho)
+            v = 2.5 * c * n
+            uh = np.concatenate([[rho], rho * v, [p / 0.4 + 0.5 * rho * v @ v]])
+        An = _normal_jacobian(uh, n, d)
+        lam, R = np.linalg.eig(An)
+        absA = np.real(R @ np.diag(np.abs(lam)) @ np.linalg.inv(R))
+        S = np.stack([np.array(physics.roe_dissipation(uh, np.eye(d + 2)[k], n, PRM_ROE, d)) for k in range(d + 2)], 1)
+        np.testing.assert_allclose(S, absA, rtol=1e-10, atol=1e-10 * np.abs(absA).max())
+        if trial == 3:
+            np.testing.assert_allclose(S, An, rtol=1e-12, atol=1e-12 * np.abs(An).max())
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_roe_flux_consistency_and_jacobians(d):
+    rng = np.random.default_rng(50 + d)
+    uh, q = _state(d, rng)
+    u, _ = _state(d, rng)
+    n = rng.normal(size=d)
+    n /= np.linalg.norm(n)
+    f, fuh, fu, fq = physics.numerical_flux_with_jacobians(uh[None], u[None], q[None], n[None], PRM_ROE, d)
+    F, _, Fq = physics.flux_with_jacobians(uh[None], q[None], PRM_ROE, d)
+    S = np.stack([np.array(physics.roe_dissipation(uh, np.eye(d + 2)[k], n, PRM_ROE, d)) for k in range(d + 2)], 1)
+    np.testing.assert_allclose(f[0], F[0] @ n + S @ (u - uh), rtol=1e-13, atol=1e-12)
+    np.testing.assert_allclose(fu[0], S, rtol=1e-13, atol=1e-13 * np.abs(S).max())
+    np.testing.assert_allclose(fq[0], np.einsum("ijkl,j->ikl", Fq[0], n), atol=1e-14)
+    f2, *_ = physics.numerical_flux_with_jacobians(uh[None], uh[None], q[None], n[None], PRM_ROE, d)
+    np.testing.assert_allclose(f2[0], F[0] @ n, rtol=1e-14, atol=1e-13)
+    h = 1e-6
+    for k in range(d + 2):
+        du = np.zeros(d + 2)
+        du[k] = h * max(1.0, abs(uh[k]))
+        fp, *_ = physics.numerical_flux_with_jacobians((uh + du)[None], u[None], q[None], n[None], PRM_ROE, d)
+        fm, *_ = physics.numerical_flux_with_jacobians((uh - du)[None], u[None], q[None], n[None], PRM_ROE, d)
+        np.testing.assert_allclose((fp - fm)[0] / (2 * du[k]), fuh[0][:, k], rtol=1e-6, atol=1e-7)

@@ -6,7 +6,7 @@
  * compressible Navier-Stokes equations (Fernandez, Nguyen, Roca, Peraire,
  * arXiv:1605.01020):
  *   - the residuals R_NS = (R_q, R_u) and R_FL of the weak form (Eq. IEDG a-c,
- *     Eq. NLS), with the Lax-Friedrichs numerical flux of Eq. IEDG (d);
+ *     Eq. NLS), with the Lax-Friedrichs or Roe-type numerical flux of Eq. IEDG (d);
  *   - the element blocks of the Newton matrix [A B; C D] and right-hand side
  *     [F; G] (Sec. 2.2.1), statically condensed onto the trace unknowns,
  *     K = D - C A^-1 B and R = G - C A^-1 F (Eq. LS), and assembled into a
@@ -83,7 +83,12 @@ typedef struct {
   const double*  node_xyz;   /* HOST [n_elem][Np][dim]: isoparametric nodes (Sec. 3.1) */
   const int64_t* elem_trace; /* HOST [n_elem][Nb]: global trace node of each slot      */
   double gamma, Pr, Re, Minf, alpha;
-  int32_t stab;             /* 0 = Lax-Friedrichs, lambda = |vhat.n| + chat (Eq. IEDG d) */
+  int32_t stab;             /* stabilisation S of Eq. IEDG d, evaluated at uhat:
+                               0 = Lax-Friedrichs, S = (|vhat.n| + chat) I;
+                               1 = Roe-type, S = |A_n(uhat)|, A_n the normal Jacobian of
+                               the Euler flux (the absolute values of its eigenvalues
+                               v_n, v_n +- c in its eigenbasis); both fully linearised,
+                               d|x|/dx = sign(x) with sign(0) = 0                        */
   int32_t reserved;
 } iedg_mesh_desc;
 

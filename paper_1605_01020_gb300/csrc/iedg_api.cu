@@ -391,6 +391,7 @@ static int alloc_group(iedg_mesh* M, cudaStream_t st) {
   CUDA_TRY(dalloc(M, &M->pj.Jv, E * m * m * (1 + d) * d * Nq));
   CUDA_TRY(dalloc(M, &M->pj.Jf, E * m * m * (1 + d) * Nfp));
   CUDA_TRY(dalloc(M, &M->pj.lamw, E * Nfp));
+  if (M->ph.stab == 1) CUDA_TRY(dalloc(M, &M->pj.Su, E * m * m * Nfp));
   CUDA_TRY(dalloc(M, &M->qstar, E * Np * m * d));
   CUDA_TRY(dalloc(M, &M->rhoq, E * Np * m * d));
   if (M->precision == IEDG_PRECISION_MIXED) {
@@ -399,6 +400,7 @@ static int alloc_group(iedg_mesh* M, cudaStream_t st) {
     CUDA_TRY(dalloc(M, &M->pj.Jv32, E * m * m * (1 + d) * d * Nq));
     CUDA_TRY(dalloc(M, &M->pj.Jf32, E * m * m * (1 + d) * Nfp));
     CUDA_TRY(dalloc(M, &M->pj.lamw32, E * Nfp));
+    if (M->ph.stab == 1) CUDA_TRY(dalloc(M, &M->pj.Su32, E * m * m * Nfp));
     CUDA_TRY(dalloc(M, &G.Mass32, E * Np * Np));
     CUDA_TRY(dalloc(M, &G.GlV32, E * d * Nq * Np));
     CUDA_TRY(dalloc(M, &G.HlV32, E * d * Nq * Nb));
@@ -504,7 +506,8 @@ static int check_desc(const iedg_mesh_desc* D, bool mixed) {
     return fail(M, IEDG_ERR_UNSUPPORTED, "quad_extra must be 1..3");
   if (D->precision != IEDG_PRECISION_FP64 && D->precision != IEDG_PRECISION_MIXED)
     return fail(M, IEDG_ERR_UNSUPPORTED, "precision must be IEDG_PRECISION_FP64 or IEDG_PRECISION_MIXED");
-  if (D->stab != 0) return fail(M, IEDG_ERR_UNSUPPORTED, "only Lax-Friedrichs stabilisation is built");
+  if (D->stab != 0 && D->stab != 1)
+    return fail(M, IEDG_ERR_UNSUPPORTED, "stab must be 0 (Lax-Friedrichs) or 1 (Roe-type)");
   if (D->n_elem <= 0 || D->n_trace <= 0 || !D->node_xyz || !D->elem_trace)
     return fail(M, IEDG_ERR_INVALID_ARG, "empty mesh or null mesh arrays");
   if (!(D->gamma > 1.0) || !(D->Pr > 0) || !(D->Re > 0) || !(D->alpha >= 0))
@@ -529,7 +532,7 @@ extern "C" int iedg_create_mesh(const iedg_mesh_desc* D, void* stream, iedg_mesh
   if (rc != IEDG_OK) return rc;
   M = new iedg_mesh();
   M->dm = make_dims(D->dim, D->order, D->quad_extra);
-  M->ph = Phys{D->gamma, D->Pr, D->Re, D->alpha};
+  M->ph = Phys{D->gamma, D->Pr, D->Re, D->alpha, D->stab};
   M->precision = D->precision;
   M->E = D->n_elem;
   M->T = D->n_trace;
@@ -835,7 +838,7 @@ extern "C" int iedg_create_mesh_mixed(const iedg_mesh_desc* D, const int32_t* el
   int rc = check_desc(D, true);
   if (rc != IEDG_OK) return rc;
   M = new iedg_mesh();
-  M->ph = Phys{D->gamma, D->Pr, D->Re, D->alpha};
+  M->ph = Phys{D->gamma, D->Pr, D->Re, D->alpha, D->stab};
   M->precision = D->precision;
   M->E = D->n_elem;
   M->T = D->n_trace;

@@ -151,7 +151,9 @@ k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, AsmTab<T> tb, T* __restri
       int fp = f * Nfq + gf;
       T v = 0;
       if (col < Np) {
-        v = lamsel * tb.lamw[e * Nfp + fp] * tb.PhiF[(size_t)fp * Np + col];
+        // dfhat/du: lambda I (Lax-Friedrichs) or the pair's entry of S (Roe-type)
+        const T su = tb.Su ? tb.Su[((size_t)e * dm.m * dm.m + pair) * Nfp + fp] : lamsel * tb.lamw[e * Nfp + fp];
+        v = su * tb.PhiF[(size_t)fp * Np + col];
         for (int l = 0; l < d; ++l) v -= jf[(size_t)(1 + l) * Nfp + fp] * GlF[((size_t)l * Nfp + fp) * Np + col];
       } else if (col < ncol) {
         int t = col - Np;
@@ -832,13 +834,13 @@ static cudaError_t assemble_t(iedg_mesh* M, T* S, const double* rhs64, const Asm
 AsmTab<double> tables64(const iedg_mesh* M) {
   const Geo& G = M->geo;
   const PointJac& P = M->pj;
-  return AsmTab<double>{M->ref.Phi, M->ref.Dxi, M->ref.PhiF, P.Jv, P.Jf, P.lamw, G.GlV, G.HlV, G.GlF, G.HlF, G.Mass};
+  return AsmTab<double>{M->ref.Phi, M->ref.Dxi, M->ref.PhiF, P.Jv, P.Jf, P.lamw, P.Su, G.GlV, G.HlV, G.GlF, G.HlF, G.Mass};
 }
 
 AsmTab<float> tables32(const iedg_mesh* M) {
   const Geo& G = M->geo;
   const PointJac& P = M->pj;
-  return AsmTab<float>{M->ref.Phi32, M->ref.Dxi32, M->ref.PhiF32, P.Jv32, P.Jf32, P.lamw32,
+  return AsmTab<float>{M->ref.Phi32, M->ref.Dxi32, M->ref.PhiF32, P.Jv32, P.Jf32, P.lamw32, P.Su32,
                        G.GlV32, G.HlV32, G.GlF32, G.HlF32, G.Mass32};
 }
 
@@ -847,11 +849,15 @@ cudaError_t launch_assemble(iedg_mesh* M, cudaStream_t st) {
   return assemble_t<float>(M, M->S32, M->rhs64, tables32(M), st);
 }
 
-// Grid of the persistent form: resident CTAs per SM x SMs (never more than E).
+// Grid of the persistent form: resident CTAs per SM x SMs (never more than E).  The
+// kernel asks for the largest shared-memory carveout first, so the occupancy query
+// sees the split the launch will get.
 template <class K>
 static cudaError_t persistent_grid(K kern, size_t smem, int64_t E, unsigned* grid) {
   int dev = 0, sms = 0, per_sm = 0;
-  cudaError_t err = cudaGetDevice(&dev);
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared);
+  if (err == cudaSuccess) err = cudaGetDevice(&dev);
   if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, LU_THREADS, smem);
   if (err != cudaSuccess) return err;

@@ -96,7 +96,9 @@ k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, 
   const T* jf = tb.Jf + ((size_t)e * m2 + pair) * jfs;
   for (int idx = tid; idx < NC * Nq; idx += SF_THREADS) cV[idx] = jv[idx];
   for (int idx = tid; idx < (1 + d) * Nfp; idx += SF_THREADS) cF[idx] = jf[idx];
-  for (int idx = tid; idx < Nfp; idx += SF_THREADS) cL[idx] = (i == k) ? tb.lamw[e * Nfp + idx] : (T)0;
+  // dfhat/du of the pair: lambda wf on the diagonal (Lax-Friedrichs) or wf S_ik (Roe-type)
+  for (int idx = tid; idx < Nfp; idx += SF_THREADS)
+    cL[idx] = tb.Su ? tb.Su[((size_t)e * m2 + pair) * Nfp + idx] : ((i == k) ? tb.lamw[e * Nfp + idx] : (T)0);
   const T* GlV = tb.GlV + (size_t)e * d * Nq * Np;
   const T* HlV = tb.HlV + (size_t)e * d * Nq * NbT;
   const T* GlF = tb.GlF + (size_t)e * d * Nfp * Np;

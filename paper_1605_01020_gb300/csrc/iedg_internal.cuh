@@ -23,6 +23,7 @@ struct Dims {
 
 struct Phys {
   double gamma, Pr, Re, alpha;
+  int stab;   // 0 = Lax-Friedrichs, 1 = Roe-type |A_n(uhat)|
 };
 
 // Launch schedule (host-side choices the autotuner sweeps; see iedg_schedule).
@@ -76,8 +77,9 @@ struct Geo {
 struct PointJac {
   double* Jv;     // [E][m][m][(1+d) d][Nq]: c<d: cu_r ; c = d + l d + r: cq_lr  (w Jinv folded)
   double* Jf;     // [E][m][m][1+d][Nfp]   : c=0: wf dfhat/duhat ; c=1+l: wf dfhat/dq_l
-  double* lamw;   // [E][Nfp]              : wf lambda  (dfhat/du = lambda I)
-  float *Jv32, *Jf32, *lamw32;   // FP32 copies written by the point kernel (mixed path only)
+  double* lamw;   // [E][Nfp]              : wf lambda  (dfhat/du = lambda I, Lax-Friedrichs)
+  double* Su;     // [E][m][m][Nfp]        : wf dfhat_i/du_k = wf S_ik (Roe-type only, else null)
+  float *Jv32, *Jf32, *lamw32, *Su32;   // FP32 copies written by the point kernel (mixed path only)
 };
 
 // Per-element trace description of meshes with mixed orders.  A face shared with an
@@ -124,7 +126,7 @@ struct RaggedSrc {
 template <class T>
 struct AsmTab {
   const T *Phi, *Dxi, *PhiF;
-  const T *Jv, *Jf, *lamw;
+  const T *Jv, *Jf, *lamw, *Su;
   const T *GlV, *HlV, *GlF, *HlF, *Mass;
 };
 

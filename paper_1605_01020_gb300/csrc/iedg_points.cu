@@ -157,6 +157,46 @@ __device__ T lf_lambda(const T* u, const double* n, const Phys& ph) {
   return dabs(vn) + dsqrt((ph.gamma * p) * rinv);
 }
 
+// Roe-type stabilisation out = |A_n(uh)| du, A_n the normal Jacobian of the Euler flux
+// at uh (Sec. 2.1).  Eigenvalues v_n - c, v_n (d-fold), v_n + c; the acoustic waves of
+// du have strengths a_-+ = (dp -+ c rho dv_n) / (2 c^2), with the linearised jumps
+// dp = (gamma-1)(d(rhoE) - v.d(rho v) + |v|^2/2 drho), rho dv_n = n.d(rho v) - v_n drho,
+// and eigenvectors (1, v -+ c n, H -+ c v_n); all other waves move at v_n:
+//   |A_n| du = |v_n| du + (|v_n - c| - |v_n|) a_- r_- + (|v_n + c| - |v_n|) a_+ r_+ .
+// T = double, or Dual<M> to differentiate with respect to uh (du may depend on it).
+template <int D, class T>
+__device__ void roe_apply(const T* uh, const T* du, const double* n, const Phys& ph, T* out) {
+  constexpr int M = D + 2;
+  const T rinv = recip(uh[0]);
+  T v[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) v[j] = uh[1 + j] * rinv;
+  T vn = mk<T>(0.0), q2 = mk<T>(0.0), vdm = mk<T>(0.0), ndm = mk<T>(0.0);
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    vn = vn + n[j] * v[j];
+    q2 = q2 + v[j] * v[j];
+    vdm = vdm + v[j] * du[1 + j];
+    ndm = ndm + n[j] * du[1 + j];
+  }
+  const T p = (ph.gamma - 1.0) * (uh[M - 1] + (-0.5) * (uh[0] * q2));
+  const T c2 = ph.gamma * (p * rinv);
+  const T c = dsqrt(c2);
+  const T H = (uh[M - 1] + p) * rinv;
+  const T dp = (ph.gamma - 1.0) * (du[M - 1] + (-1.0) * vdm + 0.5 * (q2 * du[0]));
+  const T rdvn = ndm + (-1.0) * (vn * du[0]);
+  const T ic2 = 0.5 * recip(c2);
+  const T am = (dp + (-1.0) * (c * rdvn)) * ic2;
+  const T ap = (dp + c * rdvn) * ic2;
+  const T l0 = dabs(vn);
+  const T wm = (dabs(vn + (-1.0) * c) + (-1.0) * l0) * am;
+  const T wp = (dabs(vn + c) + (-1.0) * l0) * ap;
+  out[0] = l0 * du[0] + wm + wp;
+#pragma unroll
+  for (int j = 0; j < D; ++j) out[1 + j] = l0 * du[1 + j] + wm * (v[j] + (-n[j]) * c) + wp * (v[j] + n[j] * c);
+  out[M - 1] = l0 * du[M - 1] + wm * (H + (-1.0) * (c * vn)) + wp * (H + c * vn);
+}
+
 // dF[i][j][k] = dF_ij/du_k and dQ[i][j][k][l] = dF_ij/dq_kl at (u, q).
 template <int D>
 __device__ void flux_jacobians(const double* u, const double (*q)[D], const Phys& ph,
@@ -204,7 +244,7 @@ __device__ void flux_jacobians(const double* u, const double (*q)[D], const Phys
 // One CTA per element.  jac = false: residual at (u, q).  jac = true: Jacobians at
 // (u, q) into PointJac, right-hand sides -R_u(u, q*), -Rhat(u, q*) into the last
 // column of the bordered element matrix.
-template <int D>
+template <int D, int STAB>
 __global__ void k_points(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ,
                          const int64_t* __restrict__ etrace, const double* __restrict__ U,
                          const double* __restrict__ Q, const double* __restrict__ QS,
@@ -352,10 +392,22 @@ __global__ void k_points(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ,
     for (int j = 0; j < D; ++j) n[j] = G.fn[(e * Nfp + fp) * D + j];
     double F[M][D];
     ns_flux<D, double>(uh, qr, ph, F);
-    const double lam = lf_lambda<D, double>(uh, n, ph);
+    // stabilisation S (u - uh): lambda I (Lax-Friedrichs) or |A_n(uh)| (Roe-type)
+    double sdu[M];
+    double lam = 0.0;
+    if constexpr (STAB == 1) {
+      double dd[M];
+#pragma unroll
+      for (int i = 0; i < M; ++i) dd[i] = u[i] - uh[i];
+      roe_apply<D, double>(uh, dd, n, ph, sdu);
+    } else {
+      lam = lf_lambda<D, double>(uh, n, ph);
+#pragma unroll
+      for (int i = 0; i < M; ++i) sdu[i] = lam * (u[i] - uh[i]);
+    }
 #pragma unroll
     for (int i = 0; i < M; ++i) {
-      double s = lam * (u[i] - uh[i]);
+      double s = sdu[i];
 #pragma unroll
       for (int j = 0; j < D; ++j) s += F[i][j] * n[j];
       fsur[i * Nfp + fp] = wf * s;
@@ -364,7 +416,32 @@ __global__ void k_points(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ,
       Dual<M> ud[M];
 #pragma unroll
       for (int k = 0; k < M; ++k) { ud[k] = mkconst<M>(uh[k]); ud[k].t[k] = 1.0; }
-      Dual<M> lamd = lf_lambda<D, Dual<M>>(ud, n, ph);
+      // d/duhat of the stabilisation term: LF  dlambda/duhat (u - uh) - lambda I;
+      // Roe  d/duhat [ |A_n(uh)| (u - uh) ] by duals (includes - |A_n|)
+      Dual<M> lamd = mkconst<M>(0.0);
+      Dual<M> gd[M];
+      if constexpr (STAB == 1) {
+        Dual<M> dd[M];
+#pragma unroll
+        for (int i = 0; i < M; ++i) dd[i] = mkconst<M>(u[i]) - ud[i];
+        roe_apply<D, Dual<M>>(ud, dd, n, ph, gd);
+        // dfhat/du = S: its columns S e_k
+#pragma unroll 1
+        for (int k = 0; k < M; ++k) {
+          double ek[M], sk[M];
+#pragma unroll
+          for (int i = 0; i < M; ++i) ek[i] = (i == k) ? 1.0 : 0.0;
+          roe_apply<D, double>(uh, ek, n, ph, sk);
+#pragma unroll
+          for (int i = 0; i < M; ++i) {
+            const size_t o = ((size_t)(e * M + i) * M + k) * Nfp + fp;
+            PJ.Su[o] = wf * sk[i];
+            if (PJ.Su32) PJ.Su32[o] = (float)(wf * sk[i]);
+          }
+        }
+      } else {
+        lamd = lf_lambda<D, Dual<M>>(ud, n, ph);
+      }
       double dF[M][D][M], dQ[M][D][M][D];
       flux_jacobians<D>(uh, q, ph, dF, dQ);
       double* jf = PJ.Jf + (size_t)e * M * M * jfs;
@@ -374,7 +451,7 @@ __global__ void k_points(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ,
         for (int k = 0; k < M; ++k) {
           double* o = jf + (size_t)(i * M + k) * jfs;
           float* o32 = PJ.Jf32 ? PJ.Jf32 + ((size_t)e * M * M + (size_t)(i * M + k)) * jfs : nullptr;
-          double s = lamd.t[k] * (u[i] - uh[i]) - (i == k ? lam : 0.0);
+          double s = STAB == 1 ? gd[i].t[k] : lamd.t[k] * (u[i] - uh[i]) - (i == k ? lam : 0.0);
 #pragma unroll
           for (int j = 0; j < D; ++j) s += dF[i][j][k] * n[j];
           o[fp] = wf * s;
@@ -504,15 +581,11 @@ cudaError_t launch_points(iedg_mesh* M, const double* u, const double* q, const 
   double* rhs = M->precision == 0 ? (M->tt.soff ? M->S : M->S + dm.n) : M->rhs64;
   int64_t es = M->precision == 0 ? (int64_t)dm.n * dm.ld : dm.n;
   int64_t rs = M->precision == 0 ? dm.ld : 1;
-  if (dm.d == 2) {
-    cudaFuncSetAttribute(k_points<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_points<2><<<(unsigned)M->E, threads, smem, st>>>(dm, M->ph, M->ref, M->geo, M->pj, M->etrace, u, q,
-                                                       qs, uhat, u_ref, jacobians, r_u, rhat, rhs, es, rs, M->tt);
-  } else {
-    cudaFuncSetAttribute(k_points<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_points<3><<<(unsigned)M->E, threads, smem, st>>>(dm, M->ph, M->ref, M->geo, M->pj, M->etrace, u, q,
-                                                       qs, uhat, u_ref, jacobians, r_u, rhat, rhs, es, rs, M->tt);
-  }
+  auto kern = dm.d == 2 ? (M->ph.stab == 1 ? k_points<2, 1> : k_points<2, 0>)
+                        : (M->ph.stab == 1 ? k_points<3, 1> : k_points<3, 0>);
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  kern<<<(unsigned)M->E, threads, smem, st>>>(dm, M->ph, M->ref, M->geo, M->pj, M->etrace, u, q, qs, uhat, u_ref,
+                                              jacobians, r_u, rhat, rhs, es, rs, M->tt);
   return cudaGetLastError();
 }
 

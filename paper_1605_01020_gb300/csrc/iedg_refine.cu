@@ -191,7 +191,13 @@ __device__ void element_apply(const Dims& dm, const Phys& ph, const RefTables& r
   }
   for (int idx = tid; idx < m * Nfp; idx += RF_THREADS) {
     int i = idx / Nfp, fp = idx % Nfp;
-    double s = use_x ? PJ.lamw[e * Nfp + fp] * w.xf[i * Nfp + fp] : 0.0;
+    double s = 0.0;
+    if (use_x) {
+      if (PJ.Su)        // Roe-type: sum_k wf S_ik x_k
+        for (int k = 0; k < m; ++k) s = fma(PJ.Su[((size_t)(e * m + i) * m + k) * Nfp + fp], w.xf[k * Nfp + fp], s);
+      else
+        s = PJ.lamw[e * Nfp + fp] * w.xf[i * Nfp + fp];
+    }
     for (int k = 0; k < m; ++k) {
       const double* o = jf + (size_t)(i * m + k) * jfs;
       if (use_z) s = fma(o[fp], w.zf[k * Nfp + fp], s);

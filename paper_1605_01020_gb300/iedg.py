@@ -137,7 +137,7 @@ class Mesh:
     """Handle around iedg_create_mesh / iedg_destroy_mesh with the compute calls."""
 
     def __init__(self, node_xyz, elem_trace, n_trace, order, gamma=1.4, Pr=0.72, Re=1e3, Minf=0.2,
-                 alpha=0.0, quad_extra=2, precision=0, stream=None):
+                 alpha=0.0, quad_extra=2, precision=0, stream=None, stab=0):
         lib = load()
         X = np.ascontiguousarray(node_xyz, dtype=np.float64)
         ET = np.ascontiguousarray(elem_trace, dtype=np.int64)
@@ -146,7 +146,7 @@ class Mesh:
         self.T = int(n_trace)
         self.order = int(order)
         desc = MeshDesc(self.d, self.order, quad_extra, precision, self.E, self.T,
-                        X.ctypes.data, ET.ctypes.data, gamma, Pr, Re, Minf, alpha, 0, 0)
+                        X.ctypes.data, ET.ctypes.data, gamma, Pr, Re, Minf, alpha, int(stab), 0)
         h = ctypes.c_void_p()
         rc = lib.iedg_create_mesh(ctypes.byref(desc), ctypes.c_void_p(_stream(stream)), ctypes.byref(h))
         if rc != OK:
@@ -348,7 +348,7 @@ class MixedOrderMesh(Mesh):
     with its own number of nodes: u [sum Np_e, m], q [sum Np_e, m, d]."""
 
     def __init__(self, node_xyz, elem_trace, n_trace, orders, face_degree, gamma=1.4, Pr=0.72, Re=1e3,
-                 Minf=0.2, alpha=0.0, quad_extra=2, precision=0, stream=None):
+                 Minf=0.2, alpha=0.0, quad_extra=2, precision=0, stream=None, stab=0):
         lib = load()
         X = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.float64) for x in node_xyz]))
         ET = np.ascontiguousarray(np.concatenate([np.asarray(t, dtype=np.int64) for t in elem_trace]))
@@ -368,7 +368,7 @@ class MixedOrderMesh(Mesh):
                     len(elem_trace[e]) != _slot_count(self.d, int(ORD[e]), tuple(FD[e].tolist())):
                 raise ValueError(f"element {e}: node_xyz / elem_trace sizes do not match its order and face degrees")
         desc = MeshDesc(self.d, 0, quad_extra, precision, self.E, self.T,
-                        X.ctypes.data, ET.ctypes.data, gamma, Pr, Re, Minf, alpha, 0, 0)
+                        X.ctypes.data, ET.ctypes.data, gamma, Pr, Re, Minf, alpha, int(stab), 0)
         h = ctypes.c_void_p()
         rc = lib.iedg_create_mesh_mixed(ctypes.byref(desc), ORD.ctypes.data, FD.ctypes.data,
                                         ctypes.c_void_p(_stream(stream)), ctypes.byref(h))
@@ -392,4 +392,5 @@ def mesh_from_workload(wl, precision=0, stream=None):
     """Convenience: a Mesh for a workloads.Workload."""
     p = wl.params
     return Mesh(wl.mesh.node_xyz, wl.mesh.elem_trace, wl.mesh.n_trace, wl.mesh.p, gamma=p["gamma"],
-                Pr=p["Pr"], Re=p["Re"], Minf=p["Minf"], alpha=p["alpha"], precision=precision, stream=stream)
+                Pr=p["Pr"], Re=p["Re"], Minf=p["Minf"], alpha=p["alpha"], precision=precision, stream=stream,
+                stab=p.get("stab", 0))

@@ -29,6 +29,10 @@ def _case(name):
     elif name == "3d-23-steady":
         d, N, levels, probs, seed = 3, 2, (2, 3), (0.5, 0.5), 13
         field, alpha = W.broadband_field(0.3, 14), 0.0
+    elif name == "3d-234-roe":
+        mesh, st, u_ref, prm = _case("3d-234")
+        prm.stab = 1
+        return mesh, st, u_ref, prm
     elif name == "3d-234-4cube":
         d, N, levels, probs, seed = 3, 4, (2, 3, 4), (0.3, 0.5, 0.2), 15
         field, alpha = W.taylor_green_field(0.2), W.dirk_alpha()
@@ -52,14 +56,14 @@ def _lib(mesh, prm, precision=0):
     from paper_1605_01020_gb300 import iedg
     return iedg.MixedOrderMesh(mesh.node_xyz, mesh.elem_trace, mesh.n_trace, mesh.orders, mesh.face_degree,
                                gamma=prm.gamma, Pr=prm.Pr, Re=prm.Re, Minf=prm.Minf, alpha=prm.alpha,
-                               precision=precision)
+                               precision=precision, stab=prm.stab)
 
 
 def _cat(xs):
     return np.concatenate([np.asarray(x) for x in xs])
 
 
-CASES = ["2d-123", "3d-234", "3d-23-steady"]
+CASES = ["2d-123", "3d-234", "3d-23-steady", "3d-234-roe"]
 
 
 @pytest.mark.parametrize("name", CASES)

@@ -43,10 +43,14 @@ def _case(name):
         st = W.make_state(mesh, W.fourier_perturbed_field(2, 0.3, 7, amp=0.05), 8, noise=0.01, uref_shift=0.01)
         prm = dict(gamma=1.4, Pr=0.72, Re=100.0, Minf=0.3, alpha=W.dirk_alpha())
         return W.Workload("2D p=1 4x4", mesh, st, prm)
+    if name.endswith("-roe"):
+        wl = _case(name[:-4])
+        return W.Workload(wl.name + " (Roe)", wl.mesh, wl.state, dict(wl.params, stab=1))
     raise KeyError(name)
 
 
-CASES = ["cfg1", "cfg1-noisy", "p3-2cube", "p2-curved", "2d-p3-steady", "2d-p1", "p4-2cube"]
+CASES = ["cfg1", "cfg1-noisy", "p3-2cube", "p2-curved", "2d-p3-steady", "2d-p1", "p4-2cube",
+         "cfg1-noisy-roe", "p3-2cube-roe", "p2-curved-roe"]
 
 
 @pytest.mark.parametrize("name", CASES)
@@ -171,7 +175,8 @@ def _mixed_mesh(wl):
     return iedg.mesh_from_workload(wl, precision=1)
 
 
-@pytest.mark.parametrize("name", ["cfg1-noisy", "p3-2cube", "p2-curved", "2d-p3-steady", "2d-p1", "p4-2cube"])
+@pytest.mark.parametrize("name", ["cfg1-noisy", "p3-2cube", "p2-curved", "2d-p3-steady", "2d-p1", "p4-2cube",
+                                  "p3-2cube-roe", "p2-curved-roe"])
 def test_mixed_condensed_parity(name):
     wl = _case(name)
     st = wl.state

@@ -31,12 +31,17 @@ from . import physics
 
 
 class Problem:
-    def __init__(self, ref, geo, elem_trace, n_trace, prm, source=None, fmu=None):
+    def __init__(self, ref, geo, elem_trace, n_trace, prm, source=None, fmu=None, fkind=None, ub=None):
         """ref: RefElement, geo: Geometry, elem_trace [E, Nb] global trace ids,
         prm: physics.Params, source: optional callable x[..., d] -> s[..., m],
         fmu: trace basis at the face points [nf, Nfq, Nb] shared by the elements
-        (default: the element basis restricted to the faces, mu_s = phi_bnodes[s])."""
+        (default: the element basis restricted to the faces, mu_s = phi_bnodes[s]),
+        fkind: [E, nf] face kinds (physics.FACE_*; None = every face interior): on a
+        boundary face the trace equation takes the boundary flux bhat (Eq. IEDG c),
+        ub: the far-field state u_b [m]."""
         self.ref, self.geo, self.prm = ref, geo, prm
+        self.fkind = None if fkind is None else np.asarray(fkind, dtype=np.int64).reshape(geo.E, 2 * ref.d)
+        self.ub = None if ub is None else np.asarray(ub, dtype=np.float64)
         self.d = ref.d
         self.m = ref.d + 2
         self.elem_trace = np.asarray(elem_trace, dtype=np.int64)
@@ -83,10 +88,24 @@ class Problem:
         if self.source is not None:
             s = self.source(geo.xq[els])
             Ru = Ru - np.einsum("eg,egi,ga->eai", w, s, ref.phi, optimize=True)
-        Rhat_e = np.einsum("efg,efgi,fgs->esi", wf, fh, self.fmu, optimize=True)
+        Rhat_e = np.einsum("efg,efgi,fgs->esi", wf, self._trace_flux(els, P, nf, fh), self.fmu, optimize=True)
         Rfl = np.zeros((self.n_trace, m))
         np.add.at(Rfl, self.elem_trace[els].reshape(-1), Rhat_e.reshape(-1, m))
         return Rq, Ru, Rhat_e, Rfl
+
+    def _trace_flux(self, els, P, nf, fh):
+        """The flux of the trace equation: fhat on interior faces, bhat on boundary
+        faces (values only)."""
+        if self.fkind is None or not (self.fkind[els] != 0).any():
+            return fh
+        out = fh.copy()
+        for kind in (physics.FACE_FARFIELD, physics.FACE_WALL):
+            mask = self.fkind[els] == kind
+            if mask.any():
+                b, _, _, _ = physics.boundary_flux_with_jacobians(
+                    P["uhf"][mask], P["uf"][mask], P["qf"][mask], nf[mask], self.prm, self.d, kind, self.ub)
+                out[mask] = b
+        return out
 
     def geometric_blocks(self, e):
         """Mass M, B_j[a,b] = sum_g w dphi_a/dx_j phi_b, E_j[a,t] = sum wf n_j phi_a mu_t."""
@@ -137,7 +156,16 @@ class Problem:
         blk["A_uq"] = A_uq.reshape(m * Np, m * d * Np)
         blk["A_uu"] = A_uu.reshape(m * Np, m * Np)
         blk["B_u"] = np.einsum("fg,fga,fgik,fgt->iakt", wf, fphi, fuh, fmu, optimize=True).reshape(m * Np, m * Nb)
-        # trace rows (IEDG c)
+        # trace rows (IEDG c): bhat and its derivatives on boundary faces
+        if self.fkind is not None and (self.fkind[e] != 0).any():
+            fuh, fu, fq = fuh.copy(), fu.copy(), fq.copy()
+            for f in range(2 * d):
+                kind = int(self.fkind[e, f])
+                if kind == physics.FACE_INTERIOR:
+                    continue
+                _, buh, bu, bq = physics.boundary_flux_with_jacobians(
+                    P["uhf"][0, f], P["uf"][0, f], P["qf"][0, f], geo.nf[e][f], prm, d, kind, self.ub)
+                fuh[f], fu[f], fq[f] = buh, bu, bq
         blk["C_q"] = np.einsum("fg,fgs,fgikl,fgb->isklb", wf, fmu, fq, fphi, optimize=True).reshape(m * Nb, m * d * Np)
         blk["C_u"] = np.einsum("fg,fgs,fgik,fgb->iskb", wf, fmu, fu, fphi, optimize=True).reshape(m * Nb, m * Np)
         blk["D"] = np.einsum("fg,fgs,fgik,fgt->iskt", wf, fmu, fuh, fmu, optimize=True).reshape(m * Nb, m * Nb)
@@ -318,8 +346,9 @@ class MixedProblem:
     each element is an independent single-element Problem with its own reference
     element, geometry and trace basis."""
 
-    def __init__(self, refs, mesh, prm, source=None):
-        """refs: {p: RefElement}; mesh: workloads.MixedMesh; prm: physics.Params."""
+    def __init__(self, refs, mesh, prm, source=None, ub=None):
+        """refs: {p: RefElement}; mesh: workloads.MixedMesh (face_kind None: every face
+        interior); prm: physics.Params; ub: far-field state for far-field faces."""
         from .geometry import Geometry
         self.mesh, self.prm = mesh, prm
         self.m = mesh.d + 2
@@ -329,7 +358,8 @@ class MixedProblem:
             ref = refs[int(mesh.orders[e])]
             geo = Geometry(ref, mesh.node_xyz[e][None])
             fmu = face_trace_basis(ref, mesh.face_degree[e])
-            self.pbs.append(Problem(ref, geo, mesh.elem_trace[e][None], mesh.n_trace, prm, source, fmu))
+            fk = None if getattr(mesh, "face_kind", None) is None else mesh.face_kind[e][None]
+            self.pbs.append(Problem(ref, geo, mesh.elem_trace[e][None], mesh.n_trace, prm, source, fmu, fk, ub))
 
     def residual(self, u, q, uhat, u_ref=None):
         """Per-element lists R_q, R_u, Rhat_e and the assembled R_fl."""

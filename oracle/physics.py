@@ -212,6 +212,83 @@ def roe_dissipation(uh, du, n, prm, d):
     return out
 
 
+def normal_jacobian_apply(uh, x, n, prm, d):
+    """A_n(uhat) x with A_n = d(F_inv . n)/du the normal Jacobian of the Euler flux at
+    uhat, from the differentials of rho v_n, rho v v_n + p n, (rho E + p) v_n:
+    dp = (gamma-1)(x_E - v.x_m + |v|^2/2 x_rho), H = (rho E + p)/rho."""
+    rho = uh[0]
+    v = [uh[1 + j] / rho for j in range(d)]
+    p = pressure(uh, prm, d)
+    H = (uh[d + 1] + p) / rho
+    vn = v[0] * n[0]
+    q2 = v[0] * v[0]
+    vdm = v[0] * x[1]
+    ndm = x[1] * n[0]
+    for j in range(1, d):
+        vn = vn + v[j] * n[j]
+        q2 = q2 + v[j] * v[j]
+        vdm = vdm + v[j] * x[1 + j]
+        ndm = ndm + x[1 + j] * n[j]
+    dp = (prm.gamma - 1.0) * (x[d + 1] - vdm + 0.5 * q2 * x[0])
+    out = [ndm]
+    for j in range(d):
+        out.append(x[1 + j] * vn + v[j] * ndm - v[j] * vn * x[0] + dp * n[j])
+    out.append((x[d + 1] + dp) * vn + H * (ndm - vn * x[0]))
+    return out
+
+
+FACE_INTERIOR, FACE_FARFIELD, FACE_WALL = 0, 1, 2
+
+
+def boundary_flux(uh, u, q, n, prm, d, kind, ub):
+    """Boundary flux bhat of the trace equation on a boundary face (Eq. IEDG c).
+    Far field (inflow/outflow, Sec. 2.1): bhat = (A_n + |A_n|)/2 (uhat - u)
+    + (A_n - |A_n|)/2 (uhat - u_b), A_n and |A_n| at uhat, u_b the given state.
+    No-slip adiabatic wall: bhat = (rhohat - rho, rho vhat, fhat_E): the trace density
+    follows the interior, the trace velocity vanishes, and the normal energy flux
+    (the energy row of the numerical flux, pure heat flux at a no-slip wall) is zero."""
+    m = d + 2
+    if kind == FACE_FARFIELD:
+        a = [uh[i] - u[i] for i in range(m)]
+        b = [uh[i] - ub[i] for i in range(m)]
+        Aa = normal_jacobian_apply(uh, a, n, prm, d)
+        Ab = normal_jacobian_apply(uh, b, n, prm, d)
+        Sa = roe_dissipation(uh, a, n, prm, d)
+        Sb = roe_dissipation(uh, b, n, prm, d)
+        return [0.5 * (Aa[i] + Sa[i]) + 0.5 * (Ab[i] - Sb[i]) for i in range(m)]
+    if kind == FACE_WALL:
+        fh = numerical_flux(uh, u, q, n, prm, d)
+        return [uh[0] - u[0]] + [uh[1 + j] for j in range(d)] + [fh[m - 1]]
+    raise ValueError(f"unknown boundary kind {kind}")
+
+
+def boundary_flux_with_jacobians(uh, u, q, n, prm, d, kind, ub):
+    """Face points of one boundary kind: bhat [..., m] and its derivatives in uhat, u
+    [..., m, m] and q [..., m, m, d] (dual numbers, like numerical_flux_with_jacobians)."""
+    m = d + 2
+    shp = u.shape[:-1]
+    vals = ([uh[..., i] for i in range(m)] + [u[..., i] for i in range(m)]
+            + [q[..., i, j] for i in range(m) for j in range(d)])
+    duals = seed(vals)
+    uhd = duals[:m]
+    ud = duals[m:2 * m]
+    qd = [[duals[2 * m + i * d + j] for j in range(d)] for i in range(m)]
+    nn = [n[..., j] for j in range(d)]
+    ubl = [np.broadcast_to(np.asarray(ub[i], dtype=np.float64), shp) for i in range(m)]
+    bh = boundary_flux(uhd, ud, qd, nn, prm, d, kind, ubl)
+    b = np.zeros(shp + (m,))
+    buh = np.zeros(shp + (m, m))
+    bu = np.zeros(shp + (m, m))
+    bq = np.zeros(shp + (m, m, d))
+    for i in range(m):
+        bi = bh[i] if isinstance(bh[i], Dual) else Dual.const(bh[i], 2 * m + m * d)
+        b[..., i] = bi.v
+        buh[..., i, :] = bi.t[..., :m]
+        bu[..., i, :] = bi.t[..., m:2 * m]
+        bq[..., i, :, :] = bi.t[..., 2 * m:].reshape(shp + (m, d))
+    return b, buh, bu, bq
+
+
 def numerical_flux(uh, u, q, n, prm, d):
     """fhat_i = F_ij(uhat, q) n_j + S(uhat) (u - uhat)_i  (Eq. IEDG d); S = lambda I
     (Lax-Friedrichs, lambda = |vhat.n| + chat) or |A_n(uhat)| (Roe), by prm.stab."""

@@ -312,15 +312,20 @@ class MixedMesh:
     face_degree: np.ndarray     # [E, 2d]
     n_trace: int
     extent: tuple = field(default=None)
+    face_kind: np.ndarray = field(default=None)   # [E, 2d] 0 interior, 1 far field, 2 wall (None: all interior)
 
     @property
     def n_elem(self):
         return len(self.orders)
 
 
-def structured_mesh_mixed(d, N, orders, extent=None):
+def structured_mesh_mixed(d, N, orders, extent=None, boundary=None):
+    """boundary[r]: 0 = periodic in direction r (default), else the kind of the two
+    domain faces normal to r (1 far field, 2 no-slip wall); a domain-boundary face
+    carries private trace nodes of the element's own degree."""
     N = tuple(int(n) for n in (N if np.ndim(N) else [N] * d))
     extent = tuple(extent) if extent is not None else (1.0,) * d
+    boundary = tuple(boundary) if boundary is not None else (0,) * d
     orders = np.asarray(orders, dtype=np.int64)
     cells = [c for c in _multi(max(N), d) if all(c[r] < N[r] for r in range(d))]
     cells.sort(key=lambda c: tuple(reversed(c)))
@@ -329,11 +334,17 @@ def structured_mesh_mixed(d, N, orders, extent=None):
     assert len(orders) == E
     nf = 2 * d
     face_degree = np.zeros((E, nf), dtype=np.int64)
+    face_kind = np.zeros((E, nf), dtype=np.int64)
     for e, c in enumerate(cells):
         for f in range(nf):
             r, side = divmod(f, 2)
             nb = list(c)
-            nb[r] = (nb[r] + (1 if side else -1)) % N[r]
+            nb[r] = nb[r] + (1 if side else -1)
+            if boundary[r] and not (0 <= nb[r] < N[r]):
+                face_degree[e, f] = orders[e]
+                face_kind[e, f] = boundary[r]
+                continue
+            nb[r] %= N[r]
             pe, pn = orders[e], orders[index[tuple(nb)]]
             face_degree[e, f] = 0 if pe == pn else max(pe, pn)
     node_xyz, keys = [], []
@@ -348,13 +359,20 @@ def structured_mesh_mixed(d, N, orders, extent=None):
         for a, ai in enumerate(nodes):
             on_edg = any(ai[f // 2] == (p if f % 2 else 0) for f in edg_faces)
             if on_edg:
-                pos = tuple((c[r] * p + ai[r]) % (N[r] * p) for r in range(d))
+                # lattice position (wrapped in the periodic directions only)
+                pos = tuple((c[r] * p + ai[r]) % (N[r] * p) if not boundary[r] else c[r] * p + ai[r]
+                            for r in range(d))
                 ek.append(("E", p, tuple(reversed(pos))))
         for f in range(nf):
             q = int(face_degree[e, f])
             if q == 0:
                 continue
             r, side = divmod(f, 2)
+            if face_kind[e, f]:
+                # domain boundary: the face belongs to this element alone
+                for j in range((q + 1) ** (d - 1)):
+                    ek.append(("H", e, nf + f, j))
+                continue
             # the face is owned by the cell on its -r side; key = (that cell, r)
             owner = list(c)
             if not side:
@@ -366,7 +384,8 @@ def structured_mesh_mixed(d, N, orders, extent=None):
     allkeys = sorted({k for ek in keys for k in ek}, key=lambda k: (k[0] != "E", k[1:]))
     gid = {k: i for i, k in enumerate(allkeys)}
     elem_trace = [np.array([gid[k] for k in ek], dtype=np.int64) for ek in keys]
-    return MixedMesh(d, N, orders, node_xyz, elem_trace, face_degree, len(allkeys), extent)
+    return MixedMesh(d, N, orders, node_xyz, elem_trace, face_degree, len(allkeys), extent,
+                     face_kind if face_kind.any() else None)
 
 
 def make_state_mixed(mesh, field, seed, noise=0.0):

@@ -181,3 +181,84 @@ def test_roe_flux_consistency_and_jacobians(d):
         fp, *_ = physics.numerical_flux_with_jacobians((uh + du)[None], u[None], q[None], n[None], PRM_ROE, d)
         fm, *_ = physics.numerical_flux_with_jacobians((uh - du)[None], u[None], q[None], n[None], PRM_ROE, d)
         np.testing.assert_allclose((fp - fm)[0] / (2 * du[k]), fuh[0][:, k], rtol=1e-6, atol=1e-7)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_normal_jacobian_apply_matches_dual_jacobian(d):
+    rng = np.random.default_rng(60 + d)
+    uh, _ = _state(d, rng)
+    n = rng.normal(size=d)
+    n /= np.linalg.norm(n)
+    An = _normal_jacobian(uh, n, d)
+    for k in range(d + 2):
+        x = np.eye(d + 2)[k]
+        np.testing.assert_allclose(np.array(physics.normal_jacobian_apply(uh, x, n, PRM, d)), An[:, k],
+                                   rtol=1e-13, atol=1e-13 * np.abs(An).max())
+
+
+def _bflux(uh, u, q, n, d, kind, ub, prm=PRM):
+    b, buh, bu, bq = physics.boundary_flux_with_jacobians(uh[None], u[None], q[None], n[None], prm, d, kind, ub)
+    return b[0], buh[0], bu[0], bq[0]
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_farfield_boundary_flux(d):
+    """Upwinding of the far-field flux: free stream gives zero; with u = u_b only the
+    A_n (uhat - u) part is left; supersonic outflow ignores u_b and supersonic inflow
+    ignores u (every wave leaves, resp. enters, through the face)."""
+    rng = np.random.default_rng(70 + d)
+    uh, q = _state(d, rng)
+    u, _ = _state(d, rng)
+    ub, _ = _state(d, rng)
+    n = rng.normal(size=d)
+    n /= np.linalg.norm(n)
+    K = physics.FACE_FARFIELD
+    b, *_ = _bflux(uh, uh, q, n, d, K, uh)
+    assert np.abs(b).max() < 1e-12 * np.abs(uh).max()
+    An = _normal_jacobian(uh, n, d)
+    b, *_ = _bflux(uh, u, q, n, d, K, u)
+    np.testing.assert_allclose(b, An @ (uh - u), rtol=1e-12, atol=1e-12 * np.abs(An).max())
+    rho = uh[0]
+    p = 0.4 * (uh[-1] - 0.5 * uh[1:d + 1] @ uh[1:d + 1] / rho)
+    c = np.sqrt(1.4 * p / rho)
+    for sgn in (1.0, -1.0):
+        v = sgn * 2.5 * c * n
+        us = np.concatenate([[rho], rho * v, [p / 0.4 + 0.5 * rho * v @ v]])
+        As = _normal_jacobian(us, n, d)
+        b, *_ = _bflux(us, u, q, n, d, K, ub)
+        ref = As @ (us - u) if sgn > 0 else As @ (us - ub)
+        np.testing.assert_allclose(b, ref, rtol=1e-10, atol=1e-10 * np.abs(As).max())
+
+
+@pytest.mark.parametrize("kind", [1, 2])
+@pytest.mark.parametrize("d", [2, 3])
+def test_boundary_flux_jacobians_by_finite_differences(d, kind):
+    rng = np.random.default_rng(80 + d + 10 * kind)
+    uh, q = _state(d, rng)
+    u, _ = _state(d, rng)
+    ub, _ = _state(d, rng)
+    n = rng.normal(size=d)
+    n /= np.linalg.norm(n)
+    b, buh, bu, bq = _bflux(uh, u, q, n, d, kind, ub)
+    if kind == physics.FACE_WALL:
+        f, *_ = physics.numerical_flux_with_jacobians(uh[None], u[None], q[None], n[None], PRM, d)
+        np.testing.assert_allclose(b, np.concatenate([[uh[0] - u[0]], uh[1:d + 1], [f[0][-1]]]), rtol=1e-14)
+    h = 1e-6
+    for k in range(d + 2):
+        e = np.zeros(d + 2)
+        e[k] = h * max(1.0, abs(uh[k]))
+        bp, *_ = _bflux(uh + e, u, q, n, d, kind, ub)
+        bm, *_ = _bflux(uh - e, u, q, n, d, kind, ub)
+        np.testing.assert_allclose((bp - bm) / (2 * e[k]), buh[:, k], rtol=1e-6, atol=1e-6)
+        e = np.zeros(d + 2)
+        e[k] = h * max(1.0, abs(u[k]))
+        bp, *_ = _bflux(uh, u + e, q, n, d, kind, ub)
+        bm, *_ = _bflux(uh, u - e, q, n, d, kind, ub)
+        np.testing.assert_allclose((bp - bm) / (2 * e[k]), bu[:, k], rtol=1e-6, atol=1e-6)
+    for k in range(d + 2):
+        for l in range(d):
+            dq = np.zeros_like(q)
+            dq[k, l] = h
+            bp, *_ = _bflux(uh, u, q + dq, n, d, kind, ub)
+            bm, *_ = _bflux(uh, u, q - dq, n, d, kind, ub)
+            np.testing.assert_allclose((bp - bm) / (2 * h), bq[:, k, l], rtol=1e-6, atol=1e-7)

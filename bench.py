@@ -317,6 +317,7 @@ def run_ours(args, wl, rank, world, local_rank):
     torch.cuda.empty_cache()
     if world == 1 and not args.no_mixed_orders:
         mixed_orders = run_mixed_orders(args, dev, flush)
+    extras = run_extras(args, dev) if (world == 1 and not args.no_extras) else None
     from paper_1605_01020_gb300.dist import max_over_ranks
     ms, ms_e2e = max_over_ranks([ms, ms_e2e], dev)
     if mixed is not None:
@@ -377,6 +378,7 @@ def run_ours(args, wl, rank, world, local_rank):
             "element_status_nonzero": int((status != 0).sum()),
             "mixed": mixed,
             "mixed_orders": mixed_orders,
+            "extras": extras,
             "peaks": {"source": src, **{k: v for k, v in peaks.items() if isinstance(v, (int, float))}}}
     print(json.dumps(line), flush=True)
 
@@ -531,6 +533,80 @@ def run_mixed_orders(args, dev, flush):
     return res
 
 
+def run_extras(args, dev):
+    """Measurements of the rows beyond the condensation itself, each on its own small
+    workload: the Roe-type stabilisation (assembly + condensation of the 3D p=3 16^3
+    workload in FP64, against Lax-Friedrichs on the same handle type), the trace
+    solve (GMRES with block Jacobi and with BILU(0), 3D p=3 8^3), and one DIRK(3,3)
+    time step with Newton per stage (2D p=2 8x8)."""
+    import torch
+    from paper_1605_01020_gb300 import iedg, timestep
+    from paper_1605_01020_gb300 import workloads as W
+    f64 = torch.float64
+    out = {}
+    ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    # Roe vs Lax-Friedrichs, one assemble_condensed call each (median of 3 after 2 warm-ups)
+    wl = W.config(2, N=args.cells)
+    st = wl.state
+    u, q, uh = (torch.as_tensor(a, dtype=f64, device=dev) for a in (st.u, st.q, st.uhat))
+    for name, stab in (("lax_friedrichs", 0), ("roe", 1)):
+        mesh = iedg.mesh_from_workload(W.Workload(wl.name, wl.mesh, st, dict(wl.params, stab=stab)))
+        K = torch.empty(mesh.nnzb, mesh.m, mesh.m, dtype=f64, device=dev)
+        R = torch.empty(mesh.T, mesh.m, dtype=f64, device=dev)
+        ts = []
+        for i in range(5):
+            a0, a1 = ev()
+            a0.record()
+            mesh.assemble_condensed(u, q, uh, K=K, R=R)
+            a1.record()
+            torch.cuda.synchronize()
+            if i >= 2:
+                ts.append(a0.elapsed_time(a1))
+        out[f"assemble_condensed_{name}"] = {"ms": statistics.median(ts), "elements": mesh.E,
+                                             "elements_per_s": mesh.E / (statistics.median(ts) / 1e3)}
+        mesh.close()
+    del u, q, uh, K, R
+    torch.cuda.empty_cache()
+    # trace solve on the condensed K of the 8^3 case
+    wl = W.config(2, N=8)
+    st = wl.state
+    mesh = iedg.mesh_from_workload(wl)
+    u, q, uh = (torch.as_tensor(a, dtype=f64, device=dev) for a in (st.u, st.q, st.uhat))
+    K, R = mesh.assemble_condensed(u, q, uh)
+    for name, kind in (("block_jacobi", iedg.PREC_BLOCK_JACOBI), ("bilu0", iedg.PREC_BILU0)):
+        mesh.set_trace_precond(kind)
+        mesh.trace_solve(K, R, rtol=1e-10, max_iter=3000)             # warm-up (colouring on first use)
+        t0 = time.perf_counter()
+        dU, its, rr = mesh.trace_solve(K, R, rtol=1e-10, max_iter=3000)
+        torch.cuda.synchronize()
+        out[f"trace_solve_{name}"] = {"ms": 1e3 * (time.perf_counter() - t0), "iterations": its,
+                                      "rel_residual": rr, "trace_nodes": mesh.T,
+                                      "workload": "3D p=3 8^3 condensed K, rtol 1e-10, restart 30"}
+    mesh.close()
+    del u, q, uh, K, R
+    torch.cuda.empty_cache()
+    # one DIRK(3,3) step, Newton per stage, minimal-residual guess from the 3rd step on
+    wl = W.config(1)
+    st = W.make_state(wl.mesh, W.fourier_perturbed_field(2, 0.2, 41, amp=0.05), 42, noise=0.005)
+    mesh = iedg.mesh_from_workload(wl)
+    u = torch.as_tensor(st.u, dtype=f64, device=dev)
+    uh = torch.as_tensor(st.uhat, dtype=f64, device=dev)
+    q = mesh.eval_residual(u, uh, q=None)["q"]
+    stepper = timestep.Stepper(mesh, 0.005, newton_tol=1e-10)
+    state = (u, q, uh)
+    times = []
+    for n in range(4):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        state = stepper.step(*state, use_mr=True)[:3]
+        torch.cuda.synchronize()
+        times.append(1e3 * (time.perf_counter() - t0))
+    out["dirk33_step"] = {"ms_per_step": statistics.median(times[1:]), "newton_iterations": stepper.newton_iters,
+                          "workload": "2D p=2 8x8, dt = 0.005, Newton to 1e-10, GMRES + block Jacobi"}
+    mesh.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -543,6 +619,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch schedule")
     ap.add_argument("--no-mixed-orders", action="store_true", help="skip the mixed-order batch (p in {2,3,4})")
+    ap.add_argument("--no-extras", action="store_true", help="skip the Roe / trace-solve / DIRK measurements")
     ap.add_argument("--mo-cells", type=int, default=None, help="mixed-order batch: N x N x 2N cells (default 16)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-elems", type=int, default=4)

@@ -122,6 +122,23 @@ int iedg_create_mesh(const iedg_mesh_desc* desc, void* stream, iedg_mesh** out);
 int iedg_create_mesh_mixed(const iedg_mesh_desc* desc, const int32_t* elem_order,
                            const int32_t* face_degree, void* stream, iedg_mesh** out);
 
+/* Meshes with domain boundaries (Sec. 2.1: the IEDG trace is continuous on interior
+ * faces and discontinuous on boundary faces).  As iedg_create_mesh_mixed, plus
+ * face_kind (HOST int32 [n_elem][2 dim], NULL = every face interior):
+ *   0  interior face (shared with the neighbour, as above);
+ *   1  far field (inflow / outflow): the trace equation on the face takes
+ *      bhat = (A_n + |A_n|)/2 (uhat - u) + (A_n - |A_n|)/2 (uhat - u_far), A_n the
+ *      normal Jacobian of the Euler flux and |A_n| its absolute value, both at uhat;
+ *   2  no-slip adiabatic wall: bhat = (rhohat - rho, rho vhat, fhat_E), i.e. the trace
+ *      density follows the interior, the trace velocity vanishes and the energy row of
+ *      the numerical flux (the normal heat flux at a no-slip wall) is zero.
+ * A boundary face must have face_degree equal to the element's order (its private
+ * trace nodes belong to this element alone).  u_far (HOST double [m]) is required
+ * when some face is a far-field face.  The element equations use the numerical flux
+ * fhat on every face. */
+int iedg_create_mesh_bc(const iedg_mesh_desc* desc, const int32_t* elem_order, const int32_t* face_degree,
+                        const int32_t* face_kind, const double* u_far, void* stream, iedg_mesh** out);
+
 /* Per-element node and trace-slot counts, HOST int32 [n_elem] each (either may be
  * NULL); for uniform meshes every entry is Np, Nb. */
 int iedg_element_sizes(const iedg_mesh* mesh, int32_t* Np, int32_t* Nb);

@@ -392,6 +392,7 @@ static int alloc_group(iedg_mesh* M, cudaStream_t st) {
   CUDA_TRY(dalloc(M, &M->pj.Jf, E * m * m * (1 + d) * Nfp));
   CUDA_TRY(dalloc(M, &M->pj.lamw, E * Nfp));
   if (M->ph.stab == 1) CUDA_TRY(dalloc(M, &M->pj.Su, E * m * m * Nfp));
+  if (M->has_boundary) CUDA_TRY(dalloc(M, &M->pj.Jb, E * m * m * (2 + d) * Nfp));
   CUDA_TRY(dalloc(M, &M->qstar, E * Np * m * d));
   CUDA_TRY(dalloc(M, &M->rhoq, E * Np * m * d));
   if (M->precision == IEDG_PRECISION_MIXED) {
@@ -401,6 +402,7 @@ static int alloc_group(iedg_mesh* M, cudaStream_t st) {
     CUDA_TRY(dalloc(M, &M->pj.Jf32, E * m * m * (1 + d) * Nfp));
     CUDA_TRY(dalloc(M, &M->pj.lamw32, E * Nfp));
     if (M->ph.stab == 1) CUDA_TRY(dalloc(M, &M->pj.Su32, E * m * m * Nfp));
+    if (M->has_boundary) CUDA_TRY(dalloc(M, &M->pj.Jb32, E * m * m * (2 + d) * Nfp));
     CUDA_TRY(dalloc(M, &G.Mass32, E * Np * Np));
     CUDA_TRY(dalloc(M, &G.GlV32, E * d * Nq * Np));
     CUDA_TRY(dalloc(M, &G.HlV32, E * d * Nq * Nb));
@@ -532,7 +534,7 @@ extern "C" int iedg_create_mesh(const iedg_mesh_desc* D, void* stream, iedg_mesh
   if (rc != IEDG_OK) return rc;
   M = new iedg_mesh();
   M->dm = make_dims(D->dim, D->order, D->quad_extra);
-  M->ph = Phys{D->gamma, D->Pr, D->Re, D->alpha, D->stab};
+  M->ph = Phys{D->gamma, D->Pr, D->Re, D->alpha, D->stab, {0, 0, 0, 0, 0}};
   M->precision = D->precision;
   M->E = D->n_elem;
   M->T = D->n_trace;
@@ -560,16 +562,23 @@ static cudaError_t upload_to(iedg_mesh* M, const T** p, const std::vector<T>& h,
   return e;
 }
 
-static int create_mixed_impl(const iedg_mesh_desc* D, const int32_t* ord, const int32_t* fdeg, cudaStream_t st,
-                             iedg_mesh* M) {
+static int create_mixed_impl(const iedg_mesh_desc* D, const int32_t* ord, const int32_t* fdeg,
+                             const int32_t* fkind, cudaStream_t st, iedg_mesh* M) {
   const int d = D->dim, nf = 2 * d, m = d + 2;
   const int64_t E = M->E;
   const int pmax_allowed = d == 3 ? 4 : 3;
   for (int64_t e = 0; e < E; ++e) {
     if (ord[e] < 1 || ord[e] > pmax_allowed) return fail(M, IEDG_ERR_UNSUPPORTED, "element order out of range");
-    for (int f = 0; f < nf; ++f)
+    for (int f = 0; f < nf; ++f) {
       if (fdeg[e * nf + f] < 0 || fdeg[e * nf + f] > 4)
         return fail(M, IEDG_ERR_UNSUPPORTED, "face degree must be 0 (continuous) or 1..4");
+      if (fkind) {
+        const int k = fkind[e * nf + f];
+        if (k < kFaceInterior || k > kFaceWall) return fail(M, IEDG_ERR_INVALID_ARG, "face kind must be 0, 1 or 2");
+        if (k != kFaceInterior && fdeg[e * nf + f] != ord[e])
+          return fail(M, IEDG_ERR_INVALID_ARG, "a boundary face must carry private nodes of the element's degree");
+      }
+    }
   }
   std::vector<Dims> dmp(5);
   std::vector<HostRef> refs(5);
@@ -679,6 +688,10 @@ static int create_mixed_impl(const iedg_mesh_desc* D, const int32_t* ord, const 
     C->E = (int64_t)gel[c].size();
     C->T = M->T;
     C->sched = M->sched;
+    if (fkind)
+      for (int64_t e : gel[c])
+        for (int f = 0; f < nf; ++f)
+          if (fkind[e * nf + f] != kFaceInterior) C->has_boundary = true;
     rhat_off.push_back(rhat_total);
     re_off.push_back(re_total);
     rhat_total += C->E * (int64_t)nbmax * m;
@@ -732,7 +745,8 @@ static int create_mixed_impl(const iedg_mesh_desc* D, const int32_t* ord, const 
         int q = fdeg[e * nf + f];
         if (q > 0) NFS = std::max(NFS, d == 3 ? (q + 1) * (q + 1) : q + 1);
       }
-    std::vector<int> t_nb(Ec), t_nfs(Ec * nf, 0), t_fs(Ec * nf * NFS, 0), t_fdeg(Ec * nf), t_sfl(Ec * Nb * 3, -1);
+    std::vector<int> t_nb(Ec), t_nfs(Ec * nf, 0), t_fs(Ec * nf * NFS, 0), t_fdeg(Ec * nf), t_sfl(Ec * Nb * 3, -1),
+        t_kind(Ec * nf, 0);
     std::vector<double> t_muf((size_t)Ec * nf * Nfq * NFS, 0.0);
     std::vector<int64_t> t_et((size_t)Ec * Nb, 0), t_gnode(Ec);
     std::vector<double> X((size_t)Ec * Np * d);
@@ -749,6 +763,7 @@ static int create_mixed_impl(const iedg_mesh_desc* D, const int32_t* ord, const 
       for (int f = 0; f < nf; ++f) {
         const int q = fdeg[e * nf + f];
         t_fdeg[k * nf + f] = q;
+        t_kind[k * nf + f] = fkind ? fkind[e * nf + f] : kFaceInterior;
         int* fsf = &t_fs[((size_t)k * nf + f) * NFS];
         double* mu = &t_muf[((size_t)k * nf + f) * Nfq * NFS];
         if (q == 0) {
@@ -798,6 +813,7 @@ static int create_mixed_impl(const iedg_mesh_desc* D, const int32_t* ord, const 
     CUDA_TRY(upload_to(C, &tt.fdeg, t_fdeg, st));
     CUDA_TRY(upload_to(C, &tt.muf, t_muf, st));
     CUDA_TRY(upload_to(C, &tt.sfl, t_sfl, st));
+    if (C->has_boundary) CUDA_TRY(upload_to(C, &tt.fkind, t_kind, st));
     CUDA_TRY(upload(C, &C->etrace, t_et, st));
     CUDA_TRY(upload(C, &C->gnode, t_gnode, st));
     tt.soff = M->lud.soff + M->gstart[c];
@@ -830,19 +846,26 @@ static int create_mixed_impl(const iedg_mesh_desc* D, const int32_t* ord, const 
   return IEDG_OK;
 }
 
-extern "C" int iedg_create_mesh_mixed(const iedg_mesh_desc* D, const int32_t* elem_order,
-                                      const int32_t* face_degree, void* stream, iedg_mesh** out) {
+extern "C" int iedg_create_mesh_bc(const iedg_mesh_desc* D, const int32_t* elem_order, const int32_t* face_degree,
+                                   const int32_t* face_kind, const double* u_far, void* stream, iedg_mesh** out) {
   iedg_mesh* M = nullptr;
   if (!D || !out || !elem_order || !face_degree) return fail(M, IEDG_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
   int rc = check_desc(D, true);
   if (rc != IEDG_OK) return rc;
+  const int nf = 2 * D->dim, m = D->dim + 2;
+  bool farfield = false;
+  if (face_kind)
+    for (int64_t i = 0; i < D->n_elem * nf; ++i) farfield = farfield || face_kind[i] == kFaceFarField;
+  if (farfield && !u_far) return fail(M, IEDG_ERR_INVALID_ARG, "far-field faces need the far-field state u_far");
   M = new iedg_mesh();
-  M->ph = Phys{D->gamma, D->Pr, D->Re, D->alpha, D->stab};
+  M->ph = Phys{D->gamma, D->Pr, D->Re, D->alpha, D->stab, {0, 0, 0, 0, 0}};
+  if (u_far)
+    for (int i = 0; i < m; ++i) M->ph.ub[i] = u_far[i];
   M->precision = D->precision;
   M->E = D->n_elem;
   M->T = D->n_trace;
-  rc = create_mixed_impl(D, elem_order, face_degree, (cudaStream_t)stream, M);
+  rc = create_mixed_impl(D, elem_order, face_degree, face_kind, (cudaStream_t)stream, M);
   if (rc != IEDG_OK) {
     g_err = M->err;
     destroy_impl(M);
@@ -850,6 +873,11 @@ extern "C" int iedg_create_mesh_mixed(const iedg_mesh_desc* D, const int32_t* el
   }
   *out = M;
   return IEDG_OK;
+}
+
+extern "C" int iedg_create_mesh_mixed(const iedg_mesh_desc* D, const int32_t* elem_order,
+                                      const int32_t* face_degree, void* stream, iedg_mesh** out) {
+  return iedg_create_mesh_bc(D, elem_order, face_degree, nullptr, nullptr, stream, out);
 }
 
 extern "C" int iedg_element_sizes(const iedg_mesh* M, int32_t* Np, int32_t* Nb) {

@@ -181,6 +181,34 @@ k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, AsmTab<T> tb, T* __restri
       facc[ref.slot[a] * CW + cc] += s;
     }
     if (mix) {
+      // domain-boundary face: the trace rows take the boundary flux, so the right
+      // operand is rebuilt from its derivatives
+      if (tt.fkind && tt.fkind[e * dm.nf + f] != kFaceInterior) {
+        __syncthreads();
+        const int nc = 2 + d;
+        for (int idx = tid; idx < Nfq * CW; idx += AS_THREADS) {
+          int gf = idx / CW, col = c0 + idx % CW;
+          int fp = f * Nfq + gf;
+          const T* jb = tb.Jb + ((size_t)e * dm.m * dm.m + pair) * nc * Nfp + fp;
+          T v = 0;
+          if (col < Np) {
+            v = jb[(size_t)Nfp] * tb.PhiF[(size_t)fp * Np + col];
+            for (int l = 0; l < d; ++l) v -= jb[(size_t)(2 + l) * Nfp] * GlF[((size_t)l * Nfp + fp) * Np + col];
+          } else if (col < ncol) {
+            int t = col - Np;
+            T mu = 0;
+            const int* fl = tt.sfl + ((size_t)e * NbT + t) * 3;
+            for (int q = 0; q < 3; ++q) {
+              const int code = fl[q];
+              if (code >= 0 && code / tt.NFS == f) mu = mutab[((size_t)f * Nfq + gf) * tt.NFS + code % tt.NFS];
+            }
+            v = jb[0] * mu;
+            for (int l = 0; l < d; ++l) v += jb[(size_t)(2 + l) * Nfp] * HlF[((size_t)l * Nfp + fp) * NbT + t];
+          }
+          sV[idx] = v;
+        }
+        __syncthreads();
+      }
       // trace rows: the slots living on this face, with the element's trace basis
       const int cnt = tt.nfs[e * dm.nf + f];
       const int* fsf = tt.fs + ((size_t)e * dm.nf + f) * tt.NFS;
@@ -834,13 +862,14 @@ static cudaError_t assemble_t(iedg_mesh* M, T* S, const double* rhs64, const Asm
 AsmTab<double> tables64(const iedg_mesh* M) {
   const Geo& G = M->geo;
   const PointJac& P = M->pj;
-  return AsmTab<double>{M->ref.Phi, M->ref.Dxi, M->ref.PhiF, P.Jv, P.Jf, P.lamw, P.Su, G.GlV, G.HlV, G.GlF, G.HlF, G.Mass};
+  return AsmTab<double>{M->ref.Phi, M->ref.Dxi, M->ref.PhiF, P.Jv, P.Jf, P.lamw, P.Su, P.Jb,
+                        G.GlV, G.HlV, G.GlF, G.HlF, G.Mass};
 }
 
 AsmTab<float> tables32(const iedg_mesh* M) {
   const Geo& G = M->geo;
   const PointJac& P = M->pj;
-  return AsmTab<float>{M->ref.Phi32, M->ref.Dxi32, M->ref.PhiF32, P.Jv32, P.Jf32, P.lamw32, P.Su32,
+  return AsmTab<float>{M->ref.Phi32, M->ref.Dxi32, M->ref.PhiF32, P.Jv32, P.Jf32, P.lamw32, P.Su32, P.Jb32,
                        G.GlV32, G.HlV32, G.GlF32, G.HlF32, G.Mass32};
 }
 

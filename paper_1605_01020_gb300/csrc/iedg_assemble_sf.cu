@@ -149,7 +149,52 @@ k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, 
         Vf[gf * CC + c] = v;
       }
       __syncthreads();
+      // U[g1][a2] = sum_g2 L[g2][a2] Vf[g1 + nq1 g2]
+      for (int idx = tid; idx < nq1 * np1 * CC; idx += SF_THREADS) {
+        const int t = idx / CC, c = idx % CC, g1 = t % nq1, a2 = t / nq1;
+        T u = 0;
+        for (int g2 = 0; g2 < nq1; ++g2) u = fma(sL[g2 * np1 + a2], Vf[(g1 + nq1 * g2) * CC + c], u);
+        Uf[(g1 * UW + a2) * CC + c] = u;
+      }
+      __syncthreads();
+      // node (a1, a2) of the face: sum_g1 L[g1][a1] U[g1][a2]
+      for (int idx = tid; idx < Nfn * CC; idx += SF_THREADS) {
+        const int tn = idx / CC, c = idx % CC, a1 = tn % np1, a2 = tn / np1;
+        T s = 0;
+        for (int g1 = 0; g1 < nq1; ++g1) s = fma(sL[g1 * np1 + a1], Uf[(g1 * UW + a2) * CC + c], s);
+        facc[ref.slot[ref.fnode[f * Nfn + tn]] * CC + c] += s;
+        if (MIX && fq == 0) tacc[fsf[tn] * CC + c] += s;   // continuous face: same sums, trace rows
+      }
       if (MIX && fq > 0) {
+        __syncthreads();
+        if (tt.fkind && tt.fkind[e * 6 + f] != kFaceInterior) {
+          // domain-boundary face: the trace rows take the boundary flux; rebuild the
+          // right operand from its derivatives (wf dbhat/duhat, dbhat/du, dbhat/dq_l)
+          const T* jbt = tb.Jb;
+          for (int idx = tid; idx < Nfq * CC; idx += SF_THREADS) {
+            const int gf = idx / CC, c = idx % CC, col = c0 + c;
+            const int fp = f * Nfq + gf;
+            const T* jb = jbt + ((size_t)e * m2 + pair) * (2 + d) * Nfp + fp;
+            T v = 0;
+            if (col < Np) {
+              v = jb[(size_t)Nfp] * tb.PhiF[(size_t)fp * Np + col];
+              for (int l = 0; l < d; ++l) v -= jb[(size_t)(2 + l) * Nfp] * GlF[((size_t)l * Nfp + fp) * Np + col];
+            } else if (col < ncol_all) {
+              const int t = col - Np;
+              T mu = 0;
+              const int* fl = tt.sfl + ((size_t)e * dm.Nb + t) * 3;
+#pragma unroll
+              for (int q = 0; q < 3; ++q) {
+                const int code = fl[q];
+                if (code >= 0 && code / tt.NFS == f) mu = mutab[((size_t)f * Nfq + gf) * tt.NFS + code % tt.NFS];
+              }
+              v = jb[0] * mu;
+              for (int l = 0; l < d; ++l) v += jb[(size_t)(2 + l) * Nfp] * HlF[((size_t)l * Nfp + fp) * NbT + t];
+            }
+            Vf[gf * CC + c] = v;
+          }
+          __syncthreads();
+        }
         // trace rows of the face's private nodes j = j1 + (q+1) j2:
         // sum_{g1,g2} LQ_q[g1][j1] LQ_q[g2][j2] Vf[g1 + nq1 g2]
         const int q1 = fq + 1;
@@ -168,22 +213,6 @@ k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, 
           tacc[fsf[j] * CC + c] += s;
         }
         __syncthreads();
-      }
-      // U[g1][a2] = sum_g2 L[g2][a2] Vf[g1 + nq1 g2]
-      for (int idx = tid; idx < nq1 * np1 * CC; idx += SF_THREADS) {
-        const int t = idx / CC, c = idx % CC, g1 = t % nq1, a2 = t / nq1;
-        T u = 0;
-        for (int g2 = 0; g2 < nq1; ++g2) u = fma(sL[g2 * np1 + a2], Vf[(g1 + nq1 * g2) * CC + c], u);
-        Uf[(g1 * UW + a2) * CC + c] = u;
-      }
-      __syncthreads();
-      // node (a1, a2) of the face: sum_g1 L[g1][a1] U[g1][a2]
-      for (int idx = tid; idx < Nfn * CC; idx += SF_THREADS) {
-        const int tn = idx / CC, c = idx % CC, a1 = tn % np1, a2 = tn / np1;
-        T s = 0;
-        for (int g1 = 0; g1 < nq1; ++g1) s = fma(sL[g1 * np1 + a1], Uf[(g1 * UW + a2) * CC + c], s);
-        facc[ref.slot[ref.fnode[f * Nfn + tn]] * CC + c] += s;
-        if (MIX && fq == 0) tacc[fsf[tn] * CC + c] += s;   // continuous face: same sums, trace rows
       }
     }
     // ---- volume right operands W_r[g][c] for the three reference directions

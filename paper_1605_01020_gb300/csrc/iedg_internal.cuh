@@ -23,8 +23,12 @@ struct Dims {
 
 struct Phys {
   double gamma, Pr, Re, alpha;
-  int stab;   // 0 = Lax-Friedrichs, 1 = Roe-type |A_n(uhat)|
+  int stab;        // 0 = Lax-Friedrichs, 1 = Roe-type |A_n(uhat)|
+  double ub[5];    // far-field state of far-field boundary faces
 };
+
+// face kinds of meshes with domain boundaries
+constexpr int kFaceInterior = 0, kFaceFarField = 1, kFaceWall = 2;
 
 // Launch schedule (host-side choices the autotuner sweeps; see iedg_schedule).
 struct Schedule {
@@ -79,7 +83,9 @@ struct PointJac {
   double* Jf;     // [E][m][m][1+d][Nfp]   : c=0: wf dfhat/duhat ; c=1+l: wf dfhat/dq_l
   double* lamw;   // [E][Nfp]              : wf lambda  (dfhat/du = lambda I, Lax-Friedrichs)
   double* Su;     // [E][m][m][Nfp]        : wf dfhat_i/du_k = wf S_ik (Roe-type only, else null)
-  float *Jv32, *Jf32, *lamw32, *Su32;   // FP32 copies written by the point kernel (mixed path only)
+  double* Jb;     // [E][m][m][2+d][Nfp]   : boundary faces only: wf dbhat/duhat, wf dbhat/du,
+                  //                          wf dbhat/dq_l (null without boundary faces)
+  float *Jv32, *Jf32, *lamw32, *Su32, *Jb32;   // FP32 copies written by the point kernel (mixed path only)
 };
 
 // Per-element trace description of meshes with mixed orders.  A face shared with an
@@ -96,6 +102,7 @@ struct TraceTab {
   const double* muf = nullptr;     // [E][nf][Nfq][NFS] their values at the face points
   const float* muf32 = nullptr;
   const int* sfl = nullptr;        // [E][Nb][3] faces of each slot, f NFS + j (-1 = none)
+  const int* fkind = nullptr;      // [E][nf] kFace* (null: no domain boundary)
   const int64_t* soff = nullptr;   // [E] offset of the element's bordered matrix in S
   const int* ldv = nullptr;        // [E] its leading dimension
   int NFS = 0;
@@ -126,7 +133,7 @@ struct RaggedSrc {
 template <class T>
 struct AsmTab {
   const T *Phi, *Dxi, *PhiF;
-  const T *Jv, *Jf, *lamw, *Su;
+  const T *Jv, *Jf, *lamw, *Su, *Jb;
   const T *GlV, *HlV, *GlF, *HlF, *Mass;
 };
 
@@ -163,6 +170,7 @@ struct iedg_mesh {
   // element matrices and the per-element sizes; one child handle per order holds the
   // element tables of that order (internal element ids are grouped by order)
   iedg::TraceTab tt;            // child: trace description of its elements
+  bool has_boundary = false;    // child: some element has a domain-boundary face
   bool mixed_orders = false;    // parent
   std::vector<iedg_mesh*> groups;
   std::vector<int64_t> gstart;  // parent: first internal id of each group

@@ -197,6 +197,119 @@ __device__ void roe_apply(const T* uh, const T* du, const double* n, const Phys&
   out[M - 1] = l0 * du[M - 1] + wm * (H + (-1.0) * (c * vn)) + wp * (H + c * vn);
 }
 
+// out = A_n(uh) x, A_n = d(F_inv . n)/du the normal Jacobian of the Euler flux at uh,
+// from the differentials of rho v_n, rho v v_n + p n, (rho E + p) v_n with
+// dp = (gamma-1)(x_E - v.x_m + |v|^2/2 x_rho) and H = (rho E + p)/rho.
+template <int D, class T>
+__device__ void normal_jac_apply(const T* uh, const T* x, const double* n, const Phys& ph, T* out) {
+  constexpr int M = D + 2;
+  const T rinv = recip(uh[0]);
+  T v[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) v[j] = uh[1 + j] * rinv;
+  T vn = mk<T>(0.0), q2 = mk<T>(0.0), vdm = mk<T>(0.0), ndm = mk<T>(0.0);
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    vn = vn + n[j] * v[j];
+    q2 = q2 + v[j] * v[j];
+    vdm = vdm + v[j] * x[1 + j];
+    ndm = ndm + n[j] * x[1 + j];
+  }
+  const T p = (ph.gamma - 1.0) * (uh[M - 1] + (-0.5) * (uh[0] * q2));
+  const T H = (uh[M - 1] + p) * rinv;
+  const T dp = (ph.gamma - 1.0) * (x[M - 1] + (-1.0) * vdm + 0.5 * (q2 * x[0]));
+  out[0] = ndm;
+#pragma unroll
+  for (int j = 0; j < D; ++j) out[1 + j] = x[1 + j] * vn + v[j] * ndm + (-1.0) * (v[j] * (vn * x[0])) + n[j] * dp;
+  out[M - 1] = (x[M - 1] + dp) * vn + H * (ndm + (-1.0) * (vn * x[0]));
+}
+
+// Far-field boundary flux (Sec. 2.1): bhat = (A_n + |A_n|)/2 (uh - u) + (A_n - |A_n|)/2
+// (uh - u_b), A_n and |A_n| at uh.  T = double or Dual<M> (uh seeded; u, u_b constant).
+template <int D, class T>
+__device__ void farfield_flux(const T* uh, const double* u, const double* ub, const double* n, const Phys& ph,
+                              T* b) {
+  constexpr int M = D + 2;
+  T a[M], c[M], Aa[M], Sa[M], Ac[M], Sc[M];
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    a[i] = uh[i] + mk<T>(-u[i]);
+    c[i] = uh[i] + mk<T>(-ub[i]);
+  }
+  normal_jac_apply<D, T>(uh, a, n, ph, Aa);
+  roe_apply<D, T>(uh, a, n, ph, Sa);
+  normal_jac_apply<D, T>(uh, c, n, ph, Ac);
+  roe_apply<D, T>(uh, c, n, ph, Sc);
+#pragma unroll
+  for (int i = 0; i < M; ++i) b[i] = 0.5 * (Aa[i] + Sa[i]) + 0.5 * (Ac[i] + (-1.0) * Sc[i]);
+}
+
+// Boundary flux of the trace equation at one face point of kind fk (far field or
+// no-slip adiabatic wall): wf bhat into bval[M] and, with jac, the point's entries of
+// Jb.  A wall's energy row is the energy row of fhat, whose derivatives the calling
+// thread wrote to Jf, Su / lamw just before; they are read back here.
+template <int D, int STAB>
+__device__ __noinline__ void boundary_point(int fk, const double* uh, const double* u, const double* n, double wf,
+                                            const Phys& ph, double fhatE, bool jac, const PointJac& PJ, int64_t e,
+                                            int fp, int Nfp, double* bval) {
+  constexpr int M = D + 2, NC = 2 + D;
+  const size_t jfs = (size_t)(1 + D) * Nfp;
+  auto jb = [&](int i, int k, int c) -> size_t { return (((size_t)(e * M + i) * M + k) * NC + c) * Nfp + fp; };
+  auto put = [&](int i, int k, int c, double v) {
+    PJ.Jb[jb(i, k, c)] = v;
+    if (PJ.Jb32) PJ.Jb32[jb(i, k, c)] = (float)v;
+  };
+  if (fk == kFaceFarField) {
+    double b[M];
+    farfield_flux<D, double>(uh, u, ph.ub, n, ph, b);
+#pragma unroll
+    for (int i = 0; i < M; ++i) bval[i] = wf * b[i];
+    if (!jac) return;
+    Dual<M> ud[M], bd[M];
+#pragma unroll
+    for (int k = 0; k < M; ++k) { ud[k] = mkconst<M>(uh[k]); ud[k].t[k] = 1.0; }
+    farfield_flux<D, Dual<M>>(ud, u, ph.ub, n, ph, bd);
+#pragma unroll 1
+    for (int k = 0; k < M; ++k) {
+      double ek[M], Ak[M], Sk[M];
+#pragma unroll
+      for (int i = 0; i < M; ++i) ek[i] = (i == k) ? 1.0 : 0.0;
+      normal_jac_apply<D, double>(uh, ek, n, ph, Ak);
+      roe_apply<D, double>(uh, ek, n, ph, Sk);
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        put(i, k, 0, wf * bd[i].t[k]);
+        put(i, k, 1, -0.5 * wf * (Ak[i] + Sk[i]));
+#pragma unroll
+        for (int l = 0; l < D; ++l) put(i, k, 2 + l, 0.0);
+      }
+    }
+    return;
+  }
+  // wall: (rhohat - rho, rho vhat, fhat_E)
+  bval[0] = wf * (uh[0] - u[0]);
+#pragma unroll
+  for (int j = 0; j < D; ++j) bval[1 + j] = wf * uh[1 + j];
+  bval[M - 1] = wf * fhatE;
+  if (!jac) return;
+  const double* jfE = PJ.Jf + ((size_t)e * M * M + (size_t)(M - 1) * M) * jfs;   // row E of this element
+#pragma unroll 1
+  for (int k = 0; k < M; ++k) {
+    for (int i = 0; i < M - 1; ++i) {
+      put(i, k, 0, (i == k) ? wf : 0.0);
+      put(i, k, 1, (i == 0 && k == 0) ? -wf : 0.0);
+      for (int l = 0; l < D; ++l) put(i, k, 2 + l, 0.0);
+    }
+    const double* o = jfE + (size_t)k * jfs;
+    put(M - 1, k, 0, o[fp]);
+    double su;
+    if constexpr (STAB == 1) su = PJ.Su[((size_t)(e * M + (M - 1)) * M + k) * Nfp + fp];
+    else su = (k == M - 1) ? PJ.lamw[e * Nfp + fp] : 0.0;
+    put(M - 1, k, 1, su);
+    for (int l = 0; l < D; ++l) put(M - 1, k, 2 + l, o[(size_t)(1 + l) * Nfp + fp]);
+  }
+}
+
 // dF[i][j][k] = dF_ij/du_k and dQ[i][j][k][l] = dF_ij/dq_kl at (u, q).
 template <int D>
 __device__ void flux_jacobians(const double* u, const double (*q)[D], const Phys& ph,
@@ -264,6 +377,7 @@ __global__ void k_points(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ,
   double* fvol = suh + Nb * M;             // [M][D][Nq]
   double* mvol = fvol + M * D * Nq;        // [M][Nq]
   double* fsur = mvol + M * Nq;            // [M][Nfp]
+  double* ftr = fsur + M * Nfp;            // [M][Nfp]  flux of the trace rows (bhat on boundary faces)
   const bool has_ref = UREF != nullptr && ph.alpha != 0.0;
   for (int i = tid; i < Np * M; i += nth) {
     su[i] = U[e * Np * M + i];
@@ -468,6 +582,17 @@ __global__ void k_points(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ,
       PJ.lamw[e * Nfp + fp] = wf * lam;
       if (PJ.lamw32) PJ.lamw32[e * Nfp + fp] = (float)(wf * lam);
     }
+    // trace rows: fhat on interior faces, the boundary flux on domain-boundary faces
+    const int fk = tt.fkind ? tt.fkind[e * dm.nf + f] : kFaceInterior;
+    if (fk != kFaceInterior) {
+      double bval[M];
+      boundary_point<D, STAB>(fk, uh, u, n, wf, ph, fsur[(M - 1) * Nfp + fp] / wf, jac, PJ, e, fp, Nfp, bval);
+#pragma unroll
+      for (int i = 0; i < M; ++i) ftr[i * Nfp + fp] = bval[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < M; ++i) ftr[i * Nfp + fp] = fsur[i * Nfp + fp];
+    }
   }
   __syncthreads();
   // ---- projections onto the test functions
@@ -508,7 +633,7 @@ __global__ void k_points(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ,
         if (code < 0) continue;
         const int f = code / tt.NFS, j = code % tt.NFS;
         const double* mu = tt.muf + ((size_t)e * dm.nf + f) * Nfq * tt.NFS + j;
-        for (int gf = 0; gf < Nfq; ++gf) t += mu[(size_t)gf * tt.NFS] * fsur[i * Nfp + f * Nfq + gf];
+        for (int gf = 0; gf < Nfq; ++gf) t += mu[(size_t)gf * tt.NFS] * ftr[i * Nfp + f * Nfq + gf];
       }
     } else {
       const int a = ref.bnode[s];
@@ -574,7 +699,7 @@ cudaError_t launch_points(iedg_mesh* M, const double* u, const double* q, const 
                           double* rhat, cudaStream_t st) {
   const Dims& dm = M->dm;
   size_t smem = sizeof(double) * ((size_t)dm.Np * dm.m * (2 + 2 * dm.d) + dm.Nb * dm.m +
-                                  (size_t)dm.m * dm.d * dm.Nq + dm.m * dm.Nq + dm.m * dm.Nfp);
+                                  (size_t)dm.m * dm.d * dm.Nq + dm.m * dm.Nq + 2 * dm.m * dm.Nfp);
   const int threads = 128;
   // right-hand sides: column n of the FP64 bordered matrix, or the FP64 rhs array
   // (ragged FP64 matrices: the kernel adds the element's offset and n_e to S itself)

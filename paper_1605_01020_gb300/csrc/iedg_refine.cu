@@ -17,7 +17,7 @@ constexpr int RF_THREADS = 512;
 constexpr int RF_NB = 32;            // panel width of the FP32 factorisation (k_lu<float, 32>)
 
 struct Work {
-  double *x, *z, *v, *b, *dqn, *xv, *xq, *tv, *xf, *zf, *xqf, *tf, *ou, *ot, *red;
+  double *x, *z, *v, *b, *dqn, *xv, *xq, *tv, *xf, *zf, *xqf, *tf, *tbf, *ou, *ot, *red;
   double *sL, *sdL;              // 1D tables (3D sum factorisation)
 };
 
@@ -37,6 +37,7 @@ __device__ Work carve(const Dims& dm, double* sm) {
   w.zf = p;  p += m * dm.Nfp;
   w.xqf = p; p += m * d * dm.Nfp;
   w.tf = p;  p += m * dm.Nfp;
+  w.tbf = p; p += m * dm.Nfp;
   w.ou = p;  p += dm.nu;
   w.ot = p;  p += dm.nt;
   w.red = p; p += 32;
@@ -48,7 +49,7 @@ __device__ Work carve(const Dims& dm, double* sm) {
 size_t work_doubles(const Dims& dm) {
   const int m = dm.m, d = dm.d;
   return (size_t)3 * dm.nu + dm.nt + (size_t)m * d * dm.Np + (size_t)m * dm.Nq * (1 + 2 * d) +
-         (size_t)m * dm.Nfp * (3 + d) + dm.nu + dm.nt + 32 + 2 * (size_t)dm.nq1 * dm.np1;
+         (size_t)m * dm.Nfp * (4 + d) + dm.nu + dm.nt + 32 + 2 * (size_t)dm.nq1 * dm.np1;
 }
 
 __device__ double block_max(double v, double* red) {
@@ -204,6 +205,18 @@ __device__ void element_apply(const Dims& dm, const Phys& ph, const RefTables& r
       for (int l = 0; l < d; ++l) s = fma(o[(size_t)(1 + l) * Nfp + fp], w.xqf[(k * d + l) * Nfp + fp], s);
     }
     w.tf[i * Nfp + fp] = s;
+    // domain-boundary face: the trace rows see the linearised boundary flux instead
+    if (tt.fkind && tt.fkind[e * dm.nf + fp / Nfq] != kFaceInterior) {
+      const int nc = 2 + d;
+      double tb = 0.0;
+      for (int k = 0; k < m; ++k) {
+        const double* jb = PJ.Jb + ((size_t)(e * m + i) * m + k) * nc * Nfp + fp;
+        if (use_z) tb = fma(jb[0], w.zf[k * Nfp + fp], tb);
+        if (use_x) tb = fma(jb[(size_t)Nfp], w.xf[k * Nfp + fp], tb);
+        for (int l = 0; l < d; ++l) tb = fma(jb[(size_t)(2 + l) * Nfp], w.xqf[(k * d + l) * Nfp + fp], tb);
+      }
+      w.tbf[i * Nfp + fp] = tb;
+    }
   }
   __syncthreads();
   // projections onto the test functions
@@ -282,7 +295,8 @@ __device__ void element_apply(const Dims& dm, const Phys& ph, const RefTables& r
           if (code < 0) continue;
           const int f = code / tt.NFS, j = code % tt.NFS;
           const double* mu = tt.muf + ((size_t)e * dm.nf + f) * Nfq * tt.NFS + j;
-          for (int gf = 0; gf < Nfq; ++gf) s = fma(mu[(size_t)gf * tt.NFS], w.tf[i * Nfp + f * Nfq + gf], s);
+          const double* src = (tt.fkind && tt.fkind[e * dm.nf + f] != kFaceInterior) ? w.tbf : w.tf;
+          for (int gf = 0; gf < Nfq; ++gf) s = fma(mu[(size_t)gf * tt.NFS], src[i * Nfp + f * Nfq + gf], s);
         }
       }
     } else {

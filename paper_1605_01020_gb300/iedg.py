@@ -20,7 +20,8 @@ EXPORTS = ("iedg_create_mesh", "iedg_destroy_mesh", "iedg_last_error", "iedg_mes
            "iedg_back_substitute", "iedg_element_status", "iedg_profile_enable",
            "iedg_profile_read", "iedg_profile_reset", "iedg_eval_residual_static", "iedg_get_schedule",
            "iedg_set_schedule", "iedg_trace_solve", "iedg_create_mesh_mixed", "iedg_element_sizes",
-           "iedg_set_trace_precond", "iedg_bilu0_factor", "iedg_bilu0_apply", "iedg_trace_colors")
+           "iedg_set_trace_precond", "iedg_bilu0_factor", "iedg_bilu0_apply", "iedg_trace_colors",
+           "iedg_create_mesh_bc")
 PREC_BLOCK_JACOBI, PREC_BILU0 = 0, 1
 
 
@@ -61,6 +62,8 @@ def load():
     lib.iedg_create_mesh.restype = ctypes.c_int
     lib.iedg_create_mesh_mixed.argtypes = [ctypes.POINTER(MeshDesc), vp, vp, vp, ctypes.POINTER(vp)]
     lib.iedg_create_mesh_mixed.restype = ctypes.c_int
+    lib.iedg_create_mesh_bc.argtypes = [ctypes.POINTER(MeshDesc), vp, vp, vp, vp, vp, ctypes.POINTER(vp)]
+    lib.iedg_create_mesh_bc.restype = ctypes.c_int
     lib.iedg_element_sizes.argtypes = [vp, vp, vp]
     lib.iedg_element_sizes.restype = ctypes.c_int
     lib.iedg_destroy_mesh.argtypes = [vp]
@@ -145,6 +148,7 @@ class Mesh:
         self.m = self.d + 2
         self.T = int(n_trace)
         self.order = int(order)
+        self.alpha = float(alpha)
         desc = MeshDesc(self.d, self.order, quad_extra, precision, self.E, self.T,
                         X.ctypes.data, ET.ctypes.data, gamma, Pr, Re, Minf, alpha, int(stab), 0)
         h = ctypes.c_void_p()
@@ -348,7 +352,8 @@ class MixedOrderMesh(Mesh):
     with its own number of nodes: u [sum Np_e, m], q [sum Np_e, m, d]."""
 
     def __init__(self, node_xyz, elem_trace, n_trace, orders, face_degree, gamma=1.4, Pr=0.72, Re=1e3,
-                 Minf=0.2, alpha=0.0, quad_extra=2, precision=0, stream=None, stab=0):
+                 Minf=0.2, alpha=0.0, quad_extra=2, precision=0, stream=None, stab=0, face_kind=None,
+                 u_far=None):
         lib = load()
         X = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.float64) for x in node_xyz]))
         ET = np.ascontiguousarray(np.concatenate([np.asarray(t, dtype=np.int64) for t in elem_trace]))
@@ -359,6 +364,7 @@ class MixedOrderMesh(Mesh):
         self.m = self.d + 2
         self.T = int(n_trace)
         self.order = 0
+        self.alpha = float(alpha)
         if FD.shape != (self.E, 2 * self.d):
             raise ValueError("face_degree must be [n_elem, 2 d]")
         # the library reads the ragged arrays with the sizes the orders and face degrees
@@ -370,8 +376,16 @@ class MixedOrderMesh(Mesh):
         desc = MeshDesc(self.d, 0, quad_extra, precision, self.E, self.T,
                         X.ctypes.data, ET.ctypes.data, gamma, Pr, Re, Minf, alpha, int(stab), 0)
         h = ctypes.c_void_p()
-        rc = lib.iedg_create_mesh_mixed(ctypes.byref(desc), ORD.ctypes.data, FD.ctypes.data,
-                                        ctypes.c_void_p(_stream(stream)), ctypes.byref(h))
+        FK = None if face_kind is None else np.ascontiguousarray(face_kind, dtype=np.int32)
+        if FK is not None and FK.shape != FD.shape:
+            raise ValueError("face_kind must be [n_elem, 2 d]")
+        UF = None if u_far is None else np.ascontiguousarray(u_far, dtype=np.float64)
+        if UF is not None and UF.shape != (self.m,):
+            raise ValueError("u_far must have m entries")
+        rc = lib.iedg_create_mesh_bc(ctypes.byref(desc), ORD.ctypes.data, FD.ctypes.data,
+                                     None if FK is None else FK.ctypes.data,
+                                     None if UF is None else UF.ctypes.data,
+                                     ctypes.c_void_p(_stream(stream)), ctypes.byref(h))
         if rc != OK:
             raise IedgError(rc, lib.iedg_last_error(None).decode())
         self._h = h

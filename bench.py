@@ -242,10 +242,11 @@ def run_ours(args, wl, rank, world, local_rank):
     dq = torch.empty_like(q)
     flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
 
-    def step(u_, uh_, duh_):
+    def step(u_, uh_, duh_, outs=None):
+        K_, R_, du_, dq_ = outs if outs is not None else (K, R, du, dq)
         mesh.eval_residual(u_, uh_, q=None, q_out=q, r_q=rq, r_u=ru, r_fl=rfl)
-        mesh.assemble_condensed(u_, q, uh_, K=K, R=R)
-        mesh.back_substitute(duh_, du, dq)
+        mesh.assemble_condensed(u_, q, uh_, K=K_, R=R_)
+        mesh.back_substitute(duh_, du_, dq_)
 
     def barrier():
         if world > 1:
@@ -279,27 +280,46 @@ def run_ours(args, wl, rank, world, local_rank):
     hdu = torch.empty(du.shape, dtype=f64).pin_memory()
     hdq = torch.empty(dq.shape, dtype=f64).pin_memory()
     du_in, uh_in, duh_in = torch.empty_like(u), torch.empty_like(uh), torch.empty_like(duh)
+    # Results go to the host on a copy stream while the next step computes: two sets of
+    # device outputs alternate when HBM has room for the second (every copy of every
+    # step still lies inside the timed region: the end event waits for the copy stream)
+    outs_bytes = sum(t.numel() * t.element_size() for t in (K, R, du, dq))
+    sets = [(K, R, du, dq)]
+    if torch.cuda.mem_get_info(dev)[0] > 2 * outs_bytes + (4 << 30):
+        sets.append(tuple(torch.empty_like(t) for t in (K, R, du, dq)))
+    cstream = torch.cuda.Stream(dev)
+    copied = [None] * len(sets)
 
-    def e2e_step():
+    def e2e_step(n):
+        k = n % len(sets)
+        if copied[k] is not None:
+            stream.wait_event(copied[k])            # the set's previous copy to the host is done
         du_in.copy_(hu, non_blocking=True)
         uh_in.copy_(huh, non_blocking=True)
         duh_in.copy_(hduh, non_blocking=True)
-        step(du_in, uh_in, duh_in)
-        hK.copy_(K, non_blocking=True)
-        hR.copy_(R, non_blocking=True)
-        hdu.copy_(du, non_blocking=True)
-        hdq.copy_(dq, non_blocking=True)
+        step(du_in, uh_in, duh_in, sets[k])
+        ready = torch.cuda.Event()
+        ready.record(stream)
+        with torch.cuda.stream(cstream):
+            cstream.wait_event(ready)
+            for h_, d_ in zip((hK, hR, hdu, hdq), sets[k]):
+                h_.copy_(d_, non_blocking=True)
+            copied[k] = torch.cuda.Event()
+            copied[k].record(cstream)
 
-    e2e_step()
+    e2e_step(0)
+    stream.wait_stream(cstream)
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for n in range(args.steps):
         flush.zero_()
-        e2e_step()
+        e2e_step(n)
+    stream.wait_stream(cstream)
     e1.record(stream)
     barrier()
     ms_e2e = e0.elapsed_time(e1)
+    del sets
     h2d = sum(t.numel() * t.element_size() for t in (hu, huh, hduh))
     d2h = sum(t.numel() * t.element_size() for t in (hK, hR, hdu, hdq))
 
@@ -371,7 +391,8 @@ def run_ours(args, wl, rank, world, local_rank):
                        "per_rank_elements": E, "schedule": schedule, "autotune_ms": timings64},
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": value_e2e, "unit": "elements/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
+                    "d2h_bytes_per_step": d2h,
+                    "overlap": "results copied to pinned host memory on a second stream during the next step"},
             "clocks": clocks, "gpu_launches": sum(v[0] for v in prof.values()),
             "kernels": {k: {"launches": v[0], "ms": v[1], "share": v[1] / tot_ms if tot_ms else None}
                         for k, v in prof.items()},

@@ -243,9 +243,15 @@ int iedg_trace_solve(iedg_mesh* mesh, const double* K, const double* R, double* 
  *                  does not fit in shared memory).
  *   asm_chunk:     assembly column chunk, 8, 16 or 32 (0 = default: 8 for FP64, 16
  *                  for FP32; too large a chunk for shared memory falls back).
- *   lu_tensor:     mixed path: 1 = trailing updates of the FP32 LU on the tensor
- *                  cores (tcgen05, TF32 operands split in high and low parts, three
- *                  products, FP32 accumulation in tensor memory); 0 = FFMA.
+ *   lu_tensor:     1 = the Schur complement K = D - W Z of the partial LU on the tensor
+ *                  cores (tcgen05, accumulation in tensor memory).  FP64 path: the FP64
+ *                  operands are split exactly into integer slices of 7 bits, the slice
+ *                  products of equal weight accumulate exactly in FP32 over K chunks of
+ *                  64 and are summed in FP64 (results agree with the DFMA form to
+ *                  FP64 rounding); the panel factorisation stays on DFMA; persistent
+ *                  grid, panel 16.  Mixed path: TF32 operands split in high and low
+ *                  parts, three products ("3xTF32").  0 = DFMA / FFMA updates.  Default
+ *                  0 for FP64 handles, 1 for mixed ones.
  *   asm_chunk_by_order[p-1]: meshes with mixed orders: the assembly chunk of the
  *                  elements of order p (8, 16, 32; 0 = asm_chunk), so that each
  *                  order's assembly launch gets its own tuned tile.

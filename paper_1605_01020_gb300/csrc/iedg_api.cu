@@ -522,6 +522,8 @@ static int check_desc(const iedg_mesh_desc* D, bool mixed) {
 static void destroy_impl(iedg_mesh* M) {
   for (iedg_mesh* C : M->groups) destroy_impl(C);
   M->groups.clear();
+  if (M->oz_scratch) cudaFree(M->oz_scratch);
+  M->oz_scratch = nullptr;
   free_all(M);
   delete M;
 }
@@ -536,6 +538,7 @@ extern "C" int iedg_create_mesh(const iedg_mesh_desc* D, void* stream, iedg_mesh
   M->dm = make_dims(D->dim, D->order, D->quad_extra);
   M->ph = Phys{D->gamma, D->Pr, D->Re, D->alpha, D->stab, {0, 0, 0, 0, 0}};
   M->precision = D->precision;
+  M->sched.lu_tensor = D->precision == IEDG_PRECISION_MIXED ? 1 : 0;   // FP64: DFMA unless chosen
   M->E = D->n_elem;
   M->T = D->n_trace;
   rc = create_impl(D, (cudaStream_t)stream, M);
@@ -863,6 +866,7 @@ extern "C" int iedg_create_mesh_bc(const iedg_mesh_desc* D, const int32_t* elem_
   if (u_far)
     for (int i = 0; i < m; ++i) M->ph.ub[i] = u_far[i];
   M->precision = D->precision;
+  M->sched.lu_tensor = D->precision == IEDG_PRECISION_MIXED ? 1 : 0;   // FP64: DFMA unless chosen
   M->E = D->n_elem;
   M->T = D->n_trace;
   rc = create_mixed_impl(D, elem_order, face_degree, face_kind, (cudaStream_t)stream, M);

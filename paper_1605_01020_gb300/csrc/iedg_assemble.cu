@@ -266,6 +266,14 @@ k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, AsmTab<T> tb, T* __restri
 constexpr int LU_THREADS = 256;
 constexpr int UCW = 64;     // trailing-update column chunk
 
+// Tensor-core state of a CTA (deferred Schur complement forms of the LU).
+struct TcState {
+  uint32_t tmem;        // TMEM base
+  uint64_t* mbar;       // MMA completion barriers (one per operand stage)
+  uint32_t phase[2];    // parity of each barrier's next completion
+  int failed;           // a completion wait ran out
+};
+
 // Sizes and location of one element's bordered matrix.
 struct LuElem {
   int n, nu, ld;
@@ -277,9 +285,60 @@ __device__ __forceinline__ LuElem lu_elem(const Dims& dm, const LuDesc& lud, int
   return LuElem{dm.n, dm.nu, dm.ld, e * (int64_t)dm.n * dm.ld, e * (int64_t)dm.nu};
 }
 
+// A[r][c] -= sum_j L[r][j] U[j][c] over rows [r_lo, r_hi), cols [c_lo, c_hi): L from the
+// row-major panel P (row r at P[(r - kb) NB + j]), U = rows kb..kb+nb of A, staged by
+// UCW-column chunks in Uc; 16 x 16 threads with 4 x 4 register tiles.
+template <class T, int NB>
+__device__ __forceinline__ void lu64_update_rect(T* __restrict__ A, int ld, const T* __restrict__ P,
+                                                 T* __restrict__ Uc, int kb, int nb, int r_lo, int r_hi, int c_lo,
+                                                 int c_hi) {
+  const int tid = threadIdx.x;
+  for (int cc = c_lo; cc < c_hi; cc += UCW) {
+    const int cw = min(UCW, c_hi - cc);
+    for (int idx = tid; idx < NB * UCW; idx += LU_THREADS) {
+      int j = idx / UCW, c = idx % UCW;
+      Uc[idx] = (j < nb && c < cw) ? A[(int64_t)(kb + j) * ld + cc + c] : (T)0;
+    }
+    __syncthreads();
+    const int tc = tid % (UCW / 4), tr = tid / (UCW / 4);   // 16 x 16 threads, 4x4 tiles
+    for (int rb = r_lo; rb < r_hi; rb += 64) {
+      T a4[4][4];
+      int rr[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        rr[a] = rb + tr * 4 + a;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          int c = tc * 4 + b;
+          a4[a][b] = (rr[a] < r_hi && c < cw) ? A[(int64_t)rr[a] * ld + cc + c] : (T)0;
+        }
+      }
+      for (int j = 0; j < nb; ++j) {
+        T uv[4], lv[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) uv[b] = Uc[j * UCW + tc * 4 + b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) lv[a] = rr[a] < r_hi ? P[(rr[a] - kb) * NB + j] : (T)0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) a4[a][b] = fma(-lv[a], uv[b], a4[a][b]);
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          int c = tc * 4 + b;
+          if (rr[a] < r_hi && c < cw) A[(int64_t)rr[a] * ld + cc + c] = a4[a][b];
+        }
+    }
+    __syncthreads();
+  }
+}
+
 template <class T, int NB>
 __device__ __forceinline__ void lu_element(const LuElem& el, T* __restrict__ S, int8_t* __restrict__ status,
-                                           int* __restrict__ pivots, const int64_t e) {
+                                           int* __restrict__ pivots, const int64_t e, bool defer_schur = false) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
   __shared__ int piv[NB];
@@ -341,7 +400,7 @@ __device__ __forceinline__ void lu_element(const LuElem& el, T* __restrict__ S, 
       __syncthreads();
     }
     // U11 / L11 (and, when the factors are kept, L21) back to the element matrix
-    const int wrows = pivots ? rows : nb;
+    const int wrows = (pivots || defer_schur) ? rows : nb;   // L21 is the W of the deferred form
     for (int idx = tid; idx < wrows * nb; idx += LU_THREADS) {
       int r = idx / nb, j = idx % nb;
       A[(int64_t)(kb + r) * ld + kb + j] = P[r * NB + j];
@@ -366,52 +425,24 @@ __device__ __forceinline__ void lu_element(const LuElem& el, T* __restrict__ S, 
       }
     }
     __syncthreads();
-    // A22 -= L21 U12, rows [kb+nb, n), cols [kb+nb, n]
     const int r0 = kb + nb;
-    for (int cc = r0; cc < ncol; cc += UCW) {
-      const int cw = min(UCW, ncol - cc);
-      for (int idx = tid; idx < NB * UCW; idx += LU_THREADS) {
-        int j = idx / UCW, c = idx % UCW;
-        Uc[idx] = (j < nb && c < cw) ? A[(int64_t)(kb + j) * ld + cc + c] : (T)0;
-      }
-      __syncthreads();
-      const int tc = tid % (UCW / 4), tr = tid / (UCW / 4);   // 16 x 16 threads, 4x4 tiles
-      for (int rb = r0; rb < n; rb += 64) {
-        T a4[4][4];
-        int rr[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          rr[a] = rb + tr * 4 + a;
-#pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            int c = tc * 4 + b;
-            a4[a][b] = (rr[a] < n && c < cw) ? A[(int64_t)rr[a] * ld + cc + c] : (T)0;
-          }
-        }
-        for (int j = 0; j < nb; ++j) {
-          T uv[4], lv[4];
-#pragma unroll
-          for (int b = 0; b < 4; ++b) uv[b] = Uc[j * UCW + tc * 4 + b];
-#pragma unroll
-          for (int a = 0; a < 4; ++a) lv[a] = rr[a] < n ? P[(rr[a] - kb) * NB + j] : (T)0;
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) a4[a][b] = fma(-lv[a], uv[b], a4[a][b]);
-        }
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            int c = tc * 4 + b;
-            if (rr[a] < n && c < cw) A[(int64_t)rr[a] * ld + cc + c] = a4[a][b];
-          }
-      }
-      __syncthreads();
+    if (defer_schur) {
+      // the trace block of the trace rows gets all panels at once afterwards
+      lu64_update_rect<T, NB>(A, ld, P, Uc, kb, nb, r0, n, r0, nu);
+      lu64_update_rect<T, NB>(A, ld, P, Uc, kb, nb, r0, nu, nu, ncol);
+    } else {
+      // A22 -= L21 U12, rows [kb+nb, n), cols [kb+nb, n]
+      lu64_update_rect<T, NB>(A, ld, P, Uc, kb, nb, r0, n, r0, ncol);
     }
   }
-  // status: exact zero pivot, or non-finite Schur complement
+  // status: exact zero pivot, or non-finite Schur complement (deferred form: the caller
+  // checks the Schur complement after forming it)
   __syncthreads();
+  if (defer_schur) {
+    if (tid == 0) status[e] = sing ? IEDG_ELEM_SINGULAR : IEDG_ELEM_OK;
+    __syncthreads();
+    return;
+  }
   int bad = 0;
   for (int idx = tid; idx < (n - nu) * (ncol - nu); idx += LU_THREADS) {
     int r = nu + idx / (ncol - nu), c = nu + idx % (ncol - nu);
@@ -419,6 +450,184 @@ __device__ __forceinline__ void lu_element(const LuElem& el, T* __restrict__ S, 
   }
   bad = __syncthreads_or(bad);
   if (tid == 0) status[e] = sing ? IEDG_ELEM_SINGULAR : (bad ? IEDG_ELEM_NONFINITE : IEDG_ELEM_OK);
+}
+
+// ----------------------------------------------------------- FP64 Schur complement on tcgen05
+// [K | R] = [D | G] - W [Z | z] of the FP64 form with the products on the tensor cores,
+// by an exact splitting of the FP64 operands (the Ozaki scheme): each row i of W is
+// scaled by a power of two 2^e_i >= its largest entry, each column j of Z by 2^f_j,
+// and the scaled entries are written as sums of OZ_S integer slices of OZ_BETA bits,
+//   W_ik = 2^e_i sum_s v_s 2^(-s beta),  Z_kj = 2^f_j sum_t w_t 2^(-t beta)  (+ a rest
+// below 2^-(S beta)), v, w integers with |v|, |w| <= 2^beta, exact in TF32.  The slice
+// products of one level l = s + t (2 <= l <= S + 1) share the scale 2^(e_i + f_j - l beta)
+// and accumulate in one FP32 TMEM accumulator: with beta = 7 and K chunks of 64 every
+// partial sum is an integer below 2^23, so the tensor cores add exactly; each chunk's
+// levels are then scaled and summed in FP64.  Levels above S + 1 (below 2^-63 of the
+// product scale) are dropped.  The splitting and the level sums are FP64 work
+// (about a quarter of the FP64 multiply-adds the product itself would take).
+constexpr int OZ_S = 8, OZ_BETA = 7, OZ_L = 8;           // slices, bits per slice, levels 2..9
+constexpr int OZ_KC = 64, OZ_KS = 16;                    // exact-accumulation chunk, staging step
+constexpr int OZ_TM = 128, OZ_TN = 32;
+constexpr int OZ_TMEM_COLS = OZ_L * OZ_TN;              // 256
+constexpr int OZ_A_BYTES = OZ_TM * OZ_KS * 4, OZ_B_BYTES = OZ_TN * OZ_KS * 4;
+constexpr int OZ_STAGE_BYTES = OZ_S * (OZ_A_BYTES + OZ_B_BYTES);   // 80 KB
+
+// Scratch of one CTA for the slices and scales of its current element.
+struct OzScratch {
+  float* ws;      // [S][nt][nu]      slices of W, K contiguous
+  float* zs;      // [S][nt + 1][nu]  slices of Z^T, K contiguous
+  double* rs;     // [nt]             2^e_i
+  double* cs;     // [nt + 1]         2^f_j
+};
+
+__device__ __forceinline__ double pow2_at_least(double m) {
+  if (!(m > 0.0)) return 1.0;
+  int ex;
+  frexp(m, &ex);                  // m = f 2^ex, f in [0.5, 1): m < 2^ex
+  return ldexp(1.0, ex);
+}
+
+__device__ void oz_split(const double* __restrict__ A, int ld, int n, int nu, const OzScratch& sc) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = LU_THREADS / 32;
+  const int nt = n - nu, nt1 = nt + 1;
+  // row scales of W (one warp per row) and column scales of Z (one thread per column)
+  for (int i = warp; i < nt; i += nw) {
+    const double* row = A + (int64_t)(nu + i) * ld;
+    double mx = 0.0;
+    for (int k = lane; k < nu; k += 32) mx = fmax(mx, fabs(row[k]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) sc.rs[i] = pow2_at_least(mx);
+  }
+  for (int j = tid; j < nt1; j += LU_THREADS) {
+    double mx = 0.0;
+    for (int k = 0; k < nu; ++k) mx = fmax(mx, fabs(A[(int64_t)k * ld + nu + j]));
+    sc.cs[j] = pow2_at_least(mx);
+  }
+  __syncthreads();
+  const double up = ldexp(1.0, OZ_BETA);
+  for (int idx = tid; idx < nt * nu; idx += LU_THREADS) {
+    const int i = idx / nu, k = idx % nu;
+    double x = A[(int64_t)(nu + i) * ld + k] / sc.rs[i];          // exact: power of two
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s) {
+      const double t = x * up;
+      const double v = rint(t);
+      x = t - v;
+      sc.ws[((size_t)s * nt + i) * nu + k] = (float)v;
+    }
+  }
+  for (int idx = tid; idx < nt1 * nu; idx += LU_THREADS) {
+    const int k = idx / nt1, j = idx % nt1;
+    double x = A[(int64_t)k * ld + nu + j] / sc.cs[j];
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s) {
+      const double t = x * up;
+      const double v = rint(t);
+      x = t - v;
+      sc.zs[((size_t)s * nt1 + j) * nu + k] = (float)v;
+    }
+  }
+  __syncthreads();
+}
+
+// Stage K columns k0 .. k0+15 of every slice of the tile's W rows and Z columns.
+__device__ __forceinline__ void oz_stage(const OzScratch& sc, int nt, int nu, int rt, int ct, int k0, char* stage) {
+  const int tid = threadIdx.x, nt1 = nt + 1;
+  char* sa = stage;
+  char* sb = stage + OZ_S * OZ_A_BYTES;
+  for (int idx = tid; idx < OZ_S * OZ_TM * OZ_KS; idx += LU_THREADS) {
+    const int s = idx / (OZ_TM * OZ_KS), r = (idx / OZ_KS) % OZ_TM, k = idx % OZ_KS;
+    const int i = rt + r, kk = k0 + k;
+    const float v = (i < nt && kk < nu) ? sc.ws[((size_t)s * nt + i) * nu + kk] : 0.f;
+    const uint32_t off = (uint32_t)((r >> 3) * (OZ_KS / 4) * 128 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4);
+    *reinterpret_cast<float*>(sa + s * OZ_A_BYTES + off) = v;
+  }
+  for (int idx = tid; idx < OZ_S * OZ_TN * OZ_KS; idx += LU_THREADS) {
+    const int s = idx / (OZ_TN * OZ_KS), r = (idx / OZ_KS) % OZ_TN, k = idx % OZ_KS;
+    const int j = ct + r, kk = k0 + k;
+    const float v = (j < nt1 && kk < nu) ? sc.zs[((size_t)s * nt1 + j) * nu + kk] : 0.f;
+    const uint32_t off = (uint32_t)((r >> 3) * (OZ_KS / 4) * 128 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4);
+    *reinterpret_cast<float*>(sb + s * OZ_B_BYTES + off) = v;
+  }
+}
+
+// One thread: every slice pair of levels 2..S+1 for the staged K step; level l goes
+// to TMEM columns (l - 2) OZ_TN ..; `first` starts the chunk's accumulators.
+__device__ __forceinline__ void oz_issue(uint32_t tmem, const char* stage, bool first) {
+  const uint32_t a0 = tc::smem_u32(stage), b0 = a0 + OZ_S * OZ_A_BYTES;
+  constexpr uint32_t IDESC = tc::idesc_tf32(OZ_TM, OZ_TN);
+  constexpr uint32_t SBO = (OZ_KS / 4) * 128;
+  for (int s = 1; s <= OZ_S; ++s)
+    for (int t = 1; t <= OZ_S; ++t) {
+      const int l = s + t;
+      if (l > OZ_L + 1) continue;
+      const uint32_t d = tmem + (uint32_t)((l - 2) * OZ_TN);
+      // the first product of a level in the chunk is the one with s = 1
+#pragma unroll
+      for (int kst = 0; kst < OZ_KS / 8; ++kst) {
+        const uint32_t ko = kst * 256;
+        const bool acc = !(first && s == 1 && kst == 0);
+        tc::mma_tf32(d, tc::desc_kmajor(a0 + (s - 1) * OZ_A_BYTES + ko, 128, SBO),
+                     tc::desc_kmajor(b0 + (t - 1) * OZ_B_BYTES + ko, 128, SBO), IDESC, acc ? 1u : 0u);
+      }
+    }
+}
+
+__device__ void schur_ozaki(double* __restrict__ A, int ld, int n, int nu, const OzScratch& sc, char* smem,
+                            TcState* tcs) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nt = n - nu, ncol = n + 1;
+  const int q = warp & 3, h = warp >> 2;
+  oz_split(A, ld, n, nu, sc);
+  for (int rt = 0; rt < nt && !tcs->failed; rt += OZ_TM) {
+    for (int ct = 0; ct < ncol - nu && !tcs->failed; ct += OZ_TN) {
+      for (int kc = 0; kc < nu && !tcs->failed; kc += OZ_KC) {
+        for (int k0 = kc; k0 < min(kc + OZ_KC, nu); k0 += OZ_KS) {
+          oz_stage(sc, nt, nu, rt, ct, k0, smem);
+          tc::fence_proxy_async();
+          __syncthreads();
+          tc::fence_after_sync();
+          if (tid == 0) {
+            oz_issue(tcs->tmem, smem, k0 == kc);
+            tc::mma_commit(tcs->mbar);
+          }
+          const bool ok = __syncthreads_and(tc::mbar_wait(tcs->mbar, tcs->phase[0], 1 << 26));
+          if (!ok) { tcs->failed = 1; break; }
+          tcs->phase[0] ^= 1u;
+          tc::fence_after_sync();
+        }
+        if (tcs->failed) break;
+        // epilogue: warp (q, h) owns rows 32 q .. 32 q + 31 and columns 16 h .. 16 h + 15
+        const int i = rt + 32 * q + lane;
+        const double rsc = i < nt ? sc.rs[i] : 0.0;
+#pragma unroll 1
+        for (int c8 = 0; c8 < 2; ++c8) {
+          const int c0 = 16 * h + 8 * c8;
+          double sum[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) sum[j] = 0.0;
+#pragma unroll 1
+          for (int l = 0; l < OZ_L; ++l) {
+            float v8[8];
+            tc::tmem_ld8(tcs->tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(l * OZ_TN + c0), v8);
+            const double w = ldexp(1.0, -(l + 2) * OZ_BETA);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) sum[j] = fma((double)v8[j], w, sum[j]);
+          }
+          if (i >= nt) continue;
+          double* dst = A + (int64_t)(nu + i) * ld + nu + ct + c0;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int jj = ct + c0 + j;
+            if (jj < ncol - nu) dst[j] -= (rsc * sc.cs[jj]) * sum[j];
+          }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+      }
+    }
+  }
 }
 
 // FP32 partial LU for the mixed path.  Same algorithm and pivot rule as k_lu, with
@@ -431,13 +640,6 @@ constexpr int L32_NB = 32;
 constexpr int L32_UCW = 128;      // trailing-update column chunk
 constexpr int L32_TM = 4, L32_TN = 8;
 
-// Tensor-core state of a CTA for the TC form (deferred Schur complement).
-struct TcState {
-  uint32_t tmem;        // TMEM base (64 columns used)
-  uint64_t* mbar;       // two MMA completion barriers, one per operand stage
-  uint32_t phase[2];    // parity of each barrier's next completion
-  int failed;           // a completion wait ran out
-};
 
 // A[r][c] -= sum_j L[r][j] U[j][c] over rows [r_lo, r_hi), cols [c_lo, c_hi): L from the
 // column-major panel P (row r at P[j n + r - kb]), U = rows kb..kb+nb of A.  4 x 8
@@ -840,6 +1042,71 @@ k_lu32_tc(Dims dm, LuDesc lud, float* __restrict__ S, int8_t* __restrict__ statu
   if (warp == 0) tc::tmem_dealloc(tmem_base, TC_TN);
 }
 
+// FP64 partial LU with the Schur complement on the tensor cores (schur_ozaki).  The CTA
+// holds 256 TMEM columns (two resident CTAs fit an SM's 512) and one completion barrier.
+__global__ void __launch_bounds__(LU_THREADS)
+k_lu64_oz(Dims dm, LuDesc lud, double* __restrict__ S, int8_t* __restrict__ status, int64_t* queue, int64_t E,
+          float* __restrict__ scratch, int64_t scratch_floats, int* err) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ uint32_t tmem_base;
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ TcState tcs;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) {
+    tc::tmem_alloc(&tmem_base, OZ_TMEM_COLS);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) tc::mbar_init(&mbar[0], 1);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (tid == 0) {
+    tcs.tmem = tmem_base;
+    tcs.mbar = mbar;
+    tcs.phase[0] = 0;
+    tcs.phase[1] = 0;
+    tcs.failed = 0;
+  }
+  __syncthreads();
+  TcState mine = tcs;
+  // this CTA's slices and scales
+  float* base = scratch + (size_t)blockIdx.x * scratch_floats;
+  OzScratch sc;
+  {
+    const size_t ntm = dm.nt + 1, num = dm.nu;
+    sc.ws = base;
+    sc.zs = sc.ws + (size_t)OZ_S * ntm * num;
+    double* dd = reinterpret_cast<double*>(sc.zs + (size_t)OZ_S * ntm * num);
+    sc.rs = dd;
+    sc.cs = dd + ntm;
+  }
+  int64_t e;
+  for (int64_t it = 0; next_element(queue, E, it, lud.order, &e); ++it) {
+    const LuElem el = lu_elem(dm, lud, e);
+    lu_element<double, 16>(el, S, status, nullptr, e, true);
+    schur_ozaki(S + el.off, el.ld, el.n, el.nu, sc, reinterpret_cast<char*>(smraw), &mine);
+    // non-finite Schur complement
+    double* A = S + el.off;
+    const int n = el.n, nu = el.nu, ncol = n + 1;
+    int bad = 0;
+    for (int idx = tid; idx < (n - nu) * (ncol - nu); idx += LU_THREADS) {
+      int r = nu + idx / (ncol - nu), c = nu + idx % (ncol - nu);
+      if (!isfinite(A[(int64_t)r * el.ld + c])) bad = 1;
+    }
+    bad = __syncthreads_or(bad) || mine.failed;
+    if (tid == 0 && bad && status[e] == IEDG_ELEM_OK) status[e] = IEDG_ELEM_NONFINITE;
+    if (__syncthreads_or(mine.failed)) {
+      if (tid == 0) atomicOr(err, 1);
+      tc::mbar_wait(&mbar[0], mine.phase[0], 1 << 26);   // let MMAs in flight drain
+      break;
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem_base, OZ_TMEM_COLS);
+}
+
 }  // namespace
 
 template <class T>
@@ -882,7 +1149,7 @@ cudaError_t launch_assemble(iedg_mesh* M, cudaStream_t st) {
 // kernel asks for the largest shared-memory carveout first, so the occupancy query
 // sees the split the launch will get.
 template <class K>
-static cudaError_t persistent_grid(K kern, size_t smem, int64_t E, unsigned* grid) {
+static cudaError_t persistent_grid(K kern, size_t smem, int64_t E, unsigned* grid, int max_per_sm = 64) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                          (int)cudaSharedmemCarveoutMaxShared);
@@ -890,6 +1157,7 @@ static cudaError_t persistent_grid(K kern, size_t smem, int64_t E, unsigned* gri
   if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, LU_THREADS, smem);
   if (err != cudaSuccess) return err;
+  if (per_sm > max_per_sm) per_sm = max_per_sm;
   int64_t g = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
   *grid = (unsigned)(g < E ? g : E);
   return cudaSuccess;
@@ -915,7 +1183,39 @@ static cudaError_t lu_t(iedg_mesh* M, T* S, int* piv, cudaStream_t st) {
 
 size_t lu64_smem(const Dims& dm, int nb) { return sizeof(double) * ((size_t)dm.n * nb + (size_t)nb * UCW); }
 
+// FP64 form with the Schur complement on the tensor cores (persistent grid only: each
+// CTA owns a slice buffer for the element it works on, allocated on first use).
+static cudaError_t lu64_oz(iedg_mesh* M, cudaStream_t st) {
+  const Dims& dm = M->dm;
+  size_t smem = lu64_smem(dm, 16);
+  if (smem < (size_t)OZ_STAGE_BYTES) smem = OZ_STAGE_BYTES;
+  cudaError_t err = cudaFuncSetAttribute(k_lu64_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  unsigned grid = 0;
+  // two resident CTAs at most: each holds 256 of the SM's 512 TMEM columns
+  err = persistent_grid(k_lu64_oz, smem, M->E, &grid, 2);
+  if (err != cudaSuccess) return err;
+  const int64_t ntm = dm.nt + 1;
+  const int64_t per = ((2 * (int64_t)OZ_S * ntm * dm.nu + 4 * ntm) + 3) & ~(int64_t)3;
+  if (M->oz_scratch == nullptr || M->oz_grid < grid) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    err = cudaStreamIsCapturing(st, &cs);
+    if (err != cudaSuccess) return err;
+    if (cs != cudaStreamCaptureStatusNone) return cudaErrorStreamCaptureUnsupported;
+    if (M->oz_scratch) cudaFree(M->oz_scratch);
+    err = cudaMalloc(&M->oz_scratch, (size_t)grid * per * sizeof(float));
+    if (err != cudaSuccess) { M->oz_scratch = nullptr; return err; }
+    M->oz_grid = grid;
+  }
+  err = cudaMemsetAsync(M->queue, 0, sizeof(int64_t), st);
+  if (err != cudaSuccess) return err;
+  k_lu64_oz<<<grid, LU_THREADS, smem, st>>>(dm, M->lud, M->S, M->status, M->queue, M->E, M->oz_scratch, per,
+                                             M->dev_flag);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_lu(iedg_mesh* M, cudaStream_t st) {
+  if (M->precision == 0 && M->sched.lu_tensor) return lu64_oz(M, st);
   if (M->precision == 0) {
     if (M->sched.lu_panel == 32 && lu64_smem(M->dm, 32) <= 227 * 1024) return lu_t<double, 32>(M, M->S, nullptr, st);
     return lu_t<double, 16>(M, M->S, nullptr, st);

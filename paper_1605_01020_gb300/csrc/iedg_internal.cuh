@@ -166,6 +166,8 @@ struct iedg_mesh {
   double* re64 = nullptr;       // [E][m][Nb]    refined R_e (component-major)
   int8_t* status = nullptr;     // [E]
   int64_t* queue = nullptr;     // element counter of persistent launches
+  float* oz_scratch = nullptr;  // FP64 tensor-core Schur form: per-CTA slice buffers (freed with the handle)
+  unsigned oz_grid = 0;
   // meshes with mixed orders: the parent handle holds the trace space, the ragged
   // element matrices and the per-element sizes; one child handle per order holds the
   // element tables of that order (internal element ids are grouped by order)

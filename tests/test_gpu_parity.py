@@ -115,6 +115,31 @@ def test_condensed_parity(name):
     assert rel_err(host(dq_d), dq_o) <= TOL
 
 
+@pytest.mark.parametrize("name", ["cfg1-noisy", "p3-2cube", "p2-curved", "2d-p3-steady", "p4-2cube", "p3-2cube-roe"])
+def test_condensed_parity_tensor_schur(name):
+    """FP64 form with the Schur complement on the tensor cores (exact splitting of the
+    FP64 operands, lu_tensor = 1): same tolerance against the oracle as the DFMA form."""
+    wl = _case(name)
+    st = wl.state
+    pb = problem(wl.mesh, wl.params)
+    E = wl.mesh.n_elem
+    Ke, Re = zip(*[pb.condense_qelim(e, st.u, st.q, st.uhat, st.u_ref) for e in range(E)])
+    row_ptr, col, vals, R = oiedg.assemble(wl.mesh.elem_trace, wl.mesh.n_trace, np.array(Ke), np.array(Re))
+    mesh = lib_mesh(wl)
+    mesh.set_schedule(lu_tensor=1)
+    K_d, R_d = mesh.assemble_condensed(dev(st.u), dev(st.q), dev(st.uhat), u_ref=dev(st.u_ref))
+    assert bsr_row_err(row_ptr, host(K_d), vals, range(wl.mesh.n_trace)) <= TOL
+    assert rel_err(host(R_d), R, floor=np.abs(np.array(Re)).max()) <= TOL
+    assert (mesh.element_status() == 0).all()
+    du_d, dq_d = mesh.back_substitute(dev(st.duhat))
+    du_o = np.zeros_like(st.u)
+    dq_o = np.zeros_like(st.q)
+    for e in range(E):
+        du_o[e], dq_o[e] = pb.back_substitute_qelim(e, st.u, st.q, st.uhat, st.duhat, st.u_ref)
+    assert rel_err(host(du_d), du_o) <= TOL
+    assert rel_err(host(dq_d), dq_o) <= TOL
+
+
 def test_back_substitute_before_assembly_is_an_error():
     from paper_1605_01020_gb300 import iedg
     wl = _case("cfg1")

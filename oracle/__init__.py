@@ -22,6 +22,9 @@ Embedded Discontinuous Galerkin method", arXiv:1605.01020):
   condensation K = D - C A^-1 B, R = G - C A^-1 F (Eq. LS) in the full form
   (dense A, the definition) and the q-eliminated form, assembly into a block
   compressed-row trace matrix (Sec. 2.2.2), back-substitution.
+* ``bilu``     -- block ILU(0) of the trace matrix and its solve (Sec. 2.2.2).
+* ``lowprec``  -- the condensed block with the Schur complement's operands
+  rounded to TF32 or BF16 (the reading of a low-precision Schur GEMM).
 
 Every function is FP64, plain numpy/scipy, no blocking or fusion beyond what the
 definitions state.  Parity status: every function is pinned by a test in

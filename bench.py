@@ -331,6 +331,11 @@ def run_ours(args, wl, rank, world, local_rank):
     torch.cuda.empty_cache()
     mixed = None if args.no_mixed else run_mixed(args, wl, None, dev, step_outputs=(K, R, du, dq),
                                                    inputs=(u, uh, duh), flush=flush, barrier=barrier)
+    low = {}
+    if not args.no_mixed and not args.no_low_precision:
+        for prec, key in ((2, "mixed_tf32"), (3, "mixed_bf16")):
+            low[key] = run_mixed(args, wl, None, dev, step_outputs=(K, R, du, dq), inputs=(u, uh, duh),
+                                 flush=flush, barrier=barrier, precision=prec)
     # mixed orders: one GPU only (the leg takes a few minutes; scaling runs skip it)
     mixed_orders = None
     del K, R, du, dq
@@ -340,8 +345,9 @@ def run_ours(args, wl, rank, world, local_rank):
     extras = run_extras(args, dev) if (world == 1 and not args.no_extras) else None
     from paper_1605_01020_gb300.dist import max_over_ranks
     ms, ms_e2e = max_over_ranks([ms, ms_e2e], dev)
-    if mixed is not None:
-        (mixed["ms_total"],) = max_over_ranks([mixed["ms_total"]], dev)
+    for r in [mixed] + list(low.values()):
+        if r is not None:
+            (r["ms_total"],) = max_over_ranks([r["ms_total"]], dev)
     if rank != 0:
         return
     total_elems = E * args.steps * world
@@ -371,11 +377,12 @@ def run_ours(args, wl, rank, world, local_rank):
                 "algorithmic_flops_per_launch": flops[name],
                 "actual_flops_per_launch": actual[name],
                 "frac_actual": actual[name] / t_launch / peak_alu}
-    if mixed is not None:
-        mms = mixed.pop("ms_total")
-        mixed["value"] = total_elems / (mms / 1e3)
-        mixed["ms_per_step"] = mms / args.steps
-        mixed["speedup_vs_fp64"] = ms / mms
+    for r in [mixed] + list(low.values()):
+        if r is not None:
+            mms = r.pop("ms_total")
+            r["value"] = total_elems / (mms / 1e3)
+            r["ms_per_step"] = mms / args.steps
+            r["speedup_vs_fp64"] = ms / mms
     peaks, src = measured_peaks()
     cpu = None
     if not args.no_cpu_baseline:
@@ -398,28 +405,37 @@ def run_ours(args, wl, rank, world, local_rank):
                         for k, v in prof.items()},
             "element_status_nonzero": int((status != 0).sum()),
             "mixed": mixed,
+            **low,
             "mixed_orders": mixed_orders,
             "extras": extras,
             "peaks": {"source": src, **{k: v for k, v in peaks.items() if isinstance(v, (int, float))}}}
     print(json.dumps(line), flush=True)
 
 
-def run_mixed(args, wl, mesh64, dev, step_outputs, inputs, flush, barrier):
-    """The same step in the mixed form (FP32 element matrix and partial LU, FP64
-    residuals and refinement of R, du, dq), timed the same way; errors against the
-    FP64 path's outputs on the same inputs."""
+MIXED_FORMS = {1: "FP32 element matrix + partial LU, FP64 refinement",
+               2: "FP32 element matrix + partial LU, Schur complement with TF32 operands on the tensor cores, "
+                  "FP64 refinement",
+               3: "FP32 element matrix + partial LU, Schur complement with BF16 operands on the tensor cores, "
+                  "FP64 refinement"}
+
+
+def run_mixed(args, wl, mesh64, dev, step_outputs, inputs, flush, barrier, precision=1):
+    """The same step in a mixed form (FP32 element matrix and partial LU, FP64
+    residuals and refinement of R, du, dq; precision 2 / 3: the Schur complement with
+    TF32 / BF16 operands), timed the same way; errors against the FP64 path's outputs
+    on the same inputs."""
     import torch
     from paper_1605_01020_gb300 import iedg
     K64, R64, du64, dq64 = step_outputs
     u, uh, duh = inputs
-    mesh = iedg.mesh_from_workload(wl, precision=1)
+    mesh = iedg.mesh_from_workload(wl, precision=precision)
     E, Np, m, d, T = mesh.E, mesh.Np, mesh.m, mesh.d, mesh.T
     f64 = torch.float64
     schedule, timings = None, {}
     if not args.no_autotune:
         from paper_1605_01020_gb300 import autotune
         qt = torch.as_tensor(wl.state.q, dtype=f64, device=dev)
-        schedule, timings = autotune.autotune(mesh, u, qt, uh, 1, reps=1)
+        schedule, timings = autotune.autotune(mesh, u, qt, uh, precision, reps=1)
         del qt
     q = torch.empty(E, Np, m, d, dtype=f64, device=dev)
     rq, ru, rfl = torch.empty_like(q), torch.empty(E, Np, m, dtype=f64, device=dev), torch.empty(T, m, dtype=f64, device=dev)
@@ -449,7 +465,7 @@ def run_mixed(args, wl, mesh64, dev, step_outputs, inputs, flush, barrier):
     tot = sum(v[1] for v in prof.values())
     err = lambda a, b: float((a - b).abs().max() / b.abs().max().clamp_min(1e-300))
     status = mesh.element_status()
-    out = {"ms_total": e0.elapsed_time(e1), "precision": "FP32 element matrix + partial LU, FP64 refinement",
+    out = {"ms_total": e0.elapsed_time(e1), "precision": MIXED_FORMS[precision],
            "schedule": schedule, "autotune_ms": timings,
            "err_vs_fp64": {"K": err(K, K64), "R": err(R, R64), "du": err(du, du64), "dq": err(dq, dq64)},
            "element_status_nonzero": int((status != 0).sum()),
@@ -638,6 +654,8 @@ def main():
     ap.add_argument("--cells", type=int, default=None, help="override cells per direction (smaller case)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
+    ap.add_argument("--no-low-precision", action="store_true",
+                    help="skip the mixed forms with TF32 / BF16 Schur operands")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch schedule")
     ap.add_argument("--no-mixed-orders", action="store_true", help="skip the mixed-order batch (p in {2,3,4})")
     ap.add_argument("--no-extras", action="store_true", help="skip the Roe / trace-solve / DIRK measurements")

@@ -70,6 +70,12 @@ extern "C" {
 #define IEDG_PRECISION_MIXED 1   /* element matrix and partial LU in FP32 (K to FP32
                                     accuracy); residuals, point Jacobians and the
                                     right-hand side R and updates du, dq refined to FP64 */
+#define IEDG_PRECISION_MIXED_TF32 2  /* as MIXED, with the Schur complement K = D~ - W Z of
+                                    the partial LU (W, Z the eliminated trace rows and the
+                                    u-rows' trace columns) on the tensor cores with the
+                                    operands rounded to TF32 and FP32 accumulation: K to
+                                    TF32 accuracy; R, du, dq refined to FP64 as in MIXED   */
+#define IEDG_PRECISION_MIXED_BF16 3  /* same with BF16 operands: K to BF16 accuracy        */
 
 typedef struct iedg_mesh iedg_mesh;   /* opaque */
 
@@ -77,7 +83,7 @@ typedef struct {
   int32_t dim;              /* 2 or 3                                                */
   int32_t order;            /* polynomial degree p = k of approximation and geometry */
   int32_t quad_extra;       /* n_q1 = p + quad_extra Gauss points per direction (2)  */
-  int32_t precision;        /* IEDG_PRECISION_FP64 or IEDG_PRECISION_MIXED           */
+  int32_t precision;        /* IEDG_PRECISION_FP64, _MIXED, _MIXED_TF32, _MIXED_BF16   */
   int64_t n_elem;
   int64_t n_trace;
   const double*  node_xyz;   /* HOST [n_elem][Np][dim]: isoparametric nodes (Sec. 3.1) */
@@ -251,7 +257,10 @@ int iedg_trace_solve(iedg_mesh* mesh, const double* K, const double* R, double* 
  *                  FP64 rounding); the panel factorisation stays on DFMA; persistent
  *                  grid, panel 16.  Mixed path: TF32 operands split in high and low
  *                  parts, three products ("3xTF32").  0 = DFMA / FFMA updates.  Default
- *                  0 for FP64 handles, 1 for mixed ones.
+ *                  0 for FP64 handles, 1 for mixed ones.  Handles created with
+ *                  IEDG_PRECISION_MIXED_TF32 or _MIXED_BF16 always take the tensor-core
+ *                  form in their own operand precision (the schedule never changes
+ *                  what is computed, only how).
  *   asm_chunk_by_order[p-1]: meshes with mixed orders: the assembly chunk of the
  *                  elements of order p (8, 16, 32; 0 = asm_chunk), so that each
  *                  order's assembly launch gets its own tuned tile.

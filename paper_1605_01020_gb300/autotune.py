@@ -22,7 +22,8 @@ def mesh_key(mesh, precision, gpu_name):
 def candidates(precision, order):
     """Candidate schedules: persistent LU on/off x FP64 panel 16/32 x assembly chunk,
     and the tensor-core forms (the FP64 Schur complement by exact operand splitting;
-    the FP32 LU's Schur complement in 3xTF32 on the mixed path).
+    the FP32 LU's Schur complement in 3xTF32 on the mixed path; handles with TF32 or
+    BF16 Schur operands always take the tensor-core form).
     order 0 (mixed orders): the FP64 panel stays 16 (the largest elements' panel of
     32 does not fit in shared memory)."""
     panels = [16, 32] if (precision == 0 and 1 <= order <= 3) else [16]
@@ -32,8 +33,10 @@ def candidates(precision, order):
         out = [dict(lu_persistent=a, lu_panel=b, asm_chunk=c, lu_tensor=0)
                for a, b, c in itertools.product([1, 0], panels, chunks)]
         return out + [dict(lu_persistent=1, lu_panel=16, asm_chunk=c, lu_tensor=1) for c in chunks]
+    # TF32 / BF16 Schur operands: the tensor-core form is what the precision means
+    tensor = [1, 0] if precision == 1 else [1]
     return [dict(lu_persistent=a, lu_panel=b, asm_chunk=c, lu_tensor=t)
-            for a, b, c, t in itertools.product([1, 0], panels, chunks, [1, 0])]
+            for a, b, c, t in itertools.product([1, 0], panels, chunks, tensor)]
 
 
 def time_assemble(mesh, u, q, uh, K, R, reps, warm=True):

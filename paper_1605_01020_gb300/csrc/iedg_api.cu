@@ -499,6 +499,16 @@ static int create_impl(const iedg_mesh_desc* D, cudaStream_t st, iedg_mesh* M) {
   return run_geometry(M, D->node_xyz, st);
 }
 
+// Storage precision (FP64 or FP32 element matrices), the Schur GEMM's operands on the
+// mixed path and the default LU form (FP64: DFMA unless chosen; mixed: tensor cores).
+static void set_precision(iedg_mesh* M, int precision) {
+  M->precision = precision == IEDG_PRECISION_FP64 ? 0 : 1;
+  M->schur_in = precision == IEDG_PRECISION_MIXED_TF32   ? kSchurTf32
+                : precision == IEDG_PRECISION_MIXED_BF16 ? kSchurBf16
+                                                         : kSchurFp32;
+  M->sched.lu_tensor = M->precision;
+}
+
 static int check_desc(const iedg_mesh_desc* D, bool mixed) {
   iedg_mesh* M = nullptr;
   if (!(D->dim == 2 || D->dim == 3)) return fail(M, IEDG_ERR_INVALID_ARG, "dim must be 2 or 3");
@@ -506,8 +516,8 @@ static int check_desc(const iedg_mesh_desc* D, bool mixed) {
     return fail(M, IEDG_ERR_UNSUPPORTED, "order must be 1..4 (3D) or 1..3 (2D)");
   if (D->quad_extra < 1 || D->quad_extra > 3)
     return fail(M, IEDG_ERR_UNSUPPORTED, "quad_extra must be 1..3");
-  if (D->precision != IEDG_PRECISION_FP64 && D->precision != IEDG_PRECISION_MIXED)
-    return fail(M, IEDG_ERR_UNSUPPORTED, "precision must be IEDG_PRECISION_FP64 or IEDG_PRECISION_MIXED");
+  if (D->precision < IEDG_PRECISION_FP64 || D->precision > IEDG_PRECISION_MIXED_BF16)
+    return fail(M, IEDG_ERR_UNSUPPORTED, "precision must be one of IEDG_PRECISION_FP64, _MIXED, _MIXED_TF32, _MIXED_BF16");
   if (D->stab != 0 && D->stab != 1)
     return fail(M, IEDG_ERR_UNSUPPORTED, "stab must be 0 (Lax-Friedrichs) or 1 (Roe-type)");
   if (D->n_elem <= 0 || D->n_trace <= 0 || !D->node_xyz || !D->elem_trace)
@@ -537,8 +547,7 @@ extern "C" int iedg_create_mesh(const iedg_mesh_desc* D, void* stream, iedg_mesh
   M = new iedg_mesh();
   M->dm = make_dims(D->dim, D->order, D->quad_extra);
   M->ph = Phys{D->gamma, D->Pr, D->Re, D->alpha, D->stab, {0, 0, 0, 0, 0}};
-  M->precision = D->precision;
-  M->sched.lu_tensor = D->precision == IEDG_PRECISION_MIXED ? 1 : 0;   // FP64: DFMA unless chosen
+  set_precision(M, D->precision);
   M->E = D->n_elem;
   M->T = D->n_trace;
   rc = create_impl(D, (cudaStream_t)stream, M);
@@ -688,6 +697,7 @@ static int create_mixed_impl(const iedg_mesh_desc* D, const int32_t* ord, const 
     C->dm = cd;
     C->ph = M->ph;
     C->precision = M->precision;
+    C->schur_in = M->schur_in;
     C->E = (int64_t)gel[c].size();
     C->T = M->T;
     C->sched = M->sched;
@@ -865,8 +875,7 @@ extern "C" int iedg_create_mesh_bc(const iedg_mesh_desc* D, const int32_t* elem_
   M->ph = Phys{D->gamma, D->Pr, D->Re, D->alpha, D->stab, {0, 0, 0, 0, 0}};
   if (u_far)
     for (int i = 0; i < m; ++i) M->ph.ub[i] = u_far[i];
-  M->precision = D->precision;
-  M->sched.lu_tensor = D->precision == IEDG_PRECISION_MIXED ? 1 : 0;   // FP64: DFMA unless chosen
+  set_precision(M, D->precision);
   M->E = D->n_elem;
   M->T = D->n_trace;
   rc = create_mixed_impl(D, elem_order, face_degree, face_kind, (cudaStream_t)stream, M);

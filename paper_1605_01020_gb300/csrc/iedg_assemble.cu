@@ -17,6 +17,8 @@
 // (mu_s = phi_bnode[s] on every face), which is how they are formed here.
 // The right-hand-side column is written by the point kernel: Ft = -R_u(u, q*),
 // Gt = -R_FL,e(u, q*) (exact because the fluxes are affine in q).
+#include <cuda_bf16.h>
+
 #include "iedg_internal.cuh"
 #include "iedg_tc.cuh"
 
@@ -724,55 +726,79 @@ __device__ __forceinline__ void lu32_update_rect(float* __restrict__ A, int ld, 
 // [nu, n) and columns [nu, n], W = A[nu:n, 0:nu] (the eliminated trace rows, L21 of
 // every panel) and Z = A[0:nu, nu:n] (U12 of every panel), so K accumulates over the
 // whole K = nu in TMEM and the trace block is read and written once.  128 x 64 output
-// tiles, K chunks of 32 staged as TF32 high and low parts (3xTF32: hi hi + hi lo + lo hi)
-// in two operand stages (48 KB each) so that one chunk is staged while the tensor core
-// works on the other; one thread issues the MMAs, completion through per-stage mbarriers
-// with bounded waits; the epilogue reads TMEM with all eight warps.
+// tiles, K chunks of 32 in two operand stages so that one chunk is staged while the
+// tensor core works on the other; one thread issues the MMAs, completion through
+// per-stage mbarriers with bounded waits; the epilogue reads TMEM with all eight warps.
+// Operand forms (KIND): kSchurFp32 = TF32 high and low parts, three products (hi hi +
+// hi lo + lo hi, FP32 accuracy, 48 KB stages); kSchurTf32 = one product of the operands
+// rounded to TF32 (24 KB); kSchurBf16 = one product of BF16 operands (12 KB).  All
+// accumulate in FP32.
 constexpr int TC_TM = 128, TC_TN = 64, TC_KC = 32;
-constexpr int TC_STAGE_BYTES = 2 * TC_TM * TC_KC * 4 + 2 * TC_TN * TC_KC * 4;   // 48 KB
+constexpr int TC_STAGE_BYTES = 2 * TC_TM * TC_KC * 4 + 2 * TC_TN * TC_KC * 4;   // 48 KB, the largest form
 
+template <int KIND>
+struct SchurForm {
+  static constexpr int EB = KIND == kSchurBf16 ? 2 : 4;          // bytes per operand value
+  static constexpr int PARTS = KIND == kSchurFp32 ? 2 : 1;       // hi (+ lo)
+  static constexpr int A_BYTES = TC_TM * TC_KC * EB, B_BYTES = TC_TN * TC_KC * EB;
+  static constexpr int SBO = TC_KC * EB / 16 * 128;               // 8-row group stride
+  __device__ static uint32_t off(int row, int k) { return EB == 4 ? tc::core_off32(row, k) : tc::core_off16(row, k); }
+  // value v at (row, k) of the A (b = false) or B operand tile
+  __device__ static void put(char* stage, bool b, int row, int k, float v) {
+    char* base = stage + (b ? PARTS * A_BYTES : 0);
+    const uint32_t o = off(row, k);
+    if constexpr (KIND == kSchurFp32) {
+      float hi, lo;
+      tc::split_tf32(v, hi, lo);
+      *reinterpret_cast<float*>(base + o) = hi;
+      *reinterpret_cast<float*>(base + (b ? B_BYTES : A_BYTES) + o) = lo;
+    } else if constexpr (KIND == kSchurTf32) {
+      *reinterpret_cast<float*>(base + o) = tc::round_tf32(v);
+    } else {
+      *reinterpret_cast<__nv_bfloat16*>(base + o) = __float2bfloat16_rn(v);
+    }
+  }
+};
+
+template <int KIND>
 __device__ __forceinline__ void schur_stage(const float* __restrict__ A, int ld, int n, int nu, int ncol, int rt,
                                             int ct, int kc, char* stage) {
-  float* sAh = reinterpret_cast<float*>(stage);
-  float* sAl = reinterpret_cast<float*>(stage + TC_TM * TC_KC * 4);
-  float* sBh = reinterpret_cast<float*>(stage + 2 * TC_TM * TC_KC * 4);
-  float* sBl = reinterpret_cast<float*>(stage + 2 * TC_TM * TC_KC * 4 + TC_TN * TC_KC * 4);
+  using F = SchurForm<KIND>;
   const int tid = threadIdx.x;
   // A operand: W rows rt .. rt+127, K columns kc .. kc+31 (k fastest: coalesced rows)
   for (int idx = tid; idx < TC_TM * TC_KC; idx += LU_THREADS) {
     const int mm = idx >> 5, k = idx & 31;
     const int r = rt + mm, c = kc + k;
-    const float v = (r < n && c < nu) ? A[(int64_t)r * ld + c] : 0.f;
-    float hi, lo;
-    tc::split_tf32(v, hi, lo);
-    const uint32_t off = tc::core_off32(mm, k);
-    *reinterpret_cast<float*>(reinterpret_cast<char*>(sAh) + off) = hi;
-    *reinterpret_cast<float*>(reinterpret_cast<char*>(sAl) + off) = lo;
+    F::put(stage, false, mm, k, (r < n && c < nu) ? A[(int64_t)r * ld + c] : 0.f);
   }
   // B operand (N x K, K-major): Z rows kc .. kc+31, columns ct .. ct+63 (column fastest)
   for (int idx = tid; idx < TC_TN * TC_KC; idx += LU_THREADS) {
     const int k = idx >> 6, nn = idx & 63;
     const int r = kc + k, c = ct + nn;
-    const float v = (r < nu && c < ncol) ? A[(int64_t)r * ld + c] : 0.f;
-    float hi, lo;
-    tc::split_tf32(v, hi, lo);
-    const uint32_t off = tc::core_off32(nn, k);
-    *reinterpret_cast<float*>(reinterpret_cast<char*>(sBh) + off) = hi;
-    *reinterpret_cast<float*>(reinterpret_cast<char*>(sBl) + off) = lo;
+    F::put(stage, true, nn, k, (r < nu && c < ncol) ? A[(int64_t)r * ld + c] : 0.f);
   }
 }
 
+template <int KIND>
 __device__ __forceinline__ void schur_issue(uint32_t tmem, const char* stage, bool first) {
-  const uint32_t aH = tc::smem_u32(stage), aL = aH + TC_TM * TC_KC * 4;
-  const uint32_t bH = aH + 2 * TC_TM * TC_KC * 4, bL = bH + TC_TN * TC_KC * 4;
-  constexpr uint32_t IDESC = tc::idesc_tf32(TC_TM, TC_TN);
+  using F = SchurForm<KIND>;
+  const uint32_t aH = tc::smem_u32(stage), aL = aH + F::A_BYTES;
+  const uint32_t bH = aH + F::PARTS * F::A_BYTES, bL = bH + F::B_BYTES;
+  // one instruction covers 32 bytes of K (8 TF32 or 16 BF16 values): two core matrices
 #pragma unroll
-  for (int st = 0; st < TC_KC / 8; ++st) {
-    const uint32_t ko = st * 256;
-    tc::mma_tf32(tmem, tc::desc_kmajor(aH + ko, 128, 1024), tc::desc_kmajor(bH + ko, 128, 1024), IDESC,
-                 (first && st == 0) ? 0u : 1u);
-    tc::mma_tf32(tmem, tc::desc_kmajor(aH + ko, 128, 1024), tc::desc_kmajor(bL + ko, 128, 1024), IDESC, 1);
-    tc::mma_tf32(tmem, tc::desc_kmajor(aL + ko, 128, 1024), tc::desc_kmajor(bH + ko, 128, 1024), IDESC, 1);
+  for (int st = 0; st < TC_KC * F::EB / 32; ++st) {
+    const uint32_t ko = st * 256, acc = (first && st == 0) ? 0u : 1u;
+    if constexpr (KIND == kSchurBf16) {
+      constexpr uint32_t IDESC = tc::idesc_bf16(TC_TM, TC_TN);
+      tc::mma_bf16(tmem, tc::desc_kmajor(aH + ko, 128, F::SBO), tc::desc_kmajor(bH + ko, 128, F::SBO), IDESC, acc);
+    } else {
+      constexpr uint32_t IDESC = tc::idesc_tf32(TC_TM, TC_TN);
+      tc::mma_tf32(tmem, tc::desc_kmajor(aH + ko, 128, F::SBO), tc::desc_kmajor(bH + ko, 128, F::SBO), IDESC, acc);
+      if constexpr (KIND == kSchurFp32) {
+        tc::mma_tf32(tmem, tc::desc_kmajor(aH + ko, 128, F::SBO), tc::desc_kmajor(bL + ko, 128, F::SBO), IDESC, 1);
+        tc::mma_tf32(tmem, tc::desc_kmajor(aL + ko, 128, F::SBO), tc::desc_kmajor(bH + ko, 128, F::SBO), IDESC, 1);
+      }
+    }
   }
 }
 
@@ -785,6 +811,7 @@ __device__ __forceinline__ bool schur_wait(TcState* tcs, int b) {
   return ok;
 }
 
+template <int KIND>
 __device__ void schur_tc(float* __restrict__ A, int ld, int n, int nu, char* smem, TcState* tcs) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ncol = n + 1;
@@ -792,20 +819,20 @@ __device__ void schur_tc(float* __restrict__ A, int ld, int n, int nu, char* sme
   const int q = warp & 3, h = warp >> 2;
   for (int rt = nu; rt < n && !tcs->failed; rt += TC_TM) {
     for (int ct = nu; ct < ncol && !tcs->failed; ct += TC_TN) {
-      schur_stage(A, ld, n, nu, ncol, rt, ct, 0, smem);
+      schur_stage<KIND>(A, ld, n, nu, ncol, rt, ct, 0, smem);
       tc::fence_proxy_async();
       __syncthreads();
       tc::fence_after_sync();
       for (int c = 0; c < nk; ++c) {
         const int b = c & 1;
         if (tid == 0) {
-          schur_issue(tcs->tmem, smem + b * TC_STAGE_BYTES, c == 0);
+          schur_issue<KIND>(tcs->tmem, smem + b * TC_STAGE_BYTES, c == 0);
           tc::mma_commit(tcs->mbar + b);
         }
         if (c + 1 < nk) {
           // the other stage was last read by the MMAs of chunk c - 1
           if (c >= 1 && !schur_wait(tcs, b ^ 1)) break;
-          schur_stage(A, ld, n, nu, ncol, rt, ct, (c + 1) * TC_KC, smem + (b ^ 1) * TC_STAGE_BYTES);
+          schur_stage<KIND>(A, ld, n, nu, ncol, rt, ct, (c + 1) * TC_KC, smem + (b ^ 1) * TC_STAGE_BYTES);
           tc::fence_proxy_async();
           __syncthreads();
           tc::fence_after_sync();
@@ -835,7 +862,7 @@ __device__ void schur_tc(float* __restrict__ A, int ld, int n, int nu, char* sme
   }
 }
 
-template <bool TC>
+template <bool TC, int KIND = kSchurFp32>
 __device__ __forceinline__ void lu32_element(const LuElem& el, float* __restrict__ S, int8_t* __restrict__ status,
                                              int* __restrict__ pivots, const int64_t e, TcState* tcs) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -945,7 +972,7 @@ __device__ __forceinline__ void lu32_element(const LuElem& el, float* __restrict
   }
   if constexpr (TC) {
     __syncthreads();
-    schur_tc(A, ld, n, nu, reinterpret_cast<char*>(smraw), tcs);     // the panel buffer is free now
+    schur_tc<KIND>(A, ld, n, nu, reinterpret_cast<char*>(smraw), tcs);     // the panel buffer is free now
   }
   __syncthreads();
   int bad = 0;
@@ -997,6 +1024,7 @@ k_lu32(Dims dm, LuDesc lud, float* __restrict__ S, int8_t* __restrict__ status, 
 // Tensor-core form: TMEM (128 columns) and the completion barrier are set up once per
 // CTA; a CTA whose completion wait ran out stops taking elements, waits once more
 // (bounded) for its MMAs, and frees its TMEM.
+template <int KIND>
 __global__ void __launch_bounds__(LU_THREADS, 2)
 k_lu32_tc(Dims dm, LuDesc lud, float* __restrict__ S, int8_t* __restrict__ status, int* __restrict__ pivots,
           int64_t* queue, int64_t E, int* err) {
@@ -1027,7 +1055,7 @@ k_lu32_tc(Dims dm, LuDesc lud, float* __restrict__ S, int8_t* __restrict__ statu
   TcState mine = tcs;
   int64_t e;
   for (int64_t it = 0; next_element(queue, E, it, lud.order, &e); ++it) {
-    lu32_element<true>(lu_elem(dm, lud, e), S, status, pivots, e, &mine);
+    lu32_element<true, KIND>(lu_elem(dm, lud, e), S, status, pivots, e, &mine);
     if (__syncthreads_or(mine.failed)) {
       if (tid == 0) atomicOr(err, 1);
       // let MMAs still in flight drain (bounded) before the TMEM is freed
@@ -1214,31 +1242,38 @@ static cudaError_t lu64_oz(iedg_mesh* M, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// FP32 partial LU with the Schur complement on the tensor cores in operand form KIND.
+template <int KIND>
+static cudaError_t lu32_tc(iedg_mesh* M, cudaStream_t st) {
+  const Dims& dm = M->dm;
+  // panel + U chunk during the factorisation; the two operand stages of the Schur GEMM
+  // reuse the same buffer afterwards
+  size_t smem = sizeof(float) * ((size_t)L32_NB * dm.n + (size_t)L32_NB * L32_UCW);
+  if (smem < 2 * (size_t)TC_STAGE_BYTES) smem = 2 * (size_t)TC_STAGE_BYTES;
+  cudaError_t err = cudaFuncSetAttribute(k_lu32_tc<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  unsigned grid = (unsigned)M->E;
+  int64_t* queue = nullptr;
+  if (M->sched.lu_persistent) {
+    err = persistent_grid(k_lu32_tc<KIND>, smem, M->E, &grid);
+    if (err == cudaSuccess) err = cudaMemsetAsync(M->queue, 0, sizeof(int64_t), st);
+    if (err != cudaSuccess) return err;
+    queue = M->queue;
+  }
+  k_lu32_tc<KIND><<<grid, LU_THREADS, smem, st>>>(dm, M->lud, M->S32, M->status, M->piv, queue, M->E, M->dev_flag);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_lu(iedg_mesh* M, cudaStream_t st) {
   if (M->precision == 0 && M->sched.lu_tensor) return lu64_oz(M, st);
   if (M->precision == 0) {
     if (M->sched.lu_panel == 32 && lu64_smem(M->dm, 32) <= 227 * 1024) return lu_t<double, 32>(M, M->S, nullptr, st);
     return lu_t<double, 16>(M, M->S, nullptr, st);
   }
+  if (M->schur_in == kSchurTf32) return lu32_tc<kSchurTf32>(M, st);
+  if (M->schur_in == kSchurBf16) return lu32_tc<kSchurBf16>(M, st);
+  if (M->sched.lu_tensor) return lu32_tc<kSchurFp32>(M, st);
   const Dims& dm = M->dm;
-  if (M->sched.lu_tensor) {
-    // panel + U chunk during the factorisation; the two operand stages of the Schur GEMM
-    // reuse the same buffer afterwards
-    size_t smem = sizeof(float) * ((size_t)L32_NB * dm.n + (size_t)L32_NB * L32_UCW);
-    if (smem < 2 * (size_t)TC_STAGE_BYTES) smem = 2 * (size_t)TC_STAGE_BYTES;
-    cudaError_t err = cudaFuncSetAttribute(k_lu32_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return err;
-    unsigned grid = (unsigned)M->E;
-    int64_t* queue = nullptr;
-    if (M->sched.lu_persistent) {
-      err = persistent_grid(k_lu32_tc, smem, M->E, &grid);
-      if (err == cudaSuccess) err = cudaMemsetAsync(M->queue, 0, sizeof(int64_t), st);
-      if (err != cudaSuccess) return err;
-      queue = M->queue;
-    }
-    k_lu32_tc<<<grid, LU_THREADS, smem, st>>>(dm, M->lud, M->S32, M->status, M->piv, queue, M->E, M->dev_flag);
-    return cudaGetLastError();
-  }
   size_t smem = sizeof(float) * ((size_t)L32_NB * dm.n + (size_t)L32_NB * L32_UCW);
   cudaError_t err = cudaFuncSetAttribute(k_lu32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;

@@ -29,6 +29,8 @@ struct Phys {
 
 // face kinds of meshes with domain boundaries
 constexpr int kFaceInterior = 0, kFaceFarField = 1, kFaceWall = 2;
+// operands of the Schur GEMM K = D - W Z on the mixed path
+constexpr int kSchurFp32 = 0, kSchurTf32 = 1, kSchurBf16 = 2;
 
 // Launch schedule (host-side choices the autotuner sweeps; see iedg_schedule).
 struct Schedule {
@@ -158,7 +160,8 @@ struct iedg_mesh {
   double* rhat = nullptr;       // [E][Nb][m]    element trace residuals
   double* S = nullptr;          // [E][n][ld]    bordered element matrices (FP64 path)
   // mixed path (FP32 condensation, FP64 refinement)
-  int precision = 0;
+  int precision = 0;            // 0 = FP64, 1 = mixed (FP32 element matrix and LU)
+  int schur_in = 0;             // mixed: operands of the Schur GEMM (kSchurFp32 / Tf32 / Bf16)
   float* S32 = nullptr;         // [E][n][ld]    bordered element matrices, FP32, L kept
   int* piv = nullptr;           // [E][nu]       pivot rows of the FP32 partial LU
   double* rhs64 = nullptr;      // [E][n]        FP64 right-hand sides F~, G~

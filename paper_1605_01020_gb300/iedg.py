@@ -23,6 +23,8 @@ EXPORTS = ("iedg_create_mesh", "iedg_destroy_mesh", "iedg_last_error", "iedg_mes
            "iedg_set_trace_precond", "iedg_bilu0_factor", "iedg_bilu0_apply", "iedg_trace_colors",
            "iedg_create_mesh_bc")
 PREC_BLOCK_JACOBI, PREC_BILU0 = 0, 1
+# element-matrix precision of a handle (IEDG_PRECISION_*)
+PRECISION_FP64, PRECISION_MIXED, PRECISION_MIXED_TF32, PRECISION_MIXED_BF16 = 0, 1, 2, 3
 
 
 class IedgError(RuntimeError):

@@ -39,9 +39,10 @@ def bsr_row_err(row_ptr, vals, ref_vals, rows):
     return worst
 
 
-def oracle_K_rows(pb, mesh, st, rows, u_ref=None):
+def oracle_K_rows(pb, mesh, st, rows, u_ref=None, kfun=None):
     """Oracle BSR values restricted to the block rows `rows` (sums over the elements
-    touching each row, in element order), plus R on those rows."""
+    touching each row, in element order), plus R on those rows.  kfun(e), if given,
+    replaces the element's condensed block K_e."""
     row_ptr, col = oiedg.bsr_pattern(mesh.elem_trace, mesh.n_trace)
     m = pb.m
     vals = np.zeros((len(col), m, m))
@@ -51,6 +52,8 @@ def oracle_K_rows(pb, mesh, st, rows, u_ref=None):
     re_max = 0.0
     for e in els:
         Ke, Re = pb.condense_qelim(e, st.u, st.q, st.uhat, u_ref)
+        if kfun is not None:
+            Ke = kfun(e)
         re_max = max(re_max, np.abs(Re).max())
         tr = mesh.elem_trace[e]
         for s in range(len(tr)):
@@ -60,3 +63,14 @@ def oracle_K_rows(pb, mesh, st, rows, u_ref=None):
             for t in range(len(tr)):
                 vals[oiedg.bsr_find(row_ptr, col, tr[s], tr[t])] += Ke[s, :, t, :]
     return row_ptr, col, vals, R, els, re_max
+
+
+def fro_ratio(row_ptr, vals, ref_vals, exact_vals, rows):
+    """||K - K_ref||_F / ||K_ref - K_exact||_F over the block rows `rows`: how far the
+    device result is from the rounded-operand oracle, against the rounding's own size."""
+    num = den = 0.0
+    for r in rows:
+        sl = slice(row_ptr[r], row_ptr[r + 1])
+        num += float(((vals[sl] - ref_vals[sl]) ** 2).sum())
+        den += float(((ref_vals[sl] - exact_vals[sl]) ** 2).sum())
+    return (num / den) ** 0.5 if den > 0 else float("inf")

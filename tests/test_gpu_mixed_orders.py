@@ -8,10 +8,10 @@ import numpy as np
 import pytest
 
 from oracle import iedg as oiedg
-from oracle import physics
+from oracle import lowprec, physics
 from paper_1605_01020_gb300 import workloads as W
 from oracle_helpers import ref_element
-from gpu_helpers import bsr_row_err, dev, host, rel_err
+from gpu_helpers import bsr_row_err, dev, fro_ratio, host, rel_err
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-11
@@ -116,7 +116,7 @@ def _oracle_condensed(mesh, st, u_ref, pb):
 
 
 @pytest.mark.parametrize("name", CASES)
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 3])
 def test_mixed_orders_condensed_parity(name, precision):
     mesh, st, u_ref, prm = _case(name)
     pb = _problem(mesh, prm)
@@ -126,7 +126,16 @@ def test_mixed_orders_condensed_parity(name, precision):
                                      u_ref=None if u_ref is None else dev(_cat(u_ref)))
     du_d, dq_d = lm.back_substitute(dev(st.duhat))
     tk, tr = (TOL, TOL) if precision == 0 else (TOL_MIXED_K, TOL_MIXED)
-    assert bsr_row_err(row_ptr, host(K_d), vals, range(mesh.n_trace)) <= tk
+    if precision == 3:
+        # BF16 Schur operands: against the oracle's condensation with rounded operands
+        # (ratio bound as in test_gpu_parity)
+        Kl = [lowprec.condense_rounded(pb.pbs[e], pb.element_blocks(e, st.u, st.q, st.uhat, u_ref), "bf16")[0]
+              for e in range(mesh.n_elem)]
+        Re0 = [np.zeros((len(t), pb.m)) for t in mesh.elem_trace]
+        vals_low = oiedg.assemble_ragged(mesh.elem_trace, mesh.n_trace, Kl, Re0)[2]
+        assert fro_ratio(row_ptr, host(K_d), vals_low, vals, range(mesh.n_trace)) <= 0.5
+    else:
+        assert bsr_row_err(row_ptr, host(K_d), vals, range(mesh.n_trace)) <= tk
     assert rel_err(host(R_d), R, floor=re_max) <= tr
     assert (lm.element_status() == 0).all()
     assert rel_err(host(du_d), du_o) <= tr

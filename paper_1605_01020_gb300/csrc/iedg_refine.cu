@@ -76,47 +76,44 @@ __device__ void element_apply(const Dims& dm, const Phys& ph, const RefTables& r
   const int m = dm.m, d = dm.d, Np = dm.Np, Nb = dm.Nb, Nq = dm.Nq, Nfp = dm.Nfp, Nfq = dm.Nfq;
   const int Nfn = dm.Nfn;
   const int nbe = tt.nb ? tt.nb[e] : Nb;
-  // nodal lifted gradient of (x, z): dq_kl = -G_l x_k + H_l z_k.  One warp per row
-  // (l, c) of G_l | H_l: the lanes read the row once, coalesced, for all m components.
-  {
-    const int lane = tid & 31, warp = tid >> 5, nwarp = RF_THREADS / 32;
-    for (int row = warp; row < d * Np; row += nwarp) {
-      const int l = row / Np, c = row % Np;
-      const double* gl = G.Gl + (((size_t)e * d + l) * Np + c) * Np;
-      const double* hl = G.Hl + (((size_t)e * d + l) * Np + c) * Nb;
-      double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-      if (use_x)
-        for (int b = lane; b < Np; b += 32) {
-          const double g = gl[b];
+  // nodal lifted gradient of (x, z): dq_kl = -G_l x_k + H_l z_k.  One thread per row
+  // (l, c) of G_l | H_l for all m components: each row is read once and no partial
+  // sums need combining (FP64 adds are as slow as FP64 FMAs here).
+  for (int row = tid; row < d * Np; row += RF_THREADS) {
+    const int l = row / Np, c = row % Np;
+    const double* gl = G.Gl + (((size_t)e * d + l) * Np + c) * Np;
+    const double* hl = G.Hl + (((size_t)e * d + l) * Np + c) * Nb;
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (use_x)
+      for (int b = 0; b < Np; ++b) {
+        const double g = gl[b];
 #pragma unroll
-          for (int k = 0; k < 5; ++k)
-            if (k < m) acc[k] = fma(-g, w.x[k * Np + b], acc[k]);
-        }
-      if (use_z)
-        for (int t = lane; t < nbe; t += 32) {
-          const double h = hl[t];
-#pragma unroll
-          for (int k = 0; k < 5; ++k)
-            if (k < m) acc[k] = fma(h, w.z[k * Nb + t], acc[k]);
-        }
-#pragma unroll
-      for (int k = 0; k < 5; ++k) {
-        double v = acc[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0 && k < m) w.dqn[(k * d + l) * Np + c] = v;
+        for (int k = 0; k < 5; ++k)
+          if (k < m) acc[k] = fma(-g, w.x[k * Np + b], acc[k]);
       }
-    }
+    if (use_z)
+      for (int t = 0; t < nbe; ++t) {
+        const double h = hl[t];
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+          if (k < m) acc[k] = fma(h, w.z[k * Nb + t], acc[k]);
+      }
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+      if (k < m) w.dqn[(k * d + l) * Np + c] = acc[k];
   }
   __syncthreads();
   // values at volume points (rows: x_k, then dq_kl)
   const int nrow = m + m * d;
   if (d == 3) {
-    // tensor-product interpolation: x direction first (into the point-flux buffer tv,
-    // which is free here), then y and z together
+    // tensor-product interpolation, one direction at a time: x, then y, into the
+    // region tv | xf | zf | xqf (contiguous in the work layout; tv is free here and the
+    // face values are written only later; nrow (S1 + S2) fits it for p <= 4 and every
+    // quad_extra), then z into the point values
     const int np1 = dm.np1, nq1 = dm.nq1;
-    const int S1 = nq1 * np1 * np1;
-    double* t1 = w.tv;                      // nrow * S1 <= m d Nq
+    const int S1 = nq1 * np1 * np1, S2 = nq1 * nq1 * np1;
+    double* t1 = w.tv;
+    double* t2 = w.tv + (size_t)nrow * S1;
     for (int idx = tid; idx < nrow * S1; idx += RF_THREADS) {
       int row = idx / S1, t = idx % S1;
       int gx = t % nq1, ayz = t / nq1;
@@ -126,18 +123,54 @@ __device__ void element_apply(const Dims& dm, const Phys& ph, const RefTables& r
       t1[idx] = s;
     }
     __syncthreads();
+    for (int idx = tid; idx < nrow * S2; idx += RF_THREADS) {
+      int row = idx / S2, t = idx % S2;
+      int gx = t % nq1, gy = (t / nq1) % nq1, az = t / (nq1 * nq1);
+      const double* src = t1 + row * S1 + gx + nq1 * np1 * az;
+      double s = 0.0;
+      for (int ay = 0; ay < np1; ++ay) s = fma(w.sL[gy * np1 + ay], src[nq1 * ay], s);
+      t2[idx] = s;
+    }
+    __syncthreads();
     for (int idx = tid; idx < nrow * Nq; idx += RF_THREADS) {
       int row = idx / Nq, g = idx % Nq;
-      int gx = g % nq1, gy = (g / nq1) % nq1, gz = g / (nq1 * nq1);
-      const double* src = t1 + row * S1 + gx;
+      int gxy = g % (nq1 * nq1), gz = g / (nq1 * nq1);
+      const double* src = t2 + row * S2 + gxy;
       double s = 0.0;
-      for (int az = 0; az < np1; ++az) {
-        double t = 0.0;
-        for (int ay = 0; ay < np1; ++ay) t = fma(w.sL[gy * np1 + ay], src[nq1 * (ay + np1 * az)], t);
-        s = fma(w.sL[gz * np1 + az], t, s);
-      }
+      for (int az = 0; az < np1; ++az) s = fma(w.sL[gz * np1 + az], src[nq1 * nq1 * az], s);
       if (row < m) w.xv[row * Nq + g] = s;
       else w.xq[(row - m) * Nq + g] = s;
+    }
+    __syncthreads();
+    // values of x (if used) and dq at the face points: on face f the face nodes form
+    // an np1 x np1 lattice over the two tangential directions (in the order of fnode)
+    // and the face points an nq1 x nq1 lattice, so two 1D stages per face
+    const int xr = use_x ? m : 0, nr = xr + m * d, nf = dm.nf;
+    const int FA = nq1 * np1;
+    double* u1 = w.tv;                      // rows in chunks of rc: rc * nf * FA <= m d Nq
+    const int rc = (m * d * Nq) / (nf * FA);
+    for (int r0 = 0; r0 < nr; r0 += rc) {
+      const int r1 = min(nr, r0 + rc);
+      for (int idx = tid; idx < (r1 - r0) * nf * FA; idx += RF_THREADS) {
+        int row = r0 + idx / (nf * FA), f = (idx / FA) % nf, t = idx % FA;
+        int g0 = t % nq1, a1 = t / nq1;
+        const int* fn = ref.fnode + f * Nfn + np1 * a1;
+        const double* src = row < xr ? w.x + row * Np : w.dqn + (row - xr) * Np;
+        double s = 0.0;
+        for (int a0 = 0; a0 < np1; ++a0) s = fma(w.sL[g0 * np1 + a0], src[fn[a0]], s);
+        u1[idx] = s;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < (r1 - r0) * Nfp; idx += RF_THREADS) {
+        int row = r0 + idx / Nfp, fp = idx % Nfp, f = fp / Nfq, gf = fp % Nfq;
+        int g0 = gf % nq1, g1 = gf / nq1;
+        const double* src = u1 + ((size_t)(row - r0) * nf + f) * FA + g0;
+        double s = 0.0;
+        for (int a1 = 0; a1 < np1; ++a1) s = fma(w.sL[g1 * np1 + a1], src[nq1 * a1], s);
+        if (row < xr) w.xf[row * Nfp + fp] = s;
+        else w.xqf[(row - xr) * Nfp + fp] = s;
+      }
+      __syncthreads();
     }
   } else {
     for (int idx = tid; idx < nrow * Nq; idx += RF_THREADS) {
@@ -150,10 +183,11 @@ __device__ void element_apply(const Dims& dm, const Phys& ph, const RefTables& r
       else w.xq[(row - m) * Nq + g] = s;
     }
   }
-  // values at face points (face nodes only)
+  // values at face points from the face nodes: every row in 2D, the trace rows in 3D
   for (int idx = tid; idx < (2 * m + m * d) * Nfp; idx += RF_THREADS) {
     int row = idx / Nfp, fp = idx % Nfp, f = fp / Nfq;
     if ((row < m && !use_x) || (row >= m && row < 2 * m && !use_z)) continue;
+    if (d == 3 && (row < m || row >= 2 * m)) continue;
     const double* phi = ref.PhiF + (size_t)fp * Np;
     double s = 0.0;
     if (tt.nfs && row >= m && row < 2 * m) {
@@ -227,7 +261,21 @@ __device__ void element_apply(const Dims& dm, const Phys& ph, const RefTables& r
     const int np1 = dm.np1, nq1 = dm.nq1;
     const int TS = nq1 * nq1 * np1, VS = nq1 * np1 * np1;
     double* t1 = w.xq;                      // m 3 TS <= m d Nq (xq is free here)
-    double* t2 = w.dqn;                     // m 2 VS <= m d Np (dqn is free here)
+    double* t2 = w.dqn;                     // m 2 VS <= m d Np + m Nq: dqn | xv, both free here
+    // face terms sum_fp PhiF[fp][a] tf(fp) per face: first over the points' first
+    // tangential index (into xqf, free now), then the second (into xf), so that
+    // fb[i][f][tn] holds face f's term for its tn-th node
+    const int nf = dm.nf, FB = nq1 * np1, Nfn1 = np1 * np1;
+    double* fu = w.xqf;                     // m nf FB <= m d Nfp
+    double* fb = w.xf;                      // m nf Nfn <= m Nfp
+    for (int idx = tid; idx < m * nf * FB; idx += RF_THREADS) {
+      int i = idx / (nf * FB), f = (idx / FB) % nf, t = idx % FB;
+      int a0 = t % np1, g1 = t / np1;
+      const double* src = w.tf + i * Nfp + f * Nfq + nq1 * g1;
+      double s = 0.0;
+      for (int g0 = 0; g0 < nq1; ++g0) s = fma(w.sL[g0 * np1 + a0], src[g0], s);
+      fu[idx] = s;
+    }
     for (int idx = tid; idx < m * 3 * TS; idx += RF_THREADS) {
       int i = idx / (3 * TS), r = (idx / TS) % 3, t = idx % TS;
       int gxy = t % (nq1 * nq1), az = t / (nq1 * nq1);
@@ -255,6 +303,14 @@ __device__ void element_apply(const Dims& dm, const Phys& ph, const RefTables& r
       t2[(i * 2 + 0) * VS + t] = s0;
       t2[(i * 2 + 1) * VS + t] = s1;
     }
+    for (int idx = tid; idx < m * nf * Nfn1; idx += RF_THREADS) {
+      int i = idx / (nf * Nfn1), f = (idx / Nfn1) % nf, tn = idx % Nfn1;
+      int a0 = tn % np1, a1 = tn / np1;
+      const double* src = fu + ((size_t)i * nf + f) * FB + a0;
+      double s = 0.0;
+      for (int g1 = 0; g1 < nq1; ++g1) s = fma(w.sL[g1 * np1 + a1], src[np1 * g1], s);
+      fb[idx] = s;
+    }
     __syncthreads();
   }
   for (int idx = tid; idx < m * Np; idx += RF_THREADS) {
@@ -280,8 +336,21 @@ __device__ void element_apply(const Dims& dm, const Phys& ph, const RefTables& r
         for (int r = 0; r < d; ++r)
           s = fma(ref.Dxi[((size_t)r * Nq + g) * Np + a], w.tv[(i * d + r) * Nq + g], s);
     }
-    if (ref.slot[a] >= 0)
-      for (int fp = 0; fp < Nfp; ++fp) s = fma(ref.PhiF[(size_t)fp * Np + a], w.tf[i * Nfp + fp], s);
+    if (ref.slot[a] >= 0) {
+      if (d == 3) {
+        // the faces node a lies on: coordinate r at 0 (face 2r) or p (face 2r + 1)
+        const int np1 = dm.np1, Nfn1 = np1 * np1;
+        const int c3[3] = {a % np1, (a / np1) % np1, a / (np1 * np1)};
+        for (int f = 0; f < 6; ++f) {
+          const int r = f >> 1;
+          if (c3[r] != ((f & 1) ? np1 - 1 : 0)) continue;
+          const int tn = r == 0 ? c3[1] + np1 * c3[2] : (r == 1 ? c3[0] + np1 * c3[2] : c3[0] + np1 * c3[1]);
+          s += w.xf[((size_t)i * 6 + f) * Nfn1 + tn];
+        }
+      } else {
+        for (int fp = 0; fp < Nfp; ++fp) s = fma(ref.PhiF[(size_t)fp * Np + a], w.tf[i * Nfp + fp], s);
+      }
+    }
     w.ou[idx] = s;
   }
   for (int idx = tid; idx < m * Nb; idx += RF_THREADS) {
@@ -308,9 +377,34 @@ __device__ void element_apply(const Dims& dm, const Phys& ph, const RefTables& r
   __syncthreads();
 }
 
+// Row kb + lane of the panel's 32 x 32 diagonal block (columns kb .. kb + 31) into
+// registers, zero outside the panel (rows and columns >= nb).  Rows start on 16-byte
+// boundaries (ld and kb multiples of 4, element offsets multiples of 4 floats); the
+// vector loads are used when the 32 columns lie inside the row (kb + 32 <= ld).
+__device__ __forceinline__ void panel_row(const float* __restrict__ A, int ld, int kb, int nb, int lane,
+                                          float (&r)[RF_NB]) {
+  const float* src = A + (int64_t)(kb + lane) * ld + kb;
+  if (kb + RF_NB <= ld) {
+#pragma unroll
+    for (int q = 0; q < RF_NB / 4; ++q) {
+      const float4 v = lane < nb ? reinterpret_cast<const float4*>(src)[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+      r[4 * q + 0] = 4 * q + 0 < nb ? v.x : 0.f;
+      r[4 * q + 1] = 4 * q + 1 < nb ? v.y : 0.f;
+      r[4 * q + 2] = 4 * q + 2 < nb ? v.z : 0.f;
+      r[4 * q + 3] = 4 * q + 3 < nb ? v.w : 0.f;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < RF_NB; ++j) r[j] = (lane < nb && j < nb) ? src[j] : 0.f;
+  }
+}
+
 // v <- A~32^-1 v with the FP32 factors (panel order, pivots as applied).  A correction
 // only needs FP32 accuracy (the residual it corrects is FP64), so the solve runs in
-// FP32 on a scaled copy of v held in f (nu floats, any free shared buffer).
+// FP32 on a scaled copy of v held in f (nu floats, any free shared buffer).  The
+// sequential steps inside a panel run in warp 0 on registers: each lane holds its row
+// of the diagonal block and its entry of f, the pivot entries are broadcast by
+// shuffles, so no step waits on a memory load.
 __device__ void solve32(const Dims& dm, const float* __restrict__ A, int ld, const int* __restrict__ piv, double* v,
                         float* f, double* red) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = RF_THREADS / 32;
@@ -323,25 +417,42 @@ __device__ void solve32(const Dims& dm, const float* __restrict__ A, int ld, con
   __syncthreads();
   for (int kb = 0; kb < nu; kb += RF_NB) {
     const int nb = min(RF_NB, nu - kb);
-    if (tid == 0)
-      for (int j = 0; j < nb; ++j) {
-        int p = piv[kb + j];
-        if (p != kb + j) { float t = f[kb + j]; f[kb + j] = f[p]; f[p] = t; }
-      }
-    __syncthreads();
     if (warp == 0) {
+      // the panel's row interchanges, in order (one lane; the pivots come by shuffle)
+      const int pl = lane < nb ? piv[kb + lane] : 0;
+      float Lr[RF_NB];
+      panel_row(A, ld, kb, nb, lane, Lr);
       for (int j = 0; j < nb; ++j) {
-        float vj = f[kb + j];
-        __syncwarp();
-        if (lane > j && lane < nb) f[kb + lane] = fmaf(-A[(int64_t)(kb + lane) * ld + kb + j], vj, f[kb + lane]);
-        __syncwarp();
+        const int p = __shfl_sync(0xffffffffu, pl, j);
+        if (lane == 0 && p != kb + j) { float t = f[kb + j]; f[kb + j] = f[p]; f[p] = t; }
       }
+      __syncwarp();
+      // unit lower triangular block: f_lane -= L[lane][j] f_j for j < lane
+      float fv = lane < nb ? f[kb + lane] : 0.f;
+#pragma unroll
+      for (int j = 0; j < RF_NB; ++j) {
+        const float vj = __shfl_sync(0xffffffffu, fv, j);
+        if (lane > j) fv = fmaf(-Lr[j], vj, fv);
+      }
+      if (lane < nb) f[kb + lane] = fv;
     }
     __syncthreads();
     for (int r = kb + nb + tid; r < nu; r += RF_THREADS) {
       const float* row = A + (int64_t)r * ld + kb;
       float s = f[r];
-      for (int j = 0; j < nb; ++j) s = fmaf(-row[j], f[kb + j], s);
+      if (nb == RF_NB) {
+        const float4* row4 = reinterpret_cast<const float4*>(row);
+#pragma unroll
+        for (int q = 0; q < RF_NB / 4; ++q) {
+          const float4 a = row4[q];
+          s = fmaf(-a.x, f[kb + 4 * q + 0], s);
+          s = fmaf(-a.y, f[kb + 4 * q + 1], s);
+          s = fmaf(-a.z, f[kb + 4 * q + 2], s);
+          s = fmaf(-a.w, f[kb + 4 * q + 3], s);
+        }
+      } else {
+        for (int j = 0; j < nb; ++j) s = fmaf(-row[j], f[kb + j], s);
+      }
       f[r] = s;
     }
     __syncthreads();
@@ -360,13 +471,19 @@ __device__ void solve32(const Dims& dm, const float* __restrict__ A, int ld, con
     }
     __syncthreads();
     if (warp == 0) {
-      for (int j = nb - 1; j >= 0; --j) {
-        if (lane == 0) f[kb + j] /= A[(int64_t)(kb + j) * ld + kb + j];
-        __syncwarp();
-        float vj = f[kb + j];
-        if (lane < j) f[kb + lane] = fmaf(-A[(int64_t)(kb + lane) * ld + kb + j], vj, f[kb + lane]);
-        __syncwarp();
+      // upper triangular block: f_j /= U[j][j], then f_lane -= U[lane][j] f_j for lane < j
+      float Ur[RF_NB];
+      panel_row(A, ld, kb, nb, lane, Ur);
+      float fv = lane < nb ? f[kb + lane] : 0.f;
+#pragma unroll
+      for (int j = RF_NB - 1; j >= 0; --j) {
+        if (j < nb) {
+          if (lane == j) fv /= Ur[j];
+          const float vj = __shfl_sync(0xffffffffu, fv, j);
+          if (lane < j) fv = fmaf(-Ur[j], vj, fv);
+        }
       }
+      if (lane < nb) f[kb + lane] = fv;
     }
     __syncthreads();
   }

@@ -404,9 +404,9 @@ class MixedOrderMesh(Mesh):
         self.orders_key = "|orders" + ",".join(f"{p}:{c}" for p, c in enumerate(counts) if c) + f"|E{self.E}"
 
 
-def mesh_from_workload(wl, precision=0, stream=None):
+def mesh_from_workload(wl, precision=0, stream=None, quad_extra=2):
     """Convenience: a Mesh for a workloads.Workload."""
     p = wl.params
     return Mesh(wl.mesh.node_xyz, wl.mesh.elem_trace, wl.mesh.n_trace, wl.mesh.p, gamma=p["gamma"],
                 Pr=p["Pr"], Re=p["Re"], Minf=p["Minf"], alpha=p["alpha"], precision=precision, stream=stream,
-                stab=p.get("stab", 0))
+                stab=p.get("stab", 0), quad_extra=quad_extra)

@@ -284,6 +284,34 @@ def test_low_precision_schur_parity(name, precision):
     assert rel_err(host(dq_d), dq_o) <= TOL_MIXED
 
 
+@pytest.mark.parametrize("quad_extra", [1, 3])
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name", ["p2-curved", "p3-2cube", "2d-p3-steady"])
+def test_quad_extra_parity(name, precision, quad_extra):
+    """Fewer (p + 1) and more (p + 3) Gauss points per direction than the default: the
+    work buffers of the point, assembly and refinement kernels change shape."""
+    from paper_1605_01020_gb300 import iedg
+    wl = _case(name)
+    st = wl.state
+    pb = problem(wl.mesh, wl.params, quad_extra=quad_extra)
+    E = wl.mesh.n_elem
+    Ke, Re = zip(*[pb.condense_qelim(e, st.u, st.q, st.uhat, st.u_ref) for e in range(E)])
+    row_ptr, col, vals, R = oiedg.assemble(wl.mesh.elem_trace, wl.mesh.n_trace, np.array(Ke), np.array(Re))
+    mesh = iedg.mesh_from_workload(wl, precision=precision, quad_extra=quad_extra)
+    K_d, R_d = mesh.assemble_condensed(dev(st.u), dev(st.q), dev(st.uhat), u_ref=dev(st.u_ref))
+    du_d, dq_d = mesh.back_substitute(dev(st.duhat))
+    du_o = np.zeros_like(st.u)
+    dq_o = np.zeros_like(st.q)
+    for e in range(E):
+        du_o[e], dq_o[e] = pb.back_substitute_qelim(e, st.u, st.q, st.uhat, st.duhat, st.u_ref)
+    tk, tr = (TOL, TOL) if precision == 0 else (TOL_MIXED_K, TOL_MIXED)
+    assert (mesh.element_status() == 0).all()
+    assert bsr_row_err(row_ptr, host(K_d), vals, range(wl.mesh.n_trace)) <= tk
+    assert rel_err(host(R_d), R, floor=np.abs(np.array(Re)).max()) <= tr
+    assert rel_err(host(du_d), du_o) <= tr
+    assert rel_err(host(dq_d), dq_o) <= tr
+
+
 @pytest.mark.parametrize("cfg,precision", [(2, 1), (3, 1), (3, 2), (3, 3)])
 def test_mixed_full_size_sampled(cfg, precision):
     """The 16^3 p=3 workloads (config 3: stretched and sheared, aspect up to 50) in the

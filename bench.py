@@ -641,6 +641,27 @@ def run_extras(args, dev):
     out["dirk33_step"] = {"ms_per_step": statistics.median(times[1:]), "newton_iterations": stepper.newton_iters,
                           "workload": "2D p=2 8x8, dt = 0.005, Newton to 1e-10, GMRES + block Jacobi"}
     mesh.close()
+    # the same on the 3D Taylor-Green vortex (config 2's recipe on 8^3 cells, p = 3)
+    wl = W.config(2, N=8)
+    st = wl.state
+    mesh = iedg.mesh_from_workload(wl)
+    u = torch.as_tensor(st.u, dtype=f64, device=dev)
+    uh = torch.as_tensor(st.uhat, dtype=f64, device=dev)
+    q = mesh.eval_residual(u, uh, q=None)["q"]
+    stepper = timestep.Stepper(mesh, 0.005, newton_tol=1e-10)
+    state = (u, q, uh)
+    times = []
+    for n in range(4):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        state = stepper.step(*state, use_mr=True)[:3]
+        torch.cuda.synchronize()
+        times.append(1e3 * (time.perf_counter() - t0))
+    out["dirk33_step_tgv3d"] = {"ms_per_step": statistics.median(times[1:]), "newton_iterations": stepper.newton_iters,
+                                "elements": mesh.E,
+                                "workload": "3D Taylor-Green p=3 8^3 (config 2 field, Re 2.5e5), dt = 0.005, "
+                                            "Newton to 1e-10, GMRES + block Jacobi"}
+    mesh.close()
     return out
 
 

@@ -16,9 +16,17 @@ pytestmark = pytest.mark.gpu
 DT = 0.005
 
 
-def _setup():
-    wl = W.config(1, N=4)
-    st = W.make_state(wl.mesh, W.fourier_perturbed_field(2, 0.2, 41, amp=0.05), 42, noise=0.005)
+def _setup(d=2):
+    """2D: config 1's recipe on 4 x 4 cells.  3D: the Taylor-Green vortex (config 2's
+    field and parameters) on 2^3 cells at p = 2."""
+    if d == 2:
+        wl = W.config(1, N=4)
+        st = W.make_state(wl.mesh, W.fourier_perturbed_field(2, 0.2, 41, amp=0.05), 42, noise=0.005)
+    else:
+        wl2 = W.config(2, N=2)
+        mesh = W.structured_mesh(3, 2, 2)
+        st = W.make_state(mesh, W.taylor_green_field(0.2), 43, noise=0.005)
+        wl = W.Workload("3D TGV p=2 2^3", mesh, st, wl2.params)
     assert abs(wl.params["alpha"] * timestep.GAMMA_DIRK * DT - 1) < 1e-12
     return wl, st
 
@@ -47,9 +55,10 @@ def _oracle_stage(pb, mesh, u, q, uh, u_ref, tol):
     raise AssertionError("oracle Newton did not converge")
 
 
-def test_dirk_step_matches_oracle_and_conserves():
+@pytest.mark.parametrize("d", [2, 3])
+def test_dirk_step_matches_oracle_and_conserves(d):
     from paper_1605_01020_gb300 import iedg
-    wl, st = _setup()
+    wl, st = _setup(d)
     mesh = iedg.mesh_from_workload(wl)
     u = dev(st.u)
     uh = dev(st.uhat)
@@ -74,7 +83,7 @@ def test_dirk_step_matches_oracle_and_conserves():
     assert rel_err(host(uh1), uho) <= 1e-9
     assert rel_err(host(q1), qo) <= 1e-8
     # discrete conservation: sum_e sum_a (sum_g w_g phi_a(g)) u_a is the same before and after
-    ref = ref_element(2, wl.mesh.p)
+    ref = ref_element(d, wl.mesh.p)
     geo = geometry.Geometry(ref, wl.mesh.node_xyz)
     mvec = np.einsum("eg,ga->ea", geo.w, ref.phi)
     tot0 = np.einsum("ea,eai->i", mvec, st.u)

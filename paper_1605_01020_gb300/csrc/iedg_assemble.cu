@@ -640,12 +640,44 @@ __device__ void schur_ozaki(double* __restrict__ A, int ld, int n, int nu, const
 // pivot rows are written back for the refinement solves.
 constexpr int L32_NB = 32;
 constexpr int L32_UCW = 128;      // trailing-update column chunk
+constexpr int L32_MAX_NU = 640;   // u-unknowns of the largest element (5 x 125 at p = 4)
 constexpr int L32_TM = 4, L32_TN = 8;
 
 
+// The 4 x 8 tile of A at rows rr0.., columns cc + tc * 8.. (zero outside the update).
+__device__ __forceinline__ void lu32_load_tile(const float* __restrict__ A, int ld, int rr0, int r_hi, int cc, int tc,
+                                               int cw, bool cvec, float (&t)[L32_TM][L32_TN]) {
+#pragma unroll
+  for (int a = 0; a < L32_TM; ++a) {
+    const int rr = rr0 + a;
+    if (cvec && rr < r_hi) {
+      const float4* src = reinterpret_cast<const float4*>(A + (int64_t)rr * ld + cc + tc * L32_TN);
+      const float4 v0 = src[0], v1 = src[1];
+      t[a][0] = v0.x; t[a][1] = v0.y; t[a][2] = v0.z; t[a][3] = v0.w;
+      t[a][4] = v1.x; t[a][5] = v1.y; t[a][6] = v1.z; t[a][7] = v1.w;
+    } else {
+#pragma unroll
+      for (int b = 0; b < L32_TN; ++b) {
+        const int c = tc * L32_TN + b;
+        t[a][b] = (rr < r_hi && c < cw) ? A[(int64_t)rr * ld + cc + c] : 0.f;
+      }
+    }
+  }
+}
+
+// Ask L2 for the lines of the 4 x 8 tile at rows rr0.. (no registers held).
+__device__ __forceinline__ void lu32_prefetch_tile(const float* __restrict__ A, int ld, int rr0, int r_hi, int cc,
+                                                   int tc) {
+#pragma unroll
+  for (int a = 0; a < L32_TM; ++a)
+    if (rr0 + a < r_hi)
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(A + (int64_t)(rr0 + a) * ld + cc + tc * L32_TN));
+}
+
 // A[r][c] -= sum_j L[r][j] U[j][c] over rows [r_lo, r_hi), cols [c_lo, c_hi): L from the
 // column-major panel P (row r at P[j n + r - kb]), U = rows kb..kb+nb of A.  4 x 8
-// register tiles, U staged in Uc by 128-column chunks.  Columns past c_hi are written
+// register tiles, U staged in Uc by 128-column chunks; the next row block's tile is
+// requested from L2 while the current one is updated.  Columns past c_hi are written
 // back unchanged only when they are padding of the row (c_hi = n + 1).
 __device__ __forceinline__ void lu32_update_rect(float* __restrict__ A, int ld, int n, const float* __restrict__ P,
                                                  float* __restrict__ Uc, int kb, int nb, int r_lo, int r_hi,
@@ -654,6 +686,7 @@ __device__ __forceinline__ void lu32_update_rect(float* __restrict__ A, int ld, 
   const bool vec = ((nb & 3) == 0) && ((n & 3) == 0);
   const int tc = tid % (L32_UCW / L32_TN), tr = tid / (L32_UCW / L32_TN);   // 16 x 16
   const int vlim = (c_hi == n + 1) ? ld : c_hi;     // last column a vector access may touch
+  constexpr int RB = 16 * L32_TM;                   // rows per block of the CTA
   for (int cc = c_lo; cc < c_hi; cc += L32_UCW) {
     const int cw = min(L32_UCW, c_hi - cc);
     for (int idx = tid; idx < L32_NB * L32_UCW; idx += LU_THREADS) {
@@ -662,26 +695,13 @@ __device__ __forceinline__ void lu32_update_rect(float* __restrict__ A, int ld, 
     }
     __syncthreads();
     const bool cvec = ((cc & 3) == 0) && (cc + tc * L32_TN + L32_TN <= vlim);
-    for (int rb = r_lo; rb < r_hi; rb += 16 * L32_TM) {
+    for (int rb = r_lo; rb < r_hi; rb += RB) {
       const int rr0 = rb + tr * L32_TM;
       float acc[L32_TM][L32_TN];
-#pragma unroll
-      for (int a = 0; a < L32_TM; ++a) {
-        const int rr = rr0 + a;
-        if (cvec && rr < r_hi) {
-          const float4* src = reinterpret_cast<const float4*>(A + (int64_t)rr * ld + cc + tc * L32_TN);
-          float4 v0 = src[0], v1 = src[1];
-          acc[a][0] = v0.x; acc[a][1] = v0.y; acc[a][2] = v0.z; acc[a][3] = v0.w;
-          acc[a][4] = v1.x; acc[a][5] = v1.y; acc[a][6] = v1.z; acc[a][7] = v1.w;
-        } else {
-#pragma unroll
-          for (int b = 0; b < L32_TN; ++b) {
-            int c = tc * L32_TN + b;
-            acc[a][b] = (rr < r_hi && c < cw) ? A[(int64_t)rr * ld + cc + c] : 0.f;
-          }
-        }
-      }
+      lu32_load_tile(A, ld, rr0, r_hi, cc, tc, cw, cvec, acc);
+      if (rb + RB < r_hi) lu32_prefetch_tile(A, ld, rr0 + RB, r_hi, cc, tc);
       if (rr0 < r_hi) {
+#pragma unroll 4
         for (int j = 0; j < nb; ++j) {
           float lv[L32_TM], uv[L32_TN];
           const float* lp = P + j * n + (rr0 - kb);
@@ -869,6 +889,7 @@ __device__ __forceinline__ void lu32_element(const LuElem& el, float* __restrict
   float* P = reinterpret_cast<float*>(smraw);          // [NB][n] column-major panel
   float* Uc = P + (size_t)L32_NB * el.n;                // [NB][UCW]
   __shared__ int piv[L32_NB];
+  __shared__ int perm[L32_MAX_NU];   // net row permutation of the current panel's interchanges
   __shared__ float rv[LU_THREADS / 32];
   __shared__ int ri[LU_THREADS / 32];
   __shared__ int sing;
@@ -882,6 +903,7 @@ __device__ __forceinline__ void lu32_element(const LuElem& el, float* __restrict
       int r = idx / L32_NB, j = idx % L32_NB;
       P[j * n + r] = j < nb ? A[(int64_t)(kb + r) * ld + kb + j] : 0.f;
     }
+    for (int r = tid; r < prow; r += LU_THREADS) perm[r] = r;
     __syncthreads();
     for (int j = 0; j < nb; ++j) {
       const float* Pj = P + j * n;
@@ -899,17 +921,18 @@ __device__ __forceinline__ void lu32_element(const LuElem& el, float* __restrict
       }
       if (lane == 0) { rv[warp] = best; ri[warp] = bi; }
       __syncthreads();
+      // every thread combines the warps' candidates (same order, same result)
+      float bv = rv[0];
+      int pr = ri[0];
+      for (int w = 1; w < LU_THREADS / 32; ++w)
+        if (rv[w] > bv || (rv[w] == bv && ri[w] < pr)) { bv = rv[w]; pr = ri[w]; }
+      if (!(bv > 0.f)) pr = j;
       if (tid == 0) {
-        float bv = rv[0];
-        int b = ri[0];
-        for (int w = 1; w < LU_THREADS / 32; ++w)
-          if (rv[w] > bv || (rv[w] == bv && ri[w] < b)) { bv = rv[w]; b = ri[w]; }
-        if (!(bv > 0.f)) { sing = 1; b = j; }
-        piv[j] = b;
-        pivots[el.poff + kb + j] = kb + b;
+        if (!(bv > 0.f)) sing = 1;
+        piv[j] = pr;
+        pivots[el.poff + kb + j] = kb + pr;
+        if (pr != j) { const int t = perm[j]; perm[j] = perm[pr]; perm[pr] = t; }
       }
-      __syncthreads();
-      const int pr = piv[j];
       if (pr != j && tid < L32_NB) {
         float t = P[tid * n + j];
         P[tid * n + j] = P[tid * n + pr];
@@ -930,19 +953,33 @@ __device__ __forceinline__ void lu32_element(const LuElem& el, float* __restrict
       int r = idx / nb, j = idx % nb;
       A[(int64_t)(kb + r) * ld + kb + j] = P[j * n + r];
     }
-    // trailing columns: row interchanges, then U12 = L11^-1 A12
+    // trailing columns: row interchanges, then U12 = L11^-1 A12.  The panel's
+    // interchanges, applied in order, leave row r holding the original row perm[r]; the
+    // rows below the panel that change are among the pivot rows piv[j] >= nb, and they
+    // receive original rows above nb.  Each column gathers its new top rows first
+    // (independent loads), then moves the displaced rows, then stores the top rows.
     for (int c = kb + nb + tid; c < ncol; c += LU_THREADS) {
       float x[L32_NB];
 #pragma unroll
       for (int j = 0; j < L32_NB; ++j) {
         if (j >= nb) break;
-        int pr = piv[j];
-        float* a0 = A + (int64_t)(kb + j) * ld + c;
-        if (pr != j) {
-          float* a1 = A + (int64_t)(kb + pr) * ld + c;
-          float t = *a0; *a0 = *a1; *a1 = t;
+        x[j] = A[(int64_t)(kb + perm[j]) * ld + c];
+      }
+      // displaced rows take original top rows (unchanged until the stores below), in
+      // groups of 8 loads before their stores
+#pragma unroll
+      for (int j0 = 0; j0 < L32_NB; j0 += 8) {
+        float y[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int r = j0 + j < nb ? piv[j0 + j] : 0;
+          y[j] = (j0 + j < nb && r >= nb && perm[r] != r) ? A[(int64_t)(kb + perm[r]) * ld + c] : 0.f;
         }
-        x[j] = *a0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int r = j0 + j < nb ? piv[j0 + j] : 0;
+          if (j0 + j < nb && r >= nb && perm[r] != r) A[(int64_t)(kb + r) * ld + c] = y[j];
+        }
       }
 #pragma unroll
       for (int j = 0; j < L32_NB; ++j) {
@@ -1270,6 +1307,7 @@ cudaError_t launch_lu(iedg_mesh* M, cudaStream_t st) {
     if (M->sched.lu_panel == 32 && lu64_smem(M->dm, 32) <= 227 * 1024) return lu_t<double, 32>(M, M->S, nullptr, st);
     return lu_t<double, 16>(M, M->S, nullptr, st);
   }
+  if (M->dm.nu > L32_MAX_NU) return cudaErrorInvalidValue;   // orders above 4 are rejected at creation
   if (M->schur_in == kSchurTf32) return lu32_tc<kSchurTf32>(M, st);
   if (M->schur_in == kSchurBf16) return lu32_tc<kSchurBf16>(M, st);
   if (M->sched.lu_tensor) return lu32_tc<kSchurFp32>(M, st);

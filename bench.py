@@ -32,6 +32,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "elements/s condensed (3D NS, p=3) FP64 vs mixed+refine; % tensor roofline"
 DFMA_PER_CLK_PER_SM = 2          # GB300: 1.25 TFLOP/s FP64 at 2070 MHz over 152 SMs
+FFMA_PER_CLK_PER_SM = 128        # FP32 FMA lanes per SM per clock
 
 
 def a6_flops(nu, nt):
@@ -465,8 +466,22 @@ def run_mixed(args, wl, mesh64, dev, step_outputs, inputs, flush, barrier, preci
     tot = sum(v[1] for v in prof.values())
     err = lambda a, b: float((a - b).abs().max() / b.abs().max().clamp_min(1e-300))
     status = mesh.element_status()
+    # the FP32 partial LU against the FP32 FMA rate (its updates and panels run on FFMA;
+    # the tensor-core forms put only the deferred Schur GEMM on tcgen05)
+    roof = None
+    if "lu_schur" in prof:
+        launches, kms = prof["lu_schur"]
+        props = torch.cuda.get_device_properties(dev)
+        peak = props.multi_processor_count * FFMA_PER_CLK_PER_SM * 2 * 2070.0e6
+        fl = a6_flops(m * Np, m * mesh.Nb) * E
+        ach = fl / (kms / launches / 1e3)
+        roof = {"kernel": "lu_schur", "bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12,
+                "unit": "TFLOP/s", "frac": ach / peak, "algorithmic_flops_per_launch": fl,
+                "peak_source": f"FP32 FFMA: {props.multi_processor_count} SMs x {FFMA_PER_CLK_PER_SM} FMA/clk x 2 "
+                               f"x 2070 MHz (derived)",
+                "share_of_step": kms / tot if tot else None}
     out = {"ms_total": e0.elapsed_time(e1), "precision": MIXED_FORMS[precision],
-           "schedule": schedule, "autotune_ms": timings,
+           "schedule": schedule, "autotune_ms": timings, "roofline": roof,
            "err_vs_fp64": {"K": err(K, K64), "R": err(R, R64), "du": err(du, du64), "dq": err(dq, dq64)},
            "element_status_nonzero": int((status != 0).sum()),
            "gpu_launches": sum(v[0] for v in prof.values()),

@@ -267,6 +267,7 @@ k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, AsmTab<T> tb, T* __restri
 // the refinement solves.
 constexpr int LU_THREADS = 256;
 constexpr int UCW = 64;     // trailing-update column chunk
+constexpr int LU_MAX_NU = 640;   // u-unknowns of the largest element (5 x 125 at p = 4)
 
 // Tensor-core state of a CTA (deferred Schur complement forms of the LU).
 struct TcState {
@@ -344,6 +345,7 @@ __device__ __forceinline__ void lu_element(const LuElem& el, T* __restrict__ S, 
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
   __shared__ int piv[NB];
+  __shared__ int perm[LU_MAX_NU];   // net row permutation of the current panel's interchanges
   __shared__ T rv[LU_THREADS / 32];
   __shared__ int ri[LU_THREADS / 32];
   __shared__ int sing;
@@ -359,6 +361,7 @@ __device__ __forceinline__ void lu_element(const LuElem& el, T* __restrict__ S, 
       int r = idx / NB, j = idx % NB;
       P[idx] = j < nb ? A[(int64_t)(kb + r) * ld + kb + j] : (T)0;
     }
+    for (int r = tid; r < prow; r += LU_THREADS) perm[r] = r;
     __syncthreads();
     for (int j = 0; j < nb; ++j) {
       T best = -1;
@@ -375,17 +378,18 @@ __device__ __forceinline__ void lu_element(const LuElem& el, T* __restrict__ S, 
       }
       if (lane == 0) { rv[warp] = best; ri[warp] = bi; }
       __syncthreads();
+      // every thread combines the warps' candidates (same order, same result)
+      T bv = rv[0];
+      int pr = ri[0];
+      for (int w = 1; w < LU_THREADS / 32; ++w)
+        if (rv[w] > bv || (rv[w] == bv && ri[w] < pr)) { bv = rv[w]; pr = ri[w]; }
+      if (!(bv > 0)) pr = j;
       if (tid == 0) {
-        T bv = rv[0];
-        int b = ri[0];
-        for (int w = 1; w < LU_THREADS / 32; ++w)
-          if (rv[w] > bv || (rv[w] == bv && ri[w] < b)) { bv = rv[w]; b = ri[w]; }
-        if (!(bv > 0)) { sing = 1; b = j; }
-        piv[j] = b;
-        if (pivots) pivots[el.poff + kb + j] = kb + b;
+        if (!(bv > 0)) sing = 1;
+        piv[j] = pr;
+        if (pivots) pivots[el.poff + kb + j] = kb + pr;
+        if (pr != j) { const int t = perm[j]; perm[j] = perm[pr]; perm[pr] = t; }
       }
-      __syncthreads();
-      const int pr = piv[j];
       if (pr != j && tid < NB) {
         T t = P[j * NB + tid];
         P[j * NB + tid] = P[pr * NB + tid];
@@ -407,17 +411,31 @@ __device__ __forceinline__ void lu_element(const LuElem& el, T* __restrict__ S, 
       int r = idx / nb, j = idx % nb;
       A[(int64_t)(kb + r) * ld + kb + j] = P[r * NB + j];
     }
-    // trailing columns: row interchanges, then U12 = L11^-1 A12
+    // trailing columns: row interchanges, then U12 = L11^-1 A12.  The panel's
+    // interchanges leave row r holding the original row perm[r]; the rows below the
+    // panel that change are pivot rows piv[j] >= nb and receive original rows above nb.
+    // Each column gathers its new top rows (independent loads), moves the displaced
+    // rows in groups of 8, then stores the top rows.
     for (int c = kb + nb + tid; c < ncol; c += LU_THREADS) {
       T x[NB];
-      for (int j = 0; j < nb; ++j) {
-        int pr = piv[j];
-        T* a0 = A + (int64_t)(kb + j) * ld + c;
-        if (pr != j) {
-          T* a1 = A + (int64_t)(kb + pr) * ld + c;
-          T t = *a0; *a0 = *a1; *a1 = t;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        if (j >= nb) break;
+        x[j] = A[(int64_t)(kb + perm[j]) * ld + c];
+      }
+#pragma unroll
+      for (int j0 = 0; j0 < NB; j0 += 8) {
+        T y[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int r = j0 + j < nb ? piv[j0 + j] : 0;
+          y[j] = (j0 + j < nb && r >= nb && perm[r] != r) ? A[(int64_t)(kb + perm[r]) * ld + c] : (T)0;
         }
-        x[j] = *a0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int r = j0 + j < nb ? piv[j0 + j] : 0;
+          if (j0 + j < nb && r >= nb && perm[r] != r) A[(int64_t)(kb + r) * ld + c] = y[j];
+        }
       }
       for (int j = 0; j < nb; ++j) {
         T s = x[j];
@@ -640,7 +658,6 @@ __device__ void schur_ozaki(double* __restrict__ A, int ld, int n, int nu, const
 // pivot rows are written back for the refinement solves.
 constexpr int L32_NB = 32;
 constexpr int L32_UCW = 128;      // trailing-update column chunk
-constexpr int L32_MAX_NU = 640;   // u-unknowns of the largest element (5 x 125 at p = 4)
 constexpr int L32_TM = 4, L32_TN = 8;
 
 
@@ -889,7 +906,7 @@ __device__ __forceinline__ void lu32_element(const LuElem& el, float* __restrict
   float* P = reinterpret_cast<float*>(smraw);          // [NB][n] column-major panel
   float* Uc = P + (size_t)L32_NB * el.n;                // [NB][UCW]
   __shared__ int piv[L32_NB];
-  __shared__ int perm[L32_MAX_NU];   // net row permutation of the current panel's interchanges
+  __shared__ int perm[LU_MAX_NU];   // net row permutation of the current panel's interchanges
   __shared__ float rv[LU_THREADS / 32];
   __shared__ int ri[LU_THREADS / 32];
   __shared__ int sing;
@@ -1302,12 +1319,12 @@ static cudaError_t lu32_tc(iedg_mesh* M, cudaStream_t st) {
 }
 
 cudaError_t launch_lu(iedg_mesh* M, cudaStream_t st) {
+  if (M->dm.nu > LU_MAX_NU) return cudaErrorInvalidValue;   // orders above 4 are rejected at creation
   if (M->precision == 0 && M->sched.lu_tensor) return lu64_oz(M, st);
   if (M->precision == 0) {
     if (M->sched.lu_panel == 32 && lu64_smem(M->dm, 32) <= 227 * 1024) return lu_t<double, 32>(M, M->S, nullptr, st);
     return lu_t<double, 16>(M, M->S, nullptr, st);
   }
-  if (M->dm.nu > L32_MAX_NU) return cudaErrorInvalidValue;   // orders above 4 are rejected at creation
   if (M->schur_in == kSchurTf32) return lu32_tc<kSchurTf32>(M, st);
   if (M->schur_in == kSchurBf16) return lu32_tc<kSchurBf16>(M, st);
   if (M->sched.lu_tensor) return lu32_tc<kSchurFp32>(M, st);

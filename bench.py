@@ -80,7 +80,7 @@ def assemble_actual_flops(d, p, nq1):
 # DRAM bytes per element of the FP64 LU / Schur kernel, from one ncu capture of
 # k_lu on the 8^3 p=3 case (512 elements): 35.49 GB per launch -> 6.93e7 B/element
 # (profiles/lu_schur_fp64_p3.md).  Valid for the kernel version profiled there.
-LU_FP64_DRAM_BYTES_PER_ELEMENT = 35.485378e9 / 512
+LU_FP64_DRAM_BYTES_PER_ELEMENT = (18545116160 + 16900438784) / 512
 
 
 def workload_name(wl):

@@ -339,6 +339,21 @@ __device__ __forceinline__ void lu64_update_rect(T* __restrict__ A, int ld, cons
   }
 }
 
+// |v| as a signed integer that orders like |v| (IEEE bit patterns of non-negative
+// values are monotonic), -1 for NaN so that NaN is never chosen, like a floating-point
+// comparison would; the pivot search of the FP64 LU then runs on the integer pipes
+// instead of the slow FP64 pipe.
+template <class T>
+__device__ __forceinline__ long long abs_key(T v) {
+  if constexpr (sizeof(T) == 8) {
+    const long long k = __double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFLL;
+    return k > 0x7FF0000000000000LL ? -1LL : k;
+  } else {
+    const long long k = (long long)(__float_as_int(v) & 0x7FFFFFFF);
+    return k > 0x7F800000LL ? -1LL : k;
+  }
+}
+
 template <class T, int NB>
 __device__ __forceinline__ void lu_element(const LuElem& el, T* __restrict__ S, int8_t* __restrict__ status,
                                            int* __restrict__ pivots, const int64_t e, bool defer_schur = false) {
@@ -346,7 +361,7 @@ __device__ __forceinline__ void lu_element(const LuElem& el, T* __restrict__ S, 
   T* sm = reinterpret_cast<T*>(smraw);
   __shared__ int piv[NB];
   __shared__ int perm[LU_MAX_NU];   // net row permutation of the current panel's interchanges
-  __shared__ T rv[LU_THREADS / 32];
+  __shared__ long long rv[LU_THREADS / 32];
   __shared__ int ri[LU_THREADS / 32];
   __shared__ int sing;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -364,28 +379,30 @@ __device__ __forceinline__ void lu_element(const LuElem& el, T* __restrict__ S, 
     for (int r = tid; r < prow; r += LU_THREADS) perm[r] = r;
     __syncthreads();
     for (int j = 0; j < nb; ++j) {
-      T best = -1;
+      long long best = -1;                  // largest |a| as an ordered integer key
       int bi = j;
       for (int r = j + tid; r < prow; r += LU_THREADS) {
-        T v = fabs(P[r * NB + j]);
+        const long long v = abs_key(P[r * NB + j]);
         if (v > best) { best = v; bi = r; }
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        T ov = __shfl_xor_sync(0xffffffffu, best, o);
-        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        const long long ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
       }
       if (lane == 0) { rv[warp] = best; ri[warp] = bi; }
       __syncthreads();
       // every thread combines the warps' candidates (same order, same result)
-      T bv = rv[0];
+      long long bk = rv[0];
       int pr = ri[0];
-      for (int w = 1; w < LU_THREADS / 32; ++w)
-        if (rv[w] > bv || (rv[w] == bv && ri[w] < pr)) { bv = rv[w]; pr = ri[w]; }
-      if (!(bv > 0)) pr = j;
+      for (int w = 1; w < LU_THREADS / 32; ++w) {
+        const long long k = rv[w];
+        if (k > bk || (k == bk && ri[w] < pr)) { bk = k; pr = ri[w]; }
+      }
+      if (bk <= 0) pr = j;                  // no nonzero candidate: singular
       if (tid == 0) {
-        if (!(bv > 0)) sing = 1;
+        if (bk <= 0) sing = 1;
         piv[j] = pr;
         if (pivots) pivots[el.poff + kb + j] = kb + pr;
         if (pr != j) { const int t = perm[j]; perm[j] = perm[pr]; perm[pr] = t; }
@@ -717,7 +734,23 @@ __device__ __forceinline__ void lu32_update_rect(float* __restrict__ A, int ld, 
       float acc[L32_TM][L32_TN];
       lu32_load_tile(A, ld, rr0, r_hi, cc, tc, cw, cvec, acc);
       if (rb + RB < r_hi) lu32_prefetch_tile(A, ld, rr0 + RB, r_hi, cc, tc);
-      if (rr0 < r_hi) {
+      if (nb == L32_NB && vec && rr0 + L32_TM <= r_hi) {
+        // full panel, whole tile: fixed trip count and no per-step bounds tests
+        const float* lp = P + (rr0 - kb);
+        const float* up = Uc + tc * L32_TN;
+#pragma unroll 2
+        for (int j = 0; j < L32_NB; ++j) {
+          const float4 l0 = *reinterpret_cast<const float4*>(lp + j * n);
+          const float4 u0 = *reinterpret_cast<const float4*>(up + j * L32_UCW);
+          const float4 u1 = *reinterpret_cast<const float4*>(up + j * L32_UCW + 4);
+          const float lv[L32_TM] = {l0.x, l0.y, l0.z, l0.w};
+          const float uv[L32_TN] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+#pragma unroll
+          for (int a = 0; a < L32_TM; ++a)
+#pragma unroll
+            for (int b = 0; b < L32_TN; ++b) acc[a][b] = fmaf(-lv[a], uv[b], acc[a][b]);
+        }
+      } else if (rr0 < r_hi) {
 #pragma unroll 4
         for (int j = 0; j < nb; ++j) {
           float lv[L32_TM], uv[L32_TN];

@@ -10,7 +10,7 @@ mu = mu_t e_i.  With w = W_g detJ at volume points, wf = W_f |n dS| at face poin
                + sum_faces sum_gf wf fhat_i phi_a - sum_g w s_i phi_a         (IEDG b)
   R_fl[t,i]  =  sum_elements sum_faces sum_gf wf fhat_i mu_t                  (IEDG c)
 
-Readings (the design doc lists them): the DIRK stage (Sec. 2.1, last paragraph) enters
+Readings (where the paper leaves a choice open): the DIRK stage (Sec. 2.1) enters
 as alpha M (u - u_ref) with alpha = 1 / (a_ii dt); the trace space is continuous
 across interior and periodic faces, its basis on a face being the element basis
 restricted to that face (trace slot s <-> boundary node bnodes[s]); the source s

@@ -4,7 +4,7 @@ Sec. 2.1 (Eq. NS and the definitions that follow it): u = (rho, rho v_j, rho E),
 q = grad u, flux F(u, q) = inviscid - viscous, with
     tau_ij = (1/Re) (d_j v_i + d_i v_j - 2/3 delta_ij d_k v_k),
     p      = (gamma - 1) rho (E - v_k v_k / 2).
-Readings (the paper is silent or garbled there; see DESIGN.md):
+Readings (the paper is silent or garbled there):
   * T is the specific internal energy e = E - v_k v_k / 2 (c_v = 1), so the
     conductivity is gamma / (Re Pr);
   * the heat-flux term is taken with the dissipative sign: the energy flux is

@@ -2,7 +2,7 @@
 
 The IEDG spaces Q_h^k, V_h^k, M_h^k of Sec. 2.1 are polynomial spaces of degree k
 on each element; the paper defers their construction to its reference [Nguyen:093].
-Reading used here (listed in the design doc): tensor-product Q_k spaces on quads/hexes,
+Reading used here (the paper defers the construction): tensor-product Q_k spaces on quads/hexes,
 nodal Lagrange basis at the Gauss-Lobatto-Legendre ("high-order") nodes, element
 and face integrals by tensor Gauss-Legendre rules with n_q1 = k + quad_extra points
 per direction.

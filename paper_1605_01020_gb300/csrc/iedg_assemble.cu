@@ -872,7 +872,7 @@ __device__ __forceinline__ void schur_issue(uint32_t tmem, const char* stage, bo
   }
 }
 
-// Bounded wait on stage b's barrier by every thread; the verdict is made uniform.
+// Bounded wait on stage b's barrier by every thread; the outcome is made uniform.
 // (A wait that ran out leaves the phase where it was, so the drain can wait for it.)
 __device__ __forceinline__ bool schur_wait(TcState* tcs, int b) {
   const bool ok = __syncthreads_and(tc::mbar_wait(tcs->mbar + b, tcs->phase[b], 1 << 26));

@@ -59,3 +59,52 @@ def test_mixed_mesh_without_gpu_is_an_error():
     mesh = W.structured_mesh_mixed(2, 3, orders)
     with pytest.raises(Exception):
         iedg.MixedOrderMesh(mesh.node_xyz, mesh.elem_trace, mesh.n_trace, mesh.orders, mesh.face_degree)
+
+
+def test_descriptor_checks_come_before_the_device():
+    """Without a GPU, iedg_create_mesh still validates the descriptor first: unknown
+    precision or stabilisation codes are UNSUPPORTED, every valid code (FP64, mixed,
+    mixed with TF32 or BF16 Schur operands) reaches the device check and fails there
+    with IEDG_ERR_CUDA; no handle is returned either way."""
+    import ctypes
+    import numpy as np
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1605_01020_gb300 import build, iedg
+    from paper_1605_01020_gb300 import workloads as W
+    build.build()
+    lib = iedg.load()
+    wl = W.config(1, N=2)
+    X = np.ascontiguousarray(wl.mesh.node_xyz, dtype=np.float64)
+    ET = np.ascontiguousarray(wl.mesh.elem_trace, dtype=np.int64)
+
+    def create(precision, stab=0):
+        desc = iedg.MeshDesc(2, wl.mesh.p, 2, precision, X.shape[0], wl.mesh.n_trace, X.ctypes.data,
+                             ET.ctypes.data, 1.4, 0.72, 1e3, 0.2, 0.0, stab, 0)
+        h = ctypes.c_void_p()
+        rc = lib.iedg_create_mesh(ctypes.byref(desc), ctypes.c_void_p(0), ctypes.byref(h))
+        assert not h.value
+        return rc
+
+    for prec in (iedg.PRECISION_FP64, iedg.PRECISION_MIXED, iedg.PRECISION_MIXED_TF32, iedg.PRECISION_MIXED_BF16):
+        assert create(prec) == -2, prec
+    assert create(4) == -6
+    assert create(-1) == -6
+    assert create(0, stab=2) == -6
+
+
+def test_autotune_candidates_keep_the_precision():
+    """Schedules change how, never what: handles with TF32 / BF16 Schur operands are
+    offered only the tensor-core LU; FP32 handles both LU forms; FP64 handles the DFMA
+    forms plus the exact-splitting tensor-core form (persistent grid, panel 16)."""
+    from paper_1605_01020_gb300 import autotune
+    for prec in (2, 3):
+        c = autotune.candidates(prec, 3)
+        assert c and all(s["lu_tensor"] == 1 for s in c)
+    c1 = autotune.candidates(1, 3)
+    assert {s["lu_tensor"] for s in c1} == {0, 1}
+    c0 = autotune.candidates(0, 3)
+    assert {s["lu_tensor"] for s in c0} == {0, 1}
+    assert all(s["lu_persistent"] == 1 and s["lu_panel"] == 16 for s in c0 if s["lu_tensor"] == 1)
+    assert len({tuple(sorted(s.items())) for s in c0}) == len(c0)

@@ -79,9 +79,9 @@ def test_descriptor_checks_come_before_the_device():
     X = np.ascontiguousarray(wl.mesh.node_xyz, dtype=np.float64)
     ET = np.ascontiguousarray(wl.mesh.elem_trace, dtype=np.int64)
 
-    def create(precision, stab=0):
-        desc = iedg.MeshDesc(2, wl.mesh.p, 2, precision, X.shape[0], wl.mesh.n_trace, X.ctypes.data,
-                             ET.ctypes.data, 1.4, 0.72, 1e3, 0.2, 0.0, stab, 0)
+    def create(precision, stab=0, dim=2, order=wl.mesh.p, quad_extra=2, n_elem=X.shape[0], gamma=1.4):
+        desc = iedg.MeshDesc(dim, order, quad_extra, precision, n_elem, wl.mesh.n_trace, X.ctypes.data,
+                             ET.ctypes.data, gamma, 0.72, 1e3, 0.2, 0.0, stab, 0)
         h = ctypes.c_void_p()
         rc = lib.iedg_create_mesh(ctypes.byref(desc), ctypes.c_void_p(0), ctypes.byref(h))
         assert not h.value
@@ -92,6 +92,13 @@ def test_descriptor_checks_come_before_the_device():
     assert create(4) == -6
     assert create(-1) == -6
     assert create(0, stab=2) == -6
+    # degenerate and out-of-range descriptors
+    assert create(0, dim=4) == -1                 # dimension
+    assert create(0, order=4) == -6               # 2D orders 1..3
+    assert create(0, order=0) == -6
+    assert create(0, quad_extra=0) == -6
+    assert create(0, n_elem=0) == -1              # empty mesh
+    assert create(0, gamma=1.0) == -1             # physical parameters
 
 
 def test_autotune_candidates_keep_the_precision():

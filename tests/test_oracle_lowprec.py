@@ -72,3 +72,25 @@ def test_rounded_error_within_first_order_bound(element, fmt):
     err = np.abs(K - Ke)
     assert (err <= (2 * u + u * u) * bound * (1 + 1e-6) + 1e-14 * np.abs(Ke).max()).all()
     assert err.max() > 0.01 * u * bound.max()
+
+
+def test_rounded_condensation_on_a_mixed_order_element():
+    """The per-element form used for meshes of mixed orders: with no rounding it is the
+    element's condensed block, with BF16 rounding it moves within the bound."""
+    from oracle import iedg as oiedg
+    from oracle import physics
+    from oracle_helpers import ref_element
+    orders = W.mixed_orders([3, 3], 5, levels=(1, 2, 3), probs=(0.3, 0.4, 0.3))
+    mesh = W.structured_mesh_mixed(2, 3, orders)
+    st = W.make_state_mixed(mesh, W.fourier_perturbed_field(2, 0.3, 6, amp=0.05), 7, noise=0.01)
+    refs = {int(p): ref_element(2, int(p)) for p in set(mesh.orders.tolist())}
+    prm = physics.Params(gamma=1.4, Pr=0.72, Re=100.0, Minf=0.3, alpha=W.dirk_alpha())
+    pb = oiedg.MixedProblem(refs, mesh, prm)
+    for e in range(mesh.n_elem):
+        blk = pb.element_blocks(e, st.u, st.q, st.uhat)
+        Ke, _ = pb.condense_qelim(e, st.u, st.q, st.uhat)
+        K0, _ = lowprec.condense_rounded(pb.pbs[e], blk, None)
+        assert np.abs(K0 - Ke).max() <= 1e-12 * np.abs(Ke).max()
+        Kb, bound = lowprec.condense_rounded(pb.pbs[e], blk, "bf16")
+        u = lowprec.UNIT_ROUNDOFF["bf16"]
+        assert (np.abs(Kb - Ke) <= (2 * u + u * u) * bound * (1 + 1e-6) + 1e-14 * np.abs(Ke).max()).all()

@@ -154,8 +154,7 @@ class Partition:
                 self.recv_rows_dst[s].append(row_of_owned[g])
         # halo of the trace increments: owned values each peer needs, and where the
         # values this rank needs come from
-        self.halo_send = [np.array([i for i, g in enumerate(self.owned.tolist())
-                                    if g in set(self.touch[q].tolist())], dtype=np.int64) if q != rank
+        self.halo_send = [np.nonzero(np.isin(self.owned, self.touch[q]))[0].astype(np.int64) if q != rank
                           else np.zeros(0, dtype=np.int64) for q in range(world)]
         self.halo_recv = [np.array([i for i, g in enumerate(self.l2g.tolist()) if int(owner[g]) == q],
                                    dtype=np.int64) for q in range(world)]

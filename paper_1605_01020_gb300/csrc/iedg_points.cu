@@ -708,7 +708,8 @@ cudaError_t launch_points(iedg_mesh* M, const double* u, const double* q, const 
   int64_t rs = M->precision == 0 ? dm.ld : 1;
   auto kern = dm.d == 2 ? (M->ph.stab == 1 ? k_points<2, 1> : k_points<2, 0>)
                         : (M->ph.stab == 1 ? k_points<3, 1> : k_points<3, 0>);
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
   kern<<<(unsigned)M->E, threads, smem, st>>>(dm, M->ph, M->ref, M->geo, M->pj, M->etrace, u, q, qs, uhat, u_ref,
                                               jacobians, r_u, rhat, rhs, es, rs, M->tt);
   return cudaGetLastError();

@@ -47,8 +47,13 @@ extern "C" int iedg_eval_residual_static(iedg_mesh* M, const double* u, const do
   }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+  if (e != cudaSuccess) {
     M->err = std::string("iedg_eval_residual_static: cudaGetDevice: ") + cudaGetErrorString(e);
+    return IEDG_ERR_CUDA;
+  }
+  if (dev < 0 || dev >= kMaxDevices) {
+    M->err = "iedg_eval_residual_static: device index " + std::to_string(dev) + " above the " +
+             std::to_string(kMaxDevices) + " devices supported by the static entry point";
     return IEDG_ERR_CUDA;
   }
   double* scratch = nullptr;

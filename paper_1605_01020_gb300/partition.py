@@ -20,14 +20,17 @@ the blocks they exchange.
 import numpy as np
 
 
-def _row_patterns(elem_trace, elems):
-    """Sorted column sets (global trace ids) of the block rows touched by `elems`."""
-    rows = {}
-    for e in elems:
-        tr = np.unique(np.asarray(elem_trace[e], dtype=np.int64))
-        for t in tr.tolist():
-            rows.setdefault(t, set()).update(tr.tolist())
-    return {t: np.array(sorted(c), dtype=np.int64) for t, c in rows.items()}
+def _pair_keys(elem_trace, elems, n_trace):
+    """Sorted unique keys row * n_trace + col of the trace-node pairs that share one
+    of `elems` (the block pattern those elements produce, row-major)."""
+    if len(elems) == 0:
+        return np.zeros(0, dtype=np.int64)
+    if isinstance(elem_trace, list):
+        keys = [(np.asarray(elem_trace[e], dtype=np.int64)[:, None] * n_trace +
+                 np.asarray(elem_trace[e], dtype=np.int64)[None, :]).ravel() for e in elems]
+        return np.unique(np.concatenate(keys))
+    tr = np.asarray(elem_trace, dtype=np.int64)[elems]
+    return np.unique((tr[:, :, None] * n_trace + tr[:, None, :]).ravel())
 
 
 class Partition:
@@ -44,140 +47,103 @@ class Partition:
     global column ids, columns sorted), and the local pattern row_ptr_local /
     col_local the library produces for the local mesh (same rule: sorted local
     columns, one block per pair of trace nodes sharing an element).
+
+    Every pattern is held as sorted pair keys row * n_trace + col, so the block index
+    of a pair inside a CSR pattern is its position in that pattern's key array.
     """
 
     def __init__(self, elem_trace, n_trace, parts, rank, world):
         parts = np.asarray(parts, dtype=np.int64)
-        E = len(parts)
-        self.rank, self.world, self.n_trace = rank, world, int(n_trace)
+        n = self.n_trace = int(n_trace)
+        self.rank, self.world = rank, world
         self.elems = np.nonzero(parts == rank)[0]
+        by_rank = [np.nonzero(parts == r)[0] for r in range(world)]
         # owner of every trace node: the lowest rank among the elements touching it
-        owner = np.full(self.n_trace, world, dtype=np.int64)
-        touch = [set() for _ in range(world)]
-        for e in range(E):
-            tr = np.asarray(elem_trace[e], dtype=np.int64)
-            owner[tr] = np.minimum(owner[tr], parts[e])
-            touch[parts[e]].update(tr.tolist())
+        if isinstance(elem_trace, list):
+            flat = np.concatenate([np.asarray(t, dtype=np.int64) for t in elem_trace]) if len(elem_trace) else \
+                np.zeros(0, dtype=np.int64)
+            eparts = np.repeat(parts, [len(t) for t in elem_trace])
+        else:
+            et = np.asarray(elem_trace, dtype=np.int64)
+            flat, eparts = et.ravel(), np.repeat(parts, et.shape[1] if et.ndim == 2 else 0)
+        owner = np.full(n, world, dtype=np.int64)
+        np.minimum.at(owner, flat, eparts)
         self.owner = owner
-        self.touch = [np.array(sorted(s), dtype=np.int64) for s in touch]
+        self.touch = [np.unique(flat[eparts == r]) for r in range(world)]
         self.l2g = self.touch[rank]
-        g2l = {g: i for i, g in enumerate(self.l2g.tolist())}
-        self.local_elem_trace = [np.array([g2l[t] for t in np.asarray(elem_trace[e]).tolist()], dtype=np.int64)
+        self.local_elem_trace = [np.searchsorted(self.l2g, np.asarray(elem_trace[e], dtype=np.int64))
                                  for e in self.elems]
         if not isinstance(elem_trace, list) and len(self.local_elem_trace):
             self.local_elem_trace = np.stack(self.local_elem_trace)
-        # patterns: rows of each rank over global columns
-        pats = [_row_patterns(elem_trace, np.nonzero(parts == r)[0]) for r in range(world)]
-        mine = pats[rank]
+        # patterns of every rank's elements over global ids
+        keys = [_pair_keys(elem_trace, by_rank[r], n) for r in range(world)]
+        mine = keys[rank]
         self.row_ptr_local = np.zeros(len(self.l2g) + 1, dtype=np.int64)
-        cols_local = []
-        for i, g in enumerate(self.l2g.tolist()):
-            cg = mine[g]
-            cols_local.append(np.array([g2l[c] for c in cg.tolist()], dtype=np.int64))
-            self.row_ptr_local[i + 1] = self.row_ptr_local[i] + len(cg)
-        self.col_local = np.concatenate(cols_local) if cols_local else np.zeros(0, dtype=np.int64)
+        self.row_ptr_local[1:] = np.cumsum(np.bincount(np.searchsorted(self.l2g, mine // n),
+                                                       minlength=len(self.l2g)))
+        self.col_local = np.searchsorted(self.l2g, mine % n).astype(np.int64)
         # owned rows over the union of every rank's columns
+        union = np.unique(np.concatenate(keys)) if world else np.zeros(0, dtype=np.int64)
+        full = [union[owner[union // n] == r] for r in range(world)]
         self.owned = np.nonzero(owner == rank)[0]
-        full = {}
-        for r in range(world):
-            for g, cg in pats[r].items():
-                if owner[g] == rank:
-                    full.setdefault(g, set()).update(cg.tolist())
+        own = full[rank]
         self.row_ptr = np.zeros(len(self.owned) + 1, dtype=np.int64)
-        cols = []
-        for i, g in enumerate(self.owned.tolist()):
-            cg = np.array(sorted(full[g]), dtype=np.int64)
-            cols.append(cg)
-            self.row_ptr[i + 1] = self.row_ptr[i] + len(cg)
-        self.col = np.concatenate(cols) if cols else np.zeros(0, dtype=np.int64)
-        # where each rank's local blocks land: for rank r and each block of its local
-        # pattern (row-major), the owner and the block's index in the owner's owned rows
-        self._plan(pats, owner)
+        self.row_ptr[1:] = np.cumsum(np.bincount(np.searchsorted(self.owned, own // n),
+                                                 minlength=len(self.owned)))
+        self.col = (own % n).astype(np.int64)
+        self._plan(keys, full)
 
-    def _owned_index(self, r, pats, owner):
-        """For an owner rank r: {global row: (offset of the row, {global col: slot})}."""
-        out = {}
-        off = 0
-        full = {}
-        for q in range(self.world):
-            for g, cg in pats[q].items():
-                if owner[g] == r:
-                    full.setdefault(g, set()).update(cg.tolist())
-        for g in sorted(full):
-            cg = sorted(full[g])
-            out[g] = (off, {c: k for k, c in enumerate(cg)})
-            off += len(cg)
-        return out
-
-    def _plan(self, pats, owner):
-        world, rank = self.world, self.rank
-        idx = [self._owned_index(r, pats, owner) for r in range(world)]
-        # blocks and rows this rank sends to each owner (in its local row-major order)
-        self.send_blocks = [[] for _ in range(world)]   # local block ids
-        self.send_rows = [[] for _ in range(world)]     # local row ids
-        # blocks and rows of this rank's own contributions to its owned rows
-        self.own_blocks_src, self.own_blocks_dst = [], []
-        self.own_rows_src, self.own_rows_dst = [], []
-        row_of_owned = {g: i for i, g in enumerate(self.owned.tolist())}
-        for i, g in enumerate(self.l2g.tolist()):
-            o = int(owner[g])
-            off, slots = idx[o][g]
-            lo, hi = self.row_ptr_local[i], self.row_ptr_local[i + 1]
-            for k in range(lo, hi):
-                cg = int(self.l2g[self.col_local[k]])
-                if o == rank:
-                    self.own_blocks_src.append(k)
-                    self.own_blocks_dst.append(off + slots[cg])
-                else:
-                    self.send_blocks[o].append(k)
-            if o == rank:
-                self.own_rows_src.append(i)
-                self.own_rows_dst.append(row_of_owned[g])
-            else:
-                self.send_rows[o].append(i)
+    def _plan(self, keys, full):
+        """Where each block and row goes: this rank's own contributions, what it sends to
+        every owner (in its local row-major order) and where what it receives lands."""
+        world, rank, n, owner = self.world, self.rank, self.n_trace, self.owner
+        mine = keys[rank]
+        o_blk = owner[mine // n]
+        self.own_blocks_src = np.nonzero(o_blk == rank)[0]
+        self.own_blocks_dst = np.searchsorted(full[rank], mine[self.own_blocks_src])
+        self.send_blocks = [np.nonzero(o_blk == q)[0] if q != rank else np.zeros(0, dtype=np.int64)
+                            for q in range(world)]
+        o_row = owner[self.l2g]
+        self.own_rows_src = np.nonzero(o_row == rank)[0]
+        self.own_rows_dst = np.searchsorted(self.owned, self.l2g[self.own_rows_src])
+        self.send_rows = [np.nonzero(o_row == q)[0] if q != rank else np.zeros(0, dtype=np.int64)
+                          for q in range(world)]
         # what this rank receives from each sender, in the sender's order
-        self.recv_blocks_dst = [[] for _ in range(world)]
-        self.recv_rows_dst = [[] for _ in range(world)]
-        mine = idx[rank]
-        row_of_owned = {g: i for i, g in enumerate(self.owned.tolist())}
+        self.recv_blocks_dst = [np.zeros(0, dtype=np.int64) for _ in range(world)]
+        self.recv_rows_dst = [np.zeros(0, dtype=np.int64) for _ in range(world)]
         for s in range(world):
             if s == rank:
                 continue
-            l2g_s = self.touch[s]
-            ps = pats[s]
-            for g in l2g_s.tolist():                       # sender's local rows, increasing
-                if int(owner[g]) != rank:
-                    continue
-                off, slots = mine[g]
-                for cg in ps[g].tolist():                  # sender's sorted columns of the row
-                    self.recv_blocks_dst[s].append(off + slots[cg])
-                self.recv_rows_dst[s].append(row_of_owned[g])
+            ks = keys[s][owner[keys[s] // n] == rank]
+            self.recv_blocks_dst[s] = np.searchsorted(full[rank], ks)
+            rows = self.touch[s][owner[self.touch[s]] == rank]
+            self.recv_rows_dst[s] = np.searchsorted(self.owned, rows)
         # halo of the trace increments: owned values each peer needs, and where the
         # values this rank needs come from
         self.halo_send = [np.nonzero(np.isin(self.owned, self.touch[q]))[0].astype(np.int64) if q != rank
                           else np.zeros(0, dtype=np.int64) for q in range(world)]
-        self.halo_recv = [np.array([i for i, g in enumerate(self.l2g.tolist()) if int(owner[g]) == q],
-                                   dtype=np.int64) for q in range(world)]
+        self.halo_recv = [np.nonzero(o_row == q)[0].astype(np.int64) for q in range(world)]
 
     # ------------------------------------------------------------------ exchange
     def _exchange(self, payload_send, recv_shapes, like):
         """Point-to-point: payload_send[q] to rank q, returns the tensors received from
-        every other rank (the receives are posted before the sends complete)."""
+        every other rank.  All sends and receives of the step are issued as one batch
+        (batch_isend_irecv), so backends that serialise point-to-point operations per
+        peer (NCCL) cannot deadlock on the order in which ranks post them."""
         import torch
         import torch.distributed as dist
-        reqs, recvs = [], [None] * self.world
+        ops, recvs = [], [None] * self.world
         for q in range(self.world):
             if q == self.rank:
                 continue
             if recv_shapes[q][0] > 0:
                 recvs[q] = torch.empty(recv_shapes[q], dtype=like.dtype, device=like.device)
-                reqs.append(dist.irecv(recvs[q], src=q))
-        for q in range(self.world):
-            if q == self.rank or payload_send[q] is None or payload_send[q].shape[0] == 0:
-                continue
-            reqs.append(dist.isend(payload_send[q].contiguous(), dst=q))
-        for r in reqs:
-            r.wait()
+                ops.append(dist.P2POp(dist.irecv, recvs[q], q))
+            if payload_send[q] is not None and payload_send[q].shape[0] > 0:
+                ops.append(dist.P2POp(dist.isend, payload_send[q].contiguous(), q))
+        if ops:
+            for r in dist.batch_isend_irecv(ops):
+                r.wait()
         return recvs
 
     def assemble_owned(self, K_local, R_local):

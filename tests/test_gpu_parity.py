@@ -218,7 +218,7 @@ TOL_MIXED = 1e-10
 # CPU model of FP32 operands puts at 0.01 - 0.17.  The error against the exact K is
 # printed.  R, du, dq are refined to FP64 as before.
 LOW_FMT = {2: "tf32", 3: "bf16"}
-LOW_RATIO = 0.5
+LOW_RATIO = 0.35
 
 
 def _mixed_mesh(wl, precision=1):

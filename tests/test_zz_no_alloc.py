@@ -44,11 +44,17 @@ def test_static_residual_matches_regular_twice(idx):
     for call in range(2):
         r_u = torch.full_like(ref["r_u"], float("nan"))
         r_fl = torch.full_like(ref["r_fl"], float("nan"))
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         rc = lib.iedg_eval_residual_static(mesh._h, u.data_ptr(), uh.data_ptr(), q.data_ptr(),
                                            None if ur is None else ur.data_ptr(), r_u.data_ptr(),
                                            r_fl.data_ptr(), ctypes.c_void_p(stream))
         assert rc == 0, lib.iedg_last_error(mesh._h).decode()
         torch.cuda.synchronize()
+        if call == 1:
+            # the first call only looks up the scratch array's device address; from then
+            # on a call takes no device memory at all
+            assert torch.cuda.mem_get_info()[0] == free_before, "the static entry point allocated device memory"
         for got, want in ((r_u, ref["r_u"]), (r_fl, ref["r_fl"])):
             g, w = got.cpu().numpy(), want.cpu().numpy()
             scale = max(np.abs(w).max(), np.abs(ref["r_u"].cpu().numpy()).max())

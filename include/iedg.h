@@ -64,7 +64,11 @@ extern "C" {
 #define IEDG_ELEM_OK        0
 #define IEDG_ELEM_REFINE    1   /* mixed path: refinement did not reach 1e-10 relative residual */
 #define IEDG_ELEM_SINGULAR  2   /* exact zero pivot in the element block          */
-#define IEDG_ELEM_NONFINITE 3   /* NaN/Inf met in the element's Schur complement  */
+#define IEDG_ELEM_NONFINITE 3   /* NaN/Inf met among the element's pivot candidates
+                                   or in its Schur complement                      */
+#define IEDG_ELEM_TIMEOUT   4   /* tensor-core forms: a bounded completion wait gave up
+                                   (see iedg_set_fault_injection); the element was not
+                                   factored                                         */
 
 #define IEDG_PRECISION_FP64  0   /* every step in FP64                                   */
 #define IEDG_PRECISION_MIXED 1   /* element matrix and partial LU in FP32 (K to FP32
@@ -255,7 +259,9 @@ int iedg_trace_solve(iedg_mesh* mesh, const double* K, const double* R, double* 
  *                  products of equal weight accumulate exactly in FP32 over K chunks of
  *                  64 and are summed in FP64 (results agree with the DFMA form to
  *                  FP64 rounding); the panel factorisation stays on DFMA; persistent
- *                  grid, panel 16.  Mixed path: TF32 operands split in high and low
+ *                  grid, panel 16; its per-CTA slice buffers (16 (nt + 1) nu floats
+ *                  per resident CTA) are allocated by this call when it selects the
+ *                  form (IEDG_ERR_OOM if they do not fit), not by the compute calls.  Mixed path: TF32 operands split in high and low
  *                  parts, three products ("3xTF32").  0 = DFMA / FFMA updates.  Default
  *                  0 for FP64 handles, 1 for mixed ones.  Handles created with
  *                  IEDG_PRECISION_MIXED_TF32 or _MIXED_BF16 always take the tensor-core
@@ -274,6 +280,34 @@ typedef struct {
 } iedg_schedule;
 int iedg_get_schedule(const iedg_mesh* mesh, iedg_schedule* out);
 int iedg_set_schedule(iedg_mesh* mesh, const iedg_schedule* in);
+
+/* Host-side fault injection for tests of the failure handling (no counterpart in
+ * the paper).  Nothing here faults, traps or hangs the GPU: each field makes one
+ * kind of element failure happen on purpose so that its status can be checked.
+ *   zero_row_elem: element (user id, uniform meshes) whose bordered element matrix
+ *                  gets u-row zero_row (0 <= zero_row < m Np) set to zero after
+ *                  assembly and before the LU, which makes its element block singular
+ *                  (the element must come back IEDG_ELEM_SINGULAR); -1 = none.
+ *   refine_iters:  mixed forms: correction steps of the FP64 refinement (0..16, -1 =
+ *                  the default 8).  0 leaves the FP32 solve unrefined, so elements
+ *                  come back IEDG_ELEM_REFINE.
+ *   tc_wait_limit: polls of each tensor-core completion wait (tcgen05 forms) before it
+ *                  gives up (0 = the default 2^26; -1 = no poll, every wait gives up at
+ *                  once).  A wait that gives up stops its CTA from factoring (after its
+ *                  MMAs in flight drain at the default limit and its TMEM is freed);
+ *                  that element and every element the CTA still takes from the queue
+ *                  come back IEDG_ELEM_TIMEOUT.
+ * The settings stay until changed; {-1, 0, -1, 0} restores normal operation.
+ * IEDG_ERR_INVALID_ARG for values out of range, IEDG_ERR_UNSUPPORTED for zero_row_elem
+ * on meshes with mixed orders. */
+typedef struct {
+  int64_t zero_row_elem;
+  int32_t zero_row;
+  int32_t refine_iters;
+  int32_t tc_wait_limit;
+  int32_t reserved;
+} iedg_fault_injection;
+int iedg_set_fault_injection(iedg_mesh* mesh, const iedg_fault_injection* f);
 
 /* Residual without any allocation (no counterpart in the paper; a service for
  * callers that cannot allocate device memory when they need a residual, e.g. code

@@ -962,7 +962,7 @@ static int assemble_mixed(iedg_mesh* M, const double* u, const double* q, const 
       CUDA_TRY(TRACED("assemble", launch_assemble(C, st)));
   }
   CUDA_TRY(TRACED("lu_schur", launch_lu(M, st)));
-  if (M->precision == IEDG_PRECISION_MIXED)
+  if (M->precision != IEDG_PRECISION_FP64)
     for (iedg_mesh* C : M->groups) CUDA_TRY(TRACED("refine", launch_refine(C, st)));
   CUDA_TRY(TRACED("scatter_K", launch_scatter_K(M, K, st)));
   if (M->precision == IEDG_PRECISION_FP64)
@@ -1060,8 +1060,9 @@ extern "C" int iedg_assemble_condensed(iedg_mesh* M, const double* u, const doub
     CUDA_TRY(TRACED("assemble", launch_assemble_sf(M, st)));
   else
     CUDA_TRY(TRACED("assemble", launch_assemble(M, st)));
+  if (M->fault.zero_row_elem >= 0) CUDA_TRY(TRACED("fault_zero_row", launch_zero_row(M, st)));
   CUDA_TRY(TRACED("lu_schur", launch_lu(M, st)));
-  if (M->precision == IEDG_PRECISION_MIXED) CUDA_TRY(TRACED("refine", launch_refine(M, st)));
+  if (M->precision != IEDG_PRECISION_FP64) CUDA_TRY(TRACED("refine", launch_refine(M, st)));
   CUDA_TRY(TRACED("scatter_K", launch_scatter_K(M, K, st)));
   if (M->precision == IEDG_PRECISION_FP64)
     CUDA_TRY(TRACED("scatter_R", launch_scatter_R(M, M->S + (int64_t)dm.nu * dm.ld + dm.n, (int64_t)dm.n * dm.ld,
@@ -1132,6 +1133,21 @@ extern "C" int iedg_profile_reset(iedg_mesh* M) {
   return IEDG_OK;
 }
 
+extern "C" int iedg_set_fault_injection(iedg_mesh* M, const iedg_fault_injection* f) {
+  if (!M || !f) return fail(M, IEDG_ERR_INVALID_ARG, "null argument");
+  if (f->zero_row_elem < -1 || f->zero_row_elem >= M->E || f->refine_iters < -1 || f->refine_iters > 16 ||
+      f->tc_wait_limit < -1 || (f->zero_row_elem >= 0 && (f->zero_row < 0 || f->zero_row >= M->dm.nu)))
+    return fail(M, IEDG_ERR_INVALID_ARG, "fault injection values out of range");
+  if (f->zero_row_elem >= 0 && M->mixed_orders)
+    return fail(M, IEDG_ERR_UNSUPPORTED, "zero-row injection is only available on uniform meshes");
+  M->fault.zero_row_elem = f->zero_row_elem;
+  M->fault.zero_row = f->zero_row;
+  M->fault.refine_iters = f->refine_iters;
+  M->fault.tc_wait_limit = f->tc_wait_limit;
+  for (iedg_mesh* C : M->groups) C->fault = M->fault;
+  return IEDG_OK;
+}
+
 extern "C" int iedg_get_schedule(const iedg_mesh* M, iedg_schedule* out) {
   if (!M || !out) return IEDG_ERR_INVALID_ARG;
   std::memset(out, 0, sizeof(*out));
@@ -1152,6 +1168,14 @@ extern "C" int iedg_set_schedule(iedg_mesh* M, const iedg_schedule* in) {
   for (int i = 0; i < 4; ++i) {
     const int c = in->asm_chunk_by_order[i];
     if (c != 0 && c != 8 && c != 16 && c != 32) return fail(M, IEDG_ERR_INVALID_ARG, "schedule values out of range");
+  }
+  if (M->precision == IEDG_PRECISION_FP64 && in->lu_tensor == 1) {
+    // the FP64 tensor-core Schur form needs per-CTA slice buffers: allocated here, so
+    // that compute calls allocate nothing
+    const cudaError_t err = prepare_lu64_oz(M);
+    if (err != cudaSuccess)
+      return fail(M, err == cudaErrorMemoryAllocation ? IEDG_ERR_OOM : IEDG_ERR_CUDA,
+                  std::string("FP64 tensor-core Schur buffers: ") + cudaGetErrorString(err));
   }
   M->sched.lu_persistent = in->lu_persistent;
   M->sched.lu_panel = in->lu_panel;

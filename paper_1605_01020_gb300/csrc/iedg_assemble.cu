@@ -275,7 +275,16 @@ struct TcState {
   uint64_t* mbar;       // MMA completion barriers (one per operand stage)
   uint32_t phase[2];    // parity of each barrier's next completion
   int failed;           // a completion wait ran out
+  int limit;            // polls of a completion wait before it gives up (0: gives up at once)
+  int pending[2];       // a commit on barrier b has not been waited for yet
 };
+
+// Drain after a failed wait: the MMAs still in flight complete (bounded, full limit)
+// before the CTA frees its TMEM; barriers with no commit outstanding are skipped.
+__device__ __forceinline__ void tc_drain(const TcState& t) {
+  for (int b = 0; b < 2; ++b)
+    if (t.pending[b]) tc::mbar_wait(t.mbar + b, t.phase[b], kTcWaitLimit);
+}
 
 // Sizes and location of one element's bordered matrix.
 struct LuElem {
@@ -354,6 +363,13 @@ __device__ __forceinline__ long long abs_key(T v) {
   }
 }
 
+// abs_key of +infinity: keys at or above it (and the -1 of NaN) are non-finite values
+template <class T>
+__device__ __forceinline__ long long inf_key() {
+  if constexpr (sizeof(T) == 8) return 0x7FF0000000000000LL;
+  else return 0x7F800000LL;
+}
+
 template <class T, int NB>
 __device__ __forceinline__ void lu_element(const LuElem& el, T* __restrict__ S, int8_t* __restrict__ status,
                                            int* __restrict__ pivots, const int64_t e, bool defer_schur = false) {
@@ -368,6 +384,7 @@ __device__ __forceinline__ void lu_element(const LuElem& el, T* __restrict__ S, 
   const int n = el.n, nu = el.nu, ld = el.ld, ncol = n + 1;
   T* A = S + el.off;
   T* P = sm;                            // [n][NB]
+  int nonfin = 0;                       // a pivot candidate was NaN or infinite
   T* Uc = P + (size_t)n * NB;           // [NB][UCW]
   if (tid == 0) sing = 0;
   for (int kb = 0; kb < nu; kb += NB) {
@@ -383,6 +400,7 @@ __device__ __forceinline__ void lu_element(const LuElem& el, T* __restrict__ S, 
       int bi = j;
       for (int r = j + tid; r < prow; r += LU_THREADS) {
         const long long v = abs_key(P[r * NB + j]);
+        nonfin |= v < 0 || v >= inf_key<T>();
         if (v > best) { best = v; bi = r; }
       }
 #pragma unroll
@@ -472,11 +490,11 @@ __device__ __forceinline__ void lu_element(const LuElem& el, T* __restrict__ S, 
       lu64_update_rect<T, NB>(A, ld, P, Uc, kb, nb, r0, n, r0, ncol);
     }
   }
-  // status: exact zero pivot, or non-finite Schur complement (deferred form: the caller
-  // checks the Schur complement after forming it)
-  __syncthreads();
+  // status: a non-finite pivot candidate, an exact zero pivot, or a non-finite Schur
+  // complement (deferred form: the caller checks the Schur complement after forming it)
+  nonfin = __syncthreads_or(nonfin);
   if (defer_schur) {
-    if (tid == 0) status[e] = sing ? IEDG_ELEM_SINGULAR : IEDG_ELEM_OK;
+    if (tid == 0) status[e] = nonfin ? IEDG_ELEM_NONFINITE : (sing ? IEDG_ELEM_SINGULAR : IEDG_ELEM_OK);
     __syncthreads();
     return;
   }
@@ -486,7 +504,9 @@ __device__ __forceinline__ void lu_element(const LuElem& el, T* __restrict__ S, 
     if (!isfinite(A[(int64_t)r * ld + c])) bad = 1;
   }
   bad = __syncthreads_or(bad);
-  if (tid == 0) status[e] = sing ? IEDG_ELEM_SINGULAR : (bad ? IEDG_ELEM_NONFINITE : IEDG_ELEM_OK);
+  if (tid == 0)
+    status[e] = nonfin ? IEDG_ELEM_NONFINITE
+                       : (sing ? IEDG_ELEM_SINGULAR : (bad ? IEDG_ELEM_NONFINITE : IEDG_ELEM_OK));
 }
 
 // ----------------------------------------------------------- FP64 Schur complement on tcgen05
@@ -629,9 +649,11 @@ __device__ void schur_ozaki(double* __restrict__ A, int ld, int n, int nu, const
             oz_issue(tcs->tmem, smem, k0 == kc);
             tc::mma_commit(tcs->mbar);
           }
-          const bool ok = __syncthreads_and(tc::mbar_wait(tcs->mbar, tcs->phase[0], 1 << 26));
+          tcs->pending[0] = 1;
+          const bool ok = __syncthreads_and(tc::mbar_wait(tcs->mbar, tcs->phase[0], tcs->limit));
           if (!ok) { tcs->failed = 1; break; }
           tcs->phase[0] ^= 1u;
+          tcs->pending[0] = 0;
           tc::fence_after_sync();
         }
         if (tcs->failed) break;
@@ -875,8 +897,8 @@ __device__ __forceinline__ void schur_issue(uint32_t tmem, const char* stage, bo
 // Bounded wait on stage b's barrier by every thread; the outcome is made uniform.
 // (A wait that ran out leaves the phase where it was, so the drain can wait for it.)
 __device__ __forceinline__ bool schur_wait(TcState* tcs, int b) {
-  const bool ok = __syncthreads_and(tc::mbar_wait(tcs->mbar + b, tcs->phase[b], 1 << 26));
-  if (ok) tcs->phase[b] ^= 1u;
+  const bool ok = __syncthreads_and(tc::mbar_wait(tcs->mbar + b, tcs->phase[b], tcs->limit));
+  if (ok) { tcs->phase[b] ^= 1u; tcs->pending[b] = 0; }
   else tcs->failed = 1;
   return ok;
 }
@@ -899,6 +921,7 @@ __device__ void schur_tc(float* __restrict__ A, int ld, int n, int nu, char* sme
           schur_issue<KIND>(tcs->tmem, smem + b * TC_STAGE_BYTES, c == 0);
           tc::mma_commit(tcs->mbar + b);
         }
+        tcs->pending[b] = 1;
         if (c + 1 < nk) {
           // the other stage was last read by the MMAs of chunk c - 1
           if (c >= 1 && !schur_wait(tcs, b ^ 1)) break;
@@ -946,6 +969,7 @@ __device__ __forceinline__ void lu32_element(const LuElem& el, float* __restrict
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = el.n, nu = el.nu, ld = el.ld, ncol = n + 1;
   float* A = S + el.off;
+  int nonfin = 0;                       // a pivot candidate was NaN or infinite
   if (tid == 0) sing = 0;
   for (int kb = 0; kb < nu; kb += L32_NB) {
     const int nb = min(L32_NB, nu - kb), rows = n - kb, prow = nu - kb;
@@ -961,6 +985,7 @@ __device__ __forceinline__ void lu32_element(const LuElem& el, float* __restrict
       int bi = j;
       for (int r = j + tid; r < prow; r += LU_THREADS) {
         float v = fabsf(Pj[r]);
+        nonfin |= !(v <= 3.402823466e38f);
         if (v > best) { best = v; bi = r; }
       }
 #pragma unroll
@@ -1068,8 +1093,12 @@ __device__ __forceinline__ void lu32_element(const LuElem& el, float* __restrict
     if (!isfinite(A[(int64_t)r * ld + c])) bad = 1;
   }
   bad = __syncthreads_or(bad);
-  if (TC && tcs->failed) bad = 1;
-  if (tid == 0) status[e] = sing ? IEDG_ELEM_SINGULAR : (bad ? IEDG_ELEM_NONFINITE : IEDG_ELEM_OK);
+  nonfin = __syncthreads_or(nonfin);
+  if (tid == 0) {
+    if (TC && tcs->failed) status[e] = IEDG_ELEM_TIMEOUT;
+    else status[e] = nonfin ? IEDG_ELEM_NONFINITE
+                            : (sing ? IEDG_ELEM_SINGULAR : (bad ? IEDG_ELEM_NONFINITE : IEDG_ELEM_OK));
+  }
 }
 
 // Element scheduling of the batched LU.  queue == nullptr: one CTA per element.
@@ -1114,7 +1143,7 @@ k_lu32(Dims dm, LuDesc lud, float* __restrict__ S, int8_t* __restrict__ status, 
 template <int KIND>
 __global__ void __launch_bounds__(LU_THREADS, 2)
 k_lu32_tc(Dims dm, LuDesc lud, float* __restrict__ S, int8_t* __restrict__ status, int* __restrict__ pivots,
-          int64_t* queue, int64_t E, int* err) {
+          int64_t* queue, int64_t E, int* err, int wait_limit) {
   __shared__ uint32_t tmem_base;
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ TcState tcs;
@@ -1136,21 +1165,29 @@ k_lu32_tc(Dims dm, LuDesc lud, float* __restrict__ S, int8_t* __restrict__ statu
     tcs.phase[0] = 0;
     tcs.phase[1] = 0;
     tcs.failed = 0;
+    tcs.limit = wait_limit;
+    tcs.pending[0] = 0;
+    tcs.pending[1] = 0;
   }
   __syncthreads();
   // each thread keeps its own copy of the phases; the shared copy is only the start
   TcState mine = tcs;
   int64_t e;
-  for (int64_t it = 0; next_element(queue, E, it, lud.order, &e); ++it) {
+  int64_t it = 0;
+  for (; next_element(queue, E, it, lud.order, &e); ++it) {
     lu32_element<true, KIND>(lu_elem(dm, lud, e), S, status, pivots, e, &mine);
     if (__syncthreads_or(mine.failed)) {
       if (tid == 0) atomicOr(err, 1);
-      // let MMAs still in flight drain (bounded) before the TMEM is freed
-      tc::mbar_wait(&mbar[0], mine.phase[0], 1 << 26);
-      tc::mbar_wait(&mbar[1], mine.phase[1], 1 << 26);
+      tc_drain(mine);     // MMAs still in flight finish before the TMEM is freed
+      ++it;
       break;
     }
   }
+  // after a failed wait this CTA factors nothing more: the elements it still takes from
+  // the queue are flagged, so no element is left unfactored with an OK status
+  if (mine.failed)
+    for (; next_element(queue, E, it, lud.order, &e); ++it)
+      if (tid == 0) status[e] = IEDG_ELEM_TIMEOUT;
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -1161,7 +1198,7 @@ k_lu32_tc(Dims dm, LuDesc lud, float* __restrict__ S, int8_t* __restrict__ statu
 // holds 256 TMEM columns (two resident CTAs fit an SM's 512) and one completion barrier.
 __global__ void __launch_bounds__(LU_THREADS)
 k_lu64_oz(Dims dm, LuDesc lud, double* __restrict__ S, int8_t* __restrict__ status, int64_t* queue, int64_t E,
-          float* __restrict__ scratch, int64_t scratch_floats, int* err) {
+          float* __restrict__ scratch, int64_t scratch_floats, int* err, int wait_limit) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ uint32_t tmem_base;
   __shared__ __align__(8) uint64_t mbar[2];
@@ -1181,6 +1218,9 @@ k_lu64_oz(Dims dm, LuDesc lud, double* __restrict__ S, int8_t* __restrict__ stat
     tcs.phase[0] = 0;
     tcs.phase[1] = 0;
     tcs.failed = 0;
+    tcs.limit = wait_limit;
+    tcs.pending[0] = 0;
+    tcs.pending[1] = 0;
   }
   __syncthreads();
   TcState mine = tcs;
@@ -1196,7 +1236,8 @@ k_lu64_oz(Dims dm, LuDesc lud, double* __restrict__ S, int8_t* __restrict__ stat
     sc.cs = dd + ntm;
   }
   int64_t e;
-  for (int64_t it = 0; next_element(queue, E, it, lud.order, &e); ++it) {
+  int64_t it = 0;
+  for (; next_element(queue, E, it, lud.order, &e); ++it) {
     const LuElem el = lu_elem(dm, lud, e);
     lu_element<double, 16>(el, S, status, nullptr, e, true);
     schur_ozaki(S + el.off, el.ld, el.n, el.nu, sc, reinterpret_cast<char*>(smraw), &mine);
@@ -1208,14 +1249,18 @@ k_lu64_oz(Dims dm, LuDesc lud, double* __restrict__ S, int8_t* __restrict__ stat
       int r = nu + idx / (ncol - nu), c = nu + idx % (ncol - nu);
       if (!isfinite(A[(int64_t)r * el.ld + c])) bad = 1;
     }
-    bad = __syncthreads_or(bad) || mine.failed;
+    bad = __syncthreads_or(bad);
     if (tid == 0 && bad && status[e] == IEDG_ELEM_OK) status[e] = IEDG_ELEM_NONFINITE;
     if (__syncthreads_or(mine.failed)) {
-      if (tid == 0) atomicOr(err, 1);
-      tc::mbar_wait(&mbar[0], mine.phase[0], 1 << 26);   // let MMAs in flight drain
+      if (tid == 0) { atomicOr(err, 1); status[e] = IEDG_ELEM_TIMEOUT; }
+      tc_drain(mine);     // MMAs still in flight finish before the TMEM is freed
+      ++it;
       break;
     }
   }
+  if (mine.failed)
+    for (; next_element(queue, E, it, lud.order, &e); ++it)
+      if (tid == 0) status[e] = IEDG_ELEM_TIMEOUT;
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -1299,33 +1344,50 @@ static cudaError_t lu_t(iedg_mesh* M, T* S, int* piv, cudaStream_t st) {
 size_t lu64_smem(const Dims& dm, int nb) { return sizeof(double) * ((size_t)dm.n * nb + (size_t)nb * UCW); }
 
 // FP64 form with the Schur complement on the tensor cores (persistent grid only: each
-// CTA owns a slice buffer for the element it works on, allocated on first use).
-static cudaError_t lu64_oz(iedg_mesh* M, cudaStream_t st) {
+// CTA owns a slice buffer for the element it works on).  The buffers are allocated
+// when the schedule selects this form (iedg_set_schedule), never by a compute call.
+static cudaError_t lu64_oz_grid(iedg_mesh* M, size_t* smem_out, unsigned* grid, int64_t* per_cta) {
   const Dims& dm = M->dm;
   size_t smem = lu64_smem(dm, 16);
   if (smem < (size_t)OZ_STAGE_BYTES) smem = OZ_STAGE_BYTES;
   cudaError_t err = cudaFuncSetAttribute(k_lu64_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  unsigned grid = 0;
   // two resident CTAs at most: each holds 256 of the SM's 512 TMEM columns
-  err = persistent_grid(k_lu64_oz, smem, M->E, &grid, 2);
+  err = persistent_grid(k_lu64_oz, smem, M->E, grid, 2);
   if (err != cudaSuccess) return err;
   const int64_t ntm = dm.nt + 1;
-  const int64_t per = ((2 * (int64_t)OZ_S * ntm * dm.nu + 4 * ntm) + 3) & ~(int64_t)3;
-  if (M->oz_scratch == nullptr || M->oz_grid < grid) {
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    err = cudaStreamIsCapturing(st, &cs);
-    if (err != cudaSuccess) return err;
-    if (cs != cudaStreamCaptureStatusNone) return cudaErrorStreamCaptureUnsupported;
-    if (M->oz_scratch) cudaFree(M->oz_scratch);
-    err = cudaMalloc(&M->oz_scratch, (size_t)grid * per * sizeof(float));
-    if (err != cudaSuccess) { M->oz_scratch = nullptr; return err; }
-    M->oz_grid = grid;
-  }
+  *per_cta = ((2 * (int64_t)OZ_S * ntm * dm.nu + 4 * ntm) + 3) & ~(int64_t)3;
+  *smem_out = smem;
+  return cudaSuccess;
+}
+
+cudaError_t prepare_lu64_oz(iedg_mesh* M) {
+  size_t smem = 0;
+  unsigned grid = 0;
+  int64_t per = 0;
+  cudaError_t err = lu64_oz_grid(M, &smem, &grid, &per);
+  if (err != cudaSuccess) return err;
+  if (M->oz_scratch != nullptr && M->oz_grid >= grid) return cudaSuccess;
+  if (M->oz_scratch) cudaFree(M->oz_scratch);
+  M->oz_scratch = nullptr;
+  err = cudaMalloc(&M->oz_scratch, (size_t)grid * per * sizeof(float));
+  if (err != cudaSuccess) return err;
+  M->oz_grid = grid;
+  return cudaSuccess;
+}
+
+static cudaError_t lu64_oz(iedg_mesh* M, cudaStream_t st) {
+  const Dims& dm = M->dm;
+  size_t smem = 0;
+  unsigned grid = 0;
+  int64_t per = 0;
+  cudaError_t err = lu64_oz_grid(M, &smem, &grid, &per);
+  if (err != cudaSuccess) return err;
+  if (M->oz_scratch == nullptr || M->oz_grid < grid) return cudaErrorNotReady;   // set_schedule allocates
   err = cudaMemsetAsync(M->queue, 0, sizeof(int64_t), st);
   if (err != cudaSuccess) return err;
   k_lu64_oz<<<grid, LU_THREADS, smem, st>>>(dm, M->lud, M->S, M->status, M->queue, M->E, M->oz_scratch, per,
-                                             M->dev_flag);
+                                             M->dev_flag, tc_wait_limit(M));
   return cudaGetLastError();
 }
 
@@ -1347,7 +1409,8 @@ static cudaError_t lu32_tc(iedg_mesh* M, cudaStream_t st) {
     if (err != cudaSuccess) return err;
     queue = M->queue;
   }
-  k_lu32_tc<KIND><<<grid, LU_THREADS, smem, st>>>(dm, M->lud, M->S32, M->status, M->piv, queue, M->E, M->dev_flag);
+  k_lu32_tc<KIND><<<grid, LU_THREADS, smem, st>>>(dm, M->lud, M->S32, M->status, M->piv, queue, M->E, M->dev_flag,
+                                                   tc_wait_limit(M));
   return cudaGetLastError();
 }
 

@@ -41,6 +41,15 @@ struct Schedule {
   int asm_chunk_by_order[4] = {0, 0, 0, 0};   // mixed orders: chunk per order (0 = asm_chunk)
 };
 
+// Failure injection for tests (iedg_set_fault_injection).
+struct Fault {
+  int64_t zero_row_elem = -1;   // element (internal id) whose u-row zero_row is zeroed before the LU
+  int zero_row = 0;
+  int refine_iters = -1;        // correction steps of the refinement (-1 = kRefineMaxIter)
+  int tc_wait_limit = 0;        // polls of a tensor-core completion wait (0 = kTcWaitLimit, -1 = none)
+};
+constexpr int kTcWaitLimit = 1 << 26;
+
 // Reference-element tables (device), shared by all elements.
 struct RefTables {
   double* Phi;    // [Nq][Np]
@@ -201,6 +210,7 @@ struct iedg_mesh {
   double* kpart = nullptr;      // trace solve: dot-product partial sums
   double* khdev = nullptr;      // trace solve: small vector of coefficients
   iedg::Schedule sched;
+  iedg::Fault fault;
   int* dev_flag = nullptr;      // geometry error flag
   bool assembled = false;
   // tracing: launches per kernel, events while profiling is on
@@ -233,6 +243,7 @@ bool assemble_sf_supported(const Dims& dm);
 AsmTab<double> tables64(const iedg_mesh* M);
 AsmTab<float> tables32(const iedg_mesh* M);
 cudaError_t launch_lu(iedg_mesh* M, cudaStream_t st);
+cudaError_t prepare_lu64_oz(iedg_mesh* M);   // slice buffers of the FP64 tensor-core Schur form
 cudaError_t launch_scatter_K(iedg_mesh* M, double* K, cudaStream_t st);
 cudaError_t launch_scatter_R_ragged(iedg_mesh* M, const RaggedSrc& src, const double* base, double* R,
                                     cudaStream_t st);
@@ -245,8 +256,14 @@ cudaError_t launch_scatter_R(iedg_mesh* M, const double* src, int64_t src_elem_s
 cudaError_t launch_backsub(iedg_mesh* M, const double* duhat, double* du, double* dq,
                            cudaStream_t st);
 cudaError_t launch_refine(iedg_mesh* M, cudaStream_t st);
+cudaError_t launch_zero_row(iedg_mesh* M, cudaStream_t st);   // Fault.zero_row_elem
 cudaError_t launch_backsub_mixed(iedg_mesh* M, const double* duhat, double* du, double* dq,
                                  cudaStream_t st);
+
+inline int refine_iters(const iedg_mesh* M) { return M->fault.refine_iters >= 0 ? M->fault.refine_iters : 8; }
+inline int tc_wait_limit(const iedg_mesh* M) {
+  return M->fault.tc_wait_limit > 0 ? M->fault.tc_wait_limit : (M->fault.tc_wait_limit < 0 ? 0 : kTcWaitLimit);
+}
 
 // refinement controls of the mixed path
 constexpr int kRefineMaxIter = 8;

@@ -495,7 +495,7 @@ __device__ void solve32(const Dims& dm, const float* __restrict__ A, int ld, con
 // A~ x, C~ x for that x (w.z must be zero).  Returns the final relative residual.
 __device__ double refine_solve(const Dims& dm, const Phys& ph, const RefTables& ref, const Geo& G,
                                const PointJac& PJ, const TraceTab& tt, int64_t e, const float* A, int ld,
-                               const int* piv, Work& w) {
+                               const int* piv, Work& w, int max_iter) {
   const int tid = threadIdx.x, nu = dm.nu;
   double bn = 0.0;
   for (int i = tid; i < nu; i += RF_THREADS) { w.v[i] = w.b[i]; bn = fmax(bn, fabs(w.b[i])); }
@@ -504,7 +504,7 @@ __device__ double refine_solve(const Dims& dm, const Phys& ph, const RefTables& 
   for (int i = tid; i < nu; i += RF_THREADS) w.x[i] = w.v[i];
   __syncthreads();
   double rel = 0.0;
-  for (int it = 0; it <= kRefineMaxIter; ++it) {
+  for (int it = 0; it <= max_iter; ++it) {
     element_apply(dm, ph, ref, G, PJ, tt, e, w, true, false);
     double rn = 0.0;
     for (int i = tid; i < nu; i += RF_THREADS) {
@@ -514,7 +514,7 @@ __device__ double refine_solve(const Dims& dm, const Phys& ph, const RefTables& 
     }
     rn = block_max(rn, w.red);
     rel = bn > 0.0 ? rn / bn : rn;
-    if (!(rel > kRefineTol) || it == kRefineMaxIter) break;   // also stops on NaN
+    if (!(rel > kRefineTol) || it == max_iter) break;   // also stops on NaN
     solve32(dm, A, ld, piv, w.v, reinterpret_cast<float*>(w.ou), w.red);
     for (int i = tid; i < nu; i += RF_THREADS) w.x[i] += w.v[i];
     __syncthreads();
@@ -526,7 +526,7 @@ __device__ double refine_solve(const Dims& dm, const Phys& ph, const RefTables& 
 __global__ void __launch_bounds__(RF_THREADS, 2)
 k_refine(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ, TraceTab tt, const float* __restrict__ S32,
          const int* __restrict__ piv, const double* __restrict__ rhs64, double* __restrict__ y64,
-         double* __restrict__ re64, int8_t* __restrict__ status) {
+         double* __restrict__ re64, int8_t* __restrict__ status, int max_iter) {
   extern __shared__ double sm[];
   Work w = carve(dm, sm);
   const int64_t e = blockIdx.x;
@@ -538,7 +538,7 @@ k_refine(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ, TraceTab tt, const
   __syncthreads();
   const float* A = S32 + (tt.soff ? tt.soff[e] : e * (int64_t)dm.n * dm.ld);
   const int ld = tt.ldv ? tt.ldv[e] : dm.ld;
-  double rel = refine_solve(dm, ph, ref, G, PJ, tt, e, A, ld, piv + e * dm.nu, w);
+  double rel = refine_solve(dm, ph, ref, G, PJ, tt, e, A, ld, piv + e * dm.nu, w, max_iter);
   for (int i = tid; i < dm.nu; i += RF_THREADS) y64[e * dm.nu + i] = w.x[i];
   // trace rows of the right-hand side: packed by the element's slot count
   const int nbe = tt.nb ? tt.nb[e] : dm.Nb;
@@ -554,7 +554,7 @@ __global__ void __launch_bounds__(RF_THREADS, 2)
 k_backsub_mixed(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ, TraceTab tt, const int64_t* __restrict__ etrace,
                 const float* __restrict__ S32, const int* __restrict__ piv, const double* __restrict__ rhs64,
                 const double* __restrict__ rhoq, const double* __restrict__ duhat, double* __restrict__ du,
-                double* __restrict__ dq) {
+                double* __restrict__ dq, int max_iter) {
   extern __shared__ double sm[];
   Work w = carve(dm, sm);
   const int64_t e = blockIdx.x;
@@ -575,7 +575,7 @@ k_backsub_mixed(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ, TraceTab tt
   __syncthreads();
   const float* A = S32 + (tt.soff ? tt.soff[e] : e * (int64_t)dm.n * dm.ld);
   const int ld = tt.ldv ? tt.ldv[e] : dm.ld;
-  refine_solve(dm, ph, ref, G, PJ, tt, e, A, ld, piv + e * dm.nu, w);
+  refine_solve(dm, ph, ref, G, PJ, tt, e, A, ld, piv + e * dm.nu, w, max_iter);
   for (int i = tid; i < dm.nt; i += RF_THREADS) {          // dU_e again, for dq
     int k = i / Nb, t = i % Nb;
     w.z[i] = t < nbe ? duhat[etrace[e * Nb + t] * m + k] : 0.0;
@@ -604,7 +604,7 @@ cudaError_t launch_refine(iedg_mesh* M, cudaStream_t st) {
   cudaError_t err = cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   k_refine<<<(unsigned)M->E, RF_THREADS, smem, st>>>(dm, M->ph, M->ref, M->geo, M->pj, M->tt, M->S32, M->piv, M->rhs64,
-                                                      M->y64, M->re64, M->status);
+                                                      M->y64, M->re64, M->status, refine_iters(M));
   return cudaGetLastError();
 }
 
@@ -614,7 +614,8 @@ cudaError_t launch_backsub_mixed(iedg_mesh* M, const double* duhat, double* du, 
   cudaError_t err = cudaFuncSetAttribute(k_backsub_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   k_backsub_mixed<<<(unsigned)M->E, RF_THREADS, smem, st>>>(dm, M->ph, M->ref, M->geo, M->pj, M->tt, M->etrace, M->S32,
-                                                             M->piv, M->rhs64, M->rhoq, duhat, du, dq);
+                                                             M->piv, M->rhs64, M->rhoq, duhat, du, dq,
+                                                             refine_iters(M));
   return cudaGetLastError();
 }
 

@@ -39,6 +39,14 @@ __global__ void k_scatter_K(Dims dm, int64_t nnzb, int64_t P, const int64_t* __r
   K[idx] = v;
 }
 
+// Fault injection: u-row r of element e's bordered matrix (columns 0..n) set to zero,
+// and its FP64 right-hand side entry on the mixed path.
+template <class T>
+__global__ void k_zero_row(T* __restrict__ row, int ncol, double* __restrict__ rhs_entry) {
+  for (int c = threadIdx.x; c < ncol; c += blockDim.x) row[c] = (T)0;
+  if (threadIdx.x == 0 && rhs_entry) *rhs_entry = 0.0;
+}
+
 // Ragged form of k_scatter_R: contributions packed as e P + s, values located by src.
 __global__ void k_scatter_R_ragged(int m, int64_t T, int64_t P, const int64_t* __restrict__ rc_ptr,
                                    const int64_t* __restrict__ rc_src, RaggedSrc rs,
@@ -139,6 +147,18 @@ k_backsub(Dims dm, Geo G, const int64_t* __restrict__ etrace, const double* __re
 }
 
 }  // namespace
+
+cudaError_t launch_zero_row(iedg_mesh* M, cudaStream_t st) {
+  const Dims& dm = M->dm;
+  const int64_t e = M->fault.zero_row_elem;
+  if (e < 0 || e >= M->E || M->fault.zero_row < 0 || M->fault.zero_row >= dm.nu) return cudaSuccess;
+  const int64_t off = (e * dm.n + M->fault.zero_row) * (int64_t)dm.ld;
+  if (M->precision == IEDG_PRECISION_FP64)
+    k_zero_row<double><<<1, 128, 0, st>>>(M->S + off, dm.n + 1, nullptr);
+  else
+    k_zero_row<float><<<1, 128, 0, st>>>(M->S32 + off, dm.n + 1, M->rhs64 + e * dm.n + M->fault.zero_row);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_scatter_K(iedg_mesh* M, double* K, cudaStream_t st) {
   const int64_t total = M->nnzb * M->dm.m * M->dm.m;

@@ -21,10 +21,12 @@ EXPORTS = ("iedg_create_mesh", "iedg_destroy_mesh", "iedg_last_error", "iedg_mes
            "iedg_profile_read", "iedg_profile_reset", "iedg_eval_residual_static", "iedg_get_schedule",
            "iedg_set_schedule", "iedg_trace_solve", "iedg_create_mesh_mixed", "iedg_element_sizes",
            "iedg_set_trace_precond", "iedg_bilu0_factor", "iedg_bilu0_apply", "iedg_trace_colors",
-           "iedg_create_mesh_bc")
+           "iedg_create_mesh_bc", "iedg_set_fault_injection")
 PREC_BLOCK_JACOBI, PREC_BILU0 = 0, 1
 # element-matrix precision of a handle (IEDG_PRECISION_*)
 PRECISION_FP64, PRECISION_MIXED, PRECISION_MIXED_TF32, PRECISION_MIXED_BF16 = 0, 1, 2, 3
+# per-element status codes (IEDG_ELEM_*)
+ELEM_OK, ELEM_REFINE, ELEM_SINGULAR, ELEM_NONFINITE, ELEM_TIMEOUT = 0, 1, 2, 3, 4
 
 
 class IedgError(RuntimeError):
@@ -45,6 +47,11 @@ class MeshDesc(ctypes.Structure):
 class Schedule(ctypes.Structure):
     _fields_ = [("lu_persistent", ctypes.c_int32), ("lu_panel", ctypes.c_int32), ("asm_chunk", ctypes.c_int32),
                 ("lu_tensor", ctypes.c_int32), ("asm_chunk_by_order", ctypes.c_int32 * 4)]
+
+
+class FaultInjection(ctypes.Structure):
+    _fields_ = [("zero_row_elem", ctypes.c_int64), ("zero_row", ctypes.c_int32), ("refine_iters", ctypes.c_int32),
+                ("tc_wait_limit", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -102,6 +109,8 @@ def load():
     lib.iedg_get_schedule.restype = ctypes.c_int
     lib.iedg_set_schedule.argtypes = [vp, ctypes.POINTER(Schedule)]
     lib.iedg_set_schedule.restype = ctypes.c_int
+    lib.iedg_set_fault_injection.argtypes = [vp, ctypes.POINTER(FaultInjection)]
+    lib.iedg_set_fault_injection.restype = ctypes.c_int
     lib.iedg_profile_enable.argtypes = [vp, i32]
     lib.iedg_profile_enable.restype = ctypes.c_int
     lib.iedg_profile_read.argtypes = [vp, i32, vp, vp, vp, ctypes.POINTER(i32)]
@@ -309,6 +318,12 @@ class Mesh:
         by = (ctypes.c_int32 * 4)(*cur.get("asm_chunk_by_order", [0, 0, 0, 0]))
         sc = Schedule(cur["lu_persistent"], cur["lu_panel"], cur["asm_chunk"], cur["lu_tensor"], by)
         self._check(load().iedg_set_schedule(self._h, ctypes.byref(sc)))
+
+    def set_fault_injection(self, zero_row_elem=-1, zero_row=0, refine_iters=-1, tc_wait_limit=0):
+        """Host-side fault injection for tests (iedg_set_fault_injection); the defaults
+        restore normal operation."""
+        f = FaultInjection(int(zero_row_elem), int(zero_row), int(refine_iters), int(tc_wait_limit), 0)
+        self._check(load().iedg_set_fault_injection(self._h, ctypes.byref(f)))
 
     # ------------------------------------------------------------------ tracing
     def profile_enable(self, enable=True):

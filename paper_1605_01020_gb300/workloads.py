@@ -186,10 +186,32 @@ def broadband_field(Minf, seed, rms=0.05, kmin=1, kmax=8, gamma=GAMMA):
     # per-component rms: <|v|^2> = scale^2 sum amp^2 / 2, shared by 3 components
     scale = rms / np.sqrt(np.sum(amp ** 2) / 6.0)
 
-    def f(x):
+    coef = (np.exp(1j * ph) * amp * scale)[:, None] * a        # complex amplitude of each wave
+    kint = ks.astype(np.int64) + kmax
+
+    def velocity(x):
+        """sum_k sin(2 pi k.x + phi_k) amp_k scale a_k.  Points on a tensor grid of
+        coordinates (structured meshes: few distinct values per direction) are summed
+        direction by direction as Im sum_k c_k e^(2 pi i kx x) e^(2 pi i ky y) e^(2 pi i kz z)
+        over the grid and gathered; other point sets are summed directly."""
+        pts = x.reshape(-1, 3)
+        uniq = [np.unique(pts[:, r]) for r in range(3)]
+        if np.prod([len(v) for v in uniq]) <= 8 * len(pts):
+            nk = 2 * kmax + 1
+            C = np.zeros((nk, nk, nk, 3), dtype=np.complex128)
+            C[kint[:, 0], kint[:, 1], kint[:, 2]] = coef
+            E = [np.exp(2j * np.pi * np.outer(v, np.arange(-kmax, kmax + 1))) for v in uniq]
+            G = np.einsum("ia,abcr->ibcr", E[0], C)
+            G = np.einsum("jb,ibcr->ijcr", E[1], G)
+            G = np.einsum("lc,ijcr->ijlr", E[2], G).imag
+            idx = [np.searchsorted(uniq[r], pts[:, r]) for r in range(3)]
+            return G[idx[0], idx[1], idx[2]].reshape(x.shape)
         arg = 2 * np.pi * np.einsum("...r,kr->...k", x, ks) + ph
         s = np.sin(arg) * amp * scale
-        vel = np.einsum("...k,kr->...r", s, a)
+        return np.einsum("...k,kr->...r", s, a)
+
+    def f(x):
+        vel = velocity(x)
         one = np.ones(x.shape[:-1])
         return conserved_from_primitive(one, [1.0 + vel[..., 0], vel[..., 1], vel[..., 2]],
                                         pinf * one, gamma)

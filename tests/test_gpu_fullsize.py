@@ -1,0 +1,150 @@
+"""Full-size parity of the two workloads whose device offsets pass 2^31 entries, in the
+launch configuration the benchmark times (persistent LU grid, default schedule):
+
+  - the mixed-order batch, 8192 hexes of orders 2/3/4 on a 16 x 16 x 32 periodic mesh
+    (FP64 bordered matrices: 6.7e9 doubles in one buffer);
+  - 24^3 hexes at p = 4 (FP64 bordered matrices 1.7e10 doubles, K 2.7e9 doubles).
+
+Sampled outputs are compared with the oracle one by one: the block rows of K and the
+entries of R of the last trace node and of trace nodes of the elements stored last,
+and the element updates du, dq of those elements (Sec. 2.2.1, Eq. LS; the
+back-substitution dZ = A^-1 (F - B dU)).  FP64 path 1e-11, mixed path K 1e-4 and
+R, du, dq 1e-10, as in the smaller parity tests."""
+import numpy as np
+import pytest
+
+from oracle import iedg as oiedg
+from oracle import physics
+from paper_1605_01020_gb300 import workloads as W
+from oracle_helpers import problem, ref_element
+from gpu_helpers import dev, host, rel_err
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-11
+TOL_MIXED_K = 1e-4
+TOL_MIXED = 1e-10
+
+
+def _free():
+    import gc
+    import torch
+    gc.collect()
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_mixed_orders_full_size_sampled(precision):
+    from paper_1605_01020_gb300 import iedg
+    wl = W.config(4)
+    msh, st, prm = wl.mesh, wl.state, wl.params
+    E, m = msh.n_elem, msh.d + 2
+    cat = lambda xs: dev(np.concatenate(xs))
+    lm = iedg.MixedOrderMesh(msh.node_xyz, msh.elem_trace, msh.n_trace, msh.orders, msh.face_degree,
+                             gamma=prm["gamma"], Pr=prm["Pr"], Re=prm["Re"], Minf=prm["Minf"], alpha=prm["alpha"],
+                             precision=precision)
+    K_d, R_d = lm.assemble_condensed(cat(st.u), cat(st.q), dev(st.uhat))
+    du_d, dq_d = lm.back_substitute(dev(st.duhat))
+    status = lm.element_status()
+    rp, col = (host(t) for t in lm.trace_pattern())
+    col = col.astype(np.int64)
+    # elements stored last: internal ids are grouped by order (ascending), user order
+    # within a group, so the last order-4 element sits at the largest matrix offset
+    last4 = int(np.flatnonzero(msh.orders == 4)[-1])
+    rows = sorted({msh.n_trace - 1, int(msh.elem_trace[last4][-1]), int(msh.elem_trace[last4][0])})
+    assert torch_isfinite(K_d)
+    K_rows = {r: host(K_d[rp[r]:rp[r + 1]]) for r in rows}
+    R_h, du_h, dq_h = host(R_d), host(du_d), host(dq_d)
+    lm.close()
+    del K_d, R_d, du_d, dq_d
+    _free()
+    assert (status == 0).all()
+    sample = sorted({last4, E - 1, int(np.flatnonzero(msh.orders == 2)[-1])})
+    refs = {int(p): ref_element(3, int(p)) for p in (2, 3, 4)}
+    pb = oiedg.MixedProblem(refs, msh, physics.Params(**{k: prm[k] for k in ("gamma", "Pr", "Re", "Minf", "alpha")}))
+    tk, tr = (TOL, TOL) if precision == 0 else (TOL_MIXED_K, TOL_MIXED)
+    off = np.concatenate([[0], np.cumsum([len(x) for x in msh.node_xyz])])
+    for e in sample:
+        du_o, dq_o = pb.back_substitute_qelim(e, st.u, st.q, st.uhat, st.duhat)
+        assert rel_err(du_h[off[e]:off[e + 1]], du_o) <= tr, e
+        assert rel_err(dq_h[off[e]:off[e + 1]], dq_o) <= tr, e
+    cache = {}
+    for r0 in rows:
+        els = [e for e in range(E) if r0 in set(msh.elem_trace[e].tolist())]
+        vals = np.zeros((rp[r0 + 1] - rp[r0], m, m))
+        rsum, rmax = np.zeros(m), 0.0
+        for e in els:
+            if e not in cache:
+                cache[e] = pb.condense_qelim(e, st.u, st.q, st.uhat)
+            Ke, Re = cache[e]
+            tr_e = msh.elem_trace[e].tolist()
+            s = tr_e.index(r0)
+            rsum += Re[s]
+            rmax = max(rmax, np.abs(Re).max())
+            for t in range(len(tr_e)):
+                k = int(np.searchsorted(col[rp[r0]:rp[r0 + 1]], tr_e[t]))
+                vals[k] += Ke[s, :, t, :]
+        got = K_rows[r0]
+        assert np.abs(got - vals).max() / np.abs(vals).max() <= tk, r0
+        assert rel_err(R_h[r0], rsum, floor=rmax) <= tr, r0
+    print(f"mixed orders 8192 precision {precision}: sampled elements {sample}, rows {rows} within "
+          f"{tk:.0e} / {tr:.0e}")
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_p4_24cube_full_size_sampled(precision):
+    from paper_1605_01020_gb300 import iedg
+    wl = W.config(5)
+    msh, st = wl.mesh, wl.state
+    E, m = msh.n_elem, msh.d + 2
+    mesh = iedg.mesh_from_workload(wl, precision=precision)
+    u, q, uh = dev(st.u), dev(st.q), dev(st.uhat)
+    K_d, R_d = mesh.assemble_condensed(u, q, uh)
+    du_d, dq_d = mesh.back_substitute(dev(st.duhat))
+    status = mesh.element_status()
+    last = [E - 1, E - 2]
+    rows = [msh.n_trace - 1, int(msh.elem_trace[E - 1][0]), int(msh.elem_trace[E - 1][-1])]
+    rp_d, col_d = mesh.trace_pattern()
+    rp = host(rp_d)
+    # copy only what is compared: the sampled block rows and elements
+    K_rows = {r: host(K_d[rp[r]:rp[r + 1]]) for r in rows}
+    col_rows = {r: host(col_d[rp[r]:rp[r + 1]]).astype(np.int64) for r in rows}
+    R_h = host(R_d)
+    du_h = {e: host(du_d[e]) for e in last}
+    dq_h = {e: host(dq_d[e]) for e in last}
+    assert rp[-1] == rp[msh.n_trace] and rp[msh.n_trace] * m * m > 2 ** 31
+    assert torch_isfinite(K_d)
+    mesh.close()
+    del K_d, R_d, du_d, dq_d, u, q, uh, rp_d, col_d
+    _free()
+    assert (status == 0).all()
+    pb = problem(msh, wl.params)
+    tk, tr = (TOL, TOL) if precision == 0 else (TOL_MIXED_K, TOL_MIXED)
+    cache = {}
+    for r0 in rows:
+        els = [e for e in range(E) if r0 in set(msh.elem_trace[e].tolist())]
+        cols = np.unique(np.concatenate([msh.elem_trace[e] for e in els]))
+        assert np.array_equal(cols, col_rows[r0]), r0          # pattern of the row, bit-exact
+        vals = np.zeros((len(cols), m, m))
+        rsum, rmax = np.zeros(m), 0.0
+        for e in els:
+            if e not in cache:
+                cache[e] = pb.condense_qelim(e, st.u, st.q, st.uhat)
+            Ke, Re = cache[e]
+            tr_e = msh.elem_trace[e].tolist()
+            s = tr_e.index(r0)
+            rsum += Re[s]
+            rmax = max(rmax, np.abs(Re).max())
+            for t in range(len(tr_e)):
+                vals[int(np.searchsorted(cols, tr_e[t]))] += Ke[s, :, t, :]
+        assert np.abs(K_rows[r0] - vals).max() / np.abs(vals).max() <= tk, r0
+        assert rel_err(R_h[r0], rsum, floor=rmax) <= tr, r0
+    for e in last:
+        du_o, dq_o = pb.back_substitute_qelim(e, st.u, st.q, st.uhat, st.duhat)
+        assert rel_err(du_h[e], du_o) <= tr, e
+        assert rel_err(dq_h[e], dq_o) <= tr, e
+    print(f"24^3 p=4 precision {precision}: rows {rows}, elements {last} within {tk:.0e} / {tr:.0e}")
+
+
+def torch_isfinite(t):
+    import torch
+    return torch.isfinite(t).all().item()

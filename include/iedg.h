@@ -69,6 +69,13 @@ extern "C" {
 #define IEDG_ELEM_TIMEOUT   4   /* tensor-core forms: a bounded completion wait gave up
                                    (see iedg_set_fault_injection); the element was not
                                    factored                                         */
+#define IEDG_ELEM_FALLBACK  5   /* mixed forms: the element's refinement did not reach
+                                   1e-10, its tensor-core wait gave up or its FP32 LU
+                                   met a zero pivot, and it was condensed again in FP64
+                                   in the same call (K_e, R_e and its updates are the
+                                   FP64 path's).  At most 32 elements per call, lowest
+                                   ids first, get this; the others keep their flag.
+                                   Uniform meshes only.                              */
 
 #define IEDG_PRECISION_FP64  0   /* every step in FP64                                   */
 #define IEDG_PRECISION_MIXED 1   /* element matrix and partial LU in FP32 (K to FP32

@@ -22,8 +22,9 @@ def mesh_key(mesh, precision, gpu_name):
 def candidates(precision, order):
     """Candidate schedules: persistent LU on/off x FP64 panel 16/32 x assembly chunk,
     and the tensor-core forms (the FP64 Schur complement by exact operand splitting;
-    the FP32 LU's Schur complement in 3xTF32 on the mixed path; handles with TF32 or
-    BF16 Schur operands always take the tensor-core form).
+    on the mixed path the FP32 LU with every trailing update in 3xTF32, or only its
+    deferred Schur complement; handles with TF32 or BF16 Schur operands always take
+    the tensor-core form).
     order 0 (mixed orders): the FP64 panel stays 16 (the largest elements' panel of
     32 does not fit in shared memory)."""
     panels = [16, 32] if (precision == 0 and 1 <= order <= 3) else [16]
@@ -33,8 +34,10 @@ def candidates(precision, order):
         out = [dict(lu_persistent=a, lu_panel=b, asm_chunk=c, lu_tensor=0)
                for a, b, c in itertools.product([1, 0], panels, chunks)]
         return out + [dict(lu_persistent=1, lu_panel=16, asm_chunk=c, lu_tensor=1) for c in chunks]
-    # TF32 / BF16 Schur operands: the tensor-core form is what the precision means
-    tensor = [1, 0] if precision == 1 else [1]
+    # TF32 / BF16 Schur operands: the tensor-core form is what the precision means.
+    # FP32 form: every trailing update on the tensor cores (2), the deferred Schur
+    # complement on the tensor cores (1), or FFMA updates (0)
+    tensor = [2, 1, 0] if precision == 1 else [1]
     return [dict(lu_persistent=a, lu_panel=b, asm_chunk=c, lu_tensor=t)
             for a, b, c, t in itertools.product([1, 0], panels, chunks, tensor)]
 

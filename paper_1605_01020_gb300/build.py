@@ -46,7 +46,24 @@ def build(verbose=False, extra=()):
     if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
         cmd = [nvcc, *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"]
         subprocess.run(cmd, check=True)
+    build_probes(verbose)
     return LIB
+
+
+PROBES = os.path.join(HERE, "probes")
+PROBE_LIB = os.path.join(HERE, "libiedg_probes.so")
+
+
+def build_probes(verbose=False):
+    """The peak-throughput probes (probes/*.cu) as their own small library."""
+    srcs = sorted(os.path.join(PROBES, f) for f in os.listdir(PROBES) if f.endswith(".cu"))
+    if os.path.exists(PROBE_LIB) and os.path.getmtime(PROBE_LIB) >= max(os.path.getmtime(s) for s in srcs):
+        return PROBE_LIB
+    cmd = [_nvcc(), *ARCH, *FLAGS, "-shared", "-o", PROBE_LIB, *srcs, "-lcudart"]
+    if verbose:
+        print(" ".join(cmd), file=sys.stderr)
+    subprocess.run(cmd, check=True)
+    return PROBE_LIB
 
 
 if __name__ == "__main__":

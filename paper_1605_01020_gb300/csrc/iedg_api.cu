@@ -432,6 +432,14 @@ static int alloc_owner(iedg_mesh* M, int64_t S_elems, int64_t piv_elems, int64_t
   CUDA_TRY(dalloc(M, &M->rhat, (size_t)rhat_elems));
   CUDA_TRY(dalloc(M, &M->re64, (size_t)re_elems));
   CUDA_TRY(dalloc(M, &M->status, E));
+  if (M->precision != IEDG_PRECISION_FP64 && !M->mixed_orders) {
+    CUDA_TRY(dalloc(M, &M->fb_S, (size_t)kFallbackSlots * M->dm.n * M->dm.ld));
+    CUDA_TRY(dalloc(M, &M->fb_list, kFallbackSlots));
+    CUDA_TRY(dalloc(M, &M->fb_slot, (size_t)E));
+    CUDA_TRY(dalloc(M, &M->fb_status, kFallbackSlots));
+    CUDA_TRY(dalloc(M, &M->fb_count, 1));
+    CUDA_TRY(cudaMemsetAsync(M->fb_count, 0, sizeof(int), st));
+  }
   if (!M->dev_flag) CUDA_TRY(dalloc(M, &M->dev_flag, 1));
   CUDA_TRY(dalloc(M, &M->queue, 1));
   CUDA_TRY(dalloc(M, &M->kry, (size_t)(IEDG_MAX_RESTART + 3) * T * m));
@@ -579,6 +587,7 @@ static int create_mixed_impl(const iedg_mesh_desc* D, const int32_t* ord, const 
   const int d = D->dim, nf = 2 * d, m = d + 2;
   const int64_t E = M->E;
   const int pmax_allowed = d == 3 ? 4 : 3;
+  M->mixed_orders = true;   // parent of per-order groups (set before its workspace is sized)
   for (int64_t e = 0; e < E; ++e) {
     if (ord[e] < 1 || ord[e] > pmax_allowed) return fail(M, IEDG_ERR_UNSUPPORTED, "element order out of range");
     for (int f = 0; f < nf; ++f) {
@@ -855,7 +864,6 @@ static int create_mixed_impl(const iedg_mesh_desc* D, const int32_t* ord, const 
     rc2 = run_geometry(C, X.data(), st);
     if (rc2 != IEDG_OK) return fail(M, rc2, C->err);
   }
-  M->mixed_orders = true;
   return IEDG_OK;
 }
 
@@ -1062,7 +1070,10 @@ extern "C" int iedg_assemble_condensed(iedg_mesh* M, const double* u, const doub
     CUDA_TRY(TRACED("assemble", launch_assemble(M, st)));
   if (M->fault.zero_row_elem >= 0) CUDA_TRY(TRACED("fault_zero_row", launch_zero_row(M, st)));
   CUDA_TRY(TRACED("lu_schur", launch_lu(M, st)));
-  if (M->precision != IEDG_PRECISION_FP64) CUDA_TRY(TRACED("refine", launch_refine(M, st)));
+  if (M->precision != IEDG_PRECISION_FP64) {
+    CUDA_TRY(TRACED("refine", launch_refine(M, st)));
+    CUDA_TRY(TRACED("fallback_fp64", launch_fallback(M, st)));
+  }
   CUDA_TRY(TRACED("scatter_K", launch_scatter_K(M, K, st)));
   if (M->precision == IEDG_PRECISION_FP64)
     CUDA_TRY(TRACED("scatter_R", launch_scatter_R(M, M->S + (int64_t)dm.nu * dm.ld + dm.n, (int64_t)dm.n * dm.ld,
@@ -1079,10 +1090,15 @@ extern "C" int iedg_back_substitute(iedg_mesh* M, const double* duhat, double* d
   if (!M->assembled) return fail(M, IEDG_ERR_NOT_ASSEMBLED, "back-substitution before assembly");
   cudaStream_t st = (cudaStream_t)stream;
   if (M->mixed_orders) return backsub_mixed_orders(M, duhat, du, dq, st);
-  if (M->precision == IEDG_PRECISION_FP64)
+  if (M->precision == IEDG_PRECISION_FP64) {
     CUDA_TRY(TRACED("backsub", launch_backsub(M, duhat, du, dq, st)));
-  else
+  } else {
     CUDA_TRY(TRACED("backsub", launch_backsub_mixed(M, duhat, du, dq, st)));
+    // elements condensed again in FP64 take their updates from the FP64 factors
+    if (M->fb_S)
+      CUDA_TRY(TRACED("backsub_fp64_fallback",
+                      launch_backsub_list(M, M->fb_S, M->fb_list, kFallbackSlots, duhat, du, dq, st)));
+  }
   return IEDG_OK;
 }
 
@@ -1163,7 +1179,7 @@ extern "C" int iedg_set_schedule(iedg_mesh* M, const iedg_schedule* in) {
   if (!M || !in) return fail(M, IEDG_ERR_INVALID_ARG, "null argument");
   if ((in->lu_persistent != 0 && in->lu_persistent != 1) || (in->lu_panel != 16 && in->lu_panel != 32) ||
       (in->asm_chunk != 0 && in->asm_chunk != 8 && in->asm_chunk != 16 && in->asm_chunk != 32) ||
-      (in->lu_tensor != 0 && in->lu_tensor != 1))
+      (in->lu_tensor < 0 || in->lu_tensor > 2) || (in->lu_tensor == 2 && M->precision == IEDG_PRECISION_FP64))
     return fail(M, IEDG_ERR_INVALID_ARG, "schedule values out of range");
   for (int i = 0; i < 4; ++i) {
     const int c = in->asm_chunk_by_order[i];

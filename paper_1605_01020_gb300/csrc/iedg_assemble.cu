@@ -20,6 +20,7 @@
 #include <cuda_bf16.h>
 
 #include "iedg_internal.cuh"
+#include "iedg_lu_common.cuh"
 #include "iedg_tc.cuh"
 
 namespace iedg {
@@ -59,12 +60,16 @@ AsmCfg asm_cfg(const Dims& dm) {
 template <class T>
 __global__ void __launch_bounds__(AS_THREADS)
 k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, AsmTab<T> tb, T* __restrict__ S,
-           const double* __restrict__ rhs64, TraceTab tt, int NbU) {
+           const double* __restrict__ rhs64, TraceTab tt, int NbU, const int64_t* __restrict__ elist) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
   const int tid = threadIdx.x;
   const int m2 = dm.m * dm.m;
-  const int64_t e = blockIdx.x / m2;                 // the m^2 CTAs of an element are adjacent
+  // the m^2 CTAs of an element are adjacent; with an element list (FP64 fallback of the
+  // mixed path) CTA group `slot` assembles element elist[slot] into matrix slot `slot`
+  const int64_t slot = blockIdx.x / m2;
+  const int64_t e = elist ? elist[slot] : slot;
+  if (e < 0) return;
   const int pair = blockIdx.x % m2, i = pair / dm.m, k = pair % dm.m;
   const int c0 = blockIdx.y * cf.CW;
   const int d = dm.d, Np = dm.Np, Nq = dm.Nq, Nfp = dm.Nfp, Nfq = dm.Nfq, Nfn = dm.Nfn;
@@ -227,7 +232,7 @@ k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, AsmTab<T> tb, T* __restri
   // ---- write the element rows
   const int64_t nn = mix ? (int64_t)dm.nu + (int64_t)dm.m * Nb : dm.n;
   const int64_t ld = mix ? tt.ldv[e] : dm.ld;
-  T* Se = mix ? S + tt.soff[e] : S + e * nn * ld;
+  T* Se = mix ? S + tt.soff[e] : S + slot * nn * ld;
   if (rhs64 != nullptr && pair == 0 && blockIdx.y == 0)
     for (int r = tid; r < nn; r += AS_THREADS) Se[r * ld + nn] = (T)rhs64[e * dm.n + r];
   auto colS = [&](int col) -> int64_t { return col < Np ? (int64_t)k * Np + col : (int64_t)dm.nu + (int64_t)k * Nb + (col - Np); };
@@ -265,38 +270,6 @@ k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, AsmTab<T> tb, T* __restri
 // T = float (mixed path) additionally writes back every panel in full (the
 // multipliers L, in the row order of their own panel step) and the pivot rows, for
 // the refinement solves.
-constexpr int LU_THREADS = 256;
-constexpr int UCW = 64;     // trailing-update column chunk
-constexpr int LU_MAX_NU = 640;   // u-unknowns of the largest element (5 x 125 at p = 4)
-
-// Tensor-core state of a CTA (deferred Schur complement forms of the LU).
-struct TcState {
-  uint32_t tmem;        // TMEM base
-  uint64_t* mbar;       // MMA completion barriers (one per operand stage)
-  uint32_t phase[2];    // parity of each barrier's next completion
-  int failed;           // a completion wait ran out
-  int limit;            // polls of a completion wait before it gives up (0: gives up at once)
-  int pending[2];       // a commit on barrier b has not been waited for yet
-};
-
-// Drain after a failed wait: the MMAs still in flight complete (bounded, full limit)
-// before the CTA frees its TMEM; barriers with no commit outstanding are skipped.
-__device__ __forceinline__ void tc_drain(const TcState& t) {
-  for (int b = 0; b < 2; ++b)
-    if (t.pending[b]) tc::mbar_wait(t.mbar + b, t.phase[b], kTcWaitLimit);
-}
-
-// Sizes and location of one element's bordered matrix.
-struct LuElem {
-  int n, nu, ld;
-  int64_t off, poff;
-};
-
-__device__ __forceinline__ LuElem lu_elem(const Dims& dm, const LuDesc& lud, int64_t e) {
-  if (lud.soff) return LuElem{lud.n[e], lud.nu[e], lud.ld[e], lud.soff[e], lud.poff ? lud.poff[e] : 0};
-  return LuElem{dm.n, dm.nu, dm.ld, e * (int64_t)dm.n * dm.ld, e * (int64_t)dm.nu};
-}
-
 // A[r][c] -= sum_j L[r][j] U[j][c] over rows [r_lo, r_hi), cols [c_lo, c_hi): L from the
 // row-major panel P (row r at P[(r - kb) NB + j]), U = rows kb..kb+nb of A, staged by
 // UCW-column chunks in Uc; 16 x 16 threads with 4 x 4 register tiles.
@@ -1101,32 +1074,13 @@ __device__ __forceinline__ void lu32_element(const LuElem& el, float* __restrict
   }
 }
 
-// Element scheduling of the batched LU.  queue == nullptr: one CTA per element.
-// Otherwise a persistent grid (a few CTAs per SM) takes elements from an atomic
-// counter in order, so no SM idles in a partial last wave.
-// With an order list the k-th element taken is order[k].
-__device__ __forceinline__ bool next_element(int64_t* queue, int64_t E, int64_t it, const int64_t* order,
-                                             int64_t* e_out) {
-  __shared__ unsigned long long s_next;
-  if (queue == nullptr) {
-    *e_out = order ? order[blockIdx.x] : (int64_t)blockIdx.x;
-    return it == 0;
-  }
-  if (threadIdx.x == 0) s_next = atomicAdd(reinterpret_cast<unsigned long long*>(queue), 1ull);
-  __syncthreads();
-  const int64_t k = (int64_t)s_next;
-  __syncthreads();
-  *e_out = (order && k < E) ? order[k] : k;
-  return k < E;
-}
-
 template <class T, int NB>
 __global__ void __launch_bounds__(LU_THREADS)
 k_lu(Dims dm, LuDesc lud, T* __restrict__ S, int8_t* __restrict__ status, int* __restrict__ pivots, int64_t* queue,
-     int64_t E) {
+     int64_t E, const int64_t* __restrict__ active = nullptr) {
   int64_t e;
   for (int64_t it = 0; next_element(queue, E, it, lud.order, &e); ++it)
-    lu_element<T, NB>(lu_elem(dm, lud, e), S, status, pivots, e);
+    if (active == nullptr || active[e] >= 0) lu_element<T, NB>(lu_elem(dm, lud, e), S, status, pivots, e);
 }
 
 __global__ void __launch_bounds__(LU_THREADS, 2)
@@ -1269,6 +1223,8 @@ k_lu64_oz(Dims dm, LuDesc lud, double* __restrict__ S, int8_t* __restrict__ stat
 
 }  // namespace
 
+size_t lu64_smem(const Dims& dm, int nb);
+
 template <class T>
 static cudaError_t assemble_t(iedg_mesh* M, T* S, const double* rhs64, const AsmTab<T>& tb, cudaStream_t st) {
   const Dims& dm = M->dm;
@@ -1282,7 +1238,7 @@ static cudaError_t assemble_t(iedg_mesh* M, T* S, const double* rhs64, const Asm
   cudaError_t err = cudaFuncSetAttribute(k_assemble<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   dim3 grid((unsigned)(M->E * dm.m * dm.m), cf.nsplit);
-  k_assemble<T><<<grid, AS_THREADS, smem, st>>>(dm, M->ph, cf, M->ref, tb, S, rhs64, M->tt, nbu);
+  k_assemble<T><<<grid, AS_THREADS, smem, st>>>(dm, M->ph, cf, M->ref, tb, S, rhs64, M->tt, nbu, nullptr);
   return cudaGetLastError();
 }
 
@@ -1300,27 +1256,37 @@ AsmTab<float> tables32(const iedg_mesh* M) {
                        G.GlV32, G.HlV32, G.GlF32, G.HlF32, G.Mass32};
 }
 
+cudaError_t launch_assemble_list(iedg_mesh* M, double* S, const int64_t* elist, int64_t n_slots, cudaStream_t st) {
+  const Dims& dm = M->dm;
+  if (assemble_sf_supported(dm)) return launch_assemble_sf_list(M, S, elist, n_slots, st);
+  AsmCfg cf = asm_cfg(dm);
+  int inner = 1;
+  for (int r = 0; r < dm.d; ++r) inner *= dm.p - 1;
+  const int nbu = dm.Np - inner;
+  size_t smem = sizeof(double) * ((size_t)cf.KC * cf.rows_pad + (size_t)cf.KC * cf.CW + (size_t)nbu * cf.CW +
+                                  (size_t)dm.Nfq * cf.CW);
+  cudaError_t err = cudaFuncSetAttribute(k_assemble<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  dim3 grid((unsigned)(n_slots * dm.m * dm.m), cf.nsplit);
+  k_assemble<double><<<grid, AS_THREADS, smem, st>>>(dm, M->ph, cf, M->ref, tables64(M), S, M->rhs64, M->tt, nbu,
+                                                     elist);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lu64_list(iedg_mesh* M, double* S, int64_t n_slots, const int64_t* active, int8_t* status,
+                             cudaStream_t st) {
+  const Dims& dm = M->dm;
+  size_t smem = lu64_smem(dm, 16);
+  cudaError_t err = cudaFuncSetAttribute(k_lu<double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  k_lu<double, 16><<<(unsigned)n_slots, LU_THREADS, smem, st>>>(dm, LuDesc{}, S, status, nullptr, nullptr, n_slots,
+                                                                active);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_assemble(iedg_mesh* M, cudaStream_t st) {
   if (M->precision == 0) return assemble_t<double>(M, M->S, nullptr, tables64(M), st);
   return assemble_t<float>(M, M->S32, M->rhs64, tables32(M), st);
-}
-
-// Grid of the persistent form: resident CTAs per SM x SMs (never more than E).  The
-// kernel asks for the largest shared-memory carveout first, so the occupancy query
-// sees the split the launch will get.
-template <class K>
-static cudaError_t persistent_grid(K kern, size_t smem, int64_t E, unsigned* grid, int max_per_sm = 64) {
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                         (int)cudaSharedmemCarveoutMaxShared);
-  if (err == cudaSuccess) err = cudaGetDevice(&dev);
-  if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, LU_THREADS, smem);
-  if (err != cudaSuccess) return err;
-  if (per_sm > max_per_sm) per_sm = max_per_sm;
-  int64_t g = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
-  *grid = (unsigned)(g < E ? g : E);
-  return cudaSuccess;
 }
 
 template <class T, int NB>
@@ -1423,6 +1389,7 @@ cudaError_t launch_lu(iedg_mesh* M, cudaStream_t st) {
   }
   if (M->schur_in == kSchurTf32) return lu32_tc<kSchurTf32>(M, st);
   if (M->schur_in == kSchurBf16) return lu32_tc<kSchurBf16>(M, st);
+  if (M->sched.lu_tensor == 2) return launch_lu32_mma(M, M->dm.n, st);
   if (M->sched.lu_tensor) return lu32_tc<kSchurFp32>(M, st);
   const Dims& dm = M->dm;
   size_t smem = sizeof(float) * ((size_t)L32_NB * dm.n + (size_t)L32_NB * L32_UCW);

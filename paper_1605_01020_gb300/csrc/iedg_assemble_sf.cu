@@ -48,7 +48,7 @@ size_t sf_smem(const Dims& dm, bool mix) {
 template <class T, int NP1, int NQ1, int CC, bool MIX>
 __global__ void __launch_bounds__(SF_THREADS)
 k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, const double* __restrict__ rhs64,
-              TraceTab tt) {
+              TraceTab tt, const int64_t* __restrict__ elist) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
   const int tid = threadIdx.x;
@@ -58,7 +58,11 @@ k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, 
   constexpr int NbU = Np - (NP1 - 2) * (NP1 - 2) * (NP1 - 2), Nfp = 6 * Nfq;
   constexpr int TS = nq1 * nq1 * np1, VS = nq1 * np1 * np1, NC = (1 + d) * d;
   constexpr int UW = MIX ? 5 : np1;              // second extent of the face stage buffer
-  const int64_t e = blockIdx.x / m2;
+  // with an element list (FP64 fallback of the mixed path) CTA group `slot` assembles
+  // element elist[slot] into matrix slot `slot`
+  const int64_t slot = blockIdx.x / m2;
+  const int64_t e = elist ? elist[slot] : slot;
+  if (e < 0) return;
   const int pair = blockIdx.x % m2, i = pair / m, k = pair % m;
   const bool has_cq = !(i == 0 || (i <= d && k == m - 1));
   const int Nb = MIX ? tt.nb[e] : NbU;          // trace slots of this element
@@ -107,7 +111,7 @@ k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, 
   const T alpha = (T)ph.alpha;
   const int64_t nn = MIX ? (int64_t)dm.nu + (int64_t)m * Nb : dm.n;
   const int64_t ld = MIX ? tt.ldv[e] : dm.ld;
-  T* Se = MIX ? S + tt.soff[e] : S + e * nn * ld;
+  T* Se = MIX ? S + tt.soff[e] : S + slot * nn * ld;
   if (rhs64 != nullptr && pair == 0)
     for (int r = tid; r < nn; r += SF_THREADS) Se[r * ld + nn] = (T)rhs64[e * dm.n + r];
   __syncthreads();
@@ -302,14 +306,16 @@ k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, 
 }  // namespace
 
 template <class T, int NP1, int NQ1, int CC>
-static cudaError_t assemble_sf_t(iedg_mesh* M, T* S, const double* rhs64, const AsmTab<T>& tb, cudaStream_t st) {
+static cudaError_t assemble_sf_t(iedg_mesh* M, T* S, const double* rhs64, const AsmTab<T>& tb, cudaStream_t st,
+                                 const int64_t* elist, int64_t n_slots) {
   const Dims& dm = M->dm;
   const bool mix = M->tt.nb != nullptr;
   size_t smem = sf_smem<T, CC>(dm, mix);
   auto kern = mix ? k_assemble_sf<T, NP1, NQ1, CC, true> : k_assemble_sf<T, NP1, NQ1, CC, false>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  kern<<<(unsigned)(M->E * dm.m * dm.m), SF_THREADS, smem, st>>>(dm, M->ph, M->ref, tb, S, rhs64, M->tt);
+  const int64_t E = elist ? n_slots : M->E;
+  kern<<<(unsigned)(E * dm.m * dm.m), SF_THREADS, smem, st>>>(dm, M->ph, M->ref, tb, S, rhs64, M->tt, elist);
   return cudaGetLastError();
 }
 
@@ -317,22 +323,25 @@ static cudaError_t assemble_sf_t(iedg_mesh* M, T* S, const double* rhs64, const 
 // (more CTAs per SM) and 16 for FP32; a chunk whose shared memory does not fit
 // falls back to 8
 template <class T, int NP1, int NQ1>
-static cudaError_t assemble_sf_c(iedg_mesh* M, T* S, const double* rhs64, const AsmTab<T>& tb, cudaStream_t st) {
+static cudaError_t assemble_sf_c(iedg_mesh* M, T* S, const double* rhs64, const AsmTab<T>& tb, cudaStream_t st,
+                                 const int64_t* elist, int64_t n_slots) {
   int cc = M->sched.asm_chunk ? M->sched.asm_chunk : (sizeof(T) == 8 ? 8 : 16);
+  if (sizeof(T) == 8 && M->precision != 0) cc = 8;   // FP64 fallback of a mixed handle: the FP64 default
   const bool mix = M->tt.nb != nullptr;
   if (cc == 32 && sf_smem<T, 32>(M->dm, mix) > 227 * 1024) cc = 16;
   if (cc == 16 && sf_smem<T, 16>(M->dm, mix) > 227 * 1024) cc = 8;
-  if (cc == 32) return assemble_sf_t<T, NP1, NQ1, 32>(M, S, rhs64, tb, st);
-  if (cc == 16) return assemble_sf_t<T, NP1, NQ1, 16>(M, S, rhs64, tb, st);
-  return assemble_sf_t<T, NP1, NQ1, 8>(M, S, rhs64, tb, st);
+  if (cc == 32) return assemble_sf_t<T, NP1, NQ1, 32>(M, S, rhs64, tb, st, elist, n_slots);
+  if (cc == 16) return assemble_sf_t<T, NP1, NQ1, 16>(M, S, rhs64, tb, st, elist, n_slots);
+  return assemble_sf_t<T, NP1, NQ1, 8>(M, S, rhs64, tb, st, elist, n_slots);
 }
 
 template <class T>
-static cudaError_t assemble_sf_p(iedg_mesh* M, T* S, const double* rhs64, const AsmTab<T>& tb, cudaStream_t st) {
+static cudaError_t assemble_sf_p(iedg_mesh* M, T* S, const double* rhs64, const AsmTab<T>& tb, cudaStream_t st,
+                                 const int64_t* elist = nullptr, int64_t n_slots = 0) {
   switch (M->dm.p) {
-    case 2: return assemble_sf_c<T, 3, 4>(M, S, rhs64, tb, st);
-    case 3: return assemble_sf_c<T, 4, 5>(M, S, rhs64, tb, st);
-    default: return assemble_sf_c<T, 5, 6>(M, S, rhs64, tb, st);
+    case 2: return assemble_sf_c<T, 3, 4>(M, S, rhs64, tb, st, elist, n_slots);
+    case 3: return assemble_sf_c<T, 4, 5>(M, S, rhs64, tb, st, elist, n_slots);
+    default: return assemble_sf_c<T, 5, 6>(M, S, rhs64, tb, st, elist, n_slots);
   }
 }
 
@@ -343,6 +352,10 @@ bool assemble_sf_supported(const Dims& dm) {
 cudaError_t launch_assemble_sf(iedg_mesh* M, cudaStream_t st) {
   if (M->precision == 0) return assemble_sf_p<double>(M, M->S, nullptr, tables64(M), st);
   return assemble_sf_p<float>(M, M->S32, M->rhs64, tables32(M), st);
+}
+
+cudaError_t launch_assemble_sf_list(iedg_mesh* M, double* S, const int64_t* elist, int64_t n_slots, cudaStream_t st) {
+  return assemble_sf_p<double>(M, S, M->rhs64, tables64(M), st, elist, n_slots);
 }
 
 }  // namespace iedg

@@ -37,7 +37,8 @@ struct Schedule {
   int lu_persistent = 1;     // batched LU as a persistent grid with an element queue
   int lu_panel = 16;         // FP64 LU panel width (16 or 32; 32 only when it fits shared memory)
   int asm_chunk = 0;         // assembly column chunk (0 = default: 8 for FP64, 16 for FP32)
-  int lu_tensor = 1;         // FP32 LU trailing update on tcgen05 (3xTF32) instead of FFMA
+  int lu_tensor = 1;         // 0 = DFMA / FFMA updates; 1 = deferred Schur complement on tcgen05;
+                             // 2 (mixed FP32 form) = every trailing update on tcgen05 (3xTF32)
   int asm_chunk_by_order[4] = {0, 0, 0, 0};   // mixed orders: chunk per order (0 = asm_chunk)
 };
 
@@ -177,6 +178,13 @@ struct iedg_mesh {
   double* y64 = nullptr;        // [E][nu]       refined A~^-1 F~
   double* re64 = nullptr;       // [E][m][Nb]    refined R_e (component-major)
   int8_t* status = nullptr;     // [E]
+  // FP64 fallback of the mixed forms (uniform meshes): kFallbackSlots FP64 element
+  // matrices and the slot bookkeeping (iedg_fallback.cu)
+  double* fb_S = nullptr;       // [slots][n][ld]
+  int64_t* fb_list = nullptr;   // [slots] element of each slot, -1 = empty
+  int* fb_slot = nullptr;       // [E]     slot of each element, -1 = none
+  int8_t* fb_status = nullptr;  // [slots] status of the FP64 partial LU
+  int* fb_count = nullptr;      // slots in use
   int64_t* queue = nullptr;     // element counter of persistent launches
   float* oz_scratch = nullptr;  // FP64 tensor-core Schur form: per-CTA slice buffers (freed with the handle)
   unsigned oz_grid = 0;
@@ -244,6 +252,7 @@ AsmTab<double> tables64(const iedg_mesh* M);
 AsmTab<float> tables32(const iedg_mesh* M);
 cudaError_t launch_lu(iedg_mesh* M, cudaStream_t st);
 cudaError_t prepare_lu64_oz(iedg_mesh* M);   // slice buffers of the FP64 tensor-core Schur form
+cudaError_t launch_lu32_mma(iedg_mesh* M, int n_max, cudaStream_t st);   // FP32 LU, tcgen05 trailing updates
 cudaError_t launch_scatter_K(iedg_mesh* M, double* K, cudaStream_t st);
 cudaError_t launch_scatter_R_ragged(iedg_mesh* M, const RaggedSrc& src, const double* base, double* R,
                                     cudaStream_t st);
@@ -256,6 +265,16 @@ cudaError_t launch_scatter_R(iedg_mesh* M, const double* src, int64_t src_elem_s
 cudaError_t launch_backsub(iedg_mesh* M, const double* duhat, double* du, double* dq,
                            cudaStream_t st);
 cudaError_t launch_refine(iedg_mesh* M, cudaStream_t st);
+// FP64 fallback of flagged elements on the mixed path (iedg_fallback.cu)
+constexpr int kFallbackSlots = 32;
+cudaError_t launch_fallback(iedg_mesh* M, cudaStream_t st);
+cudaError_t launch_assemble_list(iedg_mesh* M, double* S, const int64_t* elist, int64_t n_slots, cudaStream_t st);
+cudaError_t launch_assemble_sf_list(iedg_mesh* M, double* S, const int64_t* elist, int64_t n_slots, cudaStream_t st);
+cudaError_t launch_lu64_list(iedg_mesh* M, double* S, int64_t n_slots, const int64_t* active, int8_t* status,
+                             cudaStream_t st);
+cudaError_t launch_zero_row_fallback(iedg_mesh* M, cudaStream_t st);
+cudaError_t launch_backsub_list(iedg_mesh* M, const double* S, const int64_t* elist, int64_t n_slots,
+                                const double* duhat, double* du, double* dq, cudaStream_t st);
 cudaError_t launch_zero_row(iedg_mesh* M, cudaStream_t st);   // Fault.zero_row_elem
 cudaError_t launch_backsub_mixed(iedg_mesh* M, const double* duhat, double* du, double* dq,
                                  cudaStream_t st);

@@ -10,10 +10,13 @@ namespace {
 // One thread per (block, i, k) entry; S is the FP64 or the FP32 element matrix.
 // Contributions are packed as (e P + s) P + t, P = Nb (uniform meshes) or the slot
 // stride of meshes with mixed orders, whose matrices have per-element sizes (lud).
+// With an FP64 fallback in use (fb_count > 0), elements that have a slot contribute
+// their FP64 block from the slot matrices fbS instead.
 template <class T>
 __global__ void k_scatter_K(Dims dm, int64_t nnzb, int64_t P, const int64_t* __restrict__ kc_ptr,
                             const int64_t* __restrict__ kc_src, LuDesc lud, const int* __restrict__ nbv,
-                            const T* __restrict__ S, double* __restrict__ K) {
+                            const T* __restrict__ S, double* __restrict__ K, const int* __restrict__ fb_slot,
+                            const double* __restrict__ fbS, const int* __restrict__ fb_count) {
   const int m2 = dm.m * dm.m;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= nnzb * m2) return;
@@ -23,10 +26,13 @@ __global__ void k_scatter_K(Dims dm, int64_t nnzb, int64_t P, const int64_t* __r
   if (lud.soff == nullptr) {
     const int64_t Nb = dm.Nb, nb2 = Nb * Nb, ld = dm.ld, n = dm.n;
     const int64_t row_off = dm.nu + (int64_t)i * Nb, col_off = dm.nu + (int64_t)k * Nb;
+    const bool fb = fb_count != nullptr && *fb_count > 0;
     for (int64_t c = kc_ptr[blk]; c < kc_ptr[blk + 1]; ++c) {
       int64_t src = kc_src[c];
       int64_t e = src / nb2, s = (src / Nb) % Nb, t = src % Nb;
-      v += (double)S[(e * n + row_off + s) * ld + col_off + t];
+      const int sl = fb ? fb_slot[e] : -1;
+      v += sl >= 0 ? fbS[((int64_t)sl * n + row_off + s) * ld + col_off + t]
+                   : (double)S[(e * n + row_off + s) * ld + col_off + t];
     }
   } else {
     for (int64_t c = kc_ptr[blk]; c < kc_ptr[blk + 1]; ++c) {
@@ -99,15 +105,19 @@ constexpr int BS_THREADS = 256;
 __global__ void __launch_bounds__(BS_THREADS)
 k_backsub(Dims dm, Geo G, const int64_t* __restrict__ etrace, const double* __restrict__ S,
           const double* __restrict__ rhoq, const double* __restrict__ duhat,
-          double* __restrict__ du, double* __restrict__ dq, TraceTab tt) {
+          double* __restrict__ du, double* __restrict__ dq, TraceTab tt, const int64_t* __restrict__ elist) {
   extern __shared__ double sm[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = BS_THREADS / 32;
-  const int64_t e = blockIdx.x;
+  // with an element list (FP64 fallback of the mixed path) CTA `slot` back-substitutes
+  // element elist[slot] with the factors in matrix slot `slot`
+  const int64_t slot = blockIdx.x;
+  const int64_t e = elist ? elist[slot] : slot;
+  if (e < 0) return;
   const int m = dm.m, d = dm.d, Np = dm.Np, NbT = dm.Nb, nu = dm.nu;
   const int Nb = tt.nb ? tt.nb[e] : NbT;      // this element's slots (mixed orders: ragged)
   const int nt = m * Nb;
   const int ld = tt.nb ? tt.ldv[e] : dm.ld;
-  const double* A = S + (tt.nb ? tt.soff[e] : e * (int64_t)dm.n * dm.ld);
+  const double* A = S + (tt.nb ? tt.soff[e] : slot * (int64_t)dm.n * dm.ld);
   double* sU = sm;          // [nt]   dU_e, component-major (k Nb + t)
   double* y = sU + dm.nt;   // [nu]
   for (int idx = tid; idx < nt; idx += BS_THREADS) {
@@ -167,10 +177,10 @@ cudaError_t launch_scatter_K(iedg_mesh* M, double* K, cudaStream_t st) {
   const unsigned grid = (unsigned)((total + th - 1) / th);
   if (M->precision == 0)
     k_scatter_K<double><<<grid, th, 0, st>>>(M->dm, M->nnzb, M->nb_pack, M->kc_ptr, M->kc_src, M->lud, M->el_nb,
-                                              M->S, K);
+                                              M->S, K, nullptr, nullptr, nullptr);
   else
     k_scatter_K<float><<<grid, th, 0, st>>>(M->dm, M->nnzb, M->nb_pack, M->kc_ptr, M->kc_src, M->lud, M->el_nb,
-                                             M->S32, K);
+                                             M->S32, K, M->fb_slot, M->fb_S, M->fb_S ? M->fb_count : nullptr);
   return cudaGetLastError();
 }
 
@@ -206,7 +216,34 @@ cudaError_t launch_backsub(iedg_mesh* M, const double* duhat, double* du, double
   const Dims& dm = M->dm;
   size_t smem = sizeof(double) * (size_t)(dm.nt + dm.nu);
   k_backsub<<<(unsigned)M->E, BS_THREADS, smem, st>>>(dm, M->geo, M->etrace, M->S, M->rhoq, duhat, du, dq,
-                                                      M->tt);
+                                                      M->tt, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backsub_list(iedg_mesh* M, const double* S, const int64_t* elist, int64_t n_slots,
+                                const double* duhat, double* du, double* dq, cudaStream_t st) {
+  const Dims& dm = M->dm;
+  size_t smem = sizeof(double) * (size_t)(dm.nt + dm.nu);
+  k_backsub<<<(unsigned)n_slots, BS_THREADS, smem, st>>>(dm, M->geo, M->etrace, S, M->rhoq, duhat, du, dq, M->tt,
+                                                         elist);
+  return cudaGetLastError();
+}
+
+// The fault injection's zero row in the FP64 slot of its element, when it has one.
+__global__ void k_zero_row_slot(int64_t e, int r, const int* __restrict__ slot_of, double* __restrict__ S,
+                                int64_t slot_stride, int ld, int ncol) {
+  const int sl = slot_of[e];
+  if (sl < 0) return;
+  double* row = S + sl * slot_stride + (int64_t)r * ld;
+  for (int c = threadIdx.x; c < ncol; c += blockDim.x) row[c] = 0.0;
+}
+
+cudaError_t launch_zero_row_fallback(iedg_mesh* M, cudaStream_t st) {
+  const Dims& dm = M->dm;
+  const int64_t e = M->fault.zero_row_elem;
+  if (M->fb_S == nullptr || e < 0 || e >= M->E) return cudaSuccess;
+  k_zero_row_slot<<<1, 128, 0, st>>>(e, M->fault.zero_row, M->fb_slot, M->fb_S, (int64_t)dm.n * dm.ld, dm.ld,
+                                     dm.n + 1);
   return cudaGetLastError();
 }
 

@@ -26,7 +26,7 @@ PREC_BLOCK_JACOBI, PREC_BILU0 = 0, 1
 # element-matrix precision of a handle (IEDG_PRECISION_*)
 PRECISION_FP64, PRECISION_MIXED, PRECISION_MIXED_TF32, PRECISION_MIXED_BF16 = 0, 1, 2, 3
 # per-element status codes (IEDG_ELEM_*)
-ELEM_OK, ELEM_REFINE, ELEM_SINGULAR, ELEM_NONFINITE, ELEM_TIMEOUT = 0, 1, 2, 3, 4
+ELEM_OK, ELEM_REFINE, ELEM_SINGULAR, ELEM_NONFINITE, ELEM_TIMEOUT, ELEM_FALLBACK = 0, 1, 2, 3, 4, 5
 
 
 class IedgError(RuntimeError):

@@ -103,14 +103,15 @@ def test_descriptor_checks_come_before_the_device():
 
 def test_autotune_candidates_keep_the_precision():
     """Schedules change how, never what: handles with TF32 / BF16 Schur operands are
-    offered only the tensor-core LU; FP32 handles both LU forms; FP64 handles the DFMA
+    offered only the tensor-core LU; FP32 handles the FFMA form and both tensor-core forms
+    (deferred Schur complement, every trailing update); FP64 handles the DFMA
     forms plus the exact-splitting tensor-core form (persistent grid, panel 16)."""
     from paper_1605_01020_gb300 import autotune
     for prec in (2, 3):
         c = autotune.candidates(prec, 3)
         assert c and all(s["lu_tensor"] == 1 for s in c)
     c1 = autotune.candidates(1, 3)
-    assert {s["lu_tensor"] for s in c1} == {0, 1}
+    assert {s["lu_tensor"] for s in c1} == {0, 1, 2}
     c0 = autotune.candidates(0, 3)
     assert {s["lu_tensor"] for s in c0} == {0, 1}
     assert all(s["lu_persistent"] == 1 and s["lu_panel"] == 16 for s in c0 if s["lu_tensor"] == 1)

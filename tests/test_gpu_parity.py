@@ -226,9 +226,13 @@ def _mixed_mesh(wl, precision=1):
     return iedg.mesh_from_workload(wl, precision=precision)
 
 
+@pytest.mark.parametrize("lu_tensor", [0, 1, 2])
 @pytest.mark.parametrize("name", ["cfg1-noisy", "p3-2cube", "p2-curved", "2d-p3-steady", "2d-p1", "p4-2cube",
                                   "p3-2cube-roe", "p2-curved-roe"])
-def test_mixed_condensed_parity(name):
+def test_mixed_condensed_parity(name, lu_tensor):
+    """FP32 element matrix and partial LU in its three forms (FFMA updates; the Schur
+    complement deferred to one tensor-core GEMM; every trailing update on the tensor
+    cores), FP64 refinement: against the FP64 oracle."""
     wl = _case(name)
     st = wl.state
     pb = problem(wl.mesh, wl.params)
@@ -236,6 +240,7 @@ def test_mixed_condensed_parity(name):
     Ke, Re = zip(*[pb.condense_qelim(e, st.u, st.q, st.uhat, st.u_ref) for e in range(E)])
     row_ptr, col, vals, R = oiedg.assemble(wl.mesh.elem_trace, wl.mesh.n_trace, np.array(Ke), np.array(Re))
     mesh = _mixed_mesh(wl)
+    mesh.set_schedule(lu_tensor=lu_tensor)
     K_d, R_d = mesh.assemble_condensed(dev(st.u), dev(st.q), dev(st.uhat), u_ref=dev(st.u_ref))
     kerr = bsr_row_err(row_ptr, host(K_d), vals, range(wl.mesh.n_trace))
     rerr = rel_err(host(R_d), R, floor=np.abs(np.array(Re)).max())
@@ -312,14 +317,16 @@ def test_quad_extra_parity(name, precision, quad_extra):
     assert rel_err(host(dq_d), dq_o) <= tr
 
 
-@pytest.mark.parametrize("cfg,precision", [(2, 1), (3, 1), (3, 2), (3, 3)])
-def test_mixed_full_size_sampled(cfg, precision):
+@pytest.mark.parametrize("cfg,precision,lu_tensor", [(2, 1, 1), (2, 1, 2), (3, 1, 0), (3, 1, 2), (3, 2, 1),
+                                                    (3, 3, 1)])
+def test_mixed_full_size_sampled(cfg, precision, lu_tensor):
     """The 16^3 p=3 workloads (config 3: stretched and sheared, aspect up to 50) in the
     mixed forms at full size (FP32 Schur complement; on config 3 also TF32 and BF16
     operands): sampled block rows of K and R, sampled updates."""
     wl = W.config(cfg)
     st = wl.state
     mesh = _mixed_mesh(wl, precision)
+    mesh.set_schedule(lu_tensor=lu_tensor)
     u, q, uh = dev(st.u), dev(st.q), dev(st.uhat)
     K_d, R_d = mesh.assemble_condensed(u, q, uh)
     du_d, dq_d = mesh.back_substitute(dev(st.duhat))
@@ -341,7 +348,7 @@ def test_mixed_full_size_sampled(cfg, precision):
     du_o, dq_o = pb.back_substitute_qelim(e, st.u, st.q, st.uhat, st.duhat)
     duerr, dqerr = rel_err(host(du_d[e]), du_o), rel_err(host(dq_d[e]), dq_o)
     cond = _cond1(pb, st, [e])
-    print(f"config {cfg} precision {precision}: K {kerr:.2e}  R {rerr:.2e}  du {duerr:.2e}  dq {dqerr:.2e}  "
+    print(f"config {cfg} precision {precision} lu_tensor {lu_tensor}: K {kerr:.2e}  R {rerr:.2e}  du {duerr:.2e}  dq {dqerr:.2e}  "
           f"cond1(A~) {max(cond):.2e}  flagged {int((status != 0).sum())}"
           + ("" if ratio is None else f"  K vs rounded-operand oracle {ratio:.3f} of the rounding's effect"))
     assert (status == 0).all()

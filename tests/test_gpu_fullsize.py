@@ -23,6 +23,18 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-11
 TOL_MIXED_K = 1e-4
 TOL_MIXED = 1e-10
+U64 = 2.0 ** -53
+
+
+def dz_tol(cond1, precision):
+    """Tolerance of the element updates du, dq.  Both sides form A~ in FP64 with
+    different summation orders (the device sum-factorised, the oracle dense), so its
+    entries differ by a few hundred units of roundoff and the solution by up to
+    cond(A~) times that: 100 cond1(A~) u64 for the FP64 path, ten times more for the
+    mixed path (refined to a relative residual of 1e-14); never below the flat 1e-11 /
+    1e-10 of the smaller cases.  K and R keep the flat bounds."""
+    base = TOL if precision == 0 else TOL_MIXED
+    return max(base, (100.0 if precision == 0 else 1000.0) * cond1 * U64)
 
 
 def _free():
@@ -65,8 +77,12 @@ def test_mixed_orders_full_size_sampled(precision):
     off = np.concatenate([[0], np.cumsum([len(x) for x in msh.node_xyz])])
     for e in sample:
         du_o, dq_o = pb.back_substitute_qelim(e, st.u, st.q, st.uhat, st.duhat)
-        assert rel_err(du_h[off[e]:off[e + 1]], du_o) <= tr, e
-        assert rel_err(dq_h[off[e]:off[e + 1]], dq_o) <= tr, e
+        sub = pb.pbs[e]
+        cond = float(np.linalg.cond(sub.qelim(pb.element_blocks(e, st.u, st.q, st.uhat))[0], 1))
+        tz = dz_tol(cond, precision)
+        edu, edq = rel_err(du_h[off[e]:off[e + 1]], du_o), rel_err(dq_h[off[e]:off[e + 1]], dq_o)
+        print(f"element {e} (p={msh.orders[e]}): du {edu:.2e} dq {edq:.2e} cond1(A~) {cond:.2e} tol {tz:.1e}")
+        assert edu <= tz and edq <= tz, e
     cache = {}
     for r0 in rows:
         els = [e for e in range(E) if r0 in set(msh.elem_trace[e].tolist())]
@@ -140,8 +156,11 @@ def test_p4_24cube_full_size_sampled(precision):
         assert rel_err(R_h[r0], rsum, floor=rmax) <= tr, r0
     for e in last:
         du_o, dq_o = pb.back_substitute_qelim(e, st.u, st.q, st.uhat, st.duhat)
-        assert rel_err(du_h[e], du_o) <= tr, e
-        assert rel_err(dq_h[e], dq_o) <= tr, e
+        cond = float(np.linalg.cond(pb.qelim(pb.element_blocks(e, st.u, st.q, st.uhat))[0], 1))
+        tz = dz_tol(cond, precision)
+        edu, edq = rel_err(du_h[e], du_o), rel_err(dq_h[e], dq_o)
+        print(f"element {e}: du {edu:.2e} dq {edq:.2e} cond1(A~) {cond:.2e} tol {tz:.1e}")
+        assert edu <= tz and edq <= tz, e
     print(f"24^3 p=4 precision {precision}: rows {rows}, elements {last} within {tk:.0e} / {tr:.0e}")
 
 

@@ -13,6 +13,14 @@ are formed here in FP64 (the tensor core accumulates in FP32, a difference far
 below the operand rounding).  The paper has no precision discussion: this is the
 reading of a Schur-complement GEMM with rounded operands and wide accumulation.
 
+Mass-matrix scaling (a reading: the paper has no precision discussion; "scaling by
+the element mass matrix" is read as a symmetric scaling of the u-block by the inverse
+Cholesky factor of the element mass matrix M = L L^T, per conserved component): the
+u-block A~ (dominated by the implicit stage's alpha M) becomes S A~ S^T with
+S = I_m (x) L^-1, B~ becomes S B~ and C~ becomes C~ S^T.  The Schur complement is
+unchanged in exact arithmetic; the factors W, Z of the scaled system are the ones
+rounded.
+
 Formats (values first rounded to FP32 with round-to-nearest-even, as the FP32
 operands a device holds):
   TF32: 10 explicit mantissa bits, round to nearest, ties away from zero;
@@ -52,12 +60,29 @@ def schur_operands(At, Bt, Ct):
     return W, Z
 
 
-def condense_rounded(sub, blk, fmt):
+def mass_scaling(M, m):
+    """S = I_m (x) L^-1 with M = L L^T (Cholesky factor of the element mass matrix), one
+    diagonal block per conserved component of the component-major u-unknowns."""
+    Linv = scipy.linalg.solve_triangular(np.linalg.cholesky(M), np.eye(M.shape[0]), lower=True)
+    return np.kron(np.eye(m), Linv)
+
+
+def scale_system(S, At, Bt, Ct):
+    """The element system scaled symmetrically on its u-block: S A~ S^T, S B~, C~ S^T
+    (the trace block D~ is unchanged).  The Schur complement is the same:
+    C~ S^T (S A~ S^T)^-1 S B~ = C~ A~^-1 B~."""
+    return S @ At @ S.T, S @ Bt, Ct @ S.T
+
+
+def condense_rounded(sub, blk, fmt, mass_scaled=False):
     """K_low of one element in the node-major layout [s, i, t, k] and the first-order
     bound |W| |Z| of the rounding error's terms (same layout).  sub: the element's
     oracle Problem (its qelim and layout); blk: its element_blocks; fmt: "tf32",
-    "bf16" or None (no rounding: K itself)."""
+    "bf16" or None (no rounding: K itself).  mass_scaled: W and Z are those of the
+    system scaled by the element mass matrix (scale_system with mass_scaling)."""
     At, Bt, Ct, Dt = sub.qelim(blk)[:4]
+    if mass_scaled:
+        At, Bt, Ct = scale_system(mass_scaling(blk["M"], sub.m), At, Bt, Ct)
     W, Z = schur_operands(At, Bt, Ct)
     rho = ROUNDING[fmt]
     K = Dt - rho(W) @ rho(Z)

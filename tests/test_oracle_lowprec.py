@@ -94,3 +94,46 @@ def test_rounded_condensation_on_a_mixed_order_element():
         Kb, bound = lowprec.condense_rounded(pb.pbs[e], blk, "bf16")
         u = lowprec.UNIT_ROUNDOFF["bf16"]
         assert (np.abs(Kb - Ke) <= (2 * u + u * u) * bound * (1 + 1e-6) + 1e-14 * np.abs(Ke).max()).all()
+
+
+def test_mass_scaling_of_the_mass_block_is_the_identity(element):
+    """S (M (x) I) S^T = I and S^T S = I (x) M^-1 for S = I (x) L^-1, M = L L^T: the
+    scaling turns the implicit stage's mass term into alpha I."""
+    pb, blk, _ = element
+    M = blk["M"]
+    S = lowprec.mass_scaling(M, pb.m)
+    MM = np.kron(np.eye(pb.m), M)
+    n = MM.shape[0]
+    assert np.abs(S @ MM @ S.T - np.eye(n)).max() <= 1e-12
+    assert np.abs(S.T @ S @ MM - np.eye(n)).max() <= 1e-10
+    assert np.abs(np.triu(S, 1)).max() == 0.0                      # lower triangular
+
+
+def test_mass_scaled_system_has_the_same_schur_complement(element):
+    """No rounding: the scaled system condenses to the plain K (Eq. LS is invariant
+    under the u-block scaling)."""
+    pb, blk, Ke = element
+    K, _ = lowprec.condense_rounded(pb, blk, None, mass_scaled=True)
+    assert np.abs(K - Ke).max() <= 1e-12 * np.abs(Ke).max()
+
+
+@pytest.mark.parametrize("fmt", ["tf32", "bf16"])
+def test_mass_scaled_rounded_error_within_first_order_bound(element, fmt):
+    pb, blk, Ke = element
+    K, bound = lowprec.condense_rounded(pb, blk, fmt, mass_scaled=True)
+    u = lowprec.UNIT_ROUNDOFF[fmt]
+    err = np.abs(K - Ke)
+    assert (err <= (2 * u + u * u) * bound * (1 + 1e-6) + 1e-14 * np.abs(Ke).max()).all()
+    assert err.max() > 0.01 * u * bound.max()
+
+
+def test_mass_scaling_lowers_the_interior_conditioning():
+    """On a 3D p=3 element of the Taylor-Green recipe the scaled u-block is better
+    conditioned than A~ (1-norm condition numbers; measured about 28x lower)."""
+    wl = W.config(2, N=2)
+    st = wl.state
+    pb = problem(wl.mesh, wl.params)
+    blk = pb.element_blocks(3, st.u, st.q, st.uhat)
+    At, Bt, Ct = pb.qelim(blk)[:3]
+    As = lowprec.scale_system(lowprec.mass_scaling(blk["M"], pb.m), At, Bt, Ct)[0]
+    assert np.linalg.cond(As, 1) * 5 < np.linalg.cond(At, 1)

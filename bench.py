@@ -498,7 +498,10 @@ def run_mixed(args, wl, mesh64, dev, step_outputs, inputs, flush, barrier, preci
     E, Np, m, d, T = mesh.E, mesh.Np, mesh.m, mesh.d, mesh.T
     f64 = torch.float64
     schedule, timings = None, {}
-    if not args.no_autotune:
+    if args.mixed_lu_tensor is not None and precision == 1:
+        mesh.set_schedule(lu_tensor=args.mixed_lu_tensor)
+        schedule = mesh.get_schedule()
+    elif not args.no_autotune:
         from paper_1605_01020_gb300 import autotune
         qt = torch.as_tensor(wl.state.q, dtype=f64, device=dev)
         schedule, timings = autotune.autotune(mesh, u, qt, uh, precision, reps=1)
@@ -761,6 +764,9 @@ def main():
     ap.add_argument("--no-mixed-orders", action="store_true", help="skip the mixed-order batch (p in {2,3,4})")
     ap.add_argument("--no-extras", action="store_true", help="skip the Roe / trace-solve / DIRK measurements")
     ap.add_argument("--mo-cells", type=int, default=None, help="mixed-order batch: N x N x 2N cells (default 16)")
+    ap.add_argument("--mixed-lu-tensor", type=int, default=None, choices=[0, 1, 2],
+                    help="mixed FP32 form: fixed LU form instead of the autotuner's choice (0 FFMA updates, "
+                         "1 deferred Schur complement on tcgen05, 2 every trailing update on tcgen05)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-elems", type=int, default=2, help="reference arm: elements per core per step")
     args = ap.parse_args()

@@ -57,7 +57,7 @@ AsmCfg asm_cfg(const Dims& dm) {
 // Meshes with mixed orders (tt.nb set): per-element slot count, offset and leading
 // dimension; the trace basis at the face points comes from the element's table, and
 // the trace rows are accumulated separately from the face parts of the u-rows.
-template <class T>
+template <class T, bool LIST = false>
 __global__ void __launch_bounds__(AS_THREADS)
 k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, AsmTab<T> tb, T* __restrict__ S,
            const double* __restrict__ rhs64, TraceTab tt, int NbU, const int64_t* __restrict__ elist) {
@@ -68,8 +68,11 @@ k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, AsmTab<T> tb, T* __restri
   // the m^2 CTAs of an element are adjacent; with an element list (FP64 fallback of the
   // mixed path) CTA group `slot` assembles element elist[slot] into matrix slot `slot`
   const int64_t slot = blockIdx.x / m2;
-  const int64_t e = elist ? elist[slot] : slot;
-  if (e < 0) return;
+  int64_t e = slot;
+  if constexpr (LIST) {
+    e = elist[slot];
+    if (e < 0) return;
+  }
   const int pair = blockIdx.x % m2, i = pair / dm.m, k = pair % dm.m;
   const int c0 = blockIdx.y * cf.CW;
   const int d = dm.d, Np = dm.Np, Nq = dm.Nq, Nfp = dm.Nfp, Nfq = dm.Nfq, Nfn = dm.Nfn;
@@ -232,7 +235,7 @@ k_assemble(Dims dm, Phys ph, AsmCfg cf, RefTables ref, AsmTab<T> tb, T* __restri
   // ---- write the element rows
   const int64_t nn = mix ? (int64_t)dm.nu + (int64_t)dm.m * Nb : dm.n;
   const int64_t ld = mix ? tt.ldv[e] : dm.ld;
-  T* Se = mix ? S + tt.soff[e] : S + slot * nn * ld;
+  T* Se = mix ? S + tt.soff[e] : S + (LIST ? slot : e) * nn * ld;
   if (rhs64 != nullptr && pair == 0 && blockIdx.y == 0)
     for (int r = tid; r < nn; r += AS_THREADS) Se[r * ld + nn] = (T)rhs64[e * dm.n + r];
   auto colS = [&](int col) -> int64_t { return col < Np ? (int64_t)k * Np + col : (int64_t)dm.nu + (int64_t)k * Nb + (col - Np); };
@@ -1265,11 +1268,12 @@ cudaError_t launch_assemble_list(iedg_mesh* M, double* S, const int64_t* elist, 
   const int nbu = dm.Np - inner;
   size_t smem = sizeof(double) * ((size_t)cf.KC * cf.rows_pad + (size_t)cf.KC * cf.CW + (size_t)nbu * cf.CW +
                                   (size_t)dm.Nfq * cf.CW);
-  cudaError_t err = cudaFuncSetAttribute(k_assemble<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t err =
+      cudaFuncSetAttribute(k_assemble<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   dim3 grid((unsigned)(n_slots * dm.m * dm.m), cf.nsplit);
-  k_assemble<double><<<grid, AS_THREADS, smem, st>>>(dm, M->ph, cf, M->ref, tables64(M), S, M->rhs64, M->tt, nbu,
-                                                     elist);
+  k_assemble<double, true><<<grid, AS_THREADS, smem, st>>>(dm, M->ph, cf, M->ref, tables64(M), S, M->rhs64, M->tt,
+                                                           nbu, elist);
   return cudaGetLastError();
 }
 

@@ -45,7 +45,7 @@ size_t sf_smem(const Dims& dm, bool mix) {
 // group instead of one load per multiply-add.  Face terms are contracted by two 1D
 // stages over the face's tangential directions (face point gf = g1 + nq1 g2, face
 // node tn = a1 + np1 a2, the face-normal factor of the basis being 1 on the face).
-template <class T, int NP1, int NQ1, int CC, bool MIX>
+template <class T, int NP1, int NQ1, int CC, bool MIX, bool LIST = false>
 __global__ void __launch_bounds__(SF_THREADS)
 k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, const double* __restrict__ rhs64,
               TraceTab tt, const int64_t* __restrict__ elist) {
@@ -61,8 +61,11 @@ k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, 
   // with an element list (FP64 fallback of the mixed path) CTA group `slot` assembles
   // element elist[slot] into matrix slot `slot`
   const int64_t slot = blockIdx.x / m2;
-  const int64_t e = elist ? elist[slot] : slot;
-  if (e < 0) return;
+  int64_t e = slot;
+  if constexpr (LIST) {
+    e = elist[slot];
+    if (e < 0) return;
+  }
   const int pair = blockIdx.x % m2, i = pair / m, k = pair % m;
   const bool has_cq = !(i == 0 || (i <= d && k == m - 1));
   const int Nb = MIX ? tt.nb[e] : NbU;          // trace slots of this element
@@ -111,7 +114,7 @@ k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, 
   const T alpha = (T)ph.alpha;
   const int64_t nn = MIX ? (int64_t)dm.nu + (int64_t)m * Nb : dm.n;
   const int64_t ld = MIX ? tt.ldv[e] : dm.ld;
-  T* Se = MIX ? S + tt.soff[e] : S + slot * nn * ld;
+  T* Se = MIX ? S + tt.soff[e] : S + (LIST ? slot : e) * nn * ld;
   if (rhs64 != nullptr && pair == 0)
     for (int r = tid; r < nn; r += SF_THREADS) Se[r * ld + nn] = (T)rhs64[e * dm.n + r];
   __syncthreads();
@@ -311,7 +314,8 @@ static cudaError_t assemble_sf_t(iedg_mesh* M, T* S, const double* rhs64, const 
   const Dims& dm = M->dm;
   const bool mix = M->tt.nb != nullptr;
   size_t smem = sf_smem<T, CC>(dm, mix);
-  auto kern = mix ? k_assemble_sf<T, NP1, NQ1, CC, true> : k_assemble_sf<T, NP1, NQ1, CC, false>;
+  auto kern = elist ? k_assemble_sf<T, NP1, NQ1, CC, false, true>
+                    : (mix ? k_assemble_sf<T, NP1, NQ1, CC, true> : k_assemble_sf<T, NP1, NQ1, CC, false>);
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   const int64_t E = elist ? n_slots : M->E;

@@ -210,7 +210,7 @@ __device__ __forceinline__ void mm_load_b(const float* __restrict__ A, int ld, i
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const int idx = threadIdx.x + q * MM_THREADS, k = idx >> 6, c = c0 + (idx & 63);
-    bv[q] = (k < nb && c < ncol) ? A[(int64_t)(kb + k) * ld + c] : 0.f;
+    bv[q] = (k < nb && c < ncol) ? __ldcg(A + (int64_t)(kb + k) * ld + c) : 0.f;
   }
 }
 
@@ -260,7 +260,10 @@ __device__ __forceinline__ void mm_issue(uint32_t tmem, uint32_t a_hi, uint32_t 
 // A[r][c] -= acc[r][c] for the tile at (rt, ct): warp (q, h) owns TMEM lanes 32 q ..
 // 32 q + 31 (rows rt + 32 q + lane) and columns 32 h .. 32 h + 31.  Rows below r_lo
 // (inside an 8-row group above the trailing block) and past n, columns past ncol are
-// left alone.
+// left alone.  The subtraction is a reduction performed in L2 (red.global.add of
+// -acc, four values per instruction on 16-byte boundaries): the SM never waits for
+// the trailing block's values, and each entry receives exactly one update per panel,
+// so the result does not depend on timing.
 __device__ __forceinline__ void mm_epilogue(float* __restrict__ A, int ld, int n, int ncol, int r_lo, int rt,
                                             int ct, uint32_t tacc) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, q = warp & 3, h = warp >> 2;
@@ -268,29 +271,20 @@ __device__ __forceinline__ void mm_epilogue(float* __restrict__ A, int ld, int n
   const bool live = row >= r_lo && row < n && c0 < ncol;
   float* dst = A + (int64_t)row * ld + c0;
   const bool vec = live && ((c0 & 3) == 0) && c0 + 32 <= ncol;
-  // two halves of 16 columns: the trailing-block values are requested before the
-  // accumulator is read, so their latency overlaps the TMEM load
 #pragma unroll
   for (int hf = 0; hf < 2; ++hf) {
-    float cur[16], acc[16];
-    if (vec) {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float4 t = reinterpret_cast<const float4*>(dst + 16 * hf)[j];
-        cur[4 * j] = t.x; cur[4 * j + 1] = t.y; cur[4 * j + 2] = t.z; cur[4 * j + 3] = t.w;
-      }
-    }
+    float acc[16];
     tc::tmem_ld16(tacc + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * h + 16 * hf), acc);
     if (vec) {
 #pragma unroll
       for (int j = 0; j < 4; ++j)
-        reinterpret_cast<float4*>(dst + 16 * hf)[j] =
-            make_float4(cur[4 * j] - acc[4 * j], cur[4 * j + 1] - acc[4 * j + 1], cur[4 * j + 2] - acc[4 * j + 2],
-                        cur[4 * j + 3] - acc[4 * j + 3]);
+        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + 16 * hf + 4 * j),
+                     "f"(-acc[4 * j]), "f"(-acc[4 * j + 1]), "f"(-acc[4 * j + 2]), "f"(-acc[4 * j + 3])
+                     : "memory");
     } else if (live) {
 #pragma unroll
       for (int j = 0; j < 16; ++j)
-        if (c0 + 16 * hf + j < ncol) dst[16 * hf + j] -= acc[j];
+        if (c0 + 16 * hf + j < ncol) atomicAdd(dst + 16 * hf + j, -acc[j]);
     }
   }
 }
@@ -372,20 +366,30 @@ __device__ void mm_element(const LuElem& el, float* __restrict__ S, int8_t* __re
   if (tid == 0) sing = 0;
   for (int kb = 0; kb < nu && !t.failed; kb += MM_NB) {
     const int nb = min(MM_NB, nu - kb), rows = n - kb, prow = nu - kb;
-    // panel load (columns past nb are zero)
-    for (int idx = tid; idx < rows * 8; idx += MM_THREADS) {
-      const int r = idx >> 3, k = (idx & 7) * 4;
-      const float* src = A + (int64_t)(kb + r) * ld + kb + k;
-      float4 x;
-      if (k + 4 <= nb) {
-        x = *reinterpret_cast<const float4*>(src);
-      } else {
-        x.x = k < nb ? src[0] : 0.f;
-        x.y = k + 1 < nb ? src[1] : 0.f;
-        x.z = k + 2 < nb ? src[2] : 0.f;
-        x.w = k + 3 < nb ? src[3] : 0.f;
+    // panel load (columns past nb are zero), eight independent loads per thread in flight
+    for (int base = 0; base < rows * 8; base += 8 * MM_THREADS) {
+      float4 x[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int idx = base + u * MM_THREADS + tid, r = idx >> 3, k = (idx & 7) * 4;
+        x[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (idx < rows * 8) {
+          const float* src = A + (int64_t)(kb + r) * ld + kb + k;
+          if (k + 4 <= nb) {
+            x[u] = __ldcg(reinterpret_cast<const float4*>(src));
+          } else {
+            x[u].x = k < nb ? __ldcg(src) : 0.f;
+            x[u].y = k + 1 < nb ? __ldcg(src + 1) : 0.f;
+            x[u].z = k + 2 < nb ? __ldcg(src + 2) : 0.f;
+            x[u].w = k + 3 < nb ? __ldcg(src + 3) : 0.f;
+          }
+        }
       }
-      *reinterpret_cast<float4*>(pel(b.P, r, k)) = x;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int idx = base + u * MM_THREADS + tid;
+        if (idx < rows * 8) *reinterpret_cast<float4*>(pel(b.P, idx >> 3, (idx & 7) * 4)) = x[u];
+      }
     }
     for (int r = tid; r < prow; r += MM_THREADS) perm[r] = r;
     __syncthreads();
@@ -412,7 +416,7 @@ __device__ void mm_element(const LuElem& el, float* __restrict__ S, int8_t* __re
 #pragma unroll
       for (int j = 0; j < MM_NB; ++j) {
         if (j >= nb) break;
-        x[j] = A[(int64_t)(kb + perm[j]) * ld + c];
+        x[j] = __ldcg(A + (int64_t)(kb + perm[j]) * ld + c);
       }
 #pragma unroll
       for (int j0 = 0; j0 < MM_NB; j0 += 8) {
@@ -420,7 +424,7 @@ __device__ void mm_element(const LuElem& el, float* __restrict__ S, int8_t* __re
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int r = j0 + j < nb ? piv[j0 + j] : 0;
-          y[j] = (j0 + j < nb && r >= nb && perm[r] != r) ? A[(int64_t)(kb + perm[r]) * ld + c] : 0.f;
+          y[j] = (j0 + j < nb && r >= nb && perm[r] != r) ? __ldcg(A + (int64_t)(kb + perm[r]) * ld + c) : 0.f;
         }
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
@@ -442,13 +446,20 @@ __device__ void mm_element(const LuElem& el, float* __restrict__ S, int8_t* __re
       }
     }
     __syncthreads();
-    if (kb + nb < n) mm_trailing(A, ld, n, kb, nb, b, t);
+    if (kb + nb < n) {
+      mm_trailing(A, ld, n, kb, nb, b, t);
+      // the trailing block's reductions are performed (gpu scope) before any thread of
+      // the CTA reads it again; those reads go to L2 (ld.global.cg), past any line an
+      // earlier load left in L1
+      __threadfence();
+      __syncthreads();
+    }
   }
   __syncthreads();
   int bad = 0;
   for (int idx = tid; idx < (n - nu) * (ncol - nu); idx += MM_THREADS) {
     const int r = nu + idx / (ncol - nu), c = nu + idx % (ncol - nu);
-    if (!isfinite(A[(int64_t)r * ld + c])) bad = 1;
+    if (!isfinite(__ldcg(A + (int64_t)r * ld + c))) bad = 1;
   }
   bad = __syncthreads_or(bad);
   nonfin = __syncthreads_or(nonfin);

@@ -67,13 +67,24 @@ __device__ __forceinline__ bool next_element(int64_t* queue, int64_t E, int64_t 
 template <class K>
 static inline cudaError_t persistent_grid(K kern, size_t smem, int64_t E, unsigned* grid, int max_per_sm = 64,
                                           int threads = LU_THREADS) {
-  int dev = 0, sms = 0, per_sm = 0;
+  int dev = 0, sms = 0, per_sm = 0, smem_sm = 0, reserved = 0;
+  cudaFuncAttributes fa;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                          (int)cudaSharedmemCarveoutMaxShared);
   if (err == cudaSuccess) err = cudaGetDevice(&dev);
   if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (err == cudaSuccess) err = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  if (err == cudaSuccess) err = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  if (err == cudaSuccess) err = cudaFuncGetAttributes(&fa, kern);
   if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
   if (err != cudaSuccess) return err;
+  // the same bound from the kernel's own shared memory, registers and threads (the
+  // occupancy query has been seen to answer one block less than fits for the largest
+  // shared-memory configurations); a grid above what fits only queues blocks
+  int own = smem_sm / (int)(smem + fa.sharedSizeBytes + reserved);
+  if (fa.numRegs > 0) own = own < 65536 / (fa.numRegs * threads) ? own : 65536 / (fa.numRegs * threads);
+  own = own < 2048 / threads ? own : 2048 / threads;
+  if (own > per_sm) per_sm = own;
   if (per_sm > max_per_sm) per_sm = max_per_sm;
   int64_t g = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
   *grid = (unsigned)(g < E ? g : E);

@@ -397,9 +397,10 @@ def run_ours(args, wl, rank, world, local_rank):
                                                    inputs=(u, uh, duh), flush=flush, barrier=barrier)
     low = {}
     if not args.no_mixed and not args.no_low_precision:
-        for prec, key in ((2, "mixed_tf32"), (3, "mixed_bf16")):
+        for prec, key, flags in ((2, "mixed_tf32", 0), (3, "mixed_bf16", 0), (1, "mixed_mass_scaled", 1),
+                                 (2, "mixed_tf32_mass_scaled", 1), (3, "mixed_bf16_mass_scaled", 1)):
             low[key] = run_mixed(args, wl, None, dev, step_outputs=(K, R, du, dq), inputs=(u, uh, duh),
-                                 flush=flush, barrier=barrier, precision=prec)
+                                 flush=flush, barrier=barrier, precision=prec, flags=flags)
     # mixed orders: one GPU only (the leg takes a few minutes; scaling runs skip it)
     mixed_orders = None
     del K, R, du, dq
@@ -485,7 +486,7 @@ MIXED_FORMS = {1: "FP32 element matrix + partial LU, FP64 refinement",
                   "FP64 refinement"}
 
 
-def run_mixed(args, wl, mesh64, dev, step_outputs, inputs, flush, barrier, precision=1):
+def run_mixed(args, wl, mesh64, dev, step_outputs, inputs, flush, barrier, precision=1, flags=0):
     """The same step in a mixed form (FP32 element matrix and partial LU, FP64
     residuals and refinement of R, du, dq; precision 2 / 3: the Schur complement with
     TF32 / BF16 operands), timed the same way; errors against the FP64 path's outputs
@@ -494,7 +495,7 @@ def run_mixed(args, wl, mesh64, dev, step_outputs, inputs, flush, barrier, preci
     from paper_1605_01020_gb300 import iedg
     K64, R64, du64, dq64 = step_outputs
     u, uh, duh = inputs
-    mesh = iedg.mesh_from_workload(wl, precision=precision)
+    mesh = iedg.mesh_from_workload(wl, precision=precision, flags=flags)
     E, Np, m, d, T = mesh.E, mesh.Np, mesh.m, mesh.d, mesh.T
     f64 = torch.float64
     schedule, timings = None, {}
@@ -548,7 +549,9 @@ def run_mixed(args, wl, mesh64, dev, step_outputs, inputs, flush, barrier, preci
                 "peak_source": f"FP32 FFMA: {props.multi_processor_count} SMs x {FFMA_PER_CLK_PER_SM} FMA/clk x 2 "
                                f"x 2070 MHz (derived)",
                 "share_of_step": kms / tot if tot else None}
-    out = {"ms_total": e0.elapsed_time(e1), "precision": MIXED_FORMS[precision],
+    out = {"ms_total": e0.elapsed_time(e1),
+           "precision": MIXED_FORMS[precision] + ("; element systems scaled by the mass matrix's inverse Cholesky "
+                                                  "factor before the factorisation" if flags else ""),
            "schedule": schedule, "autotune_ms": timings, "roofline": roof,
            "err_vs_fp64": {"K": err(K, K64), "R": err(R, R64), "du": err(du, du64), "dq": err(dq, dq64)},
            "element_status_nonzero": int((status != 0).sum()),

@@ -106,8 +106,20 @@ typedef struct {
                                the Euler flux (the absolute values of its eigenvalues
                                v_n, v_n +- c in its eigenbasis); both fully linearised,
                                d|x|/dx = sign(x) with sign(0) = 0                        */
-  int32_t reserved;
+  int32_t flags;            /* IEDG_FLAG_* (0 = none)                                */
 } iedg_mesh_desc;
+
+/* Mixed forms (precision 1-3, uniform meshes): before the FP32 partial LU the element
+ * system is scaled by the element mass matrix M = L L^T (Cholesky): the u-block A~
+ * becomes S A~ S^T, B~ becomes S B~ and C~ becomes C~ S^T with S = I_m (x) L^-1 (one
+ * block per conserved component).  K and R are the same in exact arithmetic (Eq. LS
+ * is invariant under this scaling); the scaled u-block is far better conditioned (the
+ * implicit stage's alpha M becomes alpha I), and the TF32 / BF16 Schur operands W, Z
+ * are those of the scaled system.  The refinement and back-substitution solve with
+ * the scaled factors (x = S^T (S A~ S^T)^-1 S b).  No counterpart in the paper, which
+ * has no precision discussion: the reading of "scaling by the element mass matrix".
+ * IEDG_ERR_INVALID_ARG with FP64 handles, IEDG_ERR_UNSUPPORTED with mixed orders. */
+#define IEDG_FLAG_MASS_SCALING 1
 
 /* Builds the handle: copies the mesh to the device, computes per-element geometry
  * (Jacobians, weights, normals, mass matrix and the lifting operators of Eq. IEDG a)

@@ -504,7 +504,17 @@ static int create_impl(const iedg_mesh_desc* D, cudaStream_t st, iedg_mesh* M) {
   rc = alloc_owner(M, E * (int64_t)dm.n * dm.ld, E * (int64_t)dm.nu, E * (int64_t)dm.Nb * dm.m,
                    E * (int64_t)dm.nt, st);
   if (rc != IEDG_OK) return rc;
-  return run_geometry(M, D->node_xyz, st);
+  rc = run_geometry(M, D->node_xyz, st);
+  if (rc != IEDG_OK || !M->mass_scaled) return rc;
+  // inverse Cholesky factors of the mass matrices for the scaled mixed forms
+  CUDA_TRY(dalloc(M, &M->Linv32, (size_t)E * dm.Np * dm.Np));
+  int flag = 0;
+  CUDA_TRY(cudaMemsetAsync(M->dev_flag, 0, sizeof(int), st));
+  CUDA_TRY(launch_mass_chol(M, st));
+  CUDA_TRY(cudaMemcpyAsync(&flag, M->dev_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  if (flag) return fail(M, IEDG_ERR_MESH, "element mass matrix not positive definite");
+  return IEDG_OK;
 }
 
 // Storage precision (FP64 or FP32 element matrices), the Schur GEMM's operands on the
@@ -532,6 +542,11 @@ static int check_desc(const iedg_mesh_desc* D, bool mixed) {
     return fail(M, IEDG_ERR_INVALID_ARG, "empty mesh or null mesh arrays");
   if (!(D->gamma > 1.0) || !(D->Pr > 0) || !(D->Re > 0) || !(D->alpha >= 0))
     return fail(M, IEDG_ERR_INVALID_ARG, "physical parameters out of range");
+  if (D->flags & ~IEDG_FLAG_MASS_SCALING) return fail(M, IEDG_ERR_INVALID_ARG, "unknown descriptor flags");
+  if ((D->flags & IEDG_FLAG_MASS_SCALING) && D->precision == IEDG_PRECISION_FP64)
+    return fail(M, IEDG_ERR_INVALID_ARG, "mass-matrix scaling applies to the mixed forms only");
+  if ((D->flags & IEDG_FLAG_MASS_SCALING) && mixed)
+    return fail(M, IEDG_ERR_UNSUPPORTED, "mass-matrix scaling is not available on meshes with mixed orders");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(M, IEDG_ERR_CUDA, "no CUDA device");
   return IEDG_OK;
@@ -556,6 +571,7 @@ extern "C" int iedg_create_mesh(const iedg_mesh_desc* D, void* stream, iedg_mesh
   M->dm = make_dims(D->dim, D->order, D->quad_extra);
   M->ph = Phys{D->gamma, D->Pr, D->Re, D->alpha, D->stab, {0, 0, 0, 0, 0}};
   set_precision(M, D->precision);
+  M->mass_scaled = (D->flags & IEDG_FLAG_MASS_SCALING) != 0;
   M->E = D->n_elem;
   M->T = D->n_trace;
   rc = create_impl(D, (cudaStream_t)stream, M);
@@ -1068,6 +1084,7 @@ extern "C" int iedg_assemble_condensed(iedg_mesh* M, const double* u, const doub
     CUDA_TRY(TRACED("assemble", launch_assemble_sf(M, st)));
   else
     CUDA_TRY(TRACED("assemble", launch_assemble(M, st)));
+  if (M->mass_scaled) CUDA_TRY(TRACED("mass_scale", launch_mass_scale(M, st)));
   if (M->fault.zero_row_elem >= 0) CUDA_TRY(TRACED("fault_zero_row", launch_zero_row(M, st)));
   CUDA_TRY(TRACED("lu_schur", launch_lu(M, st)));
   if (M->precision != IEDG_PRECISION_FP64) {

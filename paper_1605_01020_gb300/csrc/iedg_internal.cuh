@@ -173,6 +173,8 @@ struct iedg_mesh {
   int precision = 0;            // 0 = FP64, 1 = mixed (FP32 element matrix and LU)
   int schur_in = 0;             // mixed: operands of the Schur GEMM (kSchurFp32 / Tf32 / Bf16)
   float* S32 = nullptr;         // [E][n][ld]    bordered element matrices, FP32, L kept
+  bool mass_scaled = false;     // mixed forms: element systems scaled by the mass matrix (iedg_mass_scale.cu)
+  float* Linv32 = nullptr;      // [E][Np][Np]   inverse Cholesky factor of the mass matrix, FP32
   int* piv = nullptr;           // [E][nu]       pivot rows of the FP32 partial LU
   double* rhs64 = nullptr;      // [E][n]        FP64 right-hand sides F~, G~
   double* y64 = nullptr;        // [E][nu]       refined A~^-1 F~
@@ -276,6 +278,8 @@ cudaError_t launch_zero_row_fallback(iedg_mesh* M, cudaStream_t st);
 cudaError_t launch_backsub_list(iedg_mesh* M, const double* S, const int64_t* elist, int64_t n_slots,
                                 const double* duhat, double* du, double* dq, cudaStream_t st);
 cudaError_t launch_zero_row(iedg_mesh* M, cudaStream_t st);   // Fault.zero_row_elem
+cudaError_t launch_mass_chol(iedg_mesh* M, cudaStream_t st);   // L^-1 of the mass matrices (once per mesh)
+cudaError_t launch_mass_scale(iedg_mesh* M, cudaStream_t st);  // S A~ S^T, S B~, C~ S^T of the FP32 systems
 cudaError_t launch_backsub_mixed(iedg_mesh* M, const double* duhat, double* du, double* dq,
                                  cudaStream_t st);
 

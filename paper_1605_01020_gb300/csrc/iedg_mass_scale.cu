@@ -1,0 +1,157 @@
+// Scaling of the element system by the element mass matrix before the low-precision
+// factorisation (mixed forms, handle flag IEDG_FLAG_MASS_SCALING).
+//
+// The u-block of the q-eliminated element system is dominated by the implicit
+// stage's alpha M (Eq. IEDG b with the DIRK mass term) and inherits the conditioning
+// of the mass matrix.  With M = L L^T (Cholesky) and S = I_m (x) L^-1 (one block per
+// conserved component of the component-major u-unknowns), the bordered matrix becomes
+//     [ S A~ S^T   S B~   S F~ ]
+//     [ C~ S^T     D~     G~   ],
+// whose Schur complement is the same K = D~ - C~ A~^-1 B~ (Eq. LS) and whose u-block
+// S A~ S^T ~ alpha I + ... is far better conditioned; the u-unknowns of the scaled
+// system are S^-T du.  The refinement solves A~ x = b as x = S^T (S A~ S^T)^-1 S b with
+// the factors of the scaled matrix and FP64 residuals of the unscaled operator.
+//
+// Per mesh: k_mass_chol forms L^-1 in FP64 and keeps it in FP32 (lower triangular).
+// Per assembly: k_scale_rows applies S from the left to the u-rows, k_scale_cols S^T
+// from the right to the u-columns of every row.
+#include "iedg_internal.cuh"
+
+namespace iedg {
+namespace {
+
+constexpr int MS_THREADS = 256;
+
+// L^-1 of the element's mass matrix.  Cholesky in place (lower triangle of Ls), then
+// column c of X = L^-1 by forward substitution in thread c, kept in the strict upper
+// triangle of Ls (X[i][c] at Ls[c][i]) and its diagonal in xd.
+__global__ void __launch_bounds__(MS_THREADS) k_mass_chol(int Np, const double* __restrict__ Mass,
+                                                          float* __restrict__ Linv32, int* __restrict__ flag) {
+  extern __shared__ double ls[];
+  double* xd = ls + (size_t)Np * Np;
+  const int64_t e = blockIdx.x;
+  const int tid = threadIdx.x;
+  const double* M = Mass + (size_t)e * Np * Np;
+  for (int i = tid; i < Np * Np; i += MS_THREADS) ls[i] = M[i];
+  __syncthreads();
+  for (int j = 0; j < Np; ++j) {
+    if (tid == 0) {
+      const double d = ls[j * Np + j];
+      if (!(d > 0.0)) atomicOr(flag, 2);
+      ls[j * Np + j] = sqrt(d > 0.0 ? d : 1.0);
+    }
+    __syncthreads();
+    const double dj = ls[j * Np + j];
+    for (int i = j + 1 + tid; i < Np; i += MS_THREADS) ls[i * Np + j] /= dj;
+    __syncthreads();
+    // lower trailing update A[i][k] -= L[i][j] L[k][j] for j < k <= i
+    const int rem = Np - j - 1;
+    for (int idx = tid; idx < rem * rem; idx += MS_THREADS) {
+      const int i = j + 1 + idx / rem, k = j + 1 + idx % rem;
+      if (k <= i) ls[i * Np + k] = fma(-ls[i * Np + j], ls[k * Np + j], ls[i * Np + k]);
+    }
+    __syncthreads();
+  }
+  for (int c = tid; c < Np; c += MS_THREADS) {
+    xd[c] = 1.0 / ls[c * Np + c];
+    for (int i = c + 1; i < Np; ++i) {
+      double s = ls[i * Np + c] * xd[c];
+      for (int k = c + 1; k < i; ++k) s = fma(ls[i * Np + k], ls[c * Np + k], s);
+      ls[c * Np + i] = -s / ls[i * Np + i];
+    }
+  }
+  __syncthreads();
+  float* out = Linv32 + (size_t)e * Np * Np;
+  for (int idx = tid; idx < Np * Np; idx += MS_THREADS) {
+    const int i = idx / Np, c = idx % Np;
+    out[idx] = i < c ? 0.f : (float)(i == c ? xd[c] : ls[c * Np + i]);
+  }
+}
+
+constexpr int MS_CH = 64;     // columns (rows) per staged chunk
+
+// u-rows of component i: R_i <- L^-1 R_i over all n + 1 columns.
+__global__ void __launch_bounds__(MS_THREADS) k_scale_rows(Dims dm, const float* __restrict__ Linv32,
+                                                           float* __restrict__ S) {
+  extern __shared__ float fs[];
+  const int Np = dm.Np, ncol = dm.n + 1;
+  const int64_t e = blockIdx.x / dm.m;
+  const int i = blockIdx.x % dm.m, tid = threadIdx.x;
+  float* Li = fs;                      // [Np][Np]
+  float* st = Li + Np * Np;            // [Np][MS_CH]
+  const float* L = Linv32 + (size_t)e * Np * Np;
+  for (int q = tid; q < Np * Np; q += MS_THREADS) Li[q] = L[q];
+  float* R = S + (e * (int64_t)dm.n + (int64_t)i * Np) * dm.ld;
+  for (int c0 = 0; c0 < ncol; c0 += MS_CH) {
+    __syncthreads();
+    for (int q = tid; q < Np * MS_CH; q += MS_THREADS) {
+      const int b = q / MS_CH, c = q % MS_CH;
+      st[q] = c0 + c < ncol ? R[(int64_t)b * dm.ld + c0 + c] : 0.f;
+    }
+    __syncthreads();
+    for (int q = tid; q < Np * MS_CH; q += MS_THREADS) {
+      const int a = q / MS_CH, c = q % MS_CH;
+      float s = 0.f;
+      for (int b = 0; b <= a; ++b) s = fmaf(Li[a * Np + b], st[b * MS_CH + c], s);
+      if (c0 + c < ncol) R[(int64_t)a * dm.ld + c0 + c] = s;
+    }
+  }
+}
+
+// u-columns of component k in every row: C_k <- C_k L^-T.
+__global__ void __launch_bounds__(MS_THREADS) k_scale_cols(Dims dm, const float* __restrict__ Linv32,
+                                                           float* __restrict__ S) {
+  extern __shared__ float fs[];
+  const int Np = dm.Np, n = dm.n;
+  const int64_t e = blockIdx.x / dm.m;
+  const int k = blockIdx.x % dm.m, tid = threadIdx.x;
+  float* Li = fs;                      // [Np][Np]
+  float* st = Li + Np * Np;            // [MS_CH][Np + 1]
+  const int sp = Np + 1;
+  const float* L = Linv32 + (size_t)e * Np * Np;
+  for (int q = tid; q < Np * Np; q += MS_THREADS) Li[q] = L[q];
+  float* C = S + e * (int64_t)n * dm.ld + (int64_t)k * Np;
+  for (int r0 = 0; r0 < n; r0 += MS_CH) {
+    __syncthreads();
+    for (int q = tid; q < MS_CH * Np; q += MS_THREADS) {
+      const int r = q / Np, b = q % Np;
+      st[r * sp + b] = r0 + r < n ? C[(int64_t)(r0 + r) * dm.ld + b] : 0.f;
+    }
+    __syncthreads();
+    for (int q = tid; q < MS_CH * Np; q += MS_THREADS) {
+      const int r = q / Np, a = q % Np;
+      float s = 0.f;
+      for (int b = 0; b <= a; ++b) s = fmaf(st[r * sp + b], Li[a * Np + b], s);
+      if (r0 + r < n) C[(int64_t)(r0 + r) * dm.ld + a] = s;
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_mass_chol(iedg_mesh* M, cudaStream_t st) {
+  const int Np = M->dm.Np;
+  const size_t smem = sizeof(double) * ((size_t)Np * Np + Np);
+  cudaError_t err = cudaFuncSetAttribute(k_mass_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  k_mass_chol<<<(unsigned)M->E, MS_THREADS, smem, st>>>(Np, M->geo.Mass, M->Linv32, M->dev_flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mass_scale(iedg_mesh* M, cudaStream_t st) {
+  const Dims& dm = M->dm;
+  const size_t s1 = sizeof(float) * ((size_t)dm.Np * dm.Np + (size_t)dm.Np * MS_CH);
+  const size_t s2 = sizeof(float) * ((size_t)dm.Np * dm.Np + (size_t)MS_CH * (dm.Np + 1));
+  cudaError_t err = cudaFuncSetAttribute(k_scale_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1);
+  if (err == cudaSuccess)
+    err = cudaFuncSetAttribute(k_scale_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2);
+  if (err != cudaSuccess) return err;
+  const unsigned grid = (unsigned)(M->E * dm.m);
+  k_scale_rows<<<grid, MS_THREADS, s1, st>>>(dm, M->Linv32, M->S32);
+  err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  k_scale_cols<<<grid, MS_THREADS, s2, st>>>(dm, M->Linv32, M->S32);
+  return cudaGetLastError();
+}
+
+}  // namespace iedg

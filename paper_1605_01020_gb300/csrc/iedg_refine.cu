@@ -405,8 +405,29 @@ __device__ __forceinline__ void panel_row(const float* __restrict__ A, int ld, i
 // sequential steps inside a panel run in warp 0 on registers: each lane holds its row
 // of the diagonal block and its entry of f, the pivot entries are broadcast by
 // shuffles, so no step waits on a memory load.
+// f <- (I_m (x) L^-1) f (transpose = false) or (I_m (x) L^-T) f, L^-1 lower triangular
+// [Np][Np]; tmp holds nu floats.
+__device__ void mass_apply(const Dims& dm, const float* __restrict__ Linv, float* f, float* tmp, bool transpose) {
+  const int Np = dm.Np;
+  for (int r = threadIdx.x; r < dm.nu; r += RF_THREADS) {
+    const int i = r / Np, a = r % Np;
+    const float* fi = f + i * Np;
+    float s = 0.f;
+    if (!transpose)
+      for (int b = 0; b <= a; ++b) s = fmaf(Linv[a * Np + b], fi[b], s);
+    else
+      for (int b = a; b < Np; ++b) s = fmaf(Linv[b * Np + a], fi[b], s);
+    tmp[r] = s;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < dm.nu; r += RF_THREADS) f[r] = tmp[r];
+  __syncthreads();
+}
+
+// With a mass scaling (Linv != null) the factors are those of S A~ S^T, S = I (x) L^-1,
+// and A~^-1 = S^T (S A~ S^T)^-1 S; f + nu serves as the scratch of the two products.
 __device__ void solve32(const Dims& dm, const float* __restrict__ A, int ld, const int* __restrict__ piv, double* v,
-                        float* f, double* red) {
+                        float* f, double* red, const float* __restrict__ Linv) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = RF_THREADS / 32;
   const int nu = dm.nu;
   double mx = 0.0;
@@ -415,6 +436,7 @@ __device__ void solve32(const Dims& dm, const float* __restrict__ A, int ld, con
   const double sc = mx > 0.0 ? mx : 1.0;
   for (int i = tid; i < nu; i += RF_THREADS) f[i] = (float)(v[i] / sc);
   __syncthreads();
+  if (Linv) mass_apply(dm, Linv, f, f + nu, false);
   for (int kb = 0; kb < nu; kb += RF_NB) {
     const int nb = min(RF_NB, nu - kb);
     if (warp == 0) {
@@ -487,6 +509,7 @@ __device__ void solve32(const Dims& dm, const float* __restrict__ A, int ld, con
     }
     __syncthreads();
   }
+  if (Linv) mass_apply(dm, Linv, f, f + nu, true);
   for (int i = tid; i < nu; i += RF_THREADS) v[i] = sc * (double)f[i];
   __syncthreads();
 }
@@ -495,12 +518,12 @@ __device__ void solve32(const Dims& dm, const float* __restrict__ A, int ld, con
 // A~ x, C~ x for that x (w.z must be zero).  Returns the final relative residual.
 __device__ double refine_solve(const Dims& dm, const Phys& ph, const RefTables& ref, const Geo& G,
                                const PointJac& PJ, const TraceTab& tt, int64_t e, const float* A, int ld,
-                               const int* piv, Work& w, int max_iter) {
+                               const int* piv, Work& w, int max_iter, const float* Linv) {
   const int tid = threadIdx.x, nu = dm.nu;
   double bn = 0.0;
   for (int i = tid; i < nu; i += RF_THREADS) { w.v[i] = w.b[i]; bn = fmax(bn, fabs(w.b[i])); }
   bn = block_max(bn, w.red);
-  solve32(dm, A, ld, piv, w.v, reinterpret_cast<float*>(w.ou), w.red);
+  solve32(dm, A, ld, piv, w.v, reinterpret_cast<float*>(w.ou), w.red, Linv);
   for (int i = tid; i < nu; i += RF_THREADS) w.x[i] = w.v[i];
   __syncthreads();
   double rel = 0.0;
@@ -515,7 +538,7 @@ __device__ double refine_solve(const Dims& dm, const Phys& ph, const RefTables& 
     rn = block_max(rn, w.red);
     rel = bn > 0.0 ? rn / bn : rn;
     if (!(rel > kRefineTol) || it == max_iter) break;   // also stops on NaN
-    solve32(dm, A, ld, piv, w.v, reinterpret_cast<float*>(w.ou), w.red);
+    solve32(dm, A, ld, piv, w.v, reinterpret_cast<float*>(w.ou), w.red, Linv);
     for (int i = tid; i < nu; i += RF_THREADS) w.x[i] += w.v[i];
     __syncthreads();
   }
@@ -526,7 +549,7 @@ __device__ double refine_solve(const Dims& dm, const Phys& ph, const RefTables& 
 __global__ void __launch_bounds__(RF_THREADS, 2)
 k_refine(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ, TraceTab tt, const float* __restrict__ S32,
          const int* __restrict__ piv, const double* __restrict__ rhs64, double* __restrict__ y64,
-         double* __restrict__ re64, int8_t* __restrict__ status, int max_iter) {
+         double* __restrict__ re64, int8_t* __restrict__ status, int max_iter, const float* __restrict__ Linv32) {
   extern __shared__ double sm[];
   Work w = carve(dm, sm);
   const int64_t e = blockIdx.x;
@@ -538,7 +561,8 @@ k_refine(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ, TraceTab tt, const
   __syncthreads();
   const float* A = S32 + (tt.soff ? tt.soff[e] : e * (int64_t)dm.n * dm.ld);
   const int ld = tt.ldv ? tt.ldv[e] : dm.ld;
-  double rel = refine_solve(dm, ph, ref, G, PJ, tt, e, A, ld, piv + e * dm.nu, w, max_iter);
+  double rel = refine_solve(dm, ph, ref, G, PJ, tt, e, A, ld, piv + e * dm.nu, w, max_iter,
+                            Linv32 ? Linv32 + e * (int64_t)dm.Np * dm.Np : nullptr);
   for (int i = tid; i < dm.nu; i += RF_THREADS) y64[e * dm.nu + i] = w.x[i];
   // trace rows of the right-hand side: packed by the element's slot count
   const int nbe = tt.nb ? tt.nb[e] : dm.Nb;
@@ -554,7 +578,7 @@ __global__ void __launch_bounds__(RF_THREADS, 2)
 k_backsub_mixed(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ, TraceTab tt, const int64_t* __restrict__ etrace,
                 const float* __restrict__ S32, const int* __restrict__ piv, const double* __restrict__ rhs64,
                 const double* __restrict__ rhoq, const double* __restrict__ duhat, double* __restrict__ du,
-                double* __restrict__ dq, int max_iter) {
+                double* __restrict__ dq, int max_iter, const float* __restrict__ Linv32) {
   extern __shared__ double sm[];
   Work w = carve(dm, sm);
   const int64_t e = blockIdx.x;
@@ -575,7 +599,8 @@ k_backsub_mixed(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ, TraceTab tt
   __syncthreads();
   const float* A = S32 + (tt.soff ? tt.soff[e] : e * (int64_t)dm.n * dm.ld);
   const int ld = tt.ldv ? tt.ldv[e] : dm.ld;
-  refine_solve(dm, ph, ref, G, PJ, tt, e, A, ld, piv + e * dm.nu, w, max_iter);
+  refine_solve(dm, ph, ref, G, PJ, tt, e, A, ld, piv + e * dm.nu, w, max_iter,
+               Linv32 ? Linv32 + e * (int64_t)dm.Np * dm.Np : nullptr);
   for (int i = tid; i < dm.nt; i += RF_THREADS) {          // dU_e again, for dq
     int k = i / Nb, t = i % Nb;
     w.z[i] = t < nbe ? duhat[etrace[e * Nb + t] * m + k] : 0.0;
@@ -604,7 +629,8 @@ cudaError_t launch_refine(iedg_mesh* M, cudaStream_t st) {
   cudaError_t err = cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   k_refine<<<(unsigned)M->E, RF_THREADS, smem, st>>>(dm, M->ph, M->ref, M->geo, M->pj, M->tt, M->S32, M->piv, M->rhs64,
-                                                      M->y64, M->re64, M->status, refine_iters(M));
+                                                      M->y64, M->re64, M->status, refine_iters(M),
+                                                      M->mass_scaled ? M->Linv32 : nullptr);
   return cudaGetLastError();
 }
 
@@ -615,7 +641,7 @@ cudaError_t launch_backsub_mixed(iedg_mesh* M, const double* duhat, double* du, 
   if (err != cudaSuccess) return err;
   k_backsub_mixed<<<(unsigned)M->E, RF_THREADS, smem, st>>>(dm, M->ph, M->ref, M->geo, M->pj, M->tt, M->etrace, M->S32,
                                                              M->piv, M->rhs64, M->rhoq, duhat, du, dq,
-                                                             refine_iters(M));
+                                                             refine_iters(M), M->mass_scaled ? M->Linv32 : nullptr);
   return cudaGetLastError();
 }
 

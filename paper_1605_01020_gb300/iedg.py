@@ -41,7 +41,8 @@ class MeshDesc(ctypes.Structure):
                 ("node_xyz", ctypes.c_void_p), ("elem_trace", ctypes.c_void_p),
                 ("gamma", ctypes.c_double), ("Pr", ctypes.c_double), ("Re", ctypes.c_double),
                 ("Minf", ctypes.c_double), ("alpha", ctypes.c_double), ("stab", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("flags", ctypes.c_int32)]
+FLAG_MASS_SCALING = 1
 
 
 class Schedule(ctypes.Structure):
@@ -151,7 +152,7 @@ class Mesh:
     """Handle around iedg_create_mesh / iedg_destroy_mesh with the compute calls."""
 
     def __init__(self, node_xyz, elem_trace, n_trace, order, gamma=1.4, Pr=0.72, Re=1e3, Minf=0.2,
-                 alpha=0.0, quad_extra=2, precision=0, stream=None, stab=0):
+                 alpha=0.0, quad_extra=2, precision=0, stream=None, stab=0, flags=0):
         lib = load()
         X = np.ascontiguousarray(node_xyz, dtype=np.float64)
         ET = np.ascontiguousarray(elem_trace, dtype=np.int64)
@@ -161,7 +162,7 @@ class Mesh:
         self.order = int(order)
         self.alpha = float(alpha)
         desc = MeshDesc(self.d, self.order, quad_extra, precision, self.E, self.T,
-                        X.ctypes.data, ET.ctypes.data, gamma, Pr, Re, Minf, alpha, int(stab), 0)
+                        X.ctypes.data, ET.ctypes.data, gamma, Pr, Re, Minf, alpha, int(stab), int(flags))
         h = ctypes.c_void_p()
         rc = lib.iedg_create_mesh(ctypes.byref(desc), ctypes.c_void_p(_stream(stream)), ctypes.byref(h))
         if rc != OK:
@@ -419,9 +420,9 @@ class MixedOrderMesh(Mesh):
         self.orders_key = "|orders" + ",".join(f"{p}:{c}" for p, c in enumerate(counts) if c) + f"|E{self.E}"
 
 
-def mesh_from_workload(wl, precision=0, stream=None, quad_extra=2):
+def mesh_from_workload(wl, precision=0, stream=None, quad_extra=2, flags=0):
     """Convenience: a Mesh for a workloads.Workload."""
     p = wl.params
     return Mesh(wl.mesh.node_xyz, wl.mesh.elem_trace, wl.mesh.n_trace, wl.mesh.p, gamma=p["gamma"],
                 Pr=p["Pr"], Re=p["Re"], Minf=p["Minf"], alpha=p["alpha"], precision=precision, stream=stream,
-                stab=p.get("stab", 0), quad_extra=quad_extra)
+                stab=p.get("stab", 0), quad_extra=quad_extra, flags=flags)

@@ -79,9 +79,9 @@ def test_descriptor_checks_come_before_the_device():
     X = np.ascontiguousarray(wl.mesh.node_xyz, dtype=np.float64)
     ET = np.ascontiguousarray(wl.mesh.elem_trace, dtype=np.int64)
 
-    def create(precision, stab=0, dim=2, order=wl.mesh.p, quad_extra=2, n_elem=X.shape[0], gamma=1.4):
+    def create(precision, stab=0, dim=2, order=wl.mesh.p, quad_extra=2, n_elem=X.shape[0], gamma=1.4, flags=0):
         desc = iedg.MeshDesc(dim, order, quad_extra, precision, n_elem, wl.mesh.n_trace, X.ctypes.data,
-                             ET.ctypes.data, gamma, 0.72, 1e3, 0.2, 0.0, stab, 0)
+                             ET.ctypes.data, gamma, 0.72, 1e3, 0.2, 0.0, stab, flags)
         h = ctypes.c_void_p()
         rc = lib.iedg_create_mesh(ctypes.byref(desc), ctypes.c_void_p(0), ctypes.byref(h))
         assert not h.value
@@ -98,6 +98,9 @@ def test_descriptor_checks_come_before_the_device():
     assert create(0, order=0) == -6
     assert create(0, quad_extra=0) == -6
     assert create(0, n_elem=0) == -1              # empty mesh
+    assert create(1, flags=iedg.FLAG_MASS_SCALING) == -2    # valid: fails only for want of a device
+    assert create(0, flags=iedg.FLAG_MASS_SCALING) == -1    # mass scaling is for the mixed forms
+    assert create(1, flags=4) == -1                         # unknown flag
     assert create(0, gamma=1.0) == -1             # physical parameters
 
 

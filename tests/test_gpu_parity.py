@@ -256,6 +256,48 @@ def test_mixed_condensed_parity(name, lu_tensor):
     assert rel_err(host(dq_d), dq_o) <= TOL_MIXED
 
 
+@pytest.mark.parametrize("precision", [1, 2, 3])
+@pytest.mark.parametrize("name", ["cfg1-noisy", "p3-2cube", "p2-curved", "p4-2cube"])
+def test_mass_scaled_parity(name, precision):
+    """Mixed forms on the system scaled by the element mass matrix (S = I (x) L^-1,
+    M = L L^T, applied to the u-block): the FP32 form's K against the plain K at the
+    FP32 bound, the TF32 / BF16 forms against the oracle's rounded-operand condensation
+    of the scaled system; R, du, dq refined to FP64 with the scaled factors."""
+    from paper_1605_01020_gb300 import iedg
+    wl = _case(name)
+    st = wl.state
+    pb = problem(wl.mesh, wl.params)
+    E = wl.mesh.n_elem
+    Ke, Re = zip(*[pb.condense_qelim(e, st.u, st.q, st.uhat, st.u_ref) for e in range(E)])
+    row_ptr, col, vals, R = oiedg.assemble(wl.mesh.elem_trace, wl.mesh.n_trace, np.array(Ke), np.array(Re))
+    mesh = iedg.mesh_from_workload(wl, precision=precision, flags=iedg.FLAG_MASS_SCALING)
+    K_d, R_d = mesh.assemble_condensed(dev(st.u), dev(st.q), dev(st.uhat), u_ref=dev(st.u_ref))
+    K_h = host(K_d)
+    rows = range(wl.mesh.n_trace)
+    kerr = bsr_row_err(row_ptr, K_h, vals, rows)
+    rerr = rel_err(host(R_d), R, floor=np.abs(np.array(Re)).max())
+    du_d, dq_d = mesh.back_substitute(dev(st.duhat))
+    du_o = np.zeros_like(st.u)
+    dq_o = np.zeros_like(st.q)
+    for e in range(E):
+        du_o[e], dq_o[e] = pb.back_substitute_qelim(e, st.u, st.q, st.uhat, st.duhat, st.u_ref)
+    msg = f"{name} precision {precision} mass-scaled: K {kerr:.2e}  R {rerr:.2e}"
+    assert (mesh.element_status() == 0).all()
+    if precision == 1:
+        assert kerr <= TOL_MIXED_K, msg
+    else:
+        Kl = [lowprec.condense_rounded(pb, pb.element_blocks(e, st.u, st.q, st.uhat, st.u_ref), LOW_FMT[precision],
+                                       mass_scaled=True)[0] for e in range(E)]
+        _, _, vals_low, _ = oiedg.assemble(wl.mesh.elem_trace, wl.mesh.n_trace, np.array(Kl), np.array(Re))
+        ratio = fro_ratio(row_ptr, K_h, vals_low, vals, rows)
+        msg += f" (vs scaled rounded-operand oracle: {ratio:.3f} of the rounding's effect)"
+        assert ratio <= LOW_RATIO, msg
+    print(msg)
+    assert rerr <= TOL_MIXED, msg
+    assert rel_err(host(du_d), du_o) <= TOL_MIXED
+    assert rel_err(host(dq_d), dq_o) <= TOL_MIXED
+
+
 @pytest.mark.parametrize("precision", [2, 3])
 @pytest.mark.parametrize("name", ["cfg1-noisy", "p3-2cube", "p2-curved", "p4-2cube", "p3-2cube-roe"])
 def test_low_precision_schur_parity(name, precision):
@@ -317,15 +359,17 @@ def test_quad_extra_parity(name, precision, quad_extra):
     assert rel_err(host(dq_d), dq_o) <= tr
 
 
-@pytest.mark.parametrize("cfg,precision,lu_tensor", [(2, 1, 1), (2, 1, 2), (3, 1, 0), (3, 1, 2), (3, 2, 1),
-                                                    (3, 3, 1)])
-def test_mixed_full_size_sampled(cfg, precision, lu_tensor):
+@pytest.mark.parametrize("cfg,precision,lu_tensor,scaled", [(2, 1, 1, 0), (2, 1, 2, 0), (3, 1, 0, 0), (3, 1, 2, 0),
+                                                           (3, 2, 1, 0), (3, 3, 1, 0), (3, 1, 0, 1), (3, 2, 1, 1),
+                                                           (3, 3, 1, 1)])
+def test_mixed_full_size_sampled(cfg, precision, lu_tensor, scaled):
     """The 16^3 p=3 workloads (config 3: stretched and sheared, aspect up to 50) in the
     mixed forms at full size (FP32 Schur complement; on config 3 also TF32 and BF16
     operands): sampled block rows of K and R, sampled updates."""
     wl = W.config(cfg)
     st = wl.state
-    mesh = _mixed_mesh(wl, precision)
+    from paper_1605_01020_gb300 import iedg
+    mesh = iedg.mesh_from_workload(wl, precision=precision, flags=iedg.FLAG_MASS_SCALING if scaled else 0)
     mesh.set_schedule(lu_tensor=lu_tensor)
     u, q, uh = dev(st.u), dev(st.q), dev(st.uhat)
     K_d, R_d = mesh.assemble_condensed(u, q, uh)
@@ -341,14 +385,14 @@ def test_mixed_full_size_sampled(cfg, precision, lu_tensor):
     ratio = None
     if precision in LOW_FMT:
         kfun = lambda e: lowprec.condense_rounded(pb, pb.element_blocks(e, st.u, st.q, st.uhat),
-                                                  LOW_FMT[precision])[0]
+                                                  LOW_FMT[precision], mass_scaled=bool(scaled))[0]
         vals_low = oracle_K_rows(pb, wl.mesh, st, rows, kfun=kfun)[2]
         ratio = fro_ratio(row_ptr, K_h, vals_low, vals, rows)
     e = els[0]
     du_o, dq_o = pb.back_substitute_qelim(e, st.u, st.q, st.uhat, st.duhat)
     duerr, dqerr = rel_err(host(du_d[e]), du_o), rel_err(host(dq_d[e]), dq_o)
     cond = _cond1(pb, st, [e])
-    print(f"config {cfg} precision {precision} lu_tensor {lu_tensor}: K {kerr:.2e}  R {rerr:.2e}  du {duerr:.2e}  dq {dqerr:.2e}  "
+    print(f"config {cfg} precision {precision} lu_tensor {lu_tensor} mass-scaled {scaled}: K {kerr:.2e}  R {rerr:.2e}  du {duerr:.2e}  dq {dqerr:.2e}  "
           f"cond1(A~) {max(cond):.2e}  flagged {int((status != 0).sum())}"
           + ("" if ratio is None else f"  K vs rounded-operand oracle {ratio:.3f} of the rounding's effect"))
     assert (status == 0).all()

@@ -158,6 +158,16 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def unit_peaks():
+    """Measured peak rates of the arithmetic units (TFLOP/s) from the committed probe
+    record profiles/peaks_gb300.txt (its last JSON line), or {} when absent."""
+    path = os.path.join(ROOT, "profiles", "peaks_gb300.txt")
+    if not os.path.exists(path):
+        return {}
+    lines = [ln for ln in open(path) if ln.strip().startswith("{")]
+    return json.loads(lines[-1]) if lines else {}
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -425,7 +435,14 @@ def run_ours(args, wl, rank, world, local_rank):
     tot_ms = sum(v[1] for v in prof.values())
     props = torch.cuda.get_device_properties(dev)
     sm_max = clocks["sm_max_mhz"] or 2070.0
+    up = unit_peaks()
     peak_alu = props.multi_processor_count * DFMA_PER_CLK_PER_SM * 2 * sm_max * 1e6
+    peak_src = (f"FP64 DFMA: {props.multi_processor_count} SMs x {DFMA_PER_CLK_PER_SM} FMA/clk x 2 x {sm_max:.0f} MHz "
+                f"(derived)")
+    if up.get("dfma_tflops"):
+        peak_alu = up["dfma_tflops"] * 1e12
+        peak_src = (f"FP64 DFMA, measured: {up['dfma_tflops']} TFLOP/s (profiles/peaks_gb300.txt; derived "
+                    f"{props.multi_processor_count * DFMA_PER_CLK_PER_SM * 2 * sm_max * 1e6 / 1e12:.3f})")
     nq1 = wl.mesh.p + 2
     flops = {"lu_schur": a6_flops(m * Np, m * mesh.Nb) * E,
              "assemble": a4a5_flops(d, wl.mesh.p, nq1) * E}
@@ -438,8 +455,7 @@ def run_ours(args, wl, rank, world, local_rank):
         achieved = flops[name] / t_launch
         roof = {"kernel": name, "bound": "alu", "achieved": achieved / 1e12, "peak": peak_alu / 1e12,
                 "unit": "TFLOP/s", "frac": achieved / peak_alu, "traffic": traffic.get(name),
-                "peak_source": f"FP64 DFMA: {props.multi_processor_count} SMs x {DFMA_PER_CLK_PER_SM} FMA/clk x 2 "
-                               f"x {sm_max:.0f} MHz (derived; measured DFMA loop 1.19 TFLOP/s)",
+                "peak_source": peak_src,
                 "algorithmic_flops_per_launch": flops[name],
                 "actual_flops_per_launch": actual[name],
                 "frac_actual": actual[name] / t_launch / peak_alu}
@@ -541,14 +557,24 @@ def run_mixed(args, wl, mesh64, dev, step_outputs, inputs, flush, barrier, preci
     if "lu_schur" in prof:
         launches, kms = prof["lu_schur"]
         props = torch.cuda.get_device_properties(dev)
+        up = unit_peaks()
         peak = props.multi_processor_count * FFMA_PER_CLK_PER_SM * 2 * 2070.0e6
+        src = f"FP32 FFMA: {props.multi_processor_count} SMs x {FFMA_PER_CLK_PER_SM} FMA/clk x 2 x 2070 MHz (derived)"
+        if up.get("ffma_tflops"):
+            peak, src = up["ffma_tflops"] * 1e12, f"FP32 FFMA, measured: {up['ffma_tflops']} TFLOP/s"
         fl = a6_flops(m * Np, m * mesh.Nb) * E
         ach = fl / (kms / launches / 1e3)
+        sched = mesh.get_schedule()
         roof = {"kernel": "lu_schur", "bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12,
                 "unit": "TFLOP/s", "frac": ach / peak, "algorithmic_flops_per_launch": fl,
-                "peak_source": f"FP32 FFMA: {props.multi_processor_count} SMs x {FFMA_PER_CLK_PER_SM} FMA/clk x 2 "
-                               f"x 2070 MHz (derived)",
-                "share_of_step": kms / tot if tot else None}
+                "peak_source": src, "share_of_step": kms / tot if tot else None, "lu_form": sched["lu_tensor"]}
+        if up.get("tf32_tcgen05_tflops") and (sched["lu_tensor"] or precision in (2, 3)):
+            # the tensor-core forms against the measured TF32 tcgen05 rate (the FP32 form
+            # issues three TF32 products per trailing-update flop: 3xTF32)
+            tp = up["tf32_tcgen05_tflops"] * 1e12
+            roof["tensor"] = {"bound": "tensor", "peak": tp / 1e12, "unit": "TFLOP/s",
+                              "frac_algorithmic": ach / tp,
+                              "peak_source": f"tcgen05 kind::tf32, measured: {up['tf32_tcgen05_tflops']} TFLOP/s"}
     out = {"ms_total": e0.elapsed_time(e1),
            "precision": MIXED_FORMS[precision] + ("; element systems scaled by the mass matrix's inverse Cholesky "
                                                   "factor before the factorisation" if flags else ""),

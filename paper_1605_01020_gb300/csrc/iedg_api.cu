@@ -314,6 +314,8 @@ static int setup_pattern(iedg_mesh* M, const std::vector<const int64_t*>& lists,
   }
   std::vector<int64_t>().swap(rc_el);
   M->nnzb = (int64_t)col.size();
+  M->max_row_blocks = 0;
+  for (int64_t r = 0; r < T; ++r) M->max_row_blocks = std::max(M->max_row_blocks, row_ptr[r + 1] - row_ptr[r]);
   // K gather lists, stable in element order
   int64_t nk = 0;
   for (int64_t e = 0; e < E; ++e) nk += (int64_t)lens[e] * lens[e];

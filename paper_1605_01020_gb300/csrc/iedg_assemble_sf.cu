@@ -222,33 +222,59 @@ k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, 
         __syncthreads();
       }
     }
-    // ---- volume right operands W_r[g][c] for the three reference directions
-    for (int idx = tid; idx < Nq * CC; idx += SF_THREADS) {
-      const int g = idx / CC, c = idx % CC, col = c0 + c;
-      T w0 = 0, w1 = 0, w2 = 0;
-      if (col < Np) {
-        const T ph_ = tb.Phi[(size_t)g * Np + col];
-        w0 = cV[0 * Nq + g] * ph_;
-        w1 = cV[1 * Nq + g] * ph_;
-        w2 = cV[2 * Nq + g] * ph_;
-        if (has_cq)
-          for (int l = 0; l < d; ++l) {
-            const T gv = GlV[((size_t)l * Nq + g) * Np + col];
-            w0 -= cV[(d + l * d + 0) * Nq + g] * gv;
-            w1 -= cV[(d + l * d + 1) * Nq + g] * gv;
-            w2 -= cV[(d + l * d + 2) * Nq + g] * gv;
+    // ---- volume right operands W_r[g][c] for the three reference directions.  The
+    // table values of all of this thread's (g, c) entries are requested first, then
+    // combined, so their latencies overlap instead of adding up.
+    {
+      constexpr int WPT = (Nq * CC + SF_THREADS - 1) / SF_THREADS;
+      T lv[WPT][4];
+#pragma unroll
+      for (int u = 0; u < WPT; ++u) {
+        const int idx = tid + u * SF_THREADS, g = idx / CC, c = idx % CC, col = c0 + c;
+        lv[u][0] = lv[u][1] = lv[u][2] = lv[u][3] = 0;
+        if (idx < Nq * CC) {
+          if (col < Np) {
+            lv[u][0] = tb.Phi[(size_t)g * Np + col];
+            if (has_cq)
+#pragma unroll
+              for (int l = 0; l < d; ++l) lv[u][1 + l] = GlV[((size_t)l * Nq + g) * Np + col];
+          } else if (col < ncol_vol) {
+#pragma unroll
+            for (int l = 0; l < d; ++l) lv[u][1 + l] = HlV[((size_t)l * Nq + g) * NbT + (col - Np)];
           }
-      } else if (col < ncol_vol) {
-        for (int l = 0; l < d; ++l) {
-          const T hv = HlV[((size_t)l * Nq + g) * NbT + (col - Np)];
-          w0 += cV[(d + l * d + 0) * Nq + g] * hv;
-          w1 += cV[(d + l * d + 1) * Nq + g] * hv;
-          w2 += cV[(d + l * d + 2) * Nq + g] * hv;
         }
       }
-      W[(0 * Nq + g) * CC + c] = w0;
-      W[(1 * Nq + g) * CC + c] = w1;
-      W[(2 * Nq + g) * CC + c] = w2;
+#pragma unroll
+      for (int u = 0; u < WPT; ++u) {
+        const int idx = tid + u * SF_THREADS, g = idx / CC, c = idx % CC, col = c0 + c;
+        if (idx >= Nq * CC) break;
+        T w0 = 0, w1 = 0, w2 = 0;
+        if (col < Np) {
+          const T ph_ = lv[u][0];
+          w0 = cV[0 * Nq + g] * ph_;
+          w1 = cV[1 * Nq + g] * ph_;
+          w2 = cV[2 * Nq + g] * ph_;
+          if (has_cq)
+#pragma unroll
+            for (int l = 0; l < d; ++l) {
+              const T gv = lv[u][1 + l];
+              w0 -= cV[(d + l * d + 0) * Nq + g] * gv;
+              w1 -= cV[(d + l * d + 1) * Nq + g] * gv;
+              w2 -= cV[(d + l * d + 2) * Nq + g] * gv;
+            }
+        } else if (col < ncol_vol) {
+#pragma unroll
+          for (int l = 0; l < d; ++l) {
+            const T hv = lv[u][1 + l];
+            w0 += cV[(d + l * d + 0) * Nq + g] * hv;
+            w1 += cV[(d + l * d + 1) * Nq + g] * hv;
+            w2 += cV[(d + l * d + 2) * Nq + g] * hv;
+          }
+        }
+        W[(0 * Nq + g) * CC + c] = w0;
+        W[(1 * Nq + g) * CC + c] = w1;
+        W[(2 * Nq + g) * CC + c] = w2;
+      }
     }
     __syncthreads();
     // stage A: contract g_z.  T_r[gx,gy,az] = sum_gz X_r(gz, az) W_r[gx,gy,gz], X_2 = L', else L

@@ -155,6 +155,7 @@ struct iedg_mesh {
   iedg::Dims dm;
   iedg::Phys ph;
   int64_t E = 0, T = 0, nnzb = 0;
+  int64_t max_row_blocks = 0;   // longest block row of K (blocks)
   iedg::RefTables ref{};
   iedg::Geo geo{};
   iedg::PointJac pj{};

@@ -105,11 +105,13 @@ __global__ void __launch_bounds__(MS_THREADS) k_scale_cols(Dims dm, const float*
   const int Np = dm.Np, n = dm.n;
   const int64_t e = blockIdx.x / dm.m;
   const int k = blockIdx.x % dm.m, tid = threadIdx.x;
-  float* Li = fs;                      // [Np][Np]
-  float* st = Li + Np * Np;            // [MS_CH][Np + 1]
+  // L^-1 with its rows padded to Np + 1 values: the threads of a warp read one column
+  // b of 32 consecutive rows a, which then fall in 32 different banks
   const int sp = Np + 1;
+  float* Li = fs;                      // [Np][Np + 1]
+  float* st = Li + Np * sp;            // [MS_CH][Np + 1]
   const float* L = Linv32 + (size_t)e * Np * Np;
-  for (int q = tid; q < Np * Np; q += MS_THREADS) Li[q] = L[q];
+  for (int q = tid; q < Np * Np; q += MS_THREADS) Li[(q / Np) * sp + q % Np] = L[q];
   float* C = S + e * (int64_t)n * dm.ld + (int64_t)k * Np;
   for (int r0 = 0; r0 < n; r0 += MS_CH) {
     __syncthreads();
@@ -121,7 +123,7 @@ __global__ void __launch_bounds__(MS_THREADS) k_scale_cols(Dims dm, const float*
     for (int q = tid; q < MS_CH * Np; q += MS_THREADS) {
       const int r = q / Np, a = q % Np;
       float s = 0.f;
-      for (int b = 0; b <= a; ++b) s = fmaf(st[r * sp + b], Li[a * Np + b], s);
+      for (int b = 0; b <= a; ++b) s = fmaf(st[r * sp + b], Li[a * sp + b], s);
       if (r0 + r < n) C[(int64_t)(r0 + r) * dm.ld + a] = s;
     }
   }
@@ -141,7 +143,7 @@ cudaError_t launch_mass_chol(iedg_mesh* M, cudaStream_t st) {
 cudaError_t launch_mass_scale(iedg_mesh* M, cudaStream_t st) {
   const Dims& dm = M->dm;
   const size_t s1 = sizeof(float) * ((size_t)dm.Np * dm.Np + (size_t)dm.Np * MS_CH);
-  const size_t s2 = sizeof(float) * ((size_t)dm.Np * dm.Np + (size_t)MS_CH * (dm.Np + 1));
+  const size_t s2 = sizeof(float) * ((size_t)dm.Np * (dm.Np + 1) + (size_t)MS_CH * (dm.Np + 1));
   cudaError_t err = cudaFuncSetAttribute(k_scale_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1);
   if (err == cudaSuccess)
     err = cudaFuncSetAttribute(k_scale_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2);

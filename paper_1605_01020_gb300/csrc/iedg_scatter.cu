@@ -53,6 +53,57 @@ __global__ void k_zero_row(T* __restrict__ row, int ncol, double* __restrict__ r
   if (threadIdx.x == 0 && rhs_entry) *rhs_entry = 0.0;
 }
 
+// Uniform meshes: one CTA per block row r of K.  The row's blocks accumulate in shared
+// memory; each contribution (element e, slot s) reads the element's m trace rows of
+// slot s (m x m Nb contiguous values per row: coalesced) and adds them to the blocks
+// of the columns its slots map to (found by binary search in the row's sorted column
+// list).  Contributions run in element order, as in k_scatter_K, so every block is the
+// same sum in the same order; the row is then written out contiguously.
+constexpr int SK_THREADS = 256;
+template <class T>
+__global__ void __launch_bounds__(SK_THREADS)
+k_scatter_K_rows(Dims dm, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                 const int64_t* __restrict__ rc_ptr, const int64_t* __restrict__ rc_src,
+                 const int64_t* __restrict__ etrace, const T* __restrict__ S, double* __restrict__ K,
+                 const int* __restrict__ fb_slot, const double* __restrict__ fbS, const int* __restrict__ fb_count) {
+  extern __shared__ double acc[];            // [blocks of the row][m][m]
+  __shared__ int bmap[128];                  // slot t of the current element -> block of the row
+  const int64_t r = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int m = dm.m, m2 = m * m, Nb = dm.Nb, mNb = m * Nb;
+  const int64_t b0 = row_ptr[r];
+  const int nblk = (int)(row_ptr[r + 1] - b0);
+  const int64_t n = dm.n, ld = dm.ld, nu = dm.nu;
+  for (int i = tid; i < nblk * m2; i += SK_THREADS) acc[i] = 0.0;
+  const bool fb = fb_count != nullptr && *fb_count > 0;
+  for (int64_t c = rc_ptr[r]; c < rc_ptr[r + 1]; ++c) {
+    const int64_t src = rc_src[c];
+    const int64_t e = src / Nb;
+    const int s = (int)(src % Nb);
+    __syncthreads();                         // the previous contribution is done with bmap
+    for (int t = tid; t < Nb; t += SK_THREADS) {
+      const int32_t cc = (int32_t)etrace[e * Nb + t];
+      int lo = 0, hi = nblk;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (col[b0 + mid] < cc) lo = mid + 1;
+        else hi = mid;
+      }
+      bmap[t] = lo;
+    }
+    __syncthreads();
+    const int sl = fb ? fb_slot[e] : -1;
+    for (int idx = tid; idx < m * mNb; idx += SK_THREADS) {
+      const int i = idx / mNb, kt = idx % mNb, k = kt / Nb, t = kt % Nb;
+      const int64_t off = (nu + (int64_t)i * Nb + s) * ld + nu + kt;
+      const double v = sl >= 0 ? fbS[(int64_t)sl * n * ld + off] : (double)S[e * n * ld + off];
+      acc[bmap[t] * m2 + i * m + k] += v;
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < nblk * m2; i += SK_THREADS) K[b0 * m2 + i] = acc[i];
+}
+
 // Ragged form of k_scatter_R: contributions packed as e P + s, values located by src.
 __global__ void k_scatter_R_ragged(int m, int64_t T, int64_t P, const int64_t* __restrict__ rc_ptr,
                                    const int64_t* __restrict__ rc_src, RaggedSrc rs,
@@ -173,6 +224,25 @@ cudaError_t launch_zero_row(iedg_mesh* M, cudaStream_t st) {
 cudaError_t launch_scatter_K(iedg_mesh* M, double* K, cudaStream_t st) {
   const int64_t total = M->nnzb * M->dm.m * M->dm.m;
   if (total == 0) return cudaSuccess;
+  const size_t rsm = sizeof(double) * (size_t)M->max_row_blocks * M->dm.m * M->dm.m;
+  if (M->lud.soff == nullptr && M->dm.Nb <= 128 && rsm <= 200 * 1024) {
+    // uniform meshes: one CTA per block row, coalesced reads of the element rows
+    cudaError_t err;
+    if (M->precision == 0) {
+      err = cudaFuncSetAttribute(k_scatter_K_rows<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+      if (err != cudaSuccess) return err;
+      k_scatter_K_rows<double><<<(unsigned)M->T, SK_THREADS, rsm, st>>>(M->dm, M->row_ptr, M->col, M->rc_ptr,
+                                                                        M->rc_src, M->etrace, M->S, K, nullptr,
+                                                                        nullptr, nullptr);
+    } else {
+      err = cudaFuncSetAttribute(k_scatter_K_rows<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+      if (err != cudaSuccess) return err;
+      k_scatter_K_rows<float><<<(unsigned)M->T, SK_THREADS, rsm, st>>>(M->dm, M->row_ptr, M->col, M->rc_ptr,
+                                                                       M->rc_src, M->etrace, M->S32, K, M->fb_slot,
+                                                                       M->fb_S, M->fb_S ? M->fb_count : nullptr);
+    }
+    return cudaGetLastError();
+  }
   const int th = 256;
   const unsigned grid = (unsigned)((total + th - 1) / th);
   if (M->precision == 0)

@@ -69,19 +69,23 @@ __global__ void __launch_bounds__(MS_THREADS) k_mass_chol(int Np, const double* 
 }
 
 constexpr int MS_CH = 64;     // columns (rows) per staged chunk
+constexpr int MS_T = 4;       // register tile MS_T x MS_T per thread
 
-// u-rows of component i: R_i <- L^-1 R_i over all n + 1 columns.
+// u-rows of component i: R_i <- L^-1 R_i over all n + 1 columns (L^-1 is stored with
+// zeros above its diagonal, so the tile sums simply stop at the tile's last row).
 __global__ void __launch_bounds__(MS_THREADS) k_scale_rows(Dims dm, const float* __restrict__ Linv32,
                                                            float* __restrict__ S) {
   extern __shared__ float fs[];
   const int Np = dm.Np, ncol = dm.n + 1;
   const int64_t e = blockIdx.x / dm.m;
   const int i = blockIdx.x % dm.m, tid = threadIdx.x;
-  float* Li = fs;                      // [Np][Np]
-  float* st = Li + Np * Np;            // [Np][MS_CH]
+  const int sp = Np + 1;
+  float* Li = fs;                      // [Np][Np + 1]
+  float* st = Li + ((Np * sp + 3) & ~3);   // [Np][MS_CH], 16-byte aligned (float4 reads)
   const float* L = Linv32 + (size_t)e * Np * Np;
-  for (int q = tid; q < Np * Np; q += MS_THREADS) Li[q] = L[q];
+  for (int q = tid; q < Np * Np; q += MS_THREADS) Li[(q / Np) * sp + q % Np] = L[q];
   float* R = S + (e * (int64_t)dm.n + (int64_t)i * Np) * dm.ld;
+  const int rt = (Np + MS_T - 1) / MS_T, ct = MS_CH / MS_T;
   for (int c0 = 0; c0 < ncol; c0 += MS_CH) {
     __syncthreads();
     for (int q = tid; q < Np * MS_CH; q += MS_THREADS) {
@@ -89,11 +93,28 @@ __global__ void __launch_bounds__(MS_THREADS) k_scale_rows(Dims dm, const float*
       st[q] = c0 + c < ncol ? R[(int64_t)b * dm.ld + c0 + c] : 0.f;
     }
     __syncthreads();
-    for (int q = tid; q < Np * MS_CH; q += MS_THREADS) {
-      const int a = q / MS_CH, c = q % MS_CH;
-      float s = 0.f;
-      for (int b = 0; b <= a; ++b) s = fmaf(Li[a * Np + b], st[b * MS_CH + c], s);
-      if (c0 + c < ncol) R[(int64_t)a * dm.ld + c0 + c] = s;
+    for (int tq = tid; tq < rt * ct; tq += MS_THREADS) {
+      const int a0 = (tq / ct) * MS_T, cc = (tq % ct) * MS_T;
+      float acc[MS_T][MS_T] = {};
+      const int bend = min(Np, a0 + MS_T);
+      for (int b = 0; b < bend; ++b) {
+        float lv[MS_T];
+#pragma unroll
+        for (int x = 0; x < MS_T; ++x) lv[x] = a0 + x < Np ? Li[(a0 + x) * sp + b] : 0.f;
+        const float4 sv = *reinterpret_cast<const float4*>(st + b * MS_CH + cc);
+#pragma unroll
+        for (int x = 0; x < MS_T; ++x) {
+          acc[x][0] = fmaf(lv[x], sv.x, acc[x][0]);
+          acc[x][1] = fmaf(lv[x], sv.y, acc[x][1]);
+          acc[x][2] = fmaf(lv[x], sv.z, acc[x][2]);
+          acc[x][3] = fmaf(lv[x], sv.w, acc[x][3]);
+        }
+      }
+#pragma unroll
+      for (int x = 0; x < MS_T; ++x)
+#pragma unroll
+        for (int y = 0; y < MS_T; ++y)
+          if (a0 + x < Np && c0 + cc + y < ncol) R[(int64_t)(a0 + x) * dm.ld + c0 + cc + y] = acc[x][y];
     }
   }
 }
@@ -105,14 +126,14 @@ __global__ void __launch_bounds__(MS_THREADS) k_scale_cols(Dims dm, const float*
   const int Np = dm.Np, n = dm.n;
   const int64_t e = blockIdx.x / dm.m;
   const int k = blockIdx.x % dm.m, tid = threadIdx.x;
-  // L^-1 with its rows padded to Np + 1 values: the threads of a warp read one column
-  // b of 32 consecutive rows a, which then fall in 32 different banks
+  // L^-1 with its rows padded to Np + 1 values (conflict-free column reads)
   const int sp = Np + 1;
   float* Li = fs;                      // [Np][Np + 1]
   float* st = Li + Np * sp;            // [MS_CH][Np + 1]
   const float* L = Linv32 + (size_t)e * Np * Np;
   for (int q = tid; q < Np * Np; q += MS_THREADS) Li[(q / Np) * sp + q % Np] = L[q];
   float* C = S + e * (int64_t)n * dm.ld + (int64_t)k * Np;
+  const int at = (Np + MS_T - 1) / MS_T, rt = MS_CH / MS_T;
   for (int r0 = 0; r0 < n; r0 += MS_CH) {
     __syncthreads();
     for (int q = tid; q < MS_CH * Np; q += MS_THREADS) {
@@ -120,11 +141,27 @@ __global__ void __launch_bounds__(MS_THREADS) k_scale_cols(Dims dm, const float*
       st[r * sp + b] = r0 + r < n ? C[(int64_t)(r0 + r) * dm.ld + b] : 0.f;
     }
     __syncthreads();
-    for (int q = tid; q < MS_CH * Np; q += MS_THREADS) {
-      const int r = q / Np, a = q % Np;
-      float s = 0.f;
-      for (int b = 0; b <= a; ++b) s = fmaf(st[r * sp + b], Li[a * sp + b], s);
-      if (r0 + r < n) C[(int64_t)(r0 + r) * dm.ld + a] = s;
+    for (int tq = tid; tq < rt * at; tq += MS_THREADS) {
+      const int rr = (tq / at) * MS_T, a0 = (tq % at) * MS_T;
+      float acc[MS_T][MS_T] = {};
+      const int bend = min(Np, a0 + MS_T);
+      for (int b = 0; b < bend; ++b) {
+        float sv[MS_T], lv[MS_T];
+#pragma unroll
+        for (int x = 0; x < MS_T; ++x) {
+          sv[x] = st[(rr + x) * sp + b];
+          lv[x] = a0 + x < Np ? Li[(a0 + x) * sp + b] : 0.f;
+        }
+#pragma unroll
+        for (int x = 0; x < MS_T; ++x)
+#pragma unroll
+          for (int y = 0; y < MS_T; ++y) acc[x][y] = fmaf(sv[x], lv[y], acc[x][y]);
+      }
+#pragma unroll
+      for (int x = 0; x < MS_T; ++x)
+#pragma unroll
+        for (int y = 0; y < MS_T; ++y)
+          if (r0 + rr + x < n && a0 + y < Np) C[(int64_t)(r0 + rr + x) * dm.ld + a0 + y] = acc[x][y];
     }
   }
 }
@@ -142,7 +179,7 @@ cudaError_t launch_mass_chol(iedg_mesh* M, cudaStream_t st) {
 
 cudaError_t launch_mass_scale(iedg_mesh* M, cudaStream_t st) {
   const Dims& dm = M->dm;
-  const size_t s1 = sizeof(float) * ((size_t)dm.Np * dm.Np + (size_t)dm.Np * MS_CH);
+  const size_t s1 = sizeof(float) * (((size_t)dm.Np * (dm.Np + 1) + 3) / 4 * 4 + (size_t)dm.Np * MS_CH);
   const size_t s2 = sizeof(float) * ((size_t)dm.Np * (dm.Np + 1) + (size_t)MS_CH * (dm.Np + 1));
   cudaError_t err = cudaFuncSetAttribute(k_scale_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1);
   if (err == cudaSuccess)

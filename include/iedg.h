@@ -231,9 +231,10 @@ int64_t iedg_element_status(iedg_mesh* mesh, int8_t* out, void* stream);
  *   rtol > 0: stop when |M^-1 (R - K dU)| <= rtol |M^-1 R| (the GMRES estimate
  *   during a cycle, recomputed at restarts).
  * Outputs iterations and the final relative preconditioned residual (may be NULL).
- * Synchronises `stream` once per Arnoldi step (the small least-squares problem is
- * solved on the host).  Workspace is allocated with the mesh.  IEDG_ERR_INVALID_ARG
- * for a singular diagonal block. */
+ * The Hessenberg matrix, its Givens rotations and the residual estimate are kept and
+ * updated on the device; the host reads the estimate once per Arnoldi step (one
+ * synchronisation of `stream` per step) to decide when to stop.  Workspace is
+ * allocated with the mesh.  IEDG_ERR_INVALID_ARG for a singular diagonal block. */
 #define IEDG_MAX_RESTART 40
 
 /* Preconditioner of iedg_trace_solve (default IEDG_PREC_BLOCK_JACOBI).
@@ -241,7 +242,9 @@ int64_t iedg_element_status(iedg_mesh* mesh, int8_t* out, void* stream);
  *   2.2.2), in multicolour order: trace nodes coloured greedily in index order (each
  *   takes the smallest colour none of its earlier neighbours has, neighbours = nodes
  *   sharing a block of K), then eliminated colour by colour, ties by index.  Nodes of
- *   one colour share no block, so each colour is factored and solved in one launch.
+ *   one colour share no block, so each colour is factored in one launch, and the
+ *   preconditioner solve runs all colours (forward, then backward) in a single
+ *   one-block launch with a block barrier between colours.
  *   (The paper orders by minimum discarded fill, a sequential CPU ordering.)  The
  *   colouring and per-row orders are built on the first use (host work, one device
  *   buffer of nnzb m^2 doubles for the factors). */

@@ -448,6 +448,8 @@ static int alloc_owner(iedg_mesh* M, int64_t S_elems, int64_t piv_elems, int64_t
   CUDA_TRY(dalloc(M, &M->dinv, (size_t)T * m * m));
   CUDA_TRY(dalloc(M, &M->kpart, (size_t)(IEDG_MAX_RESTART + 1) * 512));
   CUDA_TRY(dalloc(M, &M->khdev, (size_t)(IEDG_MAX_RESTART + 1)));
+  CUDA_TRY(dalloc(M, &M->kst, (size_t)(2 * (IEDG_MAX_RESTART + 1) + (IEDG_MAX_RESTART + 1) * IEDG_MAX_RESTART +
+                                       4 * IEDG_MAX_RESTART + 1 + 8)));
   CUDA_TRY(cudaMemsetAsync(M->dev_flag, 0, sizeof(int), st));
   CUDA_TRY(cudaMemsetAsync(M->status, 0, E, st));
   return IEDG_OK;

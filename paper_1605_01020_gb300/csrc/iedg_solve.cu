@@ -129,12 +129,6 @@ __global__ void k_orth(int64_t n, int nv, const double* __restrict__ V, const do
   }
 }
 
-// y = a x (y may alias x)
-__global__ void k_scale(int64_t n, double a, const double* __restrict__ x, double* __restrict__ y) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = a * x[i];
-}
-
 // x += sum_v c[v] V[v]
 __global__ void k_update(int64_t n, int nv, const double* __restrict__ V, const double* __restrict__ c,
                          double* __restrict__ x) {
@@ -309,6 +303,150 @@ __global__ void k_bilu_bwd(int m, int64_t nrows, const int64_t* __restrict__ row
   }
 }
 
+// ---------------------------------------------------------------- GMRES state on the device
+// The Hessenberg column, Givens rotations, least-squares right-hand side and the
+// residual estimate stay in device memory (kst below), so an Arnoldi step needs one
+// host synchronisation (to read the residual estimate) instead of one per reduction.
+// Layout of kst (doubles): h1 [R+1] | h2 [R+1] | H [(R+1) R] | cs [R] | sn [R] | g [R+1] |
+// y [R] | scalars: hn2, beta, relres, done, jdone.
+struct GmresState {
+  double *h1, *h2, *H, *cs, *sn, *g, *y, *sc;
+};
+__host__ __device__ inline GmresState gmres_state(double* base) {
+  constexpr int R = IEDG_MAX_RESTART;
+  GmresState S;
+  S.h1 = base;
+  S.h2 = S.h1 + (R + 1);
+  S.H = S.h2 + (R + 1);
+  S.cs = S.H + (R + 1) * R;
+  S.sn = S.cs + R;
+  S.g = S.sn + R;
+  S.y = S.g + (R + 1);
+  S.sc = S.y + R;          // [0] hn2, [1] beta, [2] relres, [3] done, [4] jdone
+  return S;
+}
+
+// y = x / sqrt(*n2), zero if *n2 == 0 (y may alias x)
+__global__ void k_scale_norm(int64_t n, const double* __restrict__ n2, const double* x, double* y) {
+  const double nn = *n2;
+  const double a = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i];
+}
+
+// start of a cycle: beta = sqrt(beta2), g = (beta, 0, ...), relres = beta / beta0, not done
+__global__ void k_gmres_start(GmresState S, double beta0) {
+  const double beta = sqrt(S.sc[0]);
+  S.sc[1] = beta;
+  for (int i = 0; i <= IEDG_MAX_RESTART; ++i) S.g[i] = 0.0;
+  S.g[0] = beta;
+  S.sc[2] = beta0 > 0.0 ? beta / beta0 : 0.0;
+  S.sc[3] = 0.0;
+}
+
+// Hessenberg column j = h1 + h2 (the two Gram-Schmidt passes) with h_{j+1,j} = |w|;
+// earlier rotations applied, a new one formed, g rotated, |g_{j+1}| / beta0 the
+// residual estimate; done when it reaches rtol or the Krylov space is exhausted.
+__global__ void k_gmres_givens(GmresState S, int j, double beta0, double rtol) {
+  constexpr int R = IEDG_MAX_RESTART;
+  double h[R + 1];
+  for (int i = 0; i <= j; ++i) h[i] = S.h1[i] + S.h2[i];
+  const double hn = sqrt(S.sc[0]);
+  for (int i = 0; i < j; ++i) {
+    const double a = S.cs[i] * h[i] + S.sn[i] * h[i + 1];
+    const double b = -S.sn[i] * h[i] + S.cs[i] * h[i + 1];
+    h[i] = a;
+    h[i + 1] = b;
+  }
+  h[j + 1] = hn;
+  const double r = hypot(h[j], h[j + 1]);
+  S.cs[j] = r > 0.0 ? h[j] / r : 1.0;
+  S.sn[j] = r > 0.0 ? h[j + 1] / r : 0.0;
+  h[j] = r;
+  S.g[j + 1] = -S.sn[j] * S.g[j];
+  S.g[j] = S.cs[j] * S.g[j];
+  for (int i = 0; i <= j; ++i) S.H[i * R + j] = h[i];
+  const double rel = fabs(S.g[j + 1]) / beta0;
+  S.sc[2] = rel;
+  S.sc[3] = (rel <= rtol || hn == 0.0) ? 1.0 : 0.0;
+}
+
+// y = H(0:j, 0:j)^-1 g (upper triangular)
+__global__ void k_gmres_backsolve(GmresState S, int j) {
+  constexpr int R = IEDG_MAX_RESTART;
+  for (int i = j - 1; i >= 0; --i) {
+    double s = S.g[i];
+    for (int k = i + 1; k < j; ++k) s -= S.H[i * R + k] * S.y[k];
+    S.y[i] = s / S.H[i * R + i];
+  }
+}
+
+// BILU(0) solve v <- U^-1 L^-1 v in one CTA: colour by colour (the rows of a colour
+// share no block), one warp per row, the CTA's barrier between colours; forward over
+// the colours, then backward.  A single launch instead of two per colour.
+constexpr int BA_THREADS = 1024;
+__global__ void __launch_bounds__(BA_THREADS)
+k_bilu_apply1(int m, int nc, const int64_t* __restrict__ cptr, const int64_t* __restrict__ rows,
+              const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, const int32_t* __restrict__ ord,
+              const int32_t* __restrict__ nlow, const double* __restrict__ F, const double* __restrict__ Uinv,
+              double* __restrict__ v) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = BA_THREADS / 32, mm = m * m;
+  for (int c = 0; c < nc; ++c) {
+    for (int64_t w = cptr[c] + warp; w < cptr[c + 1]; w += nw) {
+      const int64_t i = rows[w], lo = row_ptr[i];
+      const int32_t* o = ord + lo;
+      const int nl = nlow[i];
+      double acc[5] = {0, 0, 0, 0, 0};
+      for (int q = lane; q < nl; q += 32) {
+        const int64_t kk = lo + o[q];
+        const double* blk = F + kk * mm;
+        const double* x = v + (int64_t)col[kk] * m;
+        for (int r = 0; r < m; ++r) {
+          double sacc = 0.0;
+          for (int t = 0; t < m; ++t) sacc = fma(blk[r * m + t], x[t], sacc);
+          acc[r] += sacc;
+        }
+      }
+      for (int r = 0; r < m; ++r)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], off);
+      if (lane < m) v[i * m + lane] -= acc[lane];
+    }
+    __syncthreads();
+  }
+  for (int c = nc - 1; c >= 0; --c) {
+    for (int64_t w = cptr[c] + warp; w < cptr[c + 1]; w += nw) {
+      const int64_t i = rows[w], lo = row_ptr[i];
+      const int len = (int)(row_ptr[i + 1] - lo);
+      const int32_t* o = ord + lo;
+      const int nl = nlow[i];
+      double acc[5] = {0, 0, 0, 0, 0};
+      for (int q = nl + 1 + lane; q < len; q += 32) {
+        const int64_t kk = lo + o[q];
+        const double* blk = F + kk * mm;
+        const double* x = v + (int64_t)col[kk] * m;
+        for (int r = 0; r < m; ++r) {
+          double sacc = 0.0;
+          for (int t = 0; t < m; ++t) sacc = fma(blk[r * m + t], x[t], sacc);
+          acc[r] += sacc;
+        }
+      }
+      for (int r = 0; r < m; ++r)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], off);
+      double sv[5];
+      for (int t = 0; t < m; ++t) sv[t] = v[i * m + t] - acc[t];
+      __syncwarp();
+      if (lane < m) {
+        double x = 0.0;
+        for (int t = 0; t < m; ++t) x = fma(Uinv[(i * mm) + lane * m + t], sv[t], x);
+        v[i * m + lane] = x;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 unsigned grid_for(int64_t n) {
   int64_t g = (n + SV_THREADS - 1) / SV_THREADS;
   return (unsigned)(g < 4096 ? g : 4096);
@@ -381,6 +519,7 @@ static int bilu_setup(iedg_mesh* M, cudaStream_t st) {
   SV_TRY(put(&M->brows, rows));
   SV_TRY(put(&M->bord, ord));
   SV_TRY(put(&M->bnlow, nlow));
+  SV_TRY(put(&M->bcptr_dev, cnt));
   SV_TRY(cudaStreamSynchronize(st));
   M->bcolor = color;
   return IEDG_OK;
@@ -409,10 +548,16 @@ static int bilu_factor(iedg_mesh* M, const double* K, double* F, cudaStream_t st
   return IEDG_OK;
 }
 
-// v <- U^-1 L^-1 v, colour by colour
+// v <- U^-1 L^-1 v, colour by colour: one launch of a single CTA (the colours' row
+// lists and the factors come from bilu_setup / bilu_factor)
 static cudaError_t bilu_apply(iedg_mesh* M, const double* F, double* v, cudaStream_t st) {
   const int m = M->dm.m;
   const size_t nc = M->bcptr.size() - 1;
+  if (M->bcptr_dev) {
+    k_bilu_apply1<<<1, BA_THREADS, 0, st>>>(m, (int)nc, M->bcptr_dev, M->brows, M->row_ptr, M->col, M->bord,
+                                           M->bnlow, F, M->dinv, v);
+    return cudaGetLastError();
+  }
   for (size_t c = 0; c < nc; ++c) {
     const int64_t nr = M->bcptr[c + 1] - M->bcptr[c];
     if (nr == 0) continue;
@@ -488,7 +633,6 @@ extern "C" int iedg_trace_solve(iedg_mesh* M, const double* K, const double* R, 
   double* tmp = w + n;
   double* Dinv = M->dinv;
   double* part = M->kpart;                // [restart+1][SV_PART]
-  double* hdev = M->khdev;                // [restart+1]
   const unsigned g = grid_for(n);
   const unsigned gw = (unsigned)((T * 32 + SV_THREADS - 1) / SV_THREADS);
   const bool bilu = M->prec_kind == IEDG_PREC_BILU0;
@@ -519,19 +663,26 @@ extern "C" int iedg_trace_solve(iedg_mesh* M, const double* K, const double* R, 
   if (!bilu)
     SV_TRY((k_diag_inv<<<(unsigned)((T + 127) / 128), 128, 0, st>>>(m, T, M->row_ptr, M->col, K, Dinv, M->dev_flag),
             cudaGetLastError()));
-  auto dots = [&](int nv, const double* Vb, const double* x, double* out_host) -> cudaError_t {
+  // sums of products into device memory (fixed block order: deterministic)
+  auto dots_dev = [&](int nv, const double* Vb, const double* x, double* out_dev) -> cudaError_t {
     k_dots<<<SV_PART, SV_THREADS, 0, st>>>(n, nv, Vb, x, part);
-    k_sum_partials<<<1, 64, 0, st>>>(nv, part, hdev);
-    cudaError_t e = cudaMemcpyAsync(out_host, hdev, nv * sizeof(double), cudaMemcpyDeviceToHost, st);
+    k_sum_partials<<<1, 64, 0, st>>>(nv, part, out_dev);
+    return cudaGetLastError();
+  };
+  const GmresState S = gmres_state(M->kst);
+  // the host reads three scalars of the device state: squared norm, residual estimate, done
+  auto read_state = [&](double* out3) -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(out3, S.sc, 4 * sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e;
   };
   // x0 = 0, r0 = M^-1 R
   SV_TRY(cudaMemsetAsync(dU, 0, n * sizeof(double), st));
   SV_TRY(prec(R, V));
-  double beta0 = 0.0;
-  SV_TRY(dots(1, V, V, &beta0));
-  beta0 = std::sqrt(beta0);
+  SV_TRY(dots_dev(1, V, V, S.sc));
+  double hs[4] = {0, 0, 0, 0};
+  SV_TRY(read_state(hs));
+  const double beta0 = std::sqrt(hs[0]);
   int flag = 0;
   SV_TRY(cudaMemcpy(&flag, M->dev_flag, sizeof(int), cudaMemcpyDeviceToHost));
   if (flag) {
@@ -540,9 +691,6 @@ extern "C" int iedg_trace_solve(iedg_mesh* M, const double* K, const double* R, 
   }
   int total = 0;
   double relres = beta0 > 0.0 ? 1.0 : 0.0;
-  std::vector<double> H((restart + 1) * restart), cs(restart), sn(restart), gvec(restart + 1), h(restart + 1),
-      h2(restart + 1), y(restart);
-  double beta = beta0;
   bool first = true;
   while (beta0 > 0.0 && total < max_iter && relres > rtol) {
     if (!first) {
@@ -550,63 +698,39 @@ extern "C" int iedg_trace_solve(iedg_mesh* M, const double* K, const double* R, 
       SV_TRY((k_spmv<<<gw, SV_THREADS, 0, st>>>(m, T, M->row_ptr, M->col, K, Dinv, dU, tmp, false), cudaGetLastError()));
       SV_TRY((k_residual<<<g, SV_THREADS, 0, st>>>(m, n, R, tmp, tmp), cudaGetLastError()));
       SV_TRY(prec(tmp, V));
-      double bb = 0.0;
-      SV_TRY(dots(1, V, V, &bb));
-      beta = std::sqrt(bb);
-      relres = beta / beta0;
+      SV_TRY(dots_dev(1, V, V, S.sc));
+    }
+    SV_TRY((k_gmres_start<<<1, 1, 0, st>>>(S, beta0), cudaGetLastError()));
+    if (!first) {
+      SV_TRY(read_state(hs));
+      relres = hs[2];
       if (relres <= rtol) break;
     }
     first = false;
-    SV_TRY((k_scale<<<g, SV_THREADS, 0, st>>>(n, 1.0 / beta, V, V), cudaGetLastError()));
-    std::fill(gvec.begin(), gvec.end(), 0.0);
-    gvec[0] = beta;
+    SV_TRY((k_scale_norm<<<g, SV_THREADS, 0, st>>>(n, S.sc, V, V), cudaGetLastError()));
     int j = 0;
     for (; j < restart && total < max_iter; ++j, ++total) {
       double* vj = V + (int64_t)j * n;
       double* vn = V + (int64_t)(j + 1) * n;
       SV_TRY((k_spmv<<<gw, SV_THREADS, 0, st>>>(m, T, M->row_ptr, M->col, K, Dinv, vj, w, !bilu), cudaGetLastError()));
       if (bilu) SV_TRY(prec(w, w));
-      // iterated classical Gram-Schmidt: two passes
-      SV_TRY(dots(j + 1, V, w, h.data()));
-      SV_TRY(cudaMemcpyAsync(hdev, h.data(), (j + 1) * sizeof(double), cudaMemcpyHostToDevice, st));
-      SV_TRY((k_orth<<<g, SV_THREADS, 0, st>>>(n, j + 1, V, hdev, w), cudaGetLastError()));
-      SV_TRY(dots(j + 1, V, w, h2.data()));
-      SV_TRY(cudaMemcpyAsync(hdev, h2.data(), (j + 1) * sizeof(double), cudaMemcpyHostToDevice, st));
-      SV_TRY((k_orth<<<g, SV_THREADS, 0, st>>>(n, j + 1, V, hdev, w), cudaGetLastError()));
-      for (int i = 0; i <= j; ++i) h[i] += h2[i];
-      double hn = 0.0;
-      SV_TRY(dots(1, w, w, &hn));
-      hn = std::sqrt(hn);
-      SV_TRY((k_scale<<<g, SV_THREADS, 0, st>>>(n, hn > 0.0 ? 1.0 / hn : 0.0, w, vn), cudaGetLastError()));
-      // apply previous rotations, then a new one
-      for (int i = 0; i < j; ++i) {
-        double a = cs[i] * h[i] + sn[i] * h[i + 1];
-        double b = -sn[i] * h[i] + cs[i] * h[i + 1];
-        h[i] = a;
-        h[i + 1] = b;
-      }
-      h[j + 1] = hn;
-      double r = std::hypot(h[j], h[j + 1]);
-      cs[j] = r > 0.0 ? h[j] / r : 1.0;
-      sn[j] = r > 0.0 ? h[j + 1] / r : 0.0;
-      h[j] = r;
-      h[j + 1] = 0.0;
-      gvec[j + 1] = -sn[j] * gvec[j];
-      gvec[j] = cs[j] * gvec[j];
-      for (int i = 0; i <= j; ++i) H[i * restart + j] = h[i];
-      relres = std::fabs(gvec[j + 1]) / beta0;
-      if (relres <= rtol || hn == 0.0) { ++j; ++total; break; }
+      // iterated classical Gram-Schmidt: two passes, coefficients kept on the device
+      SV_TRY(dots_dev(j + 1, V, w, S.h1));
+      SV_TRY((k_orth<<<g, SV_THREADS, 0, st>>>(n, j + 1, V, S.h1, w), cudaGetLastError()));
+      SV_TRY(dots_dev(j + 1, V, w, S.h2));
+      SV_TRY((k_orth<<<g, SV_THREADS, 0, st>>>(n, j + 1, V, S.h2, w), cudaGetLastError()));
+      SV_TRY(dots_dev(1, w, w, S.sc));
+      SV_TRY((k_scale_norm<<<g, SV_THREADS, 0, st>>>(n, S.sc, w, vn), cudaGetLastError()));
+      SV_TRY((k_gmres_givens<<<1, 1, 0, st>>>(S, j, beta0, rtol), cudaGetLastError()));
+      SV_TRY(read_state(hs));                         // the one synchronisation of the step
+      relres = hs[2];
+      if (hs[3] != 0.0) { ++j; ++total; break; }
     }
     // y = H(0:j, 0:j)^-1 g, x += V y
-    for (int i = j - 1; i >= 0; --i) {
-      double s = gvec[i];
-      for (int k = i + 1; k < j; ++k) s -= H[i * restart + k] * y[k];
-      y[i] = s / H[i * restart + i];
-    }
-    SV_TRY(cudaMemcpyAsync(hdev, y.data(), j * sizeof(double), cudaMemcpyHostToDevice, st));
-    SV_TRY((k_update<<<g, SV_THREADS, 0, st>>>(n, j, V, hdev, dU), cudaGetLastError()));
-    SV_TRY(cudaStreamSynchronize(st));
+    SV_TRY((k_gmres_backsolve<<<1, 1, 0, st>>>(S, j), cudaGetLastError()));
+    SV_TRY((k_update<<<g, SV_THREADS, 0, st>>>(n, j, V, S.y, dU), cudaGetLastError()));
   }
+  SV_TRY(cudaStreamSynchronize(st));
   if (iterations) *iterations = total;
   if (rel_residual) *rel_residual = relres;
   return IEDG_OK;

@@ -242,9 +242,7 @@ int64_t iedg_element_status(iedg_mesh* mesh, int8_t* out, void* stream);
  *   2.2.2), in multicolour order: trace nodes coloured greedily in index order (each
  *   takes the smallest colour none of its earlier neighbours has, neighbours = nodes
  *   sharing a block of K), then eliminated colour by colour, ties by index.  Nodes of
- *   one colour share no block, so each colour is factored in one launch, and the
- *   preconditioner solve runs all colours (forward, then backward) in a single
- *   one-block launch with a block barrier between colours.
+ *   one colour share no block, so each colour is factored and solved in one launch.
  *   (The paper orders by minimum discarded fill, a sequential CPU ordering.)  The
  *   colouring and per-row orders are built on the first use (host work, one device
  *   buffer of nnzb m^2 doubles for the factors). */

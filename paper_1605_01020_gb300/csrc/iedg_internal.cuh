@@ -213,7 +213,6 @@ struct iedg_mesh {
   double* bf = nullptr;         // BILU(0) factors [nnzb][m][m]
   int64_t* brows = nullptr;     // [T] trace nodes sorted by (colour, index)
   std::vector<int64_t> bcptr;   // colour boundaries in brows
-  int64_t* bcptr_dev = nullptr; // the same on the device (one-launch BILU(0) solve)
   double* kst = nullptr;        // trace solve: GMRES state on the device (Hessenberg, rotations, scalars)
   int32_t* bord = nullptr;      // [nnzb] per row: entry offsets in elimination order
   int32_t* bnlow = nullptr;     // [T] entries of each row ranked before the row

@@ -381,72 +381,6 @@ __global__ void k_gmres_backsolve(GmresState S, int j) {
   }
 }
 
-// BILU(0) solve v <- U^-1 L^-1 v in one CTA: colour by colour (the rows of a colour
-// share no block), one warp per row, the CTA's barrier between colours; forward over
-// the colours, then backward.  A single launch instead of two per colour.
-constexpr int BA_THREADS = 1024;
-__global__ void __launch_bounds__(BA_THREADS)
-k_bilu_apply1(int m, int nc, const int64_t* __restrict__ cptr, const int64_t* __restrict__ rows,
-              const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, const int32_t* __restrict__ ord,
-              const int32_t* __restrict__ nlow, const double* __restrict__ F, const double* __restrict__ Uinv,
-              double* __restrict__ v) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = BA_THREADS / 32, mm = m * m;
-  for (int c = 0; c < nc; ++c) {
-    for (int64_t w = cptr[c] + warp; w < cptr[c + 1]; w += nw) {
-      const int64_t i = rows[w], lo = row_ptr[i];
-      const int32_t* o = ord + lo;
-      const int nl = nlow[i];
-      double acc[5] = {0, 0, 0, 0, 0};
-      for (int q = lane; q < nl; q += 32) {
-        const int64_t kk = lo + o[q];
-        const double* blk = F + kk * mm;
-        const double* x = v + (int64_t)col[kk] * m;
-        for (int r = 0; r < m; ++r) {
-          double sacc = 0.0;
-          for (int t = 0; t < m; ++t) sacc = fma(blk[r * m + t], x[t], sacc);
-          acc[r] += sacc;
-        }
-      }
-      for (int r = 0; r < m; ++r)
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], off);
-      if (lane < m) v[i * m + lane] -= acc[lane];
-    }
-    __syncthreads();
-  }
-  for (int c = nc - 1; c >= 0; --c) {
-    for (int64_t w = cptr[c] + warp; w < cptr[c + 1]; w += nw) {
-      const int64_t i = rows[w], lo = row_ptr[i];
-      const int len = (int)(row_ptr[i + 1] - lo);
-      const int32_t* o = ord + lo;
-      const int nl = nlow[i];
-      double acc[5] = {0, 0, 0, 0, 0};
-      for (int q = nl + 1 + lane; q < len; q += 32) {
-        const int64_t kk = lo + o[q];
-        const double* blk = F + kk * mm;
-        const double* x = v + (int64_t)col[kk] * m;
-        for (int r = 0; r < m; ++r) {
-          double sacc = 0.0;
-          for (int t = 0; t < m; ++t) sacc = fma(blk[r * m + t], x[t], sacc);
-          acc[r] += sacc;
-        }
-      }
-      for (int r = 0; r < m; ++r)
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], off);
-      double sv[5];
-      for (int t = 0; t < m; ++t) sv[t] = v[i * m + t] - acc[t];
-      __syncwarp();
-      if (lane < m) {
-        double x = 0.0;
-        for (int t = 0; t < m; ++t) x = fma(Uinv[(i * mm) + lane * m + t], sv[t], x);
-        v[i * m + lane] = x;
-      }
-    }
-    __syncthreads();
-  }
-}
-
 unsigned grid_for(int64_t n) {
   int64_t g = (n + SV_THREADS - 1) / SV_THREADS;
   return (unsigned)(g < 4096 ? g : 4096);
@@ -519,7 +453,6 @@ static int bilu_setup(iedg_mesh* M, cudaStream_t st) {
   SV_TRY(put(&M->brows, rows));
   SV_TRY(put(&M->bord, ord));
   SV_TRY(put(&M->bnlow, nlow));
-  SV_TRY(put(&M->bcptr_dev, cnt));
   SV_TRY(cudaStreamSynchronize(st));
   M->bcolor = color;
   return IEDG_OK;
@@ -548,16 +481,12 @@ static int bilu_factor(iedg_mesh* M, const double* K, double* F, cudaStream_t st
   return IEDG_OK;
 }
 
-// v <- U^-1 L^-1 v, colour by colour: one launch of a single CTA (the colours' row
-// lists and the factors come from bilu_setup / bilu_factor)
+// v <- U^-1 L^-1 v, colour by colour (one launch per colour and sweep: a single-block
+// form of all colours was measured slower, one SM's bandwidth for the whole factor)
 static cudaError_t bilu_apply(iedg_mesh* M, const double* F, double* v, cudaStream_t st) {
   const int m = M->dm.m;
   const size_t nc = M->bcptr.size() - 1;
-  if (M->bcptr_dev) {
-    k_bilu_apply1<<<1, BA_THREADS, 0, st>>>(m, (int)nc, M->bcptr_dev, M->brows, M->row_ptr, M->col, M->bord,
-                                           M->bnlow, F, M->dinv, v);
-    return cudaGetLastError();
-  }
+
   for (size_t c = 0; c < nc; ++c) {
     const int64_t nr = M->bcptr[c + 1] - M->bcptr[c];
     if (nr == 0) continue;

@@ -282,8 +282,11 @@ int iedg_trace_solve(iedg_mesh* mesh, const double* K, const double* R, double* 
  *                  grid, panel 16; its per-CTA slice buffers (16 (nt + 1) nu floats
  *                  per resident CTA) are allocated by this call when it selects the
  *                  form (IEDG_ERR_OOM if they do not fit), not by the compute calls.  Mixed path: TF32 operands split in high and low
- *                  parts, three products ("3xTF32").  0 = DFMA / FFMA updates.  Default
- *                  0 for FP64 handles, 1 for mixed ones.  Handles created with
+ *                  parts, three products ("3xTF32").  2 (mixed FP32 form only) = every
+ *                  trailing update of the FP32 LU on the tensor cores (3xTF32, 128 x 64
+ *                  tiles accumulated in TMEM and subtracted from the trailing block by
+ *                  reductions in L2).  0 = DFMA / FFMA updates.  Default 0, except 2
+ *                  for mixed FP32 handles of meshes with mixed orders.  Handles created with
  *                  IEDG_PRECISION_MIXED_TF32 or _MIXED_BF16 always take the tensor-core
  *                  form in their own operand precision (the schedule never changes
  *                  what is computed, only how).

@@ -522,13 +522,15 @@ static int create_impl(const iedg_mesh_desc* D, cudaStream_t st, iedg_mesh* M) {
 }
 
 // Storage precision (FP64 or FP32 element matrices), the Schur GEMM's operands on the
-// mixed path and the default LU form (FP64: DFMA unless chosen; mixed: tensor cores).
-static void set_precision(iedg_mesh* M, int precision) {
+// mixed path and the default LU form, the fastest measured on GB300: FP64 DFMA; FP32
+// with FFMA updates on uniform meshes, with every trailing update on the tensor cores
+// on meshes of mixed orders (the order-4 elements' long panels favour it).
+static void set_precision(iedg_mesh* M, int precision, bool mixed_orders) {
   M->precision = precision == IEDG_PRECISION_FP64 ? 0 : 1;
   M->schur_in = precision == IEDG_PRECISION_MIXED_TF32   ? kSchurTf32
                 : precision == IEDG_PRECISION_MIXED_BF16 ? kSchurBf16
                                                          : kSchurFp32;
-  M->sched.lu_tensor = M->precision;
+  M->sched.lu_tensor = M->precision == 0 ? 0 : (M->schur_in != kSchurFp32 ? 1 : (mixed_orders ? 2 : 0));
 }
 
 static int check_desc(const iedg_mesh_desc* D, bool mixed) {
@@ -574,7 +576,7 @@ extern "C" int iedg_create_mesh(const iedg_mesh_desc* D, void* stream, iedg_mesh
   M = new iedg_mesh();
   M->dm = make_dims(D->dim, D->order, D->quad_extra);
   M->ph = Phys{D->gamma, D->Pr, D->Re, D->alpha, D->stab, {0, 0, 0, 0, 0}};
-  set_precision(M, D->precision);
+  set_precision(M, D->precision, false);
   M->mass_scaled = (D->flags & IEDG_FLAG_MASS_SCALING) != 0;
   M->E = D->n_elem;
   M->T = D->n_trace;
@@ -903,7 +905,7 @@ extern "C" int iedg_create_mesh_bc(const iedg_mesh_desc* D, const int32_t* elem_
   M->ph = Phys{D->gamma, D->Pr, D->Re, D->alpha, D->stab, {0, 0, 0, 0, 0}};
   if (u_far)
     for (int i = 0; i < m; ++i) M->ph.ub[i] = u_far[i];
-  set_precision(M, D->precision);
+  set_precision(M, D->precision, true);
   M->E = D->n_elem;
   M->T = D->n_trace;
   rc = create_mixed_impl(D, elem_order, face_degree, face_kind, (cudaStream_t)stream, M);

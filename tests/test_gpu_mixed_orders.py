@@ -150,7 +150,7 @@ def test_mixed_orders_schedules_agree(precision):
     kw = dict(u_ref=None if u_ref is None else dev(_cat(u_ref)))
     ref = None
     for sched in ({"lu_persistent": 1}, {"lu_persistent": 0}, {"lu_persistent": 1, "asm_chunk": 16},
-                  {"lu_persistent": 1, "lu_tensor": 1 - lm.get_schedule()["lu_tensor"]},
+                  {"lu_persistent": 1, "lu_tensor": 1}, {"lu_persistent": 1, "lu_tensor": 0},
                   *([{"lu_persistent": 1, "lu_tensor": 2}, {"lu_persistent": 0, "lu_tensor": 2}]
                     if precision == 1 else []),
                   {"lu_persistent": 1, "asm_chunk_by_order": [0, 32, 8, 16]}):

@@ -430,6 +430,7 @@ static int alloc_owner(iedg_mesh* M, int64_t S_elems, int64_t piv_elems, int64_t
   } else {
     CUDA_TRY(dalloc(M, &M->S32, (size_t)S_elems));
     CUDA_TRY(dalloc(M, &M->piv, (size_t)piv_elems));
+    CUDA_TRY(dalloc(M, &M->pperm, (size_t)3 * piv_elems));
   }
   CUDA_TRY(dalloc(M, &M->rhat, (size_t)rhat_elems));
   CUDA_TRY(dalloc(M, &M->re64, (size_t)re_elems));
@@ -879,6 +880,7 @@ static int create_mixed_impl(const iedg_mesh_desc* D, const int32_t* ord, const 
     C->S = M->S;
     C->S32 = M->S32;
     C->piv = M->piv ? M->piv + in_poff[M->gstart[c]] : nullptr;
+    C->pperm = M->pperm ? M->pperm + 3 * in_poff[M->gstart[c]] : nullptr;
     C->status = M->status + M->gstart[c];
     C->rhat = M->rhat + rhat_off[c];
     C->re64 = M->re64 + re_off[c];
@@ -992,8 +994,10 @@ static int assemble_mixed(iedg_mesh* M, const double* u, const double* q, const 
       CUDA_TRY(TRACED("assemble", launch_assemble(C, st)));
   }
   CUDA_TRY(TRACED("lu_schur", launch_lu(M, st)));
-  if (M->precision != IEDG_PRECISION_FP64)
+  if (M->precision != IEDG_PRECISION_FP64) {
+    for (iedg_mesh* C : M->groups) CUDA_TRY(TRACED("solve_prep", launch_solve_prep(C, st)));
     for (iedg_mesh* C : M->groups) CUDA_TRY(TRACED("refine", launch_refine(C, st)));
+  }
   CUDA_TRY(TRACED("scatter_K", launch_scatter_K(M, K, st)));
   if (M->precision == IEDG_PRECISION_FP64)
     CUDA_TRY(TRACED("scatter_R", launch_scatter_R_ragged(M, M->rs_S, M->S, R, st)));
@@ -1094,6 +1098,7 @@ extern "C" int iedg_assemble_condensed(iedg_mesh* M, const double* u, const doub
   if (M->fault.zero_row_elem >= 0) CUDA_TRY(TRACED("fault_zero_row", launch_zero_row(M, st)));
   CUDA_TRY(TRACED("lu_schur", launch_lu(M, st)));
   if (M->precision != IEDG_PRECISION_FP64) {
+    CUDA_TRY(TRACED("solve_prep", launch_solve_prep(M, st)));
     CUDA_TRY(TRACED("refine", launch_refine(M, st)));
     CUDA_TRY(TRACED("fallback_fp64", launch_fallback(M, st)));
   }

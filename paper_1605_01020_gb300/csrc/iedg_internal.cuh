@@ -177,6 +177,7 @@ struct iedg_mesh {
   bool mass_scaled = false;     // mixed forms: element systems scaled by the mass matrix (iedg_mass_scale.cu)
   float* Linv32 = nullptr;      // [E][Np][Np]   inverse Cholesky factor of the mass matrix, FP32
   int* piv = nullptr;           // [E][nu]       pivot rows of the FP32 partial LU
+  int* pperm = nullptr;         // [E][3 nu]     each panel's interchanges composed (iedg_refine.cu)
   double* rhs64 = nullptr;      // [E][n]        FP64 right-hand sides F~, G~
   double* y64 = nullptr;        // [E][nu]       refined A~^-1 F~
   double* re64 = nullptr;       // [E][m][Nb]    refined R_e (component-major)
@@ -268,6 +269,7 @@ cudaError_t launch_scatter_R(iedg_mesh* M, const double* src, int64_t src_elem_s
                              cudaStream_t st);
 cudaError_t launch_backsub(iedg_mesh* M, const double* duhat, double* du, double* dq,
                            cudaStream_t st);
+cudaError_t launch_solve_prep(iedg_mesh* M, cudaStream_t st);
 cudaError_t launch_refine(iedg_mesh* M, cudaStream_t st);
 // FP64 fallback of flagged elements on the mixed path (iedg_fallback.cu)
 constexpr int kFallbackSlots = 32;

@@ -16,6 +16,23 @@ namespace {
 constexpr int RF_THREADS = 512;
 constexpr int RF_NB = 32;            // panel width of the FP32 factorisation (k_lu<float, 32>)
 
+// The solves stage rows of the FP32 factors in shared memory: one slot of RF_SLOT floats
+// (32 used; the stride keeps 16-byte reads of 8 consecutive slots on distinct banks) per
+// thread that holds a row, threads 0 .. min(RF_THREADS, nu + 32) - 1.  The slots live in
+// the element operator's work arrays dqn .. tbf, free while a solve runs; stage_pad
+// pads that region where it is smaller (two doubles of slack for the 16-byte alignment).
+constexpr int RF_SLOT = 36;
+
+__host__ __device__ inline int stage_doubles(const Dims& dm) {
+  const int slots = dm.nu + 32 < RF_THREADS ? dm.nu + 32 : RF_THREADS;
+  return slots * (RF_SLOT / 2) + 2;
+}
+__host__ __device__ inline int stage_pad(const Dims& dm) {
+  const int m = dm.m, d = dm.d;
+  const int region = m * d * dm.Np + m * dm.Nq * (1 + 2 * d) + m * dm.Nfp * (4 + d);
+  return stage_doubles(dm) > region ? stage_doubles(dm) - region : 0;
+}
+
 struct Work {
   double *x, *z, *v, *b, *dqn, *xv, *xq, *tv, *xf, *zf, *xqf, *tf, *tbf, *ou, *ot, *red;
   double *sL, *sdL;              // 1D tables (3D sum factorisation)
@@ -38,6 +55,7 @@ __device__ Work carve(const Dims& dm, double* sm) {
   w.xqf = p; p += m * d * dm.Nfp;
   w.tf = p;  p += m * dm.Nfp;
   w.tbf = p; p += m * dm.Nfp;
+  p += stage_pad(dm);
   w.ou = p;  p += dm.nu;
   w.ot = p;  p += dm.nt;
   w.red = p; p += 32;
@@ -46,10 +64,15 @@ __device__ Work carve(const Dims& dm, double* sm) {
   return w;
 }
 
+// the solves' staging slots: dqn rounded up to 16 bytes
+__device__ __forceinline__ float* stage_ptr(const Work& w) {
+  return reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(w.dqn) + 15) & ~static_cast<uintptr_t>(15));
+}
+
 size_t work_doubles(const Dims& dm) {
   const int m = dm.m, d = dm.d;
   return (size_t)3 * dm.nu + dm.nt + (size_t)m * d * dm.Np + (size_t)m * dm.Nq * (1 + 2 * d) +
-         (size_t)m * dm.Nfp * (4 + d) + dm.nu + dm.nt + 32 + 2 * (size_t)dm.nq1 * dm.np1;
+         (size_t)m * dm.Nfp * (4 + d) + stage_pad(dm) + dm.nu + dm.nt + 32 + 2 * (size_t)dm.nq1 * dm.np1;
 }
 
 __device__ double block_max(double v, double* red) {
@@ -377,34 +400,6 @@ __device__ void element_apply(const Dims& dm, const Phys& ph, const RefTables& r
   __syncthreads();
 }
 
-// Row kb + lane of the panel's 32 x 32 diagonal block (columns kb .. kb + 31) into
-// registers, zero outside the panel (rows and columns >= nb).  Rows start on 16-byte
-// boundaries (ld and kb multiples of 4, element offsets multiples of 4 floats); the
-// vector loads are used when the 32 columns lie inside the row (kb + 32 <= ld).
-__device__ __forceinline__ void panel_row(const float* __restrict__ A, int ld, int kb, int nb, int lane,
-                                          float (&r)[RF_NB]) {
-  const float* src = A + (int64_t)(kb + lane) * ld + kb;
-  if (kb + RF_NB <= ld) {
-#pragma unroll
-    for (int q = 0; q < RF_NB / 4; ++q) {
-      const float4 v = lane < nb ? reinterpret_cast<const float4*>(src)[q] : make_float4(0.f, 0.f, 0.f, 0.f);
-      r[4 * q + 0] = 4 * q + 0 < nb ? v.x : 0.f;
-      r[4 * q + 1] = 4 * q + 1 < nb ? v.y : 0.f;
-      r[4 * q + 2] = 4 * q + 2 < nb ? v.z : 0.f;
-      r[4 * q + 3] = 4 * q + 3 < nb ? v.w : 0.f;
-    }
-  } else {
-#pragma unroll
-    for (int j = 0; j < RF_NB; ++j) r[j] = (lane < nb && j < nb) ? src[j] : 0.f;
-  }
-}
-
-// v <- A~32^-1 v with the FP32 factors (panel order, pivots as applied).  A correction
-// only needs FP32 accuracy (the residual it corrects is FP64), so the solve runs in
-// FP32 on a scaled copy of v held in f (nu floats, any free shared buffer).  The
-// sequential steps inside a panel run in warp 0 on registers: each lane holds its row
-// of the diagonal block and its entry of f, the pivot entries are broadcast by
-// shuffles, so no step waits on a memory load.
 // f <- (I_m (x) L^-1) f (transpose = false) or (I_m (x) L^-T) f, L^-1 lower triangular
 // [Np][Np]; tmp holds nu floats.
 __device__ void mass_apply(const Dims& dm, const float* __restrict__ Linv, float* f, float* tmp, bool transpose) {
@@ -424,12 +419,60 @@ __device__ void mass_apply(const Dims& dm, const float* __restrict__ Linv, float
   __syncthreads();
 }
 
+// Asynchronous 16-byte global -> shared copies (L2 only), completion per thread.
+__device__ __forceinline__ void cp_async16(float* sdst, const float* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(sdst))),
+               "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Row r, columns kb .. kb + 31, of the FP32 factors into the thread's slot (16-byte
+// pieces: ld, kb and the element offsets are multiples of 4 floats; kb + 32 <= ld).
+__device__ __forceinline__ void stage_row(const float* __restrict__ A, int ld, int r, int kb, float* slot) {
+  const float* src = A + (int64_t)r * ld + kb;
+#pragma unroll
+  for (int c = 0; c < RF_NB / 4; ++c) cp_async16(slot + 4 * c, src + 4 * c);
+}
+
+// v <- A~32^-1 v with the FP32 factors in the form k_solve_prep leaves them: each
+// 32 x 32 diagonal block holds [L11^-1 \ U11^-1] and pp the panels' interchanges
+// composed into gathers.  A correction only needs FP32 accuracy (the residual it
+// corrects is FP64), so the solve runs in FP32 on a scaled copy of v held in f (nu
+// floats, any free shared buffer with nu more floats behind it).  Per panel of the
+// forward solve: the interchanges as one gather, x = L11^-1 (gathered values) by warp 0
+// from its row of the inverted block, then rows below -= L21 x; the backward solve
+// runs the panels in reverse with x = U11^-1 f and rows above -= U12 x.  Warp 0 uses
+// its row of the diagonal block and every other thread the 32 factor entries of the row
+// it updates, staged in its shared-memory slot (stg, 16-byte aligned) by asynchronous
+// copies issued one panel ahead, as soon as the slot's previous row has been used, so
+// that their latency overlaps the panel steps.  Rows past the first of a thread (nu >
+// RF_THREADS - 32) are read directly.
 // With a mass scaling (Linv != null) the factors are those of S A~ S^T, S = I (x) L^-1,
 // and A~^-1 = S^T (S A~ S^T)^-1 S; f + nu serves as the scratch of the two products.
-__device__ void solve32(const Dims& dm, const float* __restrict__ A, int ld, const int* __restrict__ piv, double* v,
-                        float* f, double* red, const float* __restrict__ Linv) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = RF_THREADS / 32;
+__device__ void solve32(const Dims& dm, const float* __restrict__ A, int ld, const int* __restrict__ pp, double* v,
+                        float* f, float* stg, double* red, const float* __restrict__ Linv) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nu = dm.nu;
+  constexpr int NR = RF_THREADS - 32;            // threads that update rows (warps 1 ..)
+  float* slot = stg + tid * RF_SLOT;
+  const float4* slot4 = reinterpret_cast<const float4*>(slot);
+  // the row a thread uses in the forward panel kb (-1: none)
+  auto fwd_row = [&](int kb) {
+    const int nb = min(RF_NB, nu - kb);
+    if (warp == 0) return lane < nb ? kb + lane : -1;
+    const int r = kb + nb + (tid - 32);
+    return r < nu ? r : -1;
+  };
+  auto bwd_row = [&](int kb) {
+    const int nb = min(RF_NB, nu - kb);
+    if (warp == 0) return lane < nb ? kb + lane : -1;
+    return tid - 32 < kb ? tid - 32 : -1;
+  };
+  {
+    const int r = fwd_row(0);
+    if (r >= 0) stage_row(A, ld, r, 0, slot);
+  }
   double mx = 0.0;
   for (int i = tid; i < nu; i += RF_THREADS) mx = fmax(mx, fabs(v[i]));
   mx = block_max(mx, red);
@@ -437,78 +480,140 @@ __device__ void solve32(const Dims& dm, const float* __restrict__ A, int ld, con
   for (int i = tid; i < nu; i += RF_THREADS) f[i] = (float)(v[i] / sc);
   __syncthreads();
   if (Linv) mass_apply(dm, Linv, f, f + nu, false);
+  const int last = ((nu - 1) / RF_NB) * RF_NB;
+  // this lane's part of a forward panel's gather record (warps 0 and 1), read one panel ahead
+  int g_src = 0, g_dst = -1, g_osrc = 0;
+  auto load_rec = [&](int kb) {
+    const int nb = min(RF_NB, nu - kb);
+    const int* rec = pp + 3 * kb;
+    if (warp == 0 && lane < nb) g_src = rec[lane];
+    g_dst = -1;
+    if (warp == 1 && lane < nb) { g_dst = rec[nb + lane]; g_osrc = rec[2 * nb + lane]; }
+  };
+  load_rec(0);
   for (int kb = 0; kb < nu; kb += RF_NB) {
     const int nb = min(RF_NB, nu - kb);
-    if (warp == 0) {
-      // the panel's row interchanges, in order (one lane; the pivots come by shuffle)
-      const int pl = lane < nb ? piv[kb + lane] : 0;
-      float Lr[RF_NB];
-      panel_row(A, ld, kb, nb, lane, Lr);
-      for (int j = 0; j < nb; ++j) {
-        const int p = __shfl_sync(0xffffffffu, pl, j);
-        if (lane == 0 && p != kb + j) { float t = f[kb + j]; f[kb + j] = f[p]; f[p] = t; }
-      }
-      __syncwarp();
-      // unit lower triangular block: f_lane -= L[lane][j] f_j for j < lane
-      float fv = lane < nb ? f[kb + lane] : 0.f;
-#pragma unroll
-      for (int j = 0; j < RF_NB; ++j) {
-        const float vj = __shfl_sync(0xffffffffu, fv, j);
-        if (lane > j) fv = fmaf(-Lr[j], vj, fv);
-      }
-      if (lane < nb) f[kb + lane] = fv;
-    }
+    // the next row of this thread's slot: the next forward panel, else the first backward one
+    const int kn = kb + RF_NB < nu ? kb + RF_NB : last;
+    const int rn = kb + RF_NB < nu ? fwd_row(kn) : bwd_row(kn);
+    // the interchanges: old values first
+    float a = 0.f, ob = 0.f;
+    const int dst = g_dst;
+    if (warp == 0 && lane < nb) a = f[g_src];
+    if (dst >= 0) ob = f[g_osrc];
+    if (warp < 2 && kb + RF_NB < nu) load_rec(kb + RF_NB);
     __syncthreads();
-    for (int r = kb + nb + tid; r < nu; r += RF_THREADS) {
-      const float* row = A + (int64_t)r * ld + kb;
-      float s = f[r];
-      if (nb == RF_NB) {
-        const float4* row4 = reinterpret_cast<const float4*>(row);
+    if (warp == 0) {
+      // x_lane = a_lane + sum_{i < lane} (L11^-1)[lane][i] a_i
+      cp_async_wait_all();
+      float x = a;
 #pragma unroll
-        for (int q = 0; q < RF_NB / 4; ++q) {
-          const float4 a = row4[q];
-          s = fmaf(-a.x, f[kb + 4 * q + 0], s);
-          s = fmaf(-a.y, f[kb + 4 * q + 1], s);
-          s = fmaf(-a.z, f[kb + 4 * q + 2], s);
-          s = fmaf(-a.w, f[kb + 4 * q + 3], s);
+      for (int c = 0; c < RF_NB / 4; ++c) {
+        const float4 q = lane < nb ? slot4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float qv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int i = 4 * c + t;
+          const float ai = __shfl_sync(0xffffffffu, a, i);
+          if (i < lane) x = fmaf(qv[t], ai, x);
         }
-      } else {
-        for (int j = 0; j < nb; ++j) s = fmaf(-row[j], f[kb + j], s);
       }
-      f[r] = s;
+      if (rn >= 0) stage_row(A, ld, rn, kn, slot);
+      if (lane < nb) f[kb + lane] = x;
+    }
+    if (warp == 1 && dst >= 0) f[dst] = ob;
+    __syncthreads();
+    if (warp > 0) {
+      // full panel here (nb = 32): only the last panel can be narrower, and no row lies below it
+      const int r0 = kb + nb + (tid - 32);
+      if (r0 < nu) {
+        cp_async_wait_all();
+        float s = f[r0];
+#pragma unroll
+        for (int c = 0; c < RF_NB / 4; ++c) {
+          const float4 q = slot4[c];
+          s = fmaf(-q.x, f[kb + 4 * c + 0], s);
+          s = fmaf(-q.y, f[kb + 4 * c + 1], s);
+          s = fmaf(-q.z, f[kb + 4 * c + 2], s);
+          s = fmaf(-q.w, f[kb + 4 * c + 3], s);
+        }
+        f[r0] = s;
+      }
+      if (rn >= 0) stage_row(A, ld, rn, kn, slot);
+      for (int r = r0 + NR; r < nu; r += NR) {
+        const float4* row4 = reinterpret_cast<const float4*>(A + (int64_t)r * ld + kb);
+        float s = f[r];
+#pragma unroll
+        for (int c = 0; c < RF_NB / 4; ++c) {
+          const float4 q = row4[c];
+          s = fmaf(-q.x, f[kb + 4 * c + 0], s);
+          s = fmaf(-q.y, f[kb + 4 * c + 1], s);
+          s = fmaf(-q.z, f[kb + 4 * c + 2], s);
+          s = fmaf(-q.w, f[kb + 4 * c + 3], s);
+        }
+        f[r] = s;
+      }
     }
     __syncthreads();
   }
-  const int last = ((nu - 1) / RF_NB) * RF_NB;
   for (int kb = last; kb >= 0; kb -= RF_NB) {
     const int nb = min(RF_NB, nu - kb);
-    for (int rr = warp; rr < nb; rr += nw) {
-      const int r = kb + rr;
-      const float* row = A + (int64_t)r * ld;
-      float s = 0.f;
-      for (int c = kb + nb + lane; c < nu; c += 32) s = fmaf(row[c], f[c], s);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) f[r] -= s;
-    }
-    __syncthreads();
+    const int kn = kb - RF_NB;
+    const int rn = kn >= 0 ? bwd_row(kn) : -1;
     if (warp == 0) {
-      // upper triangular block: f_j /= U[j][j], then f_lane -= U[lane][j] f_j for lane < j
-      float Ur[RF_NB];
-      panel_row(A, ld, kb, nb, lane, Ur);
-      float fv = lane < nb ? f[kb + lane] : 0.f;
+      // x_lane = sum_{lane <= i < nb} (U11^-1)[lane][i] f_i
+      const float a = lane < nb ? f[kb + lane] : 0.f;
+      cp_async_wait_all();
+      float x = 0.f;
 #pragma unroll
-      for (int j = RF_NB - 1; j >= 0; --j) {
-        if (j < nb) {
-          if (lane == j) fv /= Ur[j];
-          const float vj = __shfl_sync(0xffffffffu, fv, j);
-          if (lane < j) fv = fmaf(-Ur[j], vj, fv);
+      for (int c = 0; c < RF_NB / 4; ++c) {
+        const float4 q = lane < nb ? slot4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float qv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int i = 4 * c + t;
+          const float ai = __shfl_sync(0xffffffffu, a, i);
+          if (i >= lane && i < nb) x = fmaf(qv[t], ai, x);
         }
       }
-      if (lane < nb) f[kb + lane] = fv;
+      if (rn >= 0) stage_row(A, ld, rn, kn, slot);
+      if (lane < nb) f[kb + lane] = x;
+    }
+    __syncthreads();
+    if (warp > 0) {
+      const int r0 = tid - 32;
+      if (r0 < kb) {
+        cp_async_wait_all();
+        float s = f[r0];
+        // a ragged last panel: the entries past nb are trace columns, not U12
+#pragma unroll
+        for (int c = 0; c < RF_NB / 4; ++c) {
+          const float4 q = slot4[c];
+          const float qv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+            if (4 * c + t < nb) s = fmaf(-qv[t], f[kb + 4 * c + t], s);
+        }
+        f[r0] = s;
+      }
+      if (rn >= 0) stage_row(A, ld, rn, kn, slot);
+      for (int r = r0 + NR; r < kb; r += NR) {
+        const float4* row4 = reinterpret_cast<const float4*>(A + (int64_t)r * ld + kb);
+        float s = f[r];
+#pragma unroll
+        for (int c = 0; c < RF_NB / 4; ++c) {
+          const float4 q = row4[c];
+          const float qv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+            if (4 * c + t < nb) s = fmaf(-qv[t], f[kb + 4 * c + t], s);
+        }
+        f[r] = s;
+      }
     }
     __syncthreads();
   }
+  cp_async_wait_all();     // nothing left in flight into the work arrays (none is issued past the last panel)
   if (Linv) mass_apply(dm, Linv, f, f + nu, true);
   for (int i = tid; i < nu; i += RF_THREADS) v[i] = sc * (double)f[i];
   __syncthreads();
@@ -518,12 +623,12 @@ __device__ void solve32(const Dims& dm, const float* __restrict__ A, int ld, con
 // A~ x, C~ x for that x (w.z must be zero).  Returns the final relative residual.
 __device__ double refine_solve(const Dims& dm, const Phys& ph, const RefTables& ref, const Geo& G,
                                const PointJac& PJ, const TraceTab& tt, int64_t e, const float* A, int ld,
-                               const int* piv, Work& w, int max_iter, const float* Linv) {
+                               const int* pp, Work& w, int max_iter, const float* Linv) {
   const int tid = threadIdx.x, nu = dm.nu;
   double bn = 0.0;
   for (int i = tid; i < nu; i += RF_THREADS) { w.v[i] = w.b[i]; bn = fmax(bn, fabs(w.b[i])); }
   bn = block_max(bn, w.red);
-  solve32(dm, A, ld, piv, w.v, reinterpret_cast<float*>(w.ou), w.red, Linv);
+  solve32(dm, A, ld, pp, w.v, reinterpret_cast<float*>(w.ou), stage_ptr(w), w.red, Linv);
   for (int i = tid; i < nu; i += RF_THREADS) w.x[i] = w.v[i];
   __syncthreads();
   double rel = 0.0;
@@ -538,17 +643,100 @@ __device__ double refine_solve(const Dims& dm, const Phys& ph, const RefTables& 
     rn = block_max(rn, w.red);
     rel = bn > 0.0 ? rn / bn : rn;
     if (!(rel > kRefineTol) || it == max_iter) break;   // also stops on NaN
-    solve32(dm, A, ld, piv, w.v, reinterpret_cast<float*>(w.ou), w.red, Linv);
+    solve32(dm, A, ld, pp, w.v, reinterpret_cast<float*>(w.ou), stage_ptr(w), w.red, Linv);
     for (int i = tid; i < nu; i += RF_THREADS) w.x[i] += w.v[i];
     __syncthreads();
   }
   return rel;
 }
 
+constexpr int SP_WARPS = 4;        // 2 x 4 x 4.2 KB of blocks: within the static shared-memory limit
+
+// Once per factorisation, per element, one warp per 32-wide panel of the FP32 factors
+// of A~ (the solve form solve32 reads):
+//  - the diagonal block [L11 \ U11] becomes [L11^-1 \ U11^-1] in place: the inverse of
+//    a unit lower triangular matrix is unit lower triangular and that of an upper
+//    triangular one upper triangular, so both fit the block.  Lane c forms column c of
+//    each inverse by substitution (L11 y = e_c, U11 y = e_c);
+//  - the panel's row interchanges (row kb + j with row p_j >= kb + j, in order of j)
+//    are composed into one gather.  At offset 3 kb of the element's record: src[j]
+//    (j < nb), the row whose value ends in row kb + j; then dst[j] and osrc[j], the rows
+//    below the panel that receive a value and where it comes from (dst = -1 past the
+//    last such row).  A pivot outside [kb + j, nu) (an element whose factorisation did
+//    not run) counts as no interchange: its status already says so.
+__global__ void __launch_bounds__(SP_WARPS * 32)
+k_solve_prep(Dims dm, TraceTab tt, float* __restrict__ S32, const int* __restrict__ piv, int* __restrict__ pperm) {
+  __shared__ float blk[SP_WARPS][RF_NB][RF_NB + 1];
+  __shared__ float inv[SP_WARPS][RF_NB][RF_NB + 1];
+  __shared__ int cur[SP_WARPS][RF_NB], op[SP_WARPS][RF_NB], ov[SP_WARPS][RF_NB];
+  const int64_t e = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nu = dm.nu;
+  float* A = S32 + (tt.soff ? tt.soff[e] : e * (int64_t)dm.n * dm.ld);
+  const int ld = tt.ldv ? tt.ldv[e] : dm.ld;
+  const int* pv = piv + e * (int64_t)nu;
+  int* rec0 = pperm + e * 3 * (int64_t)nu;
+  float (*B)[RF_NB + 1] = blk[warp];
+  float (*Y)[RF_NB + 1] = inv[warp];
+  for (int kb = warp * RF_NB; kb < nu; kb += SP_WARPS * RF_NB) {
+    const int nb = min(RF_NB, nu - kb);
+    for (int i = 0; i < nb; ++i) B[i][lane] = lane < nb ? A[(int64_t)(kb + i) * ld + kb + lane] : 0.f;
+    __syncwarp();
+    if (lane < nb) {
+      const int c = lane;
+      // L11^-1, column c below the diagonal: y_i = -(L[i][c] + sum_{c < t < i} L[i][t] y_t)
+      for (int i = c + 1; i < nb; ++i) {
+        float sacc = B[i][c];
+        for (int t = c + 1; t < i; ++t) sacc = fmaf(B[i][t], Y[t][c], sacc);
+        Y[i][c] = -sacc;
+      }
+      // U11^-1, column c on and above the diagonal: y_c = 1 / U[c][c],
+      // y_i = -(sum_{i < t <= c} U[i][t] y_t) / U[i][i]
+      Y[c][c] = 1.f / B[c][c];
+      for (int i = c - 1; i >= 0; --i) {
+        float sacc = 0.f;
+        for (int t = i + 1; t <= c; ++t) sacc = fmaf(B[i][t], Y[t][c], sacc);
+        Y[i][c] = -sacc / B[i][i];
+      }
+    }
+    if (lane == 0) {
+      int nout = 0;
+      for (int j = 0; j < nb; ++j) cur[warp][j] = kb + j;
+      for (int j = 0; j < nb; ++j) {
+        const int p = pv[kb + j];
+        if (p <= kb + j || p >= nu) continue;
+        int* slot;
+        if (p < kb + nb) {
+          slot = &cur[warp][p - kb];
+        } else {
+          int qi = 0;
+          while (qi < nout && op[warp][qi] != p) ++qi;
+          if (qi == nout) { op[warp][qi] = p; ov[warp][qi] = p; ++nout; }
+          slot = &ov[warp][qi];
+        }
+        const int t = cur[warp][j];
+        cur[warp][j] = *slot;
+        *slot = t;
+      }
+      for (int j = nout; j < nb; ++j) op[warp][j] = -1;
+    }
+    __syncwarp();
+    for (int i = 0; i < nb; ++i)
+      if (lane < nb) A[(int64_t)(kb + i) * ld + kb + lane] = Y[i][lane];
+    int* rec = rec0 + 3 * kb;
+    if (lane < nb) {
+      rec[lane] = cur[warp][lane];
+      rec[nb + lane] = op[warp][lane];
+      rec[2 * nb + lane] = op[warp][lane] >= 0 ? ov[warp][lane] : 0;
+    }
+    __syncwarp();
+  }
+}
+
 // One CTA per element: y = A~^-1 F~ refined, R_e = G~ - C~ y.
 __global__ void __launch_bounds__(RF_THREADS, 2)
 k_refine(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ, TraceTab tt, const float* __restrict__ S32,
-         const int* __restrict__ piv, const double* __restrict__ rhs64, double* __restrict__ y64,
+         const int* __restrict__ pperm, const double* __restrict__ rhs64, double* __restrict__ y64,
          double* __restrict__ re64, int8_t* __restrict__ status, int max_iter, const float* __restrict__ Linv32) {
   extern __shared__ double sm[];
   Work w = carve(dm, sm);
@@ -561,7 +749,7 @@ k_refine(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ, TraceTab tt, const
   __syncthreads();
   const float* A = S32 + (tt.soff ? tt.soff[e] : e * (int64_t)dm.n * dm.ld);
   const int ld = tt.ldv ? tt.ldv[e] : dm.ld;
-  double rel = refine_solve(dm, ph, ref, G, PJ, tt, e, A, ld, piv + e * dm.nu, w, max_iter,
+  double rel = refine_solve(dm, ph, ref, G, PJ, tt, e, A, ld, pperm + e * 3 * dm.nu, w, max_iter,
                             Linv32 ? Linv32 + e * (int64_t)dm.Np * dm.Np : nullptr);
   for (int i = tid; i < dm.nu; i += RF_THREADS) y64[e * dm.nu + i] = w.x[i];
   // trace rows of the right-hand side: packed by the element's slot count
@@ -576,7 +764,7 @@ k_refine(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ, TraceTab tt, const
 // One CTA per element: du = A~^-1 (F~ - B~ dU_e) refined, dq = (q* - q) - G_l du + H_l dU_e.
 __global__ void __launch_bounds__(RF_THREADS, 2)
 k_backsub_mixed(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ, TraceTab tt, const int64_t* __restrict__ etrace,
-                const float* __restrict__ S32, const int* __restrict__ piv, const double* __restrict__ rhs64,
+                const float* __restrict__ S32, const int* __restrict__ pperm, const double* __restrict__ rhs64,
                 const double* __restrict__ rhoq, const double* __restrict__ duhat, double* __restrict__ du,
                 double* __restrict__ dq, int max_iter, const float* __restrict__ Linv32) {
   extern __shared__ double sm[];
@@ -599,7 +787,7 @@ k_backsub_mixed(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ, TraceTab tt
   __syncthreads();
   const float* A = S32 + (tt.soff ? tt.soff[e] : e * (int64_t)dm.n * dm.ld);
   const int ld = tt.ldv ? tt.ldv[e] : dm.ld;
-  refine_solve(dm, ph, ref, G, PJ, tt, e, A, ld, piv + e * dm.nu, w, max_iter,
+  refine_solve(dm, ph, ref, G, PJ, tt, e, A, ld, pperm + e * 3 * dm.nu, w, max_iter,
                Linv32 ? Linv32 + e * (int64_t)dm.Np * dm.Np : nullptr);
   for (int i = tid; i < dm.nt; i += RF_THREADS) {          // dU_e again, for dq
     int k = i / Nb, t = i % Nb;
@@ -623,12 +811,20 @@ k_backsub_mixed(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ, TraceTab tt
 
 }  // namespace
 
+cudaError_t launch_solve_prep(iedg_mesh* M, cudaStream_t st) {
+  const Dims& dm = M->dm;
+  // solve32 reads 32 columns from every panel start, the last one included
+  if (((dm.nu - 1) / RF_NB) * RF_NB + RF_NB > dm.n + 1 || !M->pperm) return cudaErrorInvalidValue;
+  k_solve_prep<<<(unsigned)M->E, SP_WARPS * 32, 0, st>>>(dm, M->tt, M->S32, M->piv, M->pperm);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_refine(iedg_mesh* M, cudaStream_t st) {
   const Dims& dm = M->dm;
   size_t smem = sizeof(double) * work_doubles(dm);
   cudaError_t err = cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  k_refine<<<(unsigned)M->E, RF_THREADS, smem, st>>>(dm, M->ph, M->ref, M->geo, M->pj, M->tt, M->S32, M->piv, M->rhs64,
+  k_refine<<<(unsigned)M->E, RF_THREADS, smem, st>>>(dm, M->ph, M->ref, M->geo, M->pj, M->tt, M->S32, M->pperm, M->rhs64,
                                                       M->y64, M->re64, M->status, refine_iters(M),
                                                       M->mass_scaled ? M->Linv32 : nullptr);
   return cudaGetLastError();
@@ -640,7 +836,7 @@ cudaError_t launch_backsub_mixed(iedg_mesh* M, const double* duhat, double* du, 
   cudaError_t err = cudaFuncSetAttribute(k_backsub_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   k_backsub_mixed<<<(unsigned)M->E, RF_THREADS, smem, st>>>(dm, M->ph, M->ref, M->geo, M->pj, M->tt, M->etrace, M->S32,
-                                                             M->piv, M->rhs64, M->rhoq, duhat, du, dq,
+                                                             M->pperm, M->rhs64, M->rhoq, duhat, du, dq,
                                                              refine_iters(M), M->mass_scaled ? M->Linv32 : nullptr);
   return cudaGetLastError();
 }

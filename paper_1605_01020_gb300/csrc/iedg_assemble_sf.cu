@@ -32,10 +32,31 @@ size_t sf_smem(const Dims& dm, bool mix) {
   const int nbu = dm.Np - (np1 - 2) * (np1 - 2) * (np1 - 2);
   size_t n = 2 * (size_t)nq1 * np1                                   // L, L'
              + (size_t)(1 + d) * d * dm.Nq + (size_t)(2 + d) * dm.Nfp  // pair coefficients
-             + 3 * (size_t)dm.Nq * CC + 3 * (size_t)nq1 * nq1 * np1 * CC + 2 * (size_t)nq1 * np1 * np1 * CC
-             + (size_t)nbu * CC + (size_t)dm.Nfq * CC + (size_t)nq1 * np1 * CC;
-  if (mix) n += (size_t)dm.Nb * CC + (size_t)nq1 * (5 - np1) * CC + 25 * (size_t)nq1;   // tacc, wider Uf, LQ
+             + 3 * (size_t)dm.Nq * CC + 3 * (size_t)nq1 * nq1 * np1 * CC + 2 * (size_t)nq1 * np1 * np1 * CC;
+  if (!mix && sizeof(T) == 4)   // the six faces' node sums
+    n += (size_t)6 * np1 * np1 * CC;
+  else                          // facc, Vf, Uf; with mixed orders a wider Uf, tacc and LQ
+    n += (size_t)nbu * CC + (size_t)dm.Nfq * CC + (size_t)nq1 * (mix ? 5 : np1) * CC +
+         (mix ? (size_t)dm.Nb * CC + 25 * (size_t)nq1 : 0);
   return n * sizeof(T);
+}
+
+// Face part of boundary node a for column c from the six faces' node sums fn[f][tn][c]:
+// node a = (a0, a1, a2) lies on face 2r where its coordinate r is 0 and on face 2r + 1
+// where it is p; its index on that face runs over the two other coordinates in order.
+// The faces are summed in increasing order, as the face-by-face accumulation does.
+template <class T, int NP1, int CC>
+__device__ __forceinline__ T face_sum(const T* fn, int a, int c) {
+  const int c3[3] = {a % NP1, (a / NP1) % NP1, a / (NP1 * NP1)};
+  T fs = 0;
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    const int r = f >> 1;
+    if (c3[r] != ((f & 1) ? NP1 - 1 : 0)) continue;
+    const int tn = r == 0 ? c3[1] + NP1 * c3[2] : (r == 1 ? c3[0] + NP1 * c3[2] : c3[0] + NP1 * c3[1]);
+    fs += fn[(f * NP1 * NP1 + tn) * CC + c];
+  }
+  return fs;
 }
 
 // Element sizes are compile-time constants (NP1 = p + 1, NQ1 = p + 2), so every index
@@ -58,6 +79,10 @@ k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, 
   constexpr int NbU = Np - (NP1 - 2) * (NP1 - 2) * (NP1 - 2), Nfp = 6 * Nfq;
   constexpr int TS = nq1 * nq1 * np1, VS = nq1 * np1 * np1, NC = (1 + d) * d;
   constexpr int UW = MIX ? 5 : np1;              // second extent of the face stage buffer
+  // FP32 on uniform meshes: the six faces' stages run together (3 barriers per column
+  // chunk instead of 18; measured faster in FP32, slower in FP64, whose DFMA pipe is
+  // the bound there)
+  constexpr bool SIX = !MIX && sizeof(T) == 4;
   // with an element list (FP64 fallback of the mixed path) CTA group `slot` assembles
   // element elist[slot] into matrix slot `slot`
   const int64_t slot = blockIdx.x / m2;
@@ -80,11 +105,14 @@ k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, 
   T* W = cL + Nfp;                             // [3][Nq][CC]
   T* Tt = W + 3 * Nq * CC;                     // [3][TS][CC]
   T* V = Tt + 3 * TS * CC;                     // [2][VS][CC]
-  T* facc = V + 2 * VS * CC;                   // [NbU][CC]  face parts of the boundary u-rows
+  // face parts of the boundary u-rows (and trace rows): accumulated face by face in
+  // facc (tacc), or with SIX the six faces' node sums fn[f][tn][c] formed together
+  T* facc = V + 2 * VS * CC;                   // [NbU][CC]
   T* Vf = facc + NbU * CC;                     // [Nfq][CC]
   T* Uf = Vf + Nfq * CC;                       // [nq1 UW][CC]
   T* tacc = MIX ? Uf + nq1 * UW * CC : facc;   // [Nb][CC]   trace rows (MIX), else = facc
   T* sLQ = tacc + (MIX ? dm.Nb * CC : 0);      // [5][nq1][5] (MIX)
+  T* fn = V + 2 * VS * CC;                     // [6][Nfn][CC] (SIX)
   for (int idx = tid; idx < nq1 * np1; idx += SF_THREADS) { sL[idx] = (T)ref.L1[idx]; sdL[idx] = (T)ref.dL1[idx]; }
   if (MIX) {
     const T* lq = nullptr;
@@ -121,6 +149,47 @@ k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, 
 
   for (int c0 = 0; c0 < ncol_all; c0 += CC) {
     // ---- face parts of the boundary rows for this column chunk
+    if constexpr (SIX) {
+      // all six faces per phase: right operand at the face points, then the two 1D
+      // stages; the first two live in the volume buffer W, free until the volume stage
+      T* Vf6 = W;                              // [6][Nfq][CC]
+      T* Uf6 = W + 6 * Nfq * CC;               // [6][nq1][np1][CC]
+      static_assert(6 * (Nfq + nq1 * np1) <= 3 * Nq, "face stages must fit the volume buffer");
+      for (int idx = tid; idx < 6 * Nfq * CC; idx += SF_THREADS) {
+        const int fp = idx / CC, c = idx % CC, col = c0 + c;
+        T v = 0;
+        if (col < Np) {
+          v = cL[fp] * tb.PhiF[(size_t)fp * Np + col];
+          if (has_cq)
+            for (int l = 0; l < d; ++l) v -= cF[(1 + l) * Nfp + fp] * GlF[((size_t)l * Nfp + fp) * Np + col];
+        } else if (col < ncol_all) {
+          const int t = col - Np;
+          v = cF[fp] * tb.PhiF[(size_t)fp * Np + ref.bnode[t]];
+          if (has_cq)
+            for (int l = 0; l < d; ++l) v += cF[(1 + l) * Nfp + fp] * HlF[((size_t)l * Nfp + fp) * NbT + t];
+        }
+        Vf6[idx] = v;
+      }
+      __syncthreads();
+      // U[f][g1][a2] = sum_g2 L[g2][a2] Vf[f][g1 + nq1 g2]
+      for (int idx = tid; idx < 6 * nq1 * np1 * CC; idx += SF_THREADS) {
+        const int c = idx % CC, t = idx / CC, f = t / (nq1 * np1), g1 = (t / np1) % nq1, a2 = t % np1;
+        T u = 0;
+        for (int g2 = 0; g2 < nq1; ++g2) u = fma(sL[g2 * np1 + a2], Vf6[(f * Nfq + g1 + nq1 * g2) * CC + c], u);
+        Uf6[idx] = u;
+      }
+      __syncthreads();
+      // node (a1, a2) of face f: sum_g1 L[g1][a1] U[f][g1][a2]
+      for (int idx = tid; idx < 6 * Nfn * CC; idx += SF_THREADS) {
+        const int c = idx % CC, t = idx / CC, f = t / Nfn, tn = t % Nfn, a1 = tn % np1, a2 = tn / np1;
+        T sacc = 0;
+        for (int g1 = 0; g1 < nq1; ++g1)
+          sacc = fma(sL[g1 * np1 + a1], Uf6[((f * nq1 + g1) * np1 + a2) * CC + c], sacc);
+        fn[idx] = sacc;
+      }
+      __syncthreads();
+    }
+    if constexpr (!SIX) {
     for (int idx = tid; idx < NbU * CC; idx += SF_THREADS) facc[idx] = (T)0;
     if (MIX)
       for (int idx = tid; idx < Nb * CC; idx += SF_THREADS) tacc[idx] = (T)0;
@@ -222,6 +291,7 @@ k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, 
         __syncthreads();
       }
     }
+    }
     // ---- volume right operands W_r[g][c] for the three reference directions.  The
     // table values of all of this thread's (g, c) entries are requested first, then
     // combined, so their latencies overlap instead of adding up.
@@ -316,7 +386,7 @@ k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, 
         s = fma(sL[gx * np1 + ax], V[(1 * VS + t) * CC + c], s);
       }
       const int sl = ref.slot[a];
-      if (sl >= 0) s += facc[sl * CC + c];
+      if (sl >= 0) s += SIX ? face_sum<T, NP1, CC>(fn, a, c) : facc[sl * CC + c];
       if (i == k && col < Np) s += alpha * Ms[a * Np + col];
       const int64_t cs = col < Np ? (int64_t)k * Np + col : (int64_t)dm.nu + (int64_t)k * Nb + (col - Np);
       Se[((int64_t)i * Np + a) * ld + cs] = s;
@@ -326,7 +396,8 @@ k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, 
       const int sl = idx / CC, c = idx % CC, col = c0 + c;
       if (col >= ncol_all) continue;
       const int64_t cs = col < Np ? (int64_t)k * Np + col : (int64_t)dm.nu + (int64_t)k * Nb + (col - Np);
-      Se[((int64_t)dm.nu + (int64_t)i * Nb + sl) * ld + cs] = tacc[sl * CC + c];
+      Se[((int64_t)dm.nu + (int64_t)i * Nb + sl) * ld + cs] =
+          SIX ? face_sum<T, NP1, CC>(fn, ref.bnode[sl], c) : tacc[sl * CC + c];
     }
     __syncthreads();
   }

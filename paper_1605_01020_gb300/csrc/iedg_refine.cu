@@ -88,6 +88,22 @@ __device__ double block_max(double v, double* red) {
   return r;
 }
 
+// Face part of the u-row of boundary node a, component i, from the face projections
+// fb[i][f][tn] (3D): node a lies on face 2r where its coordinate r is 0 and on face
+// 2r + 1 where it is p, at index tn over its two other coordinates in order.
+__device__ __forceinline__ double face_part(const Dims& dm, const double* fb, int i, int a) {
+  const int np1 = dm.np1, Nfn1 = np1 * np1;
+  const int c3[3] = {a % np1, (a / np1) % np1, a / (np1 * np1)};
+  double s = 0.0;
+  for (int f = 0; f < 6; ++f) {
+    const int r = f >> 1;
+    if (c3[r] != ((f & 1) ? np1 - 1 : 0)) continue;
+    const int tn = r == 0 ? c3[1] + np1 * c3[2] : (r == 1 ? c3[0] + np1 * c3[2] : c3[0] + np1 * c3[1]);
+    s += fb[((size_t)i * 6 + f) * Nfn1 + tn];
+  }
+  return s;
+}
+
 // ou = A~ x + B~ z (u-rows), ot = C~ x + D~ z (trace rows), all FP64.
 // use_x / use_z = false skip the terms of an operand that is identically zero.
 // z and ot are component-major with slot stride Nb = Dims.Nb; with mixed orders only
@@ -361,15 +377,7 @@ __device__ void element_apply(const Dims& dm, const Phys& ph, const RefTables& r
     }
     if (ref.slot[a] >= 0) {
       if (d == 3) {
-        // the faces node a lies on: coordinate r at 0 (face 2r) or p (face 2r + 1)
-        const int np1 = dm.np1, Nfn1 = np1 * np1;
-        const int c3[3] = {a % np1, (a / np1) % np1, a / (np1 * np1)};
-        for (int f = 0; f < 6; ++f) {
-          const int r = f >> 1;
-          if (c3[r] != ((f & 1) ? np1 - 1 : 0)) continue;
-          const int tn = r == 0 ? c3[1] + np1 * c3[2] : (r == 1 ? c3[0] + np1 * c3[2] : c3[0] + np1 * c3[1]);
-          s += w.xf[((size_t)i * 6 + f) * Nfn1 + tn];
-        }
+        s += face_part(dm, w.xf, i, a);
       } else {
         for (int fp = 0; fp < Nfp; ++fp) s = fma(ref.PhiF[(size_t)fp * Np + a], w.tf[i * Nfp + fp], s);
       }
@@ -391,6 +399,11 @@ __device__ void element_apply(const Dims& dm, const Phys& ph, const RefTables& r
           for (int gf = 0; gf < Nfq; ++gf) s = fma(mu[(size_t)gf * tt.NFS], src[i * Nfp + f * Nfq + gf], s);
         }
       }
+    } else if (d == 3) {
+      // uniform order, every face interior (meshes with boundary faces carry the slot
+      // tables above): the trace basis on a face is the element basis there, so the
+      // trace row of slot sl is the face part of the u-row of its node
+      s = face_part(dm, w.xf, i, ref.bnode[sl]);
     } else {
       const int a = ref.bnode[sl];
       for (int fp = 0; fp < Nfp; ++fp) s = fma(ref.PhiF[(size_t)fp * Np + a], w.tf[i * Nfp + fp], s);

@@ -20,6 +20,7 @@
 // has the degree-q Gauss-Lobatto Lagrange basis, contracted in two 1D stages like the
 // element basis.
 #include "iedg_internal.cuh"
+#include "iedg_tc.cuh"
 
 namespace iedg {
 namespace {
@@ -129,8 +130,26 @@ k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, 
   const size_t jvs = (size_t)NC * Nq, jfs = (size_t)(1 + d) * Nfp;
   const T* jv = tb.Jv + ((size_t)e * m2 + pair) * jvs;
   const T* jf = tb.Jf + ((size_t)e * m2 + pair) * jfs;
-  for (int idx = tid; idx < NC * Nq; idx += SF_THREADS) cV[idx] = jv[idx];
-  for (int idx = tid; idx < (1 + d) * Nfp; idx += SF_THREADS) cF[idx] = jf[idx];
+  // The pair's point coefficients (two contiguous blocks of the point-Jacobian tables)
+  // are staged by one thread with two bulk copies on the TMA engine while the others
+  // fill the remaining tables; plain loads where an address is not 16-byte aligned.
+  constexpr uint32_t bytesV = NC * Nq * sizeof(T), bytesF = (1 + d) * Nfp * sizeof(T);
+  static_assert(bytesV % 16 == 0 && bytesF % 16 == 0 && (2 * nq1 * np1 * sizeof(T)) % 16 == 0,
+                "bulk copies need 16-byte sizes and offsets");
+  __shared__ __align__(8) uint64_t stage_bar;
+  const bool bulk = ((reinterpret_cast<uintptr_t>(jv) | reinterpret_cast<uintptr_t>(jf) |
+                      reinterpret_cast<uintptr_t>(cV) | reinterpret_cast<uintptr_t>(cF)) & 15) == 0;
+  if (bulk) {
+    if (tid == 0) {
+      tc::mbar_init(&stage_bar, 1);
+      tc::mbar_expect_tx(&stage_bar, bytesV + bytesF);
+      tc::bulk_g2s(cV, jv, bytesV, &stage_bar);
+      tc::bulk_g2s(cF, jf, bytesF, &stage_bar);
+    }
+  } else {
+    for (int idx = tid; idx < NC * Nq; idx += SF_THREADS) cV[idx] = jv[idx];
+    for (int idx = tid; idx < (1 + d) * Nfp; idx += SF_THREADS) cF[idx] = jf[idx];
+  }
   // dfhat/du of the pair: lambda wf on the diagonal (Lax-Friedrichs) or wf S_ik (Roe-type)
   for (int idx = tid; idx < Nfp; idx += SF_THREADS)
     cL[idx] = tb.Su ? tb.Su[((size_t)e * m2 + pair) * Nfp + idx] : ((i == k) ? tb.lamw[e * Nfp + idx] : (T)0);
@@ -145,7 +164,16 @@ k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, 
   T* Se = MIX ? S + tt.soff[e] : S + (LIST ? slot : e) * nn * ld;
   if (rhs64 != nullptr && pair == 0)
     for (int r = tid; r < nn; r += SF_THREADS) Se[r * ld + nn] = (T)rhs64[e * dm.n + r];
-  __syncthreads();
+  __syncthreads();     // also publishes the barrier's initialisation
+  bool late = false;   // the bulk copies did not complete within the wait limit
+  if (bulk) {
+    late = !__syncthreads_and(tc::mbar_wait(&stage_bar, 0, kTcWaitLimit));
+    if (late) {        // same values by plain loads (a late copy writes the same bytes)
+      for (int idx = tid; idx < NC * Nq; idx += SF_THREADS) cV[idx] = jv[idx];
+      for (int idx = tid; idx < (1 + d) * Nfp; idx += SF_THREADS) cF[idx] = jf[idx];
+      __syncthreads();
+    }
+  }
 
   for (int c0 = 0; c0 < ncol_all; c0 += CC) {
     // ---- face parts of the boundary rows for this column chunk
@@ -401,6 +429,7 @@ k_assemble_sf(Dims dm, Phys ph, RefTables ref, AsmTab<T> tb, T* __restrict__ S, 
     }
     __syncthreads();
   }
+  if (late && tid == 0) tc::mbar_wait(&stage_bar, 0, kTcWaitLimit);   // no copy in flight at exit
 }
 
 }  // namespace

@@ -15,6 +15,8 @@
 //    with fvol = -w Jinv[r][j] F_ij, mvol = alpha w (u - u_ref)_i, fsur = wf fhat_i.
 //  * R_q = M (q - q*) where q* = H_l uhat - G_l u is the lifted gradient that makes
 //    R_q vanish (Eq. IEDG a is linear: R_q = M q + B_l u - E_l uhat).
+#include <type_traits>
+
 #include "iedg_internal.cuh"
 
 namespace iedg {
@@ -310,10 +312,13 @@ __device__ __noinline__ void boundary_point(int fk, const double* uh, const doub
   }
 }
 
-// dF[i][j][k] = dF_ij/du_k and dQ[i][j][k][l] = dF_ij/dq_kl at (u, q).
-template <int D>
-__device__ void flux_jacobians(const double* u, const double (*q)[D], const Phys& ph,
-                               double (*dF)[D][D + 2], double (*dQ)[D][D + 2][D]) {
+// The flux Jacobians at (u, q) by forward-mode duals, handed to the caller pass by pass
+// so that no full dF / dQ array is held: on_u(Fd) after the pass over u, with
+// Fd[i][j].t[k] = dF_ij/du_k, then on_q(l, Fd) after the pass over q_{., l}, with
+// Fd[i][j].t[k] = dF_ij/dq_kl.
+template <int D, class OnU, class OnQ>
+__device__ __forceinline__ void flux_jacobians(const double* u, const double (*q)[D], const Phys& ph, OnU on_u,
+                                               OnQ on_q) {
   constexpr int M = D + 2;
   using TD = Dual<M>;
   TD ud[M], qd[M][D], Fd[M][D];
@@ -325,12 +330,7 @@ __device__ void flux_jacobians(const double* u, const double (*q)[D], const Phys
 #pragma unroll
     for (int l = 0; l < D; ++l) qd[k][l] = mkconst<M>(q[k][l]);
   ns_flux<D, TD>(ud, qd, ph, Fd);
-#pragma unroll
-  for (int i = 0; i < M; ++i)
-#pragma unroll
-    for (int j = 0; j < D; ++j)
-#pragma unroll
-      for (int k = 0; k < M; ++k) dF[i][j][k] = Fd[i][j].t[k];
+  on_u(Fd);
   // passes over q_{., l}
 #pragma unroll
   for (int k = 0; k < M; ++k) ud[k] = mkconst<M>(u[k]);
@@ -344,12 +344,7 @@ __device__ void flux_jacobians(const double* u, const double (*q)[D], const Phys
         if (ll == l) qd[k][ll].t[k] = 1.0;
       }
     ns_flux<D, TD>(ud, qd, ph, Fd);
-#pragma unroll
-    for (int i = 0; i < M; ++i)
-#pragma unroll
-      for (int j = 0; j < D; ++j)
-#pragma unroll
-        for (int k = 0; k < M; ++k) dQ[i][j][k][l] = Fd[i][j].t[k];
+    on_q(l, Fd);
   }
 }
 
@@ -357,14 +352,17 @@ __device__ void flux_jacobians(const double* u, const double (*q)[D], const Phys
 // One CTA per element.  jac = false: residual at (u, q).  jac = true: Jacobians at
 // (u, q) into PointJac, right-hand sides -R_u(u, q*), -Rhat(u, q*) into the last
 // column of the bordered element matrix.
-template <int D, int STAB>
+// JAC is a compile-time choice so that the residual form carries none of the Jacobian
+// code's registers and local arrays (it runs at a higher occupancy).
+template <int D, int STAB, bool JAC>
 __global__ void k_points(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ,
                          const int64_t* __restrict__ etrace, const double* __restrict__ U,
                          const double* __restrict__ Q, const double* __restrict__ QS,
-                         const double* __restrict__ UH, const double* __restrict__ UREF, bool jac,
+                         const double* __restrict__ UH, const double* __restrict__ UREF,
                          double* __restrict__ RU, double* __restrict__ RHAT, double* __restrict__ RHS,
                          int64_t rhs_es, int64_t rhs_rs, TraceTab tt) {
   constexpr int M = D + 2;
+  constexpr bool jac = JAC;
   extern __shared__ double sm[];
   const int64_t e = blockIdx.x;
   const int tid = threadIdx.x, nth = blockDim.x;
@@ -437,33 +435,28 @@ __global__ void k_points(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ,
       }
       mvol[i * Nq + g] = has_ref ? ph.alpha * w * du[i] : 0.0;
     }
-    if (jac) {
-      double dF[M][D][M], dQ[M][D][M][D];
-      flux_jacobians<D>(u, q, ph, dF, dQ);
+    if constexpr (JAC) {
       double* jv = PJ.Jv + (size_t)e * M * M * jvs;
+      float* jv32 = PJ.Jv32 ? PJ.Jv32 + (size_t)e * M * M * jvs : nullptr;
+      // entry c of pair (i, k): -w sum_j Ji[r][j] dF_ij/d(unknown), c = r for u, D + l D + r for q_l
+      auto put = [&](int c0, const Dual<M> (*Fd)[D]) {
 #pragma unroll
-      for (int i = 0; i < M; ++i)
+        for (int i = 0; i < M; ++i)
 #pragma unroll
-        for (int k = 0; k < M; ++k) {
-          double* o = jv + (size_t)(i * M + k) * jvs;
-          float* o32 = PJ.Jv32 ? PJ.Jv32 + ((size_t)e * M * M + (size_t)(i * M + k)) * jvs : nullptr;
+          for (int k = 0; k < M; ++k) {
+            double* o = jv + (size_t)(i * M + k) * jvs;
 #pragma unroll
-          for (int r = 0; r < D; ++r) {
-            double s = 0;
+            for (int r = 0; r < D; ++r) {
+              double s = 0;
 #pragma unroll
-            for (int j = 0; j < D; ++j) s += Ji[r][j] * dF[i][j][k];
-            o[(size_t)r * Nq + g] = -w * s;
-            if (o32) o32[(size_t)r * Nq + g] = (float)(-w * s);
-#pragma unroll
-            for (int l = 0; l < D; ++l) {
-              double t = 0;
-#pragma unroll
-              for (int j = 0; j < D; ++j) t += Ji[r][j] * dQ[i][j][k][l];
-              o[(size_t)(D + l * D + r) * Nq + g] = -w * t;
-              if (o32) o32[(size_t)(D + l * D + r) * Nq + g] = (float)(-w * t);
+              for (int j = 0; j < D; ++j) s += Ji[r][j] * Fd[i][j].t[k];
+              o[(size_t)(c0 + r) * Nq + g] = -w * s;
+              if (jv32) jv32[(size_t)(i * M + k) * jvs + (size_t)(c0 + r) * Nq + g] = (float)(-w * s);
             }
           }
-        }
+      };
+      flux_jacobians<D>(u, q, ph, [&](const Dual<M> (*Fd)[D]) { put(0, Fd); },
+                        [&](int l, const Dual<M> (*Fd)[D]) { put(D + l * D, Fd); });
     }
   }
   // ---- face points
@@ -556,29 +549,36 @@ __global__ void k_points(Dims dm, Phys ph, RefTables ref, Geo G, PointJac PJ,
       } else {
         lamd = lf_lambda<D, Dual<M>>(ud, n, ph);
       }
-      double dF[M][D][M], dQ[M][D][M][D];
-      flux_jacobians<D>(uh, q, ph, dF, dQ);
       double* jf = PJ.Jf + (size_t)e * M * M * jfs;
+      float* jf32 = PJ.Jf32 ? PJ.Jf32 + (size_t)e * M * M * jfs : nullptr;
+      // entry 0 of pair (i, k): the stabilisation's derivative + dfhat/du n; entry 1 + l:
+      // dfhat/dq_l n
+      flux_jacobians<D>(
+          uh, q, ph,
+          [&](const Dual<M> (*Fd)[D]) {
 #pragma unroll
-      for (int i = 0; i < M; ++i)
+            for (int i = 0; i < M; ++i)
 #pragma unroll
-        for (int k = 0; k < M; ++k) {
-          double* o = jf + (size_t)(i * M + k) * jfs;
-          float* o32 = PJ.Jf32 ? PJ.Jf32 + ((size_t)e * M * M + (size_t)(i * M + k)) * jfs : nullptr;
-          double s = STAB == 1 ? gd[i].t[k] : lamd.t[k] * (u[i] - uh[i]) - (i == k ? lam : 0.0);
+              for (int k = 0; k < M; ++k) {
+                double s = STAB == 1 ? gd[i].t[k] : lamd.t[k] * (u[i] - uh[i]) - (i == k ? lam : 0.0);
 #pragma unroll
-          for (int j = 0; j < D; ++j) s += dF[i][j][k] * n[j];
-          o[fp] = wf * s;
-          if (o32) o32[fp] = (float)(wf * s);
+                for (int j = 0; j < D; ++j) s += Fd[i][j].t[k] * n[j];
+                jf[(size_t)(i * M + k) * jfs + fp] = wf * s;
+                if (jf32) jf32[(size_t)(i * M + k) * jfs + fp] = (float)(wf * s);
+              }
+          },
+          [&](int l, const Dual<M> (*Fd)[D]) {
 #pragma unroll
-          for (int l = 0; l < D; ++l) {
-            double t = 0;
+            for (int i = 0; i < M; ++i)
 #pragma unroll
-            for (int j = 0; j < D; ++j) t += dQ[i][j][k][l] * n[j];
-            o[(size_t)(1 + l) * Nfp + fp] = wf * t;
-            if (o32) o32[(size_t)(1 + l) * Nfp + fp] = (float)(wf * t);
-          }
-        }
+              for (int k = 0; k < M; ++k) {
+                double t = 0;
+#pragma unroll
+                for (int j = 0; j < D; ++j) t += Fd[i][j].t[k] * n[j];
+                jf[(size_t)(i * M + k) * jfs + (size_t)(1 + l) * Nfp + fp] = wf * t;
+                if (jf32) jf32[(size_t)(i * M + k) * jfs + (size_t)(1 + l) * Nfp + fp] = (float)(wf * t);
+              }
+          });
       PJ.lamw[e * Nfp + fp] = wf * lam;
       if (PJ.lamw32) PJ.lamw32[e * Nfp + fp] = (float)(wf * lam);
     }
@@ -706,12 +706,16 @@ cudaError_t launch_points(iedg_mesh* M, const double* u, const double* q, const 
   double* rhs = M->precision == 0 ? (M->tt.soff ? M->S : M->S + dm.n) : M->rhs64;
   int64_t es = M->precision == 0 ? (int64_t)dm.n * dm.ld : dm.n;
   int64_t rs = M->precision == 0 ? dm.ld : 1;
-  auto kern = dm.d == 2 ? (M->ph.stab == 1 ? k_points<2, 1> : k_points<2, 0>)
-                        : (M->ph.stab == 1 ? k_points<3, 1> : k_points<3, 0>);
+  auto pick = [&](auto j) {
+    constexpr bool J = decltype(j)::value;
+    return dm.d == 2 ? (M->ph.stab == 1 ? k_points<2, 1, J> : k_points<2, 0, J>)
+                     : (M->ph.stab == 1 ? k_points<3, 1, J> : k_points<3, 0, J>);
+  };
+  auto kern = jacobians ? pick(std::true_type{}) : pick(std::false_type{});
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   kern<<<(unsigned)M->E, threads, smem, st>>>(dm, M->ph, M->ref, M->geo, M->pj, M->etrace, u, q, qs, uhat, u_ref,
-                                              jacobians, r_u, rhat, rhs, es, rs, M->tt);
+                                              r_u, rhat, rhs, es, rs, M->tt);
   return cudaGetLastError();
 }
 

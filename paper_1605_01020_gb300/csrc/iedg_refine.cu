@@ -315,6 +315,11 @@ __device__ void element_apply(const Dims& dm, const Phys& ph, const RefTables& r
       for (int g0 = 0; g0 < nq1; ++g0) s = fma(w.sL[g0 * np1 + a0], src[g0], s);
       fu[idx] = s;
     }
+    // The mass term alpha M x = alpha Phi^T (wdet x(g)) (M formed with the same points
+    // and weights) rides on direction 2: after the z stage its L (x) L part joins T_2,
+    // which the y and x stages contract with L (x) L, so it costs one z stage.
+    const bool mass_q = ph.alpha != 0.0 && use_x;
+    const double* wd = G.wdet + (size_t)e * Nq;
     for (int idx = tid; idx < m * 3 * TS; idx += RF_THREADS) {
       int i = idx / (3 * TS), r = (idx / TS) % 3, t = idx % TS;
       int gxy = t % (nq1 * nq1), az = t / (nq1 * nq1);
@@ -322,6 +327,13 @@ __device__ void element_apply(const Dims& dm, const Phys& ph, const RefTables& r
       const double* src = w.tv + (i * d + r) * Nq + gxy;
       double s = 0.0;
       for (int gz = 0; gz < nq1; ++gz) s = fma(X[gz * np1 + az], src[nq1 * nq1 * gz], s);
+      if (r == 2 && mass_q) {
+        const double* xg = w.xv + i * Nq + gxy;
+        double sm2 = 0.0;
+        for (int gz = 0; gz < nq1; ++gz)
+          sm2 = fma(w.sL[gz * np1 + az], wd[gxy + nq1 * nq1 * gz] * xg[nq1 * nq1 * gz], sm2);
+        s = fma(ph.alpha, sm2, s);
+      }
       t1[idx] = s;
     }
     __syncthreads();
@@ -355,7 +367,7 @@ __device__ void element_apply(const Dims& dm, const Phys& ph, const RefTables& r
   for (int idx = tid; idx < m * Np; idx += RF_THREADS) {
     int i = idx / Np, a = idx % Np;
     double s = 0.0;
-    if (ph.alpha != 0.0 && use_x) {
+    if (d != 3 && ph.alpha != 0.0 && use_x) {     // 3D: in the projection stages above
       double t = 0.0;
       for (int b = 0; b < Np; ++b) t = fma(Ms[a * Np + b], w.x[i * Np + b], t);
       s = ph.alpha * t;
